@@ -1,0 +1,52 @@
+"""The oracle's own definitions of the splines and lattices it evaluates.
+
+Written independently of the product package.  Direction sets are those of the
+box splines benchmarked in Sec. 5.1 (tensor-product cubic on the Cartesian
+lattice, the linear rhombic-dodecahedron and the doubled "quintic" box splines
+on BCC, the six-direction truncated-octahedron box spline on FCC) and of the ZP
+element of Fig. 1.
+
+Lattices are stored as unions of Cartesian cosets of scale*Z^s:
+  CC  = Z^3                                   (scale 1, |det L| = 1)
+  BCC = 2Z^3 u (2Z^3 + (1,1,1))               (scale 2, |det L| = 4)
+  FCC = {n in Z^3 : n0+n1+n2 even}            (scale 2, |det L| = 2)
+  Z^2 for the ZP element                      (scale 1, |det L| = 1)
+"""
+from .lib import OrcSpec
+
+E1, E2, E3 = (1, 0, 0), (0, 1, 0), (0, 0, 1)
+
+BCC_DIRS = ((1, 1, 1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1))
+FCC_DIRS = ((1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (0, 1, 1), (0, 1, -1))
+BCC_COSETS = ((0, 0, 0), (1, 1, 1))
+FCC_COSETS = ((0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 1, 1))
+
+
+def tricubic(closed_form: bool = True) -> OrcSpec:
+    """Tensor-product cubic B-spline on Z^3; kind 1 is the closed form, kind 0
+    the same function through the box-spline recurrence (each axis four times)."""
+    dirs = (E1,) * 4 + (E2,) * 4 + (E3,) * 4
+    return OrcSpec(3, dirs, 1.0, 1, ((0, 0, 0),), (1, 1, 1), 1 if closed_form else 0,
+                   "tricubic")
+
+
+def bcc_linear() -> OrcSpec:
+    return OrcSpec(3, BCC_DIRS, 4.0, 2, BCC_COSETS, (1, 1, 1), 0, "bcc_linear")
+
+
+def bcc_quintic() -> OrcSpec:
+    return OrcSpec(3, BCC_DIRS + BCC_DIRS, 4.0, 2, BCC_COSETS, (1, 1, 1), 0, "bcc_quintic")
+
+
+def fcc6() -> OrcSpec:
+    return OrcSpec(3, FCC_DIRS, 2.0, 2, FCC_COSETS, (1, 1, 1), 0, "fcc6")
+
+
+def zp2d() -> OrcSpec:
+    """ZP element of Fig. 1: directions (1,0),(0,1),(1,1),(-1,1) on Z^2."""
+    return OrcSpec(2, ((1, 0), (0, 1), (1, 1), (-1, 1)), 1.0, 1, ((0, 0),), (1, 1, 1), 0,
+                   "zp2d")
+
+
+ALL_3D = {"tricubic": tricubic, "bcc_linear": bcc_linear, "bcc_quintic": bcc_quintic,
+          "fcc6": fcc6}
