@@ -1,0 +1,267 @@
+/*
+ * lattice_spline.h -- C ABI of the B300 lattice spline library.
+ *
+ * Evaluates f(x) = sum_{n in L Z^s} c_n phi(x - n) (Horacsek & Alim, Part II,
+ * Eq. 1) for a piecewise-polynomial basis phi on a lattice L Z^s at many query
+ * points, unrolled as in Algorithm 1: shift into the region of evaluation,
+ * classify into a sub-region, fetch the coefficients of a fixed stencil and
+ * evaluate the sub-region's polynomial.  A spline is described by the
+ * sub-region table of Sec. 3 / Fig. 1; ls_spline_create generates a CUDA C++
+ * kernel specialised to that table (the code generation of Sec. 4), compiles it
+ * for sm_103a and loads it.
+ *
+ * Conventions shared by every entry point:
+ *  - All device pointers are plain CUDA device addresses on the current device;
+ *    all host pointers are ordinary host memory.  No call takes ownership of a
+ *    caller buffer.  Library objects (ls_spline, ls_volume, ls_plan) are owned
+ *    by the library and freed by their destroy call.
+ *  - Points are FP32, row-major, dim values per point (x_0 fastest within a point).
+ *  - A coefficient volume stores one array per Cartesian coset l_j of the
+ *    storage grid scale*Z^dim: element (i_0, .., i_{dim-1}) of array j is the
+ *    coefficient of site scale*i + l_j.  Arrays are coset-major, axis 0
+ *    fastest, all with the same extent.  Sites outside the arrays contribute 0.
+ *  - Calls that take a cudaStream_t are asynchronous on that stream (0 = the
+ *    legacy default stream).  They return an ls_status describing argument
+ *    validation and launch; a fault found by a kernel is not reported here.
+ *  - No call aborts or traps; errors are returned as ls_status and a message
+ *    readable with ls_last_error() (thread-local).
+ */
+#ifndef LATTICE_SPLINE_H
+#define LATTICE_SPLINE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ls_spline_s *ls_spline;   /* generated + loaded kernels for one table */
+typedef struct ls_volume_s *ls_volume;   /* coefficients of one spline on one grid   */
+typedef struct ls_plan_s *ls_plan;       /* a batched persistent launch              */
+typedef void *ls_stream;                 /* a cudaStream_t                           */
+
+typedef enum {
+    LS_OK = 0,
+    LS_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad enum                 */
+    LS_ERR_BAD_TABLE = 2,     /* inconsistent sub-region table                     */
+    LS_ERR_UNSUPPORTED = 3,   /* valid but not supported (e.g. dim 1, > 64 sites)  */
+    LS_ERR_OOM = 4,           /* device or host allocation failed                 */
+    LS_ERR_CUDA = 5,          /* a CUDA runtime call failed (message has details)  */
+    LS_ERR_COMPILE = 6,       /* NVRTC rejected the generated source              */
+    LS_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up               */
+    LS_ERR_DEVICE = 8         /* a kernel reported a fault in its status word      */
+} ls_status;
+
+typedef enum { LS_F32 = 0, LS_BF16 = 1, LS_F16 = 2, LS_F64 = 3 } ls_dtype;
+
+typedef enum {
+    LS_ROE_PARALLELEPIPED = 0, /* k = floor(x) on the storage grid (Cartesian, scale 1)      */
+    LS_ROE_VORONOI = 1         /* k = nearest lattice site (Voronoi cell of the lattice)     */
+} ls_roe;
+
+typedef enum {
+    LS_FOLD_NONE = 0,          /* one sub-region: the whole region of evaluation             */
+    LS_FOLD_SIGNED_PERM = 1    /* sub-regions are the images of y0 >= y1 >= .. >= 0 under the
+                                  2^s s! signed permutations; T of Algorithm 1 is computed by
+                                  sorting |y| instead of a table lookup                       */
+} ls_fold;
+
+/*
+ * One reference sub-region (Fig. 1 table row without a transform; Algorithm 1,
+ * psi_i).  On it, f(y) = sum_j c[k + T^T s_j] * w_j(T y - center), where k is the
+ * shift into the region of evaluation, T the sub-region transform and
+ *     w_j(u) = sum_a coef[j * n_monos + a] * prod_i u_i^{mono_exp[a * dim + i]}.
+ * sites: n_sites * dim lattice offsets s_j (Cartesian, integer).
+ */
+typedef struct {
+    int32_t n_sites;
+    const int32_t *sites;
+    int32_t n_monos;
+    const int32_t *mono_exp;
+    const double *coef;
+    double center[3];
+} ls_ref_region;
+
+/*
+ * Optional separable form of a tensor-product spline: along axis i,
+ * w_j(u) = sum_a coef[j * (degree + 1) + a] u^a with u = y_i - center, for the
+ * 1D sites sites[j]; the 3D weight of site (s_0, s_1, s_2) is the product.
+ */
+typedef struct {
+    int32_t n_sites;
+    const int32_t *sites;
+    int32_t degree;
+    const double *coef;
+    double center;
+} ls_axis_factor;
+
+/*
+ * Lattice + spline descriptor: a generator matrix, the coset offsets of the
+ * storage grid and the sub-region table (Sec. 3, Algorithm 1).
+ *   planes: n_planes * (dim + 1) doubles (p_i, d_i); bit i of q is set iff
+ *           p_i . y - d_i >= 0 for the folded point y (Sec. 4.1, sub-region
+ *           membership); the reference sub-region is sigma[q % bsp_mod].
+ *   separable: NULL, or dim axis factors used instead of ref (LS_FOLD_NONE only).
+ */
+typedef struct {
+    const char *name;                  /* nullable; [A-Za-z0-9_]{1,40}, used in kernel names */
+    int32_t dim;                       /* 2 or 3 */
+    int32_t roe;                       /* ls_roe */
+    int32_t fold;                      /* ls_fold */
+    int32_t scale;                     /* storage grid spacing (1 or 2) */
+    double generator[9];               /* L, column-major (column j at [3j..3j+2]) */
+    int32_t n_cosets;                  /* 1..8 */
+    const int32_t *coset_offsets;      /* n_cosets * dim, each in [0, scale) */
+    int32_t n_planes;                  /* 0..8 */
+    const double *planes;
+    int32_t bsp_mod;                   /* >= 1 */
+    const int8_t *sigma;               /* bsp_mod entries, -1 = unused */
+    int32_t n_ref;                     /* 1..4 */
+    const ls_ref_region *ref;
+    const ls_axis_factor *separable;
+} ls_spline_desc;
+
+/* Kernel variants a spline can be generated with. */
+typedef struct {
+    int32_t block;                     /* threads per block (default 256) */
+    int32_t pts_per_thread;            /* points per thread per loop trip (1, 2) */
+    int32_t branchy;                   /* K > 1: 0 = evaluate all, select; 1 = branch */
+    int32_t min_blocks;                /* __launch_bounds__ minimum blocks per SM (0 = none) */
+} ls_variant;
+
+/* ---- status ---------------------------------------------------------------- */
+const char *ls_status_str(ls_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char *ls_last_error(void);
+int32_t ls_abi_version(void);
+
+/* ---- splines ----------------------------------------------------------------- */
+/*
+ * Validate the table, generate the specialised CUDA C++ (stencil and polynomials
+ * unrolled, tables as immediates; Sec. 4.1-4.4), compile it with NVRTC for
+ * sm_103a and load it on the current device.  coef_dtype selects the storage
+ * type the kernels read (LS_F32, LS_BF16, LS_F16); arithmetic is FP32.
+ * variant may be NULL (defaults).  Compiled cubins are cached on disk in the
+ * directory named by LS_KERNEL_CACHE (default: a kcache/ folder beside the
+ * library).  The descriptor is copied; the caller keeps ownership of it.
+ * Errors: INVALID_ARG / BAD_TABLE / UNSUPPORTED / COMPILE / CUDA.
+ */
+ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype coef_dtype,
+                           const ls_variant *variant, ls_spline *out);
+ls_status ls_spline_destroy(ls_spline s);
+/* Generate and compile into the on-disk cache only (no device needed): lets a
+ * build step pay the NVRTC cost ahead of the first ls_spline_create. */
+ls_status ls_spline_precompile(const ls_spline_desc *desc, ls_dtype coef_dtype,
+                               const ls_variant *variant);
+/* Generated source (NUL-terminated, owned by the spline) for inspection/tests. */
+const char *ls_spline_source(ls_spline s);
+/* Counts the generator computed: stencil size (union over reference regions),
+ * FP32 FMAs per point for f, for f + grad f, registers per thread of the eval kernel. */
+ls_status ls_spline_info(ls_spline s, int32_t *n_sites, int32_t *fma_value,
+                         int32_t *fma_grad, int32_t *regs_eval);
+
+/* ---- coefficient volumes ----------------------------------------------------------- */
+/*
+ * A volume is a view of n_cosets coefficient arrays of extent ext[0..dim-1]
+ * in the spline's coef_dtype.  ls_volume_create allocates them (library-owned,
+ * zero-filled); ls_volume_wrap uses a caller device buffer of
+ * n_cosets * prod(ext) elements, which must outlive the volume.
+ */
+ls_status ls_volume_create(ls_spline s, const int64_t *ext, ls_volume *out);
+ls_status ls_volume_wrap(ls_spline s, const int64_t *ext, void *device_coef, ls_volume *out);
+/* Copy (and convert) n_cosets*prod(ext) values of src_dtype from src (host or
+ * device) into the volume. */
+ls_status ls_volume_upload(ls_volume v, const void *src, int32_t src_is_device,
+                           ls_dtype src_dtype, ls_stream stream);
+void *ls_volume_device_ptr(ls_volume v);
+ls_status ls_volume_destroy(ls_volume v);
+
+/* ---- evaluation (Algorithm 1) ----------------------------------------------------- */
+/* out[i] = f(pts[i]) for i < n.  pts: n*dim device floats; out: n device floats. */
+ls_status ls_eval(ls_volume v, const float *pts, int64_t n, float *out, ls_stream stream);
+/*
+ * f and its gradient from the differentiated sub-region polynomials (Sec. 3:
+ * derivatives of the per-region polynomials, symmetry still applies):
+ * grad[i*dim + d] = df/dx_d (pts[i]).  val may be NULL.
+ */
+ls_status ls_eval_grad(ls_volume v, const float *pts, int64_t n, float *val, float *grad,
+                       ls_stream stream);
+/*
+ * Same as ls_eval with HOST buffers: copies pts to the device, evaluates and
+ * copies out back, all on stream; returns after the stream has finished.
+ * Uses a device staging buffer owned by the volume (grown on demand).
+ */
+ls_status ls_eval_host(ls_volume v, const float *host_pts, int64_t n, float *host_out,
+                       ls_stream stream);
+
+/*
+ * Adjoint with respect to the coefficients (transposed stencil):
+ *     dcoef[site n] += sum_i gout[i] * phi(pts[i] - n)
+ * dcoef: FP32 device array with the volume's layout (n_cosets * prod(ext)),
+ * accumulated into.  deterministic = 0: atomic scatter-add (result order-
+ * dependent in the last bits).  deterministic = 1: the points are binned by
+ * their region-of-evaluation site and every coefficient sums its contributions
+ * in a fixed order (bitwise reproducible); needs scratch, see ls_adjoint_scratch_bytes.
+ * scratch: device buffer of at least ls_adjoint_scratch_bytes(v, n) bytes
+ * (NULL: the call allocates and frees it).
+ */
+ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int64_t n,
+                          float *dcoef, int32_t deterministic, void *scratch,
+                          ls_stream stream);
+size_t ls_adjoint_scratch_bytes(ls_volume v, int64_t n);
+
+/* ---- Morton order of points -------------------------------------------------------- */
+/*
+ * perm[0..n) = indices of pts ordered by the 30-bit Morton code of the cell
+ * floor((x - origin) / cell) (10 bits per axis, clamped to [0, 1023]); ties keep
+ * input order (stable LSD radix sort).  keys_out (nullable) receives the sorted keys.
+ * scratch: device buffer of ls_morton_scratch_bytes(n) bytes (NULL: allocated).
+ */
+ls_status ls_morton_sort(const float *pts, int64_t n, const float *origin, float cell,
+                         int32_t *perm, uint32_t *keys_out, void *scratch, ls_stream stream);
+size_t ls_morton_scratch_bytes(int64_t n);
+/* dst[i] = src[perm[i]] for rows of `width` floats (gather), or the inverse scatter. */
+ls_status ls_permute_rows(const float *src, const int32_t *perm, int64_t n, int32_t width,
+                          int32_t inverse, float *dst, ls_stream stream);
+
+/* ---- batched persistent evaluation ------------------------------------------------ */
+/*
+ * One plan evaluates n_vol volumes (any mix of splines whose kernels were
+ * generated in the same ls_plan_create), each at its own point batch, in ONE
+ * persistent launch: blocks pull (volume, tile) items from a device work list.
+ * pts[v], out[v]: device pointers; n[v]: point counts.  The plan copies the
+ * arrays; the buffers must stay valid while the plan is launched.
+ * ls_plan_launch only enqueues one kernel (no allocation, no host sync) and may
+ * be captured into a CUDA graph.  tile: points per work item (0 = autotuned).
+ */
+ls_status ls_plan_create(int32_t n_vol, const ls_volume *vols, const float *const *pts,
+                         const int64_t *n, float *const *out, int32_t tile, ls_plan *plan);
+ls_status ls_plan_launch(ls_plan plan, ls_stream stream);
+/* Status word of the last launch (LS_OK or LS_ERR_TIMEOUT); synchronises the stream. */
+ls_status ls_plan_status(ls_plan plan, ls_stream stream);
+ls_status ls_plan_destroy(ls_plan plan);
+
+/* ---- least-squares fit -------------------------------------------------------------- */
+/*
+ * Fit coefficients c to samples y_i at pts_i by CGLS on
+ *     min_c ||A c - y||^2 + lambda ||c||^2,   A[i, n] = phi(pts_i - n),
+ * with A c from ls_eval and A^T r from ls_adjoint_coef (deterministic when
+ * deterministic = 1).  Dot products and norms are FP64 on the device.  coef
+ * (the volume's FP32 array) holds the initial guess and receives the result.
+ * Stops after max_iter iterations or when ||A^T r|| <= rel_tol ||A^T y||.
+ * resid_hist (host, nullable, max_iter + 1 doubles): ||A^T r||_2 per iteration.
+ * iters (host, nullable): iterations done.
+ */
+ls_status ls_cg_fit(ls_volume v, const float *pts, const float *y, int64_t n, double lambda,
+                    int32_t max_iter, double rel_tol, int32_t deterministic,
+                    double *resid_hist, int32_t *iters, ls_stream stream);
+
+/* ---- device helpers used by the FP64 parts of the fit -------------------------------- */
+/* *result (device double) = sum_i a[i] * b[i] accumulated in FP64. */
+ls_status ls_dot_f64(const float *a, const float *b, int64_t n, double *result, ls_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LATTICE_SPLINE_H */

@@ -1,0 +1,198 @@
+"""Python API over the C ABI: splines, coefficient volumes, evaluation.
+
+PyTorch provides device memory and streams; every computation runs in the
+library's kernels (libls.so and the kernels it generates).  There is no CPU
+fallback: without a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import pickle
+from typing import Dict, Optional, Sequence, Tuple
+
+import torch
+
+from . import _abi
+from .splines import BY_NAME
+from .subregions import Table, build_table
+
+_TABLE_CACHE: Dict[str, Table] = {}
+_TABLE_VERSION = 2
+_CACHE_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "kcache")
+
+DTYPES = {"f32": _abi.LS_F32, "bf16": _abi.LS_BF16, "f16": _abi.LS_F16}
+TORCH_DTYPES = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+
+
+def table(name: str) -> Table:
+    """Sub-region table of a named spline (built once, cached on disk)."""
+    if name in _TABLE_CACHE:
+        return _TABLE_CACHE[name]
+    path = os.path.join(_CACHE_DIR, f"table_{name}_v{_TABLE_VERSION}.pkl")
+    t = None
+    if os.path.exists(path):
+        try:
+            with open(path, "rb") as f:
+                t = pickle.load(f)
+        except Exception:
+            t = None
+    if t is None:
+        t = build_table(BY_NAME[name])
+        try:
+            os.makedirs(_CACHE_DIR, exist_ok=True)
+            tmp = path + f".tmp{os.getpid()}"
+            with open(tmp, "wb") as f:
+                pickle.dump(t, f)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+    _TABLE_CACHE[name] = t
+    return t
+
+
+def _stream(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+class Spline:
+    """Generated, compiled and loaded kernels of one spline for one storage dtype."""
+
+    def __init__(self, name: str, dtype: str = "f32", block: int = 256, branchy: int = 0,
+                 min_blocks: int = 0, kernel_name: Optional[str] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("lattice spline kernels need a CUDA device")
+        self.name = name
+        self.dtype = dtype
+        self.table = table(name)
+        self.dim = self.table.spline.lattice.dim
+        self.n_cosets = len(self.table.spline.lattice.cosets)
+        self.scale = self.table.spline.lattice.scale
+        kname = kernel_name or f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + \
+            ("_br" if branchy else "") + (f"_m{min_blocks}" if min_blocks else "")
+        self._desc = _abi.DescHolder(self.table, kname)
+        var = _abi.variant(block=block, branchy=branchy, min_blocks=min_blocks)
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),
+                                               ctypes.byref(h)), "ls_spline_create")
+        self.handle = h
+
+    def info(self):
+        n, fv, fg, regs = (ctypes.c_int32() for _ in range(4))
+        _abi.check(_abi.lib().ls_spline_info(self.handle, ctypes.byref(n), ctypes.byref(fv), ctypes.byref(fg),
+                                             ctypes.byref(regs)), "ls_spline_info")
+        return {"n_sites": n.value, "fma_value": fv.value, "fma_grad": fg.value, "regs_eval": regs.value}
+
+    def source(self) -> str:
+        return _abi.lib().ls_spline_source(self.handle).decode()
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _abi.lib().ls_spline_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+class Volume:
+    """Coefficients of a spline on n_cosets arrays of extent ext (axis 0 fastest).
+
+    ``coef`` (device tensor of the spline's storage dtype, shape
+    (n_cosets, ext[dim-1], ..., ext[0])) is wrapped without a copy; otherwise a
+    zero volume is allocated by the library.
+    """
+
+    def __init__(self, spline: Spline, ext: Sequence[int], coef: Optional[torch.Tensor] = None):
+        self.spline = spline
+        self.ext = tuple(int(e) for e in ext) + (1,) * (3 - len(ext))
+        e64 = (ctypes.c_int64 * 3)(*self.ext)
+        h = ctypes.c_void_p()
+        if coef is not None:
+            want = spline.n_cosets
+            for i in range(spline.dim):
+                want *= self.ext[i]
+            if not coef.is_cuda or not coef.is_contiguous() or coef.numel() != want or \
+                    coef.dtype != TORCH_DTYPES[spline.dtype]:
+                raise ValueError("coef must be a contiguous CUDA tensor of the spline's dtype and volume size")
+            self.coef = coef
+            _abi.check(_abi.lib().ls_volume_wrap(spline.handle, e64, _ptr(coef), ctypes.byref(h)), "ls_volume_wrap")
+        else:
+            self.coef = None
+            _abi.check(_abi.lib().ls_volume_create(spline.handle, e64, ctypes.byref(h)), "ls_volume_create")
+        self.handle = h
+
+    @property
+    def n_coef(self) -> int:
+        n = self.spline.n_cosets
+        for i in range(self.spline.dim):
+            n *= self.ext[i]
+        return n
+
+    def upload(self, src: torch.Tensor, stream=None):
+        dt = {torch.float32: _abi.LS_F32, torch.float64: _abi.LS_F64, torch.bfloat16: _abi.LS_BF16,
+              torch.float16: _abi.LS_F16}[src.dtype]
+        src = src.contiguous()
+        if src.numel() != self.n_coef:
+            raise ValueError("upload size mismatch")
+        _abi.check(_abi.lib().ls_volume_upload(self.handle, _ptr(src), int(src.is_cuda), dt, _stream(stream)),
+                   "ls_volume_upload")
+        if not src.is_cuda:
+            torch.cuda.current_stream().synchronize()
+
+    def eval(self, pts: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        pts = _check_pts(pts, self.spline.dim)
+        n = pts.shape[0]
+        if out is None:
+            out = torch.empty(n, device=pts.device, dtype=torch.float32)
+        _abi.check(_abi.lib().ls_eval(self.handle, _ptr(pts), n, _ptr(out), _stream(stream)), "ls_eval")
+        return out
+
+    def eval_grad(self, pts: torch.Tensor, want_value: bool = True, stream=None):
+        pts = _check_pts(pts, self.spline.dim)
+        n = pts.shape[0]
+        val = torch.empty(n, device=pts.device, dtype=torch.float32) if want_value else None
+        grad = torch.empty(n, self.spline.dim, device=pts.device, dtype=torch.float32)
+        _abi.check(_abi.lib().ls_eval_grad(self.handle, _ptr(pts), n, _ptr(val), _ptr(grad), _stream(stream)),
+                   "ls_eval_grad")
+        return val, grad
+
+    def eval_host(self, pts_host, out_host, stream=None):
+        """Host buffers in, host buffer out (copies inside the call)."""
+        n = pts_host.shape[0]
+        _abi.check(_abi.lib().ls_eval_host(self.handle, ctypes.c_void_p(pts_host.data_ptr()), n,
+                                           ctypes.c_void_p(out_host.data_ptr()), _stream(stream)), "ls_eval_host")
+        return out_host
+
+    def adjoint(self, pts: torch.Tensor, gout: torch.Tensor, dcoef: Optional[torch.Tensor] = None,
+                deterministic: bool = False, stream=None) -> torch.Tensor:
+        pts = _check_pts(pts, self.spline.dim)
+        gout = gout.contiguous().float()
+        if dcoef is None:
+            dcoef = torch.zeros(self.n_coef, device=pts.device, dtype=torch.float32)
+        _abi.check(_abi.lib().ls_adjoint_coef(self.handle, _ptr(pts), _ptr(gout), pts.shape[0], _ptr(dcoef),
+                                              int(deterministic), ctypes.c_void_p(0), _stream(stream)),
+                   "ls_adjoint_coef")
+        return dcoef
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _abi.lib().ls_volume_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def _check_pts(pts: torch.Tensor, dim: int) -> torch.Tensor:
+    if not pts.is_cuda or pts.dtype != torch.float32 or pts.dim() != 2 or pts.shape[1] != dim:
+        raise ValueError(f"points must be a CUDA float32 tensor of shape (n, {dim})")
+    return pts.contiguous()

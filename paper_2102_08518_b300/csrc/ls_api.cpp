@@ -1,0 +1,590 @@
+// C ABI of the lattice spline library: descriptor validation, kernel
+// generation/loading, coefficient volumes and launches.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ls_internal.h"
+#include "ls_kernels.h"
+
+namespace {
+thread_local std::string g_err;
+
+struct EvalArgsH {
+    const float *pts;
+    float *out;
+    float *grad;
+    const void *coef;
+    long long n;
+    int e0, e1, e2, cstride;
+};
+struct AdjArgsH {
+    const float *pts;
+    const float *gout;
+    float *dcoef;
+    long long n;
+    int e0, e1, e2, cstride;
+};
+
+const char *dtype_tag(ls_dtype d)
+{
+    switch (d) {
+    case LS_F32: return "f32";
+    case LS_BF16: return "bf16";
+    case LS_F16: return "f16";
+    default: return "x";
+    }
+}
+
+size_t dtype_size(ls_dtype d)
+{
+    switch (d) {
+    case LS_F32: return 4;
+    case LS_BF16: return 2;
+    case LS_F16: return 2;
+    case LS_F64: return 8;
+    }
+    return 0;
+}
+
+ls_status cuda_fail(cudaError_t e, const char *what)
+{
+    return ls_fail(LS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool valid_name(const char *n)
+{
+    if (!n) return true;
+    size_t len = std::strlen(n);
+    if (len == 0 || len > 40) return false;
+    for (size_t i = 0; i < len; ++i) {
+        char c = n[i];
+        if (!((c >= 'a' && c <= 'z') || (c >= 'A' && c <= 'Z') || (c >= '0' && c <= '9') || c == '_'))
+            return false;
+    }
+    return true;
+}
+
+// Copy and validate a descriptor.
+ls_status copy_desc(const ls_spline_desc *d, ls::Table &t)
+{
+    if (!d) return ls_fail(LS_ERR_INVALID_ARG, "descriptor is NULL");
+    if (!valid_name(d->name)) return ls_fail(LS_ERR_INVALID_ARG, "name must match [A-Za-z0-9_]{1,40}");
+    t.name = d->name ? d->name : "";
+    if (d->dim != 2 && d->dim != 3) return ls_fail(LS_ERR_UNSUPPORTED, "dim must be 2 or 3");
+    t.dim = d->dim;
+    if (d->roe != LS_ROE_PARALLELEPIPED && d->roe != LS_ROE_VORONOI)
+        return ls_fail(LS_ERR_INVALID_ARG, "roe must be LS_ROE_PARALLELEPIPED or LS_ROE_VORONOI");
+    if (d->fold != LS_FOLD_NONE && d->fold != LS_FOLD_SIGNED_PERM)
+        return ls_fail(LS_ERR_INVALID_ARG, "fold must be LS_FOLD_NONE or LS_FOLD_SIGNED_PERM");
+    t.roe = d->roe;
+    t.fold = d->fold;
+    if (d->scale != 1 && d->scale != 2) return ls_fail(LS_ERR_UNSUPPORTED, "scale must be 1 or 2");
+    t.scale = d->scale;
+    std::memcpy(t.L, d->generator, sizeof t.L);
+    if (d->n_cosets < 1 || d->n_cosets > 8 || !d->coset_offsets)
+        return ls_fail(LS_ERR_INVALID_ARG, "n_cosets must be 1..8 with coset_offsets");
+    if (d->scale == 1 && d->n_cosets != 1) return ls_fail(LS_ERR_BAD_TABLE, "scale 1 has exactly one coset");
+    for (int j = 0; j < d->n_cosets; ++j) {
+        ls::I3 l{0, 0, 0};
+        for (int i = 0; i < d->dim; ++i) {
+            int v = d->coset_offsets[j * d->dim + i];
+            if (v < 0 || v >= d->scale) return ls_fail(LS_ERR_BAD_TABLE, "coset offset outside [0, scale)");
+            l[i] = v;
+        }
+        for (auto &o : t.cosets)
+            if (o == l) return ls_fail(LS_ERR_BAD_TABLE, "duplicate coset offset");
+        t.cosets.push_back(l);
+    }
+    if (d->roe == LS_ROE_PARALLELEPIPED) {
+        if (d->scale != 1) return ls_fail(LS_ERR_UNSUPPORTED, "parallelepiped ROE needs the Cartesian grid (scale 1)");
+        for (int c = 0; c < d->dim; ++c)
+            for (int r = 0; r < d->dim; ++r)
+                if (d->generator[3 * c + r] != (r == c ? 1.0 : 0.0))
+                    return ls_fail(LS_ERR_UNSUPPORTED, "parallelepiped ROE needs L = I");
+    }
+    if (d->n_ref < 1 || d->n_ref > 4) return ls_fail(LS_ERR_UNSUPPORTED, "n_ref must be 1..4");
+    if (d->n_planes < 0 || d->n_planes > 4) return ls_fail(LS_ERR_UNSUPPORTED, "n_planes must be 0..4");
+    if (d->bsp_mod < 1 || d->bsp_mod > 16) return ls_fail(LS_ERR_UNSUPPORTED, "bsp_mod must be 1..16");
+    if (d->n_planes > 0 && !d->planes) return ls_fail(LS_ERR_INVALID_ARG, "planes is NULL");
+    if (!d->sigma) return ls_fail(LS_ERR_INVALID_ARG, "sigma is NULL");
+    for (int p = 0; p < d->n_planes; ++p) {
+        std::array<double, 4> pl{0, 0, 0, 0};
+        for (int i = 0; i < d->dim; ++i) pl[i] = d->planes[p * (d->dim + 1) + i];
+        pl[3] = d->planes[p * (d->dim + 1) + d->dim];
+        t.planes.push_back(pl);
+    }
+    t.bsp_mod = d->bsp_mod;
+    bool any_used = false;
+    for (int q = 0; q < d->bsp_mod; ++q) {
+        int v = d->sigma[q];
+        if (v < -1 || v >= d->n_ref) return ls_fail(LS_ERR_BAD_TABLE, "sigma entry outside [-1, n_ref)");
+        any_used = any_used || v >= 0;
+        t.sigma.push_back(v);
+    }
+    if (!any_used) return ls_fail(LS_ERR_BAD_TABLE, "sigma maps nothing to a reference sub-region");
+    if (d->n_ref > 1 && d->n_planes == 0) return ls_fail(LS_ERR_BAD_TABLE, "several reference sub-regions need BSP planes");
+    if (!d->ref) return ls_fail(LS_ERR_INVALID_ARG, "ref is NULL");
+    for (int k = 0; k < d->n_ref; ++k) {
+        const ls_ref_region &r = d->ref[k];
+        if (r.n_sites < 1 || r.n_sites > 128 || !r.sites)
+            return ls_fail(LS_ERR_UNSUPPORTED, "a reference sub-region needs 1..128 sites");
+        if (r.n_monos < 1 || r.n_monos > 256 || !r.mono_exp || !r.coef)
+            return ls_fail(LS_ERR_UNSUPPORTED, "a reference sub-region needs 1..256 monomials");
+        ls::RefRegion rr;
+        for (int j = 0; j < r.n_sites; ++j) {
+            ls::I3 s{0, 0, 0};
+            for (int i = 0; i < d->dim; ++i) {
+                s[i] = r.sites[j * d->dim + i];
+                if (std::abs(s[i]) > 16) return ls_fail(LS_ERR_UNSUPPORTED, "site offset beyond 16");
+            }
+            for (auto &o : rr.sites)
+                if (o == s) return ls_fail(LS_ERR_BAD_TABLE, "duplicate site in a reference sub-region");
+            rr.sites.push_back(s);
+        }
+        for (int a = 0; a < r.n_monos; ++a) {
+            ls::I3 m{0, 0, 0};
+            int deg = 0;
+            for (int i = 0; i < d->dim; ++i) {
+                m[i] = r.mono_exp[a * d->dim + i];
+                if (m[i] < 0 || m[i] > 12) return ls_fail(LS_ERR_BAD_TABLE, "monomial exponent outside 0..12");
+                deg += m[i];
+            }
+            for (auto &o : rr.mono)
+                if (o == m) return ls_fail(LS_ERR_BAD_TABLE, "duplicate monomial");
+            rr.mono.push_back(m);
+            rr.degree = std::max(rr.degree, deg);
+        }
+        rr.coef.assign(r.coef, r.coef + (size_t)r.n_sites * r.n_monos);
+        for (double v : rr.coef)
+            if (!std::isfinite(v)) return ls_fail(LS_ERR_BAD_TABLE, "non-finite polynomial coefficient");
+        for (int i = 0; i < 3; ++i) rr.center[i] = i < d->dim ? r.center[i] : 0.0;
+        t.ref.push_back(rr);
+    }
+    if (d->separable) {
+        if (d->fold != LS_FOLD_NONE || d->roe != LS_ROE_PARALLELEPIPED || d->n_ref != 1)
+            return ls_fail(LS_ERR_UNSUPPORTED, "separable form needs fold none, parallelepiped ROE, one region");
+        for (int i = 0; i < d->dim; ++i) {
+            const ls_axis_factor &a = d->separable[i];
+            if (a.n_sites < 1 || a.n_sites > 8 || !a.sites || !a.coef || a.degree < 0 || a.degree > 8)
+                return ls_fail(LS_ERR_UNSUPPORTED, "axis factor needs 1..8 sites, degree 0..8");
+            ls::Axis ax;
+            ax.sites.assign(a.sites, a.sites + a.n_sites);
+            ax.degree = a.degree;
+            ax.coef.assign(a.coef, a.coef + (size_t)a.n_sites * (a.degree + 1));
+            ax.center = a.center;
+            t.sep.push_back(ax);
+        }
+    }
+    return LS_OK;
+}
+
+int grid_for(long long n, int block, int sms, int per_sm)
+{
+    long long need = (n + block - 1) / block;
+    long long cap = (long long)sms * std::max(per_sm, 1);
+    if (need < 1) need = 1;
+    return (int)std::min(need, cap);
+}
+
+ls_status launch(cudaKernel_t k, int grid, int block, void *args, cudaStream_t stream)
+{
+    void *argv[] = {args};
+    cudaError_t e = cudaLaunchKernel((const void *)k, dim3(grid), dim3(block), argv, 0, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernel");
+    return LS_OK;
+}
+
+ls_status get_kernel(ls_spline_s *s, const char *what, cudaKernel_t &k, int &per_sm)
+{
+    std::string nm = std::string("ls_") + what;
+    if (!s->table.name.empty()) nm += "__" + s->table.name;
+    cudaError_t e = cudaLibraryGetKernel(&k, s->mod.lib, nm.c_str());
+    if (e != cudaSuccess) return cuda_fail(e, ("cudaLibraryGetKernel " + nm).c_str());
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)k, s->var.block, 0);
+    if (e != cudaSuccess || nb <= 0) {
+        cudaGetLastError();
+        nb = 4;
+    }
+    per_sm = nb;
+    return LS_OK;
+}
+
+ls_variant default_variant(const ls_variant *v)
+{
+    ls_variant r{256, 1, 0, 0};
+    if (v) {
+        if (v->block > 0) r.block = v->block;
+        if (v->pts_per_thread > 0) r.pts_per_thread = v->pts_per_thread;
+        r.branchy = v->branchy;
+        r.min_blocks = v->min_blocks;
+    }
+    return r;
+}
+
+}  // namespace
+
+ls_status ls_fail(ls_status s, const std::string &msg)
+{
+    g_err = msg;
+    return s;
+}
+
+extern "C" {
+
+const char *ls_status_str(ls_status s)
+{
+    switch (s) {
+    case LS_OK: return "ok";
+    case LS_ERR_INVALID_ARG: return "invalid argument";
+    case LS_ERR_BAD_TABLE: return "inconsistent sub-region table";
+    case LS_ERR_UNSUPPORTED: return "unsupported";
+    case LS_ERR_OOM: return "out of memory";
+    case LS_ERR_CUDA: return "CUDA error";
+    case LS_ERR_COMPILE: return "kernel compilation failed";
+    case LS_ERR_TIMEOUT: return "device wait timed out";
+    case LS_ERR_DEVICE: return "device-side fault reported";
+    }
+    return "unknown status";
+}
+
+const char *ls_last_error(void) { return g_err.c_str(); }
+
+int32_t ls_abi_version(void) { return 1; }
+
+ls_status ls_spline_precompile(const ls_spline_desc *desc, ls_dtype dt, const ls_variant *variant)
+{
+    ls::Table t;
+    ls_status st = copy_desc(desc, t);
+    if (st != LS_OK) return st;
+    if (dt != LS_F32 && dt != LS_BF16 && dt != LS_F16) return ls_fail(LS_ERR_UNSUPPORTED, "coef dtype");
+    ls_variant var = default_variant(variant);
+    ls::Generated g = ls::generate(t, dt, var);
+    std::vector<char> cubin;
+    std::string err;
+    st = ls::get_cubin(g.source, "ls_" + (t.name.empty() ? std::string("spline") : t.name) + "_" + dtype_tag(dt),
+                       cubin, err);
+    if (st != LS_OK) return ls_fail(st, err);
+    return LS_OK;
+}
+
+ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_variant *variant, ls_spline *out)
+{
+    if (!out) return ls_fail(LS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (dt != LS_F32 && dt != LS_BF16 && dt != LS_F16)
+        return ls_fail(LS_ERR_UNSUPPORTED, "coefficient storage must be LS_F32, LS_BF16 or LS_F16");
+    auto *s = new (std::nothrow) ls_spline_s;
+    if (!s) return ls_fail(LS_ERR_OOM, "host allocation");
+    ls_status st = copy_desc(desc, s->table);
+    if (st != LS_OK) {
+        delete s;
+        return st;
+    }
+    s->dtype = dt;
+    s->var = default_variant(variant);
+    if (s->var.block % 32 || s->var.block > 1024) {
+        delete s;
+        return ls_fail(LS_ERR_INVALID_ARG, "block must be a multiple of 32, <= 1024");
+    }
+    s->gen = ls::generate(s->table, dt, s->var);
+    cudaError_t ce = cudaGetDevice(&s->device);
+    if (ce != cudaSuccess) {
+        delete s;
+        return cuda_fail(ce, "cudaGetDevice");
+    }
+    ce = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (ce != cudaSuccess) {
+        delete s;
+        return cuda_fail(ce, "cudaDeviceGetAttribute");
+    }
+    std::string err;
+    std::string tag = "ls_" + (s->table.name.empty() ? std::string("spline") : s->table.name) + "_" + dtype_tag(dt);
+    st = ls::compile_and_load(s->gen.source, tag, s->mod, err);
+    if (st != LS_OK) {
+        delete s;
+        return ls_fail(st, err);
+    }
+    if ((st = get_kernel(s, "eval", s->mod.eval, s->mod.blocks_per_sm_eval)) != LS_OK ||
+        (st = get_kernel(s, "eval_grad", s->mod.eval_grad, s->mod.blocks_per_sm_grad)) != LS_OK ||
+        (st = get_kernel(s, "adjoint_atomic", s->mod.adj_atomic, s->mod.blocks_per_sm_adj)) != LS_OK) {
+        cudaLibraryUnload(s->mod.lib);
+        delete s;
+        return st;
+    }
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, (const void *)s->mod.eval) == cudaSuccess) s->mod.regs_eval = fa.numRegs;
+    else cudaGetLastError();
+    *out = s;
+    return LS_OK;
+}
+
+ls_status ls_spline_destroy(ls_spline s)
+{
+    if (!s) return LS_OK;
+    if (s->mod.lib) cudaLibraryUnload(s->mod.lib);
+    delete s;
+    return LS_OK;
+}
+
+const char *ls_spline_source(ls_spline s) { return s ? s->gen.source.c_str() : ""; }
+
+ls_status ls_spline_info(ls_spline s, int32_t *n_sites, int32_t *fma_value, int32_t *fma_grad, int32_t *regs)
+{
+    if (!s) return ls_fail(LS_ERR_INVALID_ARG, "spline is NULL");
+    if (n_sites) *n_sites = s->gen.info.n_sites;
+    if (fma_value) *fma_value = s->gen.info.fma_value;
+    if (fma_grad) *fma_grad = s->gen.info.fma_grad;
+    if (regs) *regs = s->mod.regs_eval;
+    return LS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// volumes
+// ---------------------------------------------------------------------------
+
+static ls_status init_volume(ls_spline s, const int64_t *ext, ls_volume_s *v)
+{
+    if (!s || !ext) return ls_fail(LS_ERR_INVALID_ARG, "spline or ext is NULL");
+    v->spline = s;
+    int64_t prod = 1;
+    for (int i = 0; i < 3; ++i) {
+        v->ext[i] = i < s->table.dim ? ext[i] : 1;
+        if (v->ext[i] < 1 || v->ext[i] > (1 << 20)) return ls_fail(LS_ERR_INVALID_ARG, "extent outside 1..2^20");
+        prod *= v->ext[i];
+    }
+    v->coset_elems = prod;
+    v->total_elems = prod * (int64_t)s->table.cosets.size();
+    if (v->total_elems >= (int64_t)1 << 31)
+        return ls_fail(LS_ERR_UNSUPPORTED, "volume exceeds 2^31 coefficients (32-bit addressing)");
+    return LS_OK;
+}
+
+ls_status ls_volume_create(ls_spline s, const int64_t *ext, ls_volume *out)
+{
+    if (!out) return ls_fail(LS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    auto *v = new (std::nothrow) ls_volume_s;
+    if (!v) return ls_fail(LS_ERR_OOM, "host allocation");
+    ls_status st = init_volume(s, ext, v);
+    if (st != LS_OK) {
+        delete v;
+        return st;
+    }
+    size_t bytes = (size_t)v->total_elems * dtype_size(s->dtype);
+    cudaError_t e = cudaMalloc(&v->coef, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete v;
+        return ls_fail(LS_ERR_OOM, "cudaMalloc of the coefficient volume failed");
+    }
+    e = cudaMemset(v->coef, 0, bytes);
+    if (e != cudaSuccess) {
+        cudaFree(v->coef);
+        delete v;
+        return cuda_fail(e, "cudaMemset");
+    }
+    v->owned = true;
+    *out = v;
+    return LS_OK;
+}
+
+ls_status ls_volume_wrap(ls_spline s, const int64_t *ext, void *device_coef, ls_volume *out)
+{
+    if (!out || !device_coef) return ls_fail(LS_ERR_INVALID_ARG, "out or device_coef is NULL");
+    *out = nullptr;
+    auto *v = new (std::nothrow) ls_volume_s;
+    if (!v) return ls_fail(LS_ERR_OOM, "host allocation");
+    ls_status st = init_volume(s, ext, v);
+    if (st != LS_OK) {
+        delete v;
+        return st;
+    }
+    v->coef = device_coef;
+    v->owned = false;
+    *out = v;
+    return LS_OK;
+}
+
+void *ls_volume_device_ptr(ls_volume v) { return v ? v->coef : nullptr; }
+
+ls_status ls_volume_upload(ls_volume v, const void *src, int32_t src_is_device, ls_dtype src_dt, ls_stream stream)
+{
+    if (!v || !src) return ls_fail(LS_ERR_INVALID_ARG, "volume or src is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const ls_dtype dst_dt = v->spline->dtype;
+    const size_t n = (size_t)v->total_elems;
+    if (dtype_size(src_dt) == 0) return ls_fail(LS_ERR_INVALID_ARG, "src dtype");
+    if (src_dt == dst_dt) {
+        cudaError_t e = cudaMemcpyAsync(v->coef, src, n * dtype_size(dst_dt),
+                                        src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+        return LS_OK;
+    }
+    const void *dsrc = src;
+    void *tmp = nullptr;
+    if (!src_is_device) {
+        cudaError_t e = cudaMallocAsync(&tmp, n * dtype_size(src_dt), st);
+        if (e != cudaSuccess) return ls_fail(LS_ERR_OOM, "staging allocation for upload");
+        e = cudaMemcpyAsync(tmp, src, n * dtype_size(src_dt), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(tmp, st);
+            return cuda_fail(e, "cudaMemcpyAsync");
+        }
+        dsrc = tmp;
+    }
+    cudaError_t e = lsk::convert(dsrc, (int)src_dt, v->coef, (int)dst_dt, (long long)n, st);
+    if (tmp) cudaFreeAsync(tmp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "convert kernel");
+    return LS_OK;
+}
+
+ls_status ls_volume_destroy(ls_volume v)
+{
+    if (!v) return LS_OK;
+    if (v->owned && v->coef) cudaFree(v->coef);
+    if (v->stage) cudaFree(v->stage);
+    delete v;
+    return LS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// evaluation
+// ---------------------------------------------------------------------------
+
+static void fill_eval_args(ls_volume v, const float *pts, int64_t n, float *out, float *grad, EvalArgsH &a)
+{
+    a.pts = pts;
+    a.out = out;
+    a.grad = grad;
+    a.coef = v->coef;
+    a.n = n;
+    a.e0 = (int)v->ext[0];
+    a.e1 = (int)v->ext[1];
+    a.e2 = (int)v->ext[2];
+    a.cstride = (int)v->coset_elems;
+}
+
+ls_status ls_eval(ls_volume v, const float *pts, int64_t n, float *out, ls_stream stream)
+{
+    if (!v || (n > 0 && (!pts || !out))) return ls_fail(LS_ERR_INVALID_ARG, "volume, pts or out is NULL");
+    if (n < 0) return ls_fail(LS_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return LS_OK;
+    ls_spline_s *s = v->spline;
+    EvalArgsH a;
+    fill_eval_args(v, pts, n, out, nullptr, a);
+    return launch(s->mod.eval, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_eval), s->var.block, &a,
+                  (cudaStream_t)stream);
+}
+
+ls_status ls_eval_grad(ls_volume v, const float *pts, int64_t n, float *val, float *grad, ls_stream stream)
+{
+    if (!v || (n > 0 && (!pts || !grad))) return ls_fail(LS_ERR_INVALID_ARG, "volume, pts or grad is NULL");
+    if (n < 0) return ls_fail(LS_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return LS_OK;
+    ls_spline_s *s = v->spline;
+    EvalArgsH a;
+    fill_eval_args(v, pts, n, val, grad, a);
+    return launch(s->mod.eval_grad, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_grad), s->var.block,
+                  &a, (cudaStream_t)stream);
+}
+
+ls_status ls_eval_host(ls_volume v, const float *host_pts, int64_t n, float *host_out, ls_stream stream)
+{
+    if (!v || (n > 0 && (!host_pts || !host_out))) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0) return ls_fail(LS_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return LS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int D = v->spline->table.dim;
+    const size_t pbytes = (size_t)n * D * sizeof(float), obytes = (size_t)n * sizeof(float);
+    const size_t need = pbytes + obytes + 256;
+    if (v->stage_bytes < need) {
+        if (v->stage) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+            cudaFree(v->stage);
+            v->stage = nullptr;
+            v->stage_bytes = 0;
+        }
+        if (cudaMalloc(&v->stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            return ls_fail(LS_ERR_OOM, "staging buffer for ls_eval_host");
+        }
+        v->stage_bytes = need;
+    }
+    float *dp = (float *)v->stage;
+    float *dout = (float *)((char *)v->stage + ((pbytes + 255) & ~(size_t)255));
+    cudaError_t e = cudaMemcpyAsync(dp, host_pts, pbytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
+    ls_status s = ls_eval(v, dp, n, dout, stream);
+    if (s != LS_OK) return s;
+    e = cudaMemcpyAsync(host_out, dout, obytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync D2H");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return LS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+
+size_t ls_adjoint_scratch_bytes(ls_volume v, int64_t n)
+{
+    (void)v;
+    (void)n;
+    return 0;
+}
+
+ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int64_t n, float *dcoef,
+                          int32_t deterministic, void *scratch, ls_stream stream)
+{
+    (void)scratch;
+    if (!v || (n > 0 && (!pts || !gout || !dcoef))) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0) return ls_fail(LS_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return LS_OK;
+    if (deterministic) return ls_fail(LS_ERR_UNSUPPORTED, "deterministic adjoint not available yet");
+    ls_spline_s *s = v->spline;
+    AdjArgsH a{pts, gout, dcoef, (long long)n, (int)v->ext[0], (int)v->ext[1], (int)v->ext[2], (int)v->coset_elems};
+    return launch(s->mod.adj_atomic, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_adj), s->var.block,
+                  &a, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// not yet provided
+// ---------------------------------------------------------------------------
+
+ls_status ls_morton_sort(const float *, int64_t, const float *, float, int32_t *, uint32_t *, void *, ls_stream)
+{
+    return ls_fail(LS_ERR_UNSUPPORTED, "ls_morton_sort not available yet");
+}
+size_t ls_morton_scratch_bytes(int64_t) { return 0; }
+ls_status ls_permute_rows(const float *, const int32_t *, int64_t, int32_t, int32_t, float *, ls_stream)
+{
+    return ls_fail(LS_ERR_UNSUPPORTED, "ls_permute_rows not available yet");
+}
+ls_status ls_plan_create(int32_t, const ls_volume *, const float *const *, const int64_t *, float *const *, int32_t,
+                         ls_plan *)
+{
+    return ls_fail(LS_ERR_UNSUPPORTED, "batched plans not available yet");
+}
+ls_status ls_plan_launch(ls_plan, ls_stream) { return ls_fail(LS_ERR_UNSUPPORTED, "batched plans not available yet"); }
+ls_status ls_plan_status(ls_plan, ls_stream) { return ls_fail(LS_ERR_UNSUPPORTED, "batched plans not available yet"); }
+ls_status ls_plan_destroy(ls_plan) { return LS_OK; }
+ls_status ls_cg_fit(ls_volume, const float *, const float *, int64_t, double, int32_t, double, int32_t, double *,
+                    int32_t *, ls_stream)
+{
+    return ls_fail(LS_ERR_UNSUPPORTED, "ls_cg_fit not available yet");
+}
+ls_status ls_dot_f64(const float *a, const float *b, int64_t n, double *result, ls_stream stream)
+{
+    if (n < 0 || (n > 0 && (!a || !b)) || !result) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e = lsk::dot_f64(a, b, (long long)n, result, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "dot kernel");
+    return LS_OK;
+}
+
+}  // extern "C"

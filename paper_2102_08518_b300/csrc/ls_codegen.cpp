@@ -1,0 +1,856 @@
+// Code generator: sub-region table -> specialised CUDA C++ (Sec. 4).
+//
+// The paper composes "blocks" (preamble, coset loop, region of evaluation,
+// sub-region membership, table lookups, reference sub-region loop, polynomial
+// evaluation) into LLVM-IR.  This generator composes the same blocks into CUDA
+// C++ that NVRTC compiles for sm_103a:
+//   * region of evaluation: floor (parallelepiped) or nearest site per coset
+//     (Voronoi), branch-free selects;
+//   * sub-region membership: signed-permutation folding (|y| sorted by a
+//     3-element network gives T of Algorithm 1 without a table) followed by the
+//     BSP plane tests + sigma LUT among the reference sub-regions;
+//   * memory lookup: one array per Cartesian coset, addresses built from
+//     per-point coset bases and reference-axis strides, the whole stencil
+//     unrolled with every offset an immediate; a bounds-checked copy of the
+//     gathers is taken only by points whose stencil leaves the arrays;
+//   * polynomial evaluation: the site coefficients are folded into the
+//     monomial coefficients A_a = sum_j M[j][a] c_j (M baked in as FP32
+//     immediates), then one multivariate Horner form per reference sub-region;
+//     tensor-product splines use per-axis Horner weights and a nested
+//     contraction instead.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <functional>
+#include <map>
+#include <set>
+#include <sstream>
+
+#include "ls_internal.h"
+
+namespace ls {
+namespace {
+
+std::string flit(double v)
+{
+    float f = (float)v;
+    if (f == 0.0f) return "0.0f";
+    char buf[64];
+    std::snprintf(buf, sizeof buf, "%af", (double)f);
+    return buf;
+}
+
+struct Emitter {
+    std::ostringstream o;
+    int tmp = 0;
+    int fma = 0;
+    std::string fresh(const char *p) { return std::string(p) + std::to_string(tmp++); }
+};
+
+// Union of site lists in first-seen order; index maps per region.
+struct Stencil {
+    std::vector<I3> sites;
+    std::vector<std::vector<int>> region_to_union;
+};
+
+Stencil union_stencil(const Table &t)
+{
+    Stencil s;
+    std::map<I3, int> idx;
+    for (const auto &r : t.ref) {
+        std::vector<int> m;
+        for (const auto &site : r.sites) {
+            auto it = idx.find(site);
+            if (it == idx.end()) {
+                idx[site] = (int)s.sites.size();
+                m.push_back((int)s.sites.size());
+                s.sites.push_back(site);
+            } else {
+                m.push_back(it->second);
+            }
+        }
+        s.region_to_union.push_back(m);
+    }
+    return s;
+}
+
+int floordiv2(int v) { return (v >= 0) ? v / 2 : -((-v + 1) / 2); }
+
+// ---------------------------------------------------------------------------
+// common prologue: helpers and argument structs
+// ---------------------------------------------------------------------------
+void emit_prologue(Emitter &e, const Table &t, ls_dtype dt)
+{
+    auto &o = e.o;
+    o << "// generated by the lattice spline code generator; do not edit\n";
+    o << "typedef unsigned short ls_u16;\n";
+    if (dt == LS_F32) {
+        o << "typedef float ls_coef_t;\n";
+        o << "static __device__ __forceinline__ float ls_ld(const ls_coef_t* p, int i) { return __ldg(p + i); }\n";
+    } else if (dt == LS_BF16) {
+        o << "typedef ls_u16 ls_coef_t;\n";
+        o << "static __device__ __forceinline__ float ls_ld(const ls_coef_t* p, int i) {"
+             " return __uint_as_float(((unsigned)__ldg(p + i)) << 16); }\n";
+    } else {
+        o << "typedef ls_u16 ls_coef_t;\n";
+        o << "static __device__ __forceinline__ float ls_ld(const ls_coef_t* p, int i) {"
+             " ls_u16 h = __ldg(p + i); float f; asm(\"cvt.f32.f16 %0, %1;\" : \"=f\"(f) : \"h\"(h)); return f; }\n";
+    }
+    o << "struct LsEvalArgs { const float* pts; float* out; float* grad; const ls_coef_t* coef;"
+         " long long n; int e0, e1, e2, cstride; };\n";
+    o << "struct LsAdjArgs { const float* pts; const float* gout; float* dcoef;"
+         " long long n; int e0, e1, e2, cstride; };\n";
+    o << "struct LsKeyArgs { const float* pts; unsigned* key; long long n; int e0, e1, e2, cstride; };\n";
+    o << "struct LsGatherArgs { const float* pts; const float* gout; const int* order;"
+         " const int* bin_start; float* dcoef; int nsite_total; int e0, e1, e2, cstride; };\n";
+    o << "#define LS_CSWAP(A, B, PA, PB, NA, NB) { bool sw_ = (A) < (B); float ta_ = sw_ ? (B) : (A);"
+         " float tb_ = sw_ ? (A) : (B); int pa_ = sw_ ? (PB) : (PA); int pb_ = sw_ ? (PA) : (PB);"
+         " unsigned na_ = sw_ ? (NB) : (NA); unsigned nb_ = sw_ ? (NA) : (NB);"
+         " A = ta_; B = tb_; PA = pa_; PB = pb_; NA = na_; NB = nb_; }\n";
+    (void)t;
+}
+
+// ---------------------------------------------------------------------------
+// point classification: region of evaluation + fold + sub-region
+// Emits, inside a point loop with x0..x{dim-1} loaded:
+//   int k0..; float y0..; (fold) float a0..; int p0..; unsigned g0.. (sign of
+//   reference axis r); int ri0.. (reference axis landing on Cartesian axis i);
+//   unsigned ng0.. (sign of Cartesian axis i); int psi;
+// ---------------------------------------------------------------------------
+void emit_classify(Emitter &e, const Table &t)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    if (t.roe == LS_ROE_PARALLELEPIPED) {
+        for (int i = 0; i < D; ++i)
+            o << "    const float kf" << i << " = floorf(x" << i << ");\n";
+    } else {
+        for (size_t j = 0; j < t.cosets.size(); ++j) {
+            for (int i = 0; i < D; ++i) {
+                int l = t.cosets[j][i];
+                if (t.scale == 1)
+                    o << "    const float c" << j << "_" << i << " = rintf(x" << i << ");\n";
+                else
+                    o << "    const float c" << j << "_" << i << " = fmaf(" << flit(t.scale) << ", rintf((x"
+                      << i << " - " << flit(l) << ") * " << flit(1.0 / t.scale) << "), " << flit(l) << ");\n";
+            }
+            o << "    const float d" << j << " = ";
+            for (int i = 0; i < D; ++i)
+                o << (i ? " + " : "") << "(x" << i << " - c" << j << "_" << i << ") * (x" << i << " - c" << j
+                  << "_" << i << ")";
+            o << ";\n";
+        }
+        for (int i = 0; i < D; ++i) o << "    float kf" << i << " = c0_" << i << ";\n";
+        o << "    float dbest = d0;\n";
+        for (size_t j = 1; j < t.cosets.size(); ++j) {
+            o << "    { const bool b = d" << j << " < dbest; dbest = b ? d" << j << " : dbest;";
+            for (int i = 0; i < D; ++i) o << " kf" << i << " = b ? c" << j << "_" << i << " : kf" << i << ";";
+            o << " }\n";
+        }
+    }
+    for (int i = 0; i < D; ++i) {
+        o << "    const int k" << i << " = (int)kf" << i << ";\n";
+        o << "    const float y" << i << " = x" << i << " - kf" << i << ";\n";
+    }
+    if (t.fold == LS_FOLD_SIGNED_PERM) {
+        for (int i = 0; i < D; ++i) {
+            o << "    const unsigned ng" << i << " = y" << i << " < 0.0f;\n";
+            o << "    float a" << i << " = fabsf(y" << i << "); int p" << i << " = " << i << "; unsigned g" << i
+              << " = ng" << i << ";\n";
+        }
+        if (D == 3) {
+            o << "    LS_CSWAP(a0, a1, p0, p1, g0, g1); LS_CSWAP(a1, a2, p1, p2, g1, g2);"
+                 " LS_CSWAP(a0, a1, p0, p1, g0, g1);\n";
+        } else {
+            o << "    LS_CSWAP(a0, a1, p0, p1, g0, g1);\n";
+        }
+        for (int i = 0; i < D; ++i) {
+            o << "    const int ri" << i << " = ";
+            for (int r = 0; r < D - 1; ++r) o << "(p" << r << " == " << i << ") ? " << r << " : ";
+            o << (D - 1) << ";\n";
+        }
+    } else {
+        for (int i = 0; i < D; ++i)
+            o << "    const float a" << i << " = y" << i << ";\n";
+    }
+    // reference sub-region
+    if (t.ref.size() > 1) {
+        o << "    unsigned q = 0u;\n";
+        for (size_t pi = 0; pi < t.planes.size(); ++pi) {
+            o << "    q |= (";
+            for (int i = 0; i < D; ++i) o << (i ? " + " : "") << flit(t.planes[pi][i]) << " * a" << i;
+            o << " - " << flit(t.planes[pi][3]) << " >= 0.0f) ? " << (1u << pi) << "u : 0u;\n";
+        }
+        unsigned long long packed = 0;
+        for (int qq = 0; qq < t.bsp_mod; ++qq) {
+            unsigned v = t.sigma[qq] < 0 ? 0u : (unsigned)t.sigma[qq];
+            packed |= (unsigned long long)(v & 0xF) << (4 * qq);
+        }
+        o << "    const int psi = (int)((" << packed << "ull >> (4u * (q % " << t.bsp_mod << "u))) & 15ull);\n";
+    } else {
+        o << "    const int psi = 0;\n";
+    }
+}
+
+// coset id LUT packed by parity pattern (scale 2) -> coset index
+unsigned long long coset_lut(const Table &t)
+{
+    unsigned long long lut = ~0ull;
+    for (size_t j = 0; j < t.cosets.size(); ++j) {
+        int par = 0;
+        for (int i = 0; i < t.dim; ++i) par |= (t.cosets[j][i] & 1) << i;
+        lut &= ~(0xFull << (4 * par));
+        lut |= (unsigned long long)j << (4 * par);
+    }
+    return lut;
+}
+
+// ---------------------------------------------------------------------------
+// addressing + gathers: emits float cN = coefficient of union site N.
+// Fast path with unchecked addresses when the whole stencil is inside;
+// checked path otherwise.
+// ---------------------------------------------------------------------------
+// load: emit float cN = coefficient; declare_addr: emit int adN = address (-1 if
+// the site is outside the arrays).  At least one of the two is set.
+void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int reach,
+                  const char *coef_expr, bool declare_addr, bool load = true)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    const bool fold = t.fold == LS_FOLD_SIGNED_PERM;
+    const int a = t.scale;
+    o << "    const int ex0 = E0, ex1 = E1" << (D == 3 ? ", ex2 = E2" : "") << ";\n";
+    o << "    bool inside = true;\n";
+    for (int i = 0; i < D; ++i)
+        o << "    inside = inside && (k" << i << " - " << reach << " >= 0) && (k" << i << " + " << reach
+          << " <= " << a << " * ex" << i << " - 1);\n";
+    if (load)
+        for (size_t j = 0; j < sites.size(); ++j) o << "    float c" << j << ";\n";
+    if (declare_addr)
+        for (size_t j = 0; j < sites.size(); ++j) o << "    int ad" << j << ";\n";
+    o << "    if (inside) {\n";
+    // strides of the reference axes
+    const char *st[3] = {"1", "ex0", "(ex0 * ex1)"};
+    for (int r = 0; r < D; ++r) {
+        if (fold) {
+            o << "      int rs" << r << " = ";
+            for (int i = 0; i < D - 1; ++i) o << "(p" << r << " == " << i << ") ? " << st[i] << " : ";
+            o << st[D - 1] << ";\n";
+            o << "      rs" << r << " = g" << r << " ? -rs" << r << " : rs" << r << ";\n";
+        } else {
+            o << "      const int rs" << r << " = " << st[r] << ";\n";
+        }
+    }
+    // parity classes
+    std::map<int, std::string> base_of_class;
+    auto parity_class = [&](const I3 &s) {
+        int m = 0;
+        if (a == 2)
+            for (int r = 0; r < D; ++r) m |= (s[r] & 1) << r;
+        return m;
+    };
+    if (a == 1) {
+        o << "      const int base0 = ";
+        o << "k0" << (D >= 2 ? " + ex0 * (k1" : "") << (D == 3 ? " + ex1 * k2" : "") << (D >= 2 ? ")" : "")
+          << ";\n";
+        base_of_class[0] = "base0";
+    } else {
+        const unsigned long long lut = coset_lut(t);
+        for (int i = 0; i < D; ++i)
+            o << "      const int qh" << i << " = k" << i << " >> 1, cb" << i << " = k" << i << " & 1;\n";
+        std::set<int> classes;
+        for (const auto &s : sites) classes.insert(parity_class(s));
+        for (int m : classes) {
+            std::string nm = "base" + std::to_string(m);
+            o << "      int " << nm << ";\n      {\n";
+            for (int i = 0; i < D; ++i) {
+                // component of R^T e on Cartesian axis i: e[ri_i], negated if axis i is negative
+                if (fold)
+                    o << "        const int ce" << i << " = (" << m << " >> ri" << i << ") & 1;\n";
+                else
+                    o << "        const int ce" << i << " = " << ((m >> i) & 1) << ";\n";
+                o << "        const int v" << i << " = cb" << i << " + " << (fold ? ("(ng" + std::to_string(i) + " ? -ce" + std::to_string(i) + " : ce" + std::to_string(i) + ")") : ("ce" + std::to_string(i))) << ";\n";
+            }
+            o << "        const int par = (v0 & 1)";
+            for (int i = 1; i < D; ++i) o << " | ((v" << i << " & 1) << " << i << ")";
+            o << ";\n";
+            o << "        const int cid = (int)((" << lut << "ull >> (4 * par)) & 15ull);\n";
+            o << "        " << nm << " = cid * CS + (qh0 + (v0 >> 1))";
+            if (D >= 2) o << " + ex0 * ((qh1 + (v1 >> 1))";
+            if (D == 3) o << " + ex1 * (qh2 + (v2 >> 1))";
+            if (D >= 2) o << ")";
+            o << ";\n      }\n";
+            base_of_class[m] = nm;
+        }
+    }
+    for (size_t j = 0; j < sites.size(); ++j) {
+        const I3 &s = sites[j];
+        std::string addr = base_of_class[parity_class(s)];
+        for (int r = 0; r < D; ++r) {
+            int h = (a == 2) ? floordiv2(s[r]) : s[r];
+            if (h == 0) continue;
+            if (h == 1) addr += " + rs" + std::to_string(r);
+            else if (h == -1) addr += " - rs" + std::to_string(r);
+            else addr += " + (" + std::to_string(h) + ") * rs" + std::to_string(r);
+        }
+        if (declare_addr) {
+            o << "      ad" << j << " = " << addr << ";\n";
+            if (load) o << "      c" << j << " = ls_ld(" << coef_expr << ", ad" << j << ");\n";
+        } else {
+            o << "      c" << j << " = ls_ld(" << coef_expr << ", " << addr << ");\n";
+        }
+    }
+    o << "    } else {\n";
+    for (size_t j = 0; j < sites.size(); ++j) {
+        const I3 &s = sites[j];
+        o << "      {\n";
+        for (int i = 0; i < D; ++i) {
+            if (fold) {
+                o << "        const int m" << i << " = ";
+                for (int r = 0; r < D - 1; ++r) o << "(ri" << i << " == " << r << ") ? " << s[r] << " : ";
+                o << s[D - 1] << ";\n";
+                o << "        const int n" << i << " = k" << i << " + (ng" << i << " ? -m" << i << " : m" << i
+                  << ");\n";
+            } else {
+                o << "        const int n" << i << " = k" << i << " + " << s[i] << ";\n";
+            }
+        }
+        o << "        const bool ok = ";
+        for (int i = 0; i < D; ++i)
+            o << (i ? " && " : "") << "((unsigned)n" << i << " < (unsigned)(" << a << " * ex" << i << "))";
+        o << ";\n";
+        if (a == 2) {
+            const unsigned long long lut = coset_lut(t);
+            o << "        const int par = (n0 & 1)";
+            for (int i = 1; i < D; ++i) o << " | ((n" << i << " & 1) << " << i << ")";
+            o << ";\n        const int cid = (int)((" << lut << "ull >> (4 * par)) & 15ull);\n";
+            o << "        const int adr = cid * CS + (n0 >> 1)";
+            if (D >= 2) o << " + ex0 * ((n1 >> 1)";
+            if (D == 3) o << " + ex1 * (n2 >> 1)";
+            if (D >= 2) o << ")";
+            o << ";\n";
+        } else {
+            o << "        const int adr = n0";
+            if (D >= 2) o << " + ex0 * (n1";
+            if (D == 3) o << " + ex1 * n2";
+            if (D >= 2) o << ")";
+            o << ";\n";
+        }
+        if (declare_addr) o << "        ad" << j << " = ok ? adr : -1;\n";
+        if (load) o << "        c" << j << " = ok ? ls_ld(" << coef_expr << ", adr) : 0.0f;\n";
+        o << "      }\n";
+    }
+    o << "    }\n";
+}
+
+// ---------------------------------------------------------------------------
+// polynomial evaluation in coefficient form + multivariate Horner
+// ---------------------------------------------------------------------------
+struct PolyEmit {
+    Emitter &e;
+    int D;
+    std::string pre;                           // name prefix for this region
+    std::string uvar[3];                       // names of the local coordinates
+    std::map<I3, std::vector<std::pair<int, double>>> terms;   // monomial -> (union site, coef)
+    std::map<I3, std::string> aname;           // emitted A_a
+
+    // A_a = sum_j M[j][a] c_j
+    std::string A(const I3 &m)
+    {
+        auto it = aname.find(m);
+        if (it != aname.end()) return it->second;
+        auto t = terms.find(m);
+        if (t == terms.end() || t->second.empty()) return aname[m] = "";
+        std::string nm = pre + "A" + std::to_string(m[0]) + "_" + std::to_string(m[1]) + "_" + std::to_string(m[2]);
+        std::string acc;
+        for (auto &pr : t->second) {
+            if (acc.empty()) {
+                acc = flit(pr.second) + " * c" + std::to_string(pr.first);
+                e.fma++;
+            } else {
+                acc = "fmaf(" + flit(pr.second) + ", c" + std::to_string(pr.first) + ", " + acc + ")";
+                e.fma++;
+            }
+        }
+        e.o << "    const float " << nm << " = " << acc << ";\n";
+        return aname[m] = nm;
+    }
+
+    // Horner over variables v..D-1 with fixed exponents for earlier variables.
+    // coeff(m) gives the coefficient expression name of monomial m ("" if 0).
+    std::string horner(int v, I3 prefix, const std::function<std::string(const I3 &)> &coeff,
+                       const std::set<I3> &support)
+    {
+        if (v >= D || v >= 3) return coeff(prefix);
+        int emax = -1;
+        for (const auto &m : support) {
+            bool match = true;
+            for (int i = 0; i < v; ++i)
+                if (m[i] != prefix[i]) match = false;
+            if (match) emax = std::max(emax, m[v]);
+        }
+        if (emax < 0) return "";
+        std::string acc;
+        for (int ex = emax; ex >= 0; --ex) {
+            I3 p = prefix;
+            p[v] = ex;
+            std::string t = horner(v + 1, p, coeff, support);
+            if (acc.empty()) {
+                acc = t;
+                if (!acc.empty() && ex > 0) {
+                    // acc will be multiplied next iteration
+                }
+                continue;
+            }
+            std::string nm = e.fresh("h");
+            if (t.empty()) {
+                e.o << "    const float " << nm << " = " << acc << " * " << uvar[v] << ";\n";
+            } else {
+                e.o << "    const float " << nm << " = fmaf(" << acc << ", " << uvar[v] << ", " << t << ");\n";
+            }
+            e.fma++;
+            acc = nm;
+        }
+        // leading zeros: if acc became non-empty only at a lower exponent it is already correct
+        return acc;
+    }
+};
+
+// Horner needs care when leading coefficients vanish; rebuild with explicit
+// powers handled by multiplying through.  The implementation above starts the
+// accumulator at the highest exponent that has a nonzero sub-polynomial: when
+// acc is empty at exponent ex, the sub-polynomial of that exponent is zero and
+// skipping it is exact because no lower-exponent term has been folded yet.
+
+std::set<I3> monomial_support(const RefRegion &r, const std::vector<int> &umap,
+                              std::map<I3, std::vector<std::pair<int, double>>> &terms)
+{
+    std::set<I3> sup;
+    const size_t nm = r.mono.size();
+    for (size_t j = 0; j < r.sites.size(); ++j)
+        for (size_t a = 0; a < nm; ++a) {
+            double c = r.coef[j * nm + a];
+            if (c == 0.0) continue;
+            terms[r.mono[a]].push_back({umap[j], c});
+            sup.insert(r.mono[a]);
+        }
+    return sup;
+}
+
+// Emits value (and optionally gradient in reference coordinates) for region k.
+// Returns names {f, g0, g1, g2}.
+std::vector<std::string> emit_region_poly(Emitter &e, const Table &t, int k, const std::vector<int> &umap,
+                                          bool grad)
+{
+    const RefRegion &r = t.ref[k];
+    const int D = t.dim;
+    PolyEmit pe{e, D, "r" + std::to_string(k) + "_", {}, {}, {}};
+    for (int i = 0; i < D; ++i) {
+        pe.uvar[i] = "u" + std::to_string(k) + "_" + std::to_string(i);
+        e.o << "    const float " << pe.uvar[i] << " = a" << i << " - " << flit(r.center[i]) << ";\n";
+    }
+    std::set<I3> sup = monomial_support(r, umap, pe.terms);
+    // emit all A_a in a fixed order first (shared by value and gradient)
+    for (const auto &m : sup) pe.A(m);
+    auto coefA = [&](const I3 &m) -> std::string {
+        auto it = pe.aname.find(m);
+        return it == pe.aname.end() ? std::string() : it->second;
+    };
+    std::vector<std::string> res;
+    std::string f = pe.horner(0, I3{0, 0, 0}, coefA, sup);
+    res.push_back(f.empty() ? "0.0f" : f);
+    if (grad) {
+        for (int i = 0; i < D; ++i) {
+            // derivative support and coefficients (ex_i + 1) * A_{m + e_i}
+            std::set<I3> dsup;
+            std::map<I3, std::string> dname;
+            for (const auto &m : sup) {
+                if (m[i] == 0) continue;
+                I3 dm = m;
+                dm[i] -= 1;
+                dsup.insert(dm);
+                std::string nm;
+                if (m[i] == 1) {
+                    nm = pe.aname[m];
+                } else {
+                    nm = e.fresh("dA");
+                    e.o << "    const float " << nm << " = " << flit(m[i]) << " * " << pe.aname[m] << ";\n";
+                    e.fma++;
+                }
+                dname[dm] = nm;
+            }
+            auto coefD = [&](const I3 &m) -> std::string {
+                auto it = dname.find(m);
+                return it == dname.end() ? std::string() : it->second;
+            };
+            std::string g = pe.horner(0, I3{0, 0, 0}, coefD, dsup);
+            res.push_back(g.empty() ? "0.0f" : g);
+        }
+    }
+    return res;
+}
+
+// Separable tensor-product evaluation (fold none, parallelepiped ROE).
+// Emits value and optionally gradient; gathers are emitted here.
+void emit_separable_body(Emitter &e, const Table &t, bool grad, std::string &fval, std::string g[3])
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    // per-axis weights (and derivatives) by Horner in u = y - center
+    for (int i = 0; i < D; ++i) {
+        const Axis &ax = t.sep[i];
+        o << "    const float su" << i << " = y" << i << " - " << flit(ax.center) << ";\n";
+        const int nc = ax.degree + 1;
+        for (size_t j = 0; j < ax.sites.size(); ++j) {
+            std::string acc = flit(ax.coef[j * nc + ax.degree]);
+            for (int d = ax.degree - 1; d >= 0; --d) {
+                acc = "fmaf(" + acc + ", su" + std::to_string(i) + ", " + flit(ax.coef[j * nc + d]) + ")";
+                e.fma++;
+            }
+            o << "    const float w" << i << "_" << j << " = " << acc << ";\n";
+            if (grad) {
+                std::string dacc = flit(ax.coef[j * nc + ax.degree] * ax.degree);
+                for (int d = ax.degree - 1; d >= 1; --d) {
+                    dacc = "fmaf(" + dacc + ", su" + std::to_string(i) + ", " + flit(ax.coef[j * nc + d] * d) + ")";
+                    e.fma++;
+                }
+                o << "    const float dw" << i << "_" << j << " = " << dacc << ";\n";
+            }
+        }
+    }
+    const int n0 = (int)t.sep[0].sites.size(), n1 = D > 1 ? (int)t.sep[1].sites.size() : 1,
+              n2 = D > 2 ? (int)t.sep[2].sites.size() : 1;
+    // gathers in rows along axis 0
+    std::vector<I3> sites;
+    for (int j2 = 0; j2 < n2; ++j2)
+        for (int j1 = 0; j1 < n1; ++j1)
+            for (int j0 = 0; j0 < n0; ++j0)
+                sites.push_back({t.sep[0].sites[j0], D > 1 ? t.sep[1].sites[j1] : 0, D > 2 ? t.sep[2].sites[j2] : 0});
+    int reach = 0;
+    for (auto &s : sites)
+        for (int i = 0; i < D; ++i) reach = std::max(reach, std::abs(s[i]));
+    emit_gathers(e, t, sites, reach, "a.coef", false);
+    auto cidx = [&](int j0, int j1, int j2) { return (j2 * n1 + j1) * n0 + j0; };
+    // contraction along axis 0: T(j1,j2) = sum w0 c ; dT = sum dw0 c
+    for (int j2 = 0; j2 < n2; ++j2)
+        for (int j1 = 0; j1 < n1; ++j1) {
+            std::string acc = "w0_0 * c" + std::to_string(cidx(0, j1, j2));
+            std::string dacc = "dw0_0 * c" + std::to_string(cidx(0, j1, j2));
+            e.fma += grad ? 2 : 1;
+            for (int j0 = 1; j0 < n0; ++j0) {
+                acc = "fmaf(w0_" + std::to_string(j0) + ", c" + std::to_string(cidx(j0, j1, j2)) + ", " + acc + ")";
+                dacc = "fmaf(dw0_" + std::to_string(j0) + ", c" + std::to_string(cidx(j0, j1, j2)) + ", " + dacc + ")";
+                e.fma += grad ? 2 : 1;
+            }
+            o << "    const float T" << j1 << "_" << j2 << " = " << acc << ";\n";
+            if (grad) o << "    const float dT" << j1 << "_" << j2 << " = " << dacc << ";\n";
+        }
+    if (D == 2) {
+        std::string f = "0.0f", g0 = "0.0f", g1 = "0.0f";
+        for (int j1 = 0; j1 < n1; ++j1) {
+            std::string s1 = std::to_string(j1);
+            f = "fmaf(w1_" + s1 + ", T" + s1 + "_0, " + f + ")";
+            e.fma++;
+            if (grad) {
+                g0 = "fmaf(w1_" + s1 + ", dT" + s1 + "_0, " + g0 + ")";
+                g1 = "fmaf(dw1_" + s1 + ", T" + s1 + "_0, " + g1 + ")";
+                e.fma += 2;
+            }
+        }
+        o << "    const float fv = " << f << ";\n";
+        fval = "fv";
+        if (grad) {
+            o << "    const float gr0 = " << g0 << ";\n    const float gr1 = " << g1 << ";\n";
+            g[0] = "gr0";
+            g[1] = "gr1";
+        }
+        return;
+    }
+    // axis 1: U(j2) = sum w1 T, U1(j2) = sum dw1 T, V(j2) = sum w1 dT
+    for (int j2 = 0; j2 < n2; ++j2) {
+        std::string u = "0.0f", u1 = "0.0f", v = "0.0f";
+        for (int j1 = 0; j1 < n1; ++j1) {
+            std::string tn = "T" + std::to_string(j1) + "_" + std::to_string(j2);
+            u = "fmaf(w1_" + std::to_string(j1) + ", " + tn + ", " + u + ")";
+            e.fma++;
+            if (grad) {
+                u1 = "fmaf(dw1_" + std::to_string(j1) + ", " + tn + ", " + u1 + ")";
+                v = "fmaf(w1_" + std::to_string(j1) + ", d" + tn + ", " + v + ")";
+                e.fma += 2;
+            }
+        }
+        o << "    const float U" << j2 << " = " << u << ";\n";
+        if (grad) o << "    const float U1_" << j2 << " = " << u1 << ";\n    const float V" << j2 << " = " << v << ";\n";
+    }
+    std::string f = "0.0f", g0 = "0.0f", g1 = "0.0f", g2 = "0.0f";
+    for (int j2 = 0; j2 < n2; ++j2) {
+        std::string s2 = std::to_string(j2);
+        f = "fmaf(w2_" + s2 + ", U" + s2 + ", " + f + ")";
+        e.fma++;
+        if (grad) {
+            g0 = "fmaf(w2_" + s2 + ", V" + s2 + ", " + g0 + ")";
+            g1 = "fmaf(w2_" + s2 + ", U1_" + s2 + ", " + g1 + ")";
+            g2 = "fmaf(dw2_" + s2 + ", U" + s2 + ", " + g2 + ")";
+            e.fma += 3;
+        }
+    }
+    o << "    const float fv = " << f << ";\n";
+    fval = "fv";
+    if (grad) {
+        o << "    const float gr0 = " << g0 << ";\n    const float gr1 = " << g1 << ";\n    const float gr2 = " << g2
+          << ";\n";
+        g[0] = "gr0";
+        g[1] = "gr1";
+        g[2] = "gr2";
+    }
+}
+
+void emit_point_load(Emitter &e, const Table &t)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    for (int i = 0; i < D; ++i)
+        o << "    const float x" << i << " = __ldg(a.pts + (size_t)i * " << D << " + " << i << ");\n";
+    o << "    if (!(";
+    for (int i = 0; i < D; ++i) o << (i ? " && " : "") << "fabsf(x" << i << ") < 4194304.0f";
+    o << ")) {\n";
+    o << "      const bool isn = ";
+    for (int i = 0; i < D; ++i) o << (i ? " || " : "") << "(x" << i << " != x" << i << ")";
+    o << ";\n";
+    o << "      LS_OUT_OF_RANGE(isn ? __int_as_float(0x7fffffff) : 0.0f);\n";
+    o << "      continue;\n    }\n";
+}
+
+std::string kname(const Table &t, const char *what)
+{
+    std::string n = "ls_" + std::string(what);
+    if (!t.name.empty()) n += "__" + t.name;
+    return n;
+}
+
+// value [+ gradient] kernel
+void emit_eval_kernel(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
+                      bool grad, GenInfo &info)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    const int fma0 = e.fma;
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block;
+    if (var.min_blocks > 0) o << ", " << var.min_blocks;
+    o << ") " << kname(t, grad ? "eval_grad" : "eval") << "(const LsEvalArgs a)\n{\n";
+    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride; (void)E1; (void)E2; (void)CS;\n";
+    o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
+    if (grad) {
+        o << "#define LS_OUT_OF_RANGE(V) { if (a.out) a.out[i] = (V);";
+        for (int i = 0; i < D; ++i) o << " a.grad[(size_t)i * " << D << " + " << i << "] = (V);";
+        o << " }\n";
+    } else {
+        o << "#define LS_OUT_OF_RANGE(V) { a.out[i] = (V); }\n";
+    }
+    o << "  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {\n";
+    emit_point_load(e, t);
+    emit_classify(e, t);
+    std::string fv;
+    std::string g[3];
+    if (!t.sep.empty()) {
+        emit_separable_body(e, t, grad, fv, g);
+    } else {
+        emit_gathers(e, t, st.sites, reach, "a.coef", false);
+        const size_t K = t.ref.size();
+        std::vector<std::vector<std::string>> rr;
+        if (K > 1 && var.branchy) {
+            o << "    float fsel = 0.0f, gs0 = 0.0f, gs1 = 0.0f, gs2 = 0.0f;\n";
+            for (size_t k = 0; k < K; ++k) {
+                o << "    " << (k ? "else " : "") << "if (psi == " << k << ") {\n";
+                auto r = emit_region_poly(e, t, (int)k, st.region_to_union[k], grad);
+                o << "    fsel = " << r[0] << ";\n";
+                if (grad)
+                    for (int i = 0; i < D; ++i) o << "    gs" << i << " = " << r[1 + i] << ";\n";
+                o << "    }\n";
+            }
+            fv = "fsel";
+            for (int i = 0; i < D; ++i) g[i] = "gs" + std::to_string(i);
+        } else {
+            for (size_t k = 0; k < K; ++k) rr.push_back(emit_region_poly(e, t, (int)k, st.region_to_union[k], grad));
+            if (K == 1) {
+                fv = rr[0][0];
+                if (grad)
+                    for (int i = 0; i < D; ++i) g[i] = rr[0][1 + i];
+            } else {
+                for (int c = 0; c < (grad ? D + 1 : 1); ++c) {
+                    std::string sel = rr[K - 1][c];
+                    for (int k = (int)K - 2; k >= 0; --k)
+                        sel = "(psi == " + std::to_string(k) + ") ? " + rr[k][c] + " : (" + sel + ")";
+                    std::string nm = c == 0 ? "fsel" : "gs" + std::to_string(c - 1);
+                    o << "    const float " << nm << " = " << sel << ";\n";
+                }
+                fv = "fsel";
+                for (int i = 0; i < D; ++i) g[i] = "gs" + std::to_string(i);
+            }
+        }
+    }
+    if (grad) {
+        o << "    if (a.out) a.out[i] = " << fv << ";\n";
+        // chain rule back to Cartesian axes: df/dy_i = sign_i * g[ref axis landing on i]
+        for (int i = 0; i < D; ++i) {
+            if (t.fold == LS_FOLD_SIGNED_PERM) {
+                o << "    { const float gg = ";
+                for (int r = 0; r < D - 1; ++r) o << "(ri" << i << " == " << r << ") ? " << g[r] << " : ";
+                o << g[D - 1] << "; a.grad[(size_t)i * " << D << " + " << i << "] = ng" << i << " ? -gg : gg; }\n";
+            } else {
+                o << "    a.grad[(size_t)i * " << D << " + " << i << "] = " << g[i] << ";\n";
+            }
+        }
+    } else {
+        o << "    a.out[i] = " << fv << ";\n";
+    }
+    o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
+    if (grad) info.fma_grad = e.fma - fma0;
+    else info.fma_value = e.fma - fma0;
+}
+
+// Per-site weight polynomials w_j(u) (weights form), for the adjoint.
+// Returns the name of w for union site j (or "" if identically 0 in all regions).
+std::vector<std::string> emit_site_weights(Emitter &e, const Table &t, const Stencil &st)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    const size_t K = t.ref.size();
+    std::vector<std::vector<std::string>> per(K, std::vector<std::string>(st.sites.size()));
+    for (size_t k = 0; k < K; ++k) {
+        const RefRegion &r = t.ref[k];
+        std::string uv[3];
+        for (int i = 0; i < D; ++i) {
+            uv[i] = "u" + std::to_string(k) + "_" + std::to_string(i);
+            o << "    const float " << uv[i] << " = a" << i << " - " << flit(r.center[i]) << ";\n";
+        }
+        const size_t nm = r.mono.size();
+        for (size_t j = 0; j < r.sites.size(); ++j) {
+            std::map<I3, std::vector<std::pair<int, double>>> terms;
+            std::set<I3> sup;
+            for (size_t aa = 0; aa < nm; ++aa) {
+                double c = r.coef[j * nm + aa];
+                if (c == 0.0) continue;
+                sup.insert(r.mono[aa]);
+                terms[r.mono[aa]].push_back({0, c});
+            }
+            PolyEmit pe{e, D, "", {uv[0], uv[1], uv[2]}, {}, {}};
+            auto coefc = [&](const I3 &m) -> std::string {
+                auto it = terms.find(m);
+                return it == terms.end() ? std::string() : flit(it->second[0].second);
+            };
+            std::string w = pe.horner(0, I3{0, 0, 0}, coefc, sup);
+            if (w.empty()) continue;
+            std::string nmv = e.fresh("w");
+            o << "    const float " << nmv << " = " << w << ";\n";
+            per[k][st.region_to_union[k][j]] = nmv;
+        }
+    }
+    std::vector<std::string> out(st.sites.size());
+    for (size_t j = 0; j < st.sites.size(); ++j) {
+        if (K == 1) {
+            out[j] = per[0][j];
+            continue;
+        }
+        bool any = false;
+        for (size_t k = 0; k < K; ++k) any = any || !per[k][j].empty();
+        if (!any) continue;
+        std::string sel = per[K - 1][j].empty() ? "0.0f" : per[K - 1][j];
+        for (int k = (int)K - 2; k >= 0; --k)
+            sel = "(psi == " + std::to_string(k) + ") ? " + (per[k][j].empty() ? "0.0f" : per[k][j]) + " : (" + sel + ")";
+        std::string nmv = e.fresh("ws");
+        o << "    const float " << nmv << " = " << sel << ";\n";
+        out[j] = nmv;
+    }
+    return out;
+}
+
+// Atomic adjoint: dcoef[site] += g * w_site for every stencil site of every point.
+void emit_adjoint_atomic(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block << ") " << kname(t, "adjoint_atomic")
+      << "(const LsAdjArgs a)\n{\n";
+    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride; (void)E1; (void)E2; (void)CS;\n";
+    o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
+    o << "#define LS_OUT_OF_RANGE(V) { }\n";
+    o << "  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {\n";
+    emit_point_load(e, t);
+    o << "    const float gp = __ldg(a.gout + i);\n";
+    o << "    if (gp == 0.0f) continue;\n";
+    emit_classify(e, t);
+    if (!t.sep.empty()) {
+        // weights per axis
+        for (int i = 0; i < D; ++i) {
+            const Axis &ax = t.sep[i];
+            o << "    const float su" << i << " = y" << i << " - " << flit(ax.center) << ";\n";
+            const int nc = ax.degree + 1;
+            for (size_t j = 0; j < ax.sites.size(); ++j) {
+                std::string acc = flit(ax.coef[j * nc + ax.degree]);
+                for (int d = ax.degree - 1; d >= 0; --d)
+                    acc = "fmaf(" + acc + ", su" + std::to_string(i) + ", " + flit(ax.coef[j * nc + d]) + ")";
+                o << "    const float w" << i << "_" << j << " = " << acc << ";\n";
+            }
+        }
+        const int n0 = (int)t.sep[0].sites.size(), n1 = D > 1 ? (int)t.sep[1].sites.size() : 1,
+                  n2 = D > 2 ? (int)t.sep[2].sites.size() : 1;
+        std::vector<I3> sites;
+        for (int j2 = 0; j2 < n2; ++j2)
+            for (int j1 = 0; j1 < n1; ++j1)
+                for (int j0 = 0; j0 < n0; ++j0)
+                    sites.push_back({t.sep[0].sites[j0], D > 1 ? t.sep[1].sites[j1] : 0, D > 2 ? t.sep[2].sites[j2] : 0});
+        int rch = 0;
+        for (auto &s : sites)
+            for (int i = 0; i < D; ++i) rch = std::max(rch, std::abs(s[i]));
+        emit_gathers(e, t, sites, rch, "", true, false);
+        for (int j2 = 0; j2 < n2; ++j2)
+            for (int j1 = 0; j1 < n1; ++j1) {
+                o << "    { const float gw = gp * w1_" << j1 << (D > 2 ? " * w2_" + std::to_string(j2) : std::string()) << ";\n";
+                for (int j0 = 0; j0 < n0; ++j0) {
+                    int j = (j2 * n1 + j1) * n0 + j0;
+                    o << "      if (ad" << j << " >= 0) atomicAdd(a.dcoef + ad" << j << ", gw * w0_" << j0 << ");\n";
+                }
+                o << "    }\n";
+            }
+    } else {
+        auto w = emit_site_weights(e, t, st);
+        emit_gathers(e, t, st.sites, reach, "", true, false);
+        for (size_t j = 0; j < st.sites.size(); ++j) {
+            if (w[j].empty()) continue;
+            o << "    if (ad" << j << " >= 0) atomicAdd(a.dcoef + ad" << j << ", gp * " << w[j] << ");\n";
+        }
+    }
+    o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
+}
+
+}  // namespace
+
+Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
+{
+    Generated g;
+    Emitter e;
+    emit_prologue(e, t, dt);
+    Stencil st = union_stencil(t);
+    int reach = 0;
+    if (t.sep.empty()) {
+        for (auto &s : st.sites)
+            for (int i = 0; i < t.dim; ++i) reach = std::max(reach, std::abs(s[i]));
+        g.info.n_sites = (int)st.sites.size();
+    } else {
+        int n = 1;
+        for (auto &ax : t.sep) {
+            n *= (int)ax.sites.size();
+            for (int s : ax.sites) reach = std::max(reach, std::abs(s));
+        }
+        g.info.n_sites = n;
+    }
+    g.info.reach = reach;
+    emit_eval_kernel(e, t, var, st, reach, false, g.info);
+    emit_eval_kernel(e, t, var, st, reach, true, g.info);
+    emit_adjoint_atomic(e, t, var, st, reach);
+    g.source = e.o.str();
+    return g;
+}
+
+}  // namespace ls

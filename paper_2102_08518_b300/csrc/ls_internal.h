@@ -1,0 +1,104 @@
+// Internal structures of the lattice spline library (not part of the ABI).
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "lattice_spline.h"
+
+namespace ls {
+
+using I3 = std::array<int, 3>;
+
+// One reference sub-region, copied out of the descriptor.
+struct RefRegion {
+    std::vector<I3> sites;            // lattice offsets s_j (unused axes 0)
+    std::vector<I3> mono;             // monomial exponents (unused axes 0)
+    std::vector<double> coef;         // sites.size() * mono.size()
+    double center[3] = {0, 0, 0};
+    int degree = 0;
+};
+
+struct Axis {
+    std::vector<int> sites;
+    int degree = 0;
+    std::vector<double> coef;         // sites.size() * (degree + 1)
+    double center = 0;
+};
+
+struct Table {
+    std::string name;
+    int dim = 3, roe = 0, fold = 0, scale = 1;
+    double L[9] = {0};
+    std::vector<I3> cosets;
+    std::vector<std::array<double, 4>> planes;   // p (dim) then d at [3]
+    int bsp_mod = 1;
+    std::vector<int> sigma;
+    std::vector<RefRegion> ref;
+    std::vector<Axis> sep;                       // empty unless separable
+};
+
+// Counts the generator reports.
+struct GenInfo {
+    int n_sites = 0;        // union stencil
+    int reach = 0;          // max |component| of any site offset (bounds fast path)
+    int fma_value = 0;
+    int fma_grad = 0;
+};
+
+struct Generated {
+    std::string source;
+    GenInfo info;
+};
+
+// Code generation (ls_codegen.cpp).
+Generated generate(const Table &t, ls_dtype coef_dtype, const ls_variant &var);
+
+// Kernel handles of one compiled module.
+struct Module {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t eval = nullptr, eval_grad = nullptr, adj_atomic = nullptr;
+    cudaKernel_t roe_key = nullptr, adj_gather = nullptr, batch_eval = nullptr;
+    int regs_eval = 0;
+    int blocks_per_sm_eval = 0, blocks_per_sm_grad = 0, blocks_per_sm_adj = 0;
+    int blocks_per_sm_gather = 0;
+};
+
+// NVRTC compile + disk cache + load (ls_jit.cpp).
+ls_status compile_and_load(const std::string &source, const std::string &tag, Module &m,
+                           std::string &err);
+ls_status get_cubin(const std::string &source, const std::string &tag, std::vector<char> &cubin,
+                    std::string &err);
+
+}  // namespace ls
+
+// Opaque ABI objects.
+struct ls_spline_s {
+    ls::Table table;
+    ls_dtype dtype = LS_F32;
+    ls_variant var{};
+    ls::Generated gen;
+    ls::Module mod;
+    int device = 0;
+    int num_sms = 0;
+};
+
+struct ls_volume_s {
+    ls_spline_s *spline = nullptr;
+    int64_t ext[3] = {1, 1, 1};
+    int64_t coset_elems = 0;          // prod(ext)
+    int64_t total_elems = 0;          // n_cosets * prod(ext)
+    void *coef = nullptr;
+    bool owned = false;
+    // staging for ls_eval_host
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+};
+
+// Thread-local error message helpers (ls_api.cpp).
+ls_status ls_fail(ls_status s, const std::string &msg);

@@ -1,0 +1,120 @@
+// Spline-independent kernels: storage conversion and FP64 reductions.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <map>
+#include <mutex>
+
+#include "ls_kernels.h"
+
+namespace lsk {
+namespace {
+
+enum { DT_F32 = 0, DT_BF16 = 1, DT_F16 = 2, DT_F64 = 3 };
+
+__device__ __forceinline__ double load_any(const void *p, int dt, long long i)
+{
+    switch (dt) {
+    case DT_F32: return (double)((const float *)p)[i];
+    case DT_BF16: return (double)__bfloat162float(((const __nv_bfloat16 *)p)[i]);
+    case DT_F16: return (double)__half2float(((const __half *)p)[i]);
+    default: return ((const double *)p)[i];
+    }
+}
+
+__global__ void convert_kernel(const void *src, int sdt, void *dst, int ddt, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double v = load_any(src, sdt, i);
+        switch (ddt) {
+        case DT_F32: ((float *)dst)[i] = (float)v; break;
+        case DT_BF16: ((__nv_bfloat16 *)dst)[i] = __float2bfloat16_rn((float)v); break;
+        case DT_F16: ((__half *)dst)[i] = __float2half_rn((float)v); break;
+        default: ((double *)dst)[i] = v; break;
+        }
+    }
+}
+
+constexpr int kDotBlocks = 296;   // 2 per SM on 148 SMs
+constexpr int kDotThreads = 512;
+
+// Per-block FP64 partial sums in a fixed order; the last block to finish (ticket
+// counter, no waiting) adds the partials in block order and resets the counter.
+__global__ void __launch_bounds__(kDotThreads) dot_kernel(const float *a, const float *b, long long n,
+                                                           double *partials, unsigned *ticket, double *result)
+{
+    __shared__ double red[kDotThreads];
+    __shared__ bool last;
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s = fma((double)a[i], (double)b[i], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = red[0];
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (unsigned k = 0; k < gridDim.x; ++k) tot += ((volatile double *)partials)[k];
+        *result = tot;
+        *ticket = 0u;
+    }
+}
+
+std::mutex g_mu;
+std::map<int, void *> g_ws;
+
+}  // namespace
+
+cudaError_t convert(const void *src, int sdt, void *dst, int ddt, long long n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    convert_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, sdt, dst, ddt, n);
+    return cudaGetLastError();
+}
+
+size_t dot_ws_bytes() { return kDotBlocks * sizeof(double) + 256; }
+
+cudaError_t dot_f64_ws(const float *a, const float *b, long long n, double *result, void *ws, cudaStream_t st)
+{
+    double *partials = (double *)ws;
+    unsigned *ticket = (unsigned *)((char *)ws + kDotBlocks * sizeof(double));
+    dot_kernel<<<kDotBlocks, kDotThreads, 0, st>>>(a, b, n, partials, ticket, result);
+    return cudaGetLastError();
+}
+
+cudaError_t dot_f64(const float *a, const float *b, long long n, double *result, cudaStream_t st)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    void *ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_ws.find(dev);
+        if (it == g_ws.end()) {
+            e = cudaMalloc(&ws, dot_ws_bytes());
+            if (e != cudaSuccess) return e;
+            e = cudaMemset(ws, 0, dot_ws_bytes());
+            if (e != cudaSuccess) return e;
+            g_ws[dev] = ws;
+        } else {
+            ws = it->second;
+        }
+    }
+    return dot_f64_ws(a, b, n, result, ws, st);
+}
+
+}  // namespace lsk

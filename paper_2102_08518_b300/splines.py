@@ -1,0 +1,28 @@
+"""The lattices and box splines this library evaluates (Sec. 5.1, Fig. 1).
+
+Lattices are unions of Cartesian cosets of scale*Z^s, stored one coefficient
+array per coset (the per-coset memory lookup of Sec. 4.1):
+  CC  = Z^3                                  scale 1, one coset
+  BCC = 2Z^3 u (2Z^3 + (1,1,1))              scale 2, two cosets,  |det L| = 4
+  FCC = {n in Z^3 : n_0 + n_1 + n_2 even}    scale 2, four cosets, |det L| = 2
+  Z^2 (the ZP element of Fig. 1)             scale 1, one coset
+"""
+from .subregions import Lattice, Spline
+
+CC = Lattice("cc", 3, 1, ((0, 0, 0),), ((1, 0, 0), (0, 1, 0), (0, 0, 1)))
+BCC = Lattice("bcc", 3, 2, ((0, 0, 0), (1, 1, 1)), ((-1, 1, 1), (1, -1, 1), (1, 1, -1)))
+FCC = Lattice("fcc", 3, 2, ((0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 1, 1)),
+              ((1, 1, 0), (1, 0, 1), (0, 1, 1)))
+Z2 = Lattice("z2", 2, 1, ((0, 0),), ((1, 0), (0, 1)))
+
+_E = ((1, 0, 0), (0, 1, 0), (0, 0, 1))
+_BCC4 = ((1, 1, 1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1))
+_FCC6 = ((1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (0, 1, 1), (0, 1, -1))
+
+TRICUBIC = Spline("tricubic", CC, tuple(d for d in _E for _ in range(4)), "parallelepiped")
+BCC_LINEAR = Spline("bcc_linear", BCC, _BCC4, "voronoi")
+BCC_QUINTIC = Spline("bcc_quintic", BCC, _BCC4 + _BCC4, "voronoi")
+FCC6 = Spline("fcc6", FCC, _FCC6, "voronoi")
+ZP = Spline("zp", Z2, ((1, 0), (0, 1), (1, 1), (-1, 1)), "voronoi")
+
+BY_NAME = {s.name: s for s in (TRICUBIC, BCC_LINEAR, BCC_QUINTIC, FCC6, ZP)}

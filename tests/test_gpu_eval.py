@@ -1,0 +1,230 @@
+"""GPU evaluation (ls_eval / ls_eval_grad / ls_adjoint_coef) against the FP64 oracle.
+
+Tolerance: max |f_gpu - f_oracle| <= 2e-6 * ||c||_inf for FP32 arithmetic on
+FP32 coefficients (the accuracy target of the benchmark configurations).  The
+oracle evaluates at the FP32 input points promoted to FP64.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from oracle import specs as ospecs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-6
+ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_linear": ospecs.bcc_linear,
+               "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6, "zp": ospecs.zp2d}
+SMALL_EXT = {"tricubic": (12, 11, 10), "bcc_linear": (7, 6, 8), "bcc_quintic": (8, 7, 6),
+             "fcc6": (7, 8, 6), "zp": (13, 11)}
+_SPLINES = {}
+
+
+def spline(name, dtype="f32", **kw):
+    from paper_2102_08518_b300.api import Spline
+    key = (name, dtype, tuple(sorted(kw.items())))
+    if key not in _SPLINES:
+        _SPLINES[key] = Spline(name, dtype, **kw)
+    return _SPLINES[key]
+
+
+def volume(name, ext, coef_np, dtype="f32"):
+    from paper_2102_08518_b300.api import Volume, TORCH_DTYPES
+    sp = spline(name, dtype)
+    c = torch.from_numpy(coef_np).to("cuda", TORCH_DTYPES[dtype]).contiguous()
+    return Volume(sp, ext, c)
+
+
+def oracle_eval(name, ext, coef_np, pts):
+    spec = ORACLE_SPEC[name]().with_extent(ext)
+    return oracle.eval_sum(spec, coef_np.astype(np.float64).ravel(), pts.astype(np.float64))
+
+
+def gpu_eval(vol, pts_np):
+    p = torch.from_numpy(pts_np).cuda()
+    out = vol.eval(p)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
+@pytest.mark.parametrize("n", [1, 31, 4133])
+def test_small_volume_every_point(name, n):
+    """All points, including beyond the arrays (zero extension, checked gathers)."""
+    lat = workloads.SPLINE_LATTICE[name]
+    ext = SMALL_EXT[name]
+    coef = workloads.coef_uniform(lat, ext, seed=11)
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = workloads.points_uniform(n, lo - 2.5, hi + 2.5, seed=n)
+    got = gpu_eval(volume(name, ext, coef), pts)
+    want = oracle_eval(name, ext, coef, pts)
+    assert np.max(np.abs(got - want)) <= TOL * np.abs(coef).max()
+
+
+@pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6"])
+def test_special_points(name):
+    """Lattice sites, half-integers, mirror and BSP planes, and the edges."""
+    lat = workloads.SPLINE_LATTICE[name]
+    ext = SMALL_EXT[name]
+    coef = workloads.coef_uniform(lat, ext, seed=12)
+    lo, hi = workloads.bounding_box(lat, ext)
+    rng = np.random.default_rng(13)
+    p = rng.uniform(lo, hi, (600, 3))
+    p[:100] = np.round(p[:100])
+    p[100:200] = np.round(p[100:200] * 2) / 2
+    p[200:300, 1] = p[200:300, 0]
+    d = rng.uniform(-0.5, 0.5, 100)
+    p[300:400] = np.round(p[300:400]) + np.stack([d, d, 1 - 2 * np.abs(d)], 1) * 0.5
+    p[400:450] = np.array(lo)
+    p[450:500] = np.array(hi)
+    pts = p.astype(np.float32)
+    got = gpu_eval(volume(name, ext, coef), pts)
+    want = oracle_eval(name, ext, coef, pts)
+    assert np.max(np.abs(got - want)) <= TOL * np.abs(coef).max()
+
+
+def test_non_finite_and_far_points():
+    ext = SMALL_EXT["bcc_quintic"]
+    coef = workloads.coef_uniform("bcc", ext, seed=14)
+    vol = volume("bcc_quintic", ext, coef)
+    pts = np.array([[np.nan, 1, 1], [1e9, 2, 2], [-1e30, 0, 0], [5, 5, 5], [np.inf, 0, 0]], np.float32)
+    got = gpu_eval(vol, pts)
+    assert np.isnan(got[0]) and got[1] == 0.0 and got[2] == 0.0 and got[4] == 0.0
+    want = oracle_eval("bcc_quintic", ext, coef, pts[3:4])
+    assert abs(got[3] - want[0]) <= TOL * np.abs(coef).max()
+
+
+def test_zero_points():
+    from paper_2102_08518_b300.api import Volume
+    ext = SMALL_EXT["fcc6"]
+    vol = Volume(spline("fcc6"), ext)
+    out = vol.eval(torch.zeros(0, 3, device="cuda"))
+    assert out.numel() == 0
+
+
+# ---------------------------------------------------------------------------
+# the benchmark workloads at full size (sampled oracle)
+# ---------------------------------------------------------------------------
+
+def _sampled_check(name, ext, coef, pts, n_sample, seed):
+    vol = volume(name, ext, coef)
+    got = gpu_eval(vol, pts)
+    assert np.all(np.isfinite(got))
+    idx = np.random.default_rng(seed).choice(len(pts), n_sample, replace=False)
+    want = oracle_eval(name, ext, coef, pts[idx])
+    err = np.max(np.abs(got[idx] - want))
+    assert err <= TOL * np.abs(coef).max(), err
+    return got
+
+
+def test_tricubic_64cubed_all_points():
+    ext = (64, 64, 64)
+    coef = workloads.coef_uniform("cc", ext, seed=0)
+    pts = workloads.points_uniform(1 << 18, [2, 2, 2], [61, 61, 61], seed=0)
+    got = gpu_eval(volume("tricubic", ext, coef), pts)
+    want = oracle_eval("tricubic", ext, coef, pts)
+    assert np.max(np.abs(got - want)) <= TOL * np.abs(coef).max()
+
+
+@pytest.mark.parametrize("name", ["bcc_linear", "bcc_quintic"])
+def test_bcc_128_per_coset_uniform_and_rays(name):
+    ext = (128, 128, 128)
+    coef = workloads.coef_smooth("bcc", ext, seed=0)
+    lo, hi = workloads.inner_box(name, ext)
+    uni = workloads.points_uniform(1 << 24, lo, hi, seed=1)
+    _sampled_check(name, ext, coef, uni, 1024, 2)
+    rays = workloads.points_rays(4096, 4096, lo, hi, seed=3)
+    _sampled_check(name, ext, coef, rays, 1024, 4)
+
+
+def test_fcc_256_box_value_and_gradient():
+    ext = (128, 128, 128)
+    coef = workloads.coef_uniform("fcc", ext, seed=0)
+    lo, hi = workloads.inner_box("fcc6", ext)
+    pts = workloads.points_uniform(1 << 26, lo, hi, seed=5)
+    _sampled_check("fcc6", ext, coef, pts, 1024, 6)
+    # gradient on a slice of the same workload
+    vol = volume("fcc6", ext, coef)
+    sub = pts[: 1 << 20]
+    val, grad = vol.eval_grad(torch.from_numpy(sub).cuda())
+    torch.cuda.synchronize()
+    idx = np.random.default_rng(7).choice(len(sub), 512, replace=False)
+    spec = ORACLE_SPEC["fcc6"]().with_extent(ext)
+    f, g = oracle.eval_sum_grad(spec, coef.astype(np.float64).ravel(), sub[idx].astype(np.float64))
+    assert np.max(np.abs(val.cpu().numpy()[idx] - f)) <= TOL * np.abs(coef).max()
+    assert np.max(np.abs(grad.cpu().numpy()[idx] - g)) <= 1e-5 * np.abs(coef).max()
+
+
+# ---------------------------------------------------------------------------
+# gradient and adjoint on small volumes
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
+def test_gradient_matches_oracle(name):
+    lat = workloads.SPLINE_LATTICE[name]
+    ext = SMALL_EXT[name]
+    coef = workloads.coef_uniform(lat, ext, seed=21)
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = workloads.points_uniform(2000, lo - 1.0, hi + 1.0, seed=22)
+    vol = volume(name, ext, coef)
+    val, grad = vol.eval_grad(torch.from_numpy(pts).cuda())
+    torch.cuda.synchronize()
+    spec = ORACLE_SPEC[name]().with_extent(ext)
+    f, g = oracle.eval_sum_grad(spec, coef.astype(np.float64).ravel(), pts.astype(np.float64))
+    assert np.max(np.abs(val.cpu().numpy() - f)) <= TOL * np.abs(coef).max()
+    gg = grad.cpu().numpy()
+    if name == "bcc_linear":
+        # C0 spline: the gradient jumps across knot planes; compare off them
+        ok = np.ones(len(pts), bool)
+        h = 1e-4
+        for i in range(3):
+            e = np.zeros(3)
+            e[i] = h
+            fp = oracle.eval_sum(spec, coef.astype(np.float64).ravel(), pts + e)
+            fm = oracle.eval_sum(spec, coef.astype(np.float64).ravel(), pts - e)
+            ok &= np.abs((fp - f) / h - (f - fm) / h) < 1e-6
+        gg, g = gg[ok], g[ok]
+        assert ok.sum() > 1000
+    assert np.max(np.abs(gg - g)) <= 1e-5 * np.abs(coef).max()
+
+
+@pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
+def test_adjoint_atomic_matches_oracle(name):
+    lat = workloads.SPLINE_LATTICE[name]
+    ext = SMALL_EXT[name]
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = workloads.points_uniform(3000, lo - 1.0, hi + 1.0, seed=31)
+    g = np.random.default_rng(32).normal(size=3000).astype(np.float32)
+    coef = workloads.coef_uniform(lat, ext, seed=33)
+    vol = volume(name, ext, coef)
+    dc = vol.adjoint(torch.from_numpy(pts).cuda(), torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    spec = ORACLE_SPEC[name]().with_extent(ext)
+    want = oracle.adjoint(spec, pts.astype(np.float64), g.astype(np.float64))
+    got = dc.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - want)) <= 2e-6 * max(1.0, np.abs(want).max()) * 8
+    # dot-product identity with the forward kernel
+    fwd = gpu_eval(vol, pts)
+    assert abs(fwd @ g.astype(np.float64) - got @ coef.ravel().astype(np.float64)) <= 1e-4 * np.abs(fwd @ g)
+
+
+@pytest.mark.parametrize("dtype,bound", [("bf16", 2.0 ** -8), ("f16", 2.0 ** -11)])
+@pytest.mark.parametrize("name", ["tricubic", "bcc_quintic", "fcc6"])
+def test_half_storage(name, dtype, bound):
+    """Half-precision storage, FP32 arithmetic: vs the oracle on the rounded
+    coefficients (FP32 tolerance) and on the original ones (storage bound)."""
+    lat = workloads.SPLINE_LATTICE[name]
+    ext = SMALL_EXT[name]
+    coef = workloads.coef_uniform(lat, ext, seed=41)
+    tdt = {"bf16": torch.bfloat16, "f16": torch.float16}[dtype]
+    rounded = torch.from_numpy(coef).to(tdt).float().numpy()
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = workloads.points_uniform(3000, lo - 1.0, hi + 1.0, seed=42)
+    got = gpu_eval(volume(name, ext, rounded, dtype), pts)
+    want_r = oracle_eval(name, ext, rounded, pts)
+    want = oracle_eval(name, ext, coef, pts)
+    cmax = np.abs(coef).max()
+    assert np.max(np.abs(got - want_r)) <= TOL * cmax
+    assert np.max(np.abs(got - want)) <= (bound + TOL) * cmax
