@@ -225,6 +225,15 @@ size_t ls_morton_scratch_bytes(int64_t n);
 ls_status ls_permute_rows(const float *src, const int32_t *perm, int64_t n, int32_t width,
                           int32_t inverse, float *dst, ls_stream stream);
 
+/*
+ * Measurement probe for the gather roofline: every one of nthreads threads
+ * issues loads_per_thread independent 4-byte loads from table at hashed indices
+ * in [0, 2^floor(log2(table_elems))) and writes their sum to out[thread].
+ * blocks: grid size (0 = 148 * 8).
+ */
+ls_status ls_probe_gather(const float *table, int64_t table_elems, int32_t loads_per_thread, float *out,
+                          int64_t nthreads, int32_t blocks, ls_stream stream);
+
 /* ---- batched persistent evaluation ------------------------------------------------ */
 /*
  * One plan evaluates n_vol volumes (any mix of splines whose kernels were

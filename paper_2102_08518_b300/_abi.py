@@ -84,6 +84,8 @@ SIGNATURES = {
     "ls_morton_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "ls_permute_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "ls_probe_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p]),
     "ls_plan_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_void_p), c_i64p, ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),

@@ -196,3 +196,52 @@ def _check_pts(pts: torch.Tensor, dim: int) -> torch.Tensor:
     if not pts.is_cuda or pts.dtype != torch.float32 or pts.dim() != 2 or pts.shape[1] != dim:
         raise ValueError(f"points must be a CUDA float32 tensor of shape (n, {dim})")
     return pts.contiguous()
+
+
+# ---------------------------------------------------------------------------
+# point ordering and device reductions
+# ---------------------------------------------------------------------------
+
+def morton_sort(pts: torch.Tensor, origin=(0.0, 0.0, 0.0), cell: float = 1.0, want_keys: bool = False,
+                scratch: Optional[torch.Tensor] = None, stream=None):
+    """perm (int32) ordering points by the Morton code of their cell; stable."""
+    pts = _check_pts(pts, 3)
+    n = pts.shape[0]
+    perm = torch.empty(n, dtype=torch.int32, device=pts.device)
+    keys = torch.empty(n, dtype=torch.int32, device=pts.device) if want_keys else None
+    o = (ctypes.c_float * 3)(*[float(v) for v in origin])
+    _abi.check(_abi.lib().ls_morton_sort(_ptr(pts), n, o, float(cell), _ptr(perm), _ptr(keys), _ptr(scratch),
+                                         _stream(stream)), "ls_morton_sort")
+    return (perm, keys) if want_keys else perm
+
+
+def morton_scratch_bytes(n: int) -> int:
+    return int(_abi.lib().ls_morton_scratch_bytes(n))
+
+
+def permute_rows(src: torch.Tensor, perm: torch.Tensor, inverse: bool = False, stream=None) -> torch.Tensor:
+    """dst[i] = src[perm[i]] (inverse: dst[perm[i]] = src[i]) for rows of src."""
+    src = src.contiguous()
+    n = src.shape[0]
+    width = src.numel() // max(n, 1)
+    dst = torch.empty_like(src)
+    _abi.check(_abi.lib().ls_permute_rows(_ptr(src), _ptr(perm), n, width, int(inverse), _ptr(dst),
+                                          _stream(stream)), "ls_permute_rows")
+    return dst
+
+
+def dot_f64(a: torch.Tensor, b: torch.Tensor, stream=None) -> torch.Tensor:
+    """sum a*b accumulated in FP64 on the device (returns a 1-element float64 tensor)."""
+    a = a.contiguous().float()
+    b = b.contiguous().float()
+    out = torch.empty(1, dtype=torch.float64, device=a.device)
+    _abi.check(_abi.lib().ls_dot_f64(_ptr(a), _ptr(b), a.numel(), _ptr(out), _stream(stream)), "ls_dot_f64")
+    return out
+
+
+def probe_gather(table_t: torch.Tensor, loads: int, nthreads: int, blocks: int = 0, out=None, stream=None):
+    if out is None:
+        out = torch.empty(nthreads, device=table_t.device)
+    _abi.check(_abi.lib().ls_probe_gather(_ptr(table_t), table_t.numel(), loads, _ptr(out), nthreads, blocks,
+                                          _stream(stream)), "ls_probe_gather")
+    return out

@@ -27,6 +27,22 @@ struct AdjArgsH {
     long long n;
     int e0, e1, e2, cstride;
 };
+struct BinArgsH {
+    const float *pts;
+    const float *gout;
+    uint32_t *key;
+    int32_t *idx;
+    void *rec;
+    long long n;
+    int e0, e1, e2, halo;
+    uint32_t nbins;
+};
+struct GatherArgsH {
+    const void *srec;
+    const uint32_t *start;
+    float *dcoef;
+    int e0, e1, e2, cstride, halo;
+};
 
 const char *dtype_tag(ls_dtype d)
 {
@@ -310,7 +326,9 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
     }
     if ((st = get_kernel(s, "eval", s->mod.eval, s->mod.blocks_per_sm_eval)) != LS_OK ||
         (st = get_kernel(s, "eval_grad", s->mod.eval_grad, s->mod.blocks_per_sm_grad)) != LS_OK ||
-        (st = get_kernel(s, "adjoint_atomic", s->mod.adj_atomic, s->mod.blocks_per_sm_adj)) != LS_OK) {
+        (st = get_kernel(s, "adjoint_atomic", s->mod.adj_atomic, s->mod.blocks_per_sm_adj)) != LS_OK ||
+        (st = get_kernel(s, "adjoint_bin", s->mod.roe_key, s->mod.blocks_per_sm_gather)) != LS_OK ||
+        (st = get_kernel(s, "adjoint_gather", s->mod.adj_gather, s->mod.blocks_per_sm_gather)) != LS_OK) {
         cudaLibraryUnload(s->mod.lib);
         delete s;
         return st;
@@ -532,40 +550,140 @@ ls_status ls_eval_host(ls_volume v, const float *host_pts, int64_t n, float *hos
 // adjoint
 // ---------------------------------------------------------------------------
 
+namespace {
+size_t al256b(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Bins of the deterministic adjoint: every lattice site of the haloed grid.
+uint64_t adjoint_nbins(ls_volume v)
+{
+    const int H = v->spline->gen.info.halo;
+    uint64_t cs = 1;
+    for (int i = 0; i < v->spline->table.dim; ++i) cs *= (uint64_t)(v->ext[i] + 2 * H);
+    return cs * v->spline->table.cosets.size();
+}
+}  // namespace
+
 size_t ls_adjoint_scratch_bytes(ls_volume v, int64_t n)
 {
-    (void)v;
-    (void)n;
-    return 0;
+    if (!v || n < 0) return 0;
+    const size_t N = (size_t)n;
+    return al256b(N * 4) * 2 + al256b(N * 16) * 2 + al256b((adjoint_nbins(v) + 2) * 4) +
+           lsk::sort_scratch_bytes(n > 0 ? n : 1) + 256;
 }
 
 ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int64_t n, float *dcoef,
                           int32_t deterministic, void *scratch, ls_stream stream)
 {
-    (void)scratch;
     if (!v || (n > 0 && (!pts || !gout || !dcoef))) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
     if (n < 0) return ls_fail(LS_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return LS_OK;
-    if (deterministic) return ls_fail(LS_ERR_UNSUPPORTED, "deterministic adjoint not available yet");
     ls_spline_s *s = v->spline;
-    AdjArgsH a{pts, gout, dcoef, (long long)n, (int)v->ext[0], (int)v->ext[1], (int)v->ext[2], (int)v->coset_elems};
-    return launch(s->mod.adj_atomic, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_adj), s->var.block,
-                  &a, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!deterministic) {
+        AdjArgsH a{pts, gout, dcoef, (long long)n, (int)v->ext[0], (int)v->ext[1], (int)v->ext[2],
+                   (int)v->coset_elems};
+        return launch(s->mod.adj_atomic, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_adj),
+                      s->var.block, &a, st);
+    }
+    if (n > ((int64_t)1 << 31) - 1) return ls_fail(LS_ERR_UNSUPPORTED, "more than 2^31-1 points");
+    const uint64_t nbins = adjoint_nbins(v);
+    if (nbins >= ((uint64_t)1 << 31)) return ls_fail(LS_ERR_UNSUPPORTED, "binning grid exceeds 2^31 sites");
+    int nbits = 1;
+    while (((uint64_t)1 << nbits) <= nbins) ++nbits;
+    const size_t N = (size_t)n;
+    const size_t need = ls_adjoint_scratch_bytes(v, n);
+    void *ws = scratch;
+    if (!ws && cudaMallocAsync(&ws, need, st) != cudaSuccess) {
+        cudaGetLastError();
+        return ls_fail(LS_ERR_OOM, "scratch for the deterministic adjoint");
+    }
+    char *p = (char *)ws;
+    uint32_t *key = (uint32_t *)p;
+    p += al256b(N * 4);
+    int32_t *idx = (int32_t *)p;
+    p += al256b(N * 4);
+    float *rec = (float *)p;
+    p += al256b(N * 16);
+    float *srec = (float *)p;
+    p += al256b(N * 16);
+    uint32_t *start = (uint32_t *)p;
+    p += al256b((nbins + 2) * 4);
+    void *sort_ws = p;
+    const int H = s->gen.info.halo;
+    ls_status res = LS_OK;
+    BinArgsH ba{pts, gout, key, idx, rec, (long long)n, (int)v->ext[0], (int)v->ext[1], (int)v->ext[2], H,
+                (uint32_t)nbins};
+    res = launch(s->mod.roe_key, grid_for(n, s->var.block, s->num_sms, 8), s->var.block, &ba, st);
+    cudaError_t e = cudaSuccess;
+    if (res == LS_OK) e = lsk::radix_sort_pairs(key, idx, n, nbits, sort_ws, st);
+    if (res == LS_OK && e == cudaSuccess) e = lsk::permute_rows(rec, idx, n, 4, 0, srec, st);
+    if (res == LS_OK && e == cudaSuccess) e = lsk::bin_starts(key, n, (uint32_t)nbins, start, st);
+    if (res == LS_OK && e != cudaSuccess) res = cuda_fail(e, "deterministic adjoint kernels");
+    if (res == LS_OK) {
+        GatherArgsH ga{srec, start, dcoef, (int)v->ext[0], (int)v->ext[1], (int)v->ext[2], (int)v->coset_elems, H};
+        res = launch(s->mod.adj_gather, grid_for(v->total_elems, s->var.block, s->num_sms, 8), s->var.block, &ga, st);
+    }
+    if (!scratch) cudaFreeAsync(ws, st);
+    return res;
 }
 
 // ---------------------------------------------------------------------------
 // not yet provided
 // ---------------------------------------------------------------------------
 
-ls_status ls_morton_sort(const float *, int64_t, const float *, float, int32_t *, uint32_t *, void *, ls_stream)
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t ls_morton_scratch_bytes(int64_t n)
 {
-    return ls_fail(LS_ERR_UNSUPPORTED, "ls_morton_sort not available yet");
+    if (n <= 0) return 256;
+    return al256((size_t)n * 4) + lsk::sort_scratch_bytes(n);
 }
-size_t ls_morton_scratch_bytes(int64_t) { return 0; }
-ls_status ls_permute_rows(const float *, const int32_t *, int64_t, int32_t, int32_t, float *, ls_stream)
+
+ls_status ls_morton_sort(const float *pts, int64_t n, const float *origin, float cell, int32_t *perm,
+                         uint32_t *keys_out, void *scratch, ls_stream stream)
 {
-    return ls_fail(LS_ERR_UNSUPPORTED, "ls_permute_rows not available yet");
+    if (n < 0 || (n > 0 && (!pts || !perm)) || !origin) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
+    if (!(cell > 0.0f) || !std::isfinite(cell)) return ls_fail(LS_ERR_INVALID_ARG, "cell must be positive");
+    if (n == 0) return LS_OK;
+    if (n > ((int64_t)1 << 31) - 1) return ls_fail(LS_ERR_UNSUPPORTED, "more than 2^31-1 points");
+    cudaStream_t st = (cudaStream_t)stream;
+    void *ws = scratch;
+    const size_t need = ls_morton_scratch_bytes(n);
+    if (!ws) {
+        if (cudaMallocAsync(&ws, need, st) != cudaSuccess) {
+            cudaGetLastError();
+            return ls_fail(LS_ERR_OOM, "scratch for ls_morton_sort");
+        }
+    }
+    uint32_t *keys = keys_out ? keys_out : (uint32_t *)ws;
+    void *sort_ws = (char *)ws + al256((size_t)n * 4);
+    cudaError_t e = lsk::morton_keys(pts, n, origin, cell, keys, perm, st);
+    if (e == cudaSuccess) e = lsk::radix_sort_pairs(keys, perm, n, 30, sort_ws, st);
+    if (!scratch) cudaFreeAsync(ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "morton sort kernels");
+    return LS_OK;
 }
+
+ls_status ls_permute_rows(const float *src, const int32_t *perm, int64_t n, int32_t width, int32_t inverse,
+                          float *dst, ls_stream stream)
+{
+    if (n < 0 || width < 1 || (n > 0 && (!src || !perm || !dst))) return ls_fail(LS_ERR_INVALID_ARG, "bad argument");
+    if (src == dst) return ls_fail(LS_ERR_INVALID_ARG, "src and dst must differ");
+    cudaError_t e = lsk::permute_rows(src, perm, n, width, inverse, dst, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "permute kernel");
+    return LS_OK;
+}
+
+ls_status ls_probe_gather(const float *table, int64_t table_elems, int32_t loads, float *out, int64_t nthreads,
+                          int32_t blocks, ls_stream stream)
+{
+    if (!table || !out || table_elems < 1 || loads < 1 || nthreads < 1) return ls_fail(LS_ERR_INVALID_ARG, "bad argument");
+    cudaError_t e = lsk::gather_probe(table, table_elems, loads, out, nthreads, blocks > 0 ? blocks : 148 * 8,
+                                      (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "gather probe");
+    return LS_OK;
+}
+
 ls_status ls_plan_create(int32_t, const ls_volume *, const float *const *, const int64_t *, float *const *, int32_t,
                          ls_plan *)
 {

@@ -100,9 +100,10 @@ void emit_prologue(Emitter &e, const Table &t, ls_dtype dt)
          " long long n; int e0, e1, e2, cstride; };\n";
     o << "struct LsAdjArgs { const float* pts; const float* gout; float* dcoef;"
          " long long n; int e0, e1, e2, cstride; };\n";
-    o << "struct LsKeyArgs { const float* pts; unsigned* key; long long n; int e0, e1, e2, cstride; };\n";
-    o << "struct LsGatherArgs { const float* pts; const float* gout; const int* order;"
-         " const int* bin_start; float* dcoef; int nsite_total; int e0, e1, e2, cstride; };\n";
+    o << "struct LsBinArgs { const float* pts; const float* gout; unsigned* key; int* idx; float4* rec;"
+         " long long n; int e0, e1, e2, halo; unsigned nbins; };\n";
+    o << "struct LsGatherArgs { const float4* srec; const unsigned* start; float* dcoef;"
+         " int e0, e1, e2, cstride, halo; };\n";
     o << "#define LS_CSWAP(A, B, PA, PB, NA, NB) { bool sw_ = (A) < (B); float ta_ = sw_ ? (B) : (A);"
          " float tb_ = sw_ ? (A) : (B); int pa_ = sw_ ? (PB) : (PA); int pb_ = sw_ ? (PA) : (PB);"
          " unsigned na_ = sw_ ? (NB) : (NA); unsigned nb_ = sw_ ? (NA) : (NB);"
@@ -824,6 +825,275 @@ void emit_adjoint_atomic(Emitter &e, const Table &t, const ls_variant &var, cons
     o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
 }
 
+
+// ---------------------------------------------------------------------------
+// deterministic adjoint: binning by region-of-evaluation site + per-coefficient gather
+// ---------------------------------------------------------------------------
+
+// Offsets d = n - k between a coefficient site n and the region-of-evaluation
+// site k of any point whose stencil contains n: all images T^T s_j of the
+// stencil sites under the fold group (Cartesian, deduplicated, sorted).
+std::vector<I3> reverse_offsets(const Table &t, const Stencil &st)
+{
+    std::set<I3> out;
+    const int D = t.dim;
+    std::vector<I3> sites = st.sites;
+    if (!t.sep.empty()) {
+        sites.clear();
+        const int n1 = D > 1 ? (int)t.sep[1].sites.size() : 1, n2 = D > 2 ? (int)t.sep[2].sites.size() : 1;
+        for (int j2 = 0; j2 < n2; ++j2)
+            for (int j1 = 0; j1 < n1; ++j1)
+                for (int s0 : t.sep[0].sites)
+                    sites.push_back({s0, D > 1 ? t.sep[1].sites[j1] : 0, D > 2 ? t.sep[2].sites[j2] : 0});
+    }
+    std::vector<int> perm(D);
+    for (int i = 0; i < D; ++i) perm[i] = i;
+    do {
+        for (int sg = 0; sg < (1 << D); ++sg) {
+            for (const auto &s : sites) {
+                I3 m{0, 0, 0};
+                // m[p_r] = sign * s_r
+                for (int r = 0; r < D; ++r) m[perm[r]] = ((sg >> perm[r]) & 1) ? -s[r] : s[r];
+                out.insert(m);
+            }
+            if (t.fold == LS_FOLD_NONE) break;
+        }
+        if (t.fold == LS_FOLD_NONE) break;
+    } while (std::next_permutation(perm.begin(), perm.end()));
+    return std::vector<I3>(out.begin(), out.end());
+}
+
+int bin_halo(const Table &t, int reach) { return (reach + t.scale - 1) / t.scale + 1; }
+
+void emit_adjoint_bin(Emitter &e, const Table &t, const ls_variant &var)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block << ") " << kname(t, "adjoint_bin")
+      << "(const LsBinArgs a)\n{\n";
+    o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
+    o << "  const int H = a.halo;\n";
+    o << "  const int eb0 = a.e0 + 2 * H, eb1 = a.e1 + 2 * H, eb2 = a.e2 + 2 * H; (void)eb1; (void)eb2;\n";
+    o << "#define LS_OUT_OF_RANGE(V) { a.key[i] = a.nbins; a.idx[i] = (int)i; a.rec[i] = make_float4(0.f, 0.f, 0.f, 0.f); }\n";
+    o << "  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {\n";
+    emit_point_load(e, t);
+    o << "    const float gp = __ldg(a.gout + i);\n";
+    emit_classify(e, t);
+    // bin of k in the haloed grid
+    const unsigned long long lut = coset_lut(t);
+    if (t.scale == 2) {
+        o << "    const int par = (k0 & 1)";
+        for (int i = 1; i < D; ++i) o << " | ((k" << i << " & 1) << " << i << ")";
+        o << ";\n    const int cid = (int)((" << lut << "ull >> (4 * par)) & 15ull);\n";
+        for (int i = 0; i < D; ++i) o << "    const int bi" << i << " = (k" << i << " >> 1) + H;\n";
+    } else {
+        o << "    const int cid = 0;\n";
+        for (int i = 0; i < D; ++i) o << "    const int bi" << i << " = k" << i << " + H;\n";
+    }
+    o << "    const bool inb = (gp != 0.0f)";
+    for (int i = 0; i < D; ++i) o << " && (unsigned)bi" << i << " < (unsigned)eb" << i;
+    o << ";\n";
+    o << "    const unsigned cs = (unsigned)eb0" << (D > 1 ? " * (unsigned)eb1" : "") << (D > 2 ? " * (unsigned)eb2" : "")
+      << ";\n";
+    o << "    const unsigned b = (unsigned)cid * cs + (unsigned)bi0";
+    if (D > 1) o << " + (unsigned)eb0 * ((unsigned)bi1";
+    if (D > 2) o << " + (unsigned)eb1 * (unsigned)bi2";
+    if (D > 1) o << ")";
+    o << ";\n";
+    o << "    a.key[i] = inb ? b : a.nbins;\n    a.idx[i] = (int)i;\n";
+    o << "    a.rec[i] = make_float4(y0, " << (D > 1 ? "y1" : "0.f") << ", " << (D > 2 ? "y2" : "0.f") << ", gp);\n";
+    o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
+}
+
+// Horner of w_j(u) with the site index j known only at run time: coefficients
+// read from a shared-memory table laid out monomial-major (cw[off + a*NS + j]).
+std::string emit_runtime_horner(Emitter &e, const RefRegion &r, int D, const std::string *uv, int off,
+                                const char *jvar)
+{
+    const int NS = (int)r.sites.size();
+    std::map<I3, int> mindex;
+    for (size_t a = 0; a < r.mono.size(); ++a) mindex[r.mono[a]] = (int)a;
+    std::set<I3> sup(r.mono.begin(), r.mono.end());
+    PolyEmit pe{e, D, "", {uv[0], uv[1], D > 2 ? uv[2] : std::string()}, {}, {}};
+    auto coef = [&](const I3 &m) -> std::string {
+        auto it = mindex.find(m);
+        if (it == mindex.end()) return std::string();
+        return "cw[" + std::to_string(off + it->second * NS) + " + " + jvar + "]";
+    };
+    return pe.horner(0, I3{0, 0, 0}, coef, sup);
+}
+
+void emit_adjoint_gather(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
+                         const std::vector<I3> &doffs)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    const bool sep = !t.sep.empty();
+    const int R = reach, W = 2 * reach + 1;
+    int lut_size = 1;
+    for (int i = 0; i < D; ++i) lut_size *= W;
+    int cw_total = 0;
+    std::vector<int> cw_off;
+    if (!sep) {
+        // LUT: (psi, s) -> j within region psi, or -1
+        o << "__constant__ signed char ls_jlut[" << t.ref.size() * lut_size << "] = {";
+        for (size_t k = 0; k < t.ref.size(); ++k) {
+            std::vector<int> lut(lut_size, -1);
+            for (size_t j = 0; j < t.ref[k].sites.size(); ++j) {
+                const I3 &s = t.ref[k].sites[j];
+                int idx = 0;
+                for (int i = 0; i < D; ++i) idx = idx * W + (s[i] + R);
+                lut[idx] = (int)j;
+            }
+            for (int v : lut) o << v << ",";
+        }
+        o << "};\n";
+        for (const auto &r : t.ref) {
+            cw_off.push_back(cw_total);
+            cw_total += (int)(r.mono.size() * r.sites.size());
+        }
+        o << "__constant__ float ls_cw[" << cw_total << "] = {";
+        for (const auto &r : t.ref) {
+            const size_t NS = r.sites.size(), NM = r.mono.size();
+            for (size_t a = 0; a < NM; ++a)
+                for (size_t j = 0; j < NS; ++j) o << flit(r.coef[j * NM + a]) << ",";
+        }
+        o << "};\n";
+    }
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block << ") " << kname(t, "adjoint_gather")
+      << "(const LsGatherArgs a)\n{\n";
+    if (!sep) {
+        o << "  __shared__ float cw[" << cw_total << "];\n";
+        o << "  for (int q = threadIdx.x; q < " << cw_total << "; q += blockDim.x) cw[q] = ls_cw[q];\n";
+        o << "  __syncthreads();\n";
+    }
+    o << "  const int H = a.halo;\n";
+    o << "  const int eb0 = a.e0 + 2 * H, eb1 = a.e1 + 2 * H, eb2 = a.e2 + 2 * H; (void)eb1; (void)eb2;\n";
+    o << "  const unsigned csb = (unsigned)eb0" << (D > 1 ? " * (unsigned)eb1" : "") << (D > 2 ? " * (unsigned)eb2" : "")
+      << ";\n";
+    o << "  const long long total = (long long)a.cstride * " << t.cosets.size() << ";\n";
+    o << "  for (long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x; site < total;"
+         " site += (long long)gridDim.x * blockDim.x) {\n";
+    o << "    const int cj = (int)(site / a.cstride);\n";
+    o << "    int rem = (int)(site - (long long)cj * a.cstride);\n";
+    o << "    const int i0 = rem % a.e0; rem /= a.e0;\n";
+    if (D > 1) o << "    const int i1 = rem % a.e1; rem /= a.e1;\n";
+    if (D > 2) o << "    const int i2 = rem;\n";
+    // Cartesian site n
+    for (int i = 0; i < D; ++i) {
+        o << "    int l" << i << " = 0;\n";
+        for (size_t j = 0; j < t.cosets.size(); ++j)
+            if (t.cosets[j][i]) o << "    if (cj == " << j << ") l" << i << " = " << t.cosets[j][i] << ";\n";
+        o << "    const int nn" << i << " = " << t.scale << " * i" << i << " + l" << i << ";\n";
+    }
+    o << "    float acc = 0.0f;\n";
+    const unsigned long long lut = coset_lut(t);
+    for (const auto &d : doffs) {
+        o << "    {\n";
+        for (int i = 0; i < D; ++i) o << "      const int kk" << i << " = nn" << i << " - (" << d[i] << ");\n";
+        if (t.scale == 2) {
+            o << "      const int par = (kk0 & 1)";
+            for (int i = 1; i < D; ++i) o << " | ((kk" << i << " & 1) << " << i << ")";
+            o << ";\n      const unsigned kc = (unsigned)((" << lut << "ull >> (4 * par)) & 15ull);\n";
+            for (int i = 0; i < D; ++i) o << "      const int bi" << i << " = (kk" << i << " >> 1) + H;\n";
+        } else {
+            o << "      const unsigned kc = 0u;\n";
+            for (int i = 0; i < D; ++i) o << "      const int bi" << i << " = kk" << i << " + H;\n";
+        }
+        o << "      const unsigned b = kc * csb + (unsigned)bi0";
+        if (D > 1) o << " + (unsigned)eb0 * ((unsigned)bi1";
+        if (D > 2) o << " + (unsigned)eb1 * (unsigned)bi2";
+        if (D > 1) o << ")";
+        o << ";\n";
+        o << "      const unsigned pend = __ldg(a.start + b + 1);\n";
+        o << "      for (unsigned pos = __ldg(a.start + b); pos < pend; ++pos) {\n";
+        o << "        const float4 r = __ldg(a.srec + pos);\n";
+        o << "        const float y0 = r.x" << (D > 1 ? ", y1 = r.y" : "") << (D > 2 ? ", y2 = r.z" : "")
+          << ", gp = r.w;\n";
+        if (sep) {
+            // tensor product: site offset d is the 1D site triple; weights are products
+            o << "        float w = gp;\n";
+            for (int i = 0; i < D; ++i) {
+                const Axis &ax = t.sep[i];
+                int jj = -1;
+                for (size_t q = 0; q < ax.sites.size(); ++q)
+                    if (ax.sites[q] == d[i]) jj = (int)q;
+                const int nc = ax.degree + 1;
+                std::string acc = flit(ax.coef[jj * nc + ax.degree]);
+                for (int dd = ax.degree - 1; dd >= 0; --dd)
+                    acc = "fmaf(" + acc + ", y" + std::to_string(i) + " - " + flit(ax.center) + ", " +
+                          flit(ax.coef[jj * nc + dd]) + ")";
+                o << "        w *= " << acc << ";\n";
+            }
+            o << "        acc = fmaf(1.0f, w, acc);\n";
+        } else {
+            // fold the point, then s = T d (reference offset of this site)
+            o << "        const unsigned ng0 = y0 < 0.0f" << (D > 1 ? ", ng1 = y1 < 0.0f" : "")
+              << (D > 2 ? ", ng2 = y2 < 0.0f" : "") << ";\n";
+            if (t.fold == LS_FOLD_SIGNED_PERM) {
+                for (int i = 0; i < D; ++i)
+                    o << "        float a" << i << " = fabsf(y" << i << "); int p" << i << " = " << i << "; unsigned g" << i
+                      << " = ng" << i << ";\n";
+                if (D == 3)
+                    o << "        LS_CSWAP(a0, a1, p0, p1, g0, g1); LS_CSWAP(a1, a2, p1, p2, g1, g2);"
+                         " LS_CSWAP(a0, a1, p0, p1, g0, g1);\n";
+                else
+                    o << "        LS_CSWAP(a0, a1, p0, p1, g0, g1);\n";
+                for (int r = 0; r < D; ++r) {
+                    o << "        const int dr" << r << " = ";
+                    for (int i = 0; i < D - 1; ++i) o << "(p" << r << " == " << i << ") ? " << d[i] << " : ";
+                    o << d[D - 1] << ";\n";
+                    o << "        const int s" << r << " = g" << r << " ? -dr" << r << " : dr" << r << ";\n";
+                }
+            } else {
+                for (int i = 0; i < D; ++i) o << "        const float a" << i << " = y" << i << ";\n";
+                for (int r = 0; r < D; ++r) o << "        const int s" << r << " = " << d[r] << ";\n";
+            }
+            if (t.ref.size() > 1) {
+                o << "        unsigned q = 0u;\n";
+                for (size_t pi = 0; pi < t.planes.size(); ++pi) {
+                    o << "        q |= (";
+                    for (int i = 0; i < D; ++i) o << (i ? " + " : "") << flit(t.planes[pi][i]) << " * a" << i;
+                    o << " - " << flit(t.planes[pi][3]) << " >= 0.0f) ? " << (1u << pi) << "u : 0u;\n";
+                }
+                unsigned long long packed = 0;
+                for (int qq = 0; qq < t.bsp_mod; ++qq) {
+                    unsigned v = t.sigma[qq] < 0 ? 0u : (unsigned)t.sigma[qq];
+                    packed |= (unsigned long long)(v & 0xF) << (4 * qq);
+                }
+                o << "        const int psi = (int)((" << packed << "ull >> (4u * (q % " << t.bsp_mod << "u))) & 15ull);\n";
+            } else {
+                o << "        const int psi = 0;\n";
+            }
+            o << "        bool inr = true;\n";
+            for (int r = 0; r < D; ++r) o << "        inr = inr && (s" << r << " >= " << -R << ") && (s" << r << " <= " << R << ");\n";
+            o << "        if (!inr) continue;\n";
+            {
+                std::string li = "(s0 + " + std::to_string(R) + ")";
+                for (int r = 1; r < D; ++r)
+                    li = "(" + li + " * " + std::to_string(W) + " + (s" + std::to_string(r) + " + " + std::to_string(R) + "))";
+                o << "        const int li = " << li << ";\n";
+            }
+            o << "        const int jj = ls_jlut[psi * " << lut_size << " + li];\n";
+            o << "        if (jj < 0) continue;\n";
+            for (size_t k = 0; k < t.ref.size(); ++k) {
+                o << "        " << (k ? "else " : "") << "if (psi == " << k << ") {\n";
+                std::string uv[3];
+                for (int i = 0; i < D; ++i) {
+                    uv[i] = "v" + std::to_string(k) + "_" + std::to_string(i);
+                    o << "        const float " << uv[i] << " = a" << i << " - " << flit(t.ref[k].center[i]) << ";\n";
+                }
+                std::string w = emit_runtime_horner(e, t.ref[k], D, uv, cw_off[k], "jj");
+                o << "        acc = fmaf(gp, " << (w.empty() ? "0.0f" : w) << ", acc);\n";
+                o << "        }\n";
+            }
+        }
+        o << "      }\n    }\n";
+    }
+    o << "    a.dcoef[site] += acc;\n";
+    o << "  }\n}\n\n";
+}
+
 }  // namespace
 
 Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
@@ -849,6 +1119,11 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
     emit_eval_kernel(e, t, var, st, reach, false, g.info);
     emit_eval_kernel(e, t, var, st, reach, true, g.info);
     emit_adjoint_atomic(e, t, var, st, reach);
+    emit_adjoint_bin(e, t, var);
+    std::vector<I3> doffs = reverse_offsets(t, st);
+    emit_adjoint_gather(e, t, var, st, reach, doffs);
+    g.info.n_reverse = (int)doffs.size();
+    g.info.halo = bin_halo(t, reach);
     g.source = e.o.str();
     return g;
 }

@@ -49,6 +49,8 @@ struct GenInfo {
     int reach = 0;          // max |component| of any site offset (bounds fast path)
     int fma_value = 0;
     int fma_grad = 0;
+    int n_reverse = 0;      // offsets between a coefficient and the ROE sites that can reach it
+    int halo = 0;           // halo of the binning grid (storage units)
 };
 
 struct Generated {

@@ -17,4 +17,19 @@ cudaError_t dot_f64_ws(const float *a, const float *b, long long n, double *resu
 // Same with a lazily allocated per-device scratch.
 cudaError_t dot_f64(const float *a, const float *b, long long n, double *result, cudaStream_t st);
 
+// Stable LSD radix sort of (key, value) pairs on the low nbits of the keys,
+// in place (keys/vals hold the result).  scratch: sort_scratch_bytes(n).
+size_t sort_scratch_bytes(long long n);
+cudaError_t radix_sort_pairs(uint32_t *keys, int32_t *vals, long long n, int nbits, void *scratch, cudaStream_t st);
+// keys[i] = 30-bit Morton code of floor((pts[i] - origin) * (1 / cell)) (clamped to 0..1023), vals[i] = i.
+cudaError_t morton_keys(const float *pts, long long n, const float *origin, float cell, uint32_t *keys,
+                        int32_t *vals, cudaStream_t st);
+cudaError_t iota(int32_t *v, long long n, cudaStream_t st);
+cudaError_t permute_rows(const float *src, const int32_t *perm, long long n, int width, int inverse, float *dst,
+                         cudaStream_t st);
+// start[b] = first index with sorted key >= b, for b in [0, nbins + 1] (keys <= nbins).
+cudaError_t bin_starts(const uint32_t *key, long long n, uint32_t nbins, uint32_t *start, cudaStream_t st);
+cudaError_t gather_probe(const float *table, long long table_elems, int loads, float *out, long long nthreads,
+                         int blocks, cudaStream_t st);
+
 }  // namespace lsk

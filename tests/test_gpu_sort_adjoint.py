@@ -1,0 +1,118 @@
+"""Morton sort, permutation, FP64 dot and the deterministic adjoint on the GPU."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from oracle import specs as ospecs
+
+pytestmark = pytest.mark.gpu
+
+ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_linear": ospecs.bcc_linear,
+               "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6, "zp": ospecs.zp2d}
+SMALL_EXT = {"tricubic": (12, 11, 10), "bcc_linear": (7, 6, 8), "bcc_quintic": (8, 7, 6),
+             "fcc6": (7, 8, 6), "zp": (13, 11)}
+
+
+def _expected_morton(pts, origin, cell):
+    """Keys from the oracle's Morton definition on cells computed in FP32 like the kernel."""
+    inv = np.float32(1.0) / np.float32(cell)
+    c = np.floor((pts.astype(np.float32) - np.asarray(origin, np.float32)) * inv)
+    c = np.clip(c, 0, 1023).astype(np.int64)
+    keys = np.array([oracle.morton3(int(a), int(b), int(d)) for a, b, d in c], dtype=np.int64)
+    return keys
+
+
+@pytest.mark.parametrize("n", [1, 1000, 4096 * 3 + 17, 200003])
+def test_morton_sort_bit_exact(n):
+    from paper_2102_08518_b300.api import morton_sort
+    rng = np.random.default_rng(n)
+    pts = rng.uniform(-5, 300, (n, 3)).astype(np.float32)
+    pts[: n // 3] = np.round(pts[: n // 3])        # many equal keys: stability matters
+    perm, keys = morton_sort(torch.from_numpy(pts).cuda(), origin=(0.0, 0.0, 0.0), cell=2.0, want_keys=True)
+    torch.cuda.synchronize()
+    want_keys = _expected_morton(pts, (0, 0, 0), 2.0)
+    want_perm = np.argsort(want_keys, kind="stable")
+    assert np.array_equal(perm.cpu().numpy(), want_perm)
+    assert np.array_equal(keys.cpu().numpy().astype(np.int64) & 0xFFFFFFFF, want_keys[want_perm])
+
+
+def test_permute_rows_roundtrip():
+    from paper_2102_08518_b300.api import permute_rows
+    rng = np.random.default_rng(5)
+    x = torch.from_numpy(rng.normal(size=(5001, 3)).astype(np.float32)).cuda()
+    perm = torch.from_numpy(rng.permutation(5001).astype(np.int32)).cuda()
+    y = permute_rows(x, perm)
+    assert torch.equal(y, x[perm.long()])
+    z = permute_rows(y, perm, inverse=True)
+    assert torch.equal(z, x)
+
+
+def test_dot_f64():
+    from paper_2102_08518_b300.api import dot_f64
+    rng = np.random.default_rng(6)
+    a = rng.normal(size=1_000_003).astype(np.float32)
+    b = rng.normal(size=1_000_003).astype(np.float32)
+    got = dot_f64(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()).item()
+    want = float(np.dot(a.astype(np.float64), b.astype(np.float64)))
+    assert abs(got - want) <= 1e-12 * np.sum(np.abs(a.astype(np.float64) * b))
+
+
+def _vol(name, ext, coef):
+    from paper_2102_08518_b300.api import Spline, Volume
+    return Volume(Spline(name, "f32"), ext, torch.from_numpy(coef).cuda())
+
+
+@pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
+def test_deterministic_adjoint_matches_oracle_and_is_bitwise_stable(name):
+    lat = workloads.SPLINE_LATTICE[name]
+    ext = SMALL_EXT[name]
+    lo, hi = workloads.bounding_box(lat, ext)
+    n = 5000
+    pts = workloads.points_uniform(n, lo - 2.0, hi + 2.0, seed=51)
+    g = np.random.default_rng(52).normal(size=n).astype(np.float32)
+    g[::7] = 0.0
+    coef = workloads.coef_uniform(lat, ext, seed=53)
+    vol = _vol(name, ext, coef)
+    p = torch.from_numpy(pts).cuda()
+    gg = torch.from_numpy(g).cuda()
+    d1 = vol.adjoint(p, gg, deterministic=True)
+    d2 = vol.adjoint(p, gg, deterministic=True)
+    da = vol.adjoint(p, gg, deterministic=False)
+    torch.cuda.synchronize()
+    assert torch.equal(d1, d2)
+    spec = ORACLE_SPEC[name]().with_extent(ext)
+    want = oracle.adjoint(spec, pts.astype(np.float64), g.astype(np.float64))
+    got = d1.cpu().numpy().astype(np.float64)
+    scale = max(1.0, np.abs(want).max())
+    assert np.max(np.abs(got - want)) <= 2e-5 * scale
+    assert np.max(np.abs(da.cpu().numpy() - got)) <= 2e-5 * scale
+
+
+def test_deterministic_adjoint_large_and_accumulating():
+    """2^18 points: bitwise determinism, accumulation into dcoef, the adjoint
+    identity <g, A c> = <A^T g, c>; the oracle checks a 2^11-point slice."""
+    name, ext = "bcc_quintic", (32, 32, 32)
+    coef = workloads.coef_uniform("bcc", ext, seed=61)
+    lo, hi = workloads.bounding_box("bcc", ext)
+    pts = workloads.points_uniform(1 << 18, lo, hi, seed=62)
+    g = np.random.default_rng(63).normal(size=1 << 18).astype(np.float32)
+    vol = _vol(name, ext, coef)
+    p = torch.from_numpy(pts).cuda()
+    gg = torch.from_numpy(g).cuda()
+    base = torch.full((vol.n_coef,), 0.5, device="cuda")
+    d1 = vol.adjoint(p, gg, dcoef=base.clone(), deterministic=True)
+    d2 = vol.adjoint(p, gg, dcoef=base.clone(), deterministic=True)
+    torch.cuda.synchronize()
+    assert torch.equal(d1, d2)
+    f = vol.eval(p)
+    lhs = float(torch.dot(f.double(), gg.double()))
+    rhs = float(torch.dot((d1 - base).double(), torch.from_numpy(coef.ravel()).cuda().double()))
+    assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+    sub = slice(0, 1 << 11)
+    ds = vol.adjoint(p[sub], gg[sub], deterministic=True)
+    torch.cuda.synchronize()
+    spec = ORACLE_SPEC[name]().with_extent(ext)
+    want = oracle.adjoint(spec, pts[sub].astype(np.float64), g[sub].astype(np.float64))
+    assert np.max(np.abs(ds.cpu().numpy() - want)) <= 2e-5 * max(1.0, np.abs(want).max())
