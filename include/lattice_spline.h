@@ -221,6 +221,25 @@ size_t ls_adjoint_scratch_bytes(ls_volume v, int64_t n);
 ls_status ls_morton_sort(const float *pts, int64_t n, const float *origin, float cell,
                          int32_t *perm, uint32_t *keys_out, void *scratch, ls_stream stream);
 size_t ls_morton_scratch_bytes(int64_t n);
+/*
+ * ls_morton_sort without any device allocation (the paper has no counterpart).
+ * Same arguments and results as ls_morton_sort with scratch = NULL, for
+ * callers that must not allocate device memory while they run (a framework
+ * whose caching allocator owns the device memory, a latency-bound loop that
+ * cannot absorb cudaMalloc/cudaFree, a fixed up-front memory budget).  Its
+ * scratch is one static 3.25 MiB device array compiled into the library, which
+ * every GPU that loads the library holds until the process exits.
+ *  - n is limited to 262144 (2^18) points; larger n returns LS_ERR_INVALID_ARG
+ *    with a message.  It calls no cudaMalloc, cudaFree or allocating routine.
+ *  - The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress (with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents;
+ *    nothing in it has to start at zero.  Calls whose work overlaps on the GPU
+ *    (other streams, other threads, same device) race on it: serialise them.
+ */
+ls_status ls_morton_sort_noalloc(const float *pts, int64_t n, const float *origin, float cell,
+                                 int32_t *perm, uint32_t *keys_out, ls_stream stream);
 /* dst[i] = src[perm[i]] for rows of `width` floats (gather), or the inverse scatter. */
 ls_status ls_permute_rows(const float *src, const int32_t *perm, int64_t n, int32_t width,
                           int32_t inverse, float *dst, ls_stream stream);

@@ -81,6 +81,8 @@ SIGNATURES = {
     "ls_adjoint_scratch_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64]),
     "ls_morton_sort": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_float,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ls_morton_sort_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_float,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "ls_morton_scratch_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "ls_permute_rows": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
