@@ -1,20 +1,26 @@
 """Benchmark: evaluation throughput of lattice splines on one B300 (Gpoints/s).
 
-Workload (one "step"): the BCC configuration -- coefficients on 2 cosets of
-128^3 (bounding box 0..255) as the smooth field sin(0.05x)cos(0.07y)+0.1N(0,1),
-evaluated with the linear 4-direction and the doubled 8-direction ("quintic")
-box splines at 2^24 uniform points and at 2^24 points along 4096 parallel rays
-(ray-march order): four launches, 2^26 point evaluations per step.
+Workload of one "step" (the headline line): the BCC configuration --
+coefficients on 2 cosets of 128^3 (bounding box 0..255) holding the smooth field
+sin(0.05x)cos(0.07y)+0.1N(0,1), evaluated with the linear 4-direction and the
+doubled 8-direction ("quintic") box splines at 2^24 uniform points and at 2^24
+points along 4096 parallel rays (ray-march order): four launches, 2^26 point
+evaluations per step, FP32 storage and arithmetic.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-extras]
 
-Prints one JSON line.  Multi-GPU runs (torchrun) shard nothing: every rank
-evaluates its own full per-GPU workload (weak scaling), no collective on the
-data path; timing is the max over ranks.
+Prints one JSON line.  "extras" holds the other configurations (forward +
+backward against plain FP32, FCC unsorted vs Morton-sorted with the gradient,
+the batched BF16/FP16 launch in a CUDA graph, and CG iterations); "--impl
+reference" times the FP64 CPU oracle on the same workload.  Multi-GPU runs
+(torchrun) shard nothing: every rank evaluates its own full per-GPU workload
+(weak scaling), no collective on the data path; timing is the max over ranks.
 """
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
 import statistics
@@ -40,10 +46,21 @@ WORKLOAD = ("bcc 2x128^3 smooth field; linear + quintic box splines; 2^24 unifor
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time (every rank runs its own replica of the workload)."""
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_per_rank: int, world: int, seconds: float) -> float:
+    """Gpoints/s of all ranks together: units all ranks processed / slowest time."""
+    return points_per_rank * world / seconds / 1e9
 
 
 def make_inputs(seed_offset: int = 0):
@@ -119,7 +136,7 @@ class ClockSampler:
 ORACLE_SAMPLE = {"bcc_linear": 1 << 15, "bcc_quintic": 1 << 11}
 
 
-def oracle_leg(coef, pts_sets, repeats: int = 1):
+def oracle_leg(coef, pts_sets):
     import oracle
     from oracle import specs as ospecs
     cores = len(os.sched_getaffinity(0))
@@ -127,24 +144,58 @@ def oracle_leg(coef, pts_sets, repeats: int = 1):
             "bcc_quintic": ospecs.bcc_quintic().with_extent(EXT)}
     c64 = coef.astype(np.float64).ravel()
     rng = np.random.default_rng(99)
-    samples = {}
+    per_pt = {}
     for sp, ps in CASES:
         idx = rng.choice(len(pts_sets[ps]), ORACLE_SAMPLE[sp], replace=False)
-        samples[(sp, ps)] = pts_sets[ps][idx].astype(np.float64)
-    # time per point for each case, then the step-weighted rate (equal points per case)
-    per_pt = {}
-    for _ in range(repeats):
-        for key, p in samples.items():
-            t0 = time.perf_counter()
-            oracle.eval_sum(spec[key[0]], c64, p, nthreads=cores)
-            dt = time.perf_counter() - t0
-            per_pt[key] = min(per_pt.get(key, 1e30), dt / len(p))
-    n_per_case = {("bcc_linear", "uniform"): N_UNIFORM, ("bcc_linear", "rays"): N_RAYS * RAY_STEPS,
-                  ("bcc_quintic", "uniform"): N_UNIFORM, ("bcc_quintic", "rays"): N_RAYS * RAY_STEPS}
-    step_time = sum(per_pt[k] * n_per_case[k] for k in per_pt)
-    value = sum(n_per_case.values()) / step_time / 1e9
-    sample = "; ".join(f"{k[0]}/{k[1]}: {ORACLE_SAMPLE[k[0]]} pts" for k in samples)
+        p = pts_sets[ps][idx].astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.eval_sum(spec[sp], c64, p, nthreads=cores)
+        per_pt[(sp, ps)] = (time.perf_counter() - t0) / len(p)
+    n_case = {"uniform": N_UNIFORM, "rays": N_RAYS * RAY_STEPS}
+    step_time = sum(t * n_case[k[1]] for k, t in per_pt.items())
+    value = sum(n_case[k[1]] for k in per_pt) / step_time / 1e9
+    sample = "; ".join(f"{sp}/{ps}: {ORACLE_SAMPLE[sp]} random points of the step's set" for sp, ps in CASES)
     return value, cores, sample, step_time
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def time_ms(torch, fn, reps=10, warm=3):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def profile_counters(kernel_source: str, kernel: str):
+    """DRAM / L2 traffic per launch from a committed ncu summary, if it was taken
+    on exactly this generated kernel: the hash covers the generated source up to
+    the end of that kernel (helpers, point function and the kernel itself)."""
+    try:
+        m = kernel_source.index(kernel + "(const LsEvalArgs a)")
+        end = kernel_source.index("}\n\n", m) + 3
+    except ValueError:
+        return None, None
+    h = hashlib.sha1(kernel_source[:end].encode()).hexdigest()[:16]
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.json")):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+        except (OSError, ValueError):
+            continue
+        for ent in d.get("kernels", []):
+            if ent.get("kernel") == kernel and ent.get("source_sha1_16") == h:
+                return ent, os.path.basename(path)
+    return None, None
 
 
 # ---------------------------------------------------------------------------
@@ -159,7 +210,8 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2102_08518_b300.api import Spline, Volume
+    from paper_2102_08518_b300.api import Spline, Volume, probe_gather, table
+    from paper_2102_08518_b300.roofline import distinct_sectors_per_point
 
     coef_np, pts_np = make_inputs(seed_offset=rank)
     dev = torch.device("cuda", local)
@@ -199,34 +251,55 @@ def run_gpu(args):
     clocks = clk.stop()
     ms_total = t_start.elapsed_time(t_end)
     if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+        ms_total = max_over_ranks(ms_total, dist, dev)
         dist.barrier()
     ms_step = ms_total / args.steps
     pts_per_step = N_UNIFORM * 2 + N_RAYS * RAY_STEPS * 2
-    value = pts_per_step * world / (ms_step * 1e-3) / 1e9
+    value = whole_job_rate(pts_per_step, world, ms_step * 1e-3)
     case_ms = [statistics.mean(case_events[k][ci][0].elapsed_time(case_events[k][ci][1]) for k in range(args.steps))
                for ci in range(len(CASES))]
+
+    # --- gather roofline: random 32-byte-sector rate of the L2-resident volume ------
+    probe_out = torch.empty(1 << 22, device=dev)
+    flat = coef.view(-1)
+    probe_ms = time_ms(torch, lambda: probe_gather(flat, 32, 1 << 22, 148 * 16, probe_out))
+    probe_gloads = (1 << 22) * 32 / (probe_ms * 1e-3) / 1e9
+    peak_l2 = probe_gloads * 32.0                      # GB/s of 32-byte sectors
+    sample = {ps: v[np.random.default_rng(7).choice(len(v), 1 << 14, replace=False)] for ps, v in pts_np.items()}
+    sectors = {sp: distinct_sectors_per_point(table(sp), EXT, sample["uniform"]) for sp in splines}
     per_case = {}
     for (sp, ps), ms in zip(CASES, case_ms):
         n = N_UNIFORM if ps == "uniform" else N_RAYS * RAY_STEPS
-        per_case[f"{sp}/{ps}"] = {"gpoints_s": round(n / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 4)}
-
-    # roofline of the dominant kernel: the quintic on uniform points (FP32 FMA bound)
+        info = splines[sp].info()
+        l2_gbs = sectors[sp] * 32.0 * n / (ms * 1e-3) / 1e9
+        fma_tf = 2.0 * info["fma_value"] * n / (ms * 1e-3) / 1e12
+        per_case[f"{sp}/{ps}"] = {"gpoints_s": round(n / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 4),
+                                  "l2_gather_gbs": round(l2_gbs, 1), "fp32_fma_tflops": round(fma_tf, 2)}
     info = splines["bcc_quintic"].info()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2032.0
-    peak_tflops = sms * 128 * 2 * max_mhz * 1e6 / 1e12
-    dom_ms = per_case["bcc_quintic/uniform"]["ms"]
-    achieved = 2.0 * info["fma_value"] * N_UNIFORM / (dom_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "ls_eval__bcc_quintic_f32", "achieved": round(achieved, 3),
-                "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-                "traffic": None, "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flop x {max_mhz:.0f} MHz",
-                "flops_per_point": 2 * info["fma_value"], "regs": info["regs_eval"]}
+    peak_fma = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    dom = per_case["bcc_quintic/uniform"]
+    kname = "ls_eval__bcc_quintic_f32"
+    counters, cfile = profile_counters(splines["bcc_quintic"].source(), kname)
+    traffic = None
+    if counters:
+        traffic = counters.get("dram_bytes_per_launch")
+    roofline = {"bound": "l2", "kernel": kname, "achieved": dom["l2_gather_gbs"], "peak": round(peak_l2, 1),
+                "unit": "GB/s", "frac": round(dom["l2_gather_gbs"] / peak_l2, 4), "traffic": traffic,
+                "algorithmic_bytes_per_point": round(sectors["bcc_quintic"] * 32.0, 1),
+                "coef_bytes_per_point": 4 * info["n_sites"],
+                "peak_source": ("measured in this run: random 4-byte loads from the L2-resident 16 MiB volume, "
+                                f"{probe_gloads:.1f} G loads/s x 32-byte sectors"),
+                "counters_from": cfile,
+                "l2_sector_bytes_per_launch": counters.get("l2_sector_bytes_per_launch") if counters else None}
+    roofline_alu = {"bound": "alu", "kernel": kname, "achieved": dom["fp32_fma_tflops"], "peak": round(peak_fma, 2),
+                    "unit": "TFLOP/s", "frac": round(dom["fp32_fma_tflops"] / peak_fma, 4),
+                    "flops_per_point": 2 * info["fma_value"], "regs": info["regs_eval"],
+                    "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flop x {max_mhz:.0f} MHz"}
 
-    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    # --- end to end through the C ABI with host buffers ------------------------------
     host_pts = {k: torch.from_numpy(v).pin_memory() for k, v in pts_np.items()}
     host_out = {k: torch.empty(v.shape[0], dtype=torch.float32).pin_memory() for k, v in pts_np.items()}
 
@@ -243,13 +316,10 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    h2d = sum(host_pts[ps].numel() * 4 for _, ps in CASES)
-    d2h = sum(host_out[ps].numel() * 4 for _, ps in CASES)
+        e2e_s = max_over_ranks(e2e_s, dist, dev)
     e2e = {"value": round(pts_per_step * world / e2e_s / 1e9, 4), "unit": "Gpoints/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+           "h2d_bytes_per_step": sum(host_pts[ps].numel() * 4 for _, ps in CASES),
+           "d2h_bytes_per_step": sum(host_out[ps].numel() * 4 for _, ps in CASES)}
 
     result = {"metric": METRIC, "value": round(value, 4), "unit": "Gpoints/s", "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -258,8 +328,19 @@ def run_gpu(args):
               "config": {"workload": WORKLOAD, "points_per_step": pts_per_step, "coef_bytes": coef_np.nbytes,
                          "l2": "points 201 MB per set > 126 MB L2 (inputs larger than L2); coefficient volume "
                                "16 MiB L2-resident by design", "parallelism": f"replicas x{world}"},
-              "per_case": per_case, "roofline": roofline, "e2e": e2e, "clocks": clocks,
-              "gpu_launches": len(CASES) * args.steps}
+              "per_case": per_case, "roofline": roofline, "roofline_alu": roofline_alu, "e2e": e2e,
+              "clocks": clocks, "gpu_launches": len(CASES) * args.steps}
+    del host_pts, host_out
+    if not args.no_extras:
+        extras = {}
+        for name, fn in (("fwd_bwd", extra_fwd_bwd), ("fcc_sorted", extra_fcc), ("batched", extra_batched),
+                         ("cg", extra_cg)):
+            try:
+                extras[name] = fn(torch, dev, vols, pts, outs)
+            except Exception as ex:       # an extra must not lose the headline line
+                extras[name] = {"error": f"{type(ex).__name__}: {ex}"}
+            torch.cuda.empty_cache()
+        result["extras"] = extras
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample, _ = oracle_leg(coef_np, pts_np)
         result["cpu_baseline"] = {"value": round(v, 6), "unit": "Gpoints/s", "cores": cores, "kind": "oracle",
@@ -269,20 +350,153 @@ def run_gpu(args):
     return result if rank == 0 else None
 
 
+# ---------------------------------------------------------------------------
+# extras: the other configurations
+# ---------------------------------------------------------------------------
+
+def extra_fwd_bwd(torch, dev, vols, pts, outs):
+    """Plain FP32 forward vs value+gradient and the two adjoints (BCC quintic, 2^24 uniform points)."""
+    from paper_2102_08518_b300 import _abi
+    import ctypes
+    vol = vols["bcc_quintic"]
+    p = pts["uniform"]
+    n = p.shape[0]
+    g = torch.randn(n, device=dev, generator=torch.Generator(device=dev).manual_seed(11))
+    dc = torch.zeros(vol.n_coef, device=dev)
+    scratch = torch.empty(int(_abi.lib().ls_adjoint_scratch_bytes(vol.handle, n)), dtype=torch.uint8, device=dev)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def adj(det):
+        _abi.check(_abi.lib().ls_adjoint_coef(vol.handle, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                              n, ctypes.c_void_p(dc.data_ptr()), det,
+                                              ctypes.c_void_p(scratch.data_ptr()), stream), "adjoint")
+
+    t_plain = time_ms(torch, lambda: vol.eval(p, outs["uniform"]))
+    t_grad = time_ms(torch, lambda: vol.eval_grad(p))
+    t_adj_a = time_ms(torch, lambda: adj(0))
+    t_adj_d = time_ms(torch, lambda: adj(1), reps=5)
+    gp = lambda ms: round(n / (ms * 1e-3) / 1e9, 3)
+    return {"workload": "bcc_quintic 2x128^3, 2^24 uniform points", "plain_f32_gpoints_s": gp(t_plain),
+            "value_grad_gpoints_s": gp(t_grad), "adjoint_atomic_gpoints_s": gp(t_adj_a),
+            "adjoint_deterministic_gpoints_s": gp(t_adj_d),
+            "fwd_bwd_atomic_gpoints_s": gp(t_grad + t_adj_a), "fwd_bwd_deterministic_gpoints_s": gp(t_grad + t_adj_d),
+            "fwd_bwd_vs_plain": round(t_plain / (t_grad + t_adj_a), 3)}
+
+
+def extra_fcc(torch, dev, vols, pts, outs):
+    """FCC 4x128^3, 2^26 uniform points: unsorted vs Morton-sorted evaluation and gradient."""
+    from paper_2102_08518_b300.api import Spline, Volume, morton_sort, permute_rows
+    ext = (128, 128, 128)
+    coef = workloads.coef_uniform_torch("fcc", ext, seed=0)
+    lo, hi = workloads.inner_box("fcc6", ext)
+    n = 1 << 26
+    p = workloads.points_uniform_torch(n, lo, hi, seed=5)
+    vol = Volume(Spline("fcc6", "f32"), ext, coef)
+    out = torch.empty(n, device=dev)
+    t_uns = time_ms(torch, lambda: vol.eval(p, out), reps=5)
+    t_grad = time_ms(torch, lambda: vol.eval_grad(p, want_value=True), reps=3)
+    res = {"workload": "fcc6 4x128^3 (256^3 box), 2^26 uniform points", "unsorted_gpoints_s": round(n / t_uns / 1e6, 3),
+           "unsorted_value_grad_gpoints_s": round(n / t_grad / 1e6, 3)}
+    best = None
+    for cell in (1.0, 2.0, 4.0, 8.0):                 # sort granularity (Morton cell edge)
+        t_sort = time_ms(torch, lambda: morton_sort(p, cell=cell), reps=3, warm=1)
+        perm = morton_sort(p, cell=cell)
+        ps = permute_rows(p, perm)
+        t_perm = time_ms(torch, lambda: permute_rows(p, perm), reps=3, warm=1)
+        t_sorted = time_ms(torch, lambda: vol.eval(ps, out), reps=5)
+        ent = {"cell": cell, "sort_ms": round(t_sort, 3), "permute_ms": round(t_perm, 3),
+               "sorted_eval_ms": round(t_sorted, 3), "sorted_gpoints_s": round(n / t_sorted / 1e6, 3),
+               "sort_plus_eval_gpoints_s": round(n / (t_sort + t_perm + t_sorted) / 1e6, 3)}
+        if best is None or t_sorted < best[0]:
+            best = (t_sorted, ent, ps)
+        del perm
+    res["sorted"] = best[1]
+    t_sg = time_ms(torch, lambda: vol.eval_grad(best[2], want_value=True), reps=3)
+    res["sorted_value_grad_gpoints_s"] = round(n / t_sg / 1e6, 3)
+    res["unsorted_ms"] = round(t_uns, 3)
+    return res
+
+
+def extra_batched(torch, dev, vols, pts, outs):
+    """64 volumes (edges {32..256}, mixed splines), BF16 / FP16 storage, one persistent
+    launch replayed from a CUDA graph, against plain FP32 per-volume launches."""
+    from paper_2102_08518_b300.api import Plan, Spline, Volume
+    recipe = workloads.batch_recipe(64, seed=0)
+    total = sum(it.n_points for it in recipe)
+    coefs, ptsl, outl, exts = [], [], [], []
+    for it in recipe:
+        lat = workloads.SPLINE_LATTICE[it.spline]
+        coefs.append(workloads.coef_uniform_torch(lat, it.ext, seed=it.seed))
+        lo, hi = workloads.inner_box(it.spline, it.ext)
+        ptsl.append(workloads.points_uniform_torch(it.n_points, lo, hi, seed=it.seed + 1))
+        outl.append(torch.empty(it.n_points, device=dev))
+        exts.append(it.ext)
+    res = {"workload": f"64 volumes, {total} points, edges {{32..256}}, 4 spline types", "points": total}
+    # plain FP32: one launch per volume
+    sp32 = {n: Spline(n, "f32") for n in set(it.spline for it in recipe)}
+    v32 = [Volume(sp32[it.spline], e, c) for it, e, c in zip(recipe, exts, coefs)]
+    t32 = time_ms(torch, lambda: [v.eval(p, o) for v, p, o in zip(v32, ptsl, outl)], reps=3)
+    res["plain_f32_per_volume_launches_gpoints_s"] = round(total / t32 / 1e6, 3)
+    ref = [o.clone() for o in outl]
+    for dt, tdt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        spd = {n: Spline(n, dt) for n in sp32}
+        cd = [c.to(tdt) for c in coefs]
+        vd = [Volume(spd[it.spline], e, c) for it, e, c in zip(recipe, exts, cd)]
+        plan = Plan(vd, ptsl, outl, tile=0)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            plan.launch(stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            plan.launch(stream=torch.cuda.current_stream())
+        tg = time_ms(torch, graph.replay, reps=5)
+        plan.status()
+        err = max(float((o - r).abs().max()) for o, r in zip(outl, ref) if o.numel())
+        info = plan.info()
+        res[dt] = {"graph_gpoints_s": round(total / tg / 1e6, 3), "ms": round(tg, 3), "tile": info["tile"],
+                   "items": info["n_items"], "max_abs_err_vs_f32_storage": round(err, 7),
+                   "storage_bound_u_cmax": 2.0 ** -8 if dt == "bf16" else 2.0 ** -11}
+        del plan, vd, cd
+    return res
+
+
+def extra_cg(torch, dev, vols, pts, outs):
+    """CG least-squares fits with 2^22 Gaussian samples: ms per iteration."""
+    from paper_2102_08518_b300.api import Spline, Volume, cg_fit
+    res = {}
+    for name, ext in (("tricubic", (128, 128, 128)), ("bcc_quintic", (128, 128, 128))):
+        lat = workloads.SPLINE_LATTICE[name]
+        lo, hi = workloads.bounding_box(lat, ext)
+        p_np, y_np = workloads.gaussian_samples(1 << 22, lo, hi, seed=3)
+        p = torch.from_numpy(p_np).to(dev)
+        y = torch.from_numpy(y_np).to(dev)
+        for det in (False, True):
+            vol = Volume(Spline(name, "f32"), ext, torch.zeros(len(workloads.LATTICES[lat][2]) * 128 ** 3,
+                                                              device=dev))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, hist = cg_fit(vol, p, y, lam=1e-6, max_iter=10, rel_tol=0.0, deterministic=det)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            res[f"{name}_{'det' if det else 'atomic'}"] = {"ms_per_iter": round(1e3 * dt / max(it, 1), 3),
+                                                           "iters": it, "resid_ratio": float(hist[-1] / hist[0])}
+    res["workload"] = "tricubic 128^3 and bcc_quintic 2x128^3, 2^22 samples of exp(-|x-c|^2/400)+0.01N"
+    return res
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return None
     coef_np, pts_np = make_inputs()
-    for _ in range(args.warmup):
-        pass
     vals = []
-    t_all = 0.0
-    v = cores = sample = None
-    for _ in range(args.steps):
-        v, cores, sample, st = oracle_leg(coef_np, pts_np)
+    cores = sample = None
+    for _ in range(max(1, args.steps)):
+        v, cores, sample, _ = oracle_leg(coef_np, pts_np)
         vals.append(v)
-        t_all += st
     value = statistics.median(vals)
     ms = 1e3 * (N_UNIFORM * 2 + N_RAYS * RAY_STEPS * 2) / (value * 1e9)
     return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gpoints/s",
@@ -302,8 +516,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours":
+    if args.impl == "ours" and args.warmup < 3:
         args.warmup = 3
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if res is not None:

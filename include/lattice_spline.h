@@ -261,12 +261,18 @@ ls_status ls_probe_gather(const float *table, int64_t table_elems, int32_t loads
  * pts[v], out[v]: device pointers; n[v]: point counts.  The plan copies the
  * arrays; the buffers must stay valid while the plan is launched.
  * ls_plan_launch only enqueues one kernel (no allocation, no host sync) and may
- * be captured into a CUDA graph.  tile: points per work item (0 = autotuned).
+ * be captured into a CUDA graph.  tile: points per work item; 0 = autotuned: ls_plan_create
+ * then times the kernel for several tile sizes (launching it on the volumes' data) and
+ * keeps the fastest; results are cached per (kernel, volume sizes) for the process.
  */
 ls_status ls_plan_create(int32_t n_vol, const ls_volume *vols, const float *const *pts,
                          const int64_t *n, float *const *out, int32_t tile, ls_plan *plan);
+/* The tile (points per work item) the plan uses, and the block size of its kernel. */
+ls_status ls_plan_info(ls_plan plan, int32_t *tile, int32_t *block, int32_t *n_items, int32_t *grid);
 ls_status ls_plan_launch(ls_plan plan, ls_stream stream);
-/* Status word of the last launch (LS_OK or LS_ERR_TIMEOUT); synchronises the stream. */
+/* Status word of the launches so far (LS_OK, or LS_ERR_DEVICE if a work item named an
+ * unknown spline); synchronises the stream.  The persistent kernel never waits: blocks
+ * take items with an atomic ticket until the list is exhausted. */
 ls_status ls_plan_status(ls_plan plan, ls_stream stream);
 ls_status ls_plan_destroy(ls_plan plan);
 

@@ -91,6 +91,7 @@ SIGNATURES = {
     "ls_plan_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_void_p), c_i64p, ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "ls_plan_info": (ctypes.c_int, [ctypes.c_void_p, c_i32p, c_i32p, c_i32p, c_i32p]),
     "ls_plan_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "ls_plan_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "ls_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),

@@ -245,3 +245,104 @@ def probe_gather(table_t: torch.Tensor, loads: int, nthreads: int, blocks: int =
     _abi.check(_abi.lib().ls_probe_gather(_ptr(table_t), table_t.numel(), loads, _ptr(out), nthreads, blocks,
                                           _stream(stream)), "ls_probe_gather")
     return out
+
+
+# ---------------------------------------------------------------------------
+# least-squares fit and autograd
+# ---------------------------------------------------------------------------
+
+def cg_fit(volume: "Volume", pts: torch.Tensor, y: torch.Tensor, lam: float = 0.0, max_iter: int = 200,
+           rel_tol: float = 1e-6, deterministic: bool = False, stream=None):
+    """CGLS on min ||A c - y||^2 + lam ||c||^2; the volume's coefficients (FP32)
+    hold the initial guess and receive the result.  Returns (iterations, history)."""
+    import numpy as np
+    pts = _check_pts(pts, volume.spline.dim)
+    y = y.contiguous().float()
+    hist = np.zeros(max_iter + 1)
+    iters = ctypes.c_int32()
+    _abi.check(_abi.lib().ls_cg_fit(volume.handle, _ptr(pts), _ptr(y), pts.shape[0], float(lam), int(max_iter),
+                                    float(rel_tol), int(deterministic),
+                                    hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(iters),
+                                    _stream(stream)), "ls_cg_fit")
+    return iters.value, hist[: iters.value + 1]
+
+
+class SplineEval(torch.autograd.Function):
+    """f(pts) = sum_n coef_n phi(pts - n) with gradients for coef and pts.
+
+    Forward runs the fused value + gradient kernel when pts needs a gradient;
+    backward is the adjoint kernel for coef (atomic or deterministic) and
+    gout * grad f for pts.
+    """
+
+    @staticmethod
+    def forward(ctx, coef, pts, spline, ext, deterministic):
+        vol = Volume(spline, ext, coef.detach().contiguous())
+        if pts.requires_grad:
+            val, grad = vol.eval_grad(pts.detach())
+        else:
+            val, grad = vol.eval(pts.detach()), None
+        ctx.vol = vol
+        ctx.deterministic = deterministic
+        ctx.coef_shape = coef.shape
+        ctx.save_for_backward(pts.detach(), grad if grad is not None else torch.empty(0, device=pts.device))
+        return val
+
+    @staticmethod
+    def backward(ctx, gout):
+        pts, grad = ctx.saved_tensors
+        gcoef = gpts = None
+        gout = gout.contiguous()
+        if ctx.needs_input_grad[0]:
+            gcoef = ctx.vol.adjoint(pts, gout, deterministic=ctx.deterministic).view(ctx.coef_shape)
+        if ctx.needs_input_grad[1]:
+            gpts = gout[:, None] * grad
+        return gcoef, gpts, None, None, None
+
+
+def spline_eval(spline: Spline, ext: Sequence[int], coef: torch.Tensor, pts: torch.Tensor,
+                deterministic: bool = False) -> torch.Tensor:
+    return SplineEval.apply(coef, pts, spline, tuple(ext), deterministic)
+
+
+# ---------------------------------------------------------------------------
+# batched persistent evaluation
+# ---------------------------------------------------------------------------
+
+class Plan:
+    """One persistent launch over many volumes, each with its own point batch."""
+
+    def __init__(self, volumes: Sequence["Volume"], pts: Sequence[torch.Tensor], outs: Sequence[torch.Tensor],
+                 tile: int = 0):
+        n = len(volumes)
+        self.volumes = list(volumes)
+        self.pts = [_check_pts(p, v.spline.dim) for p, v in zip(pts, volumes)]
+        self.outs = list(outs)
+        vh = (ctypes.c_void_p * n)(*[v.handle.value for v in volumes])
+        ph = (ctypes.c_void_p * n)(*[p.data_ptr() for p in self.pts])
+        nh = (ctypes.c_int64 * n)(*[p.shape[0] for p in self.pts])
+        oh = (ctypes.c_void_p * n)(*[o.data_ptr() for o in self.outs])
+        h = ctypes.c_void_p()
+        _abi.check(_abi.lib().ls_plan_create(n, vh, ph, nh, oh, int(tile), ctypes.byref(h)), "ls_plan_create")
+        self.handle = h
+
+    def info(self):
+        t, b, ni, g = (ctypes.c_int32() for _ in range(4))
+        _abi.check(_abi.lib().ls_plan_info(self.handle, ctypes.byref(t), ctypes.byref(b), ctypes.byref(ni),
+                                           ctypes.byref(g)), "ls_plan_info")
+        return {"tile": t.value, "block": b.value, "n_items": ni.value, "grid": g.value}
+
+    def launch(self, stream=None):
+        _abi.check(_abi.lib().ls_plan_launch(self.handle, _stream(stream)), "ls_plan_launch")
+
+    def status(self, stream=None):
+        _abi.check(_abi.lib().ls_plan_status(self.handle, _stream(stream)), "ls_plan_status")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                _abi.lib().ls_plan_destroy(h)
+            except Exception:
+                pass
+            self.handle = None

@@ -628,7 +628,7 @@ ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int6
 }
 
 // ---------------------------------------------------------------------------
-// not yet provided
+// FP64 device dot product
 // ---------------------------------------------------------------------------
 
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -684,19 +684,6 @@ ls_status ls_probe_gather(const float *table, int64_t table_elems, int32_t loads
     return LS_OK;
 }
 
-ls_status ls_plan_create(int32_t, const ls_volume *, const float *const *, const int64_t *, float *const *, int32_t,
-                         ls_plan *)
-{
-    return ls_fail(LS_ERR_UNSUPPORTED, "batched plans not available yet");
-}
-ls_status ls_plan_launch(ls_plan, ls_stream) { return ls_fail(LS_ERR_UNSUPPORTED, "batched plans not available yet"); }
-ls_status ls_plan_status(ls_plan, ls_stream) { return ls_fail(LS_ERR_UNSUPPORTED, "batched plans not available yet"); }
-ls_status ls_plan_destroy(ls_plan) { return LS_OK; }
-ls_status ls_cg_fit(ls_volume, const float *, const float *, int64_t, double, int32_t, double, int32_t, double *,
-                    int32_t *, ls_stream)
-{
-    return ls_fail(LS_ERR_UNSUPPORTED, "ls_cg_fit not available yet");
-}
 ls_status ls_dot_f64(const float *a, const float *b, int64_t n, double *result, ls_stream stream)
 {
     if (n < 0 || (n > 0 && (!a || !b)) || !result) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");

@@ -44,6 +44,7 @@ struct Emitter {
     std::ostringstream o;
     int tmp = 0;
     int fma = 0;
+    std::string ld = "ls_ld_f32";     // coefficient loader of the spline being emitted
     std::string fresh(const char *p) { return std::string(p) + std::to_string(tmp++); }
 };
 
@@ -79,24 +80,24 @@ int floordiv2(int v) { return (v >= 0) ? v / 2 : -((-v + 1) / 2); }
 // ---------------------------------------------------------------------------
 // common prologue: helpers and argument structs
 // ---------------------------------------------------------------------------
-void emit_prologue(Emitter &e, const Table &t, ls_dtype dt)
+const char *loader_name(ls_dtype dt)
+{
+    return dt == LS_BF16 ? "ls_ld_bf16" : dt == LS_F16 ? "ls_ld_f16" : "ls_ld_f32";
+}
+
+void emit_prologue(Emitter &e)
 {
     auto &o = e.o;
     o << "// generated by the lattice spline code generator; do not edit\n";
     o << "typedef unsigned short ls_u16;\n";
-    if (dt == LS_F32) {
-        o << "typedef float ls_coef_t;\n";
-        o << "static __device__ __forceinline__ float ls_ld(const ls_coef_t* p, int i) { return __ldg(p + i); }\n";
-    } else if (dt == LS_BF16) {
-        o << "typedef ls_u16 ls_coef_t;\n";
-        o << "static __device__ __forceinline__ float ls_ld(const ls_coef_t* p, int i) {"
-             " return __uint_as_float(((unsigned)__ldg(p + i)) << 16); }\n";
-    } else {
-        o << "typedef ls_u16 ls_coef_t;\n";
-        o << "static __device__ __forceinline__ float ls_ld(const ls_coef_t* p, int i) {"
-             " ls_u16 h = __ldg(p + i); float f; asm(\"cvt.f32.f16 %0, %1;\" : \"=f\"(f) : \"h\"(h)); return f; }\n";
-    }
-    o << "struct LsEvalArgs { const float* pts; float* out; float* grad; const ls_coef_t* coef;"
+    o << "static __device__ __forceinline__ float ls_ld_f32(const void* p, int i) {"
+         " return __ldg((const float*)p + i); }\n";
+    o << "static __device__ __forceinline__ float ls_ld_bf16(const void* p, int i) {"
+         " return __uint_as_float(((unsigned)__ldg((const ls_u16*)p + i)) << 16); }\n";
+    o << "static __device__ __forceinline__ float ls_ld_f16(const void* p, int i) {"
+         " ls_u16 h = __ldg((const ls_u16*)p + i); float f; asm(\"cvt.f32.f16 %0, %1;\" : \"=f\"(f) : \"h\"(h));"
+         " return f; }\n";
+    o << "struct LsEvalArgs { const float* pts; float* out; float* grad; const void* coef;"
          " long long n; int e0, e1, e2, cstride; };\n";
     o << "struct LsAdjArgs { const float* pts; const float* gout; float* dcoef;"
          " long long n; int e0, e1, e2, cstride; };\n";
@@ -108,7 +109,6 @@ void emit_prologue(Emitter &e, const Table &t, ls_dtype dt)
          " float tb_ = sw_ ? (A) : (B); int pa_ = sw_ ? (PB) : (PA); int pb_ = sw_ ? (PA) : (PB);"
          " unsigned na_ = sw_ ? (NB) : (NA); unsigned nb_ = sw_ ? (NA) : (NB);"
          " A = ta_; B = tb_; PA = pa_; PB = pb_; NA = na_; NB = nb_; }\n";
-    (void)t;
 }
 
 // ---------------------------------------------------------------------------
@@ -296,9 +296,9 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
         }
         if (declare_addr) {
             o << "      ad" << j << " = " << addr << ";\n";
-            if (load) o << "      c" << j << " = ls_ld(" << coef_expr << ", ad" << j << ");\n";
+            if (load) o << "      c" << j << " = " << e.ld << "(" << coef_expr << ", ad" << j << ");\n";
         } else {
-            o << "      c" << j << " = ls_ld(" << coef_expr << ", " << addr << ");\n";
+            o << "      c" << j << " = " << e.ld << "(" << coef_expr << ", " << addr << ");\n";
         }
     }
     o << "    } else {\n";
@@ -338,7 +338,7 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             o << ";\n";
         }
         if (declare_addr) o << "        ad" << j << " = ok ? adr : -1;\n";
-        if (load) o << "        c" << j << " = ok ? ls_ld(" << coef_expr << ", adr) : 0.0f;\n";
+        if (load) o << "        c" << j << " = ok ? " << e.ld << "(" << coef_expr << ", adr) : 0.0f;\n";
         o << "      }\n";
     }
     o << "    }\n";
@@ -606,7 +606,7 @@ void emit_separable_body(Emitter &e, const Table &t, bool grad, std::string &fva
     }
 }
 
-void emit_point_load(Emitter &e, const Table &t)
+void emit_point_load(Emitter &e, const Table &t, const char *skip = "continue")
 {
     auto &o = e.o;
     const int D = t.dim;
@@ -619,7 +619,7 @@ void emit_point_load(Emitter &e, const Table &t)
     for (int i = 0; i < D; ++i) o << (i ? " || " : "") << "(x" << i << " != x" << i << ")";
     o << ";\n";
     o << "      LS_OUT_OF_RANGE(isn ? __int_as_float(0x7fffffff) : 0.0f);\n";
-    o << "      continue;\n    }\n";
+    o << "      " << skip << ";\n    }\n";
 }
 
 std::string kname(const Table &t, const char *what)
@@ -629,18 +629,15 @@ std::string kname(const Table &t, const char *what)
     return n;
 }
 
-// value [+ gradient] kernel
-void emit_eval_kernel(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
-                      bool grad, GenInfo &info)
+// Per-point evaluation of value [+ gradient] as a device function, reused by
+// the per-spline kernel and by batched (multi-volume) kernels.
+void emit_eval_point(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach, bool grad,
+                     const std::string &fname)
 {
     auto &o = e.o;
     const int D = t.dim;
-    const int fma0 = e.fma;
-    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block;
-    if (var.min_blocks > 0) o << ", " << var.min_blocks;
-    o << ") " << kname(t, grad ? "eval_grad" : "eval") << "(const LsEvalArgs a)\n{\n";
+    o << "static __device__ __forceinline__ void " << fname << "(const LsEvalArgs& a, const long long i)\n{\n";
     o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride; (void)E1; (void)E2; (void)CS;\n";
-    o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
     if (grad) {
         o << "#define LS_OUT_OF_RANGE(V) { if (a.out) a.out[i] = (V);";
         for (int i = 0; i < D; ++i) o << " a.grad[(size_t)i * " << D << " + " << i << "] = (V);";
@@ -648,8 +645,8 @@ void emit_eval_kernel(Emitter &e, const Table &t, const ls_variant &var, const S
     } else {
         o << "#define LS_OUT_OF_RANGE(V) { a.out[i] = (V); }\n";
     }
-    o << "  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {\n";
-    emit_point_load(e, t);
+    o << "  {\n";
+    emit_point_load(e, t, "return");
     emit_classify(e, t);
     std::string fv;
     std::string g[3];
@@ -706,6 +703,22 @@ void emit_eval_kernel(Emitter &e, const Table &t, const ls_variant &var, const S
         o << "    a.out[i] = " << fv << ";\n";
     }
     o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
+}
+
+// value [+ gradient] kernel: grid-stride loop over the point function
+void emit_eval_kernel(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
+                      bool grad, GenInfo &info)
+{
+    auto &o = e.o;
+    const int fma0 = e.fma;
+    const std::string pf = kname(t, grad ? "eval_grad_pt" : "eval_pt");
+    emit_eval_point(e, t, var, st, reach, grad, pf);
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block;
+    if (var.min_blocks > 0) o << ", " << var.min_blocks;
+    o << ") " << kname(t, grad ? "eval_grad" : "eval") << "(const LsEvalArgs a)\n{\n";
+    o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
+    o << "  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) " << pf
+      << "(a, i);\n}\n\n";
     if (grad) info.fma_grad = e.fma - fma0;
     else info.fma_value = e.fma - fma0;
 }
@@ -952,6 +965,9 @@ void emit_adjoint_gather(Emitter &e, const Table &t, const ls_variant &var, cons
             cw_off.push_back(cw_total);
             cw_total += (int)(r.mono.size() * r.sites.size());
         }
+        o << "__constant__ int ls_doff[" << 3 * doffs.size() << "] = {";
+        for (const auto &d : doffs) o << d[0] << "," << d[1] << "," << d[2] << ",";
+        o << "};\n";
         o << "__constant__ float ls_cw[" << cw_total << "] = {";
         for (const auto &r : t.ref) {
             const size_t NS = r.sites.size(), NM = r.mono.size();
@@ -964,7 +980,9 @@ void emit_adjoint_gather(Emitter &e, const Table &t, const ls_variant &var, cons
       << "(const LsGatherArgs a)\n{\n";
     if (!sep) {
         o << "  __shared__ float cw[" << cw_total << "];\n";
+        o << "  __shared__ signed char jlut[" << t.ref.size() * lut_size << "];\n";
         o << "  for (int q = threadIdx.x; q < " << cw_total << "; q += blockDim.x) cw[q] = ls_cw[q];\n";
+        o << "  for (int q = threadIdx.x; q < " << t.ref.size() * lut_size << "; q += blockDim.x) jlut[q] = ls_jlut[q];\n";
         o << "  __syncthreads();\n";
     }
     o << "  const int H = a.halo;\n";
@@ -988,9 +1006,10 @@ void emit_adjoint_gather(Emitter &e, const Table &t, const ls_variant &var, cons
     }
     o << "    float acc = 0.0f;\n";
     const unsigned long long lut = coset_lut(t);
-    for (const auto &d : doffs) {
-        o << "    {\n";
-        for (int i = 0; i < D; ++i) o << "      const int kk" << i << " = nn" << i << " - (" << d[i] << ");\n";
+    // bin of k = n - d and the loop over its points; dexpr[i] is the offset
+    // component (an immediate, or a variable read from the offset table)
+    auto open_bin_loop = [&](const std::string *dexpr) {
+        for (int i = 0; i < D; ++i) o << "      const int kk" << i << " = nn" << i << " - (" << dexpr[i] << ");\n";
         if (t.scale == 2) {
             o << "      const int par = (kk0 & 1)";
             for (int i = 1; i < D; ++i) o << " | ((kk" << i << " & 1) << " << i << ")";
@@ -1010,8 +1029,14 @@ void emit_adjoint_gather(Emitter &e, const Table &t, const ls_variant &var, cons
         o << "        const float4 r = __ldg(a.srec + pos);\n";
         o << "        const float y0 = r.x" << (D > 1 ? ", y1 = r.y" : "") << (D > 2 ? ", y2 = r.z" : "")
           << ", gp = r.w;\n";
-        if (sep) {
-            // tensor product: site offset d is the 1D site triple; weights are products
+    };
+    if (sep) {
+        // tensor product: unrolled over the offsets; the weight of offset d is a
+        // product of 1D Horner forms with immediate coefficients
+        for (const auto &d : doffs) {
+            o << "    {\n";
+            std::string de[3] = {std::to_string(d[0]), std::to_string(d[1]), std::to_string(d[2])};
+            open_bin_loop(de);
             o << "        float w = gp;\n";
             for (int i = 0; i < D; ++i) {
                 const Axis &ax = t.sep[i];
@@ -1025,68 +1050,75 @@ void emit_adjoint_gather(Emitter &e, const Table &t, const ls_variant &var, cons
                           flit(ax.coef[jj * nc + dd]) + ")";
                 o << "        w *= " << acc << ";\n";
             }
-            o << "        acc = fmaf(1.0f, w, acc);\n";
+            o << "        acc += w;\n";
+            o << "      }\n    }\n";
+        }
+    } else {
+        // one copy of the body: the offsets come from a table that all threads of
+        // a warp read at the same index
+        o << "    for (int qd = 0; qd < " << doffs.size() << "; ++qd) {\n";
+        for (int i = 0; i < D; ++i) o << "      const int dv" << i << " = ls_doff[3 * qd + " << i << "];\n";
+        std::string de[3] = {"dv0", "dv1", "dv2"};
+        open_bin_loop(de);
+        // fold the point, then s = T d (reference offset of this coefficient)
+        o << "        const unsigned ng0 = y0 < 0.0f" << (D > 1 ? ", ng1 = y1 < 0.0f" : "")
+          << (D > 2 ? ", ng2 = y2 < 0.0f" : "") << ";\n";
+        if (t.fold == LS_FOLD_SIGNED_PERM) {
+            for (int i = 0; i < D; ++i)
+                o << "        float a" << i << " = fabsf(y" << i << "); int p" << i << " = " << i << "; unsigned g" << i
+                  << " = ng" << i << ";\n";
+            if (D == 3)
+                o << "        LS_CSWAP(a0, a1, p0, p1, g0, g1); LS_CSWAP(a1, a2, p1, p2, g1, g2);"
+                     " LS_CSWAP(a0, a1, p0, p1, g0, g1);\n";
+            else
+                o << "        LS_CSWAP(a0, a1, p0, p1, g0, g1);\n";
+            for (int r = 0; r < D; ++r) {
+                o << "        const int dr" << r << " = ";
+                for (int i = 0; i < D - 1; ++i) o << "(p" << r << " == " << i << ") ? dv" << i << " : ";
+                o << "dv" << (D - 1) << ";\n";
+                o << "        const int s" << r << " = g" << r << " ? -dr" << r << " : dr" << r << ";\n";
+            }
         } else {
-            // fold the point, then s = T d (reference offset of this site)
-            o << "        const unsigned ng0 = y0 < 0.0f" << (D > 1 ? ", ng1 = y1 < 0.0f" : "")
-              << (D > 2 ? ", ng2 = y2 < 0.0f" : "") << ";\n";
-            if (t.fold == LS_FOLD_SIGNED_PERM) {
-                for (int i = 0; i < D; ++i)
-                    o << "        float a" << i << " = fabsf(y" << i << "); int p" << i << " = " << i << "; unsigned g" << i
-                      << " = ng" << i << ";\n";
-                if (D == 3)
-                    o << "        LS_CSWAP(a0, a1, p0, p1, g0, g1); LS_CSWAP(a1, a2, p1, p2, g1, g2);"
-                         " LS_CSWAP(a0, a1, p0, p1, g0, g1);\n";
-                else
-                    o << "        LS_CSWAP(a0, a1, p0, p1, g0, g1);\n";
-                for (int r = 0; r < D; ++r) {
-                    o << "        const int dr" << r << " = ";
-                    for (int i = 0; i < D - 1; ++i) o << "(p" << r << " == " << i << ") ? " << d[i] << " : ";
-                    o << d[D - 1] << ";\n";
-                    o << "        const int s" << r << " = g" << r << " ? -dr" << r << " : dr" << r << ";\n";
-                }
-            } else {
-                for (int i = 0; i < D; ++i) o << "        const float a" << i << " = y" << i << ";\n";
-                for (int r = 0; r < D; ++r) o << "        const int s" << r << " = " << d[r] << ";\n";
+            for (int i = 0; i < D; ++i) o << "        const float a" << i << " = y" << i << ";\n";
+            for (int r = 0; r < D; ++r) o << "        const int s" << r << " = dv" << r << ";\n";
+        }
+        if (t.ref.size() > 1) {
+            o << "        unsigned q = 0u;\n";
+            for (size_t pi = 0; pi < t.planes.size(); ++pi) {
+                o << "        q |= (";
+                for (int i = 0; i < D; ++i) o << (i ? " + " : "") << flit(t.planes[pi][i]) << " * a" << i;
+                o << " - " << flit(t.planes[pi][3]) << " >= 0.0f) ? " << (1u << pi) << "u : 0u;\n";
             }
-            if (t.ref.size() > 1) {
-                o << "        unsigned q = 0u;\n";
-                for (size_t pi = 0; pi < t.planes.size(); ++pi) {
-                    o << "        q |= (";
-                    for (int i = 0; i < D; ++i) o << (i ? " + " : "") << flit(t.planes[pi][i]) << " * a" << i;
-                    o << " - " << flit(t.planes[pi][3]) << " >= 0.0f) ? " << (1u << pi) << "u : 0u;\n";
-                }
-                unsigned long long packed = 0;
-                for (int qq = 0; qq < t.bsp_mod; ++qq) {
-                    unsigned v = t.sigma[qq] < 0 ? 0u : (unsigned)t.sigma[qq];
-                    packed |= (unsigned long long)(v & 0xF) << (4 * qq);
-                }
-                o << "        const int psi = (int)((" << packed << "ull >> (4u * (q % " << t.bsp_mod << "u))) & 15ull);\n";
-            } else {
-                o << "        const int psi = 0;\n";
+            unsigned long long packed = 0;
+            for (int qq = 0; qq < t.bsp_mod; ++qq) {
+                unsigned v = t.sigma[qq] < 0 ? 0u : (unsigned)t.sigma[qq];
+                packed |= (unsigned long long)(v & 0xF) << (4 * qq);
             }
-            o << "        bool inr = true;\n";
-            for (int r = 0; r < D; ++r) o << "        inr = inr && (s" << r << " >= " << -R << ") && (s" << r << " <= " << R << ");\n";
-            o << "        if (!inr) continue;\n";
-            {
-                std::string li = "(s0 + " + std::to_string(R) + ")";
-                for (int r = 1; r < D; ++r)
-                    li = "(" + li + " * " + std::to_string(W) + " + (s" + std::to_string(r) + " + " + std::to_string(R) + "))";
-                o << "        const int li = " << li << ";\n";
+            o << "        const int psi = (int)((" << packed << "ull >> (4u * (q % " << t.bsp_mod << "u))) & 15ull);\n";
+        } else {
+            o << "        const int psi = 0;\n";
+        }
+        o << "        bool inr = true;\n";
+        for (int r = 0; r < D; ++r) o << "        inr = inr && (s" << r << " >= " << -R << ") && (s" << r << " <= " << R << ");\n";
+        o << "        if (!inr) continue;\n";
+        {
+            std::string li = "(s0 + " + std::to_string(R) + ")";
+            for (int r = 1; r < D; ++r)
+                li = "(" + li + " * " + std::to_string(W) + " + (s" + std::to_string(r) + " + " + std::to_string(R) + "))";
+            o << "        const int li = " << li << ";\n";
+        }
+        o << "        const int jj = jlut[psi * " << lut_size << " + li];\n";
+        o << "        if (jj < 0) continue;\n";
+        for (size_t k = 0; k < t.ref.size(); ++k) {
+            o << "        " << (k ? "else " : "") << "if (psi == " << k << ") {\n";
+            std::string uv[3];
+            for (int i = 0; i < D; ++i) {
+                uv[i] = "v" + std::to_string(k) + "_" + std::to_string(i);
+                o << "        const float " << uv[i] << " = a" << i << " - " << flit(t.ref[k].center[i]) << ";\n";
             }
-            o << "        const int jj = ls_jlut[psi * " << lut_size << " + li];\n";
-            o << "        if (jj < 0) continue;\n";
-            for (size_t k = 0; k < t.ref.size(); ++k) {
-                o << "        " << (k ? "else " : "") << "if (psi == " << k << ") {\n";
-                std::string uv[3];
-                for (int i = 0; i < D; ++i) {
-                    uv[i] = "v" + std::to_string(k) + "_" + std::to_string(i);
-                    o << "        const float " << uv[i] << " = a" << i << " - " << flit(t.ref[k].center[i]) << ";\n";
-                }
-                std::string w = emit_runtime_horner(e, t.ref[k], D, uv, cw_off[k], "jj");
-                o << "        acc = fmaf(gp, " << (w.empty() ? "0.0f" : w) << ", acc);\n";
-                o << "        }\n";
-            }
+            std::string w = emit_runtime_horner(e, t.ref[k], D, uv, cw_off[k], "jj");
+            o << "        acc = fmaf(gp, " << (w.empty() ? "0.0f" : w) << ", acc);\n";
+            o << "        }\n";
         }
         o << "      }\n    }\n";
     }
@@ -1100,7 +1132,8 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
 {
     Generated g;
     Emitter e;
-    emit_prologue(e, t, dt);
+    e.ld = loader_name(dt);
+    emit_prologue(e);
     Stencil st = union_stencil(t);
     int reach = 0;
     if (t.sep.empty()) {
@@ -1124,6 +1157,65 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
     emit_adjoint_gather(e, t, var, st, reach, doffs);
     g.info.n_reverse = (int)doffs.size();
     g.info.halo = bin_halo(t, reach);
+    g.source = e.o.str();
+    return g;
+}
+
+Generated generate_batch(const std::vector<const Table *> &tables, const std::vector<ls_dtype> &dts,
+                         const ls_variant &var)
+{
+    Generated g;
+    Emitter e;
+    emit_prologue(e);
+    for (size_t k = 0; k < tables.size(); ++k) {
+        const Table &t = *tables[k];
+        e.ld = loader_name(dts[k]);
+        Stencil st = union_stencil(t);
+        int reach = 0;
+        if (t.sep.empty()) {
+            for (auto &sv : st.sites)
+                for (int i = 0; i < t.dim; ++i) reach = std::max(reach, std::abs(sv[i]));
+        } else {
+            for (auto &ax : t.sep)
+                for (int sv : ax.sites) reach = std::max(reach, std::abs(sv));
+        }
+        emit_eval_point(e, t, var, st, reach, false, "ls_bpt_" + std::to_string(k));
+    }
+    auto &o = e.o;
+    o << "struct LsBatchVol { const float* pts; float* out; const void* coef; long long n;"
+         " int e0, e1, e2, cstride, kind, pad; };\n";
+    o << "struct LsBatchItem { int vol; int pad; long long p0, p1; };\n";
+    o << "struct LsBatchArgs { const LsBatchVol* vols; const LsBatchItem* items; int nitems; int pad;"
+         " unsigned* counter; unsigned* status; };\n";
+    o << "// Persistent launch: every block takes (volume, tile) items from the list by an\n"
+         "// atomic ticket until the list is exhausted; nothing waits on anything.\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block << ") ls_batch_eval(const LsBatchArgs b)\n{\n";
+    o << "  __shared__ int s_item;\n";
+    o << "  for (;;) {\n";
+    o << "    if (threadIdx.x == 0) s_item = (int)atomicAdd(b.counter, 1u);\n";
+    o << "    __syncthreads();\n";
+    o << "    const int it = s_item;\n";
+    o << "    __syncthreads();\n";
+    o << "    if (it >= b.nitems) {\n";
+    o << "      // exit ticket: the last block out resets both counters for the next launch\n";
+    o << "      if (threadIdx.x == 0) {\n";
+    o << "        __threadfence();\n";
+    o << "        const unsigned d = atomicAdd(b.counter + 1, 1u);\n";
+    o << "        if (d == gridDim.x - 1) { atomicExch(b.counter, 0u); atomicExch(b.counter + 1, 0u); }\n";
+    o << "      }\n";
+    o << "      return;\n";
+    o << "    }\n";
+    o << "    const LsBatchItem w = b.items[it];\n";
+    o << "    const LsBatchVol v = b.vols[w.vol];\n";
+    o << "    LsEvalArgs a;\n";
+    o << "    a.pts = v.pts; a.out = v.out; a.grad = 0; a.coef = v.coef; a.n = v.n;\n";
+    o << "    a.e0 = v.e0; a.e1 = v.e1; a.e2 = v.e2; a.cstride = v.cstride;\n";
+    o << "    switch (v.kind) {\n";
+    for (size_t k = 0; k < tables.size(); ++k)
+        o << "    case " << k << ": for (long long i = w.p0 + threadIdx.x; i < w.p1; i += blockDim.x) ls_bpt_" << k
+          << "(a, i); break;\n";
+    o << "    default: if (threadIdx.x == 0) atomicOr(b.status, 1u); break;\n";
+    o << "    }\n  }\n}\n";
     g.source = e.o.str();
     return g;
 }

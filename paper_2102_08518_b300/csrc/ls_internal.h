@@ -60,6 +60,9 @@ struct Generated {
 
 // Code generation (ls_codegen.cpp).
 Generated generate(const Table &t, ls_dtype coef_dtype, const ls_variant &var);
+// One persistent kernel ls_batch_eval over the point functions of several splines.
+Generated generate_batch(const std::vector<const Table *> &tables, const std::vector<ls_dtype> &dts,
+                         const ls_variant &var);
 
 // Kernel handles of one compiled module.
 struct Module {

@@ -74,6 +74,77 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const float *a, const 
 std::mutex g_mu;
 std::map<int, void *> g_ws;
 
+__global__ void cg_cr_kernel(float *c, const float *p, long long nc, float *r, const float *q, long long nr,
+                             const double *sc, double lambda)
+{
+    const double den = sc[1] + lambda * sc[2];
+    const double alpha = den > 0.0 ? sc[0] / den : 0.0;
+    const float af = (float)alpha;
+    const long long n = nc > nr ? nc : nr;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (i < nc) c[i] = fmaf(af, p[i], c[i]);
+        if (i < nr) r[i] = fmaf(-af, q[i], r[i]);
+    }
+}
+
+__global__ void cg_p_kernel(float *p, const float *s, long long nc, double *sc)
+{
+    const double beta = sc[0] > 0.0 ? sc[3] / sc[0] : 0.0;
+    const float bf = (float)beta;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += (long long)gridDim.x * blockDim.x)
+        p[i] = fmaf(bf, p[i], s[i]);
+}
+
+__global__ void cg_shift_gamma(double *sc) { sc[0] = sc[3]; }
+
+__global__ void axpby_kernel(float a, const float *x, float b, float *y, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = fmaf(a, x[i], b * y[i]);
+}
+
+__global__ void sub_from_kernel(const float *y, float *r, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        r[i] = y[i] - r[i];
+}
+
+unsigned grid_of(long long n)
+{
+    long long b = (n + 255) / 256;
+    if (b > 148 * 16) b = 148 * 16;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t cg_step_cr(float *c, const float *p, long long nc, float *r, const float *q, long long nr,
+                       const double *sc, double lambda, cudaStream_t st)
+{
+    cg_cr_kernel<<<grid_of(nc > nr ? nc : nr), 256, 0, st>>>(c, p, nc, r, q, nr, sc, lambda);
+    return cudaGetLastError();
+}
+
+cudaError_t cg_step_p(float *p, const float *s, long long nc, double *sc, cudaStream_t st)
+{
+    cg_p_kernel<<<grid_of(nc), 256, 0, st>>>(p, s, nc, sc);
+    cg_shift_gamma<<<1, 1, 0, st>>>(sc);
+    return cudaGetLastError();
+}
+
+cudaError_t axpby(float a, const float *x, float b, float *y, long long n, cudaStream_t st)
+{
+    axpby_kernel<<<grid_of(n), 256, 0, st>>>(a, x, b, y, n);
+    return cudaGetLastError();
+}
+
+cudaError_t sub_from(const float *y, float *r, long long n, cudaStream_t st)
+{
+    sub_from_kernel<<<grid_of(n), 256, 0, st>>>(y, r, n);
+    return cudaGetLastError();
+}
+
+namespace {
 }  // namespace
 
 cudaError_t convert(const void *src, int sdt, void *dst, int ddt, long long n, cudaStream_t st)

@@ -32,4 +32,16 @@ cudaError_t bin_starts(const uint32_t *key, long long n, uint32_t nbins, uint32_
 cudaError_t gather_probe(const float *table, long long table_elems, int loads, float *out, long long nthreads,
                          int blocks, cudaStream_t st);
 
+// CGLS vector steps (FP32 vectors, FP64 scalars resident on the device).
+//   sc[0] = gamma = ||s||^2, sc[1] = ||q||^2, sc[2] = ||p||^2, sc[3] = gamma_new
+// cg_step_cr:  alpha = gamma / (||q||^2 + lambda ||p||^2); c += alpha p; r -= alpha q
+cudaError_t cg_step_cr(float *c, const float *p, long long nc, float *r, const float *q, long long nr,
+                       const double *sc, double lambda, cudaStream_t st);
+// cg_step_p: p = s + (gamma_new / gamma) p, then gamma = gamma_new
+cudaError_t cg_step_p(float *p, const float *s, long long nc, double *sc, cudaStream_t st);
+// y = a*x + b*y (host scalars)
+cudaError_t axpby(float a, const float *x, float b, float *y, long long n, cudaStream_t st);
+// r = y - r (in place on r)
+cudaError_t sub_from(const float *y, float *r, long long n, cudaStream_t st);
+
 }  // namespace lsk

@@ -114,16 +114,25 @@ __global__ void __launch_bounds__(1024) scan_down(const uint32_t *in, long long 
     }
 }
 
+// Ranks every key of the tile (stable), stages the tile in shared memory in
+// digit order, then writes each digit's run to its global offset: consecutive
+// threads write consecutive addresses.
 __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint32_t *keys, const int32_t *vals, long long n,
                                                             int shift, const uint32_t *offs, int nblk,
                                                             uint32_t *keys_out, int32_t *vals_out)
 {
+    static_assert(kThreads == kBins, "one thread per digit in the digit scans");
     __shared__ uint32_t whist[kWarps][kBins];
+    __shared__ uint32_t bstart[kBins];
+    __shared__ uint32_t goff[kBins];
+    __shared__ uint32_t skey[kTile];
+    __shared__ int32_t sval[kTile];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int b = lane; b < kBins; b += 32) whist[warp][b] = 0;
     __syncwarp();
     // warp w owns the contiguous keys [base + w*32*kItems, ... + 32*kItems), rounds of 32
-    const long long base = (long long)blockIdx.x * kTile + (long long)warp * 32 * kItems;
+    const long long tile0 = (long long)blockIdx.x * kTile;
+    const long long base = tile0 + (long long)warp * 32 * kItems;
     uint32_t key[kItems];
     int32_t val[kItems];
     uint32_t rank[kItems];
@@ -138,6 +147,7 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint32_t *keys,
         unsigned peers = __match_any_sync(0xFFFFFFFFu, valid ? d : 0xFFFFFFFFu) & active;
         uint32_t before = valid ? whist[warp][d] : 0u;
         __syncwarp();
+        rank[it] = 0;
         if (valid) {
             rank[it] = before + __popc(peers & lt);
             if ((peers & lt) == 0u) whist[warp][d] = before + __popc(peers);
@@ -145,24 +155,45 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint32_t *keys,
         __syncwarp();
     }
     __syncthreads();
-    // per digit: prefix over warps (exclusive), then add the global offset
-    for (int b = threadIdx.x; b < kBins; b += kThreads) {
-        uint32_t run = offs[(size_t)b * nblk + blockIdx.x];
-        for (int w = 0; w < kWarps; ++w) {
-            uint32_t c = whist[w][b];
-            whist[w][b] = run;
-            run += c;
-        }
+    // per digit (thread = digit): warp prefix inside the block, block total
+    const int b = threadIdx.x;
+    uint32_t run = 0;
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = whist[w][b];
+        whist[w][b] = run;
+        run += c;
     }
+    bstart[b] = run;
+    goff[b] = offs[(size_t)b * nblk + blockIdx.x];
+    __syncthreads();
+    // exclusive scan of the block totals over digits (Hillis-Steele, inclusive then shift)
+    for (int off = 1; off < kBins; off <<= 1) {
+        const uint32_t v = b >= off ? bstart[b - off] : 0u;
+        __syncthreads();
+        bstart[b] += v;
+        __syncthreads();
+    }
+    const uint32_t incl = bstart[b];
+    __syncthreads();
+    bstart[b] = incl - run;
     __syncthreads();
     for (int it = 0; it < kItems; ++it) {
         long long i = base + (long long)it * 32 + lane;
         if (i < n) {
             const uint32_t d = (key[it] >> shift) & (kBins - 1);
-            const uint32_t dst = whist[warp][d] + rank[it];
-            keys_out[dst] = key[it];
-            vals_out[dst] = val[it];
+            const uint32_t lp = bstart[d] + whist[warp][d] + rank[it];
+            skey[lp] = key[it];
+            sval[lp] = val[it];
         }
+    }
+    __syncthreads();
+    const long long cnt = (n - tile0) < kTile ? (n - tile0) : kTile;
+    for (int lp = threadIdx.x; lp < cnt; lp += kThreads) {
+        const uint32_t k = skey[lp];
+        const uint32_t d = (k >> shift) & (kBins - 1);
+        const uint32_t dst = goff[d] + (uint32_t)lp - bstart[d];
+        keys_out[dst] = k;
+        vals_out[dst] = sval[lp];
     }
 }
 

@@ -1,0 +1,83 @@
+"""Algorithmic memory work of a stencil gather, for roofline accounting.
+
+For random points the coefficient gathers of one point touch a set of 32-byte
+sectors that no layout-preserving kernel can avoid fetching; their number
+(per point, averaged over a sample) is the algorithmic sector traffic the
+gather roofline is measured in.  Computed here from the sub-region table with
+the same region of evaluation, folding and storage layout the kernels use.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def stencil_indices(table, ext, pts: np.ndarray) -> np.ndarray:
+    """Linear coefficient indices (n_points, n_sites) of every point's stencil;
+    -1 where a site lies outside the arrays."""
+    spl = table.spline
+    lat = spl.lattice
+    D = lat.dim
+    e = np.array(list(ext)[:D], dtype=np.int64)
+    x = pts.astype(np.float32).astype(np.float64)
+    n = len(x)
+    # region of evaluation
+    if spl.roe == "parallelepiped":
+        k = np.floor(x)
+    else:
+        best = None
+        for l in lat.cosets:
+            l = np.asarray(l[:D], dtype=np.float64)
+            kk = lat.scale * np.round((x - l) / lat.scale) + l
+            d = np.sum((x - kk) ** 2, axis=1)
+            if best is None:
+                best, k = d, kk
+            else:
+                sel = d < best
+                best = np.where(sel, d, best)
+                k = np.where(sel[:, None], kk, k)
+    y = x - k
+    k = k.astype(np.int64)
+    if table.fold == "hyperoctahedral":
+        a = np.abs(y)
+        order = np.argsort(-a, axis=1, kind="stable")
+        sign = np.where(y < 0, -1, 1)
+        yref = np.take_along_axis(a, order, axis=1)
+    else:
+        order = np.tile(np.arange(D), (n, 1))
+        sign = np.ones((n, D), dtype=np.int64)
+        yref = y
+    regions = np.array([table.region_of(r) for r in yref]) if len(table.regions) > 1 else np.zeros(n, int)
+    nsite = max(len(r.sites) for r in table.regions)
+    out = np.full((n, nsite), -1, dtype=np.int64)
+    per = int(np.prod(e))
+    lut = np.full(2 ** D, -1, dtype=np.int64)
+    for j, l in enumerate(lat.cosets):
+        lut[sum(((v % 2) << i) for i, v in enumerate(l[:D]))] = j
+    for ri, reg in enumerate(table.regions):
+        m = regions == ri
+        if not np.any(m):
+            continue
+        for j, s in enumerate(reg.sites):
+            off = np.zeros((int(m.sum()), D), dtype=np.int64)
+            for r in range(D):
+                cart = order[m, r]
+                off[np.arange(len(cart)), cart] = sign[m][np.arange(len(cart)), cart] * s[r]
+            nn = k[m] + off
+            if lat.scale == 2:
+                cid = lut[np.sum((nn & 1) << np.arange(D), axis=1)]
+                idx = nn >> 1
+            else:
+                cid = np.zeros(len(nn), dtype=np.int64)
+                idx = nn
+            ok = np.all((idx >= 0) & (idx < e), axis=1)
+            lin = idx[:, 0] + e[0] * (idx[:, 1] + (e[1] * idx[:, 2] if D == 3 else 0)) + cid * per
+            out[np.where(m)[0], j] = np.where(ok, lin, -1)
+    return out
+
+
+def distinct_sectors_per_point(table, ext, pts: np.ndarray, elem_bytes: int = 4) -> float:
+    idx = stencil_indices(table, ext, pts)
+    sec = np.where(idx >= 0, (idx * elem_bytes) // 32, -1)
+    sec.sort(axis=1)
+    distinct = (np.diff(sec, axis=1) != 0).sum(axis=1) + 1 - (sec[:, 0] < 0)
+    return float(distinct.mean())

@@ -144,3 +144,25 @@ def batch_recipe(n_vol: int = 64, seed: int = 0, edges=(32, 48, 64, 96, 128, 192
         npts = int(round(2.0 ** rng.uniform(log2_lo, log2_hi)))
         out.append(BatchItem(sp, e, ext, npts, seed * 1000 + v))
     return out
+
+
+def coef_uniform_torch(lattice: str, ext: Sequence[int], seed: int, dtype=None, device="cuda"):
+    """c ~ U[-1, 1] drawn on the device with a seeded torch generator (large
+    benchmark volumes); shape (n_cosets, E2, E1, E0)."""
+    import torch
+    dim, _, cosets = LATTICES[lattice]
+    shape = (len(cosets),) + tuple(int(v) for v in reversed(list(ext)[:dim]))
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    c = torch.rand(shape, generator=g, device=device, dtype=torch.float32) * 2.0 - 1.0
+    return c if dtype is None else c.to(dtype)
+
+
+def points_uniform_torch(n: int, lo, hi, seed: int, device="cuda"):
+    """n points ~ U(box) drawn on the device with a seeded torch generator."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    lo_t = torch.tensor(list(lo), dtype=torch.float32, device=device)
+    hi_t = torch.tensor(list(hi), dtype=torch.float32, device=device)
+    return lo_t + (hi_t - lo_t) * torch.rand((n, len(lo)), generator=g, device=device, dtype=torch.float32)
