@@ -122,12 +122,19 @@ typedef struct {
     const ls_axis_factor *separable;
 } ls_spline_desc;
 
-/* Kernel variants a spline can be generated with. */
+/*
+ * Kernel variants a spline can be generated with.  group / depth are the
+ * group size m and pipeline depth d of Sec. 4.4 / Algorithm 2, counted in
+ * stencil sites and groups: the gathers of group g are issued only after the
+ * values of group g - depth have arrived (0 = no limit: all gathers at once).
+ */
 typedef struct {
     int32_t block;                     /* threads per block (default 256) */
-    int32_t pts_per_thread;            /* points per thread per loop trip (1, 2) */
+    int32_t pts_per_thread;            /* reserved, must be 0 or 1 */
     int32_t branchy;                   /* K > 1: 0 = evaluate all, select; 1 = branch */
     int32_t min_blocks;                /* __launch_bounds__ minimum blocks per SM (0 = none) */
+    int32_t group;                     /* m: sites per gather group (0 = all) */
+    int32_t depth;                     /* d: groups in flight (0 = unlimited) */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */

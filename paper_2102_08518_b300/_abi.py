@@ -51,7 +51,7 @@ class SplineDescC(ctypes.Structure):
 
 class VariantC(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("pts_per_thread", ctypes.c_int32), ("branchy", ctypes.c_int32),
-                ("min_blocks", ctypes.c_int32)]
+                ("min_blocks", ctypes.c_int32), ("group", ctypes.c_int32), ("depth", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); every function declared in include/lattice_spline.h
@@ -205,5 +205,5 @@ class DescHolder:
         return ctypes.cast(arr, c_f64p)
 
 
-def variant(block=256, pts_per_thread=1, branchy=0, min_blocks=0) -> VariantC:
-    return VariantC(block, pts_per_thread, branchy, min_blocks)
+def variant(block=256, pts_per_thread=1, branchy=0, min_blocks=0, group=0, depth=0) -> VariantC:
+    return VariantC(block, pts_per_thread, branchy, min_blocks, group, depth)

@@ -64,7 +64,7 @@ class Spline:
     """Generated, compiled and loaded kernels of one spline for one storage dtype."""
 
     def __init__(self, name: str, dtype: str = "f32", block: int = 256, branchy: int = 0,
-                 min_blocks: int = 0, kernel_name: Optional[str] = None):
+                 min_blocks: int = 0, group: int = 0, depth: int = 0, kernel_name: Optional[str] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("lattice spline kernels need a CUDA device")
         self.name = name
@@ -74,9 +74,12 @@ class Spline:
         self.n_cosets = len(self.table.spline.lattice.cosets)
         self.scale = self.table.spline.lattice.scale
         kname = kernel_name or f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + \
-            ("_br" if branchy else "") + (f"_m{min_blocks}" if min_blocks else "")
+            ("_br" if branchy else "") + (f"_m{min_blocks}" if min_blocks else "") + \
+            (f"_g{group}d{depth}" if group and depth else "")
+        self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
+                        "depth": depth}
         self._desc = _abi.DescHolder(self.table, kname)
-        var = _abi.variant(block=block, branchy=branchy, min_blocks=min_blocks)
+        var = _abi.variant(block=block, branchy=branchy, min_blocks=min_blocks, group=group, depth=depth)
         h = ctypes.c_void_p()
         torch.cuda.init()
         _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),
@@ -346,3 +349,77 @@ class Plan:
             except Exception:
                 pass
             self.handle = None
+
+
+# ---------------------------------------------------------------------------
+# autotuning of the evaluation kernel variant
+# ---------------------------------------------------------------------------
+
+DEFAULT_CANDIDATES = (
+    dict(block=256), dict(block=512), dict(block=256, min_blocks=2), dict(block=128, min_blocks=4),
+    dict(block=256, group=8, depth=2), dict(block=256, group=8, depth=3), dict(block=256, group=4, depth=4),
+    dict(block=512, group=8, depth=2), dict(block=512, group=16, depth=1), dict(block=256, group=16, depth=1),
+)
+
+
+def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_sets: Sequence[torch.Tensor],
+             candidates=DEFAULT_CANDIDATES, reps: int = 5, tag: str = "") -> "Spline":
+    """Generate the evaluation kernel in each candidate variant (block size,
+    minimum blocks per SM, gather group size m and depth d), time it on the
+    caller's volume and point sets, and return the fastest Spline.  The choice
+    is cached on disk per (spline, dtype, GPU, tag)."""
+    import json
+    gpu = torch.cuda.get_device_name()
+    key = f"{name}|{dtype}|{gpu}|{tuple(ext)}|{tag}|{[int(p.shape[0]) for p in pts_sets]}"
+    path = os.path.join(_CACHE_DIR, "autotune.json")
+    cache = {}
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    if key in cache:
+        return Spline(name, dtype, **cache[key]["variant"])
+    best = None
+    results = []
+    for cand in candidates:
+        sp = Spline(name, dtype, **cand)
+        vol = Volume(sp, ext, coef)
+        outs = [torch.empty(p.shape[0], device=p.device) for p in pts_sets]
+        for p, o in zip(pts_sets, outs):
+            vol.eval(p, o)
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        for _ in range(reps):
+            for p, o in zip(pts_sets, outs):
+                vol.eval(p, o)
+        e.record()
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e) / reps
+        results.append({"variant": sp.variant, "ms": ms})
+        if best is None or ms < best[0]:
+            best = (ms, sp)
+    cache[key] = {"variant": best[1].variant, "ms": best[0], "all": results}
+    try:
+        os.makedirs(_CACHE_DIR, exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return best[1]
+
+
+def autotune_record(name: str, dtype: str, ext, pts_sets, tag: str = ""):
+    """The cached autotuning entry for this workload, if any."""
+    import json
+    gpu = torch.cuda.get_device_name()
+    key = f"{name}|{dtype}|{gpu}|{tuple(ext)}|{tag}|{[int(p.shape[0]) for p in pts_sets]}"
+    try:
+        with open(os.path.join(_CACHE_DIR, "autotune.json")) as f:
+            return json.load(f).get(key)
+    except (OSError, ValueError):
+        return None

@@ -231,12 +231,14 @@ ls_status get_kernel(ls_spline_s *s, const char *what, cudaKernel_t &k, int &per
 
 ls_variant default_variant(const ls_variant *v)
 {
-    ls_variant r{256, 1, 0, 0};
+    ls_variant r{256, 1, 0, 0, 0, 0};
     if (v) {
         if (v->block > 0) r.block = v->block;
         if (v->pts_per_thread > 0) r.pts_per_thread = v->pts_per_thread;
         r.branchy = v->branchy;
-        r.min_blocks = v->min_blocks;
+        r.min_blocks = v->min_blocks > 0 ? v->min_blocks : 0;
+        r.group = v->group > 0 ? v->group : 0;
+        r.depth = v->depth > 0 ? v->depth : 0;
     }
     return r;
 }

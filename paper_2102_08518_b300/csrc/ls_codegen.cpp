@@ -214,7 +214,7 @@ unsigned long long coset_lut(const Table &t)
 // load: emit float cN = coefficient; declare_addr: emit int adN = address (-1 if
 // the site is outside the arrays).  At least one of the two is set.
 void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int reach,
-                  const char *coef_expr, bool declare_addr, bool load = true)
+                  const char *coef_expr, bool declare_addr, bool load = true, int group = 0, int depth = 0)
 {
     auto &o = e.o;
     const int D = t.dim;
@@ -284,9 +284,19 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             base_of_class[m] = nm;
         }
     }
+    const bool pipelined = load && !declare_addr && group > 0 && depth > 0 && (int)sites.size() > group * depth;
     for (size_t j = 0; j < sites.size(); ++j) {
         const I3 &s = sites[j];
         std::string addr = base_of_class[parity_class(s)];
+        if (pipelined && (int)j % group == 0 && (int)j / group >= depth) {
+            // Algorithm 2: group g is fetched only once group g - depth has arrived.
+            // tk is 0 for every value (NaN and +-inf convert to 0) but is computed
+            // from the loaded value, so the loads below cannot issue before it.
+            const int g = (int)j / group;
+            const int last = (g - depth + 1) * group - 1;
+            o << "      const int tk" << g << " = __float2int_rz(c" << last << " * 0.0f);\n";
+        }
+        if (pipelined && (int)j / group >= depth) addr += " + tk" + std::to_string((int)j / group);
         for (int r = 0; r < D; ++r) {
             int h = (a == 2) ? floordiv2(s[r]) : s[r];
             if (h == 0) continue;
@@ -653,7 +663,7 @@ void emit_eval_point(Emitter &e, const Table &t, const ls_variant &var, const St
     if (!t.sep.empty()) {
         emit_separable_body(e, t, grad, fv, g);
     } else {
-        emit_gathers(e, t, st.sites, reach, "a.coef", false);
+        emit_gathers(e, t, st.sites, reach, "a.coef", false, true, var.group, var.depth);
         const size_t K = t.ref.size();
         std::vector<std::vector<std::string>> rr;
         if (K > 1 && var.branchy) {
