@@ -196,11 +196,22 @@ ls_status ls_eval_grad(ls_volume v, const float *pts, int64_t n, float *val, flo
                        ls_stream stream);
 /*
  * Same as ls_eval with HOST buffers: copies pts to the device, evaluates and
- * copies out back, all on stream; returns after the stream has finished.
- * Uses a device staging buffer owned by the volume (grown on demand).
+ * copies out back; returns when out is complete.  The points move in chunks
+ * on two internal streams, so the host-to-device copy of one chunk, the kernels
+ * of another and the device-to-host copy of a third overlap.  Pinned host
+ * memory gives asynchronous copies; pageable memory works but serialises.
+ * Work is ordered after everything already queued on `stream`.  Staging
+ * buffers and the two streams belong to the volume (made on first use).
  */
 ls_status ls_eval_host(ls_volume v, const float *host_pts, int64_t n, float *host_out,
                        ls_stream stream);
+/*
+ * ls_eval_host for n_vol volumes (same dimension) at the same host points: the
+ * points cross to the device once, every volume is evaluated per chunk, and
+ * host_out[k] receives the values of vols[k].  Staging belongs to vols[0].
+ */
+ls_status ls_eval_host_multi(int32_t n_vol, const ls_volume *vols, const float *host_pts, int64_t n,
+                             float *const *host_out, ls_stream stream);
 
 /*
  * Adjoint with respect to the coefficients (transposed stencil):

@@ -76,6 +76,8 @@ SIGNATURES = {
                                     ctypes.c_void_p, ctypes.c_void_p]),
     "ls_eval_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_void_p]),
+    "ls_eval_host_multi": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p]),
     "ls_adjoint_coef": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                        ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "ls_adjoint_scratch_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64]),

@@ -78,6 +78,7 @@ class Spline:
             (f"_g{group}d{depth}" if group and depth else "")
         self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
                         "depth": depth}
+        self.kernel_name = kname
         self._desc = _abi.DescHolder(self.table, kname)
         var = _abi.variant(block=block, branchy=branchy, min_blocks=min_blocks, group=group, depth=depth)
         h = ctypes.c_void_p()
@@ -362,6 +363,11 @@ DEFAULT_CANDIDATES = (
 )
 
 
+# the variants that won somewhere in the full sweep (block size and occupancy;
+# limiting gathers in flight never won on B300)
+TUNE_CANDIDATES_SMALL = (dict(block=256), dict(block=384), dict(block=512), dict(block=256, min_blocks=2))
+
+
 def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_sets: Sequence[torch.Tensor],
              candidates=DEFAULT_CANDIDATES, reps: int = 5, tag: str = "") -> "Spline":
     """Generate the evaluation kernel in each candidate variant (block size,
@@ -423,3 +429,14 @@ def autotune_record(name: str, dtype: str, ext, pts_sets, tag: str = ""):
             return json.load(f).get(key)
     except (OSError, ValueError):
         return None
+
+
+def eval_host_multi(volumes: Sequence["Volume"], pts_host: torch.Tensor, outs_host: Sequence[torch.Tensor],
+                    stream=None):
+    """Host points in, one host output per volume (points cross to the device once)."""
+    n = len(volumes)
+    vh = (ctypes.c_void_p * n)(*[v.handle.value for v in volumes])
+    oh = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs_host])
+    _abi.check(_abi.lib().ls_eval_host_multi(n, vh, ctypes.c_void_p(pts_host.data_ptr()), pts_host.shape[0], oh,
+                                             _stream(stream)), "ls_eval_host_multi")
+    return outs_host

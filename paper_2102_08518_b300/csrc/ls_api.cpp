@@ -465,6 +465,13 @@ ls_status ls_volume_upload(ls_volume v, const void *src, int32_t src_is_device, 
 ls_status ls_volume_destroy(ls_volume v)
 {
     if (!v) return LS_OK;
+    for (int i = 0; i < 2; ++i)
+        if (v->hs[i]) {
+            cudaStreamSynchronize(v->hs[i]);
+            cudaStreamDestroy(v->hs[i]);
+        }
+    for (int i = 0; i < 3; ++i)
+        if (v->hev[i]) cudaEventDestroy(v->hev[i]);
     if (v->owned && v->coef) cudaFree(v->coef);
     if (v->stage) cudaFree(v->stage);
     delete v;
@@ -474,6 +481,8 @@ ls_status ls_volume_destroy(ls_volume v)
 // ---------------------------------------------------------------------------
 // evaluation
 // ---------------------------------------------------------------------------
+
+static size_t al256b(size_t b) { return (b + 255) & ~(size_t)255; }
 
 static void fill_eval_args(ls_volume v, const float *pts, int64_t n, float *out, float *grad, EvalArgsH &a)
 {
@@ -512,40 +521,75 @@ ls_status ls_eval_grad(ls_volume v, const float *pts, int64_t n, float *val, flo
                   &a, (cudaStream_t)stream);
 }
 
-ls_status ls_eval_host(ls_volume v, const float *host_pts, int64_t n, float *host_out, ls_stream stream)
+ls_status ls_eval_host_multi(int32_t n_vol, const ls_volume *vols, const float *host_pts, int64_t n,
+                             float *const *host_out, ls_stream stream)
 {
-    if (!v || (n > 0 && (!host_pts || !host_out))) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
+    if (n_vol < 1 || !vols || !vols[0] || !host_out || (n > 0 && !host_pts)) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
     if (n < 0) return ls_fail(LS_ERR_INVALID_ARG, "n < 0");
+    const int D = vols[0]->spline->table.dim;
+    for (int k = 0; k < n_vol; ++k) {
+        if (!vols[k] || (n > 0 && !host_out[k])) return ls_fail(LS_ERR_INVALID_ARG, "NULL volume or output");
+        if (vols[k]->spline->table.dim != D) return ls_fail(LS_ERR_INVALID_ARG, "volumes of different dimension");
+    }
     if (n == 0) return LS_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    const int D = v->spline->table.dim;
-    const size_t pbytes = (size_t)n * D * sizeof(float), obytes = (size_t)n * sizeof(float);
-    const size_t need = pbytes + obytes + 256;
+    ls_volume_s *v = vols[0];
+    cudaStream_t user = (cudaStream_t)stream;
+    // chunking: two stages, each holding one chunk of points and n_vol outputs
+    const int64_t chunk = std::min<int64_t>(n, (int64_t)1 << 20);
+    const size_t pbytes = al256b((size_t)chunk * D * 4), obytes = al256b((size_t)chunk * 4);
+    const size_t stage_one = pbytes + obytes * n_vol;
+    const size_t need = 2 * stage_one;
+    cudaError_t e;
+    if (!v->hs[0]) {
+        for (int i = 0; i < 2; ++i)
+            if ((e = cudaStreamCreateWithFlags(&v->hs[i], cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamCreate");
+        for (int i = 0; i < 3; ++i)
+            if ((e = cudaEventCreateWithFlags(&v->hev[i], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "cudaEventCreate");
+    }
     if (v->stage_bytes < need) {
         if (v->stage) {
-            cudaError_t e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+            cudaStreamSynchronize(v->hs[0]);
+            cudaStreamSynchronize(v->hs[1]);
             cudaFree(v->stage);
             v->stage = nullptr;
             v->stage_bytes = 0;
         }
         if (cudaMalloc(&v->stage, need) != cudaSuccess) {
             cudaGetLastError();
-            return ls_fail(LS_ERR_OOM, "staging buffer for ls_eval_host");
+            return ls_fail(LS_ERR_OOM, "staging buffers for ls_eval_host");
         }
         v->stage_bytes = need;
     }
-    float *dp = (float *)v->stage;
-    float *dout = (float *)((char *)v->stage + ((pbytes + 255) & ~(size_t)255));
-    cudaError_t e = cudaMemcpyAsync(dp, host_pts, pbytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync H2D");
-    ls_status s = ls_eval(v, dp, n, dout, stream);
-    if (s != LS_OK) return s;
-    e = cudaMemcpyAsync(host_out, dout, obytes, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync D2H");
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    // order after the caller's queued work
+    if ((e = cudaEventRecord(v->hev[2], user)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    for (int i = 0; i < 2; ++i)
+        if ((e = cudaStreamWaitEvent(v->hs[i], v->hev[2], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    int64_t c = 0;
+    for (int64_t p0 = 0; p0 < n; p0 += chunk, ++c) {
+        const int si = (int)(c & 1);
+        cudaStream_t s = v->hs[si];
+        const int64_t m = std::min<int64_t>(chunk, n - p0);
+        float *dp = (float *)((char *)v->stage + si * stage_one);
+        if ((e = cudaMemcpyAsync(dp, host_pts + p0 * D, (size_t)m * D * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync H2D");
+        for (int k = 0; k < n_vol; ++k) {
+            float *dout = (float *)((char *)dp + pbytes + k * obytes);
+            ls_status st = ls_eval(vols[k], dp, m, dout, (ls_stream)s);
+            if (st != LS_OK) return st;
+            if ((e = cudaMemcpyAsync(host_out[k] + p0, dout, (size_t)m * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+                return cuda_fail(e, "cudaMemcpyAsync D2H");
+        }
+    }
+    for (int i = 0; i < 2; ++i)
+        if ((e = cudaStreamSynchronize(v->hs[i])) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return LS_OK;
+}
+
+ls_status ls_eval_host(ls_volume v, const float *host_pts, int64_t n, float *host_out, ls_stream stream)
+{
+    return ls_eval_host_multi(1, &v, host_pts, n, &host_out, stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -553,8 +597,6 @@ ls_status ls_eval_host(ls_volume v, const float *host_pts, int64_t n, float *hos
 // ---------------------------------------------------------------------------
 
 namespace {
-size_t al256b(size_t b) { return (b + 255) & ~(size_t)255; }
-
 // Bins of the deterministic adjoint: every lattice site of the haloed grid.
 uint64_t adjoint_nbins(ls_volume v)
 {

@@ -66,6 +66,8 @@ extern "C" ls_status ls_cg_fit(ls_volume v, const float *pts, const float *y, in
     pv.coef = p;
     pv.stage = nullptr;
     pv.stage_bytes = 0;
+    pv.hs[0] = pv.hs[1] = nullptr;
+    pv.hev[0] = pv.hev[1] = pv.hev[2] = nullptr;
     pv.owned = false;
 
     auto cuda_err = [&](cudaError_t e, const char *what) {

@@ -100,9 +100,11 @@ struct ls_volume_s {
     int64_t total_elems = 0;          // n_cosets * prod(ext)
     void *coef = nullptr;
     bool owned = false;
-    // staging for ls_eval_host
+    // staging for ls_eval_host(_multi): buffers and two streams, made on first use
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    cudaStream_t hs[2] = {nullptr, nullptr};
+    cudaEvent_t hev[3] = {nullptr, nullptr, nullptr};
 };
 
 // Thread-local error message helpers (ls_api.cpp).

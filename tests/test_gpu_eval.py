@@ -228,3 +228,29 @@ def test_half_storage(name, dtype, bound):
     cmax = np.abs(coef).max()
     assert np.max(np.abs(got - want_r)) <= TOL * cmax
     assert np.max(np.abs(got - want)) <= (bound + TOL) * cmax
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_eval_host_multi_matches_device_eval(pinned):
+    """Host buffers, several volumes, chunked and overlapped: equal to ls_eval."""
+    from paper_2102_08518_b300.api import eval_host_multi
+    ext = (16, 16, 16)
+    coef_q = workloads.coef_smooth("bcc", ext, seed=1)
+    coef_l = workloads.coef_uniform("bcc", ext, seed=2)
+    vq, vl = volume("bcc_quintic", ext, coef_q), volume("bcc_linear", ext, coef_l)
+    lo, hi = workloads.bounding_box("bcc", ext)
+    n = (1 << 20) * 2 + 12345                      # more than two chunks, ragged tail
+    pts = workloads.points_uniform(n, lo, hi, seed=3)
+    hp = torch.from_numpy(pts)
+    outs = [torch.empty(n), torch.empty(n)]
+    if pinned:
+        hp = hp.pin_memory()
+        outs = [o.pin_memory() for o in outs]
+    eval_host_multi([vq, vl], hp, outs)
+    dp = torch.from_numpy(pts).cuda()
+    refq, refl = vq.eval(dp), vl.eval(dp)
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0], refq.cpu()) and torch.equal(outs[1], refl.cpu())
+    out1 = torch.empty(n)
+    vq.eval_host(torch.from_numpy(pts), out1)
+    assert torch.equal(out1, refq.cpu())
