@@ -218,10 +218,12 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     coef = torch.from_numpy(coef_np).to(dev)
     pts = {k: torch.from_numpy(v).to(dev) for k, v in pts_np.items()}
-    # evaluation kernel variant per spline, autotuned on the step's own point sets (untimed)
-    splines = {n: autotune(n, "f32", EXT, coef, [pts["uniform"], pts["rays"]], candidates=TUNE_CANDIDATES_SMALL,
-                           tag="bcc_step") for n in ("bcc_linear", "bcc_quintic")}
+    # evaluation kernel variant per (spline, point set), autotuned on the step's own points (untimed)
+    tuned = {(sp, ps): autotune(sp, "f32", EXT, coef, [pts[ps]], candidates=TUNE_CANDIDATES_SMALL,
+                                tag=f"bcc_step_{ps}") for sp, ps in CASES}
+    splines = {sp: tuned[(sp, "uniform")] for sp in ("bcc_linear", "bcc_quintic")}
     vols = {n: Volume(s, EXT, coef) for n, s in splines.items()}
+    case_vols = {(sp, ps): Volume(tuned[(sp, ps)], EXT, coef) for sp, ps in CASES}
     outs = {k: torch.empty(v.shape[0], device=dev) for k, v in pts.items()}
     stream = torch.cuda.current_stream()
 
@@ -229,7 +231,7 @@ def run_gpu(args):
         for ci, (sp, ps) in enumerate(CASES):
             if case_events is not None:
                 case_events[ci][0].record(stream)
-            vols[sp].eval(pts[ps], outs[ps])
+            case_vols[(sp, ps)].eval(pts[ps], outs[ps])
             if case_events is not None:
                 case_events[ci][1].record(stream)
 
@@ -273,7 +275,7 @@ def run_gpu(args):
     per_case = {}
     for (sp, ps), ms in zip(CASES, case_ms):
         n = N_UNIFORM if ps == "uniform" else N_RAYS * RAY_STEPS
-        info = splines[sp].info()
+        info = tuned[(sp, ps)].info()
         l2_gbs = sectors[sp] * 32.0 * n / (ms * 1e-3) / 1e9
         fma_tf = 2.0 * info["fma_value"] * n / (ms * 1e-3) / 1e12
         per_case[f"{sp}/{ps}"] = {"gpoints_s": round(n / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 4),
@@ -310,7 +312,7 @@ def run_gpu(args):
 
     def e2e_step():
         for ps in ("uniform", "rays"):
-            eval_host_multi([vols[sp] for sp in order], host_pts[ps], [host_out[(sp, ps)] for sp in order])
+            eval_host_multi([case_vols[(sp, ps)] for sp in order], host_pts[ps], [host_out[(sp, ps)] for sp in order])
 
     e2e_step()
     torch.cuda.synchronize()
@@ -335,7 +337,7 @@ def run_gpu(args):
                          "l2": "points 201 MB per set > 126 MB L2 (inputs larger than L2); coefficient volume "
                                "16 MiB L2-resident by design", "parallelism": f"replicas x{world}"},
               "per_case": per_case, "roofline": roofline, "roofline_alu": roofline_alu, "e2e": e2e,
-              "autotuned": {n: sp.variant for n, sp in splines.items()},
+              "autotuned": {f"{sp}/{ps}": tuned[(sp, ps)].variant for sp, ps in CASES},
               "clocks": clocks, "gpu_launches": len(CASES) * args.steps}
     del host_pts, host_out
     if not args.no_extras:

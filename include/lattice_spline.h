@@ -130,7 +130,9 @@ typedef struct {
  */
 typedef struct {
     int32_t block;                     /* threads per block (default 256) */
-    int32_t pts_per_thread;            /* reserved, must be 0 or 1 */
+    int32_t pts_per_thread;            /* T: consecutive points per thread; T > 1 reuses the gathers
+                                          and coefficient transform while the region-of-evaluation
+                                          site, fold and sub-region stay the same (ray order) */
     int32_t branchy;                   /* K > 1: 0 = evaluate all, select; 1 = branch */
     int32_t min_blocks;                /* __launch_bounds__ minimum blocks per SM (0 = none) */
     int32_t group;                     /* m: sites per gather group (0 = all) */

@@ -102,27 +102,32 @@ def build_library(force: bool = False) -> str:
 _lib = None
 
 
+def configure(lib):
+    """Set the ctypes signatures on a loaded oracle library (also used on
+    deliberately broken copies in the mutation tests)."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    sp = ctypes.POINTER(_CSpec)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.orc_box.restype = ctypes.c_double
+    lib.orc_box.argtypes = [ctypes.c_int32, ctypes.c_int32, dp, dp]
+    lib.orc_phi.restype = ctypes.c_int32
+    lib.orc_phi.argtypes = [sp, dp, ctypes.c_int64, dp, dp]
+    lib.orc_eval.restype = ctypes.c_int32
+    lib.orc_eval.argtypes = [sp, dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int32]
+    lib.orc_adjoint.restype = ctypes.c_int32
+    lib.orc_adjoint.argtypes = [sp, dp, dp, ctypes.c_int64, dp]
+    lib.orc_design_triplets.restype = ctypes.c_int64
+    lib.orc_design_triplets.argtypes = [sp, dp, ctypes.c_int64, i64p, i64p, dp, ctypes.c_int64]
+    lib.orc_morton3.restype = ctypes.c_uint32
+    lib.orc_morton3.argtypes = [ctypes.c_uint32] * 3
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
         build_library()
-        lib = ctypes.CDLL(_LIB)
-        dp = ctypes.POINTER(ctypes.c_double)
-        sp = ctypes.POINTER(_CSpec)
-        i64p = ctypes.POINTER(ctypes.c_int64)
-        lib.orc_box.restype = ctypes.c_double
-        lib.orc_box.argtypes = [ctypes.c_int32, ctypes.c_int32, dp, dp]
-        lib.orc_phi.restype = ctypes.c_int32
-        lib.orc_phi.argtypes = [sp, dp, ctypes.c_int64, dp, dp]
-        lib.orc_eval.restype = ctypes.c_int32
-        lib.orc_eval.argtypes = [sp, dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int32]
-        lib.orc_adjoint.restype = ctypes.c_int32
-        lib.orc_adjoint.argtypes = [sp, dp, dp, ctypes.c_int64, dp]
-        lib.orc_design_triplets.restype = ctypes.c_int64
-        lib.orc_design_triplets.argtypes = [sp, dp, ctypes.c_int64, i64p, i64p, dp, ctypes.c_int64]
-        lib.orc_morton3.restype = ctypes.c_uint32
-        lib.orc_morton3.argtypes = [ctypes.c_uint32] * 3
-        _lib = lib
+        _lib = configure(ctypes.CDLL(_LIB))
     return _lib
 
 

@@ -60,11 +60,20 @@ def _ptr(t: Optional[torch.Tensor]):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
 
 
+def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_blocks: int = 0, group: int = 0,
+                depth: int = 0, pts_per_thread: int = 1) -> str:
+    """The name tag of a generated kernel variant (unique per variant)."""
+    return f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + ("_br" if branchy else "") + \
+        (f"_m{min_blocks}" if min_blocks else "") + (f"_g{group}d{depth}" if group and depth else "") + \
+        (f"_t{pts_per_thread}" if pts_per_thread > 1 else "")
+
+
 class Spline:
     """Generated, compiled and loaded kernels of one spline for one storage dtype."""
 
     def __init__(self, name: str, dtype: str = "f32", block: int = 256, branchy: int = 0,
-                 min_blocks: int = 0, group: int = 0, depth: int = 0, kernel_name: Optional[str] = None):
+                 min_blocks: int = 0, group: int = 0, depth: int = 0, pts_per_thread: int = 1,
+                 kernel_name: Optional[str] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("lattice spline kernels need a CUDA device")
         self.name = name
@@ -73,14 +82,14 @@ class Spline:
         self.dim = self.table.spline.lattice.dim
         self.n_cosets = len(self.table.spline.lattice.cosets)
         self.scale = self.table.spline.lattice.scale
-        kname = kernel_name or f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + \
-            ("_br" if branchy else "") + (f"_m{min_blocks}" if min_blocks else "") + \
-            (f"_g{group}d{depth}" if group and depth else "")
+        kname = kernel_name or globals()["kernel_name"](name, dtype, block, branchy, min_blocks, group, depth,
+                                                         pts_per_thread)
         self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
-                        "depth": depth}
+                        "depth": depth, "pts_per_thread": pts_per_thread}
         self.kernel_name = kname
         self._desc = _abi.DescHolder(self.table, kname)
-        var = _abi.variant(block=block, branchy=branchy, min_blocks=min_blocks, group=group, depth=depth)
+        var = _abi.variant(block=block, pts_per_thread=pts_per_thread, branchy=branchy, min_blocks=min_blocks,
+                           group=group, depth=depth)
         h = ctypes.c_void_p()
         torch.cuda.init()
         _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),
@@ -365,7 +374,9 @@ DEFAULT_CANDIDATES = (
 
 # the variants that won somewhere in the full sweep (block size and occupancy;
 # limiting gathers in flight never won on B300)
-TUNE_CANDIDATES_SMALL = (dict(block=256), dict(block=384), dict(block=512), dict(block=256, min_blocks=2))
+TUNE_CANDIDATES_SMALL = (dict(block=256), dict(block=384), dict(block=512), dict(block=256, min_blocks=2),
+                         dict(block=256, pts_per_thread=4), dict(block=256, pts_per_thread=8),
+                         dict(block=128, pts_per_thread=8), dict(block=256, pts_per_thread=16))
 
 
 def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_sets: Sequence[torch.Tensor],
@@ -386,6 +397,14 @@ def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_
         cache = {}
     if key in cache:
         return Spline(name, dtype, **cache[key]["variant"])
+    # results measured earlier on this GPU model, shipped with the package
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_b300.json")) as f:
+            shipped = json.load(f)
+        if key in shipped:
+            return Spline(name, dtype, **shipped[key]["variant"])
+    except (OSError, ValueError):
+        pass
     best = None
     results = []
     for cand in candidates:

@@ -234,7 +234,7 @@ ls_variant default_variant(const ls_variant *v)
     ls_variant r{256, 1, 0, 0, 0, 0};
     if (v) {
         if (v->block > 0) r.block = v->block;
-        if (v->pts_per_thread > 0) r.pts_per_thread = v->pts_per_thread;
+        if (v->pts_per_thread > 0) r.pts_per_thread = v->pts_per_thread > 64 ? 64 : v->pts_per_thread;
         r.branchy = v->branchy;
         r.min_blocks = v->min_blocks > 0 ? v->min_blocks : 0;
         r.group = v->group > 0 ? v->group : 0;
@@ -505,8 +505,9 @@ ls_status ls_eval(ls_volume v, const float *pts, int64_t n, float *out, ls_strea
     ls_spline_s *s = v->spline;
     EvalArgsH a;
     fill_eval_args(v, pts, n, out, nullptr, a);
-    return launch(s->mod.eval, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_eval), s->var.block, &a,
-                  (cudaStream_t)stream);
+    const int T = (s->var.pts_per_thread > 1 && s->table.sep.empty()) ? s->var.pts_per_thread : 1;
+    return launch(s->mod.eval, grid_for((n + T - 1) / T, s->var.block, s->num_sms, s->mod.blocks_per_sm_eval),
+                  s->var.block, &a, (cudaStream_t)stream);
 }
 
 ls_status ls_eval_grad(ls_volume v, const float *pts, int64_t n, float *val, float *grad, ls_stream stream)

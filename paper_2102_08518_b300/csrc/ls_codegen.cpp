@@ -715,6 +715,80 @@ void emit_eval_point(Emitter &e, const Table &t, const ls_variant &var, const St
     o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
 }
 
+// Coherent-reuse evaluation kernel: each thread walks T consecutive points and
+// repeats the gathers and the coefficient transform A = M c only when the
+// region-of-evaluation site, the fold transform or the reference sub-region
+// changes; the Horner form runs per point.  For ray-ordered points most
+// neighbours share them.  Results equal the one-point-per-thread kernel.
+void emit_eval_kernel_reuse(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
+                            int T, GenInfo &info)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    const int fma0 = e.fma;
+    const size_t K = t.ref.size();
+    // monomial supports and A names per region
+    std::vector<std::map<I3, std::vector<std::pair<int, double>>>> terms(K);
+    std::vector<std::set<I3>> sup(K);
+    for (size_t k = 0; k < K; ++k) sup[k] = monomial_support(t.ref[k], st.region_to_union[k], terms[k]);
+    auto aname = [&](size_t k, const I3 &m) {
+        return "r" + std::to_string(k) + "_A" + std::to_string(m[0]) + "_" + std::to_string(m[1]) + "_" +
+               std::to_string(m[2]);
+    };
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block;
+    if (var.min_blocks > 0) o << ", " << var.min_blocks;
+    o << ") " << kname(t, "eval") << "(const LsEvalArgs a)\n{\n";
+    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride; (void)E1; (void)E2; (void)CS;\n";
+    o << "  const long long nchunk = (a.n + " << T - 1 << ") / " << T << ";\n";
+    o << "  const long long cstride_ = (long long)gridDim.x * blockDim.x;\n";
+    o << "#define LS_OUT_OF_RANGE(V) { a.out[i] = (V); }\n";
+    o << "  for (long long ch = (long long)blockIdx.x * blockDim.x + threadIdx.x; ch < nchunk; ch += cstride_) {\n";
+    for (size_t k = 0; k < K; ++k)
+        for (const auto &m : sup[k]) o << "    float " << aname(k, m) << " = 0.0f;\n";
+    o << "    int pk0 = 0x7fffffff, pk1 = 0, pk2 = 0, pcode = -1, ppsi = -1;\n";
+    o << "    const long long iend = (ch + 1) * " << T << " < a.n ? (ch + 1) * " << T << " : a.n;\n";
+    o << "    for (long long i = ch * " << T << "; i < iend; ++i) {\n";
+    emit_point_load(e, t, "continue");
+    emit_classify(e, t);
+    if (t.fold == LS_FOLD_SIGNED_PERM)
+        o << "    const int code = p0 | (p1 << 2) | ((int)g0 << 4)" << (D > 1 ? " | ((int)g1 << 5)" : "")
+          << (D > 2 ? " | ((int)g2 << 6)" : "") << ";\n";
+    else
+        o << "    const int code = 0;\n";
+    o << "    const bool same = (k0 == pk0)" << (D > 1 ? " && (k1 == pk1)" : "") << (D > 2 ? " && (k2 == pk2)" : "")
+      << " && (code == pcode) && (psi == ppsi);\n";
+    o << "    if (!same) {\n";
+    emit_gathers(e, t, st.sites, reach, "a.coef", false);
+    for (size_t k = 0; k < K; ++k)
+        for (const auto &m : sup[k]) {
+            std::string acc;
+            for (auto &pr : terms[k][m]) {
+                acc = acc.empty() ? flit(pr.second) + " * c" + std::to_string(pr.first)
+                                  : "fmaf(" + flit(pr.second) + ", c" + std::to_string(pr.first) + ", " + acc + ")";
+                e.fma++;
+            }
+            o << "    " << aname(k, m) << " = " << acc << ";\n";
+        }
+    o << "    pk0 = k0;" << (D > 1 ? " pk1 = k1;" : "") << (D > 2 ? " pk2 = k2;" : "") << " pcode = code; ppsi = psi;\n";
+    o << "    }\n";
+    std::vector<std::string> fk;
+    for (size_t k = 0; k < K; ++k) {
+        PolyEmit pe{e, D, "", {}, {}, {}};
+        for (int i = 0; i < D; ++i) {
+            pe.uvar[i] = "u" + std::to_string(k) + "_" + std::to_string(i);
+            o << "    const float " << pe.uvar[i] << " = a" << i << " - " << flit(t.ref[k].center[i]) << ";\n";
+        }
+        auto coefA = [&](const I3 &m) -> std::string { return sup[k].count(m) ? aname(k, m) : std::string(); };
+        std::string f = pe.horner(0, I3{0, 0, 0}, coefA, sup[k]);
+        fk.push_back(f.empty() ? "0.0f" : f);
+    }
+    std::string sel = fk[K - 1];
+    for (int k = (int)K - 2; k >= 0; --k) sel = "(psi == " + std::to_string(k) + ") ? " + fk[k] + " : (" + sel + ")";
+    o << "    a.out[i] = " << sel << ";\n";
+    o << "    }\n  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
+    info.fma_value = e.fma - fma0;
+}
+
 // value [+ gradient] kernel: grid-stride loop over the point function
 void emit_eval_kernel(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
                       bool grad, GenInfo &info)
@@ -1159,7 +1233,16 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
         g.info.n_sites = n;
     }
     g.info.reach = reach;
-    emit_eval_kernel(e, t, var, st, reach, false, g.info);
+    if (var.pts_per_thread > 1 && t.sep.empty()) {
+        // the point function is still emitted (batched kernels, gradient) but the
+        // value kernel walks runs of consecutive points
+        GenInfo tmp;
+        emit_eval_point(e, t, var, st, reach, false, kname(t, "eval_pt"));
+        emit_eval_kernel_reuse(e, t, var, st, reach, var.pts_per_thread, g.info);
+        (void)tmp;
+    } else {
+        emit_eval_kernel(e, t, var, st, reach, false, g.info);
+    }
     emit_eval_kernel(e, t, var, st, reach, true, g.info);
     emit_adjoint_atomic(e, t, var, st, reach);
     emit_adjoint_bin(e, t, var);

@@ -254,3 +254,26 @@ def test_eval_host_multi_matches_device_eval(pinned):
     out1 = torch.empty(n)
     vq.eval_host(torch.from_numpy(pts), out1)
     assert torch.equal(out1, refq.cpu())
+
+
+@pytest.mark.parametrize("name", ["bcc_linear", "bcc_quintic", "fcc6", "zp"])
+@pytest.mark.parametrize("T", [4, 8])
+def test_coherent_reuse_variant_is_bitwise_identical(name, T):
+    """Runs of T consecutive points per thread, reusing gathers and the
+    coefficient transform while the cell does not change: same bits as the
+    one-point-per-thread kernel, for ray-ordered, random and edge points."""
+    from paper_2102_08518_b300.api import Spline, Volume
+    lat = workloads.SPLINE_LATTICE[name]
+    ext = SMALL_EXT[name] if name == "zp" else (24, 24, 24)
+    coef = torch.from_numpy(workloads.coef_uniform(lat, ext, seed=71)).cuda()
+    lo, hi = workloads.bounding_box(lat, ext)
+    sets = [workloads.points_uniform(10007, lo - 2.0, hi + 2.0, seed=72)]
+    if len(ext) == 3:
+        sets.append(workloads.points_rays(64, 333, lo, hi, seed=73))
+    base = Volume(spline(name), ext, coef)
+    reuse = Volume(Spline(name, "f32", pts_per_thread=T), ext, coef)
+    for pts in sets:
+        p = torch.from_numpy(pts).cuda()
+        a, b = base.eval(p), reuse.eval(p)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
