@@ -211,7 +211,7 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2102_08518_b300.api import (Volume, autotune, eval_host_multi, probe_gather, table,
-                                           TUNE_CANDIDATES_SMALL)
+                                           TUNE_CANDIDATES_SMALL, _tune_key as tune_key)
     from paper_2102_08518_b300.roofline import distinct_sectors_per_point
 
     coef_np, pts_np = make_inputs(seed_offset=rank)
@@ -337,7 +337,9 @@ def run_gpu(args):
                          "l2": "points 201 MB per set > 126 MB L2 (inputs larger than L2); coefficient volume "
                                "16 MiB L2-resident by design", "parallelism": f"replicas x{world}"},
               "per_case": per_case, "roofline": roofline, "roofline_alu": roofline_alu, "e2e": e2e,
-              "autotuned": {f"{sp}/{ps}": tuned[(sp, ps)].variant for sp, ps in CASES},
+              "autotuned": {f"{sp}/{ps}": {"variant": tuned[(sp, ps)].variant,
+                                            "key": tune_key(sp, "f32", EXT, [pts[ps]], f"bcc_step_{ps}")}
+                            for sp, ps in CASES},
               "clocks": clocks, "gpu_launches": len(CASES) * args.steps}
     del host_pts, host_out
     if not args.no_extras:

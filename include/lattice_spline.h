@@ -137,6 +137,9 @@ typedef struct {
     int32_t min_blocks;                /* __launch_bounds__ minimum blocks per SM (0 = none) */
     int32_t group;                     /* m: sites per gather group (0 = all) */
     int32_t depth;                     /* d: groups in flight (0 = unlimited) */
+    int32_t blocks_per_sm;             /* grid = SMs x blocks_per_sm for the evaluation kernels
+                                          (0 = as many as fit); bounds the resident warps per SM
+                                          without taking L1 away (no recompilation) */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */

@@ -51,7 +51,8 @@ class SplineDescC(ctypes.Structure):
 
 class VariantC(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("pts_per_thread", ctypes.c_int32), ("branchy", ctypes.c_int32),
-                ("min_blocks", ctypes.c_int32), ("group", ctypes.c_int32), ("depth", ctypes.c_int32)]
+                ("min_blocks", ctypes.c_int32), ("group", ctypes.c_int32), ("depth", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); every function declared in include/lattice_spline.h
@@ -141,7 +142,7 @@ def check(status: int, where: str):
 class DescHolder:
     """A ls_spline_desc plus the arrays it points to (kept alive together)."""
 
-    def __init__(self, table, name: Optional[str] = None):
+    def __init__(self, table, name: Optional[str] = None, expansion: str = "sparse"):
         from .exactpoly import monomials_upto  # noqa: F401  (table monomials are explicit)
         spl = table.spline
         lat = spl.lattice
@@ -165,8 +166,11 @@ class DescHolder:
         sig = (ctypes.c_int8 * len(table.sigma))(*table.sigma)
         self._keep.append(sig)
         d.sigma = ctypes.cast(sig, ctypes.POINTER(ctypes.c_int8))
-        regs = (RefRegionC * len(table.regions))()
-        for k, r in enumerate(table.regions):
+        regions = table.regions
+        if expansion == "centroid" and getattr(table, "regions_centroid", None):
+            regions = table.regions_centroid
+        regs = (RefRegionC * len(regions))()
+        for k, r in enumerate(regions):
             rc = regs[k]
             rc.n_sites = len(r.sites)
             rc.sites = self._i32([v for site in r.sites for v in site])
@@ -177,7 +181,7 @@ class DescHolder:
             for i in range(3):
                 rc.center[i] = float(r.center[i]) if i < s else 0.0
         self._keep.append(regs)
-        d.n_ref = len(table.regions)
+        d.n_ref = len(regions)
         d.ref = ctypes.cast(regs, ctypes.POINTER(RefRegionC))
         if table.separable:
             axes = (AxisFactorC * s)()
@@ -207,5 +211,5 @@ class DescHolder:
         return ctypes.cast(arr, c_f64p)
 
 
-def variant(block=256, pts_per_thread=1, branchy=0, min_blocks=0, group=0, depth=0) -> VariantC:
-    return VariantC(block, pts_per_thread, branchy, min_blocks, group, depth)
+def variant(block=256, pts_per_thread=1, branchy=0, min_blocks=0, group=0, depth=0, blocks_per_sm=0) -> VariantC:
+    return VariantC(block, pts_per_thread, branchy, min_blocks, group, depth, blocks_per_sm)

@@ -18,7 +18,7 @@ from .splines import BY_NAME
 from .subregions import Table, build_table
 
 _TABLE_CACHE: Dict[str, Table] = {}
-_TABLE_VERSION = 2
+_TABLE_VERSION = 4
 _CACHE_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "kcache")
 
 DTYPES = {"f32": _abi.LS_F32, "bf16": _abi.LS_BF16, "f16": _abi.LS_F16}
@@ -61,11 +61,12 @@ def _ptr(t: Optional[torch.Tensor]):
 
 
 def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_blocks: int = 0, group: int = 0,
-                depth: int = 0, pts_per_thread: int = 1) -> str:
-    """The name tag of a generated kernel variant (unique per variant)."""
+                depth: int = 0, pts_per_thread: int = 1, blocks_per_sm: int = 0, expansion: str = "sparse") -> str:
+    """The name tag of a generated kernel variant (blocks_per_sm only sizes the
+    grid, so it shares the compiled kernel)."""
     return f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + ("_br" if branchy else "") + \
         (f"_m{min_blocks}" if min_blocks else "") + (f"_g{group}d{depth}" if group and depth else "") + \
-        (f"_t{pts_per_thread}" if pts_per_thread > 1 else "")
+        (f"_t{pts_per_thread}" if pts_per_thread > 1 else "") + ("_ec" if expansion == "centroid" else "")
 
 
 class Spline:
@@ -73,7 +74,7 @@ class Spline:
 
     def __init__(self, name: str, dtype: str = "f32", block: int = 256, branchy: int = 0,
                  min_blocks: int = 0, group: int = 0, depth: int = 0, pts_per_thread: int = 1,
-                 kernel_name: Optional[str] = None):
+                 blocks_per_sm: int = 0, expansion: str = "sparse", kernel_name: Optional[str] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("lattice spline kernels need a CUDA device")
         self.name = name
@@ -83,13 +84,14 @@ class Spline:
         self.n_cosets = len(self.table.spline.lattice.cosets)
         self.scale = self.table.spline.lattice.scale
         kname = kernel_name or globals()["kernel_name"](name, dtype, block, branchy, min_blocks, group, depth,
-                                                         pts_per_thread)
+                                                         pts_per_thread, blocks_per_sm, expansion)
         self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
-                        "depth": depth, "pts_per_thread": pts_per_thread}
+                        "depth": depth, "pts_per_thread": pts_per_thread, "blocks_per_sm": blocks_per_sm,
+                        "expansion": expansion}
         self.kernel_name = kname
-        self._desc = _abi.DescHolder(self.table, kname)
+        self._desc = _abi.DescHolder(self.table, kname, expansion)
         var = _abi.variant(block=block, pts_per_thread=pts_per_thread, branchy=branchy, min_blocks=min_blocks,
-                           group=group, depth=depth)
+                           group=group, depth=depth, blocks_per_sm=blocks_per_sm)
         h = ctypes.c_void_p()
         torch.cuda.init()
         _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),
@@ -374,9 +376,10 @@ DEFAULT_CANDIDATES = (
 
 # the variants that won somewhere in the full sweep (block size and occupancy;
 # limiting gathers in flight never won on B300)
-TUNE_CANDIDATES_SMALL = (dict(block=256), dict(block=384), dict(block=512), dict(block=256, min_blocks=2),
-                         dict(block=256, pts_per_thread=4), dict(block=256, pts_per_thread=8),
-                         dict(block=128, pts_per_thread=8), dict(block=256, pts_per_thread=16))
+TUNE_CANDIDATES_SMALL = tuple([dict(block=256, blocks_per_sm=b, expansion=x) for b in (0, 2, 3) for x in
+                               ("sparse", "centroid")] +
+                              [dict(block=512, expansion=x) for x in ("sparse", "centroid")] +
+                              [dict(block=384, expansion=x) for x in ("sparse", "centroid")])
 
 
 def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_sets: Sequence[torch.Tensor],
@@ -386,8 +389,7 @@ def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_
     caller's volume and point sets, and return the fastest Spline.  The choice
     is cached on disk per (spline, dtype, GPU, tag)."""
     import json
-    gpu = torch.cuda.get_device_name()
-    key = f"{name}|{dtype}|{gpu}|{tuple(ext)}|{tag}|{[int(p.shape[0]) for p in pts_sets]}"
+    key = _tune_key(name, dtype, ext, pts_sets, tag)
     path = os.path.join(_CACHE_DIR, "autotune.json")
     cache = {}
     try:
@@ -438,11 +440,17 @@ def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_
     return best[1]
 
 
+def _tune_key(name, dtype, ext, pts_sets, tag):
+    # the generated kernel's FMA count identifies the table version the choice was made for
+    fma = Spline(name, dtype).info()["fma_value"]
+    gpu = torch.cuda.get_device_name()
+    return f"{name}|{dtype}|fma{fma}|{gpu}|{tuple(ext)}|{tag}|{[int(p.shape[0]) for p in pts_sets]}"
+
+
 def autotune_record(name: str, dtype: str, ext, pts_sets, tag: str = ""):
     """The cached autotuning entry for this workload, if any."""
     import json
-    gpu = torch.cuda.get_device_name()
-    key = f"{name}|{dtype}|{gpu}|{tuple(ext)}|{tag}|{[int(p.shape[0]) for p in pts_sets]}"
+    key = _tune_key(name, dtype, ext, pts_sets, tag)
     try:
         with open(os.path.join(_CACHE_DIR, "autotune.json")) as f:
             return json.load(f).get(key)

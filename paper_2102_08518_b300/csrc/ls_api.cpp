@@ -231,7 +231,7 @@ ls_status get_kernel(ls_spline_s *s, const char *what, cudaKernel_t &k, int &per
 
 ls_variant default_variant(const ls_variant *v)
 {
-    ls_variant r{256, 1, 0, 0, 0, 0};
+    ls_variant r{256, 1, 0, 0, 0, 0, 0};
     if (v) {
         if (v->block > 0) r.block = v->block;
         if (v->pts_per_thread > 0) r.pts_per_thread = v->pts_per_thread > 64 ? 64 : v->pts_per_thread;
@@ -239,6 +239,7 @@ ls_variant default_variant(const ls_variant *v)
         r.min_blocks = v->min_blocks > 0 ? v->min_blocks : 0;
         r.group = v->group > 0 ? v->group : 0;
         r.depth = v->depth > 0 ? v->depth : 0;
+        r.blocks_per_sm = v->blocks_per_sm > 0 ? v->blocks_per_sm : 0;
     }
     return r;
 }
@@ -506,8 +507,10 @@ ls_status ls_eval(ls_volume v, const float *pts, int64_t n, float *out, ls_strea
     EvalArgsH a;
     fill_eval_args(v, pts, n, out, nullptr, a);
     const int T = (s->var.pts_per_thread > 1 && s->table.sep.empty()) ? s->var.pts_per_thread : 1;
-    return launch(s->mod.eval, grid_for((n + T - 1) / T, s->var.block, s->num_sms, s->mod.blocks_per_sm_eval),
-                  s->var.block, &a, (cudaStream_t)stream);
+    const int per_sm = s->var.blocks_per_sm > 0 ? std::min(s->var.blocks_per_sm, s->mod.blocks_per_sm_eval)
+                                                : s->mod.blocks_per_sm_eval;
+    return launch(s->mod.eval, grid_for((n + T - 1) / T, s->var.block, s->num_sms, per_sm), s->var.block, &a,
+                  (cudaStream_t)stream);
 }
 
 ls_status ls_eval_grad(ls_volume v, const float *pts, int64_t n, float *val, float *grad, ls_stream stream)
@@ -518,8 +521,10 @@ ls_status ls_eval_grad(ls_volume v, const float *pts, int64_t n, float *val, flo
     ls_spline_s *s = v->spline;
     EvalArgsH a;
     fill_eval_args(v, pts, n, val, grad, a);
-    return launch(s->mod.eval_grad, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_grad), s->var.block,
-                  &a, (cudaStream_t)stream);
+    const int per_sm = s->var.blocks_per_sm > 0 ? std::min(s->var.blocks_per_sm, s->mod.blocks_per_sm_grad)
+                                                : s->mod.blocks_per_sm_grad;
+    return launch(s->mod.eval_grad, grid_for(n, s->var.block, s->num_sms, per_sm), s->var.block, &a,
+                  (cudaStream_t)stream);
 }
 
 ls_status ls_eval_host_multi(int32_t n_vol, const ls_volume *vols, const float *host_pts, int64_t n,

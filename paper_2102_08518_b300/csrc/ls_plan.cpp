@@ -128,7 +128,7 @@ ls_status ls_plan_create(int32_t n_vol, const ls_volume *vols, const float *cons
         tag += "_" + (s->table.name.empty() ? std::string("s") : s->table.name);
     }
     if (tag.size() > 120) tag = tag.substr(0, 120);
-    ls_variant var{256, 1, 0, 0, 0, 0};
+    ls_variant var{256, 1, 0, 0, 0, 0, 0};
     ls::Generated g = ls::generate_batch(tabs, dts, var);
     auto *p = new (std::nothrow) ls_plan_s;
     if (!p) return ls_fail(LS_ERR_OOM, "host allocation");

@@ -118,6 +118,9 @@ class Table:
     separable: Optional[List[Axis1D]] = None
     degree: int = 0
     support_halfwidth: Tuple[Fraction, ...] = ()
+    # the same regions expanded about their dyadic centroids (an alternative the
+    # autotuner may pick: more FMAs, different register/load schedule)
+    regions_centroid: Optional[List[RefRegion]] = None
 
     def region_of(self, y_ref: Sequence[float]) -> int:
         q = 0
@@ -389,17 +392,27 @@ class TableBuilder:
         degree = len(spl.dirs) - s
         mons = monomials_upto(s, degree)
         refs = []
+        refs_c = []
         for st, members in regions:
             verts = []
             for _, cc in members:
                 verts += _vertices(cc)
-            cen = tuple(Fraction(round(float(sum(v[i] for v in verts) / len(verts)) * 64), 64)
-                        for i in range(s))
             sites = sorted(st, key=lambda n: (tuple(abs(v) for v in n), n))
+            if spl.roe == "parallelepiped":
+                # tensor-product splines are evaluated from their per-axis factors;
+                # the full table (kept for checks) is expanded about the centroid
+                vf = [[float(x) for x in v] for v in verts]
+                cen = tuple(Fraction(round(sum(v[i] for v in vf) / len(vf) * 64), 64) for i in range(s))
+            else:
+                cen = _choose_center([st[n] for n in sites], verts, [cc for _, cc in members], degree, self.rng)
             weights = [st[n].shift(cen) for n in sites]
             refs.append(RefRegion(sites=sites, center=cen, weights=weights, monomials=mons))
+            vf = [[float(x) for x in v] for v in verts]
+            cc0 = tuple(Fraction(round(sum(v[i] for v in vf) / len(vf) * 64), 64) for i in range(s))
+            refs_c.append(RefRegion(sites=sites, center=cc0, weights=[st[n].shift(cc0) for n in sites],
+                                    monomials=mons))
         table = Table(spline=spl, fold=fold, planes=planes, bsp_mod=p, sigma=sigma,
-                      regions=refs, degree=degree, support_halfwidth=self.hw)
+                      regions=refs, degree=degree, support_halfwidth=self.hw, regions_centroid=refs_c)
         table.separable = self._separable()
         return table
 
@@ -435,6 +448,80 @@ class TableBuilder:
                 weights.append(pc.shift([half - n]).shift([Fraction(1, 2)]))
             axes.append(Axis1D(sites=sites, center=Fraction(1, 2), weights=weights, degree=mult - 1))
         return axes
+
+
+def _dense(poly: Poly, deg: int, dim: int) -> np.ndarray:
+    a = np.zeros((deg + 1,) * dim)
+    for e, v in poly.c.items():
+        a[e] = float(v)
+    return a
+
+
+def _shift_dense(a: np.ndarray, c) -> np.ndarray:
+    """Coefficients of p(u + c) from those of p(u) (binomial matrix per axis)."""
+    from math import comb
+    deg = a.shape[0] - 1
+    for ax, cv in enumerate(c):
+        T = np.zeros((deg + 1, deg + 1))
+        for i in range(deg + 1):
+            for j in range(i, deg + 1):
+                T[i, j] = comb(j, i) * cv ** (j - i)
+        a = np.moveaxis(np.tensordot(T, np.moveaxis(a, ax, 0), axes=(1, 0)), 0, ax)
+    return a
+
+
+def _choose_center(weights, verts, cells, deg, rng):
+    """Expansion point of a reference sub-region's polynomials for FP32
+    evaluation.  The generated kernel spends one FMA per nonzero monomial
+    coefficient, and the FP32 rounding error of the Horner forms grows with
+    B(u) = sum_j sum_a |coef_ja| |u|^a over the region.  Among the points of the
+    1/8 grid inside the region's bounding box, take the one with the fewest
+    nonzero coefficients whose max B stays within 10 % of that of the dyadic
+    centroid (1/64 grid); ties go to the smaller B."""
+    dim = len(verts[0])
+    vf = np.array([[float(x) for x in v] for v in verts])
+    centroid = tuple(Fraction(round(float(vf[:, i].mean()) * 64), 64) for i in range(dim))
+    # samples of the region (rejection in the bounding box against the cells' constraints)
+    lo, hi = vf.min(0), vf.max(0)
+    pts = []
+    tries = 0
+    while len(pts) < 4000 and tries < 200:
+        tries += 1
+        cand = lo + (hi - lo) * np.array([[rng.random() for _ in range(dim)] for _ in range(2000)])
+        ok = np.zeros(len(cand), bool)
+        for cc in cells:
+            A = np.array([[float(x) for x in a] for a, _ in cc])
+            b = np.array([float(x) for _, x in cc])
+            ok |= np.all(cand @ A.T <= b + 1e-12, axis=1)
+        pts.extend(cand[ok].tolist())
+    if not pts:
+        return centroid
+    Y = np.array(pts[:4000])
+    dense = [_dense(w, deg, dim) for w in weights]
+    exps = np.array(list(np.ndindex(*(deg + 1,) * dim)))
+
+    def score(c):
+        cf = [float(x) for x in c]
+        U = np.abs(Y - np.array(cf))
+        powers = np.prod(U[:, None, :] ** exps[None, :, :], axis=2)          # (npts, nmono)
+        nnz, absum = 0, np.zeros(len(exps))
+        for a in dense:
+            sh = _shift_dense(a, cf).reshape(-1)
+            nz = np.abs(sh) > 1e-12
+            nnz += int(nz.sum())
+            absum += np.abs(sh) * nz
+        return nnz, float((powers @ absum).max())
+
+    base_nnz, base_b = score(centroid)
+    best = (base_nnz, base_b, centroid)
+    g0 = [int(np.floor(lo[i] * 8)) for i in range(dim)]
+    g1 = [int(np.ceil(hi[i] * 8)) for i in range(dim)]
+    for idx in itertools.product(*[range(g0[i], g1[i] + 1) for i in range(dim)]):
+        c = tuple(Fraction(v, 8) for v in idx)
+        nnz, b = score(c)
+        if b <= 1.1 * base_b and (nnz, b) < best[:2]:
+            best = (nnz, b, c)
+    return best[2]
 
 
 def _prune_planes(planes, q_to_region):

@@ -277,3 +277,18 @@ def test_coherent_reuse_variant_is_bitwise_identical(name, T):
         a, b = base.eval(p), reuse.eval(p)
         torch.cuda.synchronize()
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("name", ["bcc_linear", "bcc_quintic", "fcc6", "zp"])
+def test_centroid_expansion_variant(name):
+    """The tables expanded about the region centroids (an autotuning choice)."""
+    from paper_2102_08518_b300.api import Spline, Volume
+    lat = workloads.SPLINE_LATTICE[name]
+    ext = SMALL_EXT[name]
+    coef = workloads.coef_uniform(lat, ext, seed=81)
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = workloads.points_uniform(4000, lo - 2.0, hi + 2.0, seed=82)
+    vol = Volume(Spline(name, "f32", expansion="centroid"), ext, torch.from_numpy(coef).cuda())
+    got = gpu_eval(vol, pts)
+    want = oracle_eval(name, ext, coef, pts)
+    assert np.max(np.abs(got - want)) <= TOL * np.abs(coef).max()
