@@ -43,6 +43,7 @@ N_RAYS, RAY_STEPS = 4096, 4096
 CASES = [("bcc_linear", "uniform"), ("bcc_linear", "rays"), ("bcc_quintic", "uniform"), ("bcc_quintic", "rays")]
 WORKLOAD = ("bcc 2x128^3 smooth field; linear + quintic box splines; 2^24 uniform + 2^24 ray points "
             "(4096 rays x 4096 steps)")
+LAYOUT = "interleaved"          # default coefficient layout of the step's volumes (--layout)
 
 
 def dist_env():
@@ -176,16 +177,26 @@ def time_ms(torch, fn, reps=10, warm=3):
     return s.elapsed_time(e) / reps
 
 
-def profile_counters(kernel_source: str, kernel: str):
-    """DRAM / L2 traffic per launch from a committed ncu summary, if it was taken
-    on exactly this generated kernel: the hash covers the generated source up to
-    the end of that kernel (helpers, point function and the kernel itself)."""
+def kernel_hash(kernel_source: str, kernel: str):
+    """Hash of the generated code one evaluation kernel runs: its coefficient
+    loader, its point function and the kernel itself (not the other kernels and
+    argument structs of the module)."""
     try:
         m = kernel_source.index(kernel + "(const LsEvalArgs a)")
         end = kernel_source.index("}\n\n", m) + 3
+        pt = kernel_source.index("static __device__ __forceinline__ void ls_eval_pt__")
+        ld = [ln for ln in kernel_source.splitlines() if ln.startswith("static __device__ __forceinline__ float ls_ld_")]
     except ValueError:
+        return None
+    return hashlib.sha1(("\n".join(ld) + kernel_source[pt:end]).encode()).hexdigest()[:16]
+
+
+def profile_counters(kernel_source: str, kernel: str):
+    """DRAM / L2 traffic per launch from a committed ncu summary, if it was taken
+    on exactly this generated kernel (kernel_hash)."""
+    h = kernel_hash(kernel_source, kernel)
+    if h is None:
         return None, None
-    h = hashlib.sha1(kernel_source[:end].encode()).hexdigest()[:16]
     for path in glob.glob(os.path.join(ROOT, "profiles", "*.json")):
         try:
             with open(path) as f:
@@ -210,20 +221,21 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2102_08518_b300.api import (Volume, autotune, eval_host_multi, probe_gather, table,
+    from paper_2102_08518_b300.api import (Volume, autotune, eval_host_multi, probe_gather, relayout, table,
                                            TUNE_CANDIDATES_SMALL, _tune_key as tune_key)
     from paper_2102_08518_b300.roofline import distinct_sectors_per_point
 
     coef_np, pts_np = make_inputs(seed_offset=rank)
     dev = torch.device("cuda", local)
-    coef = torch.from_numpy(coef_np).to(dev)
+    coef_cm = torch.from_numpy(coef_np).to(dev)              # one array per coset
+    coef = relayout(coef_cm, 2, EXT, to=LAYOUT)             # the step's coefficient layout
     pts = {k: torch.from_numpy(v).to(dev) for k, v in pts_np.items()}
     # evaluation kernel variant per (spline, point set), autotuned on the step's own points (untimed)
     tuned = {(sp, ps): autotune(sp, "f32", EXT, coef, [pts[ps]], candidates=TUNE_CANDIDATES_SMALL,
-                                tag=f"bcc_step_{ps}") for sp, ps in CASES}
+                                tag=f"bcc_step_{ps}", layout=LAYOUT) for sp, ps in CASES}
     splines = {sp: tuned[(sp, "uniform")] for sp in ("bcc_linear", "bcc_quintic")}
-    vols = {n: Volume(s, EXT, coef) for n, s in splines.items()}
-    case_vols = {(sp, ps): Volume(tuned[(sp, ps)], EXT, coef) for sp, ps in CASES}
+    vols = {n: Volume(s, EXT, coef, layout=LAYOUT) for n, s in splines.items()}
+    case_vols = {(sp, ps): Volume(tuned[(sp, ps)], EXT, coef, layout=LAYOUT) for sp, ps in CASES}
     outs = {k: torch.empty(v.shape[0], device=dev) for k, v in pts.items()}
     stream = torch.cuda.current_stream()
 
@@ -271,7 +283,7 @@ def run_gpu(args):
     probe_gloads = (1 << 22) * 32 / (probe_ms * 1e-3) / 1e9
     peak_l2 = probe_gloads * 32.0                      # GB/s of 32-byte sectors
     sample = {ps: v[np.random.default_rng(7).choice(len(v), 1 << 14, replace=False)] for ps, v in pts_np.items()}
-    sectors = {sp: distinct_sectors_per_point(table(sp), EXT, sample["uniform"]) for sp in splines}
+    sectors = {sp: distinct_sectors_per_point(table(sp), EXT, sample["uniform"], layout=LAYOUT) for sp in splines}
     per_case = {}
     for (sp, ps), ms in zip(CASES, case_ms):
         n = N_UNIFORM if ps == "uniform" else N_RAYS * RAY_STEPS
@@ -294,10 +306,13 @@ def run_gpu(args):
     roofline = {"bound": "l2", "kernel": kname, "achieved": dom["l2_gather_gbs"], "peak": round(peak_l2, 1),
                 "unit": "GB/s", "frac": round(dom["l2_gather_gbs"] / peak_l2, 4), "traffic": traffic,
                 "algorithmic_bytes_per_point": round(sectors["bcc_quintic"] * 32.0, 1),
+                "algorithmic_unit": (f"distinct 32-byte sectors of one point's stencil in the {LAYOUT} layout "
+                                     f"({sectors['bcc_quintic']:.2f} per point, 2^14-point sample)"),
                 "coef_bytes_per_point": 4 * info["n_sites"],
                 "peak_source": ("measured in this run: random 4-byte loads from the L2-resident 16 MiB volume, "
                                 f"{probe_gloads:.1f} G loads/s x 32-byte sectors"),
                 "counters_from": cfile,
+                "kernel_hash": kernel_hash(splines["bcc_quintic"].source(), kname),
                 "l2_sector_bytes_per_launch": counters.get("l2_sector_bytes_per_launch") if counters else None}
     roofline_alu = {"bound": "alu", "kernel": kname, "achieved": dom["fp32_fma_tflops"], "peak": round(peak_fma, 2),
                     "unit": "TFLOP/s", "frac": round(dom["fp32_fma_tflops"] / peak_fma, 4),
@@ -334,16 +349,18 @@ def run_gpu(args):
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
               "data": "synthetic",
               "config": {"workload": WORKLOAD, "points_per_step": pts_per_step, "coef_bytes": coef_np.nbytes,
+                         "coef_layout": LAYOUT,
                          "l2": "points 201 MB per set > 126 MB L2 (inputs larger than L2); coefficient volume "
                                "16 MiB L2-resident by design", "parallelism": f"replicas x{world}"},
               "per_case": per_case, "roofline": roofline, "roofline_alu": roofline_alu, "e2e": e2e,
               "autotuned": {f"{sp}/{ps}": {"variant": tuned[(sp, ps)].variant,
-                                            "key": tune_key(sp, "f32", EXT, [pts[ps]], f"bcc_step_{ps}")}
+                                            "key": tune_key(sp, "f32", EXT, [pts[ps]], f"bcc_step_{ps}", LAYOUT)}
                             for sp, ps in CASES},
               "clocks": clocks, "gpu_launches": len(CASES) * args.steps}
     del host_pts, host_out
     if not args.no_extras:
         extras = {}
+        extras["layouts"] = extra_layouts(torch, dev, coef_cm, pts, outs, per_case)
         for name, fn in (("fwd_bwd", extra_fwd_bwd), ("fcc_sorted", extra_fcc), ("batched", extra_batched),
                          ("cg", extra_cg)):
             try:
@@ -365,48 +382,89 @@ def run_gpu(args):
 # extras: the other configurations
 # ---------------------------------------------------------------------------
 
+def extra_layouts(torch, dev, coef_cm, pts, outs, per_case):
+    """The step's four cases in the other coefficient layouts (coset-major: the
+    paper's per-coset lookup; interleaved; bricked), each with its own
+    autotuned variant, beside the headline layout's times."""
+    from paper_2102_08518_b300.api import Volume, autotune, relayout, TUNE_CANDIDATES_SMALL
+    res = {}
+    try:
+        for lay in ("coset", "interleaved", "bricked"):
+            if lay == LAYOUT:
+                continue
+            c = coef_cm if lay == "coset" else relayout(coef_cm, 2, EXT, to=lay)
+            for sp, ps in CASES:
+                s = autotune(sp, "f32", EXT, c, [pts[ps]], candidates=TUNE_CANDIDATES_SMALL, tag=f"bcc_step_{ps}",
+                             layout=lay)
+                v = Volume(s, EXT, c, layout=lay)
+                ms = time_ms(torch, lambda: v.eval(pts[ps], outs[ps]))
+                ent = res.setdefault(f"{sp}/{ps}", {f"{LAYOUT}_ms": per_case[f"{sp}/{ps}"]["ms"]})
+                ent[f"{lay}_ms"] = round(ms, 4)
+                ent[f"{lay}_variant"] = s.variant
+    except Exception as ex:
+        res["error"] = f"{type(ex).__name__}: {ex}"
+    return res
+
+
 def extra_fwd_bwd(torch, dev, vols, pts, outs):
-    """Plain FP32 forward vs value+gradient and the two adjoints (BCC quintic, 2^24 uniform points)."""
+    """Plain FP32 forward vs value+gradient and the three adjoints (BCC quintic,
+    2^24 uniform points; the warp-aggregated adjoint also on the ray points)."""
     from paper_2102_08518_b300 import _abi
     import ctypes
     vol = vols["bcc_quintic"]
     p = pts["uniform"]
     n = p.shape[0]
+    p_rays = pts["rays"]
     g = torch.randn(n, device=dev, generator=torch.Generator(device=dev).manual_seed(11))
     dc = torch.zeros(vol.n_coef, device=dev)
     scratch = torch.empty(int(_abi.lib().ls_adjoint_scratch_bytes(vol.handle, n)), dtype=torch.uint8, device=dev)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
-    def adj(det):
-        _abi.check(_abi.lib().ls_adjoint_coef(vol.handle, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(g.data_ptr()),
-                                              n, ctypes.c_void_p(dc.data_ptr()), det,
+    def adj(mode, q=None):
+        q = p if q is None else q
+        _abi.check(_abi.lib().ls_adjoint_coef(vol.handle, ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                              n, ctypes.c_void_p(dc.data_ptr()), mode,
                                               ctypes.c_void_p(scratch.data_ptr()), stream), "adjoint")
 
     t_plain = time_ms(torch, lambda: vol.eval(p, outs["uniform"]))
     t_grad = time_ms(torch, lambda: vol.eval_grad(p))
     t_adj_a = time_ms(torch, lambda: adj(0))
     t_adj_d = time_ms(torch, lambda: adj(1), reps=5)
+    t_adj_w = time_ms(torch, lambda: adj(2))
+    t_adj_f = time_ms(torch, lambda: adj(3))
+    t_rays_a = time_ms(torch, lambda: adj(0, p_rays))
+    t_rays_w = time_ms(torch, lambda: adj(2, p_rays))
     gp = lambda ms: round(n / (ms * 1e-3) / 1e9, 3)
     return {"workload": "bcc_quintic 2x128^3, 2^24 uniform points", "plain_f32_gpoints_s": gp(t_plain),
             "value_grad_gpoints_s": gp(t_grad), "adjoint_atomic_gpoints_s": gp(t_adj_a),
-            "adjoint_deterministic_gpoints_s": gp(t_adj_d),
+            "adjoint_deterministic_gpoints_s": gp(t_adj_d), "adjoint_warp_aggregated_gpoints_s": gp(t_adj_w),
+            "adjoint_deterministic_fixed_point_gpoints_s": gp(t_adj_f),
+            "fwd_bwd_deterministic_fixed_point_gpoints_s": gp(t_grad + t_adj_f),
+            "rays_adjoint_atomic_gpoints_s": gp(t_rays_a), "rays_adjoint_warp_aggregated_gpoints_s": gp(t_rays_w),
             "fwd_bwd_atomic_gpoints_s": gp(t_grad + t_adj_a), "fwd_bwd_deterministic_gpoints_s": gp(t_grad + t_adj_d),
             "fwd_bwd_vs_plain": round(t_plain / (t_grad + t_adj_a), 3)}
 
 
 def extra_fcc(torch, dev, vols, pts, outs):
     """FCC 4x128^3, 2^26 uniform points: unsorted vs Morton-sorted evaluation and gradient."""
-    from paper_2102_08518_b300.api import Spline, Volume, morton_sort, permute_rows
+    from paper_2102_08518_b300.api import Spline, Volume, morton_sort, permute_rows, relayout
     ext = (128, 128, 128)
-    coef = workloads.coef_uniform_torch("fcc", ext, seed=0)
+    coef_cm = workloads.coef_uniform_torch("fcc", ext, seed=0)
     lo, hi = workloads.inner_box("fcc6", ext)
     n = 1 << 26
     p = workloads.points_uniform_torch(n, lo, hi, seed=5)
-    vol = Volume(Spline("fcc6", "f32"), ext, coef)
+    vol_cm = Volume(Spline("fcc6", "f32"), ext, coef_cm)
     out = torch.empty(n, device=dev)
+    t_cm = time_ms(torch, lambda: vol_cm.eval(p, out), reps=5)
+    del vol_cm
+    coef = relayout(coef_cm, 4, ext, to="interleaved")
+    del coef_cm
+    vol = Volume(Spline("fcc6", "f32"), ext, coef, layout="interleaved")
     t_uns = time_ms(torch, lambda: vol.eval(p, out), reps=5)
     t_grad = time_ms(torch, lambda: vol.eval_grad(p, want_value=True), reps=3)
-    res = {"workload": "fcc6 4x128^3 (256^3 box), 2^26 uniform points", "unsorted_gpoints_s": round(n / t_uns / 1e6, 3),
+    res = {"workload": "fcc6 4x128^3 (256^3 box), 2^26 uniform points, interleaved cosets",
+           "unsorted_coset_major_gpoints_s": round(n / t_cm / 1e6, 3),
+           "unsorted_gpoints_s": round(n / t_uns / 1e6, 3),
            "unsorted_value_grad_gpoints_s": round(n / t_grad / 1e6, 3)}
     best = None
     for cell in (1.0, 2.0, 4.0, 8.0):                 # sort granularity (Morton cell edge)
@@ -528,7 +586,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--layout", default=LAYOUT, choices=["coset", "interleaved", "bricked"],
+                    help="coefficient layout of the step's volumes")
     args = ap.parse_args()
+    globals()["LAYOUT"] = args.layout
     if args.impl == "ours" and args.warmup < 3:
         args.warmup = 3
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)

@@ -16,10 +16,13 @@
  *    caller buffer.  Library objects (ls_spline, ls_volume, ls_plan) are owned
  *    by the library and freed by their destroy call.
  *  - Points are FP32, row-major, dim values per point (x_0 fastest within a point).
- *  - A coefficient volume stores one array per Cartesian coset l_j of the
+ *  - A coefficient volume holds one array per Cartesian coset l_j of the
  *    storage grid scale*Z^dim: element (i_0, .., i_{dim-1}) of array j is the
- *    coefficient of site scale*i + l_j.  Arrays are coset-major, axis 0
- *    fastest, all with the same extent.  Sites outside the arrays contribute 0.
+ *    coefficient of site scale*i + l_j; all arrays have the same extent, axis 0
+ *    fastest.  Three layouts (ls_layout): coset-major (array after array; the
+ *    per-coset memory lookup of Sec. 4.1), coset-interleaved (the n_cosets
+ *    values of one i adjacent) and bricked.  Sites outside the arrays
+ *    contribute 0.
  *  - Calls that take a cudaStream_t are asynchronous on that stream (0 = the
  *    legacy default stream).  They return an ls_status describing argument
  *    validation and launch; a fault found by a kernel is not reported here.
@@ -54,6 +57,25 @@ typedef enum {
 } ls_status;
 
 typedef enum { LS_F32 = 0, LS_BF16 = 1, LS_F16 = 2, LS_F64 = 3 } ls_dtype;
+
+/*
+ * Memory layout of a coefficient volume with C cosets of P = prod(ext) values.
+ * The value of coset j at grid index (i_0, i_1, i_2), q = i_0 + ext_0 (i_1 + ext_1 i_2), is
+ *   LS_LAYOUT_COSET_MAJOR:  element j * P + q   (one array per coset, Sec. 4.1)
+ *   LS_LAYOUT_INTERLEAVED:  element q * C + j   (cosets adjacent: the sites of
+ *                           both BCC cosets, or of all four FCC cosets, near one
+ *                           point share 32-byte sectors, so a stencil touches
+ *                           fewer of them; identical to coset-major when C = 1)
+ *   LS_LAYOUT_BRICKED:      element (b * V + w) * C + j, the grid cut into bricks
+ *                           of 4 x 2 x 2 indices (4 x 2 in 2D; V = 16 or 8) in
+ *                           x-fastest brick order b, w = (i_0 & 3) + 4 (i_1 & 1)
+ *                           + 8 (i_2 & 1) inside the brick: with FP32 and two
+ *                           cosets a brick is one 128-byte cache line, so a
+ *                           stencil touches fewer lines.  Needs ext_0 % 4 == 0,
+ *                           ext_1 % 2 == 0 (and ext_2 % 2 == 0 in 3D) and a spline
+ *                           created with ls_variant.brick = 1.
+ */
+typedef enum { LS_LAYOUT_COSET_MAJOR = 0, LS_LAYOUT_INTERLEAVED = 1, LS_LAYOUT_BRICKED = 2 } ls_layout;
 
 typedef enum {
     LS_ROE_PARALLELEPIPED = 0, /* k = floor(x) on the storage grid (Cartesian, scale 1)      */
@@ -102,7 +124,10 @@ typedef struct {
  *   planes: n_planes * (dim + 1) doubles (p_i, d_i); bit i of q is set iff
  *           p_i . y - d_i >= 0 for the folded point y (Sec. 4.1, sub-region
  *           membership); the reference sub-region is sigma[q % bsp_mod].
- *   separable: NULL, or dim axis factors used instead of ref (LS_FOLD_NONE only).
+ *   separable: NULL, or dim axis factors used instead of ref (LS_FOLD_NONE, the
+ *           Cartesian grid L = I; the region of evaluation is [0,1)^dim for
+ *           LS_ROE_PARALLELEPIPED or [-1/2,1/2]^dim around the nearest site for
+ *           LS_ROE_VORONOI, and each factor one polynomial piece there).
  */
 typedef struct {
     const char *name;                  /* nullable; [A-Za-z0-9_]{1,40}, used in kernel names */
@@ -140,6 +165,8 @@ typedef struct {
     int32_t blocks_per_sm;             /* grid = SMs x blocks_per_sm for the evaluation kernels
                                           (0 = as many as fit); bounds the resident warps per SM
                                           without taking L1 away (no recompilation) */
+    int32_t brick;                     /* 1: the kernels address LS_LAYOUT_BRICKED volumes (and only
+                                          those); 0: the linear layouts (coset-major, interleaved) */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */
@@ -176,16 +203,36 @@ ls_status ls_spline_info(ls_spline s, int32_t *n_sites, int32_t *fma_value,
 /* ---- coefficient volumes ----------------------------------------------------------- */
 /*
  * A volume is a view of n_cosets coefficient arrays of extent ext[0..dim-1]
- * in the spline's coef_dtype.  ls_volume_create allocates them (library-owned,
- * zero-filled); ls_volume_wrap uses a caller device buffer of
- * n_cosets * prod(ext) elements, which must outlive the volume.
+ * in the spline's coef_dtype, stored in `layout` (ls_layout).
+ * ls_volume_create allocates them (library-owned, zero-filled); ls_volume_wrap
+ * uses a caller device buffer of n_cosets * prod(ext) elements already in that
+ * layout, which must outlive the volume.  Every kernel reads (and the adjoint
+ * and the fit write) coefficients in the volume's layout.
+ * Errors: INVALID_ARG (NULL, extent outside 1..2^20, unknown layout, a
+ * bricked layout with extents that are not whole bricks, a layout the spline's
+ * kernels do not address), UNSUPPORTED (2^31 or more coefficients), OOM.
  */
-ls_status ls_volume_create(ls_spline s, const int64_t *ext, ls_volume *out);
-ls_status ls_volume_wrap(ls_spline s, const int64_t *ext, void *device_coef, ls_volume *out);
+ls_status ls_volume_create(ls_spline s, const int64_t *ext, int32_t layout, ls_volume *out);
+ls_status ls_volume_wrap(ls_spline s, const int64_t *ext, int32_t layout, void *device_coef,
+                         ls_volume *out);
 /* Copy (and convert) n_cosets*prod(ext) values of src_dtype from src (host or
- * device) into the volume. */
+ * device) into the volume.  src is in COSET-MAJOR layout; an interleaved
+ * volume receives the values rearranged. */
 ls_status ls_volume_upload(ls_volume v, const void *src, int32_t src_is_device,
                            ls_dtype src_dtype, ls_stream stream);
+/* The volume's ls_layout (-1 for NULL). */
+int32_t ls_volume_layout(ls_volume v);
+/*
+ * Copy n_cosets arrays of extent ext[0..dim-1] (ext[i] = 1 for i >= dim) with
+ * elements of elem_bytes (2, 4 or 8) from src in src_layout to dst in
+ * dst_layout (ls_layout): e.g. coefficients into the bricked layout, or an
+ * adjoint result of an interleaved volume back to one array per coset.  src
+ * and dst are distinct device buffers of n_cosets * prod(ext) elements.
+ * Errors: INVALID_ARG (NULL or equal buffers, bad sizes, unknown layout, a
+ * bricked side with extents that are not whole bricks).
+ */
+ls_status ls_relayout(const void *src, int32_t src_layout, void *dst, int32_t dst_layout,
+                      int32_t n_cosets, const int64_t *ext, int32_t elem_bytes, ls_stream stream);
 void *ls_volume_device_ptr(ls_volume v);
 ls_status ls_volume_destroy(ls_volume v);
 
@@ -219,18 +266,48 @@ ls_status ls_eval_host_multi(int32_t n_vol, const ls_volume *vols, const float *
                              float *const *host_out, ls_stream stream);
 
 /*
+ * How ls_adjoint_coef sums the contributions of the points to a coefficient.
+ *   LS_ADJ_ATOMIC:        one FP32 atomicAdd per (point, stencil site); the
+ *                         result depends on the order in its last bits.
+ *   LS_ADJ_DETERMINISTIC: the points are binned by their region-of-evaluation
+ *                         site and every coefficient sums its contributions in
+ *                         a fixed order: bitwise reproducible (needs scratch).
+ *   LS_ADJ_ATOMIC_WARP:   as LS_ADJ_ATOMIC, but the lanes of a warp that hit the
+ *                         same coefficient first add their values by shuffles
+ *                         (__match_any_sync) and one of them issues the atomic:
+ *                         fewer atomics when neighbouring points share sites
+ *                         (Morton-sorted or ray-ordered points).
+ *   LS_ADJ_DETERMINISTIC_FIXED: every value g * w is rounded to a multiple of
+ *                         2^-s and added exactly in an int64 per coefficient
+ *                         (integer atomics, so the order does not matter), then
+ *                         converted once: bitwise reproducible at about the
+ *                         atomic speed (needs scratch).  2^s is the largest
+ *                         power of two with sum|gout| * wmax * 2^s < 2^61
+ *                         (wmax: a bound on |phi| the generator derives from the
+ *                         table), so no sum can overflow; each value is off by at
+ *                         most 2^-(s+1) before the final FP32 rounding.  A
+ *                         non-finite gout gives an unspecified result.
+ */
+typedef enum {
+    LS_ADJ_ATOMIC = 0,
+    LS_ADJ_DETERMINISTIC = 1,
+    LS_ADJ_ATOMIC_WARP = 2,
+    LS_ADJ_DETERMINISTIC_FIXED = 3
+} ls_adjoint_mode;
+
+/*
  * Adjoint with respect to the coefficients (transposed stencil):
  *     dcoef[site n] += sum_i gout[i] * phi(pts[i] - n)
- * dcoef: FP32 device array with the volume's layout (n_cosets * prod(ext)),
- * accumulated into.  deterministic = 0: atomic scatter-add (result order-
- * dependent in the last bits).  deterministic = 1: the points are binned by
- * their region-of-evaluation site and every coefficient sums its contributions
- * in a fixed order (bitwise reproducible); needs scratch, see ls_adjoint_scratch_bytes.
- * scratch: device buffer of at least ls_adjoint_scratch_bytes(v, n) bytes
- * (NULL: the call allocates and frees it).
+ * The derivative of Eq. 1 with respect to c_n; not part of the paper, which
+ * only evaluates f.  dcoef: FP32 device array with the volume's layout
+ * (n_cosets * prod(ext)), accumulated into.  mode: ls_adjoint_mode.
+ * scratch (the two deterministic modes only): device buffer of at least
+ * ls_adjoint_scratch_bytes(v, n) bytes (NULL: the call allocates and frees it).
+ * Errors: INVALID_ARG (NULL buffers, n < 0, unknown mode), OOM, UNSUPPORTED
+ * (deterministic mode with 2^31 or more points or bins).
  */
 ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int64_t n,
-                          float *dcoef, int32_t deterministic, void *scratch,
+                          float *dcoef, int32_t mode, void *scratch,
                           ls_stream stream);
 size_t ls_adjoint_scratch_bytes(ls_volume v, int64_t n);
 
@@ -303,15 +380,15 @@ ls_status ls_plan_destroy(ls_plan plan);
 /*
  * Fit coefficients c to samples y_i at pts_i by CGLS on
  *     min_c ||A c - y||^2 + lambda ||c||^2,   A[i, n] = phi(pts_i - n),
- * with A c from ls_eval and A^T r from ls_adjoint_coef (deterministic when
- * deterministic = 1).  Dot products and norms are FP64 on the device.  coef
+ * with A c from ls_eval and A^T r from ls_adjoint_coef in adjoint_mode
+ * (ls_adjoint_mode; LS_ADJ_DETERMINISTIC makes the whole fit bitwise reproducible).  Dot products and norms are FP64 on the device.  coef
  * (the volume's FP32 array) holds the initial guess and receives the result.
  * Stops after max_iter iterations or when ||A^T r|| <= rel_tol ||A^T y||.
  * resid_hist (host, nullable, max_iter + 1 doubles): ||A^T r||_2 per iteration.
  * iters (host, nullable): iterations done.
  */
 ls_status ls_cg_fit(ls_volume v, const float *pts, const float *y, int64_t n, double lambda,
-                    int32_t max_iter, double rel_tol, int32_t deterministic,
+                    int32_t max_iter, double rel_tol, int32_t adjoint_mode,
                     double *resid_hist, int32_t *iters, ls_stream stream);
 
 /* ---- device helpers used by the FP64 parts of the fit -------------------------------- */

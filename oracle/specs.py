@@ -30,6 +30,16 @@ def tricubic(closed_form: bool = True) -> OrcSpec:
                    "tricubic")
 
 
+def trilinear() -> OrcSpec:
+    """Tensor-product linear B-spline (the hat function) on Z^3: each axis twice."""
+    return OrcSpec(3, (E1,) * 2 + (E2,) * 2 + (E3,) * 2, 1.0, 1, ((0, 0, 0),), (1, 1, 1), 0, "trilinear")
+
+
+def triquadratic() -> OrcSpec:
+    """Tensor-product quadratic B-spline on Z^3: each axis three times."""
+    return OrcSpec(3, (E1,) * 3 + (E2,) * 3 + (E3,) * 3, 1.0, 1, ((0, 0, 0),), (1, 1, 1), 0, "triquadratic")
+
+
 def bcc_linear() -> OrcSpec:
     return OrcSpec(3, BCC_DIRS, 4.0, 2, BCC_COSETS, (1, 1, 1), 0, "bcc_linear")
 
@@ -48,5 +58,5 @@ def zp2d() -> OrcSpec:
                    "zp2d")
 
 
-ALL_3D = {"tricubic": tricubic, "bcc_linear": bcc_linear, "bcc_quintic": bcc_quintic,
-          "fcc6": fcc6}
+ALL_3D = {"tricubic": tricubic, "trilinear": trilinear, "triquadratic": triquadratic,
+          "bcc_linear": bcc_linear, "bcc_quintic": bcc_quintic, "fcc6": fcc6}

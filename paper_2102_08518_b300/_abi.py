@@ -22,6 +22,10 @@ LS_F32, LS_BF16, LS_F16, LS_F64 = 0, 1, 2, 3
 # ls_roe / ls_fold
 LS_ROE_PARALLELEPIPED, LS_ROE_VORONOI = 0, 1
 LS_FOLD_NONE, LS_FOLD_SIGNED_PERM = 0, 1
+# ls_layout
+LS_LAYOUT_COSET_MAJOR, LS_LAYOUT_INTERLEAVED, LS_LAYOUT_BRICKED = 0, 1, 2
+# ls_adjoint_mode
+LS_ADJ_ATOMIC, LS_ADJ_DETERMINISTIC, LS_ADJ_ATOMIC_WARP, LS_ADJ_DETERMINISTIC_FIXED = 0, 1, 2, 3
 
 c_i32p = ctypes.POINTER(ctypes.c_int32)
 c_i64p = ctypes.POINTER(ctypes.c_int64)
@@ -52,7 +56,7 @@ class SplineDescC(ctypes.Structure):
 class VariantC(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("pts_per_thread", ctypes.c_int32), ("branchy", ctypes.c_int32),
                 ("min_blocks", ctypes.c_int32), ("group", ctypes.c_int32), ("depth", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("brick", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); every function declared in include/lattice_spline.h
@@ -66,8 +70,12 @@ SIGNATURES = {
     "ls_spline_precompile": (ctypes.c_int, [ctypes.POINTER(SplineDescC), ctypes.c_int, ctypes.POINTER(VariantC)]),
     "ls_spline_source": (ctypes.c_char_p, [ctypes.c_void_p]),
     "ls_spline_info": (ctypes.c_int, [ctypes.c_void_p, c_i32p, c_i32p, c_i32p, c_i32p]),
-    "ls_volume_create": (ctypes.c_int, [ctypes.c_void_p, c_i64p, ctypes.POINTER(ctypes.c_void_p)]),
-    "ls_volume_wrap": (ctypes.c_int, [ctypes.c_void_p, c_i64p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "ls_volume_create": (ctypes.c_int, [ctypes.c_void_p, c_i64p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
+    "ls_volume_wrap": (ctypes.c_int, [ctypes.c_void_p, c_i64p, ctypes.c_int32, ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "ls_volume_layout": (ctypes.c_int32, [ctypes.c_void_p]),
+    "ls_relayout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                   c_i64p, ctypes.c_int32, ctypes.c_void_p]),
     "ls_volume_upload": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int,
                                         ctypes.c_void_p]),
     "ls_volume_device_ptr": (ctypes.c_void_p, [ctypes.c_void_p]),
@@ -211,5 +219,6 @@ class DescHolder:
         return ctypes.cast(arr, c_f64p)
 
 
-def variant(block=256, pts_per_thread=1, branchy=0, min_blocks=0, group=0, depth=0, blocks_per_sm=0) -> VariantC:
-    return VariantC(block, pts_per_thread, branchy, min_blocks, group, depth, blocks_per_sm)
+def variant(block=256, pts_per_thread=1, branchy=0, min_blocks=0, group=0, depth=0, blocks_per_sm=0,
+            brick=0) -> VariantC:
+    return VariantC(block, pts_per_thread, branchy, min_blocks, group, depth, blocks_per_sm, brick)

@@ -22,6 +22,8 @@ _TABLE_VERSION = 4
 _CACHE_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "kcache")
 
 DTYPES = {"f32": _abi.LS_F32, "bf16": _abi.LS_BF16, "f16": _abi.LS_F16}
+LAYOUTS = {"coset": _abi.LS_LAYOUT_COSET_MAJOR, "interleaved": _abi.LS_LAYOUT_INTERLEAVED,
+           "bricked": _abi.LS_LAYOUT_BRICKED}
 TORCH_DTYPES = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
 
 
@@ -61,12 +63,14 @@ def _ptr(t: Optional[torch.Tensor]):
 
 
 def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_blocks: int = 0, group: int = 0,
-                depth: int = 0, pts_per_thread: int = 1, blocks_per_sm: int = 0, expansion: str = "sparse") -> str:
+                depth: int = 0, pts_per_thread: int = 1, blocks_per_sm: int = 0, expansion: str = "sparse",
+                brick: int = 0) -> str:
     """The name tag of a generated kernel variant (blocks_per_sm only sizes the
     grid, so it shares the compiled kernel)."""
     return f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + ("_br" if branchy else "") + \
         (f"_m{min_blocks}" if min_blocks else "") + (f"_g{group}d{depth}" if group and depth else "") + \
-        (f"_t{pts_per_thread}" if pts_per_thread > 1 else "") + ("_ec" if expansion == "centroid" else "")
+        (f"_t{pts_per_thread}" if pts_per_thread > 1 else "") + ("_ec" if expansion == "centroid" else "") + \
+        ("_bk" if brick else "")
 
 
 class Spline:
@@ -74,7 +78,8 @@ class Spline:
 
     def __init__(self, name: str, dtype: str = "f32", block: int = 256, branchy: int = 0,
                  min_blocks: int = 0, group: int = 0, depth: int = 0, pts_per_thread: int = 1,
-                 blocks_per_sm: int = 0, expansion: str = "sparse", kernel_name: Optional[str] = None):
+                 blocks_per_sm: int = 0, expansion: str = "sparse", brick: int = 0,
+                 kernel_name: Optional[str] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("lattice spline kernels need a CUDA device")
         self.name = name
@@ -84,14 +89,16 @@ class Spline:
         self.n_cosets = len(self.table.spline.lattice.cosets)
         self.scale = self.table.spline.lattice.scale
         kname = kernel_name or globals()["kernel_name"](name, dtype, block, branchy, min_blocks, group, depth,
-                                                         pts_per_thread, blocks_per_sm, expansion)
+                                                         pts_per_thread, blocks_per_sm, expansion, brick)
         self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
                         "depth": depth, "pts_per_thread": pts_per_thread, "blocks_per_sm": blocks_per_sm,
                         "expansion": expansion}
+        if brick:
+            self.variant["brick"] = 1
         self.kernel_name = kname
         self._desc = _abi.DescHolder(self.table, kname, expansion)
         var = _abi.variant(block=block, pts_per_thread=pts_per_thread, branchy=branchy, min_blocks=min_blocks,
-                           group=group, depth=depth, blocks_per_sm=blocks_per_sm)
+                           group=group, depth=depth, blocks_per_sm=blocks_per_sm, brick=brick)
         h = ctypes.c_void_p()
         torch.cuda.init()
         _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),
@@ -120,13 +127,20 @@ class Spline:
 class Volume:
     """Coefficients of a spline on n_cosets arrays of extent ext (axis 0 fastest).
 
-    ``coef`` (device tensor of the spline's storage dtype, shape
-    (n_cosets, ext[dim-1], ..., ext[0])) is wrapped without a copy; otherwise a
-    zero volume is allocated by the library.
+    ``layout``: "coset" (one array after another: shape (n_cosets, ext[dim-1],
+    ..., ext[0])), "interleaved" (the cosets' values of one grid index
+    adjacent: shape (ext[dim-1], ..., ext[0], n_cosets)) or "bricked" (bricks
+    of 4 x 2 x 2 grid indices, cosets interleaved inside; needs a spline made
+    with brick=1); see ``relayout``.
+    ``coef`` (device tensor of the spline's storage dtype in that layout) is
+    wrapped without a copy; otherwise a zero volume is allocated by the library.
     """
 
-    def __init__(self, spline: Spline, ext: Sequence[int], coef: Optional[torch.Tensor] = None):
+    def __init__(self, spline: Spline, ext: Sequence[int], coef: Optional[torch.Tensor] = None,
+                 layout: str = "coset"):
         self.spline = spline
+        self.layout = layout
+        lay = LAYOUTS[layout]
         self.ext = tuple(int(e) for e in ext) + (1,) * (3 - len(ext))
         e64 = (ctypes.c_int64 * 3)(*self.ext)
         h = ctypes.c_void_p()
@@ -138,10 +152,11 @@ class Volume:
                     coef.dtype != TORCH_DTYPES[spline.dtype]:
                 raise ValueError("coef must be a contiguous CUDA tensor of the spline's dtype and volume size")
             self.coef = coef
-            _abi.check(_abi.lib().ls_volume_wrap(spline.handle, e64, _ptr(coef), ctypes.byref(h)), "ls_volume_wrap")
+            _abi.check(_abi.lib().ls_volume_wrap(spline.handle, e64, lay, _ptr(coef), ctypes.byref(h)),
+                       "ls_volume_wrap")
         else:
             self.coef = None
-            _abi.check(_abi.lib().ls_volume_create(spline.handle, e64, ctypes.byref(h)), "ls_volume_create")
+            _abi.check(_abi.lib().ls_volume_create(spline.handle, e64, lay, ctypes.byref(h)), "ls_volume_create")
         self.handle = h
 
     @property
@@ -152,6 +167,8 @@ class Volume:
         return n
 
     def upload(self, src: torch.Tensor, stream=None):
+        """Copy coefficients given in coset-major order (host or device, any
+        float dtype) into the volume, converting dtype and layout."""
         dt = {torch.float32: _abi.LS_F32, torch.float64: _abi.LS_F64, torch.bfloat16: _abi.LS_BF16,
               torch.float16: _abi.LS_F16}[src.dtype]
         src = src.contiguous()
@@ -187,13 +204,16 @@ class Volume:
         return out_host
 
     def adjoint(self, pts: torch.Tensor, gout: torch.Tensor, dcoef: Optional[torch.Tensor] = None,
-                deterministic: bool = False, stream=None) -> torch.Tensor:
+                deterministic: bool = False, warp_aggregated: bool = False, stream=None) -> torch.Tensor:
+        """dcoef += A^T gout in the volume's layout: atomic (default), bitwise
+        deterministic, or atomic with warp aggregation of equal sites."""
         pts = _check_pts(pts, self.spline.dim)
+        mode = _adjoint_mode(deterministic, warp_aggregated)
         gout = gout.contiguous().float()
         if dcoef is None:
             dcoef = torch.zeros(self.n_coef, device=pts.device, dtype=torch.float32)
         _abi.check(_abi.lib().ls_adjoint_coef(self.handle, _ptr(pts), _ptr(gout), pts.shape[0], _ptr(dcoef),
-                                              int(deterministic), ctypes.c_void_p(0), _stream(stream)),
+                                              mode, ctypes.c_void_p(0), _stream(stream)),
                    "ls_adjoint_coef")
         return dcoef
 
@@ -205,6 +225,33 @@ class Volume:
             except Exception:
                 pass
             self.handle = None
+
+
+def _adjoint_mode(deterministic, warp_aggregated: bool) -> int:
+    """deterministic: False, True / "binned" (fixed summation order) or "fixed"
+    (fixed-point integer atomics); warp_aggregated: aggregated FP32 atomics."""
+    if deterministic and warp_aggregated:
+        raise ValueError("choose deterministic or warp_aggregated")
+    if deterministic == "fixed":
+        return _abi.LS_ADJ_DETERMINISTIC_FIXED
+    if deterministic:
+        return _abi.LS_ADJ_DETERMINISTIC
+    return _abi.LS_ADJ_ATOMIC_WARP if warp_aggregated else _abi.LS_ADJ_ATOMIC
+
+
+def relayout(coef: torch.Tensor, n_cosets: int, ext: Sequence[int], to: str = "interleaved",
+             src: str = "coset", stream=None) -> torch.Tensor:
+    """A copy of n_cosets coefficient arrays of extent ext (axis 0 first) moved
+    from layout ``src`` to layout ``to`` ("coset", "interleaved", "bricked")."""
+    coef = coef.contiguous()
+    e = tuple(int(v) for v in ext) + (1,) * (3 - len(ext))
+    if not coef.is_cuda or coef.numel() != n_cosets * e[0] * e[1] * e[2]:
+        raise ValueError("coef must be a CUDA tensor of n_cosets * prod(ext) elements")
+    dst = torch.empty_like(coef)
+    _abi.check(_abi.lib().ls_relayout(_ptr(coef), LAYOUTS[src], _ptr(dst), LAYOUTS[to], int(n_cosets),
+                                      (ctypes.c_int64 * 3)(*e), coef.element_size(), _stream(stream)),
+               "ls_relayout")
+    return dst
 
 
 def _check_pts(pts: torch.Tensor, dim: int) -> torch.Tensor:
@@ -267,7 +314,7 @@ def probe_gather(table_t: torch.Tensor, loads: int, nthreads: int, blocks: int =
 # ---------------------------------------------------------------------------
 
 def cg_fit(volume: "Volume", pts: torch.Tensor, y: torch.Tensor, lam: float = 0.0, max_iter: int = 200,
-           rel_tol: float = 1e-6, deterministic: bool = False, stream=None):
+           rel_tol: float = 1e-6, deterministic: bool = False, warp_aggregated: bool = False, stream=None):
     """CGLS on min ||A c - y||^2 + lam ||c||^2; the volume's coefficients (FP32)
     hold the initial guess and receive the result.  Returns (iterations, history)."""
     import numpy as np
@@ -276,7 +323,7 @@ def cg_fit(volume: "Volume", pts: torch.Tensor, y: torch.Tensor, lam: float = 0.
     hist = np.zeros(max_iter + 1)
     iters = ctypes.c_int32()
     _abi.check(_abi.lib().ls_cg_fit(volume.handle, _ptr(pts), _ptr(y), pts.shape[0], float(lam), int(max_iter),
-                                    float(rel_tol), int(deterministic),
+                                    float(rel_tol), _adjoint_mode(deterministic, warp_aggregated),
                                     hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(iters),
                                     _stream(stream)), "ls_cg_fit")
     return iters.value, hist[: iters.value + 1]
@@ -291,8 +338,8 @@ class SplineEval(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, coef, pts, spline, ext, deterministic):
-        vol = Volume(spline, ext, coef.detach().contiguous())
+    def forward(ctx, coef, pts, spline, ext, deterministic, layout="coset"):
+        vol = Volume(spline, ext, coef.detach().contiguous(), layout=layout)
         if pts.requires_grad:
             val, grad = vol.eval_grad(pts.detach())
         else:
@@ -312,12 +359,13 @@ class SplineEval(torch.autograd.Function):
             gcoef = ctx.vol.adjoint(pts, gout, deterministic=ctx.deterministic).view(ctx.coef_shape)
         if ctx.needs_input_grad[1]:
             gpts = gout[:, None] * grad
-        return gcoef, gpts, None, None, None
+        return gcoef, gpts, None, None, None, None
 
 
 def spline_eval(spline: Spline, ext: Sequence[int], coef: torch.Tensor, pts: torch.Tensor,
-                deterministic: bool = False) -> torch.Tensor:
-    return SplineEval.apply(coef, pts, spline, tuple(ext), deterministic)
+                deterministic: bool = False, layout: str = "coset") -> torch.Tensor:
+    """Differentiable f(pts); coef in ``layout``, and its gradient in the same layout."""
+    return SplineEval.apply(coef, pts, spline, tuple(ext), deterministic, layout)
 
 
 # ---------------------------------------------------------------------------
@@ -383,13 +431,14 @@ TUNE_CANDIDATES_SMALL = tuple([dict(block=256, blocks_per_sm=b, expansion=x) for
 
 
 def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_sets: Sequence[torch.Tensor],
-             candidates=DEFAULT_CANDIDATES, reps: int = 5, tag: str = "") -> "Spline":
+             candidates=DEFAULT_CANDIDATES, reps: int = 5, tag: str = "", layout: str = "coset") -> "Spline":
     """Generate the evaluation kernel in each candidate variant (block size,
     minimum blocks per SM, gather group size m and depth d), time it on the
-    caller's volume and point sets, and return the fastest Spline.  The choice
-    is cached on disk per (spline, dtype, GPU, tag)."""
+    caller's volume (``coef`` in ``layout``) and point sets, and return the
+    fastest Spline.  The choice is cached on disk per (spline, dtype, GPU, tag,
+    layout)."""
     import json
-    key = _tune_key(name, dtype, ext, pts_sets, tag)
+    key = _tune_key(name, dtype, ext, pts_sets, tag, layout)
     path = os.path.join(_CACHE_DIR, "autotune.json")
     cache = {}
     try:
@@ -410,8 +459,8 @@ def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_
     best = None
     results = []
     for cand in candidates:
-        sp = Spline(name, dtype, **cand)
-        vol = Volume(sp, ext, coef)
+        sp = Spline(name, dtype, **cand, **({"brick": 1} if layout == "bricked" else {}))
+        vol = Volume(sp, ext, coef, layout=layout)
         outs = [torch.empty(p.shape[0], device=p.device) for p in pts_sets]
         for p, o in zip(pts_sets, outs):
             vol.eval(p, o)
@@ -440,17 +489,18 @@ def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_
     return best[1]
 
 
-def _tune_key(name, dtype, ext, pts_sets, tag):
+def _tune_key(name, dtype, ext, pts_sets, tag, layout="coset"):
     # the generated kernel's FMA count identifies the table version the choice was made for
     fma = Spline(name, dtype).info()["fma_value"]
     gpu = torch.cuda.get_device_name()
-    return f"{name}|{dtype}|fma{fma}|{gpu}|{tuple(ext)}|{tag}|{[int(p.shape[0]) for p in pts_sets]}"
+    lay = "" if layout == "coset" else f"|{layout}"
+    return f"{name}|{dtype}|fma{fma}|{gpu}|{tuple(ext)}|{tag}|{[int(p.shape[0]) for p in pts_sets]}{lay}"
 
 
-def autotune_record(name: str, dtype: str, ext, pts_sets, tag: str = ""):
+def autotune_record(name: str, dtype: str, ext, pts_sets, tag: str = "", layout: str = "coset"):
     """The cached autotuning entry for this workload, if any."""
     import json
-    key = _tune_key(name, dtype, ext, pts_sets, tag)
+    key = _tune_key(name, dtype, ext, pts_sets, tag, layout)
     try:
         with open(os.path.join(_CACHE_DIR, "autotune.json")) as f:
             return json.load(f).get(key)

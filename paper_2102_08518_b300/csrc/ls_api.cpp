@@ -18,14 +18,16 @@ struct EvalArgsH {
     float *grad;
     const void *coef;
     long long n;
-    int e0, e1, e2, cstride;
+    int e0, e1, e2, cstride, cunit;
 };
 struct AdjArgsH {
     const float *pts;
     const float *gout;
     float *dcoef;
     long long n;
-    int e0, e1, e2, cstride;
+    int e0, e1, e2, cstride, cunit;
+    unsigned long long *iacc;
+    const float *iscale;
 };
 struct BinArgsH {
     const float *pts;
@@ -41,7 +43,7 @@ struct GatherArgsH {
     const void *srec;
     const uint32_t *start;
     float *dcoef;
-    int e0, e1, e2, cstride, halo;
+    int e0, e1, e2, cstride, cunit, halo;
 };
 
 const char *dtype_tag(ls_dtype d)
@@ -180,8 +182,12 @@ ls_status copy_desc(const ls_spline_desc *d, ls::Table &t)
         t.ref.push_back(rr);
     }
     if (d->separable) {
-        if (d->fold != LS_FOLD_NONE || d->roe != LS_ROE_PARALLELEPIPED || d->n_ref != 1)
-            return ls_fail(LS_ERR_UNSUPPORTED, "separable form needs fold none, parallelepiped ROE, one region");
+        if (d->fold != LS_FOLD_NONE || d->n_ref != 1 || d->scale != 1)
+            return ls_fail(LS_ERR_UNSUPPORTED, "separable form needs fold none, one region, the Cartesian grid");
+        for (int c = 0; c < d->dim; ++c)
+            for (int r = 0; r < d->dim; ++r)
+                if (d->generator[3 * c + r] != (c == r ? 1.0 : 0.0))
+                    return ls_fail(LS_ERR_UNSUPPORTED, "separable form needs L = I");
         for (int i = 0; i < d->dim; ++i) {
             const ls_axis_factor &a = d->separable[i];
             if (a.n_sites < 1 || a.n_sites > 8 || !a.sites || !a.coef || a.degree < 0 || a.degree > 8)
@@ -240,6 +246,7 @@ ls_variant default_variant(const ls_variant *v)
         r.group = v->group > 0 ? v->group : 0;
         r.depth = v->depth > 0 ? v->depth : 0;
         r.blocks_per_sm = v->blocks_per_sm > 0 ? v->blocks_per_sm : 0;
+        r.brick = v->brick ? 1 : 0;
     }
     return r;
 }
@@ -272,7 +279,7 @@ const char *ls_status_str(ls_status s)
 
 const char *ls_last_error(void) { return g_err.c_str(); }
 
-int32_t ls_abi_version(void) { return 1; }
+int32_t ls_abi_version(void) { return 2; }
 
 ls_status ls_spline_precompile(const ls_spline_desc *desc, ls_dtype dt, const ls_variant *variant)
 {
@@ -330,6 +337,8 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
     if ((st = get_kernel(s, "eval", s->mod.eval, s->mod.blocks_per_sm_eval)) != LS_OK ||
         (st = get_kernel(s, "eval_grad", s->mod.eval_grad, s->mod.blocks_per_sm_grad)) != LS_OK ||
         (st = get_kernel(s, "adjoint_atomic", s->mod.adj_atomic, s->mod.blocks_per_sm_adj)) != LS_OK ||
+        (st = get_kernel(s, "adjoint_warpagg", s->mod.adj_warpagg, s->mod.blocks_per_sm_warpagg)) != LS_OK ||
+        (st = get_kernel(s, "adjoint_fixed", s->mod.adj_fixed, s->mod.blocks_per_sm_fixed)) != LS_OK ||
         (st = get_kernel(s, "adjoint_bin", s->mod.roe_key, s->mod.blocks_per_sm_gather)) != LS_OK ||
         (st = get_kernel(s, "adjoint_gather", s->mod.adj_gather, s->mod.blocks_per_sm_gather)) != LS_OK) {
         cudaLibraryUnload(s->mod.lib);
@@ -367,10 +376,16 @@ ls_status ls_spline_info(ls_spline s, int32_t *n_sites, int32_t *fma_value, int3
 // volumes
 // ---------------------------------------------------------------------------
 
-static ls_status init_volume(ls_spline s, const int64_t *ext, ls_volume_s *v)
+static ls_status init_volume(ls_spline s, const int64_t *ext, int32_t layout, ls_volume_s *v)
 {
     if (!s || !ext) return ls_fail(LS_ERR_INVALID_ARG, "spline or ext is NULL");
+    if (layout != LS_LAYOUT_COSET_MAJOR && layout != LS_LAYOUT_INTERLEAVED && layout != LS_LAYOUT_BRICKED)
+        return ls_fail(LS_ERR_INVALID_ARG, "unknown layout");
+    if ((layout == LS_LAYOUT_BRICKED) != (s->var.brick != 0))
+        return ls_fail(LS_ERR_INVALID_ARG, s->var.brick ? "the spline's kernels address the bricked layout only"
+                                                       : "a bricked volume needs a spline created with variant.brick = 1");
     v->spline = s;
+    v->layout = layout;
     int64_t prod = 1;
     for (int i = 0; i < 3; ++i) {
         v->ext[i] = i < s->table.dim ? ext[i] : 1;
@@ -379,18 +394,21 @@ static ls_status init_volume(ls_spline s, const int64_t *ext, ls_volume_s *v)
     }
     v->coset_elems = prod;
     v->total_elems = prod * (int64_t)s->table.cosets.size();
+    if (layout == LS_LAYOUT_BRICKED &&
+        (v->ext[0] % 4 != 0 || (s->table.dim >= 2 && v->ext[1] % 2 != 0) || (s->table.dim == 3 && v->ext[2] % 2 != 0)))
+        return ls_fail(LS_ERR_INVALID_ARG, "bricked layout: ext[0] % 4, ext[1] % 2 and ext[2] % 2 must be 0");
     if (v->total_elems >= (int64_t)1 << 31)
         return ls_fail(LS_ERR_UNSUPPORTED, "volume exceeds 2^31 coefficients (32-bit addressing)");
     return LS_OK;
 }
 
-ls_status ls_volume_create(ls_spline s, const int64_t *ext, ls_volume *out)
+ls_status ls_volume_create(ls_spline s, const int64_t *ext, int32_t layout, ls_volume *out)
 {
     if (!out) return ls_fail(LS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     auto *v = new (std::nothrow) ls_volume_s;
     if (!v) return ls_fail(LS_ERR_OOM, "host allocation");
-    ls_status st = init_volume(s, ext, v);
+    ls_status st = init_volume(s, ext, layout, v);
     if (st != LS_OK) {
         delete v;
         return st;
@@ -413,13 +431,13 @@ ls_status ls_volume_create(ls_spline s, const int64_t *ext, ls_volume *out)
     return LS_OK;
 }
 
-ls_status ls_volume_wrap(ls_spline s, const int64_t *ext, void *device_coef, ls_volume *out)
+ls_status ls_volume_wrap(ls_spline s, const int64_t *ext, int32_t layout, void *device_coef, ls_volume *out)
 {
     if (!out || !device_coef) return ls_fail(LS_ERR_INVALID_ARG, "out or device_coef is NULL");
     *out = nullptr;
     auto *v = new (std::nothrow) ls_volume_s;
     if (!v) return ls_fail(LS_ERR_OOM, "host allocation");
-    ls_status st = init_volume(s, ext, v);
+    ls_status st = init_volume(s, ext, layout, v);
     if (st != LS_OK) {
         delete v;
         return st;
@@ -432,6 +450,33 @@ ls_status ls_volume_wrap(ls_spline s, const int64_t *ext, void *device_coef, ls_
 
 void *ls_volume_device_ptr(ls_volume v) { return v ? v->coef : nullptr; }
 
+int32_t ls_volume_layout(ls_volume v) { return v ? v->layout : -1; }
+
+ls_status ls_relayout(const void *src, int32_t src_layout, void *dst, int32_t dst_layout, int32_t n_cosets,
+                      const int64_t *ext, int32_t elem_bytes, ls_stream stream)
+{
+    if (!ext || n_cosets < 1 || n_cosets > 8) return ls_fail(LS_ERR_INVALID_ARG, "ext NULL or n_cosets outside 1..8");
+    if (elem_bytes != 2 && elem_bytes != 4 && elem_bytes != 8) return ls_fail(LS_ERR_INVALID_ARG, "elem_bytes");
+    int64_t per = 1;
+    for (int i = 0; i < 3; ++i) {
+        if (ext[i] < 1 || ext[i] > (1 << 20)) return ls_fail(LS_ERR_INVALID_ARG, "extent outside 1..2^20");
+        per *= ext[i];
+    }
+    if (per * n_cosets >= ((int64_t)1 << 31)) return ls_fail(LS_ERR_UNSUPPORTED, "2^31 or more elements");
+    for (int32_t l : {src_layout, dst_layout}) {
+        if (l < LS_LAYOUT_COSET_MAJOR || l > LS_LAYOUT_BRICKED) return ls_fail(LS_ERR_INVALID_ARG, "unknown layout");
+        if (l == LS_LAYOUT_BRICKED && (ext[0] % 4 != 0 || ext[1] % 2 != 0 || (ext[2] != 1 && ext[2] % 2 != 0)))
+            return ls_fail(LS_ERR_INVALID_ARG, "bricked layout: extents are not whole bricks");
+    }
+    if (!src || !dst || src == dst) return ls_fail(LS_ERR_INVALID_ARG, "src, dst NULL or the same buffer");
+    const lsk::LayoutGeom sg{src_layout, n_cosets, (long long)per, (int)ext[0], (int)ext[1], (int)ext[2]};
+    lsk::LayoutGeom dg = sg;
+    dg.layout = dst_layout;
+    cudaError_t e = lsk::relayout(src, sg, dst, dg, elem_bytes, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "relayout kernel");
+    return LS_OK;
+}
+
 ls_status ls_volume_upload(ls_volume v, const void *src, int32_t src_is_device, ls_dtype src_dt, ls_stream stream)
 {
     if (!v || !src) return ls_fail(LS_ERR_INVALID_ARG, "volume or src is NULL");
@@ -439,7 +484,13 @@ ls_status ls_volume_upload(ls_volume v, const void *src, int32_t src_is_device, 
     const ls_dtype dst_dt = v->spline->dtype;
     const size_t n = (size_t)v->total_elems;
     if (dtype_size(src_dt) == 0) return ls_fail(LS_ERR_INVALID_ARG, "src dtype");
-    if (src_dt == dst_dt) {
+    const int ncos = (int)v->spline->table.cosets.size();
+    const lsk::LayoutGeom dg{v->layout, ncos, (long long)v->coset_elems, (int)v->ext[0], (int)v->ext[1],
+                             (int)v->ext[2]};
+    lsk::LayoutGeom sg = dg;
+    sg.layout = LS_LAYOUT_COSET_MAJOR;
+    const bool same_order = v->layout == LS_LAYOUT_COSET_MAJOR || (v->layout == LS_LAYOUT_INTERLEAVED && ncos == 1);
+    if (src_dt == dst_dt && same_order) {
         cudaError_t e = cudaMemcpyAsync(v->coef, src, n * dtype_size(dst_dt),
                                         src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
@@ -457,7 +508,7 @@ ls_status ls_volume_upload(ls_volume v, const void *src, int32_t src_is_device, 
         }
         dsrc = tmp;
     }
-    cudaError_t e = lsk::convert(dsrc, (int)src_dt, v->coef, (int)dst_dt, (long long)n, st);
+    cudaError_t e = lsk::convert_relayout(dsrc, (int)src_dt, sg, v->coef, (int)dst_dt, dg, st);
     if (tmp) cudaFreeAsync(tmp, st);
     if (e != cudaSuccess) return cuda_fail(e, "convert kernel");
     return LS_OK;
@@ -495,7 +546,8 @@ static void fill_eval_args(ls_volume v, const float *pts, int64_t n, float *out,
     a.e0 = (int)v->ext[0];
     a.e1 = (int)v->ext[1];
     a.e2 = (int)v->ext[2];
-    a.cstride = (int)v->coset_elems;
+    a.cstride = vol_cstride(v);
+    a.cunit = vol_cunit(v);
 }
 
 ls_status ls_eval(ls_volume v, const float *pts, int64_t n, float *out, ls_stream stream)
@@ -617,21 +669,55 @@ size_t ls_adjoint_scratch_bytes(ls_volume v, int64_t n)
 {
     if (!v || n < 0) return 0;
     const size_t N = (size_t)n;
-    return al256b(N * 4) * 2 + al256b(N * 16) * 2 + al256b((adjoint_nbins(v) + 2) * 4) +
-           lsk::sort_scratch_bytes(n > 0 ? n : 1) + 256;
+    const size_t binned = al256b(N * 4) * 2 + al256b(N * 16) * 2 + al256b((adjoint_nbins(v) + 2) * 4) +
+                          lsk::sort_scratch_bytes(n > 0 ? n : 1) + 256;
+    const size_t fixed = al256b((size_t)v->total_elems * 8) + lsk::fixed_ws_bytes() + 256;
+    return binned > fixed ? binned : fixed;
 }
 
 ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int64_t n, float *dcoef,
-                          int32_t deterministic, void *scratch, ls_stream stream)
+                          int32_t mode, void *scratch, ls_stream stream)
 {
+    if (mode != LS_ADJ_ATOMIC && mode != LS_ADJ_DETERMINISTIC && mode != LS_ADJ_ATOMIC_WARP &&
+        mode != LS_ADJ_DETERMINISTIC_FIXED)
+        return ls_fail(LS_ERR_INVALID_ARG, "unknown adjoint mode");
     if (!v || (n > 0 && (!pts || !gout || !dcoef))) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
     if (n < 0) return ls_fail(LS_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return LS_OK;
     ls_spline_s *s = v->spline;
     cudaStream_t st = (cudaStream_t)stream;
-    if (!deterministic) {
+    if (mode == LS_ADJ_DETERMINISTIC_FIXED) {
+        const size_t need = ls_adjoint_scratch_bytes(v, n);
+        void *ws = scratch;
+        if (!ws && cudaMallocAsync(&ws, need, st) != cudaSuccess) {
+            cudaGetLastError();
+            return ls_fail(LS_ERR_OOM, "scratch for the fixed-point adjoint");
+        }
+        unsigned long long *acc = (unsigned long long *)ws;
+        void *fws = (char *)ws + al256b((size_t)v->total_elems * 8);
+        float *scale = nullptr;
+        double *inv = nullptr;
+        ls_status res = LS_OK;
+        cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)v->total_elems * 8, st);
+        if (e == cudaSuccess) e = lsk::fixed_prepare(gout, n, s->gen.info.wmax, fws, &scale, &inv, st);
+        if (e != cudaSuccess) res = cuda_fail(e, "fixed-point adjoint setup");
+        if (res == LS_OK) {
+            AdjArgsH a{pts, gout, dcoef, (long long)n, (int)v->ext[0], (int)v->ext[1], (int)v->ext[2],
+                       vol_cstride(v), vol_cunit(v), acc, scale};
+            res = launch(s->mod.adj_fixed, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_fixed),
+                         s->var.block, &a, st);
+        }
+        if (res == LS_OK && (e = lsk::fixed_finish(acc, inv, dcoef, v->total_elems, st)) != cudaSuccess)
+            res = cuda_fail(e, "fixed-point adjoint finish");
+        if (!scratch) cudaFreeAsync(ws, st);
+        return res;
+    }
+    if (mode != LS_ADJ_DETERMINISTIC) {
         AdjArgsH a{pts, gout, dcoef, (long long)n, (int)v->ext[0], (int)v->ext[1], (int)v->ext[2],
-                   (int)v->coset_elems};
+                   vol_cstride(v), vol_cunit(v), nullptr, nullptr};
+        if (mode == LS_ADJ_ATOMIC_WARP)
+            return launch(s->mod.adj_warpagg, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_warpagg),
+                          s->var.block, &a, st);
         return launch(s->mod.adj_atomic, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_adj),
                       s->var.block, &a, st);
     }
@@ -670,7 +756,8 @@ ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int6
     if (res == LS_OK && e == cudaSuccess) e = lsk::bin_starts(key, n, (uint32_t)nbins, start, st);
     if (res == LS_OK && e != cudaSuccess) res = cuda_fail(e, "deterministic adjoint kernels");
     if (res == LS_OK) {
-        GatherArgsH ga{srec, start, dcoef, (int)v->ext[0], (int)v->ext[1], (int)v->ext[2], (int)v->coset_elems, H};
+        GatherArgsH ga{srec, start, dcoef, (int)v->ext[0], (int)v->ext[1], (int)v->ext[2], vol_cstride(v), vol_cunit(v),
+                       H};
         res = launch(s->mod.adj_gather, grid_for(v->total_elems, s->var.block, s->num_sms, 8), s->var.block, &ga, st);
     }
     if (!scratch) cudaFreeAsync(ws, st);

@@ -25,13 +25,17 @@ size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 }  // namespace
 
 extern "C" ls_status ls_cg_fit(ls_volume v, const float *pts, const float *y, int64_t n, double lambda,
-                               int32_t max_iter, double rel_tol, int32_t deterministic, double *resid_hist,
+                               int32_t max_iter, double rel_tol, int32_t adjoint_mode, double *resid_hist,
                                int32_t *iters, ls_stream stream)
 {
     if (!v || (n > 0 && (!pts || !y))) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
     if (n <= 0 || max_iter < 0 || !(lambda >= 0.0) || !(rel_tol >= 0.0))
         return ls_fail(LS_ERR_INVALID_ARG, "n > 0, max_iter >= 0, lambda >= 0 and rel_tol >= 0 required");
     if (v->spline->dtype != LS_F32) return ls_fail(LS_ERR_UNSUPPORTED, "the fit needs FP32 coefficient storage");
+    if (adjoint_mode != LS_ADJ_ATOMIC && adjoint_mode != LS_ADJ_DETERMINISTIC && adjoint_mode != LS_ADJ_ATOMIC_WARP &&
+        adjoint_mode != LS_ADJ_DETERMINISTIC_FIXED)
+        return ls_fail(LS_ERR_INVALID_ARG, "unknown adjoint mode");
+    const bool deterministic = adjoint_mode == LS_ADJ_DETERMINISTIC || adjoint_mode == LS_ADJ_DETERMINISTIC_FIXED;
     cudaStream_t st = (cudaStream_t)stream;
     const long long nc = v->total_elems, nr = n;
     const size_t adj_bytes = deterministic ? ls_adjoint_scratch_bytes(v, n) : 0;
@@ -76,7 +80,7 @@ extern "C" ls_status ls_cg_fit(ls_volume v, const float *pts, const float *y, in
     auto adjoint_into = [&](const float *w, float *dst) -> ls_status {
         cudaError_t e = cudaMemsetAsync(dst, 0, nc * 4, st);
         if (e != cudaSuccess) return cuda_err(e, "cudaMemsetAsync");
-        return ls_adjoint_coef(v, pts, w, n, dst, deterministic, adj_ws, stream);
+        return ls_adjoint_coef(v, pts, w, n, dst, adjoint_mode, adj_ws, stream);
     };
     ls_status res;
     cudaError_t e;

@@ -45,6 +45,7 @@ struct Emitter {
     int tmp = 0;
     int fma = 0;
     std::string ld = "ls_ld_f32";     // coefficient loader of the spline being emitted
+    bool brick = false;               // bricked coefficient layout (else linear)
     std::string fresh(const char *p) { return std::string(p) + std::to_string(tmp++); }
 };
 
@@ -98,13 +99,30 @@ void emit_prologue(Emitter &e)
          " ls_u16 h = __ldg((const ls_u16*)p + i); float f; asm(\"cvt.f32.f16 %0, %1;\" : \"=f\"(f) : \"h\"(h));"
          " return f; }\n";
     o << "struct LsEvalArgs { const float* pts; float* out; float* grad; const void* coef;"
-         " long long n; int e0, e1, e2, cstride; };\n";
+         " long long n; int e0, e1, e2, cstride, cunit; };\n";
     o << "struct LsAdjArgs { const float* pts; const float* gout; float* dcoef;"
-         " long long n; int e0, e1, e2, cstride; };\n";
+         " long long n; int e0, e1, e2, cstride, cunit; unsigned long long* iacc; const float* iscale; };\n";
     o << "struct LsBinArgs { const float* pts; const float* gout; unsigned* key; int* idx; float4* rec;"
          " long long n; int e0, e1, e2, halo; unsigned nbins; };\n";
     o << "struct LsGatherArgs { const float4* srec; const unsigned* start; float* dcoef;"
-         " int e0, e1, e2, cstride, halo; };\n";
+         " int e0, e1, e2, cstride, cunit, halo; };\n";
+    // warp-aggregated scatter-add: lanes with the same address sum their values
+    // by shuffles (per-lane source lanes, warp-uniform trip count) and the
+    // lowest of them issues one atomic; ad < 0 means no site (nothing added)
+    o << "static __device__ __forceinline__ void ls_agg_add(float* base, int ad, float v) {\n"
+         "  const unsigned am = __activemask();\n"
+         "  const unsigned peers = __match_any_sync(am, ad);\n"
+         "  const unsigned lane = threadIdx.x & 31u;\n"
+         "  const int mx = (int)__reduce_max_sync(am, (unsigned)__popc(peers));\n"
+         "  float s = v;\n"
+         "  unsigned rest = peers & ~(1u << lane);\n"
+         "  for (int k = 1; k < mx; ++k) {\n"
+         "    const int src = rest ? __ffs(rest) - 1 : (int)lane;\n"
+         "    const float o = __shfl_sync(am, v, src);\n"
+         "    if (rest) { s += o; rest &= rest - 1u; }\n"
+         "  }\n"
+         "  if (ad >= 0 && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(base + ad, s);\n"
+         "}\n";
     o << "#define LS_CSWAP(A, B, PA, PB, NA, NB) { bool sw_ = (A) < (B); float ta_ = sw_ ? (B) : (A);"
          " float tb_ = sw_ ? (A) : (B); int pa_ = sw_ ? (PB) : (PA); int pb_ = sw_ ? (PA) : (PB);"
          " unsigned na_ = sw_ ? (NB) : (NA); unsigned nb_ = sw_ ? (NA) : (NB);"
@@ -229,9 +247,22 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
         for (size_t j = 0; j < sites.size(); ++j) o << "    float c" << j << ";\n";
     if (declare_addr)
         for (size_t j = 0; j < sites.size(); ++j) o << "    int ad" << j << ";\n";
+    // Address of (coset j, per-coset index q).  Linear layouts (coset-major,
+    // interleaved): j * CS + CU * (q0 + ex0 (q1 + ex1 q2)).  Bricked layout
+    // (4 x 2 x 2 indices per brick, cosets interleaved inside, e.brick):
+    // j + sum_i [BA_i q_i + BB_i (q_i >> SH_i)] with SH = (2, 1, 1), which is
+    // BH_i (q_i >> SH_i) + BA_i (q_i & mask) per axis.
+    if (e.brick) {
+        o << "    const int BA0 = CU, BA1 = 4 * CU, BA2 = 8 * CU;\n";
+        o << "    const int BH0 = " << (D == 3 ? 16 : 8) << " * CU, BH1 = BH0 * (ex0 >> 2), BH2 = BH1 * (ex1 >> 1);\n";
+        o << "    const int BB0 = BH0 - 4 * BA0, BB1 = BH1 - 2 * BA1, BB2 = BH2 - 2 * BA2;\n";
+        o << "    (void)BA2; (void)BB2;\n";
+    }
     o << "    if (inside) {\n";
-    // strides of the reference axes
-    const char *st[3] = {"1", "ex0", "(ex0 * ex1)"};
+    // strides of the reference axes (the linear part)
+    const char *st_lin[3] = {"CU", "(CU * ex0)", "(CU * ex0 * ex1)"};
+    const char *st_brk[3] = {"BA0", "BA1", "BA2"};
+    const char *const *st = e.brick ? st_brk : st_lin;
     for (int r = 0; r < D; ++r) {
         if (fold) {
             o << "      int rs" << r << " = ";
@@ -242,6 +273,22 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             o << "      const int rs" << r << " = " << st[r] << ";\n";
         }
     }
+    if (e.brick) {
+        // per reference axis: the Cartesian axis' brick shift and coefficient, the sign
+        const char *bb[3] = {"BB0", "BB1", "BB2"};
+        for (int r = 0; r < D; ++r) {
+            if (fold) {
+                o << "      const int bsh" << r << " = (p" << r << " == 0) ? 2 : 1;\n";
+                o << "      const int bbt" << r << " = ";
+                for (int i = 0; i < D - 1; ++i) o << "(p" << r << " == " << i << ") ? " << bb[i] << " : ";
+                o << bb[D - 1] << ";\n";
+                o << "      const int bsg" << r << " = g" << r << " ? -1 : 1;\n";
+            } else {
+                o << "      const int bsh" << r << " = " << (r == 0 ? 2 : 1) << ", bbt" << r << " = " << bb[r]
+                  << ", bsg" << r << " = 1;\n";
+            }
+        }
+    }
     // parity classes
     std::map<int, std::string> base_of_class;
     auto parity_class = [&](const I3 &s) {
@@ -250,11 +297,48 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             for (int r = 0; r < D; ++r) m |= (s[r] & 1) << r;
         return m;
     };
+    auto hoff = [&](const I3 &s, int r) { return (a == 2) ? floordiv2(s[r]) : s[r]; };
+    // the per-class grid index of the class' h = 0 site on each Cartesian axis
+    // (Q<m>_<i>) and its coset id; the base address of the class
+    auto emit_brick_class = [&](int m, const std::string &qexpr0, const std::string &qexpr1,
+                                const std::string &qexpr2, const std::string &cidexpr) {
+        const std::string qx[3] = {qexpr0, qexpr1, qexpr2};
+        for (int i = 0; i < D; ++i) o << "      const int Q" << m << "_" << i << " = " << qx[i] << ";\n";
+        // grid index on reference axis r: Q<m>_{p_r}
+        for (int r = 0; r < D; ++r) {
+            o << "      const int QR" << m << "_" << r << " = ";
+            if (fold) {
+                for (int i = 0; i < D - 1; ++i) o << "(p" << r << " == " << i << ") ? Q" << m << "_" << i << " : ";
+                o << "Q" << m << "_" << (D - 1) << ";\n";
+            } else {
+                o << "Q" << m << "_" << r << ";\n";
+            }
+        }
+        std::string nm = "base" + std::to_string(m);
+        o << "      const int " << nm << " = " << cidexpr;
+        for (int i = 0; i < D; ++i) o << " + BA" << i << " * Q" << m << "_" << i;
+        o << ";\n";
+        // nonlinear terms of every offset h used by this class on axis r
+        std::set<std::pair<int, int>> used;
+        for (const auto &sv : sites)
+            if (parity_class(sv) == m)
+                for (int r = 0; r < D; ++r) used.insert({r, hoff(sv, r)});
+        for (const auto &rh : used) {
+            const int r = rh.first, h = rh.second;
+            o << "      const int nl" << m << "_" << r << "_" << (h < 0 ? "m" : "") << std::abs(h) << " = bbt" << r
+              << " * ((QR" << m << "_" << r << " + bsg" << r << " * (" << h << ")) >> bsh" << r << ");\n";
+        }
+        base_of_class[m] = nm;
+    };
     if (a == 1) {
-        o << "      const int base0 = ";
-        o << "k0" << (D >= 2 ? " + ex0 * (k1" : "") << (D == 3 ? " + ex1 * k2" : "") << (D >= 2 ? ")" : "")
-          << ";\n";
-        base_of_class[0] = "base0";
+        if (e.brick) {
+            emit_brick_class(0, "k0", D >= 2 ? "k1" : "0", D == 3 ? "k2" : "0", "0");
+        } else {
+            o << "      const int base0 = CU * (";
+            o << "k0" << (D >= 2 ? " + ex0 * (k1" : "") << (D == 3 ? " + ex1 * k2" : "") << (D >= 2 ? ")" : "")
+              << ");\n";
+            base_of_class[0] = "base0";
+        }
     } else {
         const unsigned long long lut = coset_lut(t);
         for (int i = 0; i < D; ++i)
@@ -263,31 +347,43 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
         for (const auto &s : sites) classes.insert(parity_class(s));
         for (int m : classes) {
             std::string nm = "base" + std::to_string(m);
-            o << "      int " << nm << ";\n      {\n";
             for (int i = 0; i < D; ++i) {
                 // component of R^T e on Cartesian axis i: e[ri_i], negated if axis i is negative
                 if (fold)
-                    o << "        const int ce" << i << " = (" << m << " >> ri" << i << ") & 1;\n";
+                    o << "      const int ce" << m << "_" << i << " = (" << m << " >> ri" << i << ") & 1;\n";
                 else
-                    o << "        const int ce" << i << " = " << ((m >> i) & 1) << ";\n";
-                o << "        const int v" << i << " = cb" << i << " + " << (fold ? ("(ng" + std::to_string(i) + " ? -ce" + std::to_string(i) + " : ce" + std::to_string(i) + ")") : ("ce" + std::to_string(i))) << ";\n";
+                    o << "      const int ce" << m << "_" << i << " = " << ((m >> i) & 1) << ";\n";
+                o << "      const int v" << m << "_" << i << " = cb" << i << " + "
+                  << (fold ? ("(ng" + std::to_string(i) + " ? -ce" + std::to_string(m) + "_" + std::to_string(i) +
+                              " : ce" + std::to_string(m) + "_" + std::to_string(i) + ")")
+                           : ("ce" + std::to_string(m) + "_" + std::to_string(i)))
+                  << ";\n";
             }
-            o << "        const int par = (v0 & 1)";
-            for (int i = 1; i < D; ++i) o << " | ((v" << i << " & 1) << " << i << ")";
+            o << "      const int par" << m << " = (v" << m << "_0 & 1)";
+            for (int i = 1; i < D; ++i) o << " | ((v" << m << "_" << i << " & 1) << " << i << ")";
             o << ";\n";
-            o << "        const int cid = (int)((" << lut << "ull >> (4 * par)) & 15ull);\n";
-            o << "        " << nm << " = cid * CS + (qh0 + (v0 >> 1))";
-            if (D >= 2) o << " + ex0 * ((qh1 + (v1 >> 1))";
-            if (D == 3) o << " + ex1 * (qh2 + (v2 >> 1))";
-            if (D >= 2) o << ")";
-            o << ";\n      }\n";
-            base_of_class[m] = nm;
+            o << "      const int cid" << m << " = (int)((" << lut << "ull >> (4 * par" << m << ")) & 15ull);\n";
+            auto q = [&](int i) {
+                return i < D ? "qh" + std::to_string(i) + " + (v" + std::to_string(m) + "_" + std::to_string(i) + " >> 1)"
+                             : std::string("0");
+            };
+            if (e.brick) {
+                emit_brick_class(m, q(0), q(1), q(2), "cid" + std::to_string(m));
+            } else {
+                o << "      const int " << nm << " = cid" << m << " * CS + CU * ((" << q(0) << ")";
+                if (D >= 2) o << " + ex0 * ((" << q(1) << ")";
+                if (D == 3) o << " + ex1 * (" << q(2) << ")";
+                if (D >= 2) o << ")";
+                o << ");\n";
+                base_of_class[m] = nm;
+            }
         }
     }
     const bool pipelined = load && !declare_addr && group > 0 && depth > 0 && (int)sites.size() > group * depth;
     for (size_t j = 0; j < sites.size(); ++j) {
         const I3 &s = sites[j];
-        std::string addr = base_of_class[parity_class(s)];
+        const int m = parity_class(s);
+        std::string addr = base_of_class[m];
         if (pipelined && (int)j % group == 0 && (int)j / group >= depth) {
             // Algorithm 2: group g is fetched only once group g - depth has arrived.
             // tk is 0 for every value (NaN and +-inf convert to 0) but is computed
@@ -298,7 +394,10 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
         }
         if (pipelined && (int)j / group >= depth) addr += " + tk" + std::to_string((int)j / group);
         for (int r = 0; r < D; ++r) {
-            int h = (a == 2) ? floordiv2(s[r]) : s[r];
+            int h = hoff(s, r);
+            if (e.brick)
+                addr += " + nl" + std::to_string(m) + "_" + std::to_string(r) + "_" + (h < 0 ? "m" : "") +
+                        std::to_string(std::abs(h));
             if (h == 0) continue;
             if (h == 1) addr += " + rs" + std::to_string(r);
             else if (h == -1) addr += " - rs" + std::to_string(r);
@@ -335,17 +434,32 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             o << "        const int par = (n0 & 1)";
             for (int i = 1; i < D; ++i) o << " | ((n" << i << " & 1) << " << i << ")";
             o << ";\n        const int cid = (int)((" << lut << "ull >> (4 * par)) & 15ull);\n";
-            o << "        const int adr = cid * CS + (n0 >> 1)";
-            if (D >= 2) o << " + ex0 * ((n1 >> 1)";
-            if (D == 3) o << " + ex1 * (n2 >> 1)";
-            if (D >= 2) o << ")";
-            o << ";\n";
+            if (e.brick) {
+                o << "        const int adr = cid";
+                for (int i = 0; i < D; ++i)
+                    o << " + BA" << i << " * (n" << i << " >> 1) + BB" << i << " * ((n" << i << " >> 1) >> "
+                      << (i == 0 ? 2 : 1) << ")";
+                o << ";\n";
+            } else {
+                o << "        const int adr = cid * CS + CU * ((n0 >> 1)";
+                if (D >= 2) o << " + ex0 * ((n1 >> 1)";
+                if (D == 3) o << " + ex1 * (n2 >> 1)";
+                if (D >= 2) o << ")";
+                o << ");\n";
+            }
         } else {
-            o << "        const int adr = n0";
-            if (D >= 2) o << " + ex0 * (n1";
-            if (D == 3) o << " + ex1 * n2";
-            if (D >= 2) o << ")";
-            o << ";\n";
+            if (e.brick) {
+                o << "        const int adr = 0";
+                for (int i = 0; i < D; ++i)
+                    o << " + BA" << i << " * n" << i << " + BB" << i << " * (n" << i << " >> " << (i == 0 ? 2 : 1) << ")";
+                o << ";\n";
+            } else {
+                o << "        const int adr = CU * (n0";
+                if (D >= 2) o << " + ex0 * (n1";
+                if (D == 3) o << " + ex1 * n2";
+                if (D >= 2) o << ")";
+                o << ");\n";
+            }
         }
         if (declare_addr) o << "        ad" << j << " = ok ? adr : -1;\n";
         if (load) o << "        c" << j << " = ok ? " << e.ld << "(" << coef_expr << ", adr) : 0.0f;\n";
@@ -647,7 +761,8 @@ void emit_eval_point(Emitter &e, const Table &t, const ls_variant &var, const St
     auto &o = e.o;
     const int D = t.dim;
     o << "static __device__ __forceinline__ void " << fname << "(const LsEvalArgs& a, const long long i)\n{\n";
-    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride; (void)E1; (void)E2; (void)CS;\n";
+    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride, CU = a.cunit;"
+         " (void)E1; (void)E2; (void)CS; (void)CU;\n";
     if (grad) {
         o << "#define LS_OUT_OF_RANGE(V) { if (a.out) a.out[i] = (V);";
         for (int i = 0; i < D; ++i) o << " a.grad[(size_t)i * " << D << " + " << i << "] = (V);";
@@ -738,7 +853,8 @@ void emit_eval_kernel_reuse(Emitter &e, const Table &t, const ls_variant &var, c
     o << "extern \"C\" __global__ void __launch_bounds__(" << var.block;
     if (var.min_blocks > 0) o << ", " << var.min_blocks;
     o << ") " << kname(t, "eval") << "(const LsEvalArgs a)\n{\n";
-    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride; (void)E1; (void)E2; (void)CS;\n";
+    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride, CU = a.cunit;"
+         " (void)E1; (void)E2; (void)CS; (void)CU;\n";
     o << "  const long long nchunk = (a.n + " << T - 1 << ") / " << T << ";\n";
     o << "  const long long cstride_ = (long long)gridDim.x * blockDim.x;\n";
     o << "#define LS_OUT_OF_RANGE(V) { a.out[i] = (V); }\n";
@@ -864,13 +980,30 @@ std::vector<std::string> emit_site_weights(Emitter &e, const Table &t, const Ste
 }
 
 // Atomic adjoint: dcoef[site] += g * w_site for every stencil site of every point.
-void emit_adjoint_atomic(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach)
+// Scatter-add flavours of the point-wise adjoint.
+enum AdjFlavour { ADJ_ATOMIC, ADJ_WARPAGG, ADJ_FIXED };
+
+void emit_adjoint_atomic(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
+                         AdjFlavour fl)
 {
     auto &o = e.o;
     const int D = t.dim;
-    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block << ") " << kname(t, "adjoint_atomic")
+    // one scatter-add of value V at address variable AD
+    auto add = [&](const std::string &ad, const std::string &v) {
+        if (fl == ADJ_WARPAGG) return "ls_agg_add(a.dcoef, " + ad + ", " + v + ");";
+        if (fl == ADJ_FIXED)
+            return "if (" + ad + " >= 0) atomicAdd(a.iacc + " + ad + ", (unsigned long long)__float2ll_rn((" + v +
+                   ") * isc));";
+        return "if (" + ad + " >= 0) atomicAdd(a.dcoef + " + ad + ", " + v + ");";
+    };
+    const char *what = fl == ADJ_WARPAGG ? "adjoint_warpagg" : fl == ADJ_FIXED ? "adjoint_fixed" : "adjoint_atomic";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block << ") " << kname(t, what)
       << "(const LsAdjArgs a)\n{\n";
-    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride; (void)E1; (void)E2; (void)CS;\n";
+    // fixed point: each value is rounded to an integer multiple of 2^-s and summed
+    // exactly in int64, so the result does not depend on the order of the atomics
+    if (fl == ADJ_FIXED) o << "  const float isc = __ldg(a.iscale);\n";
+    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride, CU = a.cunit;"
+         " (void)E1; (void)E2; (void)CS; (void)CU;\n";
     o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
     o << "#define LS_OUT_OF_RANGE(V) { }\n";
     o << "  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {\n";
@@ -907,7 +1040,7 @@ void emit_adjoint_atomic(Emitter &e, const Table &t, const ls_variant &var, cons
                 o << "    { const float gw = gp * w1_" << j1 << (D > 2 ? " * w2_" + std::to_string(j2) : std::string()) << ";\n";
                 for (int j0 = 0; j0 < n0; ++j0) {
                     int j = (j2 * n1 + j1) * n0 + j0;
-                    o << "      if (ad" << j << " >= 0) atomicAdd(a.dcoef + ad" << j << ", gw * w0_" << j0 << ");\n";
+                    o << "      " << add("ad" + std::to_string(j), "gw * w0_" + std::to_string(j0)) << "\n";
                 }
                 o << "    }\n";
             }
@@ -916,7 +1049,7 @@ void emit_adjoint_atomic(Emitter &e, const Table &t, const ls_variant &var, cons
         emit_gathers(e, t, st.sites, reach, "", true, false);
         for (size_t j = 0; j < st.sites.size(); ++j) {
             if (w[j].empty()) continue;
-            o << "    if (ad" << j << " >= 0) atomicAdd(a.dcoef + ad" << j << ", gp * " << w[j] << ");\n";
+            o << "    " << add("ad" + std::to_string(j), "gp * " + w[j]) << "\n";
         }
     }
     o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
@@ -1073,14 +1206,28 @@ void emit_adjoint_gather(Emitter &e, const Table &t, const ls_variant &var, cons
     o << "  const int eb0 = a.e0 + 2 * H, eb1 = a.e1 + 2 * H, eb2 = a.e2 + 2 * H; (void)eb1; (void)eb2;\n";
     o << "  const unsigned csb = (unsigned)eb0" << (D > 1 ? " * (unsigned)eb1" : "") << (D > 2 ? " * (unsigned)eb2" : "")
       << ";\n";
-    o << "  const long long total = (long long)a.cstride * " << t.cosets.size() << ";\n";
+    // site = cj * cstride + q * cunit in either layout
+    o << "  const long long P = (long long)a.e0 * a.e1 * a.e2;\n";
+    o << "  const long long total = P * " << t.cosets.size() << ";\n";
     o << "  for (long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x; site < total;"
          " site += (long long)gridDim.x * blockDim.x) {\n";
-    o << "    const int cj = (int)(site / a.cstride);\n";
-    o << "    int rem = (int)(site - (long long)cj * a.cstride);\n";
-    o << "    const int i0 = rem % a.e0; rem /= a.e0;\n";
-    if (D > 1) o << "    const int i1 = rem % a.e1; rem /= a.e1;\n";
-    if (D > 2) o << "    const int i2 = rem;\n";
+    if (e.brick) {
+        // bricked: site = C * (brick * BV + within) + cj, within = (i2&1) 8 + (i1&1) 4 + (i0&3)
+        const int bv = D == 3 ? 16 : 8;
+        o << "    const int cj = (int)(site % " << t.cosets.size() << ");\n";
+        o << "    const int w = (int)(site / " << t.cosets.size() << ");\n";
+        o << "    const int wi = w & " << bv - 1 << ";\n";
+        o << "    int bk = w >> " << (D == 3 ? 4 : 3) << ";\n";
+        o << "    const int i0 = (bk % (a.e0 >> 2)) * 4 + (wi & 3); bk /= (a.e0 >> 2);\n";
+        if (D > 1) o << "    const int i1 = (bk % (a.e1 >> 1)) * 2 + ((wi >> 2) & 1); bk /= (a.e1 >> 1);\n";
+        if (D > 2) o << "    const int i2 = bk * 2 + (wi >> 3);\n";
+    } else {
+        o << "    const int cj = (int)((site / a.cstride) % " << t.cosets.size() << ");\n";
+        o << "    int rem = (int)((site / a.cunit) % P);\n";
+        o << "    const int i0 = rem % a.e0; rem /= a.e0;\n";
+        if (D > 1) o << "    const int i1 = rem % a.e1; rem /= a.e1;\n";
+        if (D > 2) o << "    const int i2 = rem;\n";
+    }
     // Cartesian site n
     for (int i = 0; i < D; ++i) {
         o << "    int l" << i << " = 0;\n";
@@ -1210,6 +1357,54 @@ void emit_adjoint_gather(Emitter &e, const Table &t, const ls_variant &var, cons
     o << "  }\n}\n\n";
 }
 
+// A bound on |w_j(u)| over the region of evaluation, for the fixed-point adjoint's
+// scale: sum_a |M[j][a]| prod_i R_i^{a_i} with R_i = |center_i| + the radius of
+// the region (1 for the parallelepiped [0,1)^s; half the sum of the generator's
+// column lengths for the Voronoi cell, which holds every point within that
+// distance of the site found by rounding in the lattice basis).
+double weight_bound(const Table &t)
+{
+    const int D = t.dim;
+    double rad = 1.0;
+    if (t.roe == LS_ROE_VORONOI) {
+        rad = 0.0;
+        for (int j = 0; j < D; ++j) {
+            double n2 = 0.0;
+            for (int i = 0; i < D; ++i) n2 += t.L[3 * j + i] * t.L[3 * j + i];
+            rad += 0.5 * std::sqrt(n2);
+        }
+        rad = std::max(rad, 1.0);
+    }
+    double wmax = 0.0;
+    if (!t.sep.empty()) {
+        wmax = 1.0;
+        for (const auto &ax : t.sep) {
+            const double R = rad + std::fabs(ax.center);
+            double m = 0.0;
+            for (size_t j = 0; j < ax.sites.size(); ++j) {
+                double b = 0.0, p = 1.0;
+                for (int d = 0; d <= ax.degree; ++d, p *= R) b += std::fabs(ax.coef[j * (ax.degree + 1) + d]) * p;
+                m = std::max(m, b);
+            }
+            wmax *= m;
+        }
+        return wmax;
+    }
+    for (const auto &r : t.ref) {
+        const size_t nm = r.mono.size();
+        for (size_t j = 0; j < r.sites.size(); ++j) {
+            double b = 0.0;
+            for (size_t a = 0; a < nm; ++a) {
+                double p = std::fabs(r.coef[j * nm + a]);
+                for (int i = 0; i < D; ++i) p *= std::pow(rad + std::fabs(r.center[i]), r.mono[a][i]);
+                b += p;
+            }
+            wmax = std::max(wmax, b);
+        }
+    }
+    return wmax;
+}
+
 }  // namespace
 
 Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
@@ -1217,6 +1412,7 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
     Generated g;
     Emitter e;
     e.ld = loader_name(dt);
+    e.brick = var.brick != 0;
     emit_prologue(e);
     Stencil st = union_stencil(t);
     int reach = 0;
@@ -1244,7 +1440,10 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
         emit_eval_kernel(e, t, var, st, reach, false, g.info);
     }
     emit_eval_kernel(e, t, var, st, reach, true, g.info);
-    emit_adjoint_atomic(e, t, var, st, reach);
+    emit_adjoint_atomic(e, t, var, st, reach, ADJ_ATOMIC);
+    emit_adjoint_atomic(e, t, var, st, reach, ADJ_WARPAGG);
+    emit_adjoint_atomic(e, t, var, st, reach, ADJ_FIXED);
+    g.info.wmax = weight_bound(t);
     emit_adjoint_bin(e, t, var);
     std::vector<I3> doffs = reverse_offsets(t, st);
     emit_adjoint_gather(e, t, var, st, reach, doffs);
@@ -1255,7 +1454,7 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
 }
 
 Generated generate_batch(const std::vector<const Table *> &tables, const std::vector<ls_dtype> &dts,
-                         const ls_variant &var)
+                         const std::vector<int> &bricks, const ls_variant &var)
 {
     Generated g;
     Emitter e;
@@ -1263,6 +1462,7 @@ Generated generate_batch(const std::vector<const Table *> &tables, const std::ve
     for (size_t k = 0; k < tables.size(); ++k) {
         const Table &t = *tables[k];
         e.ld = loader_name(dts[k]);
+        e.brick = bricks[k] != 0;
         Stencil st = union_stencil(t);
         int reach = 0;
         if (t.sep.empty()) {
@@ -1276,7 +1476,7 @@ Generated generate_batch(const std::vector<const Table *> &tables, const std::ve
     }
     auto &o = e.o;
     o << "struct LsBatchVol { const float* pts; float* out; const void* coef; long long n;"
-         " int e0, e1, e2, cstride, kind, pad; };\n";
+         " int e0, e1, e2, cstride, kind, cunit; };\n";
     o << "struct LsBatchItem { int vol; int pad; long long p0, p1; };\n";
     o << "struct LsBatchArgs { const LsBatchVol* vols; const LsBatchItem* items; int nitems; int pad;"
          " unsigned* counter; unsigned* status; };\n";
@@ -1302,7 +1502,7 @@ Generated generate_batch(const std::vector<const Table *> &tables, const std::ve
     o << "    const LsBatchVol v = b.vols[w.vol];\n";
     o << "    LsEvalArgs a;\n";
     o << "    a.pts = v.pts; a.out = v.out; a.grad = 0; a.coef = v.coef; a.n = v.n;\n";
-    o << "    a.e0 = v.e0; a.e1 = v.e1; a.e2 = v.e2; a.cstride = v.cstride;\n";
+    o << "    a.e0 = v.e0; a.e1 = v.e1; a.e2 = v.e2; a.cstride = v.cstride; a.cunit = v.cunit;\n";
     o << "    switch (v.kind) {\n";
     for (size_t k = 0; k < tables.size(); ++k)
         o << "    case " << k << ": for (long long i = w.p0 + threadIdx.x; i < w.p1; i += blockDim.x) ls_bpt_" << k

@@ -51,6 +51,7 @@ struct GenInfo {
     int fma_grad = 0;
     int n_reverse = 0;      // offsets between a coefficient and the ROE sites that can reach it
     int halo = 0;           // halo of the binning grid (storage units)
+    double wmax = 1.0;      // bound on |w_j(u)| over the region of evaluation
 };
 
 struct Generated {
@@ -62,15 +63,17 @@ struct Generated {
 Generated generate(const Table &t, ls_dtype coef_dtype, const ls_variant &var);
 // One persistent kernel ls_batch_eval over the point functions of several splines.
 Generated generate_batch(const std::vector<const Table *> &tables, const std::vector<ls_dtype> &dts,
-                         const ls_variant &var);
+                         const std::vector<int> &bricks, const ls_variant &var);
 
 // Kernel handles of one compiled module.
 struct Module {
     cudaLibrary_t lib = nullptr;
-    cudaKernel_t eval = nullptr, eval_grad = nullptr, adj_atomic = nullptr;
+    cudaKernel_t eval = nullptr, eval_grad = nullptr, adj_atomic = nullptr, adj_warpagg = nullptr;
+    cudaKernel_t adj_fixed = nullptr;
     cudaKernel_t roe_key = nullptr, adj_gather = nullptr, batch_eval = nullptr;
     int regs_eval = 0;
-    int blocks_per_sm_eval = 0, blocks_per_sm_grad = 0, blocks_per_sm_adj = 0;
+    int blocks_per_sm_eval = 0, blocks_per_sm_grad = 0, blocks_per_sm_adj = 0, blocks_per_sm_warpagg = 0;
+    int blocks_per_sm_fixed = 0;
     int blocks_per_sm_gather = 0;
 };
 
@@ -98,6 +101,7 @@ struct ls_volume_s {
     int64_t ext[3] = {1, 1, 1};
     int64_t coset_elems = 0;          // prod(ext)
     int64_t total_elems = 0;          // n_cosets * prod(ext)
+    int layout = LS_LAYOUT_COSET_MAJOR;
     void *coef = nullptr;
     bool owned = false;
     // staging for ls_eval_host(_multi): buffers and two streams, made on first use
@@ -106,6 +110,18 @@ struct ls_volume_s {
     cudaStream_t hs[2] = {nullptr, nullptr};
     cudaEvent_t hev[3] = {nullptr, nullptr, nullptr};
 };
+
+// Address of coefficient (coset j, per-coset linear index q) is
+// j * vol_cstride(v) + q * vol_cunit(v) in the linear layouts; the bricked
+// layout's kernels take C = vol_cunit(v) and compute the brick address.
+inline int vol_cstride(const ls_volume_s *v)
+{
+    return v->layout == LS_LAYOUT_COSET_MAJOR ? (int)v->coset_elems : 1;
+}
+inline int vol_cunit(const ls_volume_s *v)
+{
+    return v->layout == LS_LAYOUT_COSET_MAJOR ? 1 : (int)v->spline->table.cosets.size();
+}
 
 // Thread-local error message helpers (ls_api.cpp).
 ls_status ls_fail(ls_status s, const std::string &msg);

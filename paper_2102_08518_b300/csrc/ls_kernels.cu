@@ -22,10 +22,63 @@ __device__ __forceinline__ double load_any(const void *p, int dt, long long i)
     }
 }
 
-__global__ void convert_kernel(const void *src, int sdt, void *dst, int ddt, long long n)
+// Element index of (coset j, grid index q) in a coefficient layout (ls_layout):
+// 0 coset-major, 1 interleaved, 2 bricked (4 x 2 x 2 grid indices per brick,
+// 4 x 2 in 2D (e2 == 1), cosets interleaved inside, x fastest).
+__device__ __forceinline__ long long lay_index(const LayoutGeom &g, int j, int q0, int q1, int q2)
+{
+    const long long lin = q0 + (long long)g.e0 * (q1 + (long long)g.e1 * q2);
+    if (g.layout == 0) return (long long)j * g.per + lin;
+    if (g.layout == 1) return lin * g.ncos + j;
+    const int bv = g.e2 == 1 ? 8 : 16;
+    const long long bk = (q0 >> 2) + (long long)(g.e0 >> 2) * ((q1 >> 1) + (long long)(g.e1 >> 1) * (q2 >> 1));
+    const int wi = (q0 & 3) + 4 * (q1 & 1) + 8 * (q2 & 1);
+    return (bk * bv + wi) * g.ncos + j;
+}
+
+__device__ __forceinline__ void lay_decode(const LayoutGeom &g, long long i, int &j, int &q0, int &q1, int &q2)
+{
+    if (g.layout == 2) {
+        const int bv = g.e2 == 1 ? 8 : 16;
+        j = (int)(i % g.ncos);
+        const long long w = i / g.ncos;
+        const int wi = (int)(w % bv);
+        long long bk = w / bv;
+        q0 = (int)(bk % (g.e0 >> 2)) * 4 + (wi & 3);
+        bk /= (g.e0 >> 2);
+        q1 = (int)(bk % (g.e1 >> 1)) * 2 + ((wi >> 2) & 1);
+        bk /= (g.e1 >> 1);
+        q2 = (int)bk * 2 + (wi >> 3);
+        return;
+    }
+    long long r;
+    if (g.layout == 0) {
+        j = (int)(i / g.per);
+        r = i % g.per;
+    } else {
+        j = (int)(i % g.ncos);
+        r = i / g.ncos;
+    }
+    q0 = (int)(r % g.e0);
+    r /= g.e0;
+    q1 = (int)(r % g.e1);
+    q2 = (int)(r / g.e1);
+}
+
+// Source index of destination element i when the layout changes from s to d.
+__device__ __forceinline__ long long relayout_src(long long i, const LayoutGeom &s, const LayoutGeom &d)
+{
+    if (s.layout == d.layout) return i;
+    int j, q0, q1, q2;
+    lay_decode(d, i, j, q0, q1, q2);
+    return lay_index(s, j, q0, q1, q2);
+}
+
+__global__ void convert_kernel(const void *src, int sdt, void *dst, int ddt, long long n, LayoutGeom sg,
+                               LayoutGeom dg)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double v = load_any(src, sdt, i);
+        double v = load_any(src, sdt, relayout_src(i, sg, dg));
         switch (ddt) {
         case DT_F32: ((float *)dst)[i] = (float)v; break;
         case DT_BF16: ((__nv_bfloat16 *)dst)[i] = __float2bfloat16_rn((float)v); break;
@@ -35,11 +88,20 @@ __global__ void convert_kernel(const void *src, int sdt, void *dst, int ddt, lon
     }
 }
 
+template <typename T>
+__global__ void relayout_kernel(const T *src, T *dst, long long n, LayoutGeom sg, LayoutGeom dg)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[relayout_src(i, sg, dg)];
+}
+
 constexpr int kDotBlocks = 296;   // 2 per SM on 148 SMs
 constexpr int kDotThreads = 512;
 
 // Per-block FP64 partial sums in a fixed order; the last block to finish (ticket
 // counter, no waiting) adds the partials in block order and resets the counter.
+// ABS = 1 sums |a[i]| (b unused).
+template <int ABS>
 __global__ void __launch_bounds__(kDotThreads) dot_kernel(const float *a, const float *b, long long n,
                                                            double *partials, unsigned *ticket, double *result)
 {
@@ -47,7 +109,7 @@ __global__ void __launch_bounds__(kDotThreads) dot_kernel(const float *a, const 
     __shared__ bool last;
     double s = 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        s = fma((double)a[i], (double)b[i], s);
+        s = ABS ? s + fabs((double)a[i]) : fma((double)a[i], (double)b[i], s);
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -96,6 +158,29 @@ __global__ void cg_p_kernel(float *p, const float *s, long long nc, double *sc)
 }
 
 __global__ void cg_shift_gamma(double *sc) { sc[0] = sc[3]; }
+
+// Scale of the fixed-point adjoint: 2^s with s = 61 - ceil(log2(bound)), bound =
+// sum|g| * wmax >= any accumulated |value|, so every int64 sum stays below 2^62.
+__global__ void fixed_scale_kernel(const double *gsum, double wmax, float *scale, double *inv)
+{
+    const double b = *gsum * wmax;
+    int s = 0;
+    if (b > 0.0 && b < 1e300) {
+        int e = 0;
+        frexp(b, &e);                  // b < 2^e
+        s = 61 - e;
+        s = s < -126 ? -126 : (s > 126 ? 126 : s);
+    }
+    *scale = ldexpf(1.0f, s);
+    *inv = ldexp(1.0, -s);
+}
+
+__global__ void fixed_finish_kernel(const unsigned long long *acc, const double *inv, float *dcoef, long long n)
+{
+    const double iv = *inv;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dcoef[i] += (float)((double)(long long)acc[i] * iv);
+}
 
 __global__ void axpby_kernel(float a, const float *x, float b, float *y, long long n)
 {
@@ -149,20 +234,72 @@ namespace {
 
 cudaError_t convert(const void *src, int sdt, void *dst, int ddt, long long n, cudaStream_t st)
 {
+    LayoutGeom g{0, 1, n, (int)n, 1, 1};
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;
-    convert_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, sdt, dst, ddt, n);
+    convert_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, sdt, dst, ddt, n, g, g);
+    return cudaGetLastError();
+}
+
+cudaError_t convert_relayout(const void *src, int sdt, const LayoutGeom &sg, void *dst, int ddt, const LayoutGeom &dg,
+                             cudaStream_t st)
+{
+    const long long n = (long long)dg.ncos * dg.per;
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    convert_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, sdt, dst, ddt, n, sg, dg);
+    return cudaGetLastError();
+}
+
+cudaError_t relayout(const void *src, const LayoutGeom &sg, void *dst, const LayoutGeom &dg, int elem_bytes,
+                     cudaStream_t st)
+{
+    const long long n = (long long)dg.ncos * dg.per;
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    if (elem_bytes == 2)
+        relayout_kernel<<<(unsigned)blocks, 256, 0, st>>>((const uint16_t *)src, (uint16_t *)dst, n, sg, dg);
+    else if (elem_bytes == 4)
+        relayout_kernel<<<(unsigned)blocks, 256, 0, st>>>((const uint32_t *)src, (uint32_t *)dst, n, sg, dg);
+    else
+        relayout_kernel<<<(unsigned)blocks, 256, 0, st>>>((const uint64_t *)src, (uint64_t *)dst, n, sg, dg);
     return cudaGetLastError();
 }
 
 size_t dot_ws_bytes() { return kDotBlocks * sizeof(double) + 256; }
 
+size_t fixed_ws_bytes() { return dot_ws_bytes() + 256; }
+
+cudaError_t fixed_prepare(const float *g, long long n, double wmax, void *ws, float **scale, double **inv,
+                          cudaStream_t st)
+{
+    double *partials = (double *)ws;
+    unsigned *ticket = (unsigned *)((char *)ws + kDotBlocks * sizeof(double));
+    double *gsum = (double *)((char *)ws + dot_ws_bytes());
+    *scale = (float *)(gsum + 1);
+    *inv = gsum + 2;
+    cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    dot_kernel<1><<<kDotBlocks, kDotThreads, 0, st>>>(g, g, n, partials, ticket, gsum);
+    fixed_scale_kernel<<<1, 1, 0, st>>>(gsum, wmax, *scale, *inv);
+    return cudaGetLastError();
+}
+
+cudaError_t fixed_finish(const unsigned long long *acc, const double *inv, float *dcoef, long long n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    fixed_finish_kernel<<<grid_of(n), 256, 0, st>>>(acc, inv, dcoef, n);
+    return cudaGetLastError();
+}
+
 cudaError_t dot_f64_ws(const float *a, const float *b, long long n, double *result, void *ws, cudaStream_t st)
 {
     double *partials = (double *)ws;
     unsigned *ticket = (unsigned *)((char *)ws + kDotBlocks * sizeof(double));
-    dot_kernel<<<kDotBlocks, kDotThreads, 0, st>>>(a, b, n, partials, ticket, result);
+    dot_kernel<0><<<kDotBlocks, kDotThreads, 0, st>>>(a, b, n, partials, ticket, result);
     return cudaGetLastError();
 }
 

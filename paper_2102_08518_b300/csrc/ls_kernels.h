@@ -9,11 +9,33 @@ namespace lsk {
 
 // dst[i] = (dst_dtype) src[i]; dtypes as ls_dtype (F32, BF16, F16, F64), round to nearest even.
 cudaError_t convert(const void *src, int src_dt, void *dst, int dst_dt, long long n, cudaStream_t st);
+// Geometry of a coefficient layout: ls_layout, cosets, elements per coset, extents.
+struct LayoutGeom {
+    int layout;
+    int ncos;
+    long long per;
+    int e0, e1, e2;
+};
+// Conversion of all ncos * per elements from layout sg to layout dg (same
+// cosets and extents), dtypes as in convert.
+cudaError_t convert_relayout(const void *src, int src_dt, const LayoutGeom &sg, void *dst, int dst_dt,
+                             const LayoutGeom &dg, cudaStream_t st);
+// Layout change only, elements of elem_bytes (2, 4 or 8).
+cudaError_t relayout(const void *src, const LayoutGeom &sg, void *dst, const LayoutGeom &dg, int elem_bytes,
+                     cudaStream_t st);
 
 // *result = sum a[i] b[i] in FP64 (fixed reduction order: bitwise reproducible).
 // ws: >= dot_ws_bytes() bytes of device scratch.
 size_t dot_ws_bytes();
 cudaError_t dot_f64_ws(const float *a, const float *b, long long n, double *result, void *ws, cudaStream_t st);
+// Fixed-point adjoint helpers.  fixed_prepare: sum |g| in FP64 (fixed order) and
+// the power-of-two scale 2^s (*scale, FP32) and 2^-s (*inv, FP64) with
+// sum|g| * wmax * 2^s < 2^61; both pointers point into ws (fixed_ws_bytes()).
+// fixed_finish: dcoef[i] += (double)(int64)acc[i] * 2^-s.
+size_t fixed_ws_bytes();
+cudaError_t fixed_prepare(const float *g, long long n, double wmax, void *ws, float **scale, double **inv,
+                          cudaStream_t st);
+cudaError_t fixed_finish(const unsigned long long *acc, const double *inv, float *dcoef, long long n, cudaStream_t st);
 // Same with a lazily allocated per-device scratch.
 cudaError_t dot_f64(const float *a, const float *b, long long n, double *result, cudaStream_t st);
 

@@ -29,7 +29,7 @@ struct BatchVol {
     float *out;
     const void *coef;
     long long n;
-    int e0, e1, e2, cstride, kind, pad;
+    int e0, e1, e2, cstride, kind, cunit;
 };
 struct BatchItem {
     int vol;
@@ -115,21 +115,23 @@ ls_status ls_plan_create(int32_t n_vol, const ls_volume *vols, const float *cons
         int kind = (int)(it - kinds.begin());
         if (it == kinds.end()) kinds.push_back(v->spline);
         bv[k] = BatchVol{pts[k], out[k], v->coef, (long long)n[k], (int)v->ext[0], (int)v->ext[1], (int)v->ext[2],
-                         (int)v->coset_elems, kind, 0};
+                         vol_cstride(v), kind, vol_cunit(v)};
         cost[k] = 20.0 + (double)v->spline->gen.info.fma_value;
     }
     if (kinds.size() > 16) return ls_fail(LS_ERR_UNSUPPORTED, "more than 16 distinct splines in one plan");
     std::vector<const ls::Table *> tabs;
     std::vector<ls_dtype> dts;
+    std::vector<int> bricks;
     std::string tag = "ls_batch";
     for (auto *s : kinds) {
         tabs.push_back(&s->table);
         dts.push_back(s->dtype);
+        bricks.push_back(s->var.brick);
         tag += "_" + (s->table.name.empty() ? std::string("s") : s->table.name);
     }
     if (tag.size() > 120) tag = tag.substr(0, 120);
     ls_variant var{256, 1, 0, 0, 0, 0, 0};
-    ls::Generated g = ls::generate_batch(tabs, dts, var);
+    ls::Generated g = ls::generate_batch(tabs, dts, bricks, var);
     auto *p = new (std::nothrow) ls_plan_s;
     if (!p) return ls_fail(LS_ERR_OOM, "host allocation");
     std::string err;

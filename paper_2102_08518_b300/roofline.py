@@ -11,9 +11,12 @@ from __future__ import annotations
 import numpy as np
 
 
-def stencil_indices(table, ext, pts: np.ndarray) -> np.ndarray:
-    """Linear coefficient indices (n_points, n_sites) of every point's stencil;
-    -1 where a site lies outside the arrays."""
+def stencil_indices(table, ext, pts: np.ndarray, layout: str = "coset") -> np.ndarray:
+    """Linear coefficient indices (n_points, n_sites) of every point's stencil
+    in the volume layout ("coset": coset j's array after array j - 1;
+    "interleaved": the cosets' values of one grid index adjacent; "bricked":
+    4 x 2 x 2 bricks of grid indices with the cosets adjacent inside); -1
+    where a site lies outside the arrays."""
     spl = table.spline
     lat = spl.lattice
     D = lat.dim
@@ -70,14 +73,33 @@ def stencil_indices(table, ext, pts: np.ndarray) -> np.ndarray:
                 cid = np.zeros(len(nn), dtype=np.int64)
                 idx = nn
             ok = np.all((idx >= 0) & (idx < e), axis=1)
-            lin = idx[:, 0] + e[0] * (idx[:, 1] + (e[1] * idx[:, 2] if D == 3 else 0)) + cid * per
+            q = idx[:, 0] + e[0] * (idx[:, 1] + (e[1] * idx[:, 2] if D == 3 else 0))
+            C = len(lat.cosets)
+            if layout == "bricked":
+                i2 = idx[:, 2] if D == 3 else np.zeros_like(idx[:, 0])
+                bk = idx[:, 0] // 4 + (e[0] // 4) * (idx[:, 1] // 2 + (e[1] // 2) * (i2 // 2))
+                w = idx[:, 0] % 4 + 4 * (idx[:, 1] % 2) + 8 * (i2 % 2)
+                lin = (bk * (16 if D == 3 else 8) + w) * C + cid
+            elif layout == "interleaved":
+                lin = q * C + cid
+            else:
+                lin = q + cid * per
             out[np.where(m)[0], j] = np.where(ok, lin, -1)
     return out
 
 
-def distinct_sectors_per_point(table, ext, pts: np.ndarray, elem_bytes: int = 4) -> float:
-    idx = stencil_indices(table, ext, pts)
+def distinct_sectors_per_point(table, ext, pts: np.ndarray, elem_bytes: int = 4, layout: str = "coset") -> float:
+    idx = stencil_indices(table, ext, pts, layout)
     sec = np.where(idx >= 0, (idx * elem_bytes) // 32, -1)
+    sec.sort(axis=1)
+    distinct = (np.diff(sec, axis=1) != 0).sum(axis=1) + 1 - (sec[:, 0] < 0)
+    return float(distinct.mean())
+
+
+def distinct_lines_per_point(table, ext, pts: np.ndarray, elem_bytes: int = 4, layout: str = "coset") -> float:
+    """Distinct 128-byte cache lines of one point's stencil (L1 allocates lines)."""
+    idx = stencil_indices(table, ext, pts, layout)
+    sec = np.where(idx >= 0, (idx * elem_bytes) // 128, -1)
     sec.sort(axis=1)
     distinct = (np.diff(sec, axis=1) != 0).sum(axis=1) + 1 - (sec[:, 0] < 0)
     return float(distinct.mean())

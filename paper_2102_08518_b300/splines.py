@@ -20,9 +20,14 @@ _BCC4 = ((1, 1, 1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1))
 _FCC6 = ((1, 1, 0), (1, -1, 0), (1, 0, 1), (1, 0, -1), (0, 1, 1), (0, 1, -1))
 
 TRICUBIC = Spline("tricubic", CC, tuple(d for d in _E for _ in range(4)), "parallelepiped")
+# the paper's Cartesian comparison splines (Sec. 5.1): order 2 (knots at the
+# integers: region of evaluation [0,1)^3) and order 3 (knots at the half-integers:
+# the Voronoi cell [-1/2,1/2]^3 around the nearest site)
+TRILINEAR = Spline("trilinear", CC, tuple(d for d in _E for _ in range(2)), "parallelepiped")
+TRIQUADRATIC = Spline("triquadratic", CC, tuple(d for d in _E for _ in range(3)), "voronoi")
 BCC_LINEAR = Spline("bcc_linear", BCC, _BCC4, "voronoi")
 BCC_QUINTIC = Spline("bcc_quintic", BCC, _BCC4 + _BCC4, "voronoi")
 FCC6 = Spline("fcc6", FCC, _FCC6, "voronoi")
 ZP = Spline("zp", Z2, ((1, 0), (0, 1), (1, 1), (-1, 1)), "voronoi")
 
-BY_NAME = {s.name: s for s in (TRICUBIC, BCC_LINEAR, BCC_QUINTIC, FCC6, ZP)}
+BY_NAME = {s.name: s for s in (TRICUBIC, TRILINEAR, TRIQUADRATIC, BCC_LINEAR, BCC_QUINTIC, FCC6, ZP)}

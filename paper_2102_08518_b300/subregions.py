@@ -333,7 +333,7 @@ class TableBuilder:
             base = _parallelepiped_constraints(spl.lattice)
         fold = "none"
         cons = list(base)
-        if spl.roe == "voronoi":
+        if spl.roe == "voronoi" and not self._axis_aligned():
             if not _symmetric_under_signed_perms(spl):
                 raise NotImplementedError("Voronoi ROE without full signed-permutation symmetry")
             fold = "hyperoctahedral"
@@ -416,12 +416,23 @@ class TableBuilder:
         table.separable = self._separable()
         return table
 
+    def _axis_aligned(self) -> bool:
+        """Every direction is a unit coordinate vector on the Cartesian grid."""
+        spl = self.spl
+        if spl.lattice.scale != 1 or len(spl.lattice.cosets) != 1:
+            return False
+        return all(sum(1 for v in d if v != 0) == 1 and sum(abs(v) for v in d) == 1 for d in spl.dirs)
+
     def _separable(self) -> Optional[List[Axis1D]]:
-        """Per-axis 1D tables when every direction is a coordinate axis (parallelepiped ROE)."""
+        """Per-axis 1D tables when every direction is a coordinate axis: the
+        region of evaluation is [0,1)^s (parallelepiped, centre 1/2) or the
+        Voronoi cube [-1/2,1/2]^s (centre 0); the 1D factor must be a single
+        polynomial piece there."""
         spl = self.spl
         s = self.s
-        if spl.roe != "parallelepiped" or spl.lattice.scale != 1 or len(spl.lattice.cosets) != 1:
+        if not self._axis_aligned():
             return None
+        cen = Fraction(1, 2) if spl.roe == "parallelepiped" else Fraction(0)
         axes = []
         for i in range(s):
             mult = 0
@@ -435,7 +446,11 @@ class TableBuilder:
                 return None
             bp = BoxPieces()
             half = Fraction(mult, 2)
-            ystar = Fraction(1, 2) + Fraction(1, 1009)
+            # knots of the centred factor lie at z - half - n = integers: inside the
+            # region only at its boundary when mult is even (parallelepiped) or odd (Voronoi)
+            if (mult % 2 == 0) != (spl.roe == "parallelepiped"):
+                return None
+            ystar = cen + Fraction(1, 1009)
             sites, weights = [], []
             for n in range(-mult, mult + 1):
                 z = (ystar - n + half,)
@@ -445,8 +460,8 @@ class TableBuilder:
                 if pc.is_zero():
                     continue
                 sites.append(n)
-                weights.append(pc.shift([half - n]).shift([Fraction(1, 2)]))
-            axes.append(Axis1D(sites=sites, center=Fraction(1, 2), weights=weights, degree=mult - 1))
+                weights.append(pc.shift([half - n]).shift([cen]))
+            axes.append(Axis1D(sites=sites, center=cen, weights=weights, degree=mult - 1))
         return axes
 
 

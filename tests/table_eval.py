@@ -62,3 +62,30 @@ def eval_table(table, coef, ext, pts):
             f += flat[lin] * w.evalf(u)
         out[q] = f
     return out
+
+
+def eval_separable(table, coef, ext, pts):
+    """f at pts from the per-axis factors of a tensor-product table (the form the
+    generated kernels evaluate): product of 1D weights in u_i = y_i - centre."""
+    spl = table.spline
+    D = spl.lattice.dim
+    flat = np.asarray(coef, dtype=np.float64).ravel()
+    e = list(ext) + [1] * (3 - len(ext))
+    out = np.zeros(len(pts))
+    for q, x in enumerate(np.asarray(pts, dtype=np.float64)):
+        k = _roe(table, x)
+        y = x - k
+        ws = []
+        for i, ax in enumerate(table.separable):
+            u = y[i] - float(ax.center)
+            ws.append([(s, w.evalf([u])) for s, w in zip(ax.sites, ax.weights)])
+        f = 0.0
+        for combo in np.ndindex(*[len(w) for w in ws]):
+            n = [int(k[i]) + ws[i][combo[i]][0] for i in range(D)]
+            if any(n[i] < 0 or n[i] >= e[i] for i in range(D)):
+                continue
+            wt = np.prod([ws[i][combo[i]][1] for i in range(D)])
+            lin = n[0] + e[0] * (n[1] + (e[1] * n[2] if D == 3 else 0))
+            f += flat[lin] * wt
+        out[q] = f
+    return out

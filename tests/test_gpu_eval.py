@@ -15,10 +15,12 @@ from oracle import specs as ospecs
 pytestmark = pytest.mark.gpu
 
 TOL = 2e-6
-ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_linear": ospecs.bcc_linear,
-               "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6, "zp": ospecs.zp2d}
-SMALL_EXT = {"tricubic": (12, 11, 10), "bcc_linear": (7, 6, 8), "bcc_quintic": (8, 7, 6),
-             "fcc6": (7, 8, 6), "zp": (13, 11)}
+ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
+               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6,
+               "zp": ospecs.zp2d}
+SMALL_EXT = {"tricubic": (12, 11, 10), "trilinear": (9, 12, 10), "triquadratic": (11, 9, 12),
+             "bcc_linear": (7, 6, 8), "bcc_quintic": (8, 7, 6), "fcc6": (7, 8, 6), "zp": (13, 11)}
+ALL_NAMES = ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "fcc6", "zp"]
 _SPLINES = {}
 
 
@@ -49,7 +51,7 @@ def gpu_eval(vol, pts_np):
     return out.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
+@pytest.mark.parametrize("name", ALL_NAMES)
 @pytest.mark.parametrize("n", [1, 31, 4133])
 def test_small_volume_every_point(name, n):
     """All points, including beyond the arrays (zero extension, checked gathers)."""
@@ -63,7 +65,7 @@ def test_small_volume_every_point(name, n):
     assert np.max(np.abs(got - want)) <= TOL * np.abs(coef).max()
 
 
-@pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6"])
+@pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "fcc6"])
 def test_special_points(name):
     """Lattice sites, half-integers, mirror and BSP planes, and the edges."""
     lat = workloads.SPLINE_LATTICE[name]
@@ -161,7 +163,7 @@ def test_fcc_256_box_value_and_gradient():
 # gradient and adjoint on small volumes
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
+@pytest.mark.parametrize("name", ALL_NAMES)
 def test_gradient_matches_oracle(name):
     lat = workloads.SPLINE_LATTICE[name]
     ext = SMALL_EXT[name]
@@ -175,7 +177,7 @@ def test_gradient_matches_oracle(name):
     f, g = oracle.eval_sum_grad(spec, coef.astype(np.float64).ravel(), pts.astype(np.float64))
     assert np.max(np.abs(val.cpu().numpy() - f)) <= TOL * np.abs(coef).max()
     gg = grad.cpu().numpy()
-    if name == "bcc_linear":
+    if name in ("bcc_linear", "trilinear"):
         # C0 spline: the gradient jumps across knot planes; compare off them
         ok = np.ones(len(pts), bool)
         h = 1e-4
@@ -190,8 +192,9 @@ def test_gradient_matches_oracle(name):
     assert np.max(np.abs(gg - g)) <= 1e-5 * np.abs(coef).max()
 
 
-@pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
-def test_adjoint_atomic_matches_oracle(name):
+@pytest.mark.parametrize("warp", [False, True])
+@pytest.mark.parametrize("name", ALL_NAMES)
+def test_adjoint_atomic_matches_oracle(name, warp):
     lat = workloads.SPLINE_LATTICE[name]
     ext = SMALL_EXT[name]
     lo, hi = workloads.bounding_box(lat, ext)
@@ -199,7 +202,7 @@ def test_adjoint_atomic_matches_oracle(name):
     g = np.random.default_rng(32).normal(size=3000).astype(np.float32)
     coef = workloads.coef_uniform(lat, ext, seed=33)
     vol = volume(name, ext, coef)
-    dc = vol.adjoint(torch.from_numpy(pts).cuda(), torch.from_numpy(g).cuda())
+    dc = vol.adjoint(torch.from_numpy(pts).cuda(), torch.from_numpy(g).cuda(), warp_aggregated=warp)
     torch.cuda.synchronize()
     spec = ORACLE_SPEC[name]().with_extent(ext)
     want = oracle.adjoint(spec, pts.astype(np.float64), g.astype(np.float64))
@@ -292,3 +295,31 @@ def test_centroid_expansion_variant(name):
     got = gpu_eval(vol, pts)
     want = oracle_eval(name, ext, coef, pts)
     assert np.max(np.abs(got - want)) <= TOL * np.abs(coef).max()
+
+
+@pytest.mark.parametrize("name", ["tricubic", "bcc_quintic", "fcc6", "zp"])
+def test_warp_aggregated_adjoint_with_shared_sites(name):
+    """Points in clusters of 1..40 copies of a few positions (plus edge points), so
+    that lanes of one warp hit the same sites in groups of every size up to 32:
+    the shuffle reduction inside the groups must give the oracle's sums."""
+    lat = workloads.SPLINE_LATTICE[name]
+    ext = SMALL_EXT[name]
+    lo, hi = workloads.bounding_box(lat, ext)
+    rng = np.random.default_rng(91)
+    base = workloads.points_uniform(60, lo - 1.0, hi + 1.0, seed=92)
+    reps = rng.integers(1, 41, size=len(base))
+    pts = np.repeat(base, reps, axis=0)
+    pts[::5] += rng.uniform(-0.01, 0.01, pts[::5].shape).astype(np.float32)
+    g = rng.normal(size=len(pts)).astype(np.float32)
+    g[::11] = 0.0
+    coef = workloads.coef_uniform(lat, ext, seed=93)
+    vol = volume(name, ext, coef)
+    p, gg = torch.from_numpy(pts).cuda(), torch.from_numpy(g).cuda()
+    dw = vol.adjoint(p, gg, warp_aggregated=True)
+    da = vol.adjoint(p, gg)
+    torch.cuda.synchronize()
+    spec = ORACLE_SPEC[name]().with_extent(ext)
+    want = oracle.adjoint(spec, pts.astype(np.float64), g.astype(np.float64))
+    scale = max(1.0, np.abs(want).max())
+    assert np.max(np.abs(dw.cpu().numpy() - want)) <= 2e-5 * scale
+    assert np.max(np.abs(da.cpu().numpy() - want)) <= 2e-5 * scale

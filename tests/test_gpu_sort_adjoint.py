@@ -9,10 +9,11 @@ from oracle import specs as ospecs
 
 pytestmark = pytest.mark.gpu
 
-ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_linear": ospecs.bcc_linear,
-               "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6, "zp": ospecs.zp2d}
-SMALL_EXT = {"tricubic": (12, 11, 10), "bcc_linear": (7, 6, 8), "bcc_quintic": (8, 7, 6),
-             "fcc6": (7, 8, 6), "zp": (13, 11)}
+ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
+               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6,
+               "zp": ospecs.zp2d}
+SMALL_EXT = {"tricubic": (12, 11, 10), "trilinear": (9, 12, 10), "triquadratic": (11, 9, 12),
+             "bcc_linear": (7, 6, 8), "bcc_quintic": (8, 7, 6), "fcc6": (7, 8, 6), "zp": (13, 11)}
 
 
 def _expected_morton(pts, origin, cell):
@@ -64,7 +65,7 @@ def _vol(name, ext, coef):
     return Volume(Spline(name, "f32"), ext, torch.from_numpy(coef).cuda())
 
 
-@pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
+@pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
 def test_deterministic_adjoint_matches_oracle_and_is_bitwise_stable(name):
     lat = workloads.SPLINE_LATTICE[name]
     ext = SMALL_EXT[name]
@@ -116,3 +117,49 @@ def test_deterministic_adjoint_large_and_accumulating():
     spec = ORACLE_SPEC[name]().with_extent(ext)
     want = oracle.adjoint(spec, pts[sub].astype(np.float64), g[sub].astype(np.float64))
     assert np.max(np.abs(ds.cpu().numpy() - want)) <= 2e-5 * max(1.0, np.abs(want).max())
+
+
+@pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
+def test_fixed_point_adjoint_is_bitwise_stable_and_matches_oracle(name):
+    """Integer atomics on values rounded to multiples of 2^-s: the same bits on
+    every run and for a shuffled point order, and the oracle's sums."""
+    lat = workloads.SPLINE_LATTICE[name]
+    ext = SMALL_EXT[name]
+    lo, hi = workloads.bounding_box(lat, ext)
+    n = 6000
+    pts = workloads.points_uniform(n, lo - 2.0, hi + 2.0, seed=151)
+    g = np.random.default_rng(152).normal(size=n).astype(np.float32)
+    coef = workloads.coef_uniform(lat, ext, seed=153)
+    vol = _vol(name, ext, coef)
+    p, gg = torch.from_numpy(pts).cuda(), torch.from_numpy(g).cuda()
+    d1 = vol.adjoint(p, gg, deterministic="fixed")
+    d2 = vol.adjoint(p, gg, deterministic="fixed")
+    perm = torch.from_numpy(np.random.default_rng(154).permutation(n)).cuda()
+    d3 = vol.adjoint(p[perm].contiguous(), gg[perm].contiguous(), deterministic="fixed")
+    torch.cuda.synchronize()
+    assert torch.equal(d1, d2) and torch.equal(d1, d3)
+    spec = ORACLE_SPEC[name]().with_extent(ext)
+    want = oracle.adjoint(spec, pts.astype(np.float64), g.astype(np.float64))
+    assert np.max(np.abs(d1.cpu().numpy() - want)) <= 2e-5 * max(1.0, np.abs(want).max())
+
+
+@pytest.mark.parametrize("gscale", [1e-30, 1e-6, 1.0, 1e8, 1e25])
+def test_fixed_point_adjoint_scale_follows_gout(gscale):
+    """The power-of-two scale adapts to sum|g|: the relative error stays at the
+    FP32 level for tiny and huge gradients, and g = 0 adds nothing."""
+    name, ext = "bcc_quintic", SMALL_EXT["bcc_quintic"]
+    lo, hi = workloads.bounding_box("bcc", ext)
+    n = 3000
+    pts = workloads.points_uniform(n, lo, hi, seed=161)
+    g = (np.random.default_rng(162).normal(size=n) * gscale).astype(np.float32)
+    vol = _vol(name, ext, workloads.coef_uniform("bcc", ext, seed=163))
+    p = torch.from_numpy(pts).cuda()
+    base = torch.full((vol.n_coef,), 0.25, device="cuda")
+    d = vol.adjoint(p, torch.from_numpy(g).cuda(), dcoef=base.clone() * gscale, deterministic="fixed")
+    z = vol.adjoint(p, torch.zeros(n, device="cuda"), dcoef=base.clone(), deterministic="fixed")
+    torch.cuda.synchronize()
+    assert torch.equal(z, base)
+    spec = ORACLE_SPEC[name]().with_extent(ext)
+    want = oracle.adjoint(spec, pts.astype(np.float64), g.astype(np.float64)) + 0.25 * gscale
+    got = d.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - want)) <= 2e-5 * np.abs(want).max()

@@ -59,6 +59,30 @@ def test_centred_cubic_bspline_values():
     assert np.max(np.abs(got - want)) < 1e-11
 
 
+def _hat(t):
+    """Centred linear B-spline (order 2)."""
+    return np.maximum(0.0, 1.0 - np.abs(t))
+
+
+def _beta2(t):
+    """Centred quadratic B-spline (order 3): 3/4 - t^2 on |t| <= 1/2,
+    (3/2 - |t|)^2 / 2 on 1/2 <= |t| <= 3/2, 0 beyond."""
+    a = np.abs(t)
+    return np.where(a <= 0.5, 0.75 - a * a, np.where(a <= 1.5, 0.5 * (1.5 - a) ** 2, 0.0))
+
+
+@pytest.mark.parametrize("name,factor", [("trilinear", _hat), ("triquadratic", _beta2)])
+def test_trilinear_and_triquadratic_are_products_of_textbook_bsplines(name, factor):
+    """The recurrence with each axis repeated 2 or 3 times equals the product of
+    the closed-form centred B-splines of order 2 or 3 (incl. beta2(0) = 3/4)."""
+    rng = np.random.default_rng(2)
+    y = rng.uniform(-1.8, 1.8, (400, 3))
+    y[:5] = [[0, 0, 0], [0.5, 0, 0], [1, 1, 0], [-0.25, 0.75, 1.25], [1.5, 0, 0]]
+    got = oracle.phi(specs.ALL_3D[name](), y)
+    want = np.prod(factor(y), axis=1)
+    assert np.max(np.abs(got - want)) < 1e-13
+
+
 def test_tricubic_recurrence_matches_closed_form():
     rng = np.random.default_rng(1)
     y = rng.uniform(-2.2, 2.2, (300, 3))
@@ -193,7 +217,7 @@ def test_linear_reproduction(name):
     assert np.max(np.abs(v - (pts @ a + b))) < 1e-11
 
 
-@pytest.mark.parametrize("name", ["tricubic", "bcc_quintic", "fcc6"])
+@pytest.mark.parametrize("name", ["tricubic", "triquadratic", "bcc_quintic", "fcc6"])
 def test_quadratic_reproduction_with_moment_defect(name):
     spec = _small(ALL[name]())
     sites = _sites_and_grid(spec)
@@ -234,12 +258,13 @@ def test_cubic_reproduction_with_moment_defect(name):
     assert np.max(np.abs(v - want)) < 1e-9
 
 
-def test_bcc_linear_does_not_reproduce_quadratics():
+@pytest.mark.parametrize("name", ["bcc_linear", "trilinear"])
+def test_second_order_splines_do_not_reproduce_quadratics(name):
     """Sanity of the previous tests: a second-order spline must fail them."""
-    spec = _small(specs.bcc_linear())
+    spec = _small(specs.ALL_3D[name]())
     sites = _sites_and_grid(spec)
     rng = np.random.default_rng(5)
-    pts = _interior_pts(rng, 50, 4.5, 8.5)
+    pts = _interior_pts(rng, 50, 4.5, 6.5 if spec.scale == 1 else 8.5)
     v = oracle.eval_sum(spec, sites[:, 0] ** 2, pts)
     want = pts[:, 0] ** 2 + _moment_defect(spec.dirs, np.diag([2.0, 0, 0]))
     assert np.max(np.abs(v - want)) > 1e-3
@@ -278,7 +303,9 @@ def test_support_and_positivity(name):
     normals = np.array(normals)
     bound = 0.5 * np.abs(normals @ X.T).sum(axis=1)
     rng = np.random.default_rng(10)
-    y = rng.uniform(-4.5, 4.5, (3000, 3))
+    reach = float(np.max(bound / np.linalg.norm(normals, axis=1)))     # farthest facet of the zonotope
+    L = min(4.5, 1.6 * reach)
+    y = rng.uniform(-L, L, (3000, 3))
     margin = np.min(bound[None, :] - np.abs(y @ normals.T), axis=1) / np.linalg.norm(normals, axis=1).max()
     v = oracle.phi(spec, y)
     inside = margin > 1e-6
@@ -288,13 +315,13 @@ def test_support_and_positivity(name):
     assert np.all(v[outside] == 0.0)
 
 
-@pytest.mark.parametrize("name,det", [("tricubic", 1.0), ("bcc_linear", 4.0),
-                                      ("bcc_quintic", 4.0), ("fcc6", 2.0)])
+@pytest.mark.parametrize("name,det", [("tricubic", 1.0), ("trilinear", 1.0), ("triquadratic", 1.0),
+                                      ("bcc_linear", 4.0), ("bcc_quintic", 4.0), ("fcc6", 2.0)])
 def test_integral_equals_lattice_density(name, det):
     """integral phi = |det L| (midpoint rule on a fine grid)."""
     spec = specs.ALL_3D[name]()
     h = 1.0 / 8.0 if name != "bcc_quintic" else 1.0 / 6.0
-    R = 2.0 if name in ("tricubic", "bcc_linear", "fcc6") else 4.0
+    R = 2.0 if name in ("tricubic", "trilinear", "triquadratic", "bcc_linear", "fcc6") else 4.0
     g = np.arange(-R + h / 2, R, h)
     Y = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
     # shift by a generic offset so that no sample sits on a knot plane

@@ -11,11 +11,12 @@ import workloads
 from oracle import specs as ospecs
 from paper_2102_08518_b300 import splines
 from paper_2102_08518_b300.api import table
-from tests.table_eval import eval_table
+from tests.table_eval import eval_separable, eval_table
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_linear": ospecs.bcc_linear,
-               "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6, "zp": ospecs.zp2d}
+ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
+               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6,
+               "zp": ospecs.zp2d}
 
 
 def test_zp_table_reproduces_fig1():
@@ -37,7 +38,7 @@ def test_zp_table_reproduces_fig1():
     assert got == want
 
 
-@pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
+@pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
 def test_table_weights_partition_unity_exactly(name):
     t = table(name)
     for reg in t.regions:
@@ -57,9 +58,12 @@ def test_structural_facts_from_the_paper():
     assert len(table("bcc_quintic").regions) == 1 and len(table("bcc_linear").regions) == 1
     sep = table("tricubic").separable
     assert sep is not None and [len(a.sites) for a in sep] == [4, 4, 4]
+    # the Cartesian comparison splines: trilinear 8 lookups (Sec. 5.1, order 2), triquadratic 27
+    assert len(table("trilinear").regions[0].sites) == 8
+    assert len(table("triquadratic").regions[0].sites) == 27
 
 
-@pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
+@pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
 def test_table_matches_oracle_by_brute_force(name):
     """Algorithm 1 over the table in FP64 vs the oracle's naive sum, tiny grids,
     points everywhere (inside, near and beyond the edges)."""
@@ -93,3 +97,19 @@ def test_table_matches_oracle_on_symmetry_planes():
         want = oracle.eval_sum(spec, coef.ravel(), base)
         got = eval_table(t, coef, ext, base)
         assert np.max(np.abs(got - want)) < 1e-11, name
+
+
+@pytest.mark.parametrize("name,nsites", [("tricubic", 4), ("trilinear", 2), ("triquadratic", 3)])
+def test_separable_factors_match_oracle(name, nsites):
+    """The per-axis factors the kernels evaluate (region [0,1)^3 for even order,
+    the Voronoi cube around the nearest site for the quadratic) against the naive sum."""
+    t = table(name)
+    assert t.separable is not None and [len(a.sites) for a in t.separable] == [nsites] * 3
+    assert t.spline.roe == ("voronoi" if nsites == 3 else "parallelepiped")
+    ext = (6, 6, 6)
+    coef = workloads.coef_uniform("cc", ext, seed=13)
+    pts = workloads.points_uniform(200, [-1.5] * 3, [6.5] * 3, seed=14).astype(np.float64)
+    pts[:20] = np.round(pts[:20] * 2) / 2                      # on the knot planes
+    spec = ORACLE_SPEC[name]().with_extent(ext)
+    want = oracle.eval_sum(spec, coef.ravel(), pts)
+    assert np.max(np.abs(eval_separable(t, coef, ext, pts) - want)) < 1e-12

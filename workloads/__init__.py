@@ -22,9 +22,11 @@ LATTICES = {
     "fcc": (3, 2, ((0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 1, 1))),
     "z2": (2, 1, ((0, 0),)),
 }
-SPLINE_LATTICE = {"tricubic": "cc", "bcc_linear": "bcc", "bcc_quintic": "bcc", "fcc6": "fcc", "zp": "z2"}
+SPLINE_LATTICE = {"tricubic": "cc", "trilinear": "cc", "triquadratic": "cc", "bcc_linear": "bcc",
+                  "bcc_quintic": "bcc", "fcc6": "fcc", "zp": "z2"}
 # half-width of the support box along an axis: 1/2 sum_xi |xi_i| (input margins only)
-SUPPORT_HALF = {"tricubic": 2.0, "bcc_linear": 2.0, "bcc_quintic": 4.0, "fcc6": 2.0, "zp": 1.5}
+SUPPORT_HALF = {"tricubic": 2.0, "trilinear": 1.0, "triquadratic": 1.5, "bcc_linear": 2.0, "bcc_quintic": 4.0,
+                "fcc6": 2.0, "zp": 1.5}
 
 
 def site_coords(lattice: str, ext: Sequence[int]) -> np.ndarray:
