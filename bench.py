@@ -362,7 +362,7 @@ def run_gpu(args):
         extras = {}
         extras["layouts"] = extra_layouts(torch, dev, coef_cm, pts, outs, per_case)
         for name, fn in (("fwd_bwd", extra_fwd_bwd), ("fcc_sorted", extra_fcc), ("batched", extra_batched),
-                         ("cg", extra_cg)):
+                         ("cg", extra_cg), ("paper_orders", extra_paper_orders)):
             try:
                 extras[name] = fn(torch, dev, vols, pts, outs)
             except Exception as ex:       # an extra must not lose the headline line
@@ -529,6 +529,43 @@ def extra_batched(torch, dev, vols, pts, outs):
                    "items": info["n_items"], "max_abs_err_vs_f32_storage": round(err, 7),
                    "storage_bound_u_cmax": 2.0 ** -8 if dt == "bf16" else 2.0 ** -11}
         del plan, vd, cd
+    return res
+
+
+def extra_paper_orders(torch, dev, vols, pts, outs):
+    """The paper's per-order comparisons (Sec. 5.1: order 2 trilinear vs BCC
+    linear, order 3 triquadratic vs FCC six-direction, order 4 tricubic vs the
+    BCC quintic) on its equal-memory grids: CC 128^3, BCC 202^3 (2 x 101^3 sites),
+    FCC 161^3 (4 x 81^3 sites); 2^24 uniform points in each inner box, FP32,
+    interleaved cosets, the default kernel variant."""
+    from paper_2102_08518_b300.api import Spline, Volume, relayout
+    grids = {"trilinear": ("cc", (128,) * 3), "triquadratic": ("cc", (128,) * 3), "tricubic": ("cc", (128,) * 3),
+             "bcc_linear": ("bcc", (101,) * 3), "bcc_quintic": ("bcc", (101,) * 3), "fcc6": ("fcc", (81,) * 3)}
+    n = 1 << 24
+    res = {"workload": "2^24 uniform points per spline; CC 128^3, BCC 2x101^3, FCC 4x81^3 coefficients U[-1,1]"}
+    out = torch.empty(n, device=dev)
+    for name, (lat, ext) in grids.items():
+        ncos = len(workloads.LATTICES[lat][2])
+        c = relayout(workloads.coef_uniform_torch(lat, ext, seed=1), ncos, ext, to="interleaved")
+        lo, hi = workloads.inner_box(name, ext)
+        p = workloads.points_uniform_torch(n, lo, hi, seed=2)
+        sp = Spline(name, "f32")
+        vol = Volume(sp, ext, c, layout="interleaved")
+        ms = time_ms(torch, lambda: vol.eval(p, out))
+        info = sp.info()
+        res[name] = {"gpoints_s": round(n / ms / 1e6, 3), "ms": round(ms, 4), "sites": info["n_sites"],
+                     "fma_per_point": info["fma_value"]}
+        if all(e % b == 0 for e, b in zip(ext, (4, 2, 2))):
+            # the same volume in 4x2x2 bricks (fewer cache lines per stencil)
+            cb = relayout(c, ncos, ext, to="bricked", src="interleaved")
+            vb = Volume(Spline(name, "f32", brick=1), ext, cb, layout="bricked")
+            msb = time_ms(torch, lambda: vb.eval(p, out))
+            res[name]["bricked_gpoints_s"] = round(n / msb / 1e6, 3)
+            del cb, vb
+        del c, p, vol
+    res["order2_bcc_linear_vs_trilinear"] = round(res["bcc_linear"]["gpoints_s"] / res["trilinear"]["gpoints_s"], 3)
+    res["order3_fcc6_vs_triquadratic"] = round(res["fcc6"]["gpoints_s"] / res["triquadratic"]["gpoints_s"], 3)
+    res["order4_bcc_quintic_vs_tricubic"] = round(res["bcc_quintic"]["gpoints_s"] / res["tricubic"]["gpoints_s"], 3)
     return res
 
 

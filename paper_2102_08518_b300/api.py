@@ -423,11 +423,14 @@ DEFAULT_CANDIDATES = (
 
 
 # the variants that won somewhere in the full sweep (block size and occupancy;
-# limiting gathers in flight never won on B300)
+# limiting gathers in flight never won on B300), plus low-occupancy launches
+# (4-8 warps per SM) that keep fewer stencils competing for L1
 TUNE_CANDIDATES_SMALL = tuple([dict(block=256, blocks_per_sm=b, expansion=x) for b in (0, 2, 3) for x in
                                ("sparse", "centroid")] +
                               [dict(block=512, expansion=x) for x in ("sparse", "centroid")] +
-                              [dict(block=384, expansion=x) for x in ("sparse", "centroid")])
+                              [dict(block=384, expansion=x) for x in ("sparse", "centroid")] +
+                              [dict(block=128, blocks_per_sm=b) for b in (1, 2, 4)] +
+                              [dict(block=256, blocks_per_sm=1)])
 
 
 def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_sets: Sequence[torch.Tensor],
