@@ -361,8 +361,8 @@ def run_gpu(args):
     if not args.no_extras:
         extras = {}
         extras["layouts"] = extra_layouts(torch, dev, coef_cm, pts, outs, per_case)
-        for name, fn in (("fwd_bwd", extra_fwd_bwd), ("fcc_sorted", extra_fcc), ("batched", extra_batched),
-                         ("cg", extra_cg), ("paper_orders", extra_paper_orders)):
+        for name, fn in (("tricubic_64", extra_tricubic_64), ("fwd_bwd", extra_fwd_bwd), ("fcc_sorted", extra_fcc),
+                         ("batched", extra_batched), ("cg", extra_cg), ("paper_orders", extra_paper_orders)):
             try:
                 extras[name] = fn(torch, dev, vols, pts, outs)
             except Exception as ex:       # an extra must not lose the headline line
@@ -529,6 +529,36 @@ def extra_batched(torch, dev, vols, pts, outs):
                    "items": info["n_items"], "max_abs_err_vs_f32_storage": round(err, 7),
                    "storage_bound_u_cmax": 2.0 ** -8 if dt == "bf16" else 2.0 ** -11}
         del plan, vd, cd
+    return res
+
+
+def extra_tricubic_64(torch, dev, vols, pts, outs):
+    """Tricubic on a 64^3 volume (U[-1,1], seed 0) at 2^18 points U([2,61]^3):
+    100 launches replayed from one CUDA graph (the kernel takes microseconds),
+    one coefficient array and the bricked layout."""
+    from paper_2102_08518_b300.api import Spline, Volume, relayout
+    ext = (64, 64, 64)
+    n = 1 << 18
+    c = torch.from_numpy(workloads.coef_uniform("cc", ext, seed=0)).to(dev)
+    p = torch.from_numpy(workloads.points_uniform(n, [2, 2, 2], [61, 61, 61], seed=0)).to(dev)
+    out = torch.empty(n, device=dev)
+    res = {"workload": "tricubic 64^3 (1 MiB), 2^18 uniform points in [2,61]^3, 100 launches per graph replay"}
+    for lay, vol in (("array", Volume(Spline("tricubic", "f32"), ext, c)),
+                     ("bricked", Volume(Spline("tricubic", "f32", brick=1), ext, relayout(c, 1, ext, to="bricked"),
+                                        layout="bricked"))):
+        vol.eval(p, out)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            vol.eval(p, out, stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(100):
+                vol.eval(p, out, stream=torch.cuda.current_stream())
+        ms = time_ms(torch, g.replay, reps=5) / 100
+        res[lay] = {"gpoints_s": round(n / ms / 1e6, 3), "us_per_launch": round(ms * 1e3, 2)}
     return res
 
 

@@ -167,6 +167,9 @@ typedef struct {
                                           without taking L1 away (no recompilation) */
     int32_t brick;                     /* 1: the kernels address LS_LAYOUT_BRICKED volumes (and only
                                           those); 0: the linear layouts (coset-major, interleaved) */
+    int32_t pipeline;                  /* 1: the value kernel issues the gathers of a thread's next
+                                          point before evaluating the current one (software
+                                          pipelining; non-separable tables; pts_per_thread ignored) */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */

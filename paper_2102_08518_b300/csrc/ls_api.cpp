@@ -247,6 +247,7 @@ ls_variant default_variant(const ls_variant *v)
         r.depth = v->depth > 0 ? v->depth : 0;
         r.blocks_per_sm = v->blocks_per_sm > 0 ? v->blocks_per_sm : 0;
         r.brick = v->brick ? 1 : 0;
+        r.pipeline = v->pipeline ? 1 : 0;
     }
     return r;
 }

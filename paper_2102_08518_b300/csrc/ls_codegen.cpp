@@ -923,6 +923,85 @@ void emit_eval_kernel(Emitter &e, const Table &t, const ls_variant &var, const S
     else info.fma_value = e.fma - fma0;
 }
 
+// Software-pipelined value kernel: every thread keeps the gathers of its next
+// point in flight while it evaluates the polynomial of the current one (two
+// point states P and Q, alternating), so a few warps per SM keep the L1 miss
+// path busy while fewer stencils compete for L1.  Stage A: point load, region
+// of evaluation, sub-region, gathers; stage B: polynomial and store.
+void emit_eval_kernel_pipelined(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
+                                GenInfo &info)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    const size_t NS = st.sites.size();
+    const size_t K = t.ref.size();
+    auto stage_a = [&](const std::string &S, const std::string &idx) {
+        o << "  {\n    const long long i = " << idx << ";\n";
+        o << "    " << S << "_sp = 0;\n";
+        o << "#define LS_OUT_OF_RANGE(V) { " << S << "_sp = 1; " << S << "_sv = (V); }\n";
+        o << "    do {\n";
+        emit_point_load(e, t, "break");
+        emit_classify(e, t);
+        emit_gathers(e, t, st.sites, reach, "a.coef", false, true, 0, 0);
+        for (size_t j = 0; j < NS; ++j) o << "    " << S << "_c" << j << " = c" << j << ";\n";
+        for (int i = 0; i < D; ++i) o << "    " << S << "_a" << i << " = a" << i << ";\n";
+        o << "    " << S << "_psi = psi;\n";
+        o << "    } while (0);\n#undef LS_OUT_OF_RANGE\n  }\n";
+    };
+    auto stage_b = [&](const std::string &S, const std::string &idx) {
+        o << "  {\n";
+        for (size_t j = 0; j < NS; ++j) o << "    const float c" << j << " = " << S << "_c" << j << ";\n";
+        for (int i = 0; i < D; ++i) o << "    const float a" << i << " = " << S << "_a" << i << ";\n";
+        o << "    const int psi = " << S << "_psi; (void)psi;\n";
+        std::string fv;
+        if (K > 1 && var.branchy) {
+            o << "    float fsel = 0.0f;\n";
+            for (size_t k = 0; k < K; ++k) {
+                o << "    " << (k ? "else " : "") << "if (psi == " << k << ") {\n";
+                auto r = emit_region_poly(e, t, (int)k, st.region_to_union[k], false);
+                o << "    fsel = " << r[0] << ";\n    }\n";
+            }
+            fv = "fsel";
+        } else {
+            std::vector<std::string> rr;
+            for (size_t k = 0; k < K; ++k) rr.push_back(emit_region_poly(e, t, (int)k, st.region_to_union[k], false)[0]);
+            std::string sel = rr[K - 1];
+            for (int k = (int)K - 2; k >= 0; --k) sel = "(psi == " + std::to_string(k) + ") ? " + rr[k] + " : (" + sel + ")";
+            o << "    const float fsel = " << sel << ";\n";
+            fv = "fsel";
+        }
+        o << "    a.out[" << idx << "] = " << S << "_sp ? " << S << "_sv : " << fv << ";\n  }\n";
+    };
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block;
+    if (var.min_blocks > 0) o << ", " << var.min_blocks;
+    o << ") " << kname(t, "eval") << "(const LsEvalArgs a)\n{\n";
+    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride, CU = a.cunit;"
+         " (void)E1; (void)E2; (void)CS; (void)CU;\n";
+    o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
+    for (const char *S : {"P", "Q"}) {
+        for (size_t j = 0; j < NS; ++j) o << "  float " << S << "_c" << j << " = 0.0f;\n";
+        for (int i = 0; i < D; ++i) o << "  float " << S << "_a" << i << " = 0.0f;\n";
+        o << "  int " << S << "_psi = 0, " << S << "_sp = 0; float " << S << "_sv = 0.0f;\n";
+    }
+    o << "  long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;\n";
+    o << "  if (i0 >= a.n) return;\n";
+    stage_a("P", "i0");
+    o << "  for (;;) {\n";
+    o << "  const long long i1 = i0 + stride;\n";
+    o << "  if (i1 < a.n)\n";
+    stage_a("Q", "i1");
+    const int fma0 = e.fma;
+    stage_b("P", "i0");
+    info.fma_value = e.fma - fma0;
+    o << "  if (i1 >= a.n) break;\n";
+    o << "  i0 = i1 + stride;\n";
+    o << "  if (i0 < a.n)\n";
+    stage_a("P", "i0");
+    stage_b("Q", "i1");
+    o << "  if (i0 >= a.n) break;\n";
+    o << "  }\n}\n\n";
+}
+
 // Per-site weight polynomials w_j(u) (weights form), for the adjoint.
 // Returns the name of w for union site j (or "" if identically 0 in all regions).
 std::vector<std::string> emit_site_weights(Emitter &e, const Table &t, const Stencil &st)
@@ -1429,7 +1508,11 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
         g.info.n_sites = n;
     }
     g.info.reach = reach;
-    if (var.pts_per_thread > 1 && t.sep.empty()) {
+    if (var.pipeline && t.sep.empty()) {
+        // the point function still serves batched kernels
+        emit_eval_point(e, t, var, st, reach, false, kname(t, "eval_pt"));
+        emit_eval_kernel_pipelined(e, t, var, st, reach, g.info);
+    } else if (var.pts_per_thread > 1 && t.sep.empty()) {
         // the point function is still emitted (batched kernels, gradient) but the
         // value kernel walks runs of consecutive points
         GenInfo tmp;

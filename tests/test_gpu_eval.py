@@ -323,3 +323,32 @@ def test_warp_aggregated_adjoint_with_shared_sites(name):
     scale = max(1.0, np.abs(want).max())
     assert np.max(np.abs(dw.cpu().numpy() - want)) <= 2e-5 * scale
     assert np.max(np.abs(da.cpu().numpy() - want)) <= 2e-5 * scale
+
+
+@pytest.mark.parametrize("name", ["bcc_linear", "bcc_quintic", "fcc6", "zp"])
+@pytest.mark.parametrize("block,bps", [(128, 1), (256, 2)])
+def test_pipelined_variant(name, block, bps):
+    """Gathers of a thread's next point in flight while the current one is
+    evaluated: the oracle's values for every point count (odd, even, fewer points
+    than threads) and special points (NaN, far away)."""
+    from paper_2102_08518_b300.api import Spline, Volume
+    lat = workloads.SPLINE_LATTICE[name]
+    ext = SMALL_EXT[name]
+    coef = workloads.coef_uniform(lat, ext, seed=95)
+    lo, hi = workloads.bounding_box(lat, ext)
+    sp = Spline(name, "f32", block=block, blocks_per_sm=bps, pipeline=1)
+    vol = Volume(sp, ext, torch.from_numpy(coef).cuda())
+    plain = volume(name, ext, coef)
+    for n in (1, 2, 3, 1000, 148 * block * bps * 3 + 17):
+        pts = workloads.points_uniform(n, lo - 2.0, hi + 2.0, seed=n + 96)
+        if n > 10:
+            pts[5] = np.nan
+            pts[7] = 1e9
+        got = gpu_eval(vol, pts)
+        ref = gpu_eval(plain, pts)
+        assert np.array_equal(np.isnan(got), np.isnan(ref))
+        ok = ~np.isnan(ref)
+        assert np.max(np.abs(got[ok] - ref[ok])) <= 1e-6 * np.abs(coef).max()
+        sub = np.flatnonzero(ok)[:600]
+        want = oracle_eval(name, ext, coef, pts[sub])
+        assert np.max(np.abs(got[sub] - want)) <= TOL * np.abs(coef).max()
