@@ -170,6 +170,11 @@ typedef struct {
     int32_t pipeline;                  /* 1: the value kernel issues the gathers of a thread's next
                                           point before evaluating the current one (software
                                           pipelining; non-separable tables; pts_per_thread ignored) */
+    int32_t producers;                 /* P > 0: warp-specialized value kernel (non-separable tables):
+                                          P producer warps per block gather the coefficients of 32
+                                          points per consumer warp into shared memory, the other
+                                          block / 32 - P warps evaluate the polynomials; bounded
+                                          mbarrier waits (see ls_spline_status) */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */
@@ -198,6 +203,11 @@ ls_status ls_spline_precompile(const ls_spline_desc *desc, ls_dtype coef_dtype,
                                const ls_variant *variant);
 /* Generated source (NUL-terminated, owned by the spline) for inspection/tests. */
 const char *ls_spline_source(ls_spline s);
+/* LS_ERR_TIMEOUT if a bounded wait inside an evaluation kernel of this spline gave
+ * up since the last call (the affected outputs are then incomplete), else LS_OK;
+ * synchronises the stream and clears the word.  Only the warp-specialized value
+ * kernel waits on anything. */
+ls_status ls_spline_status(ls_spline s, ls_stream stream);
 /* Counts the generator computed: stencil size (union over reference regions),
  * FP32 FMAs per point for f, for f + grad f, registers per thread of the eval kernel. */
 ls_status ls_spline_info(ls_spline s, int32_t *n_sites, int32_t *fma_value,

@@ -56,7 +56,8 @@ class SplineDescC(ctypes.Structure):
 class VariantC(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("pts_per_thread", ctypes.c_int32), ("branchy", ctypes.c_int32),
                 ("min_blocks", ctypes.c_int32), ("group", ctypes.c_int32), ("depth", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32), ("brick", ctypes.c_int32), ("pipeline", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("brick", ctypes.c_int32), ("pipeline", ctypes.c_int32),
+                ("producers", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); every function declared in include/lattice_spline.h
@@ -69,6 +70,7 @@ SIGNATURES = {
     "ls_spline_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "ls_spline_precompile": (ctypes.c_int, [ctypes.POINTER(SplineDescC), ctypes.c_int, ctypes.POINTER(VariantC)]),
     "ls_spline_source": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "ls_spline_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "ls_spline_info": (ctypes.c_int, [ctypes.c_void_p, c_i32p, c_i32p, c_i32p, c_i32p]),
     "ls_volume_create": (ctypes.c_int, [ctypes.c_void_p, c_i64p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
     "ls_volume_wrap": (ctypes.c_int, [ctypes.c_void_p, c_i64p, ctypes.c_int32, ctypes.c_void_p,
@@ -220,5 +222,6 @@ class DescHolder:
 
 
 def variant(block=256, pts_per_thread=1, branchy=0, min_blocks=0, group=0, depth=0, blocks_per_sm=0,
-            brick=0, pipeline=0) -> VariantC:
-    return VariantC(block, pts_per_thread, branchy, min_blocks, group, depth, blocks_per_sm, brick, pipeline)
+            brick=0, pipeline=0, producers=0) -> VariantC:
+    return VariantC(block, pts_per_thread, branchy, min_blocks, group, depth, blocks_per_sm, brick, pipeline,
+                    producers)

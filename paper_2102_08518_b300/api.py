@@ -64,13 +64,13 @@ def _ptr(t: Optional[torch.Tensor]):
 
 def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_blocks: int = 0, group: int = 0,
                 depth: int = 0, pts_per_thread: int = 1, blocks_per_sm: int = 0, expansion: str = "sparse",
-                brick: int = 0, pipeline: int = 0) -> str:
+                brick: int = 0, pipeline: int = 0, producers: int = 0) -> str:
     """The name tag of a generated kernel variant (blocks_per_sm only sizes the
     grid, so it shares the compiled kernel)."""
     return f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + ("_br" if branchy else "") + \
         (f"_m{min_blocks}" if min_blocks else "") + (f"_g{group}d{depth}" if group and depth else "") + \
         (f"_t{pts_per_thread}" if pts_per_thread > 1 else "") + ("_ec" if expansion == "centroid" else "") + \
-        ("_bk" if brick else "") + ("_pp" if pipeline else "")
+        ("_bk" if brick else "") + ("_pp" if pipeline else "") + (f"_ws{producers}" if producers else "")
 
 
 class Spline:
@@ -79,7 +79,7 @@ class Spline:
     def __init__(self, name: str, dtype: str = "f32", block: int = 256, branchy: int = 0,
                  min_blocks: int = 0, group: int = 0, depth: int = 0, pts_per_thread: int = 1,
                  blocks_per_sm: int = 0, expansion: str = "sparse", brick: int = 0, pipeline: int = 0,
-                 kernel_name: Optional[str] = None):
+                 producers: int = 0, kernel_name: Optional[str] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("lattice spline kernels need a CUDA device")
         self.name = name
@@ -89,7 +89,8 @@ class Spline:
         self.n_cosets = len(self.table.spline.lattice.cosets)
         self.scale = self.table.spline.lattice.scale
         kname = kernel_name or globals()["kernel_name"](name, dtype, block, branchy, min_blocks, group, depth,
-                                                         pts_per_thread, blocks_per_sm, expansion, brick, pipeline)
+                                                         pts_per_thread, blocks_per_sm, expansion, brick, pipeline,
+                                                         producers)
         self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
                         "depth": depth, "pts_per_thread": pts_per_thread, "blocks_per_sm": blocks_per_sm,
                         "expansion": expansion}
@@ -97,10 +98,13 @@ class Spline:
             self.variant["brick"] = 1
         if pipeline:
             self.variant["pipeline"] = 1
+        if producers:
+            self.variant["producers"] = producers
         self.kernel_name = kname
         self._desc = _abi.DescHolder(self.table, kname, expansion)
         var = _abi.variant(block=block, pts_per_thread=pts_per_thread, branchy=branchy, min_blocks=min_blocks,
-                           group=group, depth=depth, blocks_per_sm=blocks_per_sm, brick=brick, pipeline=pipeline)
+                           group=group, depth=depth, blocks_per_sm=blocks_per_sm, brick=brick, pipeline=pipeline,
+                           producers=producers)
         h = ctypes.c_void_p()
         torch.cuda.init()
         _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),
@@ -115,6 +119,10 @@ class Spline:
 
     def source(self) -> str:
         return _abi.lib().ls_spline_source(self.handle).decode()
+
+    def status(self, stream=None):
+        """Raise if a bounded wait in one of this spline's kernels gave up."""
+        _abi.check(_abi.lib().ls_spline_status(self.handle, _stream(stream)), "ls_spline_status")
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -425,8 +433,8 @@ DEFAULT_CANDIDATES = (
 
 
 # the variants that won or came close somewhere in the full sweep (block size
-# and occupancy; limiting gathers in flight, 4 warps per SM and the software-
-# pipelined kernel never won on B300)
+# and occupancy; limiting gathers in flight, 4 warps per SM, the software-
+# pipelined and the warp-specialized kernels never won on B300)
 TUNE_CANDIDATES_SMALL = tuple([dict(block=256, blocks_per_sm=b, expansion=x) for b in (0, 2, 3) for x in
                                ("sparse", "centroid")] +
                               [dict(block=512, expansion=x) for x in ("sparse", "centroid")] +

@@ -19,6 +19,7 @@ struct EvalArgsH {
     const void *coef;
     long long n;
     int e0, e1, e2, cstride, cunit;
+    unsigned *status;
 };
 struct AdjArgsH {
     const float *pts;
@@ -211,10 +212,10 @@ int grid_for(long long n, int block, int sms, int per_sm)
     return (int)std::min(need, cap);
 }
 
-ls_status launch(cudaKernel_t k, int grid, int block, void *args, cudaStream_t stream)
+ls_status launch(cudaKernel_t k, int grid, int block, void *args, cudaStream_t stream, size_t smem = 0)
 {
     void *argv[] = {args};
-    cudaError_t e = cudaLaunchKernel((const void *)k, dim3(grid), dim3(block), argv, 0, stream);
+    cudaError_t e = cudaLaunchKernel((const void *)k, dim3(grid), dim3(block), argv, smem, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchKernel");
     return LS_OK;
 }
@@ -248,6 +249,7 @@ ls_variant default_variant(const ls_variant *v)
         r.blocks_per_sm = v->blocks_per_sm > 0 ? v->blocks_per_sm : 0;
         r.brick = v->brick ? 1 : 0;
         r.pipeline = v->pipeline ? 1 : 0;
+        r.producers = v->producers > 0 ? v->producers : 0;
     }
     return r;
 }
@@ -317,6 +319,10 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
         delete s;
         return ls_fail(LS_ERR_INVALID_ARG, "block must be a multiple of 32, <= 1024");
     }
+    if (s->var.producers > 0 && (s->var.producers > 8 || s->var.producers >= s->var.block / 32)) {
+        delete s;
+        return ls_fail(LS_ERR_INVALID_ARG, "producers must be 1..8 and leave at least one consumer warp");
+    }
     s->gen = ls::generate(s->table, dt, s->var);
     cudaError_t ce = cudaGetDevice(&s->device);
     if (ce != cudaSuccess) {
@@ -335,6 +341,13 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
         delete s;
         return ls_fail(st, err);
     }
+    if (cudaMalloc((void **)&s->status, 256) != cudaSuccess || cudaMemset(s->status, 0, 256) != cudaSuccess) {
+        cudaGetLastError();
+        if (s->status) cudaFree(s->status);
+        cudaLibraryUnload(s->mod.lib);
+        delete s;
+        return ls_fail(LS_ERR_OOM, "status word");
+    }
     if ((st = get_kernel(s, "eval", s->mod.eval, s->mod.blocks_per_sm_eval)) != LS_OK ||
         (st = get_kernel(s, "eval_grad", s->mod.eval_grad, s->mod.blocks_per_sm_grad)) != LS_OK ||
         (st = get_kernel(s, "adjoint_atomic", s->mod.adj_atomic, s->mod.blocks_per_sm_adj)) != LS_OK ||
@@ -342,9 +355,27 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
         (st = get_kernel(s, "adjoint_fixed", s->mod.adj_fixed, s->mod.blocks_per_sm_fixed)) != LS_OK ||
         (st = get_kernel(s, "adjoint_bin", s->mod.roe_key, s->mod.blocks_per_sm_gather)) != LS_OK ||
         (st = get_kernel(s, "adjoint_gather", s->mod.adj_gather, s->mod.blocks_per_sm_gather)) != LS_OK) {
+        cudaFree(s->status);
         cudaLibraryUnload(s->mod.lib);
         delete s;
         return st;
+    }
+    if (s->gen.info.eval_smem > 0) {
+        // warp-specialized value kernel: dynamic shared memory for its slots
+        const int smem = s->gen.info.eval_smem;
+        int nb = 0;
+        cudaError_t e2 = cudaFuncSetAttribute((const void *)s->mod.eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              smem);
+        if (e2 == cudaSuccess)
+            e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)s->mod.eval, s->var.block, smem);
+        if (e2 != cudaSuccess || nb < 1) {
+            cudaGetLastError();
+            cudaFree(s->status);
+            cudaLibraryUnload(s->mod.lib);
+            delete s;
+            return ls_fail(LS_ERR_UNSUPPORTED, "the warp-specialized kernel does not fit on an SM (shared memory)");
+        }
+        s->mod.blocks_per_sm_eval = nb;
     }
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, (const void *)s->mod.eval) == cudaSuccess) s->mod.regs_eval = fa.numRegs;
@@ -357,7 +388,20 @@ ls_status ls_spline_destroy(ls_spline s)
 {
     if (!s) return LS_OK;
     if (s->mod.lib) cudaLibraryUnload(s->mod.lib);
+    if (s->status) cudaFree(s->status);
     delete s;
+    return LS_OK;
+}
+
+ls_status ls_spline_status(ls_spline s, ls_stream stream)
+{
+    if (!s) return ls_fail(LS_ERR_INVALID_ARG, "spline is NULL");
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, s->status, sizeof v, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess && v) e = cudaMemsetAsync(s->status, 0, sizeof v, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the status word");
+    if (v) return ls_fail(LS_ERR_TIMEOUT, "a bounded wait in an evaluation kernel gave up");
     return LS_OK;
 }
 
@@ -549,6 +593,7 @@ static void fill_eval_args(ls_volume v, const float *pts, int64_t n, float *out,
     a.e2 = (int)v->ext[2];
     a.cstride = vol_cstride(v);
     a.cunit = vol_cunit(v);
+    a.status = v->spline->status;
 }
 
 ls_status ls_eval(ls_volume v, const float *pts, int64_t n, float *out, ls_stream stream)
@@ -563,7 +608,7 @@ ls_status ls_eval(ls_volume v, const float *pts, int64_t n, float *out, ls_strea
     const int per_sm = s->var.blocks_per_sm > 0 ? std::min(s->var.blocks_per_sm, s->mod.blocks_per_sm_eval)
                                                 : s->mod.blocks_per_sm_eval;
     return launch(s->mod.eval, grid_for((n + T - 1) / T, s->var.block, s->num_sms, per_sm), s->var.block, &a,
-                  (cudaStream_t)stream);
+                  (cudaStream_t)stream, (size_t)s->gen.info.eval_smem);
 }
 
 ls_status ls_eval_grad(ls_volume v, const float *pts, int64_t n, float *val, float *grad, ls_stream stream)

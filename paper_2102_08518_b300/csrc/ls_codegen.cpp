@@ -99,13 +99,25 @@ void emit_prologue(Emitter &e)
          " ls_u16 h = __ldg((const ls_u16*)p + i); float f; asm(\"cvt.f32.f16 %0, %1;\" : \"=f\"(f) : \"h\"(h));"
          " return f; }\n";
     o << "struct LsEvalArgs { const float* pts; float* out; float* grad; const void* coef;"
-         " long long n; int e0, e1, e2, cstride, cunit; };\n";
+         " long long n; int e0, e1, e2, cstride, cunit; unsigned* status; };\n";
     o << "struct LsAdjArgs { const float* pts; const float* gout; float* dcoef;"
          " long long n; int e0, e1, e2, cstride, cunit; unsigned long long* iacc; const float* iscale; };\n";
     o << "struct LsBinArgs { const float* pts; const float* gout; unsigned* key; int* idx; float4* rec;"
          " long long n; int e0, e1, e2, halo; unsigned nbins; };\n";
     o << "struct LsGatherArgs { const float4* srec; const unsigned* start; float* dcoef;"
          " int e0, e1, e2, cstride, cunit, halo; };\n";
+    // bounded wait for the completion of an mbarrier phase: gives up after about
+    // a second, sets *status to 1 and returns false (the caller's warp leaves)
+    o << "static __device__ __forceinline__ bool ls_mbar_wait(unsigned bar, unsigned parity, unsigned* status) {\n"
+         "  for (int it = 0; it < (1 << 20); ++it) {\n"
+         "    unsigned ok;\n"
+         "    asm volatile(\"{ .reg .pred p; mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, 1000;"
+         " selp.u32 %0, 1, 0, p; }\" : \"=r\"(ok) : \"r\"(bar), \"r\"(parity) : \"memory\");\n"
+         "    if (ok) return true;\n"
+         "  }\n"
+         "  if (status) atomicOr(status, 1u);\n"
+         "  return false;\n"
+         "}\n";
     // warp-aggregated scatter-add: lanes with the same address sum their values
     // by shuffles (per-lane source lanes, warp-uniform trip count) and the
     // lowest of them issues one atomic; ad < 0 means no site (nothing added)
@@ -1002,6 +1014,112 @@ void emit_eval_kernel_pipelined(Emitter &e, const Table &t, const ls_variant &va
     o << "  }\n}\n\n";
 }
 
+// Warp-specialized value kernel.  The first P warps of a block (producers)
+// classify points and gather their coefficients into shared-memory slots, one
+// slot of 32 points per consumer warp; the other warps (consumers) evaluate the
+// polynomials from the slots.  Few stencils are in flight per SM (P x 32
+// points), so their cache lines stay in L1 between the gathers of one point,
+// while many warps hide the latency of the polynomial.  Slot k has two
+// mbarriers: full[k] (the producer's lane 0 arrives after the warp's stores)
+// and empty[k] (the consumer's lane 0 arrives after the warp's loads); phases
+// alternate per round.  Every wait is bounded: a wait that gives up sets
+// *a.status and its warp leaves, so no warp can wait forever.
+// Returns the dynamic shared-memory bytes of the kernel.
+int emit_eval_kernel_ws(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
+                        GenInfo &info)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    const int NS = (int)st.sites.size();
+    const size_t K = t.ref.size();
+    const int NP = var.producers;
+    const int NC = var.block / 32 - NP;
+    const int SLOT = (NS + D + 2) * 32;          // floats: c[NS][32], a[D][32], meta (psi | flags), special value
+    const int smem = NC * SLOT * 4 + 2 * NC * 8;
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block;
+    if (var.min_blocks > 0) o << ", " << var.min_blocks;
+    o << ") " << kname(t, "eval") << "(const LsEvalArgs a)\n{\n";
+    o << "  extern __shared__ __align__(16) float ls_slots[];\n";
+    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride, CU = a.cunit;"
+         " (void)E1; (void)E2; (void)CS; (void)CU;\n";
+    o << "  const unsigned bar0 = (unsigned)__cvta_generic_to_shared(ls_slots + " << NC * SLOT << ");\n";
+    o << "  // full[k] at bar0 + 8k, empty[k] at bar0 + 8(" << NC << " + k)\n";
+    o << "  if (threadIdx.x == 0) {\n";
+    o << "    for (int k = 0; k < " << 2 * NC << "; ++k)\n";
+    o << "      asm volatile(\"mbarrier.init.shared::cta.b64 [%0], 1;\" :: \"r\"(bar0 + 8u * k) : \"memory\");\n";
+    o << "  }\n  __syncthreads();\n";
+    o << "  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n";
+    o << "  const long long TILE = " << 32 * NC << "LL;\n";
+    o << "  const long long ntiles = (a.n + TILE - 1) / TILE;\n";
+    o << "  const long long rounds = ntiles > (long long)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;\n";
+    // producers
+    o << "  if (warp < " << NP << ") {\n";
+    o << "    for (long long r = 0; r < rounds; ++r) {\n";
+    o << "      const long long tile = (long long)blockIdx.x + r * gridDim.x;\n";
+    o << "      for (int k = warp; k < " << NC << "; k += " << NP << ") {\n";
+    o << "        if (r > 0 && !ls_mbar_wait(bar0 + 8u * (" << NC << " + k), (unsigned)((r - 1) & 1), a.status)) return;\n";
+    o << "        float* sl = ls_slots + k * " << SLOT << ";\n";
+    o << "        const long long i = tile * TILE + k * 32 + lane;\n";
+    o << "        int sp = 0; float sv = 0.0f; int psi_out = 0;\n";
+    for (int j = 0; j < NS; ++j) o << "        float oc" << j << " = 0.0f;\n";
+    for (int i = 0; i < D; ++i) o << "        float oa" << i << " = 0.0f;\n";
+    o << "#define LS_OUT_OF_RANGE(V) { sp = 1; sv = (V); }\n";
+    o << "        do {\n";
+    o << "        if (i >= a.n) { sp = 2; break; }\n";
+    emit_point_load(e, t, "break");
+    emit_classify(e, t);
+    emit_gathers(e, t, st.sites, reach, "a.coef", false, true, 0, 0);
+    for (int j = 0; j < NS; ++j) o << "        oc" << j << " = c" << j << ";\n";
+    for (int i = 0; i < D; ++i) o << "        oa" << i << " = a" << i << ";\n";
+    o << "        psi_out = psi;\n";
+    o << "        } while (0);\n#undef LS_OUT_OF_RANGE\n";
+    for (int j = 0; j < NS; ++j) o << "        sl[" << j * 32 << " + lane] = oc" << j << ";\n";
+    for (int i = 0; i < D; ++i) o << "        sl[" << (NS + i) * 32 << " + lane] = oa" << i << ";\n";
+    o << "        sl[" << (NS + D) * 32 << " + lane] = __int_as_float(psi_out | (sp << 8));\n";
+    o << "        sl[" << (NS + D + 1) * 32 << " + lane] = sv;\n";
+    o << "        __syncwarp();\n";
+    o << "        if (lane == 0) asm volatile(\"mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\" :: \"r\"(bar0 + 8u * k) : \"memory\");\n";
+    o << "      }\n    }\n    return;\n  }\n";
+    // consumers
+    o << "  {\n";
+    o << "    const int k = warp - " << NP << ";\n";
+    o << "    const float* sl = ls_slots + k * " << SLOT << ";\n";
+    o << "    for (long long r = 0; r < rounds; ++r) {\n";
+    o << "      const long long tile = (long long)blockIdx.x + r * gridDim.x;\n";
+    o << "      const long long i = tile * TILE + k * 32 + lane;\n";
+    o << "      if (!ls_mbar_wait(bar0 + 8u * k, (unsigned)(r & 1), a.status)) return;\n";
+    for (int j = 0; j < NS; ++j) o << "      const float c" << j << " = sl[" << j * 32 << " + lane];\n";
+    for (int i = 0; i < D; ++i) o << "      const float a" << i << " = sl[" << (NS + i) * 32 << " + lane];\n";
+    o << "      const int meta = __float_as_int(sl[" << (NS + D) * 32 << " + lane]);\n";
+    o << "      const float sv = sl[" << (NS + D + 1) * 32 << " + lane];\n";
+    o << "      __syncwarp();\n";
+    o << "      if (lane == 0) asm volatile(\"mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\" :: \"r\"(bar0 + 8u * ("
+      << NC << " + k)) : \"memory\");\n";
+    o << "      const int psi = meta & 255, sp = meta >> 8; (void)psi;\n";
+    const int fma0 = e.fma;
+    std::string fv;
+    if (K > 1 && var.branchy) {
+        o << "      float fsel = 0.0f;\n";
+        for (size_t k = 0; k < K; ++k) {
+            o << "      " << (k ? "else " : "") << "if (psi == " << k << ") {\n";
+            auto r = emit_region_poly(e, t, (int)k, st.region_to_union[k], false);
+            o << "      fsel = " << r[0] << ";\n      }\n";
+        }
+        fv = "fsel";
+    } else {
+        std::vector<std::string> rr;
+        for (size_t k = 0; k < K; ++k) rr.push_back(emit_region_poly(e, t, (int)k, st.region_to_union[k], false)[0]);
+        std::string sel = rr[K - 1];
+        for (int k = (int)K - 2; k >= 0; --k) sel = "(psi == " + std::to_string(k) + ") ? " + rr[k] + " : (" + sel + ")";
+        o << "      const float fsel = " << sel << ";\n";
+        fv = "fsel";
+    }
+    info.fma_value = e.fma - fma0;
+    o << "      if (sp != 2) a.out[i] = sp ? sv : " << fv << ";\n";
+    o << "    }\n  }\n}\n\n";
+    return smem;
+}
+
 // Per-site weight polynomials w_j(u) (weights form), for the adjoint.
 // Returns the name of w for union site j (or "" if identically 0 in all regions).
 std::vector<std::string> emit_site_weights(Emitter &e, const Table &t, const Stencil &st)
@@ -1508,7 +1626,10 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
         g.info.n_sites = n;
     }
     g.info.reach = reach;
-    if (var.pipeline && t.sep.empty()) {
+    if (var.producers > 0 && t.sep.empty()) {
+        emit_eval_point(e, t, var, st, reach, false, kname(t, "eval_pt"));
+        g.info.eval_smem = emit_eval_kernel_ws(e, t, var, st, reach, g.info);
+    } else if (var.pipeline && t.sep.empty()) {
         // the point function still serves batched kernels
         emit_eval_point(e, t, var, st, reach, false, kname(t, "eval_pt"));
         emit_eval_kernel_pipelined(e, t, var, st, reach, g.info);
@@ -1585,7 +1706,7 @@ Generated generate_batch(const std::vector<const Table *> &tables, const std::ve
     o << "    const LsBatchVol v = b.vols[w.vol];\n";
     o << "    LsEvalArgs a;\n";
     o << "    a.pts = v.pts; a.out = v.out; a.grad = 0; a.coef = v.coef; a.n = v.n;\n";
-    o << "    a.e0 = v.e0; a.e1 = v.e1; a.e2 = v.e2; a.cstride = v.cstride; a.cunit = v.cunit;\n";
+    o << "    a.e0 = v.e0; a.e1 = v.e1; a.e2 = v.e2; a.cstride = v.cstride; a.cunit = v.cunit; a.status = b.status;\n";
     o << "    switch (v.kind) {\n";
     for (size_t k = 0; k < tables.size(); ++k)
         o << "    case " << k << ": for (long long i = w.p0 + threadIdx.x; i < w.p1; i += blockDim.x) ls_bpt_" << k

@@ -52,6 +52,7 @@ struct GenInfo {
     int n_reverse = 0;      // offsets between a coefficient and the ROE sites that can reach it
     int halo = 0;           // halo of the binning grid (storage units)
     double wmax = 1.0;      // bound on |w_j(u)| over the region of evaluation
+    int eval_smem = 0;      // dynamic shared memory of the value kernel (warp-specialized variant)
 };
 
 struct Generated {
@@ -94,6 +95,7 @@ struct ls_spline_s {
     ls::Module mod;
     int device = 0;
     int num_sms = 0;
+    unsigned *status = nullptr;       // device word: bounded waits that gave up (warp-specialized kernel)
 };
 
 struct ls_volume_s {

@@ -352,3 +352,34 @@ def test_pipelined_variant(name, block, bps):
         sub = np.flatnonzero(ok)[:600]
         want = oracle_eval(name, ext, coef, pts[sub])
         assert np.max(np.abs(got[sub] - want)) <= TOL * np.abs(coef).max()
+
+
+@pytest.mark.parametrize("name", ["bcc_linear", "bcc_quintic", "fcc6", "zp"])
+@pytest.mark.parametrize("block,producers", [(512, 2), (256, 1), (512, 4)])
+def test_warp_specialized_variant(name, block, producers):
+    """Producer warps gather into shared-memory slots, consumer warps evaluate:
+    the oracle's values and the plain kernel's for point counts below one tile,
+    with partial tiles and with several rounds per block; no wait gives up."""
+    from paper_2102_08518_b300.api import Spline, Volume
+    lat = workloads.SPLINE_LATTICE[name]
+    ext = SMALL_EXT[name]
+    coef = workloads.coef_uniform(lat, ext, seed=97)
+    lo, hi = workloads.bounding_box(lat, ext)
+    sp = Spline(name, "f32", block=block, producers=producers)
+    vol = Volume(sp, ext, torch.from_numpy(coef).cuda())
+    plain = volume(name, ext, coef)
+    tile = 32 * (block // 32 - producers)
+    for n in (1, 31, tile - 1, tile + 1, 148 * tile * 3 + 77):
+        pts = workloads.points_uniform(n, lo - 2.0, hi + 2.0, seed=n + 98)
+        if n > 40:
+            pts[33] = np.nan
+            pts[35] = -1e9
+        got = gpu_eval(vol, pts)
+        ref = gpu_eval(plain, pts)
+        assert np.array_equal(np.isnan(got), np.isnan(ref))
+        ok = ~np.isnan(ref)
+        assert np.max(np.abs(got[ok] - ref[ok])) <= 1e-6 * np.abs(coef).max()
+        sub = np.flatnonzero(ok)[:600]
+        want = oracle_eval(name, ext, coef, pts[sub])
+        assert np.max(np.abs(got[sub] - want)) <= TOL * np.abs(coef).max()
+    sp.status()
