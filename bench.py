@@ -428,6 +428,7 @@ def extra_fwd_bwd(torch, dev, vols, pts, outs):
 
     t_plain = time_ms(torch, lambda: vol.eval(p, outs["uniform"]))
     t_grad = time_ms(torch, lambda: vol.eval_grad(p))
+    t_hess = time_ms(torch, lambda: vol.eval_hess(p))
     t_adj_a = time_ms(torch, lambda: adj(0))
     t_adj_d = time_ms(torch, lambda: adj(1), reps=5)
     t_adj_w = time_ms(torch, lambda: adj(2))
@@ -436,7 +437,8 @@ def extra_fwd_bwd(torch, dev, vols, pts, outs):
     t_rays_w = time_ms(torch, lambda: adj(2, p_rays))
     gp = lambda ms: round(n / (ms * 1e-3) / 1e9, 3)
     return {"workload": "bcc_quintic 2x128^3, 2^24 uniform points", "plain_f32_gpoints_s": gp(t_plain),
-            "value_grad_gpoints_s": gp(t_grad), "adjoint_atomic_gpoints_s": gp(t_adj_a),
+            "value_grad_gpoints_s": gp(t_grad), "value_grad_hessian_gpoints_s": gp(t_hess),
+            "adjoint_atomic_gpoints_s": gp(t_adj_a),
             "adjoint_deterministic_gpoints_s": gp(t_adj_d), "adjoint_warp_aggregated_gpoints_s": gp(t_adj_w),
             "adjoint_deterministic_fixed_point_gpoints_s": gp(t_adj_f),
             "fwd_bwd_deterministic_fixed_point_gpoints_s": gp(t_grad + t_adj_f),

@@ -260,6 +260,17 @@ ls_status ls_eval(ls_volume v, const float *pts, int64_t n, float *out, ls_strea
 ls_status ls_eval_grad(ls_volume v, const float *pts, int64_t n, float *val, float *grad,
                        ls_stream stream);
 /*
+ * f, its gradient and its Hessian from the twice-differentiated sub-region
+ * polynomials (Sec. 3: derivatives of the per-region polynomials; the symmetry
+ * transforms still apply: H = T^T H_ref T):
+ * hess[i*6 + q] = d2f/dx_a dx_b (pts[i]) for (a,b) = (0,0) (1,1) (2,2) (0,1)
+ * (0,2) (1,2) in 3D, hess[i*3 + q] for (0,0) (1,1) (0,1) in 2D.  val and grad may
+ * be NULL.  Continuous for C^2 splines (tricubic, BCC quintic); elsewhere a
+ * point on a knot plane gets the value of one of the adjacent polynomial pieces.
+ */
+ls_status ls_eval_hess(ls_volume v, const float *pts, int64_t n, float *val, float *grad, float *hess,
+                       ls_stream stream);
+/*
  * Same as ls_eval with HOST buffers: copies pts to the device, evaluates and
  * copies out back; returns when out is complete.  The points move in chunks
  * on two internal streams, so the host-to-device copy of one chunk, the kernels

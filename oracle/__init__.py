@@ -11,9 +11,9 @@ recurrence.  ``specs`` holds the oracle's own copy of the spline and lattice
 definitions of the benchmarked splines (Sec. 5.1) and of the ZP element of
 Fig. 1.
 """
-from .lib import (OrcSpec, box, phi, phi_grad, eval_sum, eval_sum_grad, adjoint,
+from .lib import (OrcSpec, box, phi, phi_grad, phi_hess, eval_sum, eval_sum_grad, eval_sum_hess, adjoint,
                   design_triplets, morton3, build_library, library_path)
 from . import specs
 
-__all__ = ["OrcSpec", "box", "phi", "phi_grad", "eval_sum", "eval_sum_grad", "adjoint",
+__all__ = ["OrcSpec", "box", "phi", "phi_grad", "phi_hess", "eval_sum", "eval_sum_grad", "eval_sum_hess", "adjoint",
            "design_triplets", "morton3", "build_library", "library_path", "specs"]

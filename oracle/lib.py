@@ -120,6 +120,10 @@ def configure(lib):
     lib.orc_design_triplets.argtypes = [sp, dp, ctypes.c_int64, i64p, i64p, dp, ctypes.c_int64]
     lib.orc_morton3.restype = ctypes.c_uint32
     lib.orc_morton3.argtypes = [ctypes.c_uint32] * 3
+    lib.orc_phi_hess.restype = ctypes.c_int32
+    lib.orc_phi_hess.argtypes = [sp, dp, ctypes.c_int64, dp]
+    lib.orc_eval_hess.restype = ctypes.c_int32
+    lib.orc_eval_hess.argtypes = [sp, dp, dp, ctypes.c_int64, dp, ctypes.c_int32]
     return lib
 
 
@@ -195,6 +199,31 @@ def eval_sum_grad(spec: OrcSpec, coef, pts, nthreads: int = 0):
                         nthreads) != 0:
         raise RuntimeError("orc_eval failed")
     return out, g
+
+
+def _hess_width(dim: int) -> int:
+    return 6 if dim == 3 else 3
+
+
+def phi_hess(spec: OrcSpec, y) -> np.ndarray:
+    """Hessian of phi at points y: (n, 6) as xx yy zz xy xz yz in 3D, (n, 3) as xx yy xy in 2D."""
+    y = _f64(y).reshape(-1, spec.dim)
+    h = np.zeros((len(y), _hess_width(spec.dim)))
+    cs = spec.to_c()
+    if _load().orc_phi_hess(ctypes.byref(cs), _dptr(y), len(y), _dptr(h)) != 0:
+        raise RuntimeError("orc_phi_hess failed")
+    return h
+
+
+def eval_sum_hess(spec: OrcSpec, coef, pts, nthreads: int = 0) -> np.ndarray:
+    """Hessian of the naive convolution sum (same layout as phi_hess)."""
+    c = _f64(coef).ravel()
+    p = _f64(pts).reshape(-1, spec.dim)
+    h = np.zeros((len(p), _hess_width(spec.dim)))
+    cs = spec.to_c()
+    if _load().orc_eval_hess(ctypes.byref(cs), _dptr(c), _dptr(p), len(p), _dptr(h), nthreads) != 0:
+        raise RuntimeError("orc_eval_hess failed")
+    return h
 
 
 def adjoint(spec: OrcSpec, pts, g) -> np.ndarray:

@@ -46,7 +46,12 @@
  *
  * Gradients use the box spline derivative identity
  *     D_xi M_Xi(x) = M_{Xi\xi}(x) - M_{Xi\xi}(x - xi)
- * along s independent directions whose removal keeps Xi spanning.
+ * along s independent directions whose removal keeps Xi spanning.  Applied
+ * twice it gives, for two columns i != j of Xi (possibly equal directions),
+ *     D_xi_i D_xi_j M_Xi(x) = sum_{a,b in {0,1}} (-1)^(a+b) M_{Xi\{i,j}}(x - a xi_i - b xi_j),
+ * which is 0 off the knot planes when Xi\{i,j} does not span (rule R1); the
+ * Hessian H is the symmetric matrix with xi_i^T H xi_j equal to these values
+ * for every pair, solved by least squares over all pairs.
  *
  * Everything is plain FP64 with round-to-nearest; no fast-math.
  */
@@ -392,6 +397,14 @@ static double beta3(double t)
     return 0.0;
 }
 
+static double d2beta3(double t)
+{
+    double a = fabs(t);
+    if (a < 1.0) return -2.0 + 3.0 * a;
+    if (a < 2.0) return 2.0 - a;
+    return 0.0;
+}
+
 static double dbeta3(double t)
 {
     double a = fabs(t), sg = (t < 0.0) ? -1.0 : 1.0;
@@ -656,6 +669,153 @@ static double phi_generic(phi_ctx *p, const double *y, double *g)
 }
 
 /* ------------------------------------------------------------------------- */
+/* Hessian                                                                    */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    phi_ctx *p;
+    int npair;
+    int pi[ORC_MAXDIR * (ORC_MAXDIR - 1) / 2], pj[ORC_MAXDIR * (ORC_MAXDIR - 1) / 2];
+    box_memo *pm;                  /* M_{Xi \ {i, j}} per pair */
+    double ninv[6][6];             /* inverse of the normal matrix of the pair equations */
+    double rows[ORC_MAXDIR * (ORC_MAXDIR - 1) / 2][6];
+    int nh;                        /* unknowns: 6 (3D: 00 11 22 01 02 12) or 3 (2D: 00 11 01) */
+} hess_ctx;
+
+static const int HA[6] = {0, 1, 2, 0, 0, 1}, HB[6] = {0, 1, 2, 1, 2, 2};
+static const int HA2[3] = {0, 1, 0}, HB2[3] = {0, 1, 1};
+
+/* Invert an n x n matrix (n <= 6) by Gauss-Jordan with partial pivoting. */
+static int invert_small(int n, double a[6][6], double inv[6][6])
+{
+    double m[6][12];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < 2 * n; ++c) m[r][c] = c < n ? a[r][c] : (c - n == r ? 1.0 : 0.0);
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(m[r][c]) > fabs(m[piv][c])) piv = r;
+        if (fabs(m[piv][c]) < 1e-12) return -1;
+        if (piv != c)
+            for (int q = 0; q < 2 * n; ++q) { double t = m[c][q]; m[c][q] = m[piv][q]; m[piv][q] = t; }
+        double d = m[c][c];
+        for (int q = 0; q < 2 * n; ++q) m[c][q] /= d;
+        for (int r = 0; r < n; ++r)
+            if (r != c) {
+                double f = m[r][c];
+                for (int q = 0; q < 2 * n; ++q) m[r][q] -= f * m[c][q];
+            }
+    }
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) inv[r][c] = m[r][c + n];
+    return 0;
+}
+
+static int hess_init(hess_ctx *h, phi_ctx *p)
+{
+    memset(h, 0, sizeof(*h));
+    h->p = p;
+    const orc_spec *sp = p->sp;
+    const int k = sp->dim, m = sp->ndir;
+    h->nh = k == 3 ? 6 : 3;
+    if (sp->kind == 1) return 0;
+    h->npair = m * (m - 1) / 2;
+    h->pm = (box_memo *)calloc((size_t)h->npair, sizeof(box_memo));
+    if (!h->pm) return -1;
+    double ata[6][6];
+    memset(ata, 0, sizeof(ata));
+    int q = 0;
+    for (int i = 0; i < m; ++i)
+        for (int j = i + 1; j < m; ++j, ++q) {
+            h->pi[q] = i;
+            h->pj[q] = j;
+            double rest[ORC_MAXDIR * 3];
+            int mr = 0;
+            for (int c = 0; c < m; ++c)
+                if (c != i && c != j) { for (int t = 0; t < 3; ++t) rest[3 * mr + t] = sp->dirs[3 * c + t]; ++mr; }
+            if (memo_init(&h->pm[q], k, mr, rest)) return -1;
+            /* xi_i^T H xi_j in the unknowns */
+            const double *u = sp->dirs + 3 * i, *v = sp->dirs + 3 * j;
+            for (int e = 0; e < h->nh; ++e) {
+                int a = k == 3 ? HA[e] : HA2[e], b = k == 3 ? HB[e] : HB2[e];
+                h->rows[q][e] = a == b ? u[a] * v[a] : u[a] * v[b] + u[b] * v[a];
+            }
+            for (int r = 0; r < h->nh; ++r)
+                for (int c = 0; c < h->nh; ++c) ata[r][c] += h->rows[q][r] * h->rows[q][c];
+        }
+    return invert_small(h->nh, ata, h->ninv);
+}
+
+static void hess_free(hess_ctx *h)
+{
+    if (h->pm) {
+        for (int q = 0; q < h->npair; ++q) memo_free(&h->pm[q]);
+        free(h->pm);
+    }
+}
+
+/* Hessian of phi at y off every knot plane (out: nh values). */
+static void hess_generic(hess_ctx *h, const double *y, double *out)
+{
+    const orc_spec *sp = h->p->sp;
+    const int k = sp->dim;
+    for (int e = 0; e < h->nh; ++e) out[e] = 0.0;
+    if (outside_support(h->p, y)) return;
+    double x[3] = {0, 0, 0};
+    for (int i = 0; i < k; ++i) x[i] = y[i] + h->p->half[i];
+    double atb[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = 0; q < h->npair; ++q) {
+        const double *u = sp->dirs + 3 * h->pi[q], *v = sp->dirs + 3 * h->pj[q];
+        double d = 0.0;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                double xs[3] = {0, 0, 0};
+                for (int i = 0; i < k; ++i) xs[i] = x[i] - a * u[i] - b * v[i];
+                d += ((a + b) & 1 ? -1.0 : 1.0) * memo_eval(&h->pm[q], xs);
+            }
+        d *= sp->detL;
+        for (int e = 0; e < h->nh; ++e) atb[e] += h->rows[q][e] * d;
+    }
+    for (int r = 0; r < h->nh; ++r)
+        for (int c = 0; c < h->nh; ++c) out[r] += h->ninv[r][c] * atb[c];
+}
+
+/* Hessian of phi at y; on a knot plane the limit from the side of a fixed
+ * generic direction (as for the value and the gradient). */
+static void hess_eval(hess_ctx *h, const double *y, double *out)
+{
+    const orc_spec *sp = h->p->sp;
+    const int k = sp->dim;
+    if (sp->kind == 1) {
+        double b[3], db[3], d2[3];
+        for (int i = 0; i < 3; ++i) { b[i] = beta3(y[i]); db[i] = dbeta3(y[i]); d2[i] = d2beta3(y[i]); }
+        for (int e = 0; e < h->nh; ++e) {
+            int a = k == 3 ? HA[e] : HA2[e], c = k == 3 ? HB[e] : HB2[e];
+            double t = 1.0;
+            for (int i = 0; i < k; ++i) {
+                if (a == c) t *= (i == a) ? d2[i] : b[i];
+                else t *= (i == a || i == c) ? db[i] : b[i];
+            }
+            out[e] = t;
+        }
+        return;
+    }
+    double x[3] = {0, 0, 0};
+    for (int i = 0; i < k; ++i) x[i] = y[i] + h->p->half[i];
+    if (on_knot_plane(h->p, x)) {
+        static const double vdir[3] = {0.5377451, 0.3141593, 0.7993603};
+        const double delta = 1e-7;
+        double y1[3] = {0, 0, 0}, y2[3] = {0, 0, 0}, o1[6], o2[6];
+        for (int i = 0; i < k; ++i) { y1[i] = y[i] + delta * vdir[i]; y2[i] = y[i] + 2 * delta * vdir[i]; }
+        hess_generic(h, y1, o1);
+        hess_generic(h, y2, o2);
+        for (int e = 0; e < h->nh; ++e) out[e] = 2.0 * o1[e] - o2[e];
+        return;
+    }
+    hess_generic(h, y, out);
+}
+
+/* ------------------------------------------------------------------------- */
 /* exported entry points                                                       */
 /* ------------------------------------------------------------------------- */
 
@@ -877,6 +1037,69 @@ uint32_t orc_morton3(uint32_t c0, uint32_t c1, uint32_t c2)
         for (int i = 0; i < 3; ++i)
             key |= ((c[i] >> b) & 1u) << (3 * b + i);
     return key;
+}
+
+/* Hessian of phi at n points y (n*dim): hess n*6 (3D: xx yy zz xy xz yz) or n*3 (2D: xx yy xy). */
+int32_t orc_phi_hess(const orc_spec *sp, const double *y, int64_t n, double *hess)
+{
+    phi_ctx p;
+    hess_ctx h;
+    if (phi_init(&p, sp, 0)) return -1;
+    if (hess_init(&h, &p)) { hess_free(&h); phi_free(&p); return -1; }
+    const int k = sp->dim;
+    for (int64_t q = 0; q < n; ++q) hess_eval(&h, y + k * q, hess + h.nh * q);
+    hess_free(&h);
+    phi_free(&p);
+    return 0;
+}
+
+typedef struct {
+    hess_ctx *h;
+    const double *coef;
+    double hs[6];
+} hess_acc;
+
+static void hess_site(void *vctx, int64_t lin, const double *y)
+{
+    hess_acc *e = (hess_acc *)vctx;
+    double c = e->coef[lin];
+    if (c == 0.0) return;
+    double o[6];
+    hess_eval(e->h, y, o);
+    for (int t = 0; t < e->h->nh; ++t) e->hs[t] += c * o[t];
+}
+
+/* Hessian of the naive sum (Eq. 1) at n points: hess n*6 (3D) or n*3 (2D). */
+int32_t orc_eval_hess(const orc_spec *sp, const double *coef, const double *pts, int64_t n, double *hess,
+                      int32_t nthreads)
+{
+    int err = 0;
+    const int k = sp->dim;
+#pragma omp parallel num_threads(nthreads_or_default(nthreads)) reduction(| : err)
+    {
+        phi_ctx p;
+        hess_ctx h;
+        if (phi_init(&p, sp, 0)) {
+            err = 1;
+        } else if (hess_init(&h, &p)) {
+            hess_free(&h);
+            phi_free(&p);
+            err = 1;
+        } else {
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t q = 0; q < n; ++q) {
+                hess_acc e;
+                memset(&e, 0, sizeof(e));
+                e.h = &h;
+                e.coef = coef;
+                for_each_site(sp, pts + k * q, hess_site, &e);
+                for (int t = 0; t < h.nh; ++t) hess[h.nh * q + t] = e.hs[t];
+            }
+            hess_free(&h);
+            phi_free(&p);
+        }
+    }
+    return err ? -1 : 0;
 }
 
 int32_t orc_abi_version(void) { return 1; }

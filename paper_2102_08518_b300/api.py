@@ -206,6 +206,19 @@ class Volume:
                    "ls_eval_grad")
         return val, grad
 
+    def eval_hess(self, pts: torch.Tensor, want_value: bool = True, want_grad: bool = True, stream=None):
+        """(f, grad f, Hessian) with the Hessian as (n, 6) xx yy zz xy xz yz in 3D,
+        (n, 3) xx yy xy in 2D; f and grad are None unless wanted."""
+        pts = _check_pts(pts, self.spline.dim)
+        n = pts.shape[0]
+        dim = self.spline.dim
+        val = torch.empty(n, device=pts.device, dtype=torch.float32) if want_value else None
+        grad = torch.empty(n, dim, device=pts.device, dtype=torch.float32) if want_grad else None
+        hess = torch.empty(n, 6 if dim == 3 else 3, device=pts.device, dtype=torch.float32)
+        _abi.check(_abi.lib().ls_eval_hess(self.handle, _ptr(pts), n, _ptr(val), _ptr(grad), _ptr(hess),
+                                           _stream(stream)), "ls_eval_hess")
+        return val, grad, hess
+
     def eval_host(self, pts_host, out_host, stream=None):
         """Host buffers in, host buffer out (copies inside the call)."""
         n = pts_host.shape[0]

@@ -20,6 +20,7 @@ struct EvalArgsH {
     long long n;
     int e0, e1, e2, cstride, cunit;
     unsigned *status;
+    float *hess;
 };
 struct AdjArgsH {
     const float *pts;
@@ -350,6 +351,7 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
     }
     if ((st = get_kernel(s, "eval", s->mod.eval, s->mod.blocks_per_sm_eval)) != LS_OK ||
         (st = get_kernel(s, "eval_grad", s->mod.eval_grad, s->mod.blocks_per_sm_grad)) != LS_OK ||
+        (st = get_kernel(s, "eval_hess", s->mod.eval_hess, s->mod.blocks_per_sm_hess)) != LS_OK ||
         (st = get_kernel(s, "adjoint_atomic", s->mod.adj_atomic, s->mod.blocks_per_sm_adj)) != LS_OK ||
         (st = get_kernel(s, "adjoint_warpagg", s->mod.adj_warpagg, s->mod.blocks_per_sm_warpagg)) != LS_OK ||
         (st = get_kernel(s, "adjoint_fixed", s->mod.adj_fixed, s->mod.blocks_per_sm_fixed)) != LS_OK ||
@@ -594,6 +596,7 @@ static void fill_eval_args(ls_volume v, const float *pts, int64_t n, float *out,
     a.cstride = vol_cstride(v);
     a.cunit = vol_cunit(v);
     a.status = v->spline->status;
+    a.hess = nullptr;
 }
 
 ls_status ls_eval(ls_volume v, const float *pts, int64_t n, float *out, ls_stream stream)
@@ -623,6 +626,20 @@ ls_status ls_eval_grad(ls_volume v, const float *pts, int64_t n, float *val, flo
                                                 : s->mod.blocks_per_sm_grad;
     return launch(s->mod.eval_grad, grid_for(n, s->var.block, s->num_sms, per_sm), s->var.block, &a,
                   (cudaStream_t)stream);
+}
+
+ls_status ls_eval_hess(ls_volume v, const float *pts, int64_t n, float *val, float *grad, float *hess,
+                       ls_stream stream)
+{
+    if (!v || (n > 0 && (!pts || !hess))) return ls_fail(LS_ERR_INVALID_ARG, "volume, pts or hess is NULL");
+    if (n < 0) return ls_fail(LS_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return LS_OK;
+    ls_spline_s *s = v->spline;
+    EvalArgsH a;
+    fill_eval_args(v, pts, n, val, grad, a);
+    a.hess = hess;
+    return launch(s->mod.eval_hess, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_hess), s->var.block,
+                  &a, (cudaStream_t)stream);
 }
 
 ls_status ls_eval_host_multi(int32_t n_vol, const ls_volume *vols, const float *host_pts, int64_t n,

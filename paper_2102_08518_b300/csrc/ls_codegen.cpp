@@ -99,7 +99,7 @@ void emit_prologue(Emitter &e)
          " ls_u16 h = __ldg((const ls_u16*)p + i); float f; asm(\"cvt.f32.f16 %0, %1;\" : \"=f\"(f) : \"h\"(h));"
          " return f; }\n";
     o << "struct LsEvalArgs { const float* pts; float* out; float* grad; const void* coef;"
-         " long long n; int e0, e1, e2, cstride, cunit; unsigned* status; };\n";
+         " long long n; int e0, e1, e2, cstride, cunit; unsigned* status; float* hess; };\n";
     o << "struct LsAdjArgs { const float* pts; const float* gout; float* dcoef;"
          " long long n; int e0, e1, e2, cstride, cunit; unsigned long long* iacc; const float* iscale; };\n";
     o << "struct LsBinArgs { const float* pts; const float* gout; unsigned* key; int* idx; float4* rec;"
@@ -576,8 +576,14 @@ std::set<I3> monomial_support(const RefRegion &r, const std::vector<int> &umap,
 
 // Emits value (and optionally gradient in reference coordinates) for region k.
 // Returns names {f, g0, g1, g2}.
+// Hessian entries in the order (0,0) (1,1) (2,2) (0,1) (0,2) (1,2) in 3D, (0,0) (1,1) (0,1) in 2D.
+const int HI3[6] = {0, 1, 2, 0, 0, 1}, HJ3[6] = {0, 1, 2, 1, 2, 2};
+const int HI2[3] = {0, 1, 0}, HJ2[3] = {0, 1, 1};
+
+// Value, and for nd >= 1 the gradient, for nd >= 2 also the Hessian, all in
+// reference coordinates: returns {f, g_0..g_{D-1}, h_0..h_{NH-1}}.
 std::vector<std::string> emit_region_poly(Emitter &e, const Table &t, int k, const std::vector<int> &umap,
-                                          bool grad)
+                                          int grad)
 {
     const RefRegion &r = t.ref[k];
     const int D = t.dim;
@@ -624,15 +630,162 @@ std::vector<std::string> emit_region_poly(Emitter &e, const Table &t, int k, con
             res.push_back(g.empty() ? "0.0f" : g);
         }
     }
+    if (grad >= 2) {
+        const int NH = D == 3 ? 6 : 3;
+        for (int q = 0; q < NH; ++q) {
+            const int i = D == 3 ? HI3[q] : HI2[q], j = D == 3 ? HJ3[q] : HJ2[q];
+            // d^2/du_i du_j u^m = m_i (m_i - 1) u^{m - 2e_i} (i = j), m_i m_j u^{m - e_i - e_j} (i != j)
+            std::set<I3> hsup;
+            std::map<I3, std::string> hname;
+            for (const auto &m : sup) {
+                const int fac = (i == j) ? m[i] * (m[i] - 1) : m[i] * m[j];
+                if (fac == 0) continue;
+                I3 dm = m;
+                dm[i] -= 1;
+                dm[j] -= 1;
+                hsup.insert(dm);
+                std::string nm;
+                if (fac == 1) {
+                    nm = pe.aname[m];
+                } else {
+                    nm = e.fresh("hA");
+                    e.o << "    const float " << nm << " = " << flit(fac) << " * " << pe.aname[m] << ";\n";
+                    e.fma++;
+                }
+                hname[dm] = nm;
+            }
+            auto coefH = [&](const I3 &m) -> std::string {
+                auto it = hname.find(m);
+                return it == hname.end() ? std::string() : it->second;
+            };
+            std::string h = pe.horner(0, I3{0, 0, 0}, coefH, hsup);
+            res.push_back(h.empty() ? "0.0f" : h);
+        }
+    }
     return res;
 }
 
 // Separable tensor-product evaluation (fold none, parallelepiped ROE).
 // Emits value and optionally gradient; gathers are emitted here.
-void emit_separable_body(Emitter &e, const Table &t, bool grad, std::string &fval, std::string g[3])
+// Value, gradient and Hessian of a tensor-product spline: per-axis weights and
+// their first and second derivatives, the gathers, then factorised sums
+// sum_j2 W2 sum_j1 W1 sum_j0 W0 c for each derivative pattern (orders 0-2 per
+// axis, total at most 2).
+void emit_separable_hess(Emitter &e, const Table &t, std::string &fval, std::string g[3], std::string h[6])
 {
     auto &o = e.o;
     const int D = t.dim;
+    for (int i = 0; i < D; ++i) {
+        const Axis &ax = t.sep[i];
+        o << "    const float su" << i << " = y" << i << " - " << flit(ax.center) << ";\n";
+        const int nc = ax.degree + 1;
+        for (size_t j = 0; j < ax.sites.size(); ++j) {
+            for (int der = 0; der <= 2; ++der) {
+                // d^der/du^der of sum_d coef[d] u^d by Horner
+                std::string acc;
+                for (int d = ax.degree; d >= der; --d) {
+                    double fac = 1.0;
+                    for (int q = 0; q < der; ++q) fac *= (double)(d - q);
+                    const std::string c = flit(ax.coef[j * nc + d] * fac);
+                    if (acc.empty()) acc = c;
+                    else {
+                        acc = "fmaf(" + acc + ", su" + std::to_string(i) + ", " + c + ")";
+                        e.fma++;
+                    }
+                }
+                if (acc.empty()) acc = "0.0f";
+                o << "    const float w" << der << "_" << i << "_" << j << " = " << acc << ";\n";
+            }
+        }
+    }
+    const int n[3] = {(int)t.sep[0].sites.size(), D > 1 ? (int)t.sep[1].sites.size() : 1,
+                      D > 2 ? (int)t.sep[2].sites.size() : 1};
+    std::vector<I3> sites;
+    for (int j2 = 0; j2 < n[2]; ++j2)
+        for (int j1 = 0; j1 < n[1]; ++j1)
+            for (int j0 = 0; j0 < n[0]; ++j0)
+                sites.push_back({t.sep[0].sites[j0], D > 1 ? t.sep[1].sites[j1] : 0, D > 2 ? t.sep[2].sites[j2] : 0});
+    int reach = 0;
+    for (auto &sv : sites)
+        for (int i = 0; i < D; ++i) reach = std::max(reach, std::abs(sv[i]));
+    emit_gathers(e, t, sites, reach, "a.coef", false, true, 0, 0);
+    auto cidx = [&](int j0, int j1, int j2) { return (j2 * n[1] + j1) * n[0] + j0; };
+    // derivative patterns (d0, d1, d2): f, g, h in output order
+    std::vector<I3> pats = {{0, 0, 0}};
+    for (int i = 0; i < D; ++i) { I3 p{0, 0, 0}; p[i] = 1; pats.push_back(p); }
+    const int NH = D == 3 ? 6 : 3;
+    for (int q = 0; q < NH; ++q) {
+        const int i = D == 3 ? HI3[q] : HI2[q], j = D == 3 ? HJ3[q] : HJ2[q];
+        I3 p{0, 0, 0};
+        p[i] += 1;
+        p[j] += 1;
+        pats.push_back(p);
+    }
+    std::map<std::pair<int, int>, bool> t01;        // (d0, d1) partial sums needed
+    std::map<int, bool> t0;
+    for (auto &p : pats) { t0[p[0]] = true; t01[{p[0], p[1]}] = true; }
+    for (auto &kv : t0) {
+        const int d0 = kv.first;
+        for (int j2 = 0; j2 < n[2]; ++j2)
+            for (int j1 = 0; j1 < n[1]; ++j1) {
+                std::string acc;
+                for (int j0 = 0; j0 < n[0]; ++j0) {
+                    const std::string term = "w" + std::to_string(d0) + "_0_" + std::to_string(j0);
+                    const std::string c = "c" + std::to_string(cidx(j0, j1, j2));
+                    acc = acc.empty() ? term + " * " + c : "fmaf(" + term + ", " + c + ", " + acc + ")";
+                    e.fma++;
+                }
+                o << "    const float T" << d0 << "_" << j1 << "_" << j2 << " = " << acc << ";\n";
+            }
+    }
+    std::map<std::pair<int, int>, std::vector<std::string>> U;
+    for (auto &kv : t01) {
+        const int d0 = kv.first.first, d1 = kv.first.second;
+        for (int j2 = 0; j2 < n[2]; ++j2) {
+            std::string acc;
+            for (int j1 = 0; j1 < n[1]; ++j1) {
+                const std::string tn = "T" + std::to_string(d0) + "_" + std::to_string(j1) + "_" + std::to_string(j2);
+                if (D == 1) { acc = tn; break; }
+                const std::string term = "w" + std::to_string(d1) + "_1_" + std::to_string(j1);
+                acc = acc.empty() ? term + " * " + tn : "fmaf(" + term + ", " + tn + ", " + acc + ")";
+                e.fma++;
+            }
+            std::string nm = "U" + std::to_string(d0) + std::to_string(d1) + "_" + std::to_string(j2);
+            o << "    const float " << nm << " = " << acc << ";\n";
+            U[{d0, d1}].push_back(nm);
+        }
+    }
+    std::vector<std::string> outs;
+    for (auto &p : pats) {
+        const auto &uv = U[{p[0], p[1]}];
+        std::string acc;
+        if (D == 2) {
+            acc = uv[0];
+        } else {
+            for (int j2 = 0; j2 < n[2]; ++j2) {
+                const std::string term = "w" + std::to_string(p[2]) + "_2_" + std::to_string(j2);
+                acc = acc.empty() ? term + " * " + uv[j2] : "fmaf(" + term + ", " + uv[j2] + ", " + acc + ")";
+                e.fma++;
+            }
+        }
+        std::string nm = e.fresh("sh");
+        o << "    const float " << nm << " = " << acc << ";\n";
+        outs.push_back(nm);
+    }
+    fval = outs[0];
+    for (int i = 0; i < D; ++i) g[i] = outs[1 + i];
+    for (int q = 0; q < NH; ++q) h[q] = outs[1 + D + q];
+}
+
+void emit_separable_body(Emitter &e, const Table &t, int grad, std::string &fval, std::string g[3],
+                         std::string *h = nullptr)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    if (grad >= 2) {
+        emit_separable_hess(e, t, fval, g, h);
+        return;
+    }
     // per-axis weights (and derivatives) by Horner in u = y - center
     for (int i = 0; i < D; ++i) {
         const Axis &ax = t.sep[i];
@@ -838,6 +991,106 @@ void emit_eval_point(Emitter &e, const Table &t, const ls_variant &var, const St
         }
     } else {
         o << "    a.out[i] = " << fv << ";\n";
+    }
+    o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
+}
+
+// Value, gradient and Hessian at one point (Sec. 3: the derivatives of the
+// per-region polynomials; symmetry still applies).  In the folded frame the
+// Hessian of f is H_ref; on Cartesian axes a, b it is
+//     H[a][b] = s_a s_b H_ref[r(a)][r(b)]
+// with r(a) the reference axis that lands on axis a and s_a its sign.  Output
+// a.hess[i * NH + q] in the order xx yy zz xy xz yz (2D: xx yy xy); a.out and
+// a.grad may be null.
+void emit_eval_point_hess(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
+                          const std::string &fname)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    const int NH = D == 3 ? 6 : 3;
+    const int NO = 1 + D + NH;
+    o << "static __device__ __forceinline__ void " << fname << "(const LsEvalArgs& a, const long long i)\n{\n";
+    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride, CU = a.cunit;"
+         " (void)E1; (void)E2; (void)CS; (void)CU;\n";
+    o << "#define LS_OUT_OF_RANGE(V) { if (a.out) a.out[i] = (V); if (a.grad) {";
+    for (int i = 0; i < D; ++i) o << " a.grad[(size_t)i * " << D << " + " << i << "] = (V);";
+    o << " }";
+    for (int q = 0; q < NH; ++q) o << " a.hess[(size_t)i * " << NH << " + " << q << "] = (V);";
+    o << " }\n";
+    o << "  {\n";
+    emit_point_load(e, t, "return");
+    emit_classify(e, t);
+    std::vector<std::string> res(NO);
+    if (!t.sep.empty()) {
+        std::string g[3], h[6];
+        emit_separable_body(e, t, 2, res[0], g, h);
+        for (int i = 0; i < D; ++i) res[1 + i] = g[i];
+        for (int q = 0; q < NH; ++q) res[1 + D + q] = h[q];
+    } else {
+        emit_gathers(e, t, st.sites, reach, "a.coef", false, true, 0, 0);
+        const size_t K = t.ref.size();
+        if (K > 1 && var.branchy) {
+            for (int c = 0; c < NO; ++c) o << "    float hs" << c << " = 0.0f;\n";
+            for (size_t k = 0; k < K; ++k) {
+                o << "    " << (k ? "else " : "") << "if (psi == " << k << ") {\n";
+                auto r = emit_region_poly(e, t, (int)k, st.region_to_union[k], 2);
+                for (int c = 0; c < NO; ++c) o << "    hs" << c << " = " << r[c] << ";\n";
+                o << "    }\n";
+            }
+            for (int c = 0; c < NO; ++c) res[c] = "hs" + std::to_string(c);
+        } else {
+            std::vector<std::vector<std::string>> rr;
+            for (size_t k = 0; k < K; ++k) rr.push_back(emit_region_poly(e, t, (int)k, st.region_to_union[k], 2));
+            for (int c = 0; c < NO; ++c) {
+                std::string sel = rr[K - 1][c];
+                for (int k = (int)K - 2; k >= 0; --k)
+                    sel = "(psi == " + std::to_string(k) + ") ? " + rr[k][c] + " : (" + sel + ")";
+                o << "    const float hs" << c << " = " << sel << ";\n";
+                res[c] = "hs" + std::to_string(c);
+            }
+        }
+    }
+    o << "    if (a.out) a.out[i] = " << res[0] << ";\n";
+    const bool fold = t.fold == LS_FOLD_SIGNED_PERM;
+    o << "    if (a.grad) {\n";
+    for (int i = 0; i < D; ++i) {
+        if (fold) {
+            o << "    { const float gg = ";
+            for (int r = 0; r < D - 1; ++r) o << "(ri" << i << " == " << r << ") ? " << res[1 + r] << " : ";
+            o << res[1 + D - 1] << "; a.grad[(size_t)i * " << D << " + " << i << "] = ng" << i << " ? -gg : gg; }\n";
+        } else {
+            o << "    a.grad[(size_t)i * " << D << " + " << i << "] = " << res[1 + i] << ";\n";
+        }
+    }
+    o << "    }\n";
+    // reference Hessian entry of reference axes (r1, r2)
+    auto href = [&](int r1, int r2) {
+        if (r1 > r2) std::swap(r1, r2);
+        for (int q = 0; q < NH; ++q) {
+            const int qi = D == 3 ? HI3[q] : HI2[q], qj = D == 3 ? HJ3[q] : HJ2[q];
+            if (qi == r1 && qj == r2) return res[1 + D + q];
+        }
+        return std::string("0.0f");
+    };
+    for (int q = 0; q < NH; ++q) {
+        const int ca = D == 3 ? HI3[q] : HI2[q], cb = D == 3 ? HJ3[q] : HJ2[q];
+        if (fold) {
+            std::string sel;
+            for (int r1 = D - 1; r1 >= 0; --r1) {
+                std::string inner;
+                for (int r2 = D - 1; r2 >= 0; --r2)
+                    inner = inner.empty() ? href(r1, r2)
+                                          : "(ri" + std::to_string(cb) + " == " + std::to_string(r2) + ") ? " +
+                                                href(r1, r2) + " : (" + inner + ")";
+                sel = sel.empty() ? inner
+                                  : "(ri" + std::to_string(ca) + " == " + std::to_string(r1) + ") ? (" + inner +
+                                        ") : (" + sel + ")";
+            }
+            o << "    { const float hh = " << sel << "; a.hess[(size_t)i * " << NH << " + " << q << "] = (ng" << ca
+              << " ^ ng" << cb << ") ? -hh : hh; }\n";
+        } else {
+            o << "    a.hess[(size_t)i * " << NH << " + " << q << "] = " << href(ca, cb) << ";\n";
+        }
     }
     o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
 }
@@ -1644,6 +1897,17 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
         emit_eval_kernel(e, t, var, st, reach, false, g.info);
     }
     emit_eval_kernel(e, t, var, st, reach, true, g.info);
+    {
+        const int fma0 = e.fma;
+        const std::string pf = kname(t, "eval_hess_pt");
+        emit_eval_point_hess(e, t, var, st, reach, pf);
+        e.o << "extern \"C\" __global__ void __launch_bounds__(" << var.block << ") " << kname(t, "eval_hess")
+            << "(const LsEvalArgs a)\n{\n";
+        e.o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
+        e.o << "  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) " << pf
+            << "(a, i);\n}\n\n";
+        g.info.fma_hess = e.fma - fma0;
+    }
     emit_adjoint_atomic(e, t, var, st, reach, ADJ_ATOMIC);
     emit_adjoint_atomic(e, t, var, st, reach, ADJ_WARPAGG);
     emit_adjoint_atomic(e, t, var, st, reach, ADJ_FIXED);

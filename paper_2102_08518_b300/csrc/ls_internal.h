@@ -49,6 +49,7 @@ struct GenInfo {
     int reach = 0;          // max |component| of any site offset (bounds fast path)
     int fma_value = 0;
     int fma_grad = 0;
+    int fma_hess = 0;
     int n_reverse = 0;      // offsets between a coefficient and the ROE sites that can reach it
     int halo = 0;           // halo of the binning grid (storage units)
     double wmax = 1.0;      // bound on |w_j(u)| over the region of evaluation
@@ -70,11 +71,11 @@ Generated generate_batch(const std::vector<const Table *> &tables, const std::ve
 struct Module {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t eval = nullptr, eval_grad = nullptr, adj_atomic = nullptr, adj_warpagg = nullptr;
-    cudaKernel_t adj_fixed = nullptr;
+    cudaKernel_t adj_fixed = nullptr, eval_hess = nullptr;
     cudaKernel_t roe_key = nullptr, adj_gather = nullptr, batch_eval = nullptr;
     int regs_eval = 0;
     int blocks_per_sm_eval = 0, blocks_per_sm_grad = 0, blocks_per_sm_adj = 0, blocks_per_sm_warpagg = 0;
-    int blocks_per_sm_fixed = 0;
+    int blocks_per_sm_fixed = 0, blocks_per_sm_hess = 0;
     int blocks_per_sm_gather = 0;
 };
 

@@ -434,3 +434,111 @@ def test_morton_definition():
         # de-interleave with plain integer arithmetic
         back = [sum(((k >> (3 * bit + i)) & 1) << bit for bit in range(10)) for i in range(3)]
         assert back == [a, b, c]
+
+
+# --------------------------------------------------------------------------
+# Hessian (second derivatives of the per-region polynomials, Sec. 3)
+# --------------------------------------------------------------------------
+
+_HIDX = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+
+
+def _hmat(h):
+    H = np.zeros(h.shape[:-1] + (3, 3))
+    for k, (a, b) in enumerate(_HIDX):
+        H[..., a, b] = h[..., k]
+        H[..., b, a] = h[..., k]
+    return H
+
+
+def _d2_factors(name):
+    """Closed-form second derivatives of the centred 1D B-splines (orders 2-4)."""
+    def hat(t):
+        return np.maximum(0.0, 1.0 - np.abs(t)), -np.sign(t) * (np.abs(t) < 1), np.zeros_like(t)
+
+    def quad(t):
+        a = np.abs(t)
+        b = np.where(a <= 0.5, 0.75 - a * a, np.where(a <= 1.5, 0.5 * (1.5 - a) ** 2, 0.0))
+        db = np.where(a <= 0.5, -2 * t, np.where(a <= 1.5, -np.sign(t) * (1.5 - a), 0.0))
+        d2 = np.where(a <= 0.5, -2.0, np.where(a <= 1.5, 1.0, 0.0))
+        return b, db, d2
+
+    def cub(t):
+        a = np.abs(t)
+        b = np.where(a < 1, 2 / 3 - a * a + 0.5 * a ** 3, np.where(a < 2, (2 - a) ** 3 / 6, 0.0))
+        db = np.where(a < 1, -2 * t + 1.5 * t * a, np.where(a < 2, -0.5 * np.sign(t) * (2 - a) ** 2, 0.0))
+        d2 = np.where(a < 1, -2 + 3 * a, np.where(a < 2, 2 - a, 0.0))
+        return b, db, d2
+    return {"trilinear": hat, "triquadratic": quad, "tricubic": cub}[name]
+
+
+@pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic"])
+def test_hessian_of_tensor_products_matches_closed_form(name):
+    """The pair-wise derivative identity through the recurrence (kind 0 for the
+    tricubic too) equals the product of closed-form B-spline derivatives."""
+    spec = specs.tricubic(closed_form=False) if name == "tricubic" else specs.ALL_3D[name]()
+    rng = np.random.default_rng(21)
+    # the recurrence over 12 directions is slow: fewer points for the tricubic
+    y = rng.uniform(-2.2, 2.2, (12 if name == "tricubic" else 300, 3))
+    f = _d2_factors(name)
+    b, db, d2 = f(y)
+    want = np.zeros((len(y), 6))
+    for k, (p, q) in enumerate(_HIDX):
+        t = np.ones(len(y))
+        for i in range(3):
+            if p == q:
+                t *= d2[:, i] if i == p else b[:, i]
+            else:
+                t *= db[:, i] if i in (p, q) else b[:, i]
+        want[:, k] = t
+    got = oracle.phi_hess(spec, y)
+    assert np.max(np.abs(got - want)) < 1e-12
+
+
+@pytest.mark.parametrize("name", sorted(specs.ALL_3D))
+def test_hessian_matches_central_differences_of_gradient(name):
+    spec = specs.ALL_3D[name]()
+    rng = np.random.default_rng(22)
+    y = rng.uniform(-2.0, 2.0, (150, 3))
+    H = _hmat(oracle.phi_hess(spec, y))
+    fd = np.zeros_like(H)
+    fd2 = np.zeros_like(H)
+    for i in range(3):
+        for h, out in ((1e-5, fd), (2e-5, fd2)):
+            e = np.zeros(3)
+            e[i] = h
+            out[:, i, :] = (oracle.phi_grad(spec, y + e)[1] - oracle.phi_grad(spec, y - e)[1]) / (2 * h)
+    # points within a step of a knot plane show up as disagreeing differences
+    smooth = np.max(np.abs(fd - fd2), axis=(1, 2)) < 1e-6
+    assert smooth.sum() > 100
+    assert np.max(np.abs(H[smooth] - fd[smooth])) < 1e-8
+
+
+@pytest.mark.parametrize("name", ["tricubic", "triquadratic", "bcc_quintic", "fcc6"])
+def test_hessian_of_reproduced_quadratic_is_exact(name):
+    """Splines of order >= 3 reproduce quadratics up to a constant (the moment
+    defect), so the Hessian of sum_n p(n) phi(x - n) is the Hessian of p."""
+    spec = _small(ALL[name]())
+    sites = _sites_and_grid(spec)
+    rng = np.random.default_rng(23)
+    Q = rng.normal(size=(3, 3))
+    Q = Q + Q.T
+    vals = 0.5 * np.einsum("ni,ij,nj->n", sites, Q, sites) + sites @ rng.normal(size=3)
+    pts = _interior_pts(rng, 60, 4.5, 6.5 if spec.scale == 1 else 8.5)
+    H = _hmat(oracle.eval_sum_hess(spec, vals, pts))
+    assert np.max(np.abs(H - Q[None])) < 1e-9
+
+
+@pytest.mark.parametrize("name", ["bcc_quintic", "fcc6", "triquadratic"])
+def test_hessian_transforms_with_the_lattice_symmetries(name):
+    """phi(R y) = phi(y) for the signed permutations R, so H(R y) = R H(y) R^T."""
+    spec = specs.ALL_3D[name]()
+    rng = np.random.default_rng(24)
+    y = rng.uniform(-1.8, 1.8, (30, 3))
+    H = _hmat(oracle.phi_hess(spec, y))
+    for p, s in SIGNED_PERMS_3[::7]:
+        R = np.zeros((3, 3))
+        for i in range(3):
+            R[i, p[i]] = s[i]
+        HR = _hmat(oracle.phi_hess(spec, y @ R.T))
+        assert np.max(np.abs(HR - np.einsum("ij,njk,lk->nil", R, H, R))) < 1e-11
