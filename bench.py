@@ -587,6 +587,17 @@ def extra_paper_orders(torch, dev, vols, pts, outs):
         info = sp.info()
         res[name] = {"gpoints_s": round(n / ms / 1e6, 3), "ms": round(ms, 4), "sites": info["n_sites"],
                      "fma_per_point": info["fma_value"]}
+        if lat == "cc":
+            # the paper's linear texture fetch (Sec. 4.4.1): pairs of sites per hardware lerp
+            cl = relayout(c, 1, ext, to="coset", src="interleaved")
+            vl = Volume(sp, ext, cl)
+            vl.texture_sync()
+            mst = time_ms(torch, lambda: vl.eval_linear_fetch(p, out))
+            ref = vol.eval(p[: 1 << 20]).clone()
+            err = float((vl.eval_linear_fetch(p[: 1 << 20]) - ref).abs().max())
+            res[name]["linear_fetch_gpoints_s"] = round(n / mst / 1e6, 3)
+            res[name]["linear_fetch_max_abs_err"] = round(err, 6)
+            del cl, vl
         if all(e % b == 0 for e, b in zip(ext, (4, 2, 2))):
             # the same volume in 4x2x2 bricks (fewer cache lines per stencil)
             cb = relayout(c, ncos, ext, to="bricked", src="interleaved")

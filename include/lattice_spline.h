@@ -271,6 +271,21 @@ ls_status ls_eval_grad(ls_volume v, const float *pts, int64_t n, float *val, flo
 ls_status ls_eval_hess(ls_volume v, const float *pts, int64_t n, float *val, float *grad, float *hess,
                        ls_stream stream);
 /*
+ * The linear texture fetch of Sec. 4.4.1 for 3D tensor-product splines with
+ * FP32 coefficients in one array (trilinear, triquadratic, tricubic): pairs of
+ * neighbouring sites become one hardware-interpolated fetch at the weighted
+ * position, so at most 2 x 2 x 2 trilinear fetches replace the stencil's
+ * gathers.  ls_volume_texture_sync copies the volume's current coefficients
+ * into a texture (a 3D CUDA array owned by the volume, made on the first call;
+ * zero outside the arrays); call it again after changing them.
+ * ls_eval_linear_fetch evaluates from that copy: out[i] = f(pts[i]) within
+ * 6/256 ||c||_inf, because the texture unit interpolates with 8-bit fixed-point
+ * fractions (not for the 2e-6 accuracy of ls_eval).
+ * Errors: UNSUPPORTED (not such a spline or storage), INVALID_ARG (not synced).
+ */
+ls_status ls_volume_texture_sync(ls_volume v, ls_stream stream);
+ls_status ls_eval_linear_fetch(ls_volume v, const float *pts, int64_t n, float *out, ls_stream stream);
+/*
  * Same as ls_eval with HOST buffers: copies pts to the device, evaluates and
  * copies out back; returns when out is complete.  The points move in chunks
  * on two internal streams, so the host-to-device copy of one chunk, the kernels

@@ -87,6 +87,9 @@ SIGNATURES = {
                                     ctypes.c_void_p, ctypes.c_void_p]),
     "ls_eval_hess": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ls_volume_texture_sync": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "ls_eval_linear_fetch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
     "ls_eval_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_void_p]),
     "ls_eval_host_multi": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,

@@ -219,6 +219,20 @@ class Volume:
                                            _stream(stream)), "ls_eval_hess")
         return val, grad, hess
 
+    def texture_sync(self, stream=None):
+        """Copy the coefficients into the volume's texture (for eval_linear_fetch)."""
+        _abi.check(_abi.lib().ls_volume_texture_sync(self.handle, _stream(stream)), "ls_volume_texture_sync")
+
+    def eval_linear_fetch(self, pts: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """f(pts) by hardware-interpolated texture fetches (tensor-product splines;
+        within 6/256 of max|c|, see ls_eval_linear_fetch)."""
+        pts = _check_pts(pts, self.spline.dim)
+        if out is None:
+            out = torch.empty(pts.shape[0], device=pts.device, dtype=torch.float32)
+        _abi.check(_abi.lib().ls_eval_linear_fetch(self.handle, _ptr(pts), pts.shape[0], _ptr(out), _stream(stream)),
+                   "ls_eval_linear_fetch")
+        return out
+
     def eval_host(self, pts_host, out_host, stream=None):
         """Host buffers in, host buffer out (copies inside the call)."""
         n = pts_host.shape[0]

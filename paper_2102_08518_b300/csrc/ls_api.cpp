@@ -573,6 +573,8 @@ ls_status ls_volume_destroy(ls_volume v)
         if (v->hev[i]) cudaEventDestroy(v->hev[i]);
     if (v->owned && v->coef) cudaFree(v->coef);
     if (v->stage) cudaFree(v->stage);
+    if (v->tex) cudaDestroyTextureObject(v->tex);
+    if (v->tex_array) cudaFreeArray(v->tex_array);
     delete v;
     return LS_OK;
 }

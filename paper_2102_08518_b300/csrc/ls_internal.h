@@ -112,6 +112,10 @@ struct ls_volume_s {
     size_t stage_bytes = 0;
     cudaStream_t hs[2] = {nullptr, nullptr};
     cudaEvent_t hev[3] = {nullptr, nullptr, nullptr};
+    // texture copy for ls_eval_linear_fetch, made by ls_volume_texture_sync
+    cudaArray_t tex_array = nullptr;
+    cudaTextureObject_t tex = 0;
+    bool tex_ready = false;
 };
 
 // Address of coefficient (coset j, per-coset linear index q) is
