@@ -371,7 +371,7 @@ def run_gpu(args):
         result["extras"] = extras
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample, _ = oracle_leg(coef_np, pts_np)
-        result["cpu_baseline"] = {"value": round(v, 6), "unit": "Gpoints/s", "cores": cores, "kind": "oracle",
+        result["cpu_baseline"] = {"value": float(f"{v:.4g}"), "unit": "Gpoints/s", "cores": cores, "kind": "oracle",
                                   "sample": sample}
     if world > 1:
         dist.destroy_process_group()
@@ -490,14 +490,18 @@ def extra_fcc(torch, dev, vols, pts, outs):
 
 def extra_batched(torch, dev, vols, pts, outs):
     """64 volumes (edges {32..256}, mixed splines), BF16 / FP16 storage, one persistent
-    launch replayed from a CUDA graph, against plain FP32 per-volume launches."""
-    from paper_2102_08518_b300.api import Plan, Spline, Volume
+    launch replayed from a CUDA graph, against plain FP32 per-volume launches;
+    BCC and FCC volumes with interleaved cosets."""
+    from paper_2102_08518_b300.api import Plan, Spline, Volume, relayout
     recipe = workloads.batch_recipe(64, seed=0)
     total = sum(it.n_points for it in recipe)
-    coefs, ptsl, outl, exts = [], [], [], []
+    coefs, ptsl, outl, exts, lays = [], [], [], [], []
     for it in recipe:
         lat = workloads.SPLINE_LATTICE[it.spline]
-        coefs.append(workloads.coef_uniform_torch(lat, it.ext, seed=it.seed))
+        ncos = len(workloads.LATTICES[lat][2])
+        c = workloads.coef_uniform_torch(lat, it.ext, seed=it.seed)
+        lays.append("interleaved" if ncos > 1 else "coset")
+        coefs.append(relayout(c, ncos, it.ext, to="interleaved") if ncos > 1 else c)
         lo, hi = workloads.inner_box(it.spline, it.ext)
         ptsl.append(workloads.points_uniform_torch(it.n_points, lo, hi, seed=it.seed + 1))
         outl.append(torch.empty(it.n_points, device=dev))
@@ -505,14 +509,14 @@ def extra_batched(torch, dev, vols, pts, outs):
     res = {"workload": f"64 volumes, {total} points, edges {{32..256}}, 4 spline types", "points": total}
     # plain FP32: one launch per volume
     sp32 = {n: Spline(n, "f32") for n in set(it.spline for it in recipe)}
-    v32 = [Volume(sp32[it.spline], e, c) for it, e, c in zip(recipe, exts, coefs)]
+    v32 = [Volume(sp32[it.spline], e, c, layout=l) for it, e, c, l in zip(recipe, exts, coefs, lays)]
     t32 = time_ms(torch, lambda: [v.eval(p, o) for v, p, o in zip(v32, ptsl, outl)], reps=3)
     res["plain_f32_per_volume_launches_gpoints_s"] = round(total / t32 / 1e6, 3)
     ref = [o.clone() for o in outl]
     for dt, tdt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
         spd = {n: Spline(n, dt) for n in sp32}
         cd = [c.to(tdt) for c in coefs]
-        vd = [Volume(spd[it.spline], e, c) for it, e, c in zip(recipe, exts, cd)]
+        vd = [Volume(spd[it.spline], e, c, layout=l) for it, e, c, l in zip(recipe, exts, cd, lays)]
         plan = Plan(vd, ptsl, outl, tile=0)
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
@@ -613,26 +617,29 @@ def extra_paper_orders(torch, dev, vols, pts, outs):
 
 
 def extra_cg(torch, dev, vols, pts, outs):
-    """CG least-squares fits with 2^22 Gaussian samples: ms per iteration."""
+    """CG least-squares fits with 2^22 Gaussian samples: ms per iteration with the
+    atomic adjoint and the two deterministic ones (binned, fixed point);
+    tricubic on bricked coefficients, BCC quintic with interleaved cosets."""
     from paper_2102_08518_b300.api import Spline, Volume, cg_fit
     res = {}
-    for name, ext in (("tricubic", (128, 128, 128)), ("bcc_quintic", (128, 128, 128))):
+    for name, ext, lay in (("tricubic", (128, 128, 128), "bricked"), ("bcc_quintic", (128, 128, 128), "interleaved")):
         lat = workloads.SPLINE_LATTICE[name]
         lo, hi = workloads.bounding_box(lat, ext)
         p_np, y_np = workloads.gaussian_samples(1 << 22, lo, hi, seed=3)
         p = torch.from_numpy(p_np).to(dev)
         y = torch.from_numpy(y_np).to(dev)
-        for det in (False, True):
-            vol = Volume(Spline(name, "f32"), ext, torch.zeros(len(workloads.LATTICES[lat][2]) * 128 ** 3,
-                                                              device=dev))
+        sp = Spline(name, "f32", brick=int(lay == "bricked"))
+        for tag, det in (("atomic", False), ("det_binned", True), ("det_fixed", "fixed")):
+            vol = Volume(sp, ext, torch.zeros(len(workloads.LATTICES[lat][2]) * 128 ** 3, device=dev), layout=lay)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             it, hist = cg_fit(vol, p, y, lam=1e-6, max_iter=10, rel_tol=0.0, deterministic=det)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
-            res[f"{name}_{'det' if det else 'atomic'}"] = {"ms_per_iter": round(1e3 * dt / max(it, 1), 3),
-                                                           "iters": it, "resid_ratio": float(hist[-1] / hist[0])}
-    res["workload"] = "tricubic 128^3 and bcc_quintic 2x128^3, 2^22 samples of exp(-|x-c|^2/400)+0.01N"
+            res[f"{name}_{tag}"] = {"ms_per_iter": round(1e3 * dt / max(it, 1), 3), "iters": it,
+                                    "resid_ratio": float(hist[-1] / hist[0])}
+    res["workload"] = ("tricubic 128^3 (bricked) and bcc_quintic 2x128^3 (interleaved), 2^22 samples of "
+                       "exp(-|x-c|^2/400)+0.01N")
     return res
 
 
@@ -648,13 +655,14 @@ def run_reference(args):
         vals.append(v)
     value = statistics.median(vals)
     ms = 1e3 * (N_UNIFORM * 2 + N_RAYS * RAY_STEPS * 2) / (value * 1e9)
-    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gpoints/s",
+    value = float(f"{value:.4g}")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gpoints/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": round(value, 6), "unit": "Gpoints/s", "cores": cores, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "Gpoints/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
-            "e2e": {"value": round(value, 6), "unit": "Gpoints/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": value, "unit": "Gpoints/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
 

@@ -40,7 +40,7 @@ def _case(name, ext, nsamp):
     return _CASES[key]
 
 
-@pytest.mark.parametrize("deterministic", [False, True])
+@pytest.mark.parametrize("deterministic", [False, True, "fixed"])
 @pytest.mark.parametrize("name,ext,nsamp", [("tricubic", (16, 16, 16), 1 << 15),
                                             ("bcc_quintic", (8, 8, 8), 1 << 13)])
 def test_cg_fit_matches_exact_least_squares(name, ext, nsamp, deterministic):
@@ -60,7 +60,8 @@ def test_cg_fit_matches_exact_least_squares(name, ext, nsamp, deterministic):
     assert np.max(np.abs(A @ got - A @ want)) <= 1e-3 * np.max(np.abs(A @ want))
 
 
-def test_cg_fit_deterministic_is_bitwise_reproducible():
+@pytest.mark.parametrize("mode", [True, "fixed"])
+def test_cg_fit_deterministic_is_bitwise_reproducible(mode):
     from paper_2102_08518_b300.api import Spline, Volume, cg_fit
     name, ext = "bcc_quintic", (8, 8, 8)
     lo, hi = workloads.bounding_box("bcc", ext)
@@ -69,7 +70,7 @@ def test_cg_fit_deterministic_is_bitwise_reproducible():
     for _ in range(2):
         vol = Volume(Spline(name, "f32"), ext, torch.zeros(2 * 8 ** 3, device="cuda"))
         cg_fit(vol, torch.from_numpy(pts).cuda(), torch.from_numpy(y).cuda(), lam=1e-4, max_iter=30,
-               rel_tol=0.0, deterministic=True)
+               rel_tol=0.0, deterministic=mode)
         out.append(vol.coef.clone())
     assert torch.equal(out[0], out[1])
 
