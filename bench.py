@@ -643,6 +643,53 @@ def extra_cg(torch, dev, vols, pts, outs):
     return res
 
 
+PROFILE_CASES = ("fcc6_eval", "quintic_adjoint_atomic", "quintic_adjoint_fixed", "quintic_hessian",
+                 "tricubic_linear_fetch")
+
+
+def run_profile_case(name: str):
+    """One case for a profiler: set up, then launch its kernel three times.
+    Inputs exceed L2 (2^24 points, 201 MB) so DRAM counters mean something;
+    a few GB at most on the device.  Prints one JSON line with the kernel times."""
+    import torch
+    from paper_2102_08518_b300.api import Spline, Volume, relayout
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = 1 << 24
+    if name == "fcc6_eval":
+        ext = (128, 128, 128)
+        c = relayout(workloads.coef_uniform_torch("fcc", ext, seed=0), 4, ext, to="interleaved")
+        vol = Volume(Spline("fcc6", "f32"), ext, c, layout="interleaved")
+        lo, hi = workloads.inner_box("fcc6", ext)
+        p = workloads.points_uniform_torch(n, lo, hi, seed=5)
+        out = torch.empty(n, device=dev)
+        fn = lambda: vol.eval(p, out)
+    elif name.startswith("quintic_"):
+        coef_np, pts_np = make_inputs()
+        c = relayout(torch.from_numpy(coef_np).to(dev), 2, EXT, to="interleaved")
+        vol = Volume(Spline("bcc_quintic", "f32"), EXT, c, layout="interleaved")
+        p = torch.from_numpy(pts_np["uniform"]).to(dev)
+        g = torch.randn(n, device=dev, generator=torch.Generator(device=dev).manual_seed(11))
+        dc = torch.zeros(vol.n_coef, device=dev)
+        if name == "quintic_hessian":
+            fn = lambda: vol.eval_hess(p)
+        else:
+            det = "fixed" if name.endswith("fixed") else False
+            fn = lambda: vol.adjoint(p, g, dcoef=dc, deterministic=det)
+    elif name == "tricubic_linear_fetch":
+        ext = (128, 128, 128)
+        vol = Volume(Spline("tricubic", "f32"), ext, workloads.coef_uniform_torch("cc", ext, seed=1))
+        vol.texture_sync()
+        lo, hi = workloads.inner_box("tricubic", ext)
+        p = workloads.points_uniform_torch(n, lo, hi, seed=2)
+        out = torch.empty(n, device=dev)
+        fn = lambda: vol.eval_linear_fetch(p, out)
+    else:
+        raise ValueError(name)
+    ms = [time_ms(torch, fn, reps=1, warm=0) for _ in range(3)]
+    return {"profile_case": name, "ms": [round(v, 4) for v in ms], "points": n}
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
@@ -676,8 +723,13 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--layout", default=LAYOUT, choices=["coset", "interleaved", "bricked"],
                     help="coefficient layout of the step's volumes")
+    ap.add_argument("--only", default=None, choices=PROFILE_CASES,
+                    help="run one small case for a profiler instead of the benchmark")
     args = ap.parse_args()
     globals()["LAYOUT"] = args.layout
+    if args.only:
+        print(json.dumps(run_profile_case(args.only)))
+        return
     if args.impl == "ours" and args.warmup < 3:
         args.warmup = 3
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)
