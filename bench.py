@@ -644,7 +644,7 @@ def extra_cg(torch, dev, vols, pts, outs):
 
 
 PROFILE_CASES = ("fcc6_eval", "quintic_adjoint_atomic", "quintic_adjoint_fixed", "quintic_hessian",
-                 "tricubic_linear_fetch")
+                 "tricubic_linear_fetch", "morton_sort")
 
 
 def run_profile_case(name: str):
@@ -676,6 +676,13 @@ def run_profile_case(name: str):
         else:
             det = "fixed" if name.endswith("fixed") else False
             fn = lambda: vol.adjoint(p, g, dcoef=dc, deterministic=det)
+    elif name == "morton_sort":
+        from paper_2102_08518_b300.api import morton_scratch_bytes, morton_sort
+        n = 1 << 26
+        lo, hi = workloads.inner_box("fcc6", (128, 128, 128))
+        p = workloads.points_uniform_torch(n, lo, hi, seed=5)
+        scratch = torch.empty(morton_scratch_bytes(n), dtype=torch.uint8, device=dev)
+        fn = lambda: morton_sort(p, cell=1.0, scratch=scratch)
     elif name == "tricubic_linear_fetch":
         ext = (128, 128, 128)
         vol = Volume(Spline("tricubic", "f32"), ext, workloads.coef_uniform_torch("cc", ext, seed=1))

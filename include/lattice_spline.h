@@ -366,7 +366,7 @@ size_t ls_morton_scratch_bytes(int64_t n);
  * callers that must not allocate device memory while they run (a framework
  * whose caching allocator owns the device memory, a latency-bound loop that
  * cannot absorb cudaMalloc/cudaFree, a fixed up-front memory budget).  Its
- * scratch is one static 3.25 MiB device array compiled into the library, which
+ * scratch is one static 3.75 MiB device array compiled into the library, which
  * every GPU that loads the library holds until the process exits.
  *  - n is limited to 262144 (2^18) points; larger n returns LS_ERR_INVALID_ARG
  *    with a message.  It calls no cudaMalloc, cudaFree or allocating routine.

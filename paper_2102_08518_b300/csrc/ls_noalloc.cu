@@ -18,7 +18,7 @@
 namespace {
 
 constexpr long long kMaxPoints = 1LL << 18;        // largest n accepted
-constexpr size_t kScratchBytes = 3407872;           // >= ls_morton_scratch_bytes(kMaxPoints) (3.25 MiB)
+constexpr size_t kScratchBytes = 3932160;           // >= ls_morton_scratch_bytes(kMaxPoints) (3.75 MiB)
 constexpr int kMaxDevices = 64;
 
 // The scratch itself.  In host code its name is only a host-side stand-in for

@@ -1,14 +1,17 @@
 // Stable LSD radix sort of (uint32 key, int32 value) pairs, Morton keys of
 // points, row permutation, and a random-gather probe for the gather roofline.
 //
-// One radix pass (8-bit digit):
+// One radix pass (digits of RB bits, 8 or 10):
 //   1. hist:    each block counts the digits of its tile -> hist[digit * nblk + blk]
 //   2. scan:    exclusive prefix sum over hist (digit-major, so the offsets of
 //               digit d in block b follow all smaller digits and all earlier
 //               blocks of digit d: a stable global order)
 //   3. scatter: each warp ranks its keys in input order with __match_any_sync
-//               (peers with the same digit), warps are combined by a per-digit
-//               prefix over warps, keys go to offset + rank.
+//               (peers with the same digit); the lowest peer adds the group's
+//               size to the warp's digit counter with one shared-memory atomic
+//               and broadcasts the old value (atomics of one warp on one address
+//               keep program order, so ranks stay stable); warps are combined by
+//               a per-digit prefix over warps, keys go to offset + rank.
 #include <cstdint>
 
 #include "ls_kernels.h"
@@ -20,11 +23,12 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 16;                       // keys per thread
 constexpr int kTile = kThreads * kItems;         // 4096 keys per block
-constexpr int kBins = 256;
 
+template <int RB>
 __global__ void __launch_bounds__(kThreads) hist_kernel(const uint32_t *keys, long long n, int shift,
                                                          uint32_t *hist, int nblk)
 {
+    constexpr int kBins = 1 << RB;
     __shared__ uint32_t h[kBins];
     for (int b = threadIdx.x; b < kBins; b += kThreads) h[b] = 0;
     __syncthreads();
@@ -117,18 +121,22 @@ __global__ void __launch_bounds__(1024) scan_down(const uint32_t *in, long long 
 // Ranks every key of the tile (stable), stages the tile in shared memory in
 // digit order, then writes each digit's run to its global offset: consecutive
 // threads write consecutive addresses.
+template <int RB>
 __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint32_t *keys, const int32_t *vals, long long n,
                                                             int shift, const uint32_t *offs, int nblk,
                                                             uint32_t *keys_out, int32_t *vals_out)
 {
-    static_assert(kThreads == kBins, "one thread per digit in the digit scans");
-    __shared__ uint32_t whist[kWarps][kBins];
-    __shared__ uint32_t bstart[kBins];
-    __shared__ uint32_t goff[kBins];
-    __shared__ uint32_t skey[kTile];
-    __shared__ int32_t sval[kTile];
+    constexpr int kBins = 1 << RB;
+    constexpr int kPer = kBins / kThreads;         // digits per thread in the digit scans
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *whist = sm;                          // [kWarps][kBins]
+    uint32_t *bstart = whist + kWarps * kBins;     // [kBins]
+    uint32_t *goff = bstart + kBins;               // [kBins]
+    uint32_t *tsum = goff + kBins;                 // [kThreads] scan scratch
+    uint32_t *skey = tsum + kThreads;              // [kTile]
+    int32_t *sval = (int32_t *)(skey + kTile);     // [kTile]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int b = lane; b < kBins; b += 32) whist[warp][b] = 0;
+    for (int b = lane; b < kBins; b += 32) whist[warp * kBins + b] = 0;
     __syncwarp();
     // warp w owns the contiguous keys [base + w*32*kItems, ... + 32*kItems), rounds of 32
     const long long tile0 = (long long)blockIdx.x * kTile;
@@ -144,44 +152,50 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint32_t *keys,
         val[it] = valid ? vals[i] : 0;
         const uint32_t d = (key[it] >> shift) & (kBins - 1);
         const unsigned active = __ballot_sync(0xFFFFFFFFu, valid);
-        unsigned peers = __match_any_sync(0xFFFFFFFFu, valid ? d : 0xFFFFFFFFu) & active;
-        uint32_t before = valid ? whist[warp][d] : 0u;
-        __syncwarp();
-        rank[it] = 0;
-        if (valid) {
-            rank[it] = before + __popc(peers & lt);
-            if ((peers & lt) == 0u) whist[warp][d] = before + __popc(peers);
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, valid ? d : 0xFFFFFFFFu) & active;
+        const int leader = peers ? __ffs(peers) - 1 : 0;
+        uint32_t before = 0u;
+        if (valid && lane == leader) before = atomicAdd(&whist[warp * kBins + d], (uint32_t)__popc(peers));
+        before = __shfl_sync(0xFFFFFFFFu, before, leader);
+        rank[it] = valid ? before + __popc(peers & lt) : 0u;
+    }
+    __syncthreads();
+    // per digit: warp prefix inside the block, block total
+    uint32_t tot[kPer];
+    for (int q = 0; q < kPer; ++q) {
+        const int b = threadIdx.x * kPer + q;
+        uint32_t run = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = whist[w * kBins + b];
+            whist[w * kBins + b] = run;
+            run += c;
         }
-        __syncwarp();
+        tot[q] = run;
+        goff[b] = offs[(size_t)b * nblk + blockIdx.x];
     }
+    // exclusive scan of the block totals over digits: per-thread sums, then
+    // Hillis-Steele over threads
+    uint32_t mine = 0;
+    for (int q = 0; q < kPer; ++q) mine += tot[q];
+    tsum[threadIdx.x] = mine;
     __syncthreads();
-    // per digit (thread = digit): warp prefix inside the block, block total
-    const int b = threadIdx.x;
-    uint32_t run = 0;
-    for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = whist[w][b];
-        whist[w][b] = run;
-        run += c;
-    }
-    bstart[b] = run;
-    goff[b] = offs[(size_t)b * nblk + blockIdx.x];
-    __syncthreads();
-    // exclusive scan of the block totals over digits (Hillis-Steele, inclusive then shift)
-    for (int off = 1; off < kBins; off <<= 1) {
-        const uint32_t v = b >= off ? bstart[b - off] : 0u;
+    for (int off = 1; off < kThreads; off <<= 1) {
+        const uint32_t v = threadIdx.x >= off ? tsum[threadIdx.x - off] : 0u;
         __syncthreads();
-        bstart[b] += v;
+        tsum[threadIdx.x] += v;
         __syncthreads();
     }
-    const uint32_t incl = bstart[b];
-    __syncthreads();
-    bstart[b] = incl - run;
+    uint32_t run = tsum[threadIdx.x] - mine;
+    for (int q = 0; q < kPer; ++q) {
+        bstart[threadIdx.x * kPer + q] = run;
+        run += tot[q];
+    }
     __syncthreads();
     for (int it = 0; it < kItems; ++it) {
         long long i = base + (long long)it * 32 + lane;
         if (i < n) {
             const uint32_t d = (key[it] >> shift) & (kBins - 1);
-            const uint32_t lp = bstart[d] + whist[warp][d] + rank[it];
+            const uint32_t lp = bstart[d] + whist[warp * kBins + d] + rank[it];
             skey[lp] = key[it];
             sval[lp] = val[it];
         }
@@ -195,6 +209,12 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint32_t *keys,
         keys_out[dst] = k;
         vals_out[dst] = sval[lp];
     }
+}
+
+template <int RB>
+constexpr size_t scatter_smem()
+{
+    return ((size_t)kWarps * (1 << RB) + 2 * (1 << RB) + kThreads + 2 * (size_t)kTile) * 4;
 }
 
 __global__ void iota_kernel(int32_t *v, long long n)
@@ -279,10 +299,12 @@ int nblocks_for(long long n) { return (int)((n + kTile - 1) / kTile); }
 
 }  // namespace
 
+constexpr int kMaxBins = 1024;
+
 size_t sort_scratch_bytes(long long n)
 {
     const long long nblk = nblocks_for(n);
-    const long long nh = nblk * kBins;
+    const long long nh = nblk * kMaxBins;
     const long long nparts = (nh + kScanChunk - 1) / kScanChunk;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     return al(n * 4) * 2 + al(nh * 4) * 2 + al(nparts * 4) + 256;
@@ -292,9 +314,16 @@ cudaError_t radix_sort_pairs(uint32_t *keys, int32_t *vals, long long n, int nbi
 {
     if (n <= 1) return cudaSuccess;
     const int nblk = nblocks_for(n);
-    const long long nh = (long long)nblk * kBins;
+    // 10-bit digits when that saves a pass (e.g. 30-bit Morton keys: 3 passes, not 4)
+    const int rb = ((nbits + 9) / 10 < (nbits + 7) / 8) ? 10 : 8;
+    const long long nh = (long long)nblk * (1 << rb);
     const long long nparts = (nh + kScanChunk - 1) / kScanChunk;
     if (nparts > 8192) return cudaErrorInvalidValue;
+    cudaError_t ea = rb == 10 ? cudaFuncSetAttribute(scatter_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)scatter_smem<10>())
+                              : cudaFuncSetAttribute(scatter_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)scatter_smem<8>());
+    if (ea != cudaSuccess) return ea;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     char *p = (char *)scratch;
     uint32_t *k2 = (uint32_t *)p;
@@ -308,14 +337,18 @@ cudaError_t radix_sort_pairs(uint32_t *keys, int32_t *vals, long long n, int nbi
     uint32_t *part = (uint32_t *)p;
     uint32_t *ks = keys, *kd = k2;
     int32_t *vs = vals, *vd = v2;
-    int passes = (nbits + 7) / 8;
+    int passes = (nbits + rb - 1) / rb;
     for (int ps = 0; ps < passes; ++ps) {
-        const int shift = 8 * ps;
-        hist_kernel<<<nblk, kThreads, 0, st>>>(ks, n, shift, hist, nblk);
+        const int shift = rb * ps;
+        if (rb == 10) hist_kernel<10><<<nblk, kThreads, 0, st>>>(ks, n, shift, hist, nblk);
+        else hist_kernel<8><<<nblk, kThreads, 0, st>>>(ks, n, shift, hist, nblk);
         scan_reduce<<<(unsigned)nparts, 1024, 0, st>>>(hist, nh, part);
         scan_parts<<<1, 1024, 0, st>>>(part, (int)nparts);
         scan_down<<<(unsigned)nparts, 1024, 0, st>>>(hist, nh, part, offs);
-        scatter_kernel<<<nblk, kThreads, 0, st>>>(ks, vs, n, shift, offs, nblk, kd, vd);
+        if (rb == 10)
+            scatter_kernel<10><<<nblk, kThreads, scatter_smem<10>(), st>>>(ks, vs, n, shift, offs, nblk, kd, vd);
+        else
+            scatter_kernel<8><<<nblk, kThreads, scatter_smem<8>(), st>>>(ks, vs, n, shift, offs, nblk, kd, vd);
         uint32_t *tk = ks; ks = kd; kd = tk;
         int32_t *tv = vs; vs = vd; vd = tv;
     }
