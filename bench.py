@@ -314,6 +314,21 @@ def run_gpu(args):
                 "counters_from": cfile,
                 "kernel_hash": kernel_hash(splines["bcc_quintic"].source(), kname),
                 "l2_sector_bytes_per_launch": counters.get("l2_sector_bytes_per_launch") if counters else None}
+    # the same kernel read against HBM: its coefficient bytes (n_sites x 4 B per
+    # point) plus the point stream, at the measured copy bandwidth
+    hbm_peak, hbm_src = 6400.0, "fallback (no MEASURED_PEAKS.json)"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_peak, hbm_src = float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured copy)"
+    except (OSError, ValueError, KeyError):
+        pass
+    coef_gbs = (4 * info["n_sites"] + 16) * N_UNIFORM / (case_ms[2] * 1e-3) / 1e9
+    roofline_hbm = {"bound": "hbm", "kernel": kname, "achieved": round(coef_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(coef_gbs / hbm_peak, 4),
+                    "bytes_per_point": 4 * info["n_sites"] + 16,
+                    "note": "coefficient bytes per point (32 sites x 4 B) + 16 B point stream, if every coefficient "
+                            "came from HBM; the volume is L2-resident, so the binding roof is the L2 one",
+                    "peak_source": hbm_src}
     roofline_alu = {"bound": "alu", "kernel": kname, "achieved": dom["fp32_fma_tflops"], "peak": round(peak_fma, 2),
                     "unit": "TFLOP/s", "frac": round(dom["fp32_fma_tflops"] / peak_fma, 4),
                     "flops_per_point": 2 * info["fma_value"], "regs": info["regs_eval"],
@@ -352,7 +367,8 @@ def run_gpu(args):
                          "coef_layout": LAYOUT,
                          "l2": "points 201 MB per set > 126 MB L2 (inputs larger than L2); coefficient volume "
                                "16 MiB L2-resident by design", "parallelism": f"replicas x{world}"},
-              "per_case": per_case, "roofline": roofline, "roofline_alu": roofline_alu, "e2e": e2e,
+              "per_case": per_case, "roofline": roofline, "roofline_alu": roofline_alu, "roofline_hbm": roofline_hbm,
+              "e2e": e2e,
               "autotuned": {f"{sp}/{ps}": {"variant": tuned[(sp, ps)].variant,
                                             "key": tune_key(sp, "f32", EXT, [pts[ps]], f"bcc_step_{ps}", LAYOUT)}
                             for sp, ps in CASES},
@@ -448,8 +464,10 @@ def extra_fwd_bwd(torch, dev, vols, pts, outs):
 
 
 def extra_fcc(torch, dev, vols, pts, outs):
-    """FCC 4x128^3, 2^26 uniform points: unsorted vs Morton-sorted evaluation and gradient."""
-    from paper_2102_08518_b300.api import Spline, Volume, morton_sort, permute_rows, relayout
+    """FCC 4x128^3, 2^26 uniform points: unsorted vs Morton-sorted evaluation and gradient
+    (the evaluation kernel variant autotuned on the unsorted points)."""
+    from paper_2102_08518_b300.api import Spline, Volume, autotune, morton_sort, permute_rows, relayout, \
+        TUNE_CANDIDATES_SMALL
     ext = (128, 128, 128)
     coef_cm = workloads.coef_uniform_torch("fcc", ext, seed=0)
     lo, hi = workloads.inner_box("fcc6", ext)
@@ -461,13 +479,15 @@ def extra_fcc(torch, dev, vols, pts, outs):
     del vol_cm
     coef = relayout(coef_cm, 4, ext, to="interleaved")
     del coef_cm
-    vol = Volume(Spline("fcc6", "f32"), ext, coef, layout="interleaved")
+    sp = autotune("fcc6", "f32", ext, coef, [p], candidates=TUNE_CANDIDATES_SMALL, tag="fcc_uniform",
+                  layout="interleaved")
+    vol = Volume(sp, ext, coef, layout="interleaved")
     t_uns = time_ms(torch, lambda: vol.eval(p, out), reps=5)
     t_grad = time_ms(torch, lambda: vol.eval_grad(p, want_value=True), reps=3)
     res = {"workload": "fcc6 4x128^3 (256^3 box), 2^26 uniform points, interleaved cosets",
            "unsorted_coset_major_gpoints_s": round(n / t_cm / 1e6, 3),
            "unsorted_gpoints_s": round(n / t_uns / 1e6, 3),
-           "unsorted_value_grad_gpoints_s": round(n / t_grad / 1e6, 3)}
+           "unsorted_value_grad_gpoints_s": round(n / t_grad / 1e6, 3), "variant": sp.variant}
     best = None
     for cell in (1.0, 2.0, 4.0, 8.0):                 # sort granularity (Morton cell edge)
         t_sort = time_ms(torch, lambda: morton_sort(p, cell=cell), reps=3, warm=1)
@@ -723,7 +743,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
