@@ -93,3 +93,59 @@ def test_calls_with_null_handles_fail_cleanly():
     assert L.ls_eval(None, None, 0, None, None) == 1
     assert L.ls_spline_destroy(None) == 0
     assert L.ls_volume_destroy(None) == 0
+
+
+def test_new_entry_points_validate_their_arguments_without_a_device():
+    """Argument checks that return before any CUDA call."""
+    L = _abi.lib()
+    e3 = (ctypes.c_int64 * 3)(8, 6, 4)
+    buf_a, buf_b = ctypes.c_void_p(16), ctypes.c_void_p(32)            # never dereferenced: checks fail first
+    CM, IL, BK = _abi.LS_LAYOUT_COSET_MAJOR, _abi.LS_LAYOUT_INTERLEAVED, _abi.LS_LAYOUT_BRICKED
+    assert L.ls_relayout(buf_a, CM, buf_b, IL, 0, e3, 4, None) == 1            # no cosets
+    assert L.ls_relayout(buf_a, CM, buf_b, IL, 9, e3, 4, None) == 1            # more than 8
+    assert L.ls_relayout(buf_a, CM, buf_b, IL, 2, None, 4, None) == 1          # no extents
+    assert L.ls_relayout(buf_a, CM, buf_b, IL, 2, e3, 3, None) == 1            # element size
+    assert L.ls_relayout(buf_a, CM, buf_b, 7, 2, e3, 4, None) == 1             # layout
+    assert L.ls_relayout(buf_a, CM, buf_a, IL, 2, e3, 4, None) == 1            # in place
+    assert L.ls_relayout(None, CM, buf_b, IL, 2, e3, 4, None) == 1
+    odd = (ctypes.c_int64 * 3)(6, 6, 4)                                         # 6 is not a multiple of 4
+    assert L.ls_relayout(buf_a, CM, buf_b, BK, 2, odd, 4, None) == 1
+    assert b"brick" in L.ls_last_error()
+    big = (ctypes.c_int64 * 3)(1 << 11, 1 << 11, 1 << 10)                     # 2^32 elements
+    assert L.ls_relayout(buf_a, CM, buf_b, IL, 1, big, 4, None) == 3            # UNSUPPORTED
+    assert L.ls_eval_hess(None, None, 0, None, None, None, None) == 1
+    assert L.ls_volume_texture_sync(None, None) == 1
+    assert L.ls_eval_linear_fetch(None, None, 0, None, None) == 1
+    assert L.ls_spline_status(None, None) == 1
+    assert L.ls_volume_layout(None) == -1
+    assert L.ls_adjoint_coef(None, None, None, 0, None, 0, None, None) == 1
+
+
+def test_variant_fields_reach_the_generated_code():
+    """The layout, pipelining and warp-specialization variants change the
+    generated kernels (and only the value kernel for the last two)."""
+    import re
+    from paper_2102_08518_b300 import api
+    srcs = {}
+    for tag, var in (("plain", {}), ("brick", {"brick": 1}), ("pipe", {"pipeline": 1}), ("ws", {"producers": 2})):
+        h = _abi.DescHolder(table("bcc_quintic"), api.kernel_name("bcc_quintic", "f32", **var))
+        assert _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), _abi.LS_F32,
+                                               ctypes.byref(_abi.variant(**var))) == 0
+        cache = os.path.join(ROOT, "paper_2102_08518_b300", "kcache")
+        name = api.kernel_name("bcc_quintic", "f32", **var)
+        files = sorted((f for f in os.listdir(cache) if re.fullmatch(f"ls_{name}_f32_[0-9a-f]+\\.cu", f)),
+                       key=lambda f: os.path.getmtime(os.path.join(cache, f)))
+        srcs[tag] = open(os.path.join(cache, files[-1])).read()
+    assert "BB0" in srcs["brick"] and "BB0" not in srcs["plain"]
+    assert "P_c0" in srcs["pipe"] and "mbarrier.try_wait" in srcs["ws"]
+    def canon(src):
+        # generated temporaries are numbered file-wide: renumber them in order of appearance
+        names = {}
+        return re.sub(r"\b(?:h|dA|hA|sh|w)\d+\b", lambda m: names.setdefault(m.group(0), f"t{len(names)}"), src)
+
+    for tag in ("pipe", "ws"):                                # the other kernels are the plain ones
+        suffix = "pp" if tag == "pipe" else "ws2"
+        for kern in ("ls_adjoint_atomic__", "ls_eval_hess__"):
+            a = srcs["plain"][srcs["plain"].index(kern):].split("extern")[0]
+            b = srcs[tag][srcs[tag].index(kern):].split("extern")[0]
+            assert canon(a.replace("bcc_quintic_f32", "X")) == canon(b.replace(f"bcc_quintic_f32_{suffix}", "X"))
