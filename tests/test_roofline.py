@@ -1,0 +1,58 @@
+"""The algorithmic-traffic model of the benchmark's roofline (roofline.py).
+
+Its stencil indices for the interleaved and bricked layouts must be the
+coset-major indices moved by the layout maps (checked here against numpy
+reshapes, independently of the library), and the distinct-sector counts must
+follow from them.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from paper_2102_08518_b300.api import table
+from paper_2102_08518_b300.roofline import distinct_sectors_per_point, stencil_indices
+
+
+def _maps(C, ext):
+    """Element index of every coset-major element in the interleaved and bricked layouts."""
+    P = int(np.prod(ext))
+    cm = np.arange(C * P).reshape(C, *reversed(ext))            # (C, E2, E1, E0)
+    il = np.empty(C * P, np.int64)
+    il[np.ascontiguousarray(cm.reshape(C, -1).T).ravel()] = np.arange(C * P)
+    e0, e1, e2 = ext
+    bk_order = np.ascontiguousarray(cm.reshape(C, e2 // 2, 2, e1 // 2, 2, e0 // 4, 4)
+                                    .transpose(1, 3, 5, 2, 4, 6, 0)).ravel()
+    bk = np.empty(C * P, np.int64)
+    bk[bk_order] = np.arange(C * P)
+    return il, bk
+
+
+@pytest.mark.parametrize("name", ["bcc_quintic", "fcc6", "tricubic"])
+def test_layout_indices_follow_the_layout_maps(name):
+    ext = (8, 6, 10)
+    lat = workloads.SPLINE_LATTICE[name]
+    C = len(workloads.LATTICES[lat][2])
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = workloads.points_uniform(300, lo - 1.0, hi + 1.0, seed=7)
+    t = table(name)
+    cm = stencil_indices(t, ext, pts, "coset")
+    il_map, bk_map = _maps(C, ext)
+    for layout, mp in (("interleaved", il_map), ("bricked", bk_map)):
+        got = stencil_indices(t, ext, pts, layout)
+        assert np.array_equal(got >= 0, cm >= 0)
+        assert np.array_equal(got[cm >= 0], mp[cm[cm >= 0]])
+
+
+def test_distinct_sectors_of_the_benchmark_layouts():
+    """BCC quintic, 2 x 128^3: interleaving the cosets lowers the distinct
+    32-byte sectors of a stencil; a single-coset spline is unchanged."""
+    ext = (128, 128, 128)
+    pts = workloads.points_uniform(4096, *workloads.inner_box("bcc_quintic", ext), seed=1)
+    q = table("bcc_quintic")
+    a = distinct_sectors_per_point(q, ext, pts, layout="coset")
+    b = distinct_sectors_per_point(q, ext, pts, layout="interleaved")
+    assert 16.5 < a < 18.0 and 12.0 < b < 13.5
+    ptc = workloads.points_uniform(4096, *workloads.inner_box("tricubic", ext), seed=2)
+    tc = table("tricubic")
+    assert distinct_sectors_per_point(tc, ext, ptc, layout="coset") == \
+        distinct_sectors_per_point(tc, ext, ptc, layout="interleaved")
