@@ -664,7 +664,7 @@ def extra_cg(torch, dev, vols, pts, outs):
 
 
 PROFILE_CASES = ("fcc6_eval", "quintic_adjoint_atomic", "quintic_adjoint_fixed", "quintic_hessian",
-                 "tricubic_linear_fetch", "morton_sort")
+                 "tricubic_linear_fetch", "morton_sort", "fcc6_eval_sorted")
 
 
 def run_profile_case(name: str):
@@ -676,12 +676,15 @@ def run_profile_case(name: str):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     n = 1 << 24
-    if name == "fcc6_eval":
+    if name in ("fcc6_eval", "fcc6_eval_sorted"):
         ext = (128, 128, 128)
         c = relayout(workloads.coef_uniform_torch("fcc", ext, seed=0), 4, ext, to="interleaved")
         vol = Volume(Spline("fcc6", "f32"), ext, c, layout="interleaved")
         lo, hi = workloads.inner_box("fcc6", ext)
         p = workloads.points_uniform_torch(n, lo, hi, seed=5)
+        if name.endswith("sorted"):
+            from paper_2102_08518_b300.api import morton_sort, permute_rows
+            p = permute_rows(p, morton_sort(p, cell=1.0))
         out = torch.empty(n, device=dev)
         fn = lambda: vol.eval(p, out)
     elif name.startswith("quintic_"):
