@@ -502,6 +502,15 @@ def extra_fcc(torch, dev, vols, pts, outs):
             best = (t_sorted, ent, ps)
         del perm
     res["sorted"] = best[1]
+    # tile-staged value kernel (one TMA tensor copy of the block's coefficient tile)
+    staged = {}
+    for kw in ({"stage": 1}, {"stage": 1, "block": 128}, {"stage": 16, "block": 128}):
+        vst = Volume(Spline("fcc6", "f32", **kw), ext, coef, layout="interleaved")
+        t_st = time_ms(torch, lambda: vst.eval(best[2], out), reps=5)
+        vst.spline.status()
+        staged[vst.spline.kernel_name] = {"ms": round(t_st, 3), "gpoints_s": round(n / t_st / 1e6, 3)}
+        del vst
+    res["sorted_staged"] = staged
     t_sg = time_ms(torch, lambda: vol.eval_grad(best[2], want_value=True), reps=3)
     res["sorted_value_grad_gpoints_s"] = round(n / t_sg / 1e6, 3)
     res["unsorted_ms"] = round(t_uns, 3)
@@ -664,7 +673,7 @@ def extra_cg(torch, dev, vols, pts, outs):
 
 
 PROFILE_CASES = ("fcc6_eval", "quintic_adjoint_atomic", "quintic_adjoint_fixed", "quintic_hessian",
-                 "tricubic_linear_fetch", "morton_sort", "fcc6_eval_sorted")
+                 "tricubic_linear_fetch", "morton_sort", "fcc6_eval_sorted", "fcc6_eval_staged")
 
 
 def run_profile_case(name: str):
@@ -676,13 +685,13 @@ def run_profile_case(name: str):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     n = 1 << 24
-    if name in ("fcc6_eval", "fcc6_eval_sorted"):
+    if name in ("fcc6_eval", "fcc6_eval_sorted", "fcc6_eval_staged"):
         ext = (128, 128, 128)
         c = relayout(workloads.coef_uniform_torch("fcc", ext, seed=0), 4, ext, to="interleaved")
-        vol = Volume(Spline("fcc6", "f32"), ext, c, layout="interleaved")
+        vol = Volume(Spline("fcc6", "f32", stage=int(name.endswith("staged"))), ext, c, layout="interleaved")
         lo, hi = workloads.inner_box("fcc6", ext)
         p = workloads.points_uniform_torch(n, lo, hi, seed=5)
-        if name.endswith("sorted"):
+        if name.endswith("sorted") or name.endswith("staged"):
             from paper_2102_08518_b300.api import morton_sort, permute_rows
             p = permute_rows(p, morton_sort(p, cell=1.0))
         out = torch.empty(n, device=dev)

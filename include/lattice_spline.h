@@ -175,6 +175,15 @@ typedef struct {
                                           points per consumer warp into shared memory, the other
                                           block / 32 - P warps evaluate the polynomials; bounded
                                           mbarrier waits (see ls_spline_status) */
+    int32_t stage;                     /* S > 0: tile-staged value kernel for spatially sorted points
+                                          (3D, LS_F32, linear layouts): a block bounds the sites of its
+                                          blockDim consecutive points and, when they fit one tile of
+                                          S^3 grid indices per coset (S = 1: 12 for the scale-2
+                                          lattices, 16 for the Cartesian one; S must keep the tile's
+                                          first row a multiple of 16 bytes), loads that tile with one
+                                          TMA tensor copy and evaluates from shared memory; other
+                                          blocks read global memory.  Results are bit-identical to
+                                          the plain kernel.  Bounded mbarrier wait (ls_spline_status) */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */

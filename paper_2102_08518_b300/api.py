@@ -64,13 +64,14 @@ def _ptr(t: Optional[torch.Tensor]):
 
 def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_blocks: int = 0, group: int = 0,
                 depth: int = 0, pts_per_thread: int = 1, blocks_per_sm: int = 0, expansion: str = "sparse",
-                brick: int = 0, pipeline: int = 0, producers: int = 0) -> str:
+                brick: int = 0, pipeline: int = 0, producers: int = 0, stage: int = 0) -> str:
     """The name tag of a generated kernel variant (blocks_per_sm only sizes the
     grid, so it shares the compiled kernel)."""
     return f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + ("_br" if branchy else "") + \
         (f"_m{min_blocks}" if min_blocks else "") + (f"_g{group}d{depth}" if group and depth else "") + \
         (f"_t{pts_per_thread}" if pts_per_thread > 1 else "") + ("_ec" if expansion == "centroid" else "") + \
-        ("_bk" if brick else "") + ("_pp" if pipeline else "") + (f"_ws{producers}" if producers else "")
+        ("_bk" if brick else "") + ("_pp" if pipeline else "") + (f"_ws{producers}" if producers else "") + \
+        (f"_st{stage}" if stage else "")
 
 
 class Spline:
@@ -79,7 +80,7 @@ class Spline:
     def __init__(self, name: str, dtype: str = "f32", block: int = 256, branchy: int = 0,
                  min_blocks: int = 0, group: int = 0, depth: int = 0, pts_per_thread: int = 1,
                  blocks_per_sm: int = 0, expansion: str = "sparse", brick: int = 0, pipeline: int = 0,
-                 producers: int = 0, kernel_name: Optional[str] = None):
+                 producers: int = 0, stage: int = 0, kernel_name: Optional[str] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("lattice spline kernels need a CUDA device")
         self.name = name
@@ -90,7 +91,7 @@ class Spline:
         self.scale = self.table.spline.lattice.scale
         kname = kernel_name or globals()["kernel_name"](name, dtype, block, branchy, min_blocks, group, depth,
                                                          pts_per_thread, blocks_per_sm, expansion, brick, pipeline,
-                                                         producers)
+                                                         producers, stage)
         self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
                         "depth": depth, "pts_per_thread": pts_per_thread, "blocks_per_sm": blocks_per_sm,
                         "expansion": expansion}
@@ -100,11 +101,13 @@ class Spline:
             self.variant["pipeline"] = 1
         if producers:
             self.variant["producers"] = producers
+        if stage:
+            self.variant["stage"] = stage
         self.kernel_name = kname
         self._desc = _abi.DescHolder(self.table, kname, expansion)
         var = _abi.variant(block=block, pts_per_thread=pts_per_thread, branchy=branchy, min_blocks=min_blocks,
                            group=group, depth=depth, blocks_per_sm=blocks_per_sm, brick=brick, pipeline=pipeline,
-                           producers=producers)
+                           producers=producers, stage=stage)
         h = ctypes.c_void_p()
         torch.cuda.init()
         _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),

@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap and its enums; the encoder is fetched from the driver at run time
+
 #include "ls_internal.h"
 #include "ls_kernels.h"
 
@@ -21,6 +23,7 @@ struct EvalArgsH {
     int e0, e1, e2, cstride, cunit;
     unsigned *status;
     float *hess;
+    const void *tmap;
 };
 struct AdjArgsH {
     const float *pts;
@@ -239,7 +242,7 @@ ls_status get_kernel(ls_spline_s *s, const char *what, cudaKernel_t &k, int &per
 
 ls_variant default_variant(const ls_variant *v)
 {
-    ls_variant r{256, 1, 0, 0, 0, 0, 0};
+    ls_variant r{256, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (v) {
         if (v->block > 0) r.block = v->block;
         if (v->pts_per_thread > 0) r.pts_per_thread = v->pts_per_thread > 64 ? 64 : v->pts_per_thread;
@@ -251,6 +254,7 @@ ls_variant default_variant(const ls_variant *v)
         r.brick = v->brick ? 1 : 0;
         r.pipeline = v->pipeline ? 1 : 0;
         r.producers = v->producers > 0 ? v->producers : 0;
+        r.stage = v->stage > 0 ? v->stage : 0;
     }
     return r;
 }
@@ -283,7 +287,7 @@ const char *ls_status_str(ls_status s)
 
 const char *ls_last_error(void) { return g_err.c_str(); }
 
-int32_t ls_abi_version(void) { return 2; }
+int32_t ls_abi_version(void) { return 3; }
 
 ls_status ls_spline_precompile(const ls_spline_desc *desc, ls_dtype dt, const ls_variant *variant)
 {
@@ -323,6 +327,21 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
     if (s->var.producers > 0 && (s->var.producers > 8 || s->var.producers >= s->var.block / 32)) {
         delete s;
         return ls_fail(LS_ERR_INVALID_ARG, "producers must be 1..8 and leave at least one consumer warp");
+    }
+    if (s->var.stage > 0) {
+        const int C = (int)s->table.cosets.size();
+        const int edge = s->var.stage > 1 ? s->var.stage : (s->table.scale == 2 ? 12 : 16);
+        const char *why = nullptr;
+        if (s->table.dim != 3) why = "the staged kernel is 3D only";
+        else if (dt != LS_F32) why = "the staged kernel reads FP32 coefficients";
+        else if (s->var.brick || s->var.pipeline || s->var.producers > 0)
+            why = "stage excludes brick, pipeline and producers";
+        else if (edge % 4 || edge < 4 || edge * C > 256 || edge * edge * edge * C * 4 > 160 * 1024)
+            why = "stage: the tile edge must be a multiple of 4, edge * cosets <= 256, tile <= 160 KiB";
+        if (why) {
+            delete s;
+            return ls_fail(LS_ERR_INVALID_ARG, why);
+        }
     }
     s->gen = ls::generate(s->table, dt, s->var);
     cudaError_t ce = cudaGetDevice(&s->device);
@@ -449,6 +468,69 @@ static ls_status init_volume(ls_spline s, const int64_t *ext, int32_t layout, ls
     return LS_OK;
 }
 
+// TMA tensor map of the coefficient array for the staged value kernel: the
+// interleaved layout as a 3D FP32 tensor (E0 * C, E1, E2), the coset-major one
+// as 4D (E0, E1, E2, C); box = the kernel's tile (edge per axis, all cosets);
+// out-of-bounds elements read as zero.  Volumes the map cannot describe (rows
+// not a multiple of 16 bytes, an unaligned base) keep tmap = NULL, and the
+// staged kernel then reads global memory in every block.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static ls_status volume_tensor_map(ls_volume_s *v)
+{
+    ls_spline_s *s = v->spline;
+    const int edge = s->gen.info.stage_edge;
+    if (edge <= 0 || s->dtype != LS_F32 || s->table.dim != 3 || v->layout == LS_LAYOUT_BRICKED) return LS_OK;
+    const int64_t C = (int64_t)s->table.cosets.size();
+    const int64_t E0 = v->ext[0], E1 = v->ext[1], E2 = v->ext[2];
+    const bool inter = v->layout == LS_LAYOUT_INTERLEAVED || C == 1;
+    const int64_t row = inter ? E0 * C : E0;
+    if ((reinterpret_cast<uintptr_t>(v->coef) & 15) || (row * 4) % 16) return LS_OK;
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return ls_fail(LS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        }
+        encode = (EncodeTiledFn)fn;
+    }
+    alignas(64) CUtensorMap m;
+    cuuint64_t dims[4], strides[3];
+    cuuint32_t box[4], estr[4] = {1, 1, 1, 1};
+    cuuint32_t rank;
+    if (inter) {
+        rank = 3;
+        dims[0] = (cuuint64_t)(E0 * C); dims[1] = (cuuint64_t)E1; dims[2] = (cuuint64_t)E2;
+        strides[0] = (cuuint64_t)(E0 * C * 4); strides[1] = (cuuint64_t)(E0 * C * E1 * 4);
+        box[0] = (cuuint32_t)(edge * C); box[1] = box[2] = (cuuint32_t)edge;
+    } else {
+        rank = 4;
+        dims[0] = (cuuint64_t)E0; dims[1] = (cuuint64_t)E1; dims[2] = (cuuint64_t)E2; dims[3] = (cuuint64_t)C;
+        strides[0] = (cuuint64_t)(E0 * 4); strides[1] = (cuuint64_t)(E0 * E1 * 4);
+        strides[2] = (cuuint64_t)(E0 * E1 * E2 * 4);
+        box[0] = box[1] = box[2] = (cuuint32_t)edge; box[3] = (cuuint32_t)C;
+    }
+    if ((box[0] * 4) % 16) return LS_OK;
+    CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, v->coef, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return ls_fail(LS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    cudaError_t e = cudaMalloc(&v->tmap, sizeof(CUtensorMap));
+    if (e != cudaSuccess) {
+        v->tmap = nullptr;
+        return cuda_fail(e, "cudaMalloc (tensor map)");
+    }
+    e = cudaMemcpy(v->tmap, &m, sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy (tensor map)");
+    v->tmap_edge = edge;
+    return LS_OK;
+}
+
 ls_status ls_volume_create(ls_spline s, const int64_t *ext, int32_t layout, ls_volume *out)
 {
     if (!out) return ls_fail(LS_ERR_INVALID_ARG, "out is NULL");
@@ -474,6 +556,11 @@ ls_status ls_volume_create(ls_spline s, const int64_t *ext, int32_t layout, ls_v
         return cuda_fail(e, "cudaMemset");
     }
     v->owned = true;
+    st = volume_tensor_map(v);
+    if (st != LS_OK) {
+        ls_volume_destroy(v);
+        return st;
+    }
     *out = v;
     return LS_OK;
 }
@@ -491,6 +578,11 @@ ls_status ls_volume_wrap(ls_spline s, const int64_t *ext, int32_t layout, void *
     }
     v->coef = device_coef;
     v->owned = false;
+    st = volume_tensor_map(v);
+    if (st != LS_OK) {
+        ls_volume_destroy(v);
+        return st;
+    }
     *out = v;
     return LS_OK;
 }
@@ -575,6 +667,7 @@ ls_status ls_volume_destroy(ls_volume v)
     if (v->stage) cudaFree(v->stage);
     if (v->tex) cudaDestroyTextureObject(v->tex);
     if (v->tex_array) cudaFreeArray(v->tex_array);
+    if (v->tmap) cudaFree(v->tmap);
     delete v;
     return LS_OK;
 }
@@ -599,6 +692,7 @@ static void fill_eval_args(ls_volume v, const float *pts, int64_t n, float *out,
     a.cunit = vol_cunit(v);
     a.status = v->spline->status;
     a.hess = nullptr;
+    a.tmap = v->tmap;
 }
 
 ls_status ls_eval(ls_volume v, const float *pts, int64_t n, float *out, ls_stream stream)

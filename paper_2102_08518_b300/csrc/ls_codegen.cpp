@@ -95,11 +95,12 @@ void emit_prologue(Emitter &e)
          " return __ldg((const float*)p + i); }\n";
     o << "static __device__ __forceinline__ float ls_ld_bf16(const void* p, int i) {"
          " return __uint_as_float(((unsigned)__ldg((const ls_u16*)p + i)) << 16); }\n";
+    o << "static __device__ __forceinline__ float ls_sh_ld(const void* p, int i) { return ((const float*)p)[i]; }\n";
     o << "static __device__ __forceinline__ float ls_ld_f16(const void* p, int i) {"
          " ls_u16 h = __ldg((const ls_u16*)p + i); float f; asm(\"cvt.f32.f16 %0, %1;\" : \"=f\"(f) : \"h\"(h));"
          " return f; }\n";
     o << "struct LsEvalArgs { const float* pts; float* out; float* grad; const void* coef;"
-         " long long n; int e0, e1, e2, cstride, cunit; unsigned* status; float* hess; };\n";
+         " long long n; int e0, e1, e2, cstride, cunit; unsigned* status; float* hess; const void* tmap; };\n";
     o << "struct LsAdjArgs { const float* pts; const float* gout; float* dcoef;"
          " long long n; int e0, e1, e2, cstride, cunit; unsigned long long* iacc; const float* iscale; };\n";
     o << "struct LsBinArgs { const float* pts; const float* gout; unsigned* key; int* idx; float4* rec;"
@@ -921,11 +922,18 @@ std::string kname(const Table &t, const char *what)
 // Per-point evaluation of value [+ gradient] as a device function, reused by
 // the per-spline kernel and by batched (multi-volume) kernels.
 void emit_eval_point(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach, bool grad,
-                     const std::string &fname)
+                     const std::string &fname, bool coords_args = false)
 {
     auto &o = e.o;
     const int D = t.dim;
-    o << "static __device__ __forceinline__ void " << fname << "(const LsEvalArgs& a, const long long i)\n{\n";
+    if (coords_args)
+        // the point is given (finite, in range): used by the staged kernel with
+        // coordinates relative to its tile
+        o << "static __device__ __forceinline__ void " << fname
+          << "(const LsEvalArgs& a, const long long i, const float x0, const float x1, const float x2)\n{\n"
+             "  (void)x2;\n";
+    else
+        o << "static __device__ __forceinline__ void " << fname << "(const LsEvalArgs& a, const long long i)\n{\n";
     o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride, CU = a.cunit;"
          " (void)E1; (void)E2; (void)CS; (void)CU;\n";
     if (grad) {
@@ -936,7 +944,7 @@ void emit_eval_point(Emitter &e, const Table &t, const ls_variant &var, const St
         o << "#define LS_OUT_OF_RANGE(V) { a.out[i] = (V); }\n";
     }
     o << "  {\n";
-    emit_point_load(e, t, "return");
+    if (!coords_args) emit_point_load(e, t, "return");
     emit_classify(e, t);
     std::string fv;
     std::string g[3];
@@ -1371,6 +1379,170 @@ int emit_eval_kernel_ws(Emitter &e, const Table &t, const ls_variant &var, const
     o << "      if (sp != 2) a.out[i] = sp ? sv : " << fv << ";\n";
     o << "    }\n  }\n}\n\n";
     return smem;
+}
+
+// Tile edge (grid indices per axis) of the staged kernel: var.stage when > 1,
+// else 12 for the scale-2 lattices and 16 for the Cartesian one.
+int stage_edge(const Table &t, const ls_variant &var)
+{
+    if (var.stage > 1) return var.stage;
+    return t.scale == 2 ? 12 : 16;
+}
+
+// Tile-staged value kernel for spatially sorted points.  A block takes a tile
+// of blockDim consecutive points, reduces the bounding box of their
+// region-of-evaluation sites, and if that box plus the stencil reach fits the
+// fixed shared-memory tile, one thread loads the coefficient box with a single
+// TMA tensor copy (cp.async.bulk.tensor; out-of-bounds elements arrive as 0,
+// which is the zero extension beyond the arrays) completing on an mbarrier.
+// Every point of the tile is then evaluated by the same point code reading the
+// tile (coordinates shifted by an even integer vector, so y, the fold and the
+// arithmetic are unchanged); tiles that do not fit, and non-finite or far
+// points, take the global path.  a.tmap: the volume's tensor map (NULL: always
+// the global path).  The wait is bounded: on timeout *a.status is set and the
+// block leaves.  Returns the tile's dynamic shared memory in bytes.
+int emit_eval_kernel_staged(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
+                            GenInfo &info)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    const int C = (int)t.cosets.size();
+    const int sc = t.scale;
+    // tile edge in grid indices per axis (per coset): var.stage > 1 sets it
+    const int edge = stage_edge(t, var);
+    const int BQ[3] = {edge, edge, edge};
+    info.stage_edge = edge;
+    // the copy's x start must be a multiple of 16 bytes: qlo0 * C floats in the
+    // interleaved map, qlo0 floats in the coset-major one
+    const int align_inter = (C >= 4) ? 1 : 4 / C;
+    const int tile_floats = BQ[0] * BQ[1] * BQ[2] * C;
+    const int fma0 = e.fma;
+    const std::string pf_g = kname(t, "eval_pt");
+    const std::string pf_s = kname(t, "eval_pt_tile");
+    emit_eval_point(e, t, var, st, reach, false, pf_g);
+    const std::string ld_save = e.ld;
+    e.ld = "ls_sh_ld";
+    emit_eval_point(e, t, var, st, reach, false, pf_s, true);
+    e.ld = ld_save;
+    info.fma_value = (e.fma - fma0) / 2;
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block;
+    if (var.min_blocks > 0) o << ", " << var.min_blocks;
+    o << ") " << kname(t, "eval") << "(const LsEvalArgs a)\n{\n";
+    // the tensor copy's destination: the dynamic buffer rounded up to 128 bytes
+    // (the buffer is allocated 128 bytes longer than the tile)
+    o << "  extern __shared__ __align__(128) float ls_dyn[];\n";
+    o << "  __shared__ __align__(8) unsigned long long ls_bar;\n";
+    o << "  __shared__ int s_lo[3], s_hi[3];\n";
+    o << "  const unsigned bar = (unsigned)__cvta_generic_to_shared(&ls_bar);\n";
+    o << "  const unsigned dyn = (unsigned)__cvta_generic_to_shared(ls_dyn);\n";
+    o << "  const unsigned dst = (dyn + 127u) & ~127u;\n";
+    o << "  float* const ls_tile = ls_dyn + (dst - dyn) / 4u;\n";
+    o << "  if (threadIdx.x == 0) asm volatile(\"mbarrier.init.shared::cta.b64 [%0], 1;\" :: \"r\"(bar) : \"memory\");\n";
+    o << "  unsigned phase = 0;\n";
+    o << "  const long long B = blockDim.x;\n";
+    o << "  for (long long t0 = (long long)blockIdx.x * B; t0 < a.n; t0 += (long long)gridDim.x * B) {\n";
+    o << "    if (threadIdx.x < 3) { s_lo[threadIdx.x] = 0x7fffffff; s_hi[threadIdx.x] = -0x7fffffff; }\n";
+    o << "    __syncthreads();\n";
+    o << "    const long long i = t0 + threadIdx.x;\n";
+    o << "    float x0 = 0.0f, x1 = 0.0f, x2 = 0.0f;\n";
+    o << "    bool good = false;\n";
+    o << "    int kk[3] = {0, 0, 0};\n";
+    o << "    if (i < a.n) {\n";
+    o << "      x0 = __ldg(a.pts + (size_t)i * " << D << ");\n";
+    o << "      x1 = __ldg(a.pts + (size_t)i * " << D << " + 1);\n";
+    if (D == 3) o << "      x2 = __ldg(a.pts + (size_t)i * 3 + 2);\n";
+    o << "      good = fabsf(x0) < 4194304.0f && fabsf(x1) < 4194304.0f && fabsf(x2) < 4194304.0f;\n";
+    o << "    }\n";
+    o << "    if (good) {\n";
+    // region-of-evaluation site (the same decoding as the point code)
+    {
+        // reuse the classifier's region-of-evaluation part: emit it into a scratch
+        // buffer and keep the lines up to the k definitions
+        Emitter tmp;
+        tmp.ld = e.ld;
+        emit_classify(tmp, t);
+        std::string src = tmp.o.str();
+        std::string keep;
+        size_t pos = 0;
+        int seen = 0;
+        while (pos < src.size() && seen < D) {
+            size_t nl = src.find('\n', pos);
+            std::string line = src.substr(pos, nl - pos + 1);
+            keep += line;
+            for (int q = 0; q < D; ++q)
+                if (line.find("const int k" + std::to_string(q) + " = ") != std::string::npos) ++seen;
+            pos = nl + 1;
+        }
+        o << keep;
+    }
+    for (int q = 0; q < D; ++q) o << "      kk[" << q << "] = k" << q << ";\n";
+    o << "    }\n";
+    // block bounding box of the sites
+    o << "    {\n";
+    for (int q = 0; q < D; ++q) {
+        o << "      int lo" << q << " = good ? kk[" << q << "] : 0x7fffffff, hi" << q << " = good ? kk[" << q
+          << "] : -0x7fffffff;\n";
+        o << "      lo" << q << " = __reduce_min_sync(0xffffffffu, lo" << q << "); hi" << q
+          << " = __reduce_max_sync(0xffffffffu, hi" << q << ");\n";
+        o << "      if ((threadIdx.x & 31) == 0) { atomicMin(&s_lo[" << q << "], lo" << q << "); atomicMax(&s_hi[" << q
+          << "], hi" << q << "); }\n";
+    }
+    o << "    }\n";
+    o << "    __syncthreads();\n";
+    // tile origin in grid indices and whether the stencils fit
+    o << "    int qlo[3] = {0, 0, 0};\n    bool fits = a.tmap != 0 && s_lo[0] <= s_hi[0];\n";
+    o << "    const int al = " << (C == 1 ? std::string("4") : "(a.cstride == 1) ? " + std::to_string(align_inter) + " : 4")
+      << ";\n";
+    for (int q = 0; q < D; ++q) {
+        if (sc == 2) {
+            o << "    qlo[" << q << "] = (s_lo[" << q << "] - " << reach << ") >> 1;\n";
+            if (q == 0) o << "    qlo[0] &= ~(al - 1);\n";
+            o << "    fits = fits && ((s_hi[" << q << "] + " << reach << ") >> 1) - qlo[" << q << "] < " << BQ[q] << ";\n";
+        } else {
+            o << "    qlo[" << q << "] = s_lo[" << q << "] - " << reach << ";\n";
+            if (q == 0) o << "    qlo[0] &= ~(al - 1);\n";
+            o << "    fits = fits && (s_hi[" << q << "] + " << reach << ") - qlo[" << q << "] < " << BQ[q] << ";\n";
+        }
+    }
+    // qlo >= 0: x - scale * qlo is then exact in FP32 (a multiple of ulp(x),
+    // no larger than x), so the tile path computes bit-identical results
+    o << "    fits = fits && qlo[0] >= 0 && qlo[1] >= 0 && qlo[2] >= 0;\n";
+    o << "    if (fits) {\n";
+    o << "      if (threadIdx.x == 0) {\n";
+    o << "        asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n";
+    o << "        asm volatile(\"mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\" :: \"r\"(bar), \"r\"("
+      << tile_floats * 4 << ") : \"memory\");\n";
+    // coordinates: interleaved layout (3D map: (E0*C, E1, E2)) or coset-major (4D map: (E0, E1, E2, C))
+    o << "        if (" << (C == 1 ? "true" : "a.cstride == 1") << ") {\n";
+    o << "          asm volatile(\"cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+         " [%0], [%1, {%2, %3, %4}], [%5];\" :: \"r\"(dst), \"l\"(a.tmap), \"r\"(qlo[0] * " << C
+      << "), \"r\"(qlo[1]), \"r\"(qlo[2]), \"r\"(bar) : \"memory\");\n";
+    o << "        } else {\n";
+    o << "          asm volatile(\"cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+         " [%0], [%1, {%2, %3, %4, %5}], [%6];\" :: \"r\"(dst), \"l\"(a.tmap), \"r\"(qlo[0]), \"r\"(qlo[1]),"
+         " \"r\"(qlo[2]), \"r\"(0), \"r\"(bar) : \"memory\");\n";
+    o << "        }\n      }\n";
+    o << "      const bool ok = ls_mbar_wait(bar, phase, a.status);\n";
+    o << "      if (__syncthreads_or(!ok)) return;\n";
+    o << "      phase ^= 1u;\n";
+    o << "      if (good) {\n";
+    o << "        LsEvalArgs b = a;\n";
+    o << "        b.coef = ls_tile; b.e0 = " << BQ[0] << "; b.e1 = " << BQ[1] << "; b.e2 = " << (D == 3 ? BQ[2] : 1)
+      << ";\n";
+    o << "        if (" << (C == 1 ? "true" : "a.cstride == 1") << ") { b.cstride = 1; b.cunit = " << C
+      << "; } else { b.cstride = "
+      << BQ[0] * BQ[1] * BQ[2] << "; b.cunit = 1; }\n";
+    o << "        " << pf_s << "(b, i, x0 - " << sc << ".0f * (float)qlo[0], x1 - " << sc << ".0f * (float)qlo[1], "
+      << (D == 3 ? "x2 - " + std::to_string(sc) + ".0f * (float)qlo[2]" : std::string("0.0f")) << ");\n";
+    o << "      } else if (i < a.n) {\n";
+    o << "        " << pf_g << "(a, i);\n";
+    o << "      }\n";
+    o << "    } else if (i < a.n) {\n";
+    o << "      " << pf_g << "(a, i);\n";
+    o << "    }\n";
+    o << "    __syncthreads();\n";
+    o << "  }\n}\n\n";
+    return tile_floats * 4 + 128;
 }
 
 // Per-site weight polynomials w_j(u) (weights form), for the adjoint.
@@ -1879,7 +2051,9 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
         g.info.n_sites = n;
     }
     g.info.reach = reach;
-    if (var.producers > 0 && t.sep.empty()) {
+    if (var.stage && t.dim == 3) {
+        g.info.eval_smem = emit_eval_kernel_staged(e, t, var, st, reach, g.info);
+    } else if (var.producers > 0 && t.sep.empty()) {
         emit_eval_point(e, t, var, st, reach, false, kname(t, "eval_pt"));
         g.info.eval_smem = emit_eval_kernel_ws(e, t, var, st, reach, g.info);
     } else if (var.pipeline && t.sep.empty()) {
@@ -1970,7 +2144,8 @@ Generated generate_batch(const std::vector<const Table *> &tables, const std::ve
     o << "    const LsBatchVol v = b.vols[w.vol];\n";
     o << "    LsEvalArgs a;\n";
     o << "    a.pts = v.pts; a.out = v.out; a.grad = 0; a.coef = v.coef; a.n = v.n;\n";
-    o << "    a.e0 = v.e0; a.e1 = v.e1; a.e2 = v.e2; a.cstride = v.cstride; a.cunit = v.cunit; a.status = b.status;\n";
+    o << "    a.e0 = v.e0; a.e1 = v.e1; a.e2 = v.e2; a.cstride = v.cstride; a.cunit = v.cunit; a.status = b.status;"
+         " a.hess = 0; a.tmap = 0;\n";
     o << "    switch (v.kind) {\n";
     for (size_t k = 0; k < tables.size(); ++k)
         o << "    case " << k << ": for (long long i = w.p0 + threadIdx.x; i < w.p1; i += blockDim.x) ls_bpt_" << k

@@ -53,7 +53,8 @@ struct GenInfo {
     int n_reverse = 0;      // offsets between a coefficient and the ROE sites that can reach it
     int halo = 0;           // halo of the binning grid (storage units)
     double wmax = 1.0;      // bound on |w_j(u)| over the region of evaluation
-    int eval_smem = 0;      // dynamic shared memory of the value kernel (warp-specialized variant)
+    int eval_smem = 0;      // dynamic shared memory of the value kernel (warp-specialized, staged)
+    int stage_edge = 0;     // staged value kernel: tile edge in grid indices (0: not staged)
 };
 
 struct Generated {
@@ -116,6 +117,10 @@ struct ls_volume_s {
     cudaArray_t tex_array = nullptr;
     cudaTextureObject_t tex = 0;
     bool tex_ready = false;
+    // TMA tensor map (device copy, 128 bytes) for the staged value kernel, made
+    // on first use for tile edge tmap_edge
+    void *tmap = nullptr;
+    int tmap_edge = 0;
 };
 
 // Address of coefficient (coset j, per-coset linear index q) is

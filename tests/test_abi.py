@@ -40,7 +40,7 @@ def test_status_strings():
     L = _abi.lib()
     for code in range(9):
         assert L.ls_status_str(code)
-    assert L.ls_abi_version() == 2
+    assert L.ls_abi_version() == 3
 
 
 @pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
@@ -127,7 +127,8 @@ def test_variant_fields_reach_the_generated_code():
     import re
     from paper_2102_08518_b300 import api
     srcs = {}
-    for tag, var in (("plain", {}), ("brick", {"brick": 1}), ("pipe", {"pipeline": 1}), ("ws", {"producers": 2})):
+    for tag, var in (("plain", {}), ("brick", {"brick": 1}), ("pipe", {"pipeline": 1}), ("ws", {"producers": 2}),
+                     ("stage", {"stage": 1})):
         h = _abi.DescHolder(table("bcc_quintic"), api.kernel_name("bcc_quintic", "f32", **var))
         assert _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), _abi.LS_F32,
                                                ctypes.byref(_abi.variant(**var))) == 0
@@ -138,14 +139,29 @@ def test_variant_fields_reach_the_generated_code():
         srcs[tag] = open(os.path.join(cache, files[-1])).read()
     assert "BB0" in srcs["brick"] and "BB0" not in srcs["plain"]
     assert "P_c0" in srcs["pipe"] and "mbarrier.try_wait" in srcs["ws"]
+    assert "cp.async.bulk.tensor.3d" in srcs["stage"] and "cp.async.bulk.tensor" not in srcs["plain"]
     def canon(src):
         # generated temporaries are numbered file-wide: renumber them in order of appearance
         names = {}
         return re.sub(r"\b(?:h|dA|hA|sh|w)\d+\b", lambda m: names.setdefault(m.group(0), f"t{len(names)}"), src)
 
-    for tag in ("pipe", "ws"):                                # the other kernels are the plain ones
-        suffix = "pp" if tag == "pipe" else "ws2"
+    for tag in ("pipe", "ws", "stage"):                       # the other kernels are the plain ones
+        suffix = {"pipe": "pp", "ws": "ws2", "stage": "st1"}[tag]
         for kern in ("ls_adjoint_atomic__", "ls_eval_hess__"):
             a = srcs["plain"][srcs["plain"].index(kern):].split("extern")[0]
             b = srcs[tag][srcs[tag].index(kern):].split("extern")[0]
             assert canon(a.replace("bcc_quintic_f32", "X")) == canon(b.replace(f"bcc_quintic_f32_{suffix}", "X"))
+
+
+def test_stage_variant_is_validated_before_any_device_call():
+    """The staged kernel is 3D, FP32, linear layouts, tile edge a multiple of 4
+    with edge * cosets <= 256 (the TMA box) and at most 160 KiB of tile."""
+    L = _abi.lib()
+    for name, dt, var in (("fcc6", _abi.LS_F32, {"stage": 6}), ("fcc6", _abi.LS_BF16, {"stage": 1}),
+                          ("bcc_quintic", _abi.LS_F32, {"stage": 1, "brick": 1}), ("zp", _abi.LS_F32, {"stage": 1}),
+                          ("fcc6", _abi.LS_F32, {"stage": 80}), ("tricubic", _abi.LS_F32, {"stage": 36}),
+                          ("bcc_quintic", _abi.LS_F32, {"stage": 1, "producers": 2})):
+        h = _abi.DescHolder(table(name), "probe")
+        out = ctypes.c_void_p()
+        assert L.ls_spline_create(ctypes.byref(h.desc), dt, ctypes.byref(_abi.variant(**var)), ctypes.byref(out)) == 1
+        assert b"stage" in L.ls_last_error() or b"3D" in L.ls_last_error() or b"FP32" in L.ls_last_error()
