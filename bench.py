@@ -334,6 +334,32 @@ def run_gpu(args):
                     "flops_per_point": 2 * info["fma_value"], "regs": info["regs_eval"],
                     "peak_source": f"FP32 FMA: {sms} SMs x 128 lanes x 2 flop x {max_mhz:.0f} MHz"}
 
+    # the tensor-core kernel where the autotuner chose it: TF32 products executed
+    # (3 x 2 K N flop per point: the hi/lo split) against the measured sustained
+    # BF16 rate x the nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s dense)
+    roofline_tensor = None
+    from paper_2102_08518_b300.roofline import tensor_shape
+    for ci, (sp, ps) in enumerate(CASES):
+        if not tuned[(sp, ps)].variant.get("tensor"):
+            continue
+        Kt, Nt, nnz = tensor_shape(table(sp), tuned[(sp, ps)].variant.get("expansion", "sparse"))
+        n = N_UNIFORM if ps == "uniform" else N_RAYS * RAY_STEPS
+        tf = 3 * 2 * Kt * Nt * n / (case_ms[ci] * 1e-3) / 1e12
+        bf16_sus, src = 1400.0, "fallback 1.4 PFLOP/s sustained BF16"
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16_sus, src = float(json.load(f)["bf16_tflops_sustained"]), "MEASURED_PEAKS.json bf16_tflops_sustained"
+        except (OSError, ValueError, KeyError):
+            pass
+        peak_tf32 = bf16_sus * 1.1 / 2.25
+        roofline_tensor = {"bound": "tensor", "case": f"{sp}/{ps}", "kernel": "ls_eval__" + tuned[(sp, ps)].kernel_name,
+                           "achieved": round(tf, 1), "peak": round(peak_tf32, 1), "unit": "TFLOP/s",
+                           "frac": round(tf / peak_tf32, 4), "dtype": "tf32 (3 products: FP32 accuracy)",
+                           "product_shape": {"M": 128, "N": Nt, "K": Kt},
+                           "flops_per_point": 3 * 2 * Kt * Nt, "useful_flops_per_point": 2 * nnz,
+                           "peak_source": src + " x 1.1 / 2.25 (nominal TF32 / BF16 dense)"}
+        break
+
     # --- end to end through the C ABI with host buffers ------------------------------
     # each point set crosses to the device once and both splines are evaluated on it
     host_pts = {k: torch.from_numpy(v).pin_memory() for k, v in pts_np.items()}
@@ -368,6 +394,7 @@ def run_gpu(args):
                          "l2": "points 201 MB per set > 126 MB L2 (inputs larger than L2); coefficient volume "
                                "16 MiB L2-resident by design", "parallelism": f"replicas x{world}"},
               "per_case": per_case, "roofline": roofline, "roofline_alu": roofline_alu, "roofline_hbm": roofline_hbm,
+              "roofline_tensor": roofline_tensor,
               "e2e": e2e,
               "autotuned": {f"{sp}/{ps}": {"variant": tuned[(sp, ps)].variant,
                                             "key": tune_key(sp, "f32", EXT, [pts[ps]], f"bcc_step_{ps}", LAYOUT)}
@@ -672,7 +699,7 @@ def extra_cg(torch, dev, vols, pts, outs):
     return res
 
 
-PROFILE_CASES = ("fcc6_eval", "quintic_adjoint_atomic", "quintic_adjoint_fixed", "quintic_hessian",
+PROFILE_CASES = ("fcc6_eval", "quintic_eval_interleaved", "quintic_eval_bricked", "quintic_adjoint_atomic", "quintic_adjoint_fixed", "quintic_hessian",
                  "tricubic_linear_fetch", "morton_sort", "fcc6_eval_sorted", "fcc6_eval_staged")
 
 
@@ -694,6 +721,14 @@ def run_profile_case(name: str):
         if name.endswith("sorted") or name.endswith("staged"):
             from paper_2102_08518_b300.api import morton_sort, permute_rows
             p = permute_rows(p, morton_sort(p, cell=1.0))
+        out = torch.empty(n, device=dev)
+        fn = lambda: vol.eval(p, out)
+    elif name.startswith("quintic_eval_"):
+        coef_np, pts_np = make_inputs()
+        lay = name.rsplit("_", 1)[1]
+        c = relayout(torch.from_numpy(coef_np).to(dev), 2, EXT, to=lay)
+        vol = Volume(Spline("bcc_quintic", "f32", brick=int(lay == "bricked")), EXT, c, layout=lay)
+        p = torch.from_numpy(pts_np["uniform"]).to(dev)
         out = torch.empty(n, device=dev)
         fn = lambda: vol.eval(p, out)
     elif name.startswith("quintic_"):

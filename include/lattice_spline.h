@@ -184,6 +184,13 @@ typedef struct {
                                           TMA tensor copy and evaluates from shared memory; other
                                           blocks read global memory.  Results are bit-identical to
                                           the plain kernel.  Bounded mbarrier wait (ls_spline_status) */
+    int32_t tensor;                    /* T > 0: the value kernel forms the coefficient transform
+                                          A = M^T c of each tile of 128 points as one matrix product
+                                          on the tensor cores (tcgen05.mma kind::tf32, three TF32
+                                          products for FP32 accuracy, accumulator in tensor memory);
+                                          one block per SM with S slots of 128 points (S = T for
+                                          T = 2..4, else 4; forces block = 128 S); non-separable
+                                          tables.  Bounded mbarrier waits (ls_spline_status) */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */

@@ -242,7 +242,7 @@ ls_status get_kernel(ls_spline_s *s, const char *what, cudaKernel_t &k, int &per
 
 ls_variant default_variant(const ls_variant *v)
 {
-    ls_variant r{256, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    ls_variant r{256, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (v) {
         if (v->block > 0) r.block = v->block;
         if (v->pts_per_thread > 0) r.pts_per_thread = v->pts_per_thread > 64 ? 64 : v->pts_per_thread;
@@ -255,6 +255,9 @@ ls_variant default_variant(const ls_variant *v)
         r.pipeline = v->pipeline ? 1 : 0;
         r.producers = v->producers > 0 ? v->producers : 0;
         r.stage = v->stage > 0 ? v->stage : 0;
+        r.tensor = v->tensor > 0 ? v->tensor : 0;
+        // S slots of 128 points (the 128 lanes of tensor memory), S = 2..4 (default 4)
+        if (r.tensor) r.block = 128 * ((r.tensor >= 2 && r.tensor <= 4) ? r.tensor : 4);
     }
     return r;
 }
@@ -328,6 +331,16 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
         delete s;
         return ls_fail(LS_ERR_INVALID_ARG, "producers must be 1..8 and leave at least one consumer warp");
     }
+    if (s->var.tensor) {
+        const char *why = nullptr;
+        if (!s->table.sep.empty()) why = "tensor: tensor-product tables use the separable path";
+        else if (s->var.stage || s->var.pipeline || s->var.producers > 0 || s->var.pts_per_thread > 1)
+            why = "tensor excludes stage, pipeline, producers and pts_per_thread";
+        if (why) {
+            delete s;
+            return ls_fail(LS_ERR_INVALID_ARG, why);
+        }
+    }
     if (s->var.stage > 0) {
         const int C = (int)s->table.cosets.size();
         const int edge = s->var.stage > 1 ? s->var.stage : (s->table.scale == 2 ? 12 : 16);
@@ -398,6 +411,10 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
         }
         s->mod.blocks_per_sm_eval = nb;
     }
+    if (s->gen.info.tmem_cols > 0)
+        // tensor-core value kernel: one block per SM (a block that allocates
+        // tensor memory runs alone on its SM); its slots share the 512 columns
+        s->mod.blocks_per_sm_eval = 1;
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, (const void *)s->mod.eval) == cudaSuccess) s->mod.regs_eval = fa.numRegs;
     else cudaGetLastError();

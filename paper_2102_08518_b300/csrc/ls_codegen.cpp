@@ -119,6 +119,19 @@ void emit_prologue(Emitter &e)
          "  if (status) atomicOr(status, 1u);\n"
          "  return false;\n"
          "}\n";
+    // wait for an mbarrier phase by one thread (the others wait at a barrier):
+    // try_wait suspends the thread for a system-dependent time while the phase
+    // is incomplete; bounded, sets *status and returns false when it gives up
+    o << "static __device__ __forceinline__ bool ls_mbar_poll(unsigned bar, unsigned parity, unsigned* status) {\n"
+         "  for (int it = 0; it < (1 << 22); ++it) {\n"
+         "    unsigned ok;\n"
+         "    asm volatile(\"{ .reg .pred p; mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;"
+         " selp.u32 %0, 1, 0, p; }\" : \"=r\"(ok) : \"r\"(bar), \"r\"(parity) : \"memory\");\n"
+         "    if (ok) return true;\n"
+         "  }\n"
+         "  if (status) atomicOr(status, 1u);\n"
+         "  return false;\n"
+         "}\n";
     // warp-aggregated scatter-add: lanes with the same address sum their values
     // by shuffles (per-lane source lanes, warp-uniform trip count) and the
     // lowest of them issues one atomic; ad < 0 means no site (nothing added)
@@ -584,11 +597,12 @@ const int HI2[3] = {0, 1, 0}, HJ2[3] = {0, 1, 1};
 // Value, and for nd >= 1 the gradient, for nd >= 2 also the Hessian, all in
 // reference coordinates: returns {f, g_0..g_{D-1}, h_0..h_{NH-1}}.
 std::vector<std::string> emit_region_poly(Emitter &e, const Table &t, int k, const std::vector<int> &umap,
-                                          int grad)
+                                          int grad, const std::map<I3, std::string> *pre = nullptr)
 {
     const RefRegion &r = t.ref[k];
     const int D = t.dim;
     PolyEmit pe{e, D, "r" + std::to_string(k) + "_", {}, {}, {}};
+    if (pre) pe.aname = *pre;     // coefficients A_a computed elsewhere (tensor-core transform)
     for (int i = 0; i < D; ++i) {
         pe.uvar[i] = "u" + std::to_string(k) + "_" + std::to_string(i);
         e.o << "    const float " << pe.uvar[i] << " = a" << i << " - " << flit(r.center[i]) << ";\n";
@@ -1381,6 +1395,251 @@ int emit_eval_kernel_ws(Emitter &e, const Table &t, const ls_variant &var, const
     return smem;
 }
 
+// ---------------------------------------------------------------------------
+// Coefficient transform on the tensor cores.
+//
+// For the points of a tile, the coefficient form A_a = sum_j M[j][a] c_j of
+// every reference region is one dense product D = C M with C (points x union
+// sites) and M (union sites x (region, monomial) columns) constant per spline.
+// It runs as tcgen05.mma kind::tf32 with M = 128 rows (one point per TMEM
+// lane, one thread per point), N = the column count rounded up to 16,
+// K = the union sites rounded up to 8; FP32 accuracy from three TF32 products
+// (split A = A_hi + A_lo, M = M_hi + M_lo: A_hi M_hi + A_hi M_lo + A_lo M_hi).
+// C goes to tensor memory with tcgen05.st (each thread its own lane), M sits
+// in shared memory in the K-major canonical layout without swizzle (8-row x
+// 16-byte core matrices: K-adjacent ones 128 bytes apart, 8-row groups
+// 8 * K * 4 bytes apart), D comes back with tcgen05.ld and feeds the same
+// Horner forms as the FMA path.
+// ---------------------------------------------------------------------------
+struct TensorPlan {
+    int nu = 0, kp = 0, ncol = 0, n = 0, cols = 0;
+    std::vector<std::map<I3, std::vector<std::pair<int, double>>>> terms;
+    std::vector<std::set<I3>> sup;
+    std::vector<std::map<I3, int>> col;
+};
+
+TensorPlan tensor_plan(const Table &t, const Stencil &st)
+{
+    TensorPlan p;
+    const size_t K = t.ref.size();
+    p.nu = (int)st.sites.size();
+    p.kp = (p.nu + 7) / 8 * 8;
+    p.terms.resize(K);
+    p.sup.resize(K);
+    p.col.resize(K);
+    for (size_t k = 0; k < K; ++k) {
+        p.sup[k] = monomial_support(t.ref[k], st.region_to_union[k], p.terms[k]);
+        for (const auto &m : p.sup[k]) p.col[k][m] = p.ncol++;
+    }
+    p.n = std::max(16, (p.ncol + 15) / 16 * 16);
+    p.cols = 32;
+    while (p.cols < 2 * p.kp + p.n) p.cols *= 2;
+    return p;
+}
+
+// round to the nearest TF32 value (11 significant bits), ties away from zero
+double tf32_round(double v)
+{
+    if (v == 0.0 || !std::isfinite(v)) return v;
+    int ex;
+    const double m = std::frexp(v, &ex);          // v = m 2^ex, 0.5 <= |m| < 1
+    return std::ldexp(std::round(std::ldexp(m, 11)), ex - 11);
+}
+
+// power-of-two chunks of a register run for tcgen05.ld / st (x1 .. x64)
+std::vector<std::pair<int, int>> pow2_chunks(int n)
+{
+    std::vector<std::pair<int, int>> r;
+    int at = 0;
+    for (int c = 64; c >= 1; c >>= 1)
+        while (n - at >= c) {
+            r.push_back({at, c});
+            at += c;
+        }
+    return r;
+}
+
+// Slots per block of the tensor-core kernel: var.tensor when 2..4, else 4.
+int tensor_slots(const ls_variant &var) { return (var.tensor >= 2 && var.tensor <= 4) ? var.tensor : 4; }
+
+// One block per SM (a block that allocates tensor memory is the only one on
+// its SM) with S slots of 4 warps; each slot owns 128 points at a time, a
+// column range of tensor memory, an mbarrier and a named barrier, and runs
+// independently of the others.  Within a slot the tile loop is software
+// pipelined: the gathers of tile t are issued before the results of tile
+// t - 1 are read back, so the product of t - 1 runs behind them.
+void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
+                             GenInfo &info)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    const size_t K = t.ref.size();
+    const TensorPlan P = tensor_plan(t, st);
+    const int KP = P.kp, N = P.n, NU = P.nu, S = tensor_slots(var);
+    int alloc = 32;
+    while (alloc < S * P.cols) alloc *= 2;
+    info.tmem_cols = alloc;
+    // the transform matrix (hi, then lo) in the canonical shared-memory order
+    std::vector<double> B((size_t)N * KP, 0.0);
+    for (size_t k = 0; k < K; ++k)
+        for (const auto &m : P.sup[k])
+            for (const auto &pr : P.terms[k].at(m)) B[(size_t)P.col[k].at(m) * KP + pr.first] += pr.second;
+    const std::string tab = "ls_tcB_" + kname(t, "eval");
+    o << "static __device__ const float " << tab << "[" << 2 * N * KP << "] = {\n";
+    for (int h = 0; h < 2; ++h)
+        for (int idx = 0; idx < N * KP; ++idx) {
+            // idx = (n / 8) * 8 KP + (u / 4) * 32 + (n % 8) * 4 + (u % 4)
+            const int g = idx / (8 * KP), rem = idx % (8 * KP);
+            const int ug = rem / 32, r2 = rem % 32;
+            const int nn = g * 8 + r2 / 4, u = ug * 4 + r2 % 4;
+            const double v = B[(size_t)nn * KP + u];
+            const double hi = tf32_round(v);
+            o << flit(h == 0 ? hi : tf32_round(v - hi)) << ((idx + 1) % 8 == 0 ? ",\n" : ", ");
+        }
+    o << "};\n";
+    const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((128u >> 4) << 24);
+    auto reglist = [](int cnt, int op0) {
+        std::string r = "{";
+        for (int q = 0; q < cnt; ++q) r += (q ? "," : "") + std::string("%") + std::to_string(op0 + q);
+        return r + "}";
+    };
+    const int fma0 = e.fma;
+    o << "extern \"C\" __global__ void __launch_bounds__(" << 128 * S << ", 1) " << kname(t, "eval")
+      << "(const LsEvalArgs a)\n{\n";
+    o << "  __shared__ __align__(1024) float ls_sB[" << 2 * N * KP << "];\n";
+    o << "  __shared__ __align__(8) unsigned long long ls_bar[" << S << "];\n";
+    o << "  __shared__ unsigned ls_tbase;\n";
+    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride, CU = a.cunit;"
+         " (void)E1; (void)E2; (void)CS; (void)CU;\n";
+    o << "  const unsigned warp = threadIdx.x >> 5, slot = warp >> 2, lt = threadIdx.x & 127u;\n";
+    o << "  for (int q = threadIdx.x; q < " << 2 * N * KP << "; q += blockDim.x) ls_sB[q] = " << tab << "[q];\n";
+    o << "  if (warp == 0) {\n";
+    o << "    asm volatile(\"tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\" :: "
+         "\"r\"((unsigned)__cvta_generic_to_shared(&ls_tbase)), \"r\"(" << alloc << "u) : \"memory\");\n";
+    o << "    asm volatile(\"tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\" ::: \"memory\");\n";
+    o << "  }\n";
+    o << "  if (threadIdx.x < " << S << ") asm volatile(\"mbarrier.init.shared::cta.b64 [%0], 1;\" :: "
+         "\"r\"((unsigned)__cvta_generic_to_shared(&ls_bar[threadIdx.x])) : \"memory\");\n";
+    o << "  asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n";
+    o << "  asm volatile(\"tcgen05.fence::before_thread_sync;\" ::: \"memory\");\n";
+    o << "  __syncthreads();\n";
+    o << "  asm volatile(\"tcgen05.fence::after_thread_sync;\" ::: \"memory\");\n";
+    o << "  const unsigned tm = ls_tbase + slot * " << P.cols << "u;      // this slot's columns\n";
+    o << "  const unsigned tl = tm + ((32u * (warp & 3u)) << 16);   // and this warp's quarter of the lanes\n";
+    o << "  const unsigned bar = (unsigned)__cvta_generic_to_shared(&ls_bar[slot]);\n";
+    o << "  const unsigned nb = 1u + slot;                       // the slot's named barrier\n";
+    o << "  const unsigned sb = (unsigned)__cvta_generic_to_shared(ls_sB);\n";
+    o << "  unsigned phase = 0;\n  bool pending = false, bad = false;\n";
+    o << "  long long pi = 0;\n  int pst = 2, ppsi = 0;\n  float pa0 = 0.0f, pa1 = 0.0f, pa2 = 0.0f;\n";
+    o << "#define LS_OUT_OF_RANGE(V) { a.out[i] = (V); }\n";
+    o << "  for (long long tile = (long long)blockIdx.x * " << S << " + slot; ; tile += (long long)gridDim.x * " << S
+      << ") {\n";
+    o << "    const bool have = tile * 128 < a.n;\n";
+    o << "    const long long i = tile * 128 + lt;\n";
+    o << "    int stt = 2;\n";
+    for (int q = 0; q < 3; ++q) o << "    float x" << q << " = 0.0f;\n";
+    o << "    if (have && i < a.n) {\n";
+    for (int q = 0; q < D; ++q) o << "      x" << q << " = __ldg(a.pts + (size_t)i * " << D << " + " << q << ");\n";
+    o << "      if (";
+    for (int q = 0; q < D; ++q) o << (q ? " && " : "") << "fabsf(x" << q << ") < 4194304.0f";
+    o << ") stt = 0;\n      else {\n        const bool isn = ";
+    for (int q = 0; q < D; ++q) o << (q ? " || " : "") << "(x" << q << " != x" << q << ")";
+    o << ";\n        LS_OUT_OF_RANGE(isn ? __int_as_float(0x7fffffff) : 0.0f);\n        stt = 1;\n      }\n    }\n";
+    for (int j = 0; j < KP; ++j) o << "    float tc" << j << " = 0.0f;\n";
+    o << "    float ta0 = 0.0f, ta1 = 0.0f, ta2 = 0.0f;\n    int tpsi = 0;\n";
+    o << "    if (stt == 0) {\n";
+    emit_classify(e, t);
+    emit_gathers(e, t, st.sites, reach, "a.coef", false, true, var.group, var.depth);
+    for (int j = 0; j < NU; ++j) o << "    tc" << j << " = c" << j << ";\n";
+    for (int q = 0; q < D; ++q) o << "    ta" << q << " = a" << q << ";\n";
+    o << "    tpsi = psi;\n";
+    o << "    }\n";
+    // results of the previous tile
+    o << "    if (pending) {\n";
+    o << "      const bool ok = lt == 0 ? ls_mbar_poll(bar, phase, a.status) : true;\n";
+    o << "      unsigned anybad;\n";
+    o << "      asm volatile(\"{ .reg .pred p, q; setp.eq.u32 q, %1, 0; bar.red.or.pred p, %2, 128, q;"
+         " selp.u32 %0, 1, 0, p; }\" : \"=r\"(anybad) : \"r\"((unsigned)ok), \"r\"(nb) : \"memory\");\n";
+    o << "      if (anybad) { bad = true; break; }\n";
+    o << "      phase ^= 1u;\n";
+    o << "      asm volatile(\"tcgen05.fence::after_thread_sync;\" ::: \"memory\");\n";
+    for (int q = 0; q < N; ++q) o << "      unsigned td" << q << ";\n";
+    for (const auto &ch : pow2_chunks(N)) {
+        o << "      asm volatile(\"tcgen05.ld.sync.aligned.32x32b.x" << ch.second << ".b32 " << reglist(ch.second, 0)
+          << ", [%" << ch.second << "];\" : ";
+        for (int q = 0; q < ch.second; ++q) o << (q ? ", " : "") << "\"=r\"(td" << (ch.first + q) << ")";
+        o << " : \"r\"(tl + " << (2 * KP + ch.first) << "u) : \"memory\");\n";
+    }
+    o << "      asm volatile(\"tcgen05.wait::ld.sync.aligned;\" ::: \"memory\");\n";
+    o << "      if (pst == 0) {\n";
+    for (int q = 0; q < D; ++q) o << "      const float a" << q << " = pa" << q << ";\n";
+    o << "      const int psi = ppsi; (void)psi;\n";
+    std::vector<std::string> fk;
+    for (size_t k = 0; k < K; ++k) {
+        std::map<I3, std::string> pre;
+        for (const auto &m : P.sup[k]) {
+            const std::string nm = "tA" + std::to_string(P.col[k].at(m));
+            o << "      const float " << nm << " = __uint_as_float(td" << P.col[k].at(m) << ");\n";
+            pre[m] = nm;
+        }
+        fk.push_back(emit_region_poly(e, t, (int)k, st.region_to_union[k], 0, &pre)[0]);
+    }
+    std::string sel = fk[K - 1];
+    for (int k = (int)K - 2; k >= 0; --k) sel = "(psi == " + std::to_string(k) + ") ? " + fk[k] + " : (" + sel + ")";
+    o << "      a.out[pi] = " << sel << ";\n";
+    o << "      }\n";
+    o << "      pending = false;\n";
+    o << "    }\n";
+    o << "    if (!have) break;\n";
+    // split and stage this tile's coefficients (slot columns [0, KP) hi, [KP, 2 KP) lo)
+    for (int j = 0; j < KP; ++j) {
+        o << "    unsigned th" << j << ", tw" << j << ";\n";
+        o << "    asm(\"cvt.rna.tf32.f32 %0, %1;\" : \"=r\"(th" << j << ") : \"f\"(tc" << j << "));\n";
+        o << "    tw" << j << " = __float_as_uint(tc" << j << " - __uint_as_float(th" << j << "));\n";
+    }
+    for (int h = 0; h < 2; ++h)
+        for (const auto &ch : pow2_chunks(KP)) {
+            o << "    asm volatile(\"tcgen05.st.sync.aligned.32x32b.x" << ch.second << ".b32 [%0], "
+              << reglist(ch.second, 1) << ";\" :: \"r\"(tl + " << (h * KP + ch.first) << "u)";
+            for (int q = 0; q < ch.second; ++q) o << ", \"r\"(" << (h ? "tw" : "th") << (ch.first + q) << ")";
+            o << " : \"memory\");\n";
+        }
+    o << "    asm volatile(\"tcgen05.wait::st.sync.aligned;\" ::: \"memory\");\n";
+    o << "    asm volatile(\"tcgen05.fence::before_thread_sync;\" ::: \"memory\");\n";
+    o << "    asm volatile(\"bar.sync %0, 128;\" :: \"r\"(nb) : \"memory\");\n";
+    o << "    if (lt == 0) {\n";
+    o << "      asm volatile(\"tcgen05.fence::after_thread_sync;\" ::: \"memory\");\n";
+    // smem descriptors: start >> 4, LBO 128 B, SBO 32 KP B, version 1, no swizzle
+    o << "      const unsigned long long dbase = ((unsigned long long)(" << 8 * KP * 4 << " >> 4) << 32) |"
+         " ((unsigned long long)(128 >> 4) << 16) | (1ull << 46);\n";
+    const char *mma =
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p; }";
+    struct Prod { int acol; int boff; };
+    const Prod prods[3] = {{0, 0}, {0, N * KP * 4}, {KP, 0}};
+    for (int pi = 0; pi < 3; ++pi)
+        for (int s2 = 0; s2 < KP / 8; ++s2) {
+            o << "      asm volatile(\"" << mma << "\" :: \"r\"(tm + " << 2 * KP << "u), \"r\"(tm + "
+              << (prods[pi].acol + 8 * s2) << "u), \"l\"(dbase | (unsigned long long)(((sb + "
+              << (prods[pi].boff + 256 * s2) << "u) & 0x3FFFFu) >> 4)), \"r\"(" << idesc << "u), \"r\"("
+              << ((pi == 0 && s2 == 0) ? 0 : 1) << "u) : \"memory\");\n";
+        }
+    o << "      asm volatile(\"tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\" :: "
+         "\"r\"(bar) : \"memory\");\n";
+    o << "    }\n";
+    o << "    pending = true;\n    pi = i;\n    pst = stt;\n    ppsi = tpsi;\n";
+    for (int q = 0; q < D; ++q) o << "    pa" << q << " = ta" << q << ";\n";
+    o << "  }\n#undef LS_OUT_OF_RANGE\n";
+    // a wait that gave up: wait once more (bounded) for the products in flight
+    // before the tensor memory is released
+    o << "  if (bad && lt == 0) ls_mbar_poll(bar, phase, 0);\n";
+    o << "  asm volatile(\"tcgen05.fence::before_thread_sync;\" ::: \"memory\");\n";
+    o << "  __syncthreads();\n";
+    o << "  if (warp == 0) asm volatile(\"tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\" :: \"r\"(ls_tbase), \"r\"("
+      << alloc << "u) : \"memory\");\n";
+    o << "}\n\n";
+    info.fma_value = e.fma - fma0;
+}
+
 // Tile edge (grid indices per axis) of the staged kernel: var.stage when > 1,
 // else 12 for the scale-2 lattices and 16 for the Cartesian one.
 int stage_edge(const Table &t, const ls_variant &var)
@@ -2051,7 +2310,10 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
         g.info.n_sites = n;
     }
     g.info.reach = reach;
-    if (var.stage && t.dim == 3) {
+    if (var.tensor && t.sep.empty()) {
+        emit_eval_point(e, t, var, st, reach, false, kname(t, "eval_pt"));
+        emit_eval_kernel_tensor(e, t, var, st, reach, g.info);
+    } else if (var.stage && t.dim == 3) {
         g.info.eval_smem = emit_eval_kernel_staged(e, t, var, st, reach, g.info);
     } else if (var.producers > 0 && t.sep.empty()) {
         emit_eval_point(e, t, var, st, reach, false, kname(t, "eval_pt"));

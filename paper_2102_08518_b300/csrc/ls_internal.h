@@ -55,6 +55,7 @@ struct GenInfo {
     double wmax = 1.0;      // bound on |w_j(u)| over the region of evaluation
     int eval_smem = 0;      // dynamic shared memory of the value kernel (warp-specialized, staged)
     int stage_edge = 0;     // staged value kernel: tile edge in grid indices (0: not staged)
+    int tmem_cols = 0;      // tensor-core value kernel: tensor memory columns per block (0: FMA path)
 };
 
 struct Generated {

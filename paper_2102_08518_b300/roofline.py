@@ -103,3 +103,28 @@ def distinct_lines_per_point(table, ext, pts: np.ndarray, elem_bytes: int = 4, l
     sec.sort(axis=1)
     distinct = (np.diff(sec, axis=1) != 0).sum(axis=1) + 1 - (sec[:, 0] < 0)
     return float(distinct.mean())
+
+
+def tensor_shape(table, expansion: str = "sparse"):
+    """Shape of the coefficient-transform product of the tensor-core value
+    kernel: K = union stencil sites rounded up to 8 (the TF32 product's K step),
+    N = the (region, monomial) columns with a nonzero entry rounded up to 16
+    (at least 16), and the nonzero count of the transform matrix (the FMA
+    path's multiply-adds).  Returns (K, N, nnz)."""
+    regions = table.regions_centroid if expansion == "centroid" and table.regions_centroid else table.regions
+    union = []
+    for r in regions:
+        for s in r.sites:
+            if tuple(s) not in union:
+                union.append(tuple(s))
+    ncol, nnz = 0, 0
+    for r in regions:
+        M = r.coef_matrix()
+        for a in range(len(r.monomials)):
+            col = sum(1 for j in range(len(r.sites)) if M[j][a] != 0)
+            if col:
+                ncol += 1
+                nnz += col
+    K = (len(union) + 7) // 8 * 8
+    N = max(16, (ncol + 15) // 16 * 16)
+    return K, N, nnz

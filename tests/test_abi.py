@@ -165,3 +165,44 @@ def test_stage_variant_is_validated_before_any_device_call():
         out = ctypes.c_void_p()
         assert L.ls_spline_create(ctypes.byref(h.desc), dt, ctypes.byref(_abi.variant(**var)), ctypes.byref(out)) == 1
         assert b"stage" in L.ls_last_error() or b"3D" in L.ls_last_error() or b"FP32" in L.ls_last_error()
+
+
+def test_tensor_variant_is_validated_before_any_device_call():
+    """The tensor-core value kernel needs a non-separable table and excludes the
+    other value-kernel variants."""
+    L = _abi.lib()
+    for name, var in (("tricubic", {"tensor": 1}), ("trilinear", {"tensor": 1}),
+                      ("bcc_quintic", {"tensor": 1, "stage": 1}), ("fcc6", {"tensor": 1, "producers": 2}),
+                      ("bcc_quintic", {"tensor": 1, "pts_per_thread": 4})):
+        h = _abi.DescHolder(table(name), "probe")
+        out = ctypes.c_void_p()
+        assert L.ls_spline_create(ctypes.byref(h.desc), _abi.LS_F32, ctypes.byref(_abi.variant(**var)),
+                                  ctypes.byref(out)) == 1
+        assert b"tensor" in L.ls_last_error()
+
+
+def test_tensor_variant_source():
+    """The generated value kernel issues tcgen05 products from tensor memory and
+    keeps the transform matrix as TF32 hi / lo pairs."""
+    import re
+    from paper_2102_08518_b300 import api
+    var = {"tensor": 1}
+    name = api.kernel_name("bcc_quintic", "f32", **var)
+    h = _abi.DescHolder(table("bcc_quintic"), name)
+    assert _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), _abi.LS_F32, ctypes.byref(_abi.variant(**var))) == 0
+    cache = os.path.join(ROOT, "paper_2102_08518_b300", "kcache")
+    files = sorted((f for f in os.listdir(cache) if re.fullmatch(f"ls_{name}_f32_[0-9a-f]+\\.cu", f)),
+                   key=lambda f: os.path.getmtime(os.path.join(cache, f)))
+    src = open(os.path.join(cache, files[-1])).read()
+    kern = src[src.index("ls_eval__"):]
+    assert "tcgen05.mma.cta_group::1.kind::tf32" in kern and "tcgen05.alloc" in kern and "tcgen05.dealloc" in kern
+    assert kern.count("tcgen05.mma.cta_group::1.kind::tf32") == 12        # 3 products x K = 32 in steps of 8
+    # the table's hi / lo entries: every hi is a TF32 value (low 13 mantissa bits zero)
+    import struct
+    tab = src[src.index("ls_tcB_"):]
+    vals = re.findall(r"(-?0x[0-9a-fA-F.p+-]+f|0\.0f)", tab[:tab.index("};")])
+    half = len(vals) // 2
+    for v in vals[:half]:
+        f = float.fromhex(v[:-1]) if v != "0.0f" else 0.0
+        bits = struct.unpack("<I", struct.pack("<f", f))[0]
+        assert bits & 0x1FFF == 0

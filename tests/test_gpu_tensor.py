@@ -1,0 +1,114 @@
+"""The tensor-core value kernel (variant tensor) against the FP64 oracle.
+
+The coefficient transform A = M^T c of a tile of 128 points is one tcgen05
+matrix product (three TF32 products for FP32 accuracy) instead of per-thread
+FMAs; everything else is the FMA kernel's code.  Checked: every non-separable
+spline, tile-ragged point counts, points beyond the arrays, non-finite and
+far points, both linear layouts and BF16 storage, several tiles per block
+(grid-stride loop over the mbarrier phases), and agreement with the FMA
+kernel on 2^20 points.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from oracle import specs as ospecs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-6
+BF16_TOL = 2.0 ** -8 + 2e-6
+ORACLE_SPEC = {"bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6,
+               "zp": ospecs.zp2d}
+EXT = {"bcc_linear": (10, 9, 8), "bcc_quintic": (10, 8, 9), "fcc6": (9, 10, 8), "zp": (14, 12)}
+NAMES = list(EXT)
+
+
+def n_cosets(name):
+    return len(workloads.LATTICES[workloads.SPLINE_LATTICE[name]][2])
+
+
+def volume(name, ext, coef_np, layout="coset", dtype="f32", **kw):
+    from paper_2102_08518_b300.api import Spline, TORCH_DTYPES, Volume, relayout
+    c = torch.from_numpy(coef_np.astype(np.float32)).cuda()
+    if layout == "interleaved":
+        c = relayout(c, n_cosets(name), ext, to="interleaved")
+    return Volume(Spline(name, dtype, **kw), ext, c.to(TORCH_DTYPES[dtype]).contiguous(), layout=layout)
+
+
+def oracle_eval(name, ext, coef_np, pts):
+    spec = ORACLE_SPEC[name]().with_extent(ext)
+    return oracle.eval_sum(spec, coef_np.astype(np.float64).ravel(), pts.astype(np.float64))
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 3001])
+def test_tensor_matches_oracle(name, n):
+    ext = EXT[name]
+    lat = workloads.SPLINE_LATTICE[name]
+    coef = workloads.coef_uniform(lat, ext, seed=21)
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = workloads.points_uniform(n, lo - 2.5, hi + 2.5, seed=n + 7)
+    vol = volume(name, ext, coef, tensor=1)
+    got = vol.eval(torch.from_numpy(pts).cuda()).cpu().numpy().astype(np.float64)
+    vol.spline.status()
+    want = oracle_eval(name, ext, coef, pts)
+    assert np.max(np.abs(got - want)) <= TOL * np.abs(coef).max()
+
+
+@pytest.mark.parametrize("name", ["bcc_quintic", "fcc6"])
+def test_tensor_special_points(name):
+    """NaN gives NaN, infinite and far points give 0, as in the FMA kernel."""
+    ext = EXT[name]
+    lat = workloads.SPLINE_LATTICE[name]
+    coef = workloads.coef_uniform(lat, ext, seed=22)
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = workloads.points_uniform(300, lo, hi, seed=3)
+    pts[5] = np.nan
+    pts[6, 2] = np.inf
+    pts[7] = 5.0e6
+    pts[8] = lo - 30.0
+    vol = volume(name, ext, coef, tensor=1)
+    got = vol.eval(torch.from_numpy(pts).cuda()).cpu().numpy()
+    assert np.isnan(got[5]) and got[6] == 0.0 and got[7] == 0.0 and got[8] == 0.0
+    keep = np.ones(len(pts), bool)
+    keep[5:9] = False
+    want = oracle_eval(name, ext, coef, pts[keep])
+    assert np.max(np.abs(got[keep] - want)) <= TOL * np.abs(coef).max()
+    assert volume(name, ext, coef, tensor=1).eval(torch.empty(0, 3, device="cuda")).numel() == 0
+
+
+@pytest.mark.parametrize("layout,dtype", [("interleaved", "f32"), ("coset", "bf16"), ("interleaved", "bf16")])
+@pytest.mark.parametrize("name", ["bcc_quintic", "fcc6"])
+def test_tensor_layouts_and_storage(name, layout, dtype):
+    ext = EXT[name]
+    lat = workloads.SPLINE_LATTICE[name]
+    coef = workloads.coef_uniform(lat, ext, seed=23)
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = workloads.points_uniform(2000, lo - 2.0, hi + 2.0, seed=9)
+    vol = volume(name, ext, coef, layout=layout, dtype=dtype, tensor=1)
+    got = vol.eval(torch.from_numpy(pts).cuda()).cpu().numpy().astype(np.float64)
+    want = oracle_eval(name, ext, coef, pts)
+    tol = TOL if dtype == "f32" else BF16_TOL
+    assert np.max(np.abs(got - want)) <= tol * np.abs(coef).max()
+
+
+@pytest.mark.parametrize("name", ["bcc_quintic", "fcc6", "bcc_linear"])
+def test_tensor_agrees_with_fma_kernel_on_many_points(name):
+    """2^20 points, one block per SM (hundreds of tiles per block): both
+    kernels approximate the same exact sum."""
+    ext = (48, 40, 36)
+    lat = workloads.SPLINE_LATTICE[name]
+    coef = workloads.coef_uniform(lat, ext, seed=24)
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = torch.from_numpy(workloads.points_uniform(1 << 20, lo - 1.0, hi + 1.0, seed=5)).cuda()
+    plain = volume(name, ext, coef).eval(pts)
+    vt = volume(name, ext, coef, tensor=1, blocks_per_sm=1)
+    got = vt.eval(pts)
+    vt.spline.status()
+    assert torch.max(torch.abs(got - plain)).item() <= 2 * TOL * float(np.abs(coef).max())
+    idx = np.random.default_rng(1).choice(1 << 20, 1000, replace=False)
+    want = oracle_eval(name, ext, coef, pts.cpu().numpy()[idx])
+    assert np.max(np.abs(got.cpu().numpy()[idx] - want)) <= TOL * np.abs(coef).max()

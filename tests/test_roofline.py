@@ -56,3 +56,27 @@ def test_distinct_sectors_of_the_benchmark_layouts():
     tc = table("tricubic")
     assert distinct_sectors_per_point(tc, ext, ptc, layout="coset") == \
         distinct_sectors_per_point(tc, ext, ptc, layout="interleaved")
+
+
+def test_tensor_shape_matches_the_generated_kernel():
+    """K and N of the transform product against the generated tensor-core
+    kernel's shared-memory table (2 N K floats: TF32 hi and lo)."""
+    import ctypes
+    import os
+    import re
+    from paper_2102_08518_b300 import _abi, api
+    from paper_2102_08518_b300.roofline import tensor_shape
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for name in ("bcc_quintic", "fcc6", "bcc_linear"):
+        K, N, nnz = tensor_shape(api.table(name))
+        kn = api.kernel_name(name, "f32", tensor=1)
+        h = _abi.DescHolder(api.table(name), kn)
+        assert _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), _abi.LS_F32,
+                                               ctypes.byref(_abi.variant(tensor=1))) == 0
+        cache = os.path.join(root, "paper_2102_08518_b300", "kcache")
+        files = sorted((f for f in os.listdir(cache) if re.fullmatch(f"ls_{kn}_f32_[0-9a-f]+\\.cu", f)),
+                       key=lambda f: os.path.getmtime(os.path.join(cache, f)))
+        src = open(os.path.join(cache, files[-1])).read()
+        m = re.search(r"float ls_sB\[(\d+)\]", src)
+        assert int(m.group(1)) == 2 * N * K, name
+        assert K % 8 == 0 and N % 16 == 0 and nnz <= K * N
