@@ -700,7 +700,8 @@ def extra_cg(torch, dev, vols, pts, outs):
 
 
 PROFILE_CASES = ("fcc6_eval", "quintic_eval_interleaved", "quintic_eval_bricked", "quintic_adjoint_atomic", "quintic_adjoint_fixed", "quintic_hessian",
-                 "tricubic_linear_fetch", "morton_sort", "fcc6_eval_sorted", "fcc6_eval_staged")
+                 "tricubic_linear_fetch", "morton_sort", "morton_sort_2e24", "fcc6_eval_sorted",
+                 "fcc6_eval_staged")
 
 
 def run_profile_case(name: str):
@@ -743,9 +744,9 @@ def run_profile_case(name: str):
         else:
             det = "fixed" if name.endswith("fixed") else False
             fn = lambda: vol.adjoint(p, g, dcoef=dc, deterministic=det)
-    elif name == "morton_sort":
+    elif name.startswith("morton_sort"):
         from paper_2102_08518_b300.api import morton_scratch_bytes, morton_sort
-        n = 1 << 26
+        n = 1 << (24 if name.endswith("2e24") else 26)
         lo, hi = workloads.inner_box("fcc6", (128, 128, 128))
         p = workloads.points_uniform_torch(n, lo, hi, seed=5)
         scratch = torch.empty(morton_scratch_bytes(n), dtype=torch.uint8, device=dev)

@@ -1,17 +1,23 @@
 // Stable LSD radix sort of (uint32 key, int32 value) pairs, Morton keys of
 // points, row permutation, and a random-gather probe for the gather roofline.
 //
-// One radix pass (digits of RB bits, 8 or 10):
-//   1. hist:    each block counts the digits of its tile -> hist[digit * nblk + blk]
+// One radix pass (digits of RB = 8 bits) over G blocks, each owning a
+// contiguous chunk of the input (G = a few blocks per SM, so the per-block
+// digit table stays small):
+//   1. hist:    each block counts the digits of its chunk -> hist[digit * G + blk]
 //   2. scan:    exclusive prefix sum over hist (digit-major, so the offsets of
 //               digit d in block b follow all smaller digits and all earlier
 //               blocks of digit d: a stable global order)
-//   3. scatter: each warp ranks its keys in input order with __match_any_sync
-//               (peers with the same digit); the lowest peer adds the group's
-//               size to the warp's digit counter with one shared-memory atomic
-//               and broadcasts the old value (atomics of one warp on one address
-//               keep program order, so ranks stay stable); warps are combined by
-//               a per-digit prefix over warps, keys go to offset + rank.
+//   3. scatter: each block walks its chunk in tiles, in order, keeping a running
+//               output offset per digit.  Inside a tile each warp ranks its keys
+//               in input order with __match_any_sync (peers with the same
+//               digit); the lowest peer adds the group's size to the warp's
+//               digit counter with one shared-memory atomic (atomics of one
+//               warp on one address keep program order, so ranks stay stable;
+//               all rounds' atomics are issued before their results are
+//               used); warps are combined by a per-digit prefix over warps, the
+//               tile is staged in shared memory in digit order and each digit's
+//               run is written to its global offset.
 #include <cstdint>
 
 #include "ls_kernels.h"
@@ -21,22 +27,21 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 16;                       // keys per thread
-constexpr int kTile = kThreads * kItems;         // 4096 keys per block
+constexpr int kItems = 8;                        // keys per thread and tile
+constexpr int kTile = kThreads * kItems;         // 2048 keys per tile
+constexpr int kMaxChunks = 148 * 8;              // most blocks (chunks of the input) in a pass
 
 template <int RB>
 __global__ void __launch_bounds__(kThreads) hist_kernel(const uint32_t *keys, long long n, int shift,
-                                                         uint32_t *hist, int nblk)
+                                                         long long chunk, uint32_t *hist, int nblk)
 {
     constexpr int kBins = 1 << RB;
     __shared__ uint32_t h[kBins];
     for (int b = threadIdx.x; b < kBins; b += kThreads) h[b] = 0;
     __syncthreads();
-    const long long base = (long long)blockIdx.x * kTile;
-    for (int it = 0; it < kItems; ++it) {
-        long long i = base + (long long)it * kThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kBins - 1)], 1u);
-    }
+    const long long c0 = (long long)blockIdx.x * chunk;
+    const long long c1 = (c0 + chunk < n) ? c0 + chunk : n;
+    for (long long i = c0 + threadIdx.x; i < c1; i += kThreads) atomicAdd(&h[(__ldg(keys + i) >> shift) & (kBins - 1)], 1u);
     __syncthreads();
     for (int b = threadIdx.x; b < kBins; b += kThreads) hist[(size_t)b * nblk + blockIdx.x] = h[b];
 }
@@ -118,96 +123,137 @@ __global__ void __launch_bounds__(1024) scan_down(const uint32_t *in, long long 
     }
 }
 
-// Ranks every key of the tile (stable), stages the tile in shared memory in
-// digit order, then writes each digit's run to its global offset: consecutive
-// threads write consecutive addresses.
+// Ranks the keys of each tile of the block's chunk (stable), stages the tile
+// in shared memory in digit order, then writes each digit's run at the block's
+// running offset of that digit: consecutive threads write consecutive
+// addresses.
 template <int RB>
 __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint32_t *keys, const int32_t *vals, long long n,
-                                                            int shift, const uint32_t *offs, int nblk,
-                                                            uint32_t *keys_out, int32_t *vals_out)
+                                                            int shift, long long chunk, const uint32_t *offs,
+                                                            int nblk, uint32_t *keys_out, int32_t *vals_out)
 {
     constexpr int kBins = 1 << RB;
     constexpr int kPer = kBins / kThreads;         // digits per thread in the digit scans
     extern __shared__ __align__(16) uint32_t sm[];
     uint32_t *whist = sm;                          // [kWarps][kBins]
-    uint32_t *bstart = whist + kWarps * kBins;     // [kBins]
-    uint32_t *goff = bstart + kBins;               // [kBins]
-    uint32_t *tsum = goff + kBins;                 // [kThreads] scan scratch
+    uint32_t *bstart = whist + kWarps * kBins;     // [kBins] tile offsets of the digits
+    uint32_t *run = bstart + kBins;                // [kBins] running global offsets of the digits
+    uint32_t *tsum = run + kBins;                  // [kThreads] scan scratch
     uint32_t *skey = tsum + kThreads;              // [kTile]
     int32_t *sval = (int32_t *)(skey + kTile);     // [kTile]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int b = lane; b < kBins; b += 32) whist[warp * kBins + b] = 0;
-    __syncwarp();
-    // warp w owns the contiguous keys [base + w*32*kItems, ... + 32*kItems), rounds of 32
-    const long long tile0 = (long long)blockIdx.x * kTile;
-    const long long base = tile0 + (long long)warp * 32 * kItems;
-    uint32_t key[kItems];
-    int32_t val[kItems];
-    uint32_t rank[kItems];
     const unsigned lt = (1u << lane) - 1u;
-    for (int it = 0; it < kItems; ++it) {
-        long long i = base + (long long)it * 32 + lane;
-        const bool valid = i < n;
-        key[it] = valid ? keys[i] : 0xFFFFFFFFu;
-        val[it] = valid ? vals[i] : 0;
-        const uint32_t d = (key[it] >> shift) & (kBins - 1);
-        const unsigned active = __ballot_sync(0xFFFFFFFFu, valid);
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, valid ? d : 0xFFFFFFFFu) & active;
-        const int leader = peers ? __ffs(peers) - 1 : 0;
-        uint32_t before = 0u;
-        if (valid && lane == leader) before = atomicAdd(&whist[warp * kBins + d], (uint32_t)__popc(peers));
-        before = __shfl_sync(0xFFFFFFFFu, before, leader);
-        rank[it] = valid ? before + __popc(peers & lt) : 0u;
-    }
-    __syncthreads();
-    // per digit: warp prefix inside the block, block total
-    uint32_t tot[kPer];
     for (int q = 0; q < kPer; ++q) {
         const int b = threadIdx.x * kPer + q;
-        uint32_t run = 0;
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t c = whist[w * kBins + b];
-            whist[w * kBins + b] = run;
-            run += c;
+        run[b] = offs[(size_t)b * nblk + blockIdx.x];
+    }
+    const long long c0 = (long long)blockIdx.x * chunk;
+    const long long c1 = (c0 + chunk < n) ? c0 + chunk : n;
+    uint32_t nkey[kItems];
+    int32_t nval[kItems];
+    {
+        const long long b0 = c0 + (long long)warp * 32 * kItems;
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const long long i = b0 + (long long)it * 32 + lane;
+            const bool valid = i < c1;
+            nkey[it] = valid ? __ldg(keys + i) : 0xFFFFFFFFu;
+            nval[it] = valid ? __ldg(vals + i) : 0;
         }
-        tot[q] = run;
-        goff[b] = offs[(size_t)b * nblk + blockIdx.x];
     }
-    // exclusive scan of the block totals over digits: per-thread sums, then
-    // Hillis-Steele over threads
-    uint32_t mine = 0;
-    for (int q = 0; q < kPer; ++q) mine += tot[q];
-    tsum[threadIdx.x] = mine;
-    __syncthreads();
-    for (int off = 1; off < kThreads; off <<= 1) {
-        const uint32_t v = threadIdx.x >= off ? tsum[threadIdx.x - off] : 0u;
-        __syncthreads();
-        tsum[threadIdx.x] += v;
-        __syncthreads();
-    }
-    uint32_t run = tsum[threadIdx.x] - mine;
-    for (int q = 0; q < kPer; ++q) {
-        bstart[threadIdx.x * kPer + q] = run;
-        run += tot[q];
-    }
-    __syncthreads();
-    for (int it = 0; it < kItems; ++it) {
-        long long i = base + (long long)it * 32 + lane;
-        if (i < n) {
+    for (long long tile0 = c0; tile0 < c1; tile0 += kTile) {
+        for (int b = lane; b < kBins; b += 32) whist[warp * kBins + b] = 0;
+        __syncwarp();
+        // warp w owns the contiguous keys [tile0 + w*32*kItems, ... + 32*kItems), rounds of 32
+        const long long base = tile0 + (long long)warp * 32 * kItems;
+        uint32_t key[kItems], rank[kItems], before[kItems], peers[kItems];
+        int32_t val[kItems];
+        int leader[kItems];
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            key[it] = nkey[it];
+            val[it] = nval[it];
+        }
+        // the next tile's keys and values are in flight while this one is ranked
+        {
+            const long long nb = base + kTile;
+#pragma unroll
+            for (int it = 0; it < kItems; ++it) {
+                const long long i = nb + (long long)it * 32 + lane;
+                const bool valid = i < c1;
+                nkey[it] = valid ? __ldg(keys + i) : 0xFFFFFFFFu;
+                nval[it] = valid ? __ldg(vals + i) : 0;
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const long long i = base + (long long)it * 32 + lane;
+            const bool valid = i < c1;
             const uint32_t d = (key[it] >> shift) & (kBins - 1);
-            const uint32_t lp = bstart[d] + whist[warp * kBins + d] + rank[it];
-            skey[lp] = key[it];
-            sval[lp] = val[it];
+            const unsigned active = __ballot_sync(0xFFFFFFFFu, valid);
+            peers[it] = __match_any_sync(0xFFFFFFFFu, valid ? d : 0xFFFFFFFFu) & active;
+            leader[it] = peers[it] ? __ffs(peers[it]) - 1 : 0;
+            before[it] = 0u;
+            if (valid && lane == leader[it]) before[it] = atomicAdd(&whist[warp * kBins + d], (uint32_t)__popc(peers[it]));
         }
-    }
-    __syncthreads();
-    const long long cnt = (n - tile0) < kTile ? (n - tile0) : kTile;
-    for (int lp = threadIdx.x; lp < cnt; lp += kThreads) {
-        const uint32_t k = skey[lp];
-        const uint32_t d = (k >> shift) & (kBins - 1);
-        const uint32_t dst = goff[d] + (uint32_t)lp - bstart[d];
-        keys_out[dst] = k;
-        vals_out[dst] = sval[lp];
+#pragma unroll
+        for (int it = 0; it < kItems; ++it)
+            rank[it] = __shfl_sync(0xFFFFFFFFu, before[it], leader[it]) + __popc(peers[it] & lt);
+        __syncthreads();
+        // per digit: warp prefix inside the tile, tile total
+        uint32_t tot[kPer];
+        for (int q = 0; q < kPer; ++q) {
+            const int b = threadIdx.x * kPer + q;
+            uint32_t acc = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t c = whist[w * kBins + b];
+                whist[w * kBins + b] = acc;
+                acc += c;
+            }
+            tot[q] = acc;
+        }
+        // exclusive scan of the tile totals over digits: per-thread sums, a
+        // shuffle scan inside each warp, then the warps' totals
+        uint32_t mine = 0;
+        for (int q = 0; q < kPer; ++q) mine += tot[q];
+        uint32_t inc = mine;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+            if (lane >= off) inc += v;
+        }
+        if (lane == 31) tsum[warp] = inc;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (int w = 0; w < warp; ++w) wbase += tsum[w];
+        uint32_t acc = wbase + inc - mine;
+        for (int q = 0; q < kPer; ++q) {
+            bstart[threadIdx.x * kPer + q] = acc;
+            acc += tot[q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const long long i = base + (long long)it * 32 + lane;
+            if (i < c1) {
+                const uint32_t d = (key[it] >> shift) & (kBins - 1);
+                const uint32_t lp = bstart[d] + whist[warp * kBins + d] + rank[it];
+                skey[lp] = key[it];
+                sval[lp] = val[it];
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)((c1 - tile0) < kTile ? (c1 - tile0) : kTile);
+        for (int lp = threadIdx.x; lp < cnt; lp += kThreads) {
+            const uint32_t k = skey[lp];
+            const uint32_t d = (k >> shift) & (kBins - 1);
+            const uint32_t dst = run[d] + (uint32_t)lp - bstart[d];
+            keys_out[dst] = k;
+            vals_out[dst] = sval[lp];
+        }
+        __syncthreads();
+        for (int q = 0; q < kPer; ++q) run[threadIdx.x * kPer + q] += tot[q];
+        // the next tile's first barrier orders these updates before their use
     }
 }
 
@@ -295,16 +341,28 @@ __global__ void bin_starts_kernel(const uint32_t *key, long long n, uint32_t nbi
     }
 }
 
-int nblocks_for(long long n) { return (int)((n + kTile - 1) / kTile); }
+// blocks (chunks) of one pass and the keys per chunk, a whole number of tiles:
+// at least two tiles per chunk (a small digit table) and at most cap chunks
+void chunking(long long n, int cap, int &nblk, long long &chunk)
+{
+    const long long tiles = (n + kTile - 1) / kTile;
+    const long long want = tiles / 2 > 1 ? tiles / 2 : 1;
+    nblk = (int)(want < cap ? want : cap);
+    chunk = (tiles + nblk - 1) / nblk * kTile;
+    nblk = (int)((n + chunk - 1) / chunk);
+    if (nblk < 1) nblk = 1;
+}
 
 }  // namespace
 
-constexpr int kMaxBins = 1024;
+constexpr int kMaxBins = 256;             // 8-bit digits
 
 size_t sort_scratch_bytes(long long n)
 {
-    const long long nblk = nblocks_for(n);
-    const long long nh = nblk * kMaxBins;
+    int nblk;
+    long long chunk;
+    chunking(n, kMaxChunks, nblk, chunk);
+    const long long nh = (long long)nblk * kMaxBins;
     const long long nparts = (nh + kScanChunk - 1) / kScanChunk;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     return al(n * 4) * 2 + al(nh * 4) * 2 + al(nparts * 4) + 256;
@@ -313,16 +371,39 @@ size_t sort_scratch_bytes(long long n)
 cudaError_t radix_sort_pairs(uint32_t *keys, int32_t *vals, long long n, int nbits, void *scratch, cudaStream_t st)
 {
     if (n <= 1) return cudaSuccess;
-    const int nblk = nblocks_for(n);
-    // 10-bit digits when that saves a pass (e.g. 30-bit Morton keys: 3 passes, not 4)
-    const int rb = ((nbits + 9) / 10 < (nbits + 7) / 8) ? 10 : 8;
+    // 8-bit digits: on B300 four 8-bit passes over 30-bit keys beat three 10-bit
+    // ones (3.24 vs 4.14 ms for 2^26 pairs): a 2048-key tile spreads over 256
+    // instead of 1024 digits, so the output runs are 4x longer and the per-warp
+    // digit counters 4x smaller
+    const int rb = 8;
+    // one wave: as many chunks as blocks of the scatter kernel fit on the GPU
+    static int waves[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    int &wave = waves[dev];
+    if (wave == 0) {
+        int sms = 0, per = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaFuncSetAttribute(scatter_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem<8>()) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, scatter_kernel<8>, kThreads, scatter_smem<8>()) != cudaSuccess ||
+            per < 1) {
+            cudaGetLastError();
+            sms = 148;
+            per = 2;
+        }
+        wave = sms * per < kMaxChunks ? sms * per : kMaxChunks;
+    }
+    int nblk;
+    long long chunk;
+    chunking(n, wave, nblk, chunk);
     const long long nh = (long long)nblk * (1 << rb);
     const long long nparts = (nh + kScanChunk - 1) / kScanChunk;
     if (nparts > 8192) return cudaErrorInvalidValue;
-    cudaError_t ea = rb == 10 ? cudaFuncSetAttribute(scatter_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)scatter_smem<10>())
-                              : cudaFuncSetAttribute(scatter_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)scatter_smem<8>());
+    cudaError_t ea = cudaFuncSetAttribute(scatter_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)scatter_smem<8>());
     if (ea != cudaSuccess) return ea;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     char *p = (char *)scratch;
@@ -340,15 +421,11 @@ cudaError_t radix_sort_pairs(uint32_t *keys, int32_t *vals, long long n, int nbi
     int passes = (nbits + rb - 1) / rb;
     for (int ps = 0; ps < passes; ++ps) {
         const int shift = rb * ps;
-        if (rb == 10) hist_kernel<10><<<nblk, kThreads, 0, st>>>(ks, n, shift, hist, nblk);
-        else hist_kernel<8><<<nblk, kThreads, 0, st>>>(ks, n, shift, hist, nblk);
+        hist_kernel<8><<<nblk, kThreads, 0, st>>>(ks, n, shift, chunk, hist, nblk);
         scan_reduce<<<(unsigned)nparts, 1024, 0, st>>>(hist, nh, part);
         scan_parts<<<1, 1024, 0, st>>>(part, (int)nparts);
         scan_down<<<(unsigned)nparts, 1024, 0, st>>>(hist, nh, part, offs);
-        if (rb == 10)
-            scatter_kernel<10><<<nblk, kThreads, scatter_smem<10>(), st>>>(ks, vs, n, shift, offs, nblk, kd, vd);
-        else
-            scatter_kernel<8><<<nblk, kThreads, scatter_smem<8>(), st>>>(ks, vs, n, shift, offs, nblk, kd, vd);
+        scatter_kernel<8><<<nblk, kThreads, scatter_smem<8>(), st>>>(ks, vs, n, shift, chunk, offs, nblk, kd, vd);
         uint32_t *tk = ks; ks = kd; kd = tk;
         int32_t *tv = vs; vs = vd; vd = tv;
     }
