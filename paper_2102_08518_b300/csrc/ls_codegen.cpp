@@ -1508,6 +1508,7 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
       << "(const LsEvalArgs a)\n{\n";
     o << "  __shared__ __align__(1024) float ls_sB[" << 2 * N * KP << "];\n";
     o << "  __shared__ __align__(8) unsigned long long ls_bar[" << S << "];\n";
+    o << "  __shared__ unsigned ls_cnt[" << S << "];\n";
     o << "  __shared__ unsigned ls_tbase;\n";
     o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride, CU = a.cunit;"
          " (void)E1; (void)E2; (void)CS; (void)CU;\n";
@@ -1518,8 +1519,11 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
          "\"r\"((unsigned)__cvta_generic_to_shared(&ls_tbase)), \"r\"(" << alloc << "u) : \"memory\");\n";
     o << "    asm volatile(\"tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\" ::: \"memory\");\n";
     o << "  }\n";
-    o << "  if (threadIdx.x < " << S << ") asm volatile(\"mbarrier.init.shared::cta.b64 [%0], 1;\" :: "
+    o << "  if (threadIdx.x < " << S << ") {\n";
+    o << "    asm volatile(\"mbarrier.init.shared::cta.b64 [%0], 1;\" :: "
          "\"r\"((unsigned)__cvta_generic_to_shared(&ls_bar[threadIdx.x])) : \"memory\");\n";
+    o << "    ls_cnt[threadIdx.x] = 0u;\n";
+    o << "  }\n";
     o << "  asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n";
     o << "  asm volatile(\"tcgen05.fence::before_thread_sync;\" ::: \"memory\");\n";
     o << "  __syncthreads();\n";
@@ -1527,7 +1531,8 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "  const unsigned tm = ls_tbase + slot * " << P.cols << "u;      // this slot's columns\n";
     o << "  const unsigned tl = tm + ((32u * (warp & 3u)) << 16);   // and this warp's quarter of the lanes\n";
     o << "  const unsigned bar = (unsigned)__cvta_generic_to_shared(&ls_bar[slot]);\n";
-    o << "  const unsigned nb = 1u + slot;                       // the slot's named barrier\n";
+    o << "  const unsigned lane = threadIdx.x & 31u;\n";
+    o << "  const unsigned cnt = (unsigned)__cvta_generic_to_shared(&ls_cnt[slot]);   // warps staged, mod 4\n";
     o << "  const unsigned sb = (unsigned)__cvta_generic_to_shared(ls_sB);\n";
     o << "  unsigned phase = 0;\n  bool pending = false, bad = false;\n";
     o << "  long long pi = 0;\n  int pst = 2, ppsi = 0;\n  float pa0 = 0.0f, pa1 = 0.0f, pa2 = 0.0f;\n";
@@ -1556,11 +1561,11 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "    }\n";
     // results of the previous tile
     o << "    if (pending) {\n";
-    o << "      const bool ok = lt == 0 ? ls_mbar_poll(bar, phase, a.status) : true;\n";
-    o << "      unsigned anybad;\n";
-    o << "      asm volatile(\"{ .reg .pred p, q; setp.eq.u32 q, %1, 0; bar.red.or.pred p, %2, 128, q;"
-         " selp.u32 %0, 1, 0, p; }\" : \"=r\"(anybad) : \"r\"((unsigned)ok), \"r\"(nb) : \"memory\");\n";
-    o << "      if (anybad) { bad = true; break; }\n";
+    // each warp waits for the product on its own (lane 0 polls)
+    o << "      unsigned okw = 1u;\n";
+    o << "      if (lane == 0) okw = ls_mbar_poll(bar, phase, a.status) ? 1u : 0u;\n";
+    o << "      okw = __shfl_sync(0xffffffffu, okw, 0);\n";
+    o << "      if (!okw) { bad = true; break; }\n";
     o << "      phase ^= 1u;\n";
     o << "      asm volatile(\"tcgen05.fence::after_thread_sync;\" ::: \"memory\");\n";
     for (int q = 0; q < N; ++q) o << "      unsigned td" << q << ";\n";
@@ -1606,8 +1611,14 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
         }
     o << "    asm volatile(\"tcgen05.wait::st.sync.aligned;\" ::: \"memory\");\n";
     o << "    asm volatile(\"tcgen05.fence::before_thread_sync;\" ::: \"memory\");\n";
-    o << "    asm volatile(\"bar.sync %0, 128;\" :: \"r\"(nb) : \"memory\");\n";
-    o << "    if (lt == 0) {\n";
+    // no barrier: each warp counts itself in (release / acquire on the slot's
+    // counter); the fourth warp of the tile issues the product, which thereby
+    // follows every warp's tcgen05.st of this tile and tcgen05.ld of the last
+    o << "    __syncwarp();\n";
+    o << "    unsigned arrived = 0u;\n";
+    o << "    if (lane == 0) asm volatile(\"atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;\" : \"=r\"(arrived) : "
+         "\"r\"(cnt) : \"memory\");\n";
+    o << "    if (lane == 0 && (arrived & 3u) == 3u) {\n";
     o << "      asm volatile(\"tcgen05.fence::after_thread_sync;\" ::: \"memory\");\n";
     // smem descriptors: start >> 4, LBO 128 B, SBO 32 KP B, version 1, no swizzle
     o << "      const unsigned long long dbase = ((unsigned long long)(" << 8 * KP * 4 << " >> 4) << 32) |"
@@ -1631,7 +1642,7 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "  }\n#undef LS_OUT_OF_RANGE\n";
     // a wait that gave up: wait once more (bounded) for the products in flight
     // before the tensor memory is released
-    o << "  if (bad && lt == 0) ls_mbar_poll(bar, phase, 0);\n";
+    o << "  if (bad && lane == 0) ls_mbar_poll(bar, phase, 0);\n";
     o << "  asm volatile(\"tcgen05.fence::before_thread_sync;\" ::: \"memory\");\n";
     o << "  __syncthreads();\n";
     o << "  if (warp == 0) asm volatile(\"tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\" :: \"r\"(ls_tbase), \"r\"("
