@@ -188,8 +188,9 @@ typedef struct {
                                           A = M^T c of each tile of 128 points as one matrix product
                                           on the tensor cores (tcgen05.mma kind::tf32, three TF32
                                           products for FP32 accuracy, accumulator in tensor memory);
-                                          one block per SM with S slots of 128 points (S = T for
-                                          T = 2..4, else 4; forces block = 128 S); non-separable
+                                          one block per SM with S slots of 128 points, S = as many
+                                          as the 512 tensor-memory columns hold (at most 8), or T if
+                                          T = 2..8 is smaller; forces block = 128 S; non-separable
                                           tables.  Bounded mbarrier waits (ls_spline_status) */
 } ls_variant;
 

@@ -256,8 +256,6 @@ ls_variant default_variant(const ls_variant *v)
         r.producers = v->producers > 0 ? v->producers : 0;
         r.stage = v->stage > 0 ? v->stage : 0;
         r.tensor = v->tensor > 0 ? v->tensor : 0;
-        // S slots of 128 points (the 128 lanes of tensor memory), S = 2..4 (default 4)
-        if (r.tensor) r.block = 128 * ((r.tensor >= 2 && r.tensor <= 4) ? r.tensor : 4);
     }
     return r;
 }
@@ -299,6 +297,8 @@ ls_status ls_spline_precompile(const ls_spline_desc *desc, ls_dtype dt, const ls
     if (st != LS_OK) return st;
     if (dt != LS_F32 && dt != LS_BF16 && dt != LS_F16) return ls_fail(LS_ERR_UNSUPPORTED, "coef dtype");
     ls_variant var = default_variant(variant);
+    // tensor-core kernel: slots of 128 points (the 128 lanes of tensor memory)
+    if (var.tensor && t.sep.empty()) var.block = 128 * ls::tensor_slots(t, var);
     ls::Generated g = ls::generate(t, dt, var);
     std::vector<char> cubin;
     std::string err;
@@ -341,6 +341,7 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
             return ls_fail(LS_ERR_INVALID_ARG, why);
         }
     }
+    if (s->var.tensor) s->var.block = 128 * ls::tensor_slots(s->table, s->var);
     if (s->var.stage > 0) {
         const int C = (int)s->table.cosets.size();
         const int edge = s->var.stage > 1 ? s->var.stage : (s->table.scale == 2 ? 12 : 16);

@@ -1432,8 +1432,7 @@ TensorPlan tensor_plan(const Table &t, const Stencil &st)
         for (const auto &m : p.sup[k]) p.col[k][m] = p.ncol++;
     }
     p.n = std::max(16, (p.ncol + 15) / 16 * 16);
-    p.cols = 32;
-    while (p.cols < 2 * p.kp + p.n) p.cols *= 2;
+    p.cols = (2 * p.kp + p.n + 15) / 16 * 16;    // one slot's columns: A hi, A lo, D
     return p;
 }
 
@@ -1459,8 +1458,20 @@ std::vector<std::pair<int, int>> pow2_chunks(int n)
     return r;
 }
 
-// Slots per block of the tensor-core kernel: var.tensor when 2..4, else 4.
-int tensor_slots(const ls_variant &var) { return (var.tensor >= 2 && var.tensor <= 4) ? var.tensor : 4; }
+}  // namespace
+
+// Slots (128-point tiles in flight) per block of the tensor-core kernel: as
+// many as the 512 tensor-memory columns hold, at most 8 (1024 threads);
+// var.tensor = 2..8 asks for fewer.
+int tensor_slots(const Table &t, const ls_variant &var)
+{
+    const int cols = tensor_plan(t, union_stencil(t)).cols;
+    int s = std::max(1, std::min(8, 512 / cols));
+    if (var.tensor >= 2 && var.tensor < s) s = var.tensor;
+    return s;
+}
+
+namespace {
 
 // One block per SM (a block that allocates tensor memory is the only one on
 // its SM) with S slots of 4 warps; each slot owns 128 points at a time, a
@@ -1475,7 +1486,7 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     const int D = t.dim;
     const size_t K = t.ref.size();
     const TensorPlan P = tensor_plan(t, st);
-    const int KP = P.kp, N = P.n, NU = P.nu, S = tensor_slots(var);
+    const int KP = P.kp, N = P.n, NU = P.nu, S = tensor_slots(t, var);
     int alloc = 32;
     while (alloc < S * P.cols) alloc *= 2;
     info.tmem_cols = alloc;
