@@ -162,9 +162,10 @@ typedef struct {
     int32_t min_blocks;                /* __launch_bounds__ minimum blocks per SM (0 = none) */
     int32_t group;                     /* m: sites per gather group (0 = all) */
     int32_t depth;                     /* d: groups in flight (0 = unlimited) */
-    int32_t blocks_per_sm;             /* grid = SMs x blocks_per_sm for the evaluation kernels
-                                          (0 = as many as fit); bounds the resident warps per SM
-                                          without taking L1 away (no recompilation) */
+    int32_t blocks_per_sm;             /* grid = SMs x blocks_per_sm for the evaluation and the
+                                          per-point adjoint kernels (0 = as many as fit); bounds
+                                          the resident warps per SM without taking L1 away (no
+                                          recompilation) */
     int32_t brick;                     /* 1: the kernels address LS_LAYOUT_BRICKED volumes (and only
                                           those); 0: the linear layouts (coset-major, interleaved) */
     int32_t pipeline;                  /* 1: the value kernel issues the gathers of a thread's next
@@ -343,12 +344,28 @@ ls_status ls_eval_host_multi(int32_t n_vol, const ls_volume *vols, const float *
  *                         table), so no sum can overflow; each value is off by at
  *                         most 2^-(s+1) before the final FP32 rounding.  A
  *                         non-finite gout gives an unspecified result.
+ *   LS_ADJ_ATOMIC_TILED:  for spatially sorted points (Morton order): a block
+ *                         of consecutive points whose stencils fit one tile of
+ *                         grid indices (edge up to 16 on BCC/FCC, 24 on the
+ *                         Cartesian grid, at most 48 KiB of shared memory;
+ *                         variant.stage > 1 sets the edge)
+ *                         sums its contributions in shared memory and adds
+ *                         each touched coefficient to dcoef once; other blocks
+ *                         add per (point, site) as LS_ADJ_ATOMIC.  Order-
+ *                         dependent in the last bits, like LS_ADJ_ATOMIC.
+ *   LS_ADJ_DETERMINISTIC_FIXED_TILED: the same tiling on the fixed-point
+ *                         integers of LS_ADJ_DETERMINISTIC_FIXED: bitwise
+ *                         identical to that mode (needs its scratch).
+ * The tiled modes need a linear layout (coset-major or interleaved); on a
+ * bricked volume they run as their untiled counterparts.
  */
 typedef enum {
     LS_ADJ_ATOMIC = 0,
     LS_ADJ_DETERMINISTIC = 1,
     LS_ADJ_ATOMIC_WARP = 2,
-    LS_ADJ_DETERMINISTIC_FIXED = 3
+    LS_ADJ_DETERMINISTIC_FIXED = 3,
+    LS_ADJ_ATOMIC_TILED = 4,
+    LS_ADJ_DETERMINISTIC_FIXED_TILED = 5
 } ls_adjoint_mode;
 
 /*

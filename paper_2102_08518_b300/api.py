@@ -246,11 +246,13 @@ class Volume:
         return out_host
 
     def adjoint(self, pts: torch.Tensor, gout: torch.Tensor, dcoef: Optional[torch.Tensor] = None,
-                deterministic: bool = False, warp_aggregated: bool = False, stream=None) -> torch.Tensor:
+                deterministic: bool = False, warp_aggregated: bool = False, tiled: bool = False,
+                stream=None) -> torch.Tensor:
         """dcoef += A^T gout in the volume's layout: atomic (default), bitwise
-        deterministic, or atomic with warp aggregation of equal sites."""
+        deterministic, or atomic with warp aggregation of equal sites; tiled:
+        per-block shared-memory sums for spatially sorted points."""
         pts = _check_pts(pts, self.spline.dim)
-        mode = _adjoint_mode(deterministic, warp_aggregated)
+        mode = _adjoint_mode(deterministic, warp_aggregated, tiled)
         gout = gout.contiguous().float()
         if dcoef is None:
             dcoef = torch.zeros(self.n_coef, device=pts.device, dtype=torch.float32)
@@ -269,11 +271,17 @@ class Volume:
             self.handle = None
 
 
-def _adjoint_mode(deterministic, warp_aggregated: bool) -> int:
+def _adjoint_mode(deterministic, warp_aggregated: bool, tiled: bool = False) -> int:
     """deterministic: False, True / "binned" (fixed summation order) or "fixed"
-    (fixed-point integer atomics); warp_aggregated: aggregated FP32 atomics."""
+    (fixed-point integer atomics); warp_aggregated: aggregated FP32 atomics;
+    tiled: shared-memory tiles for spatially sorted points (FP32 atomics or,
+    with deterministic="fixed", the fixed-point sums)."""
     if deterministic and warp_aggregated:
         raise ValueError("choose deterministic or warp_aggregated")
+    if tiled:
+        if warp_aggregated or deterministic not in (False, "fixed"):
+            raise ValueError("tiled goes with the atomic or the fixed-point adjoint")
+        return _abi.LS_ADJ_DETERMINISTIC_FIXED_TILED if deterministic == "fixed" else _abi.LS_ADJ_ATOMIC_TILED
     if deterministic == "fixed":
         return _abi.LS_ADJ_DETERMINISTIC_FIXED
     if deterministic:
@@ -356,7 +364,8 @@ def probe_gather(table_t: torch.Tensor, loads: int, nthreads: int, blocks: int =
 # ---------------------------------------------------------------------------
 
 def cg_fit(volume: "Volume", pts: torch.Tensor, y: torch.Tensor, lam: float = 0.0, max_iter: int = 200,
-           rel_tol: float = 1e-6, deterministic: bool = False, warp_aggregated: bool = False, stream=None):
+           rel_tol: float = 1e-6, deterministic: bool = False, warp_aggregated: bool = False, tiled: bool = False,
+           stream=None):
     """CGLS on min ||A c - y||^2 + lam ||c||^2; the volume's coefficients (FP32)
     hold the initial guess and receive the result.  Returns (iterations, history)."""
     import numpy as np
@@ -365,7 +374,7 @@ def cg_fit(volume: "Volume", pts: torch.Tensor, y: torch.Tensor, lam: float = 0.
     hist = np.zeros(max_iter + 1)
     iters = ctypes.c_int32()
     _abi.check(_abi.lib().ls_cg_fit(volume.handle, _ptr(pts), _ptr(y), pts.shape[0], float(lam), int(max_iter),
-                                    float(rel_tol), _adjoint_mode(deterministic, warp_aggregated),
+                                    float(rel_tol), _adjoint_mode(deterministic, warp_aggregated, tiled),
                                     hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(iters),
                                     _stream(stream)), "ls_cg_fit")
     return iters.value, hist[: iters.value + 1]

@@ -388,6 +388,8 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
         (st = get_kernel(s, "adjoint_atomic", s->mod.adj_atomic, s->mod.blocks_per_sm_adj)) != LS_OK ||
         (st = get_kernel(s, "adjoint_warpagg", s->mod.adj_warpagg, s->mod.blocks_per_sm_warpagg)) != LS_OK ||
         (st = get_kernel(s, "adjoint_fixed", s->mod.adj_fixed, s->mod.blocks_per_sm_fixed)) != LS_OK ||
+        (st = get_kernel(s, "adjoint_tile", s->mod.adj_tile, s->mod.blocks_per_sm_tile)) != LS_OK ||
+        (st = get_kernel(s, "adjoint_tile_fixed", s->mod.adj_tile_fixed, s->mod.blocks_per_sm_tile_fixed)) != LS_OK ||
         (st = get_kernel(s, "adjoint_bin", s->mod.roe_key, s->mod.blocks_per_sm_gather)) != LS_OK ||
         (st = get_kernel(s, "adjoint_gather", s->mod.adj_gather, s->mod.blocks_per_sm_gather)) != LS_OK) {
         cudaFree(s->status);
@@ -411,6 +413,23 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
             return ls_fail(LS_ERR_UNSUPPORTED, "the warp-specialized kernel does not fit on an SM (shared memory)");
         }
         s->mod.blocks_per_sm_eval = nb;
+    }
+    {
+        // tiled adjoint kernels: their shared-memory tile and the resulting occupancy
+        const struct { cudaKernel_t k; int smem; int *per; } tk[2] = {
+            {s->mod.adj_tile, s->gen.info.adj_tile_smem, &s->mod.blocks_per_sm_tile},
+            {s->mod.adj_tile_fixed, s->gen.info.adj_tile_fixed_smem, &s->mod.blocks_per_sm_tile_fixed}};
+        for (const auto &x : tk) {
+            int nb = 0;
+            cudaError_t e2 = cudaFuncSetAttribute((const void *)x.k, cudaFuncAttributeMaxDynamicSharedMemorySize, x.smem);
+            if (e2 == cudaSuccess)
+                e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)x.k, s->var.block, x.smem);
+            if (e2 != cudaSuccess || nb < 1) {
+                cudaGetLastError();
+                nb = 0;               // the tiled modes then take the per-point kernels
+            }
+            *x.per = nb;
+        }
     }
     if (s->gen.info.tmem_cols > 0)
         // tensor-core value kernel: one block per SM (a block that allocates
@@ -852,18 +871,31 @@ size_t ls_adjoint_scratch_bytes(ls_volume v, int64_t n)
     return binned > fixed ? binned : fixed;
 }
 
+// resident blocks per SM for a launch: the occupancy figure, capped by
+// variant.blocks_per_sm when set
+static int per_sm_of(const ls_spline_s *s, int occupancy)
+{
+    return s->var.blocks_per_sm > 0 ? std::max(1, std::min(s->var.blocks_per_sm, occupancy)) : occupancy;
+}
+
 ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int64_t n, float *dcoef,
                           int32_t mode, void *scratch, ls_stream stream)
 {
     if (mode != LS_ADJ_ATOMIC && mode != LS_ADJ_DETERMINISTIC && mode != LS_ADJ_ATOMIC_WARP &&
-        mode != LS_ADJ_DETERMINISTIC_FIXED)
+        mode != LS_ADJ_DETERMINISTIC_FIXED && mode != LS_ADJ_ATOMIC_TILED && mode != LS_ADJ_DETERMINISTIC_FIXED_TILED)
         return ls_fail(LS_ERR_INVALID_ARG, "unknown adjoint mode");
     if (!v || (n > 0 && (!pts || !gout || !dcoef))) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
     if (n < 0) return ls_fail(LS_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return LS_OK;
     ls_spline_s *s = v->spline;
     cudaStream_t st = (cudaStream_t)stream;
-    if (mode == LS_ADJ_DETERMINISTIC_FIXED) {
+    // the tiled kernels address the linear layouts; elsewhere (and if their
+    // tile does not fit an SM) the per-point kernels do the same sums
+    const bool tiled_ok = v->layout != LS_LAYOUT_BRICKED;
+    if (mode == LS_ADJ_ATOMIC_TILED && (!tiled_ok || s->mod.blocks_per_sm_tile < 1)) mode = LS_ADJ_ATOMIC;
+    if (mode == LS_ADJ_DETERMINISTIC_FIXED_TILED && (!tiled_ok || s->mod.blocks_per_sm_tile_fixed < 1))
+        mode = LS_ADJ_DETERMINISTIC_FIXED;
+    if (mode == LS_ADJ_DETERMINISTIC_FIXED || mode == LS_ADJ_DETERMINISTIC_FIXED_TILED) {
         const size_t need = ls_adjoint_scratch_bytes(v, n);
         void *ws = scratch;
         if (!ws && cudaMallocAsync(&ws, need, st) != cudaSuccess) {
@@ -881,8 +913,12 @@ ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int6
         if (res == LS_OK) {
             AdjArgsH a{pts, gout, dcoef, (long long)n, (int)v->ext[0], (int)v->ext[1], (int)v->ext[2],
                        vol_cstride(v), vol_cunit(v), acc, scale};
-            res = launch(s->mod.adj_fixed, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_fixed),
-                         s->var.block, &a, st);
+            if (mode == LS_ADJ_DETERMINISTIC_FIXED_TILED)
+                res = launch(s->mod.adj_tile_fixed, grid_for(n, s->var.block, s->num_sms, per_sm_of(s, s->mod.blocks_per_sm_tile_fixed)),
+                             s->var.block, &a, st, (size_t)s->gen.info.adj_tile_fixed_smem);
+            else
+                res = launch(s->mod.adj_fixed, grid_for(n, s->var.block, s->num_sms, per_sm_of(s, s->mod.blocks_per_sm_fixed)),
+                             s->var.block, &a, st);
         }
         if (res == LS_OK && (e = lsk::fixed_finish(acc, inv, dcoef, v->total_elems, st)) != cudaSuccess)
             res = cuda_fail(e, "fixed-point adjoint finish");
@@ -893,9 +929,12 @@ ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int6
         AdjArgsH a{pts, gout, dcoef, (long long)n, (int)v->ext[0], (int)v->ext[1], (int)v->ext[2],
                    vol_cstride(v), vol_cunit(v), nullptr, nullptr};
         if (mode == LS_ADJ_ATOMIC_WARP)
-            return launch(s->mod.adj_warpagg, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_warpagg),
+            return launch(s->mod.adj_warpagg, grid_for(n, s->var.block, s->num_sms, per_sm_of(s, s->mod.blocks_per_sm_warpagg)),
                           s->var.block, &a, st);
-        return launch(s->mod.adj_atomic, grid_for(n, s->var.block, s->num_sms, s->mod.blocks_per_sm_adj),
+        if (mode == LS_ADJ_ATOMIC_TILED)
+            return launch(s->mod.adj_tile, grid_for(n, s->var.block, s->num_sms, per_sm_of(s, s->mod.blocks_per_sm_tile)),
+                          s->var.block, &a, st, (size_t)s->gen.info.adj_tile_smem);
+        return launch(s->mod.adj_atomic, grid_for(n, s->var.block, s->num_sms, per_sm_of(s, s->mod.blocks_per_sm_adj)),
                       s->var.block, &a, st);
     }
     if (n > ((int64_t)1 << 31) - 1) return ls_fail(LS_ERR_UNSUPPORTED, "more than 2^31-1 points");

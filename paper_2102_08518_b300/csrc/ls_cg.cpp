@@ -33,9 +33,11 @@ extern "C" ls_status ls_cg_fit(ls_volume v, const float *pts, const float *y, in
         return ls_fail(LS_ERR_INVALID_ARG, "n > 0, max_iter >= 0, lambda >= 0 and rel_tol >= 0 required");
     if (v->spline->dtype != LS_F32) return ls_fail(LS_ERR_UNSUPPORTED, "the fit needs FP32 coefficient storage");
     if (adjoint_mode != LS_ADJ_ATOMIC && adjoint_mode != LS_ADJ_DETERMINISTIC && adjoint_mode != LS_ADJ_ATOMIC_WARP &&
-        adjoint_mode != LS_ADJ_DETERMINISTIC_FIXED)
+        adjoint_mode != LS_ADJ_DETERMINISTIC_FIXED && adjoint_mode != LS_ADJ_ATOMIC_TILED &&
+        adjoint_mode != LS_ADJ_DETERMINISTIC_FIXED_TILED)
         return ls_fail(LS_ERR_INVALID_ARG, "unknown adjoint mode");
-    const bool deterministic = adjoint_mode == LS_ADJ_DETERMINISTIC || adjoint_mode == LS_ADJ_DETERMINISTIC_FIXED;
+    const bool deterministic = adjoint_mode == LS_ADJ_DETERMINISTIC || adjoint_mode == LS_ADJ_DETERMINISTIC_FIXED ||
+                               adjoint_mode == LS_ADJ_DETERMINISTIC_FIXED_TILED;
     cudaStream_t st = (cudaStream_t)stream;
     const long long nc = v->total_elems, nr = n;
     const size_t adj_bytes = deterministic ? ls_adjoint_scratch_bytes(v, n) : 0;

@@ -162,7 +162,7 @@ void emit_prologue(Emitter &e)
 //   reference axis r); int ri0.. (reference axis landing on Cartesian axis i);
 //   unsigned ng0.. (sign of Cartesian axis i); int psi;
 // ---------------------------------------------------------------------------
-void emit_classify(Emitter &e, const Table &t)
+void emit_classify(Emitter &e, const Table &t, const char *kshift = nullptr)
 {
     auto &o = e.o;
     const int D = t.dim;
@@ -193,8 +193,12 @@ void emit_classify(Emitter &e, const Table &t)
             o << " }\n";
         }
     }
+    // kshift: k is taken relative to an integer origin (tile-local sites); y,
+    // the fold and the sub-region do not change
     for (int i = 0; i < D; ++i) {
-        o << "    const int k" << i << " = (int)kf" << i << ";\n";
+        o << "    const int k" << i << " = (int)kf" << i;
+        if (kshift) o << " - " << kshift << i;
+        o << ";\n";
         o << "    const float y" << i << " = x" << i << " - kf" << i << ";\n";
     }
     if (t.fold == LS_FOLD_SIGNED_PERM) {
@@ -1460,6 +1464,27 @@ std::vector<std::pair<int, int>> pow2_chunks(int n)
 
 }  // namespace
 
+// The region-of-evaluation part of the classifier alone (the lines up to the
+// site k0..k{D-1}), for kernels that first bound the sites of a block's points.
+std::string roe_only(const Table &t)
+{
+    Emitter tmp;
+    emit_classify(tmp, t);
+    const std::string src = tmp.o.str();
+    std::string keep;
+    size_t pos = 0;
+    int seen = 0;
+    while (pos < src.size() && seen < t.dim) {
+        const size_t nl = src.find('\n', pos);
+        const std::string line = src.substr(pos, nl - pos + 1);
+        keep += line;
+        for (int q = 0; q < t.dim; ++q)
+            if (line.find("const int k" + std::to_string(q) + " = ") != std::string::npos) ++seen;
+        pos = nl + 1;
+    }
+    return keep;
+}
+
 // Slots (128-point tiles in flight) per block of the tensor-core kernel: as
 // many as the 512 tensor-memory columns hold, at most 8 (1024 threads);
 // var.tensor = 2..8 asks for fewer.
@@ -1736,26 +1761,7 @@ int emit_eval_kernel_staged(Emitter &e, const Table &t, const ls_variant &var, c
     o << "    }\n";
     o << "    if (good) {\n";
     // region-of-evaluation site (the same decoding as the point code)
-    {
-        // reuse the classifier's region-of-evaluation part: emit it into a scratch
-        // buffer and keep the lines up to the k definitions
-        Emitter tmp;
-        tmp.ld = e.ld;
-        emit_classify(tmp, t);
-        std::string src = tmp.o.str();
-        std::string keep;
-        size_t pos = 0;
-        int seen = 0;
-        while (pos < src.size() && seen < D) {
-            size_t nl = src.find('\n', pos);
-            std::string line = src.substr(pos, nl - pos + 1);
-            keep += line;
-            for (int q = 0; q < D; ++q)
-                if (line.find("const int k" + std::to_string(q) + " = ") != std::string::npos) ++seen;
-            pos = nl + 1;
-        }
-        o << keep;
-    }
+    o << roe_only(t);
     for (int q = 0; q < D; ++q) o << "      kk[" << q << "] = k" << q << ";\n";
     o << "    }\n";
     // block bounding box of the sites
@@ -1884,36 +1890,17 @@ std::vector<std::string> emit_site_weights(Emitter &e, const Table &t, const Ste
 
 // Atomic adjoint: dcoef[site] += g * w_site for every stencil site of every point.
 // Scatter-add flavours of the point-wise adjoint.
-enum AdjFlavour { ADJ_ATOMIC, ADJ_WARPAGG, ADJ_FIXED };
-
-void emit_adjoint_atomic(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
-                         AdjFlavour fl)
+// The adjoint's work for one point whose coordinates x0.. and gout value gp
+// are loaded: classify (kshift: sites relative to an integer origin), the
+// site weights, the site addresses (ad_j, -1 beyond the arrays) and one add
+// per site, add(address variable, value expression) giving the statement.
+void emit_adjoint_body(Emitter &e, const Table &t, const Stencil &st, int reach,
+                       const std::function<std::string(const std::string &, const std::string &)> &add,
+                       const char *kshift = nullptr)
 {
     auto &o = e.o;
     const int D = t.dim;
-    // one scatter-add of value V at address variable AD
-    auto add = [&](const std::string &ad, const std::string &v) {
-        if (fl == ADJ_WARPAGG) return "ls_agg_add(a.dcoef, " + ad + ", " + v + ");";
-        if (fl == ADJ_FIXED)
-            return "if (" + ad + " >= 0) atomicAdd(a.iacc + " + ad + ", (unsigned long long)__float2ll_rn((" + v +
-                   ") * isc));";
-        return "if (" + ad + " >= 0) atomicAdd(a.dcoef + " + ad + ", " + v + ");";
-    };
-    const char *what = fl == ADJ_WARPAGG ? "adjoint_warpagg" : fl == ADJ_FIXED ? "adjoint_fixed" : "adjoint_atomic";
-    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block << ") " << kname(t, what)
-      << "(const LsAdjArgs a)\n{\n";
-    // fixed point: each value is rounded to an integer multiple of 2^-s and summed
-    // exactly in int64, so the result does not depend on the order of the atomics
-    if (fl == ADJ_FIXED) o << "  const float isc = __ldg(a.iscale);\n";
-    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride, CU = a.cunit;"
-         " (void)E1; (void)E2; (void)CS; (void)CU;\n";
-    o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
-    o << "#define LS_OUT_OF_RANGE(V) { }\n";
-    o << "  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {\n";
-    emit_point_load(e, t);
-    o << "    const float gp = __ldg(a.gout + i);\n";
-    o << "    if (gp == 0.0f) continue;\n";
-    emit_classify(e, t);
+    emit_classify(e, t, kshift);
     if (!t.sep.empty()) {
         // weights per axis
         for (int i = 0; i < D; ++i) {
@@ -1955,9 +1942,175 @@ void emit_adjoint_atomic(Emitter &e, const Table &t, const ls_variant &var, cons
             o << "    " << add("ad" + std::to_string(j), "gp * " + w[j]) << "\n";
         }
     }
+}
+
+enum AdjFlavour { ADJ_ATOMIC, ADJ_WARPAGG, ADJ_FIXED };
+
+void emit_adjoint_atomic(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
+                         AdjFlavour fl)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    // one scatter-add of value V at address variable AD
+    auto add = [&](const std::string &ad, const std::string &v) {
+        if (fl == ADJ_WARPAGG) return "ls_agg_add(a.dcoef, " + ad + ", " + v + ");";
+        if (fl == ADJ_FIXED)
+            return "if (" + ad + " >= 0) atomicAdd(a.iacc + " + ad + ", (unsigned long long)__float2ll_rn((" + v +
+                   ") * isc));";
+        return "if (" + ad + " >= 0) atomicAdd(a.dcoef + " + ad + ", " + v + ");";
+    };
+    const char *what = fl == ADJ_WARPAGG ? "adjoint_warpagg" : fl == ADJ_FIXED ? "adjoint_fixed" : "adjoint_atomic";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block << ") " << kname(t, what)
+      << "(const LsAdjArgs a)\n{\n";
+    // fixed point: each value is rounded to an integer multiple of 2^-s and summed
+    // exactly in int64, so the result does not depend on the order of the atomics
+    if (fl == ADJ_FIXED) o << "  const float isc = __ldg(a.iscale);\n";
+    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride, CU = a.cunit;"
+         " (void)E1; (void)E2; (void)CS; (void)CU;\n";
+    o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
+    o << "#define LS_OUT_OF_RANGE(V) { }\n";
+    o << "  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {\n";
+    emit_point_load(e, t);
+    o << "    const float gp = __ldg(a.gout + i);\n";
+    o << "    if (gp == 0.0f) continue;\n";
+    emit_adjoint_body(e, t, st, reach, add);
     o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
 }
 
+
+// Tile edge (grid indices per axis) of the tiled adjoint: var.stage when > 1,
+// else the largest edge up to 16 (scale 2) or 24 (Cartesian) whose tile of
+// elem-byte values per coset takes at most 48 KiB of shared memory.
+int adjoint_tile_edge(const Table &t, const ls_variant &var, int elem)
+{
+    if (var.stage > 1) return var.stage;
+    const int C = (int)t.cosets.size();
+    int edge = t.scale == 2 ? 16 : 24;
+    auto bytes = [&](int e) {
+        long long v = (long long)C * elem;
+        for (int q = 0; q < t.dim; ++q) v *= e;
+        return v;
+    };
+    while (edge > 4 && bytes(edge) > 48 * 1024) --edge;
+    return edge;
+}
+
+// Tiled adjoint for spatially sorted points.  A block takes blockDim
+// consecutive points, bounds their region-of-evaluation sites, and if their
+// stencils fit one tile of TE^D grid indices per coset, accumulates the
+// points' contributions in shared memory (the tile as a small interleaved
+// volume: element q * C + j) and then adds every nonzero tile element to
+// global memory once: one global atomic per touched coefficient instead of
+// one per (point, site).  Other blocks take the per-point path.  fixed: the
+// values are the fixed-point integers of the deterministic mode, summed with
+// 64-bit integer atomics in shared and global memory (the same integers as
+// the untiled fixed-point kernel, so the same bits).  Returns the dynamic
+// shared memory in bytes.
+int emit_adjoint_tiled(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach, bool fixed)
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    const int C = (int)t.cosets.size();
+    const int sc = t.scale;
+    const int TE = adjoint_tile_edge(t, var, fixed ? 8 : 4);
+    int TN = C;
+    for (int q = 0; q < D; ++q) TN *= TE;
+    const char *T = fixed ? "unsigned long long" : "float";
+    auto gadd = [&](const std::string &ad, const std::string &v) -> std::string {
+        if (fixed)
+            return "if (" + ad + " >= 0) atomicAdd(a.iacc + " + ad + ", (unsigned long long)__float2ll_rn((" + v +
+                   ") * isc));";
+        return "if (" + ad + " >= 0) atomicAdd(a.dcoef + " + ad + ", " + v + ");";
+    };
+    auto tadd = [&](const std::string &ad, const std::string &v) -> std::string {
+        if (fixed)
+            return "if (" + ad + " >= 0) atomicAdd(ls_tile + " + ad + ", (unsigned long long)__float2ll_rn((" + v +
+                   ") * isc));";
+        return "if (" + ad + " >= 0) atomicAdd(ls_tile + " + ad + ", " + v + ");";
+    };
+    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block << ") "
+      << kname(t, fixed ? "adjoint_tile_fixed" : "adjoint_tile") << "(const LsAdjArgs a)\n{\n";
+    o << "  extern __shared__ __align__(16) unsigned char ls_tsm[];\n";
+    o << "  " << T << "* const ls_tile = (" << T << "*)ls_tsm;\n";
+    o << "  __shared__ int s_lo[3], s_hi[3];\n";
+    if (fixed) o << "  const float isc = __ldg(a.iscale);\n";
+    o << "  const int E0 = a.e0, E1 = a.e1, E2 = a.e2, CS = a.cstride, CU = a.cunit;"
+         " (void)E1; (void)E2; (void)CS; (void)CU;\n";
+    o << "#define LS_OUT_OF_RANGE(V) { }\n";
+    o << "  const long long B = blockDim.x;\n";
+    o << "  for (long long t0 = (long long)blockIdx.x * B; t0 < a.n; t0 += (long long)gridDim.x * B) {\n";
+    o << "    if (threadIdx.x < 3) { s_lo[threadIdx.x] = 0x7fffffff; s_hi[threadIdx.x] = -0x7fffffff; }\n";
+    o << "    __syncthreads();\n";
+    o << "    const long long i = t0 + threadIdx.x;\n";
+    o << "    float x0 = 0.0f, x1 = 0.0f, x2 = 0.0f, gp = 0.0f;\n    (void)x2;\n";
+    o << "    bool good = false;\n";
+    o << "    int kk[3] = {0, 0, 0};\n";
+    o << "    if (i < a.n) {\n";
+    for (int q = 0; q < D; ++q) o << "      x" << q << " = __ldg(a.pts + (size_t)i * " << D << " + " << q << ");\n";
+    o << "      gp = __ldg(a.gout + i);\n";
+    o << "      good = gp != 0.0f";
+    for (int q = 0; q < D; ++q) o << " && fabsf(x" << q << ") < 4194304.0f";
+    o << ";\n    }\n";
+    o << "    if (good) {\n" << roe_only(t);
+    for (int q = 0; q < D; ++q) o << "      kk[" << q << "] = k" << q << ";\n";
+    o << "    }\n";
+    for (int q = 0; q < D; ++q) {
+        o << "    {\n      int lo = good ? kk[" << q << "] : 0x7fffffff, hi = good ? kk[" << q << "] : -0x7fffffff;\n";
+        o << "      lo = __reduce_min_sync(0xffffffffu, lo); hi = __reduce_max_sync(0xffffffffu, hi);\n";
+        o << "      if ((threadIdx.x & 31) == 0) { atomicMin(&s_lo[" << q << "], lo); atomicMax(&s_hi[" << q
+          << "], hi); }\n    }\n";
+    }
+    o << "    __syncthreads();\n";
+    o << "    int qlo[3] = {0, 0, 0};\n";
+    o << "    bool fits = s_lo[0] <= s_hi[0];\n";
+    for (int q = 0; q < D; ++q) {
+        if (sc == 2) {
+            o << "    qlo[" << q << "] = (s_lo[" << q << "] - " << reach << ") >> 1;\n";
+            o << "    fits = fits && ((s_hi[" << q << "] + " << reach << ") >> 1) - qlo[" << q << "] < " << TE << ";\n";
+        } else {
+            o << "    qlo[" << q << "] = s_lo[" << q << "] - " << reach << ";\n";
+            o << "    fits = fits && (s_hi[" << q << "] + " << reach << ") - qlo[" << q << "] < " << TE << ";\n";
+        }
+    }
+    o << "    if (fits) {\n";
+    o << "      for (int q = threadIdx.x; q < " << TN << "; q += blockDim.x) ls_tile[q] = 0;\n";
+    o << "      __syncthreads();\n";
+    o << "      if (good) {\n";
+    // the tile as an interleaved volume of TE^D grid indices, sites relative to sc * qlo
+    o << "      const int ksh0 = " << sc << " * qlo[0], ksh1 = " << sc << " * qlo[1], ksh2 = " << sc
+      << " * qlo[2]; (void)ksh1; (void)ksh2;\n";
+    o << "      const int E0 = " << TE << ", E1 = " << TE << ", E2 = " << TE << ", CS = 1, CU = " << C
+      << "; (void)E1; (void)E2; (void)CS; (void)CU;\n";
+    emit_adjoint_body(e, t, st, reach, tadd, "ksh");
+    o << "      }\n";
+    o << "      __syncthreads();\n";
+    // one global add per nonzero tile element inside the arrays
+    o << "      for (int q = threadIdx.x; q < " << TN << "; q += blockDim.x) {\n";
+    o << "        const " << T << " v = ls_tile[q];\n";
+    o << "        if (v == 0) continue;\n";
+    o << "        const int j = q % " << C << ", r = q / " << C << ";\n";
+    o << "        const int g0 = qlo[0] + r % " << TE << ";\n";
+    if (D >= 2) o << "        const int g1 = qlo[1] + (r / " << TE << ") % " << TE << ";\n";
+    if (D == 3) o << "        const int g2 = qlo[2] + r / " << TE * TE << ";\n";
+    o << "        if (g0 < 0 || g0 >= E0";
+    if (D >= 2) o << " || g1 < 0 || g1 >= E1";
+    if (D == 3) o << " || g2 < 0 || g2 >= E2";
+    o << ") continue;\n";
+    o << "        const int ad = j * CS + CU * (g0";
+    if (D >= 2) o << " + E0 * (g1";
+    if (D == 3) o << " + E1 * g2";
+    if (D >= 2) o << ")";
+    o << ");\n";
+    if (fixed) o << "        atomicAdd(a.iacc + ad, v);\n";
+    else o << "        atomicAdd(a.dcoef + ad, v);\n";
+    o << "      }\n";
+    o << "      __syncthreads();\n";
+    o << "    } else if (good) {\n";
+    emit_adjoint_body(e, t, st, reach, gadd);
+    o << "    }\n";
+    o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
+    return TN * (fixed ? 8 : 4);
+}
 
 // ---------------------------------------------------------------------------
 // deterministic adjoint: binning by region-of-evaluation site + per-coefficient gather
@@ -2369,6 +2522,8 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
     emit_adjoint_atomic(e, t, var, st, reach, ADJ_ATOMIC);
     emit_adjoint_atomic(e, t, var, st, reach, ADJ_WARPAGG);
     emit_adjoint_atomic(e, t, var, st, reach, ADJ_FIXED);
+    g.info.adj_tile_smem = emit_adjoint_tiled(e, t, var, st, reach, false);
+    g.info.adj_tile_fixed_smem = emit_adjoint_tiled(e, t, var, st, reach, true);
     g.info.wmax = weight_bound(t);
     emit_adjoint_bin(e, t, var);
     std::vector<I3> doffs = reverse_offsets(t, st);

@@ -56,6 +56,8 @@ struct GenInfo {
     int eval_smem = 0;      // dynamic shared memory of the value kernel (warp-specialized, staged)
     int stage_edge = 0;     // staged value kernel: tile edge in grid indices (0: not staged)
     int tmem_cols = 0;      // tensor-core value kernel: tensor memory columns per block (0: FMA path)
+    int adj_tile_smem = 0;  // tiled adjoint kernels: dynamic shared memory (FP32 / fixed-point tile)
+    int adj_tile_fixed_smem = 0;
 };
 
 struct Generated {
@@ -75,11 +77,11 @@ Generated generate_batch(const std::vector<const Table *> &tables, const std::ve
 struct Module {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t eval = nullptr, eval_grad = nullptr, adj_atomic = nullptr, adj_warpagg = nullptr;
-    cudaKernel_t adj_fixed = nullptr, eval_hess = nullptr;
+    cudaKernel_t adj_fixed = nullptr, eval_hess = nullptr, adj_tile = nullptr, adj_tile_fixed = nullptr;
     cudaKernel_t roe_key = nullptr, adj_gather = nullptr, batch_eval = nullptr;
     int regs_eval = 0;
     int blocks_per_sm_eval = 0, blocks_per_sm_grad = 0, blocks_per_sm_adj = 0, blocks_per_sm_warpagg = 0;
-    int blocks_per_sm_fixed = 0, blocks_per_sm_hess = 0;
+    int blocks_per_sm_fixed = 0, blocks_per_sm_hess = 0, blocks_per_sm_tile = 0, blocks_per_sm_tile_fixed = 0;
     int blocks_per_sm_gather = 0;
 };
 
