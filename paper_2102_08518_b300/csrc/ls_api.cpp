@@ -298,7 +298,7 @@ ls_status ls_spline_precompile(const ls_spline_desc *desc, ls_dtype dt, const ls
     if (dt != LS_F32 && dt != LS_BF16 && dt != LS_F16) return ls_fail(LS_ERR_UNSUPPORTED, "coef dtype");
     ls_variant var = default_variant(variant);
     // tensor-core kernel: slots of 128 points (the 128 lanes of tensor memory)
-    if (var.tensor && t.sep.empty()) var.block = 128 * ls::tensor_slots(t, var);
+    if (var.tensor && t.sep.empty()) var.block = 128 * ls::tensor_slots(t, var, dt);
     ls::Generated g = ls::generate(t, dt, var);
     std::vector<char> cubin;
     std::string err;
@@ -341,7 +341,7 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
             return ls_fail(LS_ERR_INVALID_ARG, why);
         }
     }
-    if (s->var.tensor) s->var.block = 128 * ls::tensor_slots(s->table, s->var);
+    if (s->var.tensor) s->var.block = 128 * ls::tensor_slots(s->table, s->var, dt);
     if (s->var.stage > 0) {
         const int C = (int)s->table.cosets.size();
         const int edge = s->var.stage > 1 ? s->var.stage : (s->table.scale == 2 ? 12 : 16);

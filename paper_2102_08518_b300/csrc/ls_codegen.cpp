@@ -1422,7 +1422,9 @@ struct TensorPlan {
     std::vector<std::map<I3, int>> col;
 };
 
-TensorPlan tensor_plan(const Table &t, const Stencil &st)
+// split: the coefficients need a TF32 hi + lo split (FP32 storage); BF16 and
+// FP16 values are exact in TF32, so their A_lo rows and third product vanish.
+TensorPlan tensor_plan(const Table &t, const Stencil &st, bool split = true)
 {
     TensorPlan p;
     const size_t K = t.ref.size();
@@ -1436,7 +1438,7 @@ TensorPlan tensor_plan(const Table &t, const Stencil &st)
         for (const auto &m : p.sup[k]) p.col[k][m] = p.ncol++;
     }
     p.n = std::max(16, (p.ncol + 15) / 16 * 16);
-    p.cols = (2 * p.kp + p.n + 15) / 16 * 16;    // one slot's columns: A hi, A lo, D
+    p.cols = ((split ? 2 : 1) * p.kp + p.n + 15) / 16 * 16;    // one slot's columns: A hi, [A lo,] D
     return p;
 }
 
@@ -1486,12 +1488,16 @@ std::string roe_only(const Table &t)
 }
 
 // Slots (128-point tiles in flight) per block of the tensor-core kernel: as
-// many as the 512 tensor-memory columns hold, at most 8 (1024 threads);
-// var.tensor = 2..8 asks for fewer.
-int tensor_slots(const Table &t, const ls_variant &var)
+// many as the 512 tensor-memory columns hold, at most 8 (1024 threads), at
+// most 5 for the larger splines; var.tensor = 2..8 asks for fewer.
+int tensor_slots(const Table &t, const ls_variant &var, ls_dtype dt)
 {
-    const int cols = tensor_plan(t, union_stencil(t)).cols;
-    int s = std::max(1, std::min(8, 512 / cols));
+    const TensorPlan p = tensor_plan(t, union_stencil(t), dt == LS_F32);
+    // registers: a thread holds its next tile's K coefficients and its last
+    // tile's N products; past 5 slots (640 threads, 102 registers each) the
+    // larger splines spill (measured: BCC quintic BF16 at 6 slots)
+    const int cap = (p.kp + p.n >= 64) ? 5 : 8;
+    int s = std::max(1, std::min(cap, 512 / p.cols));
     if (var.tensor >= 2 && var.tensor < s) s = var.tensor;
     return s;
 }
@@ -1510,8 +1516,10 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     auto &o = e.o;
     const int D = t.dim;
     const size_t K = t.ref.size();
-    const TensorPlan P = tensor_plan(t, st);
-    const int KP = P.kp, N = P.n, NU = P.nu, S = tensor_slots(t, var);
+    const bool split = e.ld == "ls_ld_f32";     // BF16 / FP16 coefficients are exact in TF32
+    const TensorPlan P = tensor_plan(t, st, split);
+    const int KP = P.kp, N = P.n, NU = P.nu, S = tensor_slots(t, var, split ? LS_F32 : LS_BF16);
+    const int DC = (split ? 2 : 1) * KP;        // first accumulator column of a slot
     int alloc = 32;
     while (alloc < S * P.cols) alloc *= 2;
     info.tmem_cols = alloc;
@@ -1609,7 +1617,7 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
         o << "      asm volatile(\"tcgen05.ld.sync.aligned.32x32b.x" << ch.second << ".b32 " << reglist(ch.second, 0)
           << ", [%" << ch.second << "];\" : ";
         for (int q = 0; q < ch.second; ++q) o << (q ? ", " : "") << "\"=r\"(td" << (ch.first + q) << ")";
-        o << " : \"r\"(tl + " << (2 * KP + ch.first) << "u) : \"memory\");\n";
+        o << " : \"r\"(tl + " << (DC + ch.first) << "u) : \"memory\");\n";
     }
     o << "      asm volatile(\"tcgen05.wait::ld.sync.aligned;\" ::: \"memory\");\n";
     o << "      if (pst == 0) {\n";
@@ -1634,11 +1642,15 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "    if (!have) break;\n";
     // split and stage this tile's coefficients (slot columns [0, KP) hi, [KP, 2 KP) lo)
     for (int j = 0; j < KP; ++j) {
-        o << "    unsigned th" << j << ", tw" << j << ";\n";
-        o << "    asm(\"cvt.rna.tf32.f32 %0, %1;\" : \"=r\"(th" << j << ") : \"f\"(tc" << j << "));\n";
-        o << "    tw" << j << " = __float_as_uint(tc" << j << " - __uint_as_float(th" << j << "));\n";
+        if (split) {
+            o << "    unsigned th" << j << ", tw" << j << ";\n";
+            o << "    asm(\"cvt.rna.tf32.f32 %0, %1;\" : \"=r\"(th" << j << ") : \"f\"(tc" << j << "));\n";
+            o << "    tw" << j << " = __float_as_uint(tc" << j << " - __uint_as_float(th" << j << "));\n";
+        } else {
+            o << "    const unsigned th" << j << " = __float_as_uint(tc" << j << ");   // exact in TF32\n";
+        }
     }
-    for (int h = 0; h < 2; ++h)
+    for (int h = 0; h < (split ? 2 : 1); ++h)
         for (const auto &ch : pow2_chunks(KP)) {
             o << "    asm volatile(\"tcgen05.st.sync.aligned.32x32b.x" << ch.second << ".b32 [%0], "
               << reglist(ch.second, 1) << ";\" :: \"r\"(tl + " << (h * KP + ch.first) << "u)";
@@ -1663,9 +1675,9 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
         "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p; }";
     struct Prod { int acol; int boff; };
     const Prod prods[3] = {{0, 0}, {0, N * KP * 4}, {KP, 0}};
-    for (int pi = 0; pi < 3; ++pi)
+    for (int pi = 0; pi < (split ? 3 : 2); ++pi)
         for (int s2 = 0; s2 < KP / 8; ++s2) {
-            o << "      asm volatile(\"" << mma << "\" :: \"r\"(tm + " << 2 * KP << "u), \"r\"(tm + "
+            o << "      asm volatile(\"" << mma << "\" :: \"r\"(tm + " << DC << "u), \"r\"(tm + "
               << (prods[pi].acol + 8 * s2) << "u), \"l\"(dbase | (unsigned long long)(((sb + "
               << (prods[pi].boff + 256 * s2) << "u) & 0x3FFFFu) >> 4)), \"r\"(" << idesc << "u), \"r\"("
               << ((pi == 0 && s2 == 0) ? 0 : 1) << "u) : \"memory\");\n";

@@ -68,7 +68,7 @@ struct Generated {
 // Code generation (ls_codegen.cpp).
 Generated generate(const Table &t, ls_dtype coef_dtype, const ls_variant &var);
 // 128-point slots per block of the tensor-core value kernel (its block is 128 x that).
-int tensor_slots(const Table &t, const ls_variant &var);
+int tensor_slots(const Table &t, const ls_variant &var, ls_dtype coef_dtype);
 // One persistent kernel ls_batch_eval over the point functions of several splines.
 Generated generate_batch(const std::vector<const Table *> &tables, const std::vector<ls_dtype> &dts,
                          const std::vector<int> &bricks, const ls_variant &var);

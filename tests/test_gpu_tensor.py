@@ -1,8 +1,9 @@
 """The tensor-core value kernel (variant tensor) against the FP64 oracle.
 
 The coefficient transform A = M^T c of a tile of 128 points is one tcgen05
-matrix product (three TF32 products for FP32 accuracy) instead of per-thread
-FMAs; everything else is the FMA kernel's code.  Checked: every non-separable
+matrix product (three TF32 products for FP32 accuracy; two for BF16 / FP16 storage, whose
+values are exact in TF32) instead of per-thread FMAs; everything else is the
+FMA kernel's code.  Checked: every non-separable
 spline, tile-ragged point counts, points beyond the arrays, non-finite and
 far points, both linear layouts and BF16 storage, several tiles per block
 (grid-stride loop over the mbarrier phases), and agreement with the FMA
@@ -20,6 +21,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = 2e-6
 BF16_TOL = 2.0 ** -8 + 2e-6
+F16_TOL = 2.0 ** -11 + 2e-6
 ORACLE_SPEC = {"bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6,
                "zp": ospecs.zp2d}
 EXT = {"bcc_linear": (10, 9, 8), "bcc_quintic": (10, 8, 9), "fcc6": (9, 10, 8), "zp": (14, 12)}
@@ -80,7 +82,8 @@ def test_tensor_special_points(name):
     assert volume(name, ext, coef, tensor=1).eval(torch.empty(0, 3, device="cuda")).numel() == 0
 
 
-@pytest.mark.parametrize("layout,dtype", [("interleaved", "f32"), ("coset", "bf16"), ("interleaved", "bf16")])
+@pytest.mark.parametrize("layout,dtype", [("interleaved", "f32"), ("coset", "bf16"), ("interleaved", "bf16"),
+                                          ("interleaved", "f16")])
 @pytest.mark.parametrize("name", ["bcc_quintic", "fcc6"])
 def test_tensor_layouts_and_storage(name, layout, dtype):
     ext = EXT[name]
@@ -91,7 +94,7 @@ def test_tensor_layouts_and_storage(name, layout, dtype):
     vol = volume(name, ext, coef, layout=layout, dtype=dtype, tensor=1)
     got = vol.eval(torch.from_numpy(pts).cuda()).cpu().numpy().astype(np.float64)
     want = oracle_eval(name, ext, coef, pts)
-    tol = TOL if dtype == "f32" else BF16_TOL
+    tol = {"f32": TOL, "bf16": BF16_TOL, "f16": F16_TOL}[dtype]
     assert np.max(np.abs(got - want)) <= tol * np.abs(coef).max()
 
 
