@@ -694,8 +694,27 @@ def extra_cg(torch, dev, vols, pts, outs):
             dt = time.perf_counter() - t0
             res[f"{name}_{tag}"] = {"ms_per_iter": round(1e3 * dt / max(it, 1), 3), "iters": it,
                                     "resid_ratio": float(hist[-1] / hist[0])}
+        if name == "bcc_quintic":
+            # the samples Morton-sorted once before the fit (with their values):
+            # every iteration's gathers and reductions then have locality
+            from paper_2102_08518_b300.api import morton_sort, permute_rows
+            t0 = time.perf_counter()
+            perm = morton_sort(p, origin=tuple(float(v) for v in lo), cell=1.0)
+            ps, ys = permute_rows(p, perm), permute_rows(y.view(-1, 1), perm).view(-1)
+            torch.cuda.synchronize()
+            sort_ms = 1e3 * (time.perf_counter() - t0)
+            for tag, det in (("atomic", False), ("det_fixed", "fixed")):
+                vol = Volume(sp, ext, torch.zeros(len(workloads.LATTICES[lat][2]) * 128 ** 3, device=dev), layout=lay)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                it, hist = cg_fit(vol, ps, ys, lam=1e-6, max_iter=10, rel_tol=0.0, deterministic=det)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                res[f"{name}_sorted_{tag}"] = {"ms_per_iter": round(1e3 * dt / max(it, 1), 3), "iters": it,
+                                               "resid_ratio": float(hist[-1] / hist[0]),
+                                               "sort_once_ms": round(sort_ms, 3)}
     res["workload"] = ("tricubic 128^3 (bricked) and bcc_quintic 2x128^3 (interleaved), 2^22 samples of "
-                       "exp(-|x-c|^2/400)+0.01N")
+                       "exp(-|x-c|^2/400)+0.01N; bcc_quintic also with the samples Morton-sorted once")
     return res
 
 
