@@ -432,9 +432,9 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
         }
     }
     if (s->gen.info.tmem_cols > 0)
-        // tensor-core value kernel: one block per SM (a block that allocates
-        // tensor memory runs alone on its SM); its slots share the 512 columns
-        s->mod.blocks_per_sm_eval = 1;
+        // tensor-core value (+ gradient) kernels: one block per SM (a block that
+        // allocates tensor memory runs alone on its SM); its slots share the 512 columns
+        s->mod.blocks_per_sm_eval = s->mod.blocks_per_sm_grad = 1;
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, (const void *)s->mod.eval) == cudaSuccess) s->mod.regs_eval = fa.numRegs;
     else cudaGetLastError();

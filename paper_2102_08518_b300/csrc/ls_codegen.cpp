@@ -1511,8 +1511,9 @@ namespace {
 // pipelined: the gathers of tile t are issued before the results of tile
 // t - 1 are read back, so the product of t - 1 runs behind them.
 void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
-                             GenInfo &info)
+                             GenInfo &info, bool grad = false)
 {
+    const bool fold = t.fold == LS_FOLD_SIGNED_PERM;
     auto &o = e.o;
     const int D = t.dim;
     const size_t K = t.ref.size();
@@ -1528,9 +1529,10 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     for (size_t k = 0; k < K; ++k)
         for (const auto &m : P.sup[k])
             for (const auto &pr : P.terms[k].at(m)) B[(size_t)P.col[k].at(m) * KP + pr.first] += pr.second;
+    // the table is emitted with the value kernel; the value + gradient kernel reads it too
     const std::string tab = "ls_tcB_" + kname(t, "eval");
-    o << "static __device__ const float " << tab << "[" << 2 * N * KP << "] = {\n";
-    for (int h = 0; h < 2; ++h)
+    if (!grad) o << "static __device__ const float " << tab << "[" << 2 * N * KP << "] = {\n";
+    for (int h = 0; h < (grad ? 0 : 2); ++h)
         for (int idx = 0; idx < N * KP; ++idx) {
             // idx = (n / 8) * 8 KP + (u / 4) * 32 + (n % 8) * 4 + (u % 4)
             const int g = idx / (8 * KP), rem = idx % (8 * KP);
@@ -1540,7 +1542,7 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
             const double hi = tf32_round(v);
             o << flit(h == 0 ? hi : tf32_round(v - hi)) << ((idx + 1) % 8 == 0 ? ",\n" : ", ");
         }
-    o << "};\n";
+    if (!grad) o << "};\n";
     const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((128u >> 4) << 24);
     auto reglist = [](int cnt, int op0) {
         std::string r = "{";
@@ -1548,8 +1550,8 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
         return r + "}";
     };
     const int fma0 = e.fma;
-    o << "extern \"C\" __global__ void __launch_bounds__(" << 128 * S << ", 1) " << kname(t, "eval")
-      << "(const LsEvalArgs a)\n{\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << 128 * S << ", 1) "
+      << kname(t, grad ? "eval_grad" : "eval") << "(const LsEvalArgs a)\n{\n";
     o << "  __shared__ __align__(1024) float ls_sB[" << 2 * N * KP << "];\n";
     o << "  __shared__ __align__(8) unsigned long long ls_bar[" << S << "];\n";
     o << "  __shared__ unsigned ls_cnt[" << S << "];\n";
@@ -1580,7 +1582,15 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "  const unsigned sb = (unsigned)__cvta_generic_to_shared(ls_sB);\n";
     o << "  unsigned phase = 0;\n  bool pending = false, bad = false;\n";
     o << "  long long pi = 0;\n  int pst = 2, ppsi = 0;\n  float pa0 = 0.0f, pa1 = 0.0f, pa2 = 0.0f;\n";
-    o << "#define LS_OUT_OF_RANGE(V) { a.out[i] = (V); }\n";
+    if (grad) {
+        // the fold of the previous tile's point: reference axis and sign per Cartesian axis
+        o << "  int pri0 = 0, pri1 = 1, pri2 = 2;\n  unsigned png0 = 0u, png1 = 0u, png2 = 0u;\n";
+        o << "#define LS_OUT_OF_RANGE(V) { if (a.out) a.out[i] = (V);";
+        for (int q = 0; q < D; ++q) o << " a.grad[(size_t)i * " << D << " + " << q << "] = (V);";
+        o << " }\n";
+    } else {
+        o << "#define LS_OUT_OF_RANGE(V) { a.out[i] = (V); }\n";
+    }
     o << "  for (long long tile = (long long)blockIdx.x * " << S << " + slot; ; tile += (long long)gridDim.x * " << S
       << ") {\n";
     o << "    const bool have = tile * 128 < a.n;\n";
@@ -1596,12 +1606,15 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << ";\n        LS_OUT_OF_RANGE(isn ? __int_as_float(0x7fffffff) : 0.0f);\n        stt = 1;\n      }\n    }\n";
     for (int j = 0; j < KP; ++j) o << "    float tc" << j << " = 0.0f;\n";
     o << "    float ta0 = 0.0f, ta1 = 0.0f, ta2 = 0.0f;\n    int tpsi = 0;\n";
+    if (grad) o << "    int tri0 = 0, tri1 = 1, tri2 = 2;\n    unsigned tng0 = 0u, tng1 = 0u, tng2 = 0u;\n";
     o << "    if (stt == 0) {\n";
     emit_classify(e, t);
     emit_gathers(e, t, st.sites, reach, "a.coef", false, true, var.group, var.depth);
     for (int j = 0; j < NU; ++j) o << "    tc" << j << " = c" << j << ";\n";
     for (int q = 0; q < D; ++q) o << "    ta" << q << " = a" << q << ";\n";
     o << "    tpsi = psi;\n";
+    if (grad && fold)
+        for (int q = 0; q < D; ++q) o << "    tri" << q << " = ri" << q << "; tng" << q << " = ng" << q << ";\n";
     o << "    }\n";
     // results of the previous tile
     o << "    if (pending) {\n";
@@ -1623,7 +1636,7 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "      if (pst == 0) {\n";
     for (int q = 0; q < D; ++q) o << "      const float a" << q << " = pa" << q << ";\n";
     o << "      const int psi = ppsi; (void)psi;\n";
-    std::vector<std::string> fk;
+    std::vector<std::vector<std::string>> fk;
     for (size_t k = 0; k < K; ++k) {
         std::map<I3, std::string> pre;
         for (const auto &m : P.sup[k]) {
@@ -1631,11 +1644,33 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
             o << "      const float " << nm << " = __uint_as_float(td" << P.col[k].at(m) << ");\n";
             pre[m] = nm;
         }
-        fk.push_back(emit_region_poly(e, t, (int)k, st.region_to_union[k], 0, &pre)[0]);
+        fk.push_back(emit_region_poly(e, t, (int)k, st.region_to_union[k], grad ? 1 : 0, &pre));
     }
-    std::string sel = fk[K - 1];
-    for (int k = (int)K - 2; k >= 0; --k) sel = "(psi == " + std::to_string(k) + ") ? " + fk[k] + " : (" + sel + ")";
-    o << "      a.out[pi] = " << sel << ";\n";
+    // value and (reference-frame) gradient, the region picked by psi
+    std::vector<std::string> out;
+    for (int c = 0; c < (grad ? D + 1 : 1); ++c) {
+        std::string sel = fk[K - 1][c];
+        for (int k = (int)K - 2; k >= 0; --k)
+            sel = "(psi == " + std::to_string(k) + ") ? " + fk[k][c] + " : (" + sel + ")";
+        const std::string nm = c == 0 ? "tf" : "tg" + std::to_string(c - 1);
+        o << "      const float " << nm << " = " << sel << ";\n";
+        out.push_back(nm);
+    }
+    if (!grad) {
+        o << "      a.out[pi] = tf;\n";
+    } else {
+        o << "      if (a.out) a.out[pi] = tf;\n";
+        // back to Cartesian axes: df/dx_i = sign_i * g[reference axis landing on i]
+        for (int q = 0; q < D; ++q) {
+            if (fold) {
+                o << "      { const float gg = ";
+                for (int r = 0; r < D - 1; ++r) o << "(pri" << q << " == " << r << ") ? " << out[1 + r] << " : ";
+                o << out[D] << "; a.grad[(size_t)pi * " << D << " + " << q << "] = png" << q << " ? -gg : gg; }\n";
+            } else {
+                o << "      a.grad[(size_t)pi * " << D << " + " << q << "] = " << out[1 + q] << ";\n";
+            }
+        }
+    }
     o << "      }\n";
     o << "      pending = false;\n";
     o << "    }\n";
@@ -1687,6 +1722,8 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "    }\n";
     o << "    pending = true;\n    pi = i;\n    pst = stt;\n    ppsi = tpsi;\n";
     for (int q = 0; q < D; ++q) o << "    pa" << q << " = ta" << q << ";\n";
+    if (grad)
+        for (int q = 0; q < D; ++q) o << "    pri" << q << " = tri" << q << "; png" << q << " = tng" << q << ";\n";
     o << "  }\n#undef LS_OUT_OF_RANGE\n";
     // a wait that gave up: wait once more (bounded) for the products in flight
     // before the tensor memory is released
@@ -1696,7 +1733,8 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "  if (warp == 0) asm volatile(\"tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\" :: \"r\"(ls_tbase), \"r\"("
       << alloc << "u) : \"memory\");\n";
     o << "}\n\n";
-    info.fma_value = e.fma - fma0;
+    if (grad) info.fma_grad = e.fma - fma0;
+    else info.fma_value = e.fma - fma0;
 }
 
 // Tile edge (grid indices per axis) of the staged kernel: var.stage when > 1,
@@ -2519,7 +2557,8 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
     } else {
         emit_eval_kernel(e, t, var, st, reach, false, g.info);
     }
-    emit_eval_kernel(e, t, var, st, reach, true, g.info);
+    if (var.tensor && t.sep.empty()) emit_eval_kernel_tensor(e, t, var, st, reach, g.info, true);
+    else emit_eval_kernel(e, t, var, st, reach, true, g.info);
     {
         const int fma0 = e.fma;
         const std::string pf = kname(t, "eval_hess_pt");

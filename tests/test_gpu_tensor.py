@@ -115,3 +115,57 @@ def test_tensor_agrees_with_fma_kernel_on_many_points(name):
     idx = np.random.default_rng(1).choice(1 << 20, 1000, replace=False)
     want = oracle_eval(name, ext, coef, pts.cpu().numpy()[idx])
     assert np.max(np.abs(got.cpu().numpy()[idx] - want)) <= TOL * np.abs(coef).max()
+
+
+GRAD_TOL = 1e-5
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("n", [1, 129, 3001])
+def test_tensor_value_gradient_matches_oracle(name, n):
+    """The value + gradient kernel of a tensor-core spline: the same product,
+    then the gradient's Horner forms mapped back through the fold."""
+    ext = EXT[name]
+    lat = workloads.SPLINE_LATTICE[name]
+    coef = workloads.coef_uniform(lat, ext, seed=31)
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = workloads.points_uniform(n, lo - 2.0, hi + 2.0, seed=n + 17)
+    vol = volume(name, ext, coef, layout="interleaved", tensor=1)
+    val, grad = vol.eval_grad(torch.from_numpy(pts).cuda())
+    vol.spline.status()
+    spec = ORACLE_SPEC[name]().with_extent(ext)
+    want, wgrad = oracle.eval_sum_grad(spec, coef.astype(np.float64).ravel(), pts.astype(np.float64))
+    cmax = np.abs(coef).max()
+    assert np.max(np.abs(val.cpu().numpy() - want)) <= TOL * cmax
+    g = grad.cpu().numpy().astype(np.float64)
+    ok = np.ones(len(pts), bool)
+    if name == "bcc_linear":
+        # C0 spline: the gradient jumps across knot planes; compare off them
+        # (one-sided difference quotients of the oracle agree there)
+        h = 1e-4
+        D = pts.shape[1]
+        for q in range(D):
+            e = np.zeros(D)
+            e[q] = h
+            fp = oracle.eval_sum(spec, coef.astype(np.float64).ravel(), pts + e)
+            fm = oracle.eval_sum(spec, coef.astype(np.float64).ravel(), pts - e)
+            ok &= np.abs((fp - want) / h - (want - fm) / h) < 1e-6
+    assert np.max(np.abs(g[ok] - wgrad[ok]), initial=0.0) <= GRAD_TOL * cmax
+
+
+@pytest.mark.parametrize("name", ["bcc_quintic", "fcc6"])
+def test_tensor_value_gradient_agrees_with_fma_kernel(name):
+    ext = (48, 40, 36)
+    lat = workloads.SPLINE_LATTICE[name]
+    coef = workloads.coef_uniform(lat, ext, seed=32)
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = torch.from_numpy(workloads.points_uniform(1 << 20, lo - 1.0, hi + 1.0, seed=6)).cuda()
+    v0, g0 = volume(name, ext, coef, layout="interleaved").eval_grad(pts)
+    vt = volume(name, ext, coef, layout="interleaved", tensor=1)
+    v1, g1 = vt.eval_grad(pts)
+    _, g2 = vt.eval_grad(pts, want_value=False)
+    vt.spline.status()
+    cmax = float(np.abs(coef).max())
+    assert torch.max(torch.abs(v1 - v0)).item() <= 2 * TOL * cmax
+    assert torch.max(torch.abs(g1 - g0)).item() <= 2 * GRAD_TOL * cmax
+    assert torch.equal(g1, g2)
