@@ -28,7 +28,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 16;                       // keys per thread and tile
-constexpr int kTile = kThreads * kItems;         // 2048 keys per tile
+constexpr int kTile = kThreads * kItems;         // 4096 keys per tile
 constexpr int kMaxChunks = 148 * 8;              // most blocks (chunks of the input) in a pass
 
 template <int RB>
