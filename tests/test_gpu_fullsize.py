@@ -15,23 +15,28 @@ ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_linear": ospecs.bcc_linear,
 TOL = 2e-6
 
 
-def test_bench_step_with_autotuned_kernels():
+@pytest.mark.parametrize("layout", ["interleaved", "coset"])
+def test_bench_step_with_autotuned_kernels(layout):
     """The four launches of one bench step (BCC 2x128^3 smooth field, 2^24
-    uniform + 2^24 ray points), each with the variant the bench runs."""
-    from paper_2102_08518_b300.api import TUNE_CANDIDATES_SMALL, Volume, autotune
+    uniform + 2^24 ray points), each with the variant the bench runs: with the
+    cosets interleaved (the bench's layout; the quintic on ray points runs the
+    tensor-core kernel) and coset-major."""
+    from paper_2102_08518_b300.api import TUNE_CANDIDATES_SMALL, Volume, autotune, relayout
     ext = (128, 128, 128)
     coef_np = workloads.coef_smooth("bcc", ext, seed=0)
     lo, hi = workloads.inner_box("bcc_quintic", ext)
     sets = {"uniform": workloads.points_uniform(1 << 24, lo, hi, seed=1),
             "rays": workloads.points_rays(4096, 4096, lo, hi, seed=3)}
-    coef = torch.from_numpy(coef_np).cuda()
+    coef = relayout(torch.from_numpy(coef_np).cuda(), 2, ext, to=layout)
     c64 = coef_np.astype(np.float64).ravel()
     for name in ("bcc_linear", "bcc_quintic"):
         spec = ORACLE_SPEC[name]().with_extent(ext)
         for ps, pts in sets.items():
             p = torch.from_numpy(pts).cuda()
-            sp = autotune(name, "f32", ext, coef, [p], candidates=TUNE_CANDIDATES_SMALL, tag=f"bcc_step_{ps}")
-            out = Volume(sp, ext, coef).eval(p)
+            sp = autotune(name, "f32", ext, coef, [p], candidates=TUNE_CANDIDATES_SMALL, tag=f"bcc_step_{ps}",
+                          layout=layout)
+            out = Volume(sp, ext, coef, layout=layout).eval(p)
+            sp.status()
             torch.cuda.synchronize()
             got = out.cpu().numpy().astype(np.float64)
             assert np.all(np.isfinite(got))
