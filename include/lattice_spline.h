@@ -67,13 +67,13 @@ typedef enum { LS_F32 = 0, LS_BF16 = 1, LS_F16 = 2, LS_F64 = 3 } ls_dtype;
  *                           point share 32-byte sectors, so a stencil touches
  *                           fewer of them; identical to coset-major when C = 1)
  *   LS_LAYOUT_BRICKED:      element (b * V + w) * C + j, the grid cut into bricks
- *                           of 4 x 2 x 2 indices (4 x 2 in 2D; V = 16 or 8) in
- *                           x-fastest brick order b, w = (i_0 & 3) + 4 (i_1 & 1)
- *                           + 8 (i_2 & 1) inside the brick: with FP32 and two
- *                           cosets a brick is one 128-byte cache line, so a
- *                           stencil touches fewer lines.  Needs ext_0 % 4 == 0,
- *                           ext_1 % 2 == 0 (and ext_2 % 2 == 0 in 3D) and a spline
- *                           created with ls_variant.brick = 1.
+ *                           of 2 x 2 x 2 indices (2 x 2 in 2D; V = 8 or 4) in
+ *                           x-fastest brick order b, w = (i_0 & 1) + 2 (i_1 & 1)
+ *                           + 4 (i_2 & 1) inside the brick: with FP32 and two
+ *                           cosets a 32-byte sector holds a 2 x 2 patch of both
+ *                           cosets and a 128-byte line two bricks, so a compact
+ *                           stencil touches fewer sectors and lines.  Needs even
+ *                           extents and a spline created with ls_variant.brick = 1.
  */
 typedef enum { LS_LAYOUT_COSET_MAJOR = 0, LS_LAYOUT_INTERLEAVED = 1, LS_LAYOUT_BRICKED = 2 } ls_layout;
 

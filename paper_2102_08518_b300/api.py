@@ -145,7 +145,7 @@ class Volume:
     ``layout``: "coset" (one array after another: shape (n_cosets, ext[dim-1],
     ..., ext[0])), "interleaved" (the cosets' values of one grid index
     adjacent: shape (ext[dim-1], ..., ext[0], n_cosets)) or "bricked" (bricks
-    of 4 x 2 x 2 grid indices, cosets interleaved inside; needs a spline made
+    of 2 x 2 x 2 grid indices, cosets interleaved inside; needs a spline made
     with brick=1); see ``relayout``.
     ``coef`` (device tensor of the spline's storage dtype in that layout) is
     wrapped without a copy; otherwise a zero volume is allocated by the library.

@@ -498,8 +498,8 @@ static ls_status init_volume(ls_spline s, const int64_t *ext, int32_t layout, ls
     v->coset_elems = prod;
     v->total_elems = prod * (int64_t)s->table.cosets.size();
     if (layout == LS_LAYOUT_BRICKED &&
-        (v->ext[0] % 4 != 0 || (s->table.dim >= 2 && v->ext[1] % 2 != 0) || (s->table.dim == 3 && v->ext[2] % 2 != 0)))
-        return ls_fail(LS_ERR_INVALID_ARG, "bricked layout: ext[0] % 4, ext[1] % 2 and ext[2] % 2 must be 0");
+        (v->ext[0] % 2 != 0 || (s->table.dim >= 2 && v->ext[1] % 2 != 0) || (s->table.dim == 3 && v->ext[2] % 2 != 0)))
+        return ls_fail(LS_ERR_INVALID_ARG, "bricked layout: ext[0], ext[1] and ext[2] must be even");
     if (v->total_elems >= (int64_t)1 << 31)
         return ls_fail(LS_ERR_UNSUPPORTED, "volume exceeds 2^31 coefficients (32-bit addressing)");
     return LS_OK;
@@ -641,7 +641,7 @@ ls_status ls_relayout(const void *src, int32_t src_layout, void *dst, int32_t ds
     if (per * n_cosets >= ((int64_t)1 << 31)) return ls_fail(LS_ERR_UNSUPPORTED, "2^31 or more elements");
     for (int32_t l : {src_layout, dst_layout}) {
         if (l < LS_LAYOUT_COSET_MAJOR || l > LS_LAYOUT_BRICKED) return ls_fail(LS_ERR_INVALID_ARG, "unknown layout");
-        if (l == LS_LAYOUT_BRICKED && (ext[0] % 4 != 0 || ext[1] % 2 != 0 || (ext[2] != 1 && ext[2] % 2 != 0)))
+        if (l == LS_LAYOUT_BRICKED && (ext[0] % 2 != 0 || ext[1] % 2 != 0 || (ext[2] != 1 && ext[2] % 2 != 0)))
             return ls_fail(LS_ERR_INVALID_ARG, "bricked layout: extents are not whole bricks");
     }
     if (!src || !dst || src == dst) return ls_fail(LS_ERR_INVALID_ARG, "src, dst NULL or the same buffer");

@@ -279,13 +279,13 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
         for (size_t j = 0; j < sites.size(); ++j) o << "    int ad" << j << ";\n";
     // Address of (coset j, per-coset index q).  Linear layouts (coset-major,
     // interleaved): j * CS + CU * (q0 + ex0 (q1 + ex1 q2)).  Bricked layout
-    // (4 x 2 x 2 indices per brick, cosets interleaved inside, e.brick):
-    // j + sum_i [BA_i q_i + BB_i (q_i >> SH_i)] with SH = (2, 1, 1), which is
-    // BH_i (q_i >> SH_i) + BA_i (q_i & mask) per axis.
+    // (2 x 2 x 2 indices per brick, cosets interleaved inside, e.brick):
+    // j + sum_i [BA_i q_i + BB_i (q_i >> 1)], which is BH_i (q_i >> 1) +
+    // BA_i (q_i & 1) per axis.
     if (e.brick) {
-        o << "    const int BA0 = CU, BA1 = 4 * CU, BA2 = 8 * CU;\n";
-        o << "    const int BH0 = " << (D == 3 ? 16 : 8) << " * CU, BH1 = BH0 * (ex0 >> 2), BH2 = BH1 * (ex1 >> 1);\n";
-        o << "    const int BB0 = BH0 - 4 * BA0, BB1 = BH1 - 2 * BA1, BB2 = BH2 - 2 * BA2;\n";
+        o << "    const int BA0 = CU, BA1 = 2 * CU, BA2 = 4 * CU;\n";
+        o << "    const int BH0 = " << (D == 3 ? 8 : 4) << " * CU, BH1 = BH0 * (ex0 >> 1), BH2 = BH1 * (ex1 >> 1);\n";
+        o << "    const int BB0 = BH0 - 2 * BA0, BB1 = BH1 - 2 * BA1, BB2 = BH2 - 2 * BA2;\n";
         o << "    (void)BA2; (void)BB2;\n";
     }
     o << "    if (inside) {\n";
@@ -308,13 +308,13 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
         const char *bb[3] = {"BB0", "BB1", "BB2"};
         for (int r = 0; r < D; ++r) {
             if (fold) {
-                o << "      const int bsh" << r << " = (p" << r << " == 0) ? 2 : 1;\n";
+                o << "      const int bsh" << r << " = 1;\n";
                 o << "      const int bbt" << r << " = ";
                 for (int i = 0; i < D - 1; ++i) o << "(p" << r << " == " << i << ") ? " << bb[i] << " : ";
                 o << bb[D - 1] << ";\n";
                 o << "      const int bsg" << r << " = g" << r << " ? -1 : 1;\n";
             } else {
-                o << "      const int bsh" << r << " = " << (r == 0 ? 2 : 1) << ", bbt" << r << " = " << bb[r]
+                o << "      const int bsh" << r << " = 1, bbt" << r << " = " << bb[r]
                   << ", bsg" << r << " = 1;\n";
             }
         }
@@ -467,8 +467,7 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             if (e.brick) {
                 o << "        const int adr = cid";
                 for (int i = 0; i < D; ++i)
-                    o << " + BA" << i << " * (n" << i << " >> 1) + BB" << i << " * ((n" << i << " >> 1) >> "
-                      << (i == 0 ? 2 : 1) << ")";
+                    o << " + BA" << i << " * (n" << i << " >> 1) + BB" << i << " * ((n" << i << " >> 1) >> 1)";
                 o << ";\n";
             } else {
                 o << "        const int adr = cid * CS + CU * ((n0 >> 1)";
@@ -481,7 +480,7 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             if (e.brick) {
                 o << "        const int adr = 0";
                 for (int i = 0; i < D; ++i)
-                    o << " + BA" << i << " * n" << i << " + BB" << i << " * (n" << i << " >> " << (i == 0 ? 2 : 1) << ")";
+                    o << " + BA" << i << " * n" << i << " + BB" << i << " * (n" << i << " >> 1)";
                 o << ";\n";
             } else {
                 o << "        const int adr = CU * (n0";
@@ -2318,15 +2317,15 @@ void emit_adjoint_gather(Emitter &e, const Table &t, const ls_variant &var, cons
     o << "  for (long long site = (long long)blockIdx.x * blockDim.x + threadIdx.x; site < total;"
          " site += (long long)gridDim.x * blockDim.x) {\n";
     if (e.brick) {
-        // bricked: site = C * (brick * BV + within) + cj, within = (i2&1) 8 + (i1&1) 4 + (i0&3)
-        const int bv = D == 3 ? 16 : 8;
+        // bricked: site = C * (brick * BV + within) + cj, within = (i2&1) 4 + (i1&1) 2 + (i0&1)
+        const int bv = D == 3 ? 8 : 4;
         o << "    const int cj = (int)(site % " << t.cosets.size() << ");\n";
         o << "    const int w = (int)(site / " << t.cosets.size() << ");\n";
         o << "    const int wi = w & " << bv - 1 << ";\n";
-        o << "    int bk = w >> " << (D == 3 ? 4 : 3) << ";\n";
-        o << "    const int i0 = (bk % (a.e0 >> 2)) * 4 + (wi & 3); bk /= (a.e0 >> 2);\n";
-        if (D > 1) o << "    const int i1 = (bk % (a.e1 >> 1)) * 2 + ((wi >> 2) & 1); bk /= (a.e1 >> 1);\n";
-        if (D > 2) o << "    const int i2 = bk * 2 + (wi >> 3);\n";
+        o << "    int bk = w >> " << (D == 3 ? 3 : 2) << ";\n";
+        o << "    const int i0 = (bk % (a.e0 >> 1)) * 2 + (wi & 1); bk /= (a.e0 >> 1);\n";
+        if (D > 1) o << "    const int i1 = (bk % (a.e1 >> 1)) * 2 + ((wi >> 1) & 1); bk /= (a.e1 >> 1);\n";
+        if (D > 2) o << "    const int i2 = bk * 2 + (wi >> 2);\n";
     } else {
         o << "    const int cj = (int)((site / a.cstride) % " << t.cosets.size() << ");\n";
         o << "    int rem = (int)((site / a.cunit) % P);\n";

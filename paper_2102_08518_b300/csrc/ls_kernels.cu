@@ -23,32 +23,32 @@ __device__ __forceinline__ double load_any(const void *p, int dt, long long i)
 }
 
 // Element index of (coset j, grid index q) in a coefficient layout (ls_layout):
-// 0 coset-major, 1 interleaved, 2 bricked (4 x 2 x 2 grid indices per brick,
-// 4 x 2 in 2D (e2 == 1), cosets interleaved inside, x fastest).
+// 0 coset-major, 1 interleaved, 2 bricked (2 x 2 x 2 grid indices per brick,
+// 2 x 2 in 2D (e2 == 1), cosets interleaved inside, x fastest).
 __device__ __forceinline__ long long lay_index(const LayoutGeom &g, int j, int q0, int q1, int q2)
 {
     const long long lin = q0 + (long long)g.e0 * (q1 + (long long)g.e1 * q2);
     if (g.layout == 0) return (long long)j * g.per + lin;
     if (g.layout == 1) return lin * g.ncos + j;
-    const int bv = g.e2 == 1 ? 8 : 16;
-    const long long bk = (q0 >> 2) + (long long)(g.e0 >> 2) * ((q1 >> 1) + (long long)(g.e1 >> 1) * (q2 >> 1));
-    const int wi = (q0 & 3) + 4 * (q1 & 1) + 8 * (q2 & 1);
+    const int bv = g.e2 == 1 ? 4 : 8;
+    const long long bk = (q0 >> 1) + (long long)(g.e0 >> 1) * ((q1 >> 1) + (long long)(g.e1 >> 1) * (q2 >> 1));
+    const int wi = (q0 & 1) + 2 * (q1 & 1) + 4 * (q2 & 1);
     return (bk * bv + wi) * g.ncos + j;
 }
 
 __device__ __forceinline__ void lay_decode(const LayoutGeom &g, long long i, int &j, int &q0, int &q1, int &q2)
 {
     if (g.layout == 2) {
-        const int bv = g.e2 == 1 ? 8 : 16;
+        const int bv = g.e2 == 1 ? 4 : 8;
         j = (int)(i % g.ncos);
         const long long w = i / g.ncos;
         const int wi = (int)(w % bv);
         long long bk = w / bv;
-        q0 = (int)(bk % (g.e0 >> 2)) * 4 + (wi & 3);
-        bk /= (g.e0 >> 2);
-        q1 = (int)(bk % (g.e1 >> 1)) * 2 + ((wi >> 2) & 1);
+        q0 = (int)(bk % (g.e0 >> 1)) * 2 + (wi & 1);
+        bk /= (g.e0 >> 1);
+        q1 = (int)(bk % (g.e1 >> 1)) * 2 + ((wi >> 1) & 1);
         bk /= (g.e1 >> 1);
-        q2 = (int)bk * 2 + (wi >> 3);
+        q2 = (int)bk * 2 + (wi >> 2);
         return;
     }
     long long r;

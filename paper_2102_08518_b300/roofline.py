@@ -15,7 +15,7 @@ def stencil_indices(table, ext, pts: np.ndarray, layout: str = "coset") -> np.nd
     """Linear coefficient indices (n_points, n_sites) of every point's stencil
     in the volume layout ("coset": coset j's array after array j - 1;
     "interleaved": the cosets' values of one grid index adjacent; "bricked":
-    4 x 2 x 2 bricks of grid indices with the cosets adjacent inside); -1
+    2 x 2 x 2 bricks of grid indices with the cosets adjacent inside); -1
     where a site lies outside the arrays."""
     spl = table.spline
     lat = spl.lattice
@@ -77,9 +77,9 @@ def stencil_indices(table, ext, pts: np.ndarray, layout: str = "coset") -> np.nd
             C = len(lat.cosets)
             if layout == "bricked":
                 i2 = idx[:, 2] if D == 3 else np.zeros_like(idx[:, 0])
-                bk = idx[:, 0] // 4 + (e[0] // 4) * (idx[:, 1] // 2 + (e[1] // 2) * (i2 // 2))
-                w = idx[:, 0] % 4 + 4 * (idx[:, 1] % 2) + 8 * (i2 % 2)
-                lin = (bk * (16 if D == 3 else 8) + w) * C + cid
+                bk = idx[:, 0] // 2 + (e[0] // 2) * (idx[:, 1] // 2 + (e[1] // 2) * (i2 // 2))
+                w = idx[:, 0] % 2 + 2 * (idx[:, 1] % 2) + 4 * (i2 % 2)
+                lin = (bk * (8 if D == 3 else 4) + w) * C + cid
             elif layout == "interleaved":
                 lin = q * C + cid
             else:

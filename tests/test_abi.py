@@ -108,7 +108,7 @@ def test_new_entry_points_validate_their_arguments_without_a_device():
     assert L.ls_relayout(buf_a, CM, buf_b, 7, 2, e3, 4, None) == 1             # layout
     assert L.ls_relayout(buf_a, CM, buf_a, IL, 2, e3, 4, None) == 1            # in place
     assert L.ls_relayout(None, CM, buf_b, IL, 2, e3, 4, None) == 1
-    odd = (ctypes.c_int64 * 3)(6, 6, 4)                                         # 6 is not a multiple of 4
+    odd = (ctypes.c_int64 * 3)(7, 6, 4)                                         # 7 is odd: no whole bricks
     assert L.ls_relayout(buf_a, CM, buf_b, BK, 2, odd, 4, None) == 1
     assert b"brick" in L.ls_last_error()
     big = (ctypes.c_int64 * 3)(1 << 11, 1 << 11, 1 << 10)                     # 2^32 elements
@@ -196,7 +196,8 @@ def test_tensor_variant_source():
     src = open(os.path.join(cache, files[-1])).read()
     kern = src[src.index("ls_eval__"):]
     assert "tcgen05.mma.cta_group::1.kind::tf32" in kern and "tcgen05.alloc" in kern and "tcgen05.dealloc" in kern
-    assert kern.count("tcgen05.mma.cta_group::1.kind::tf32") == 12        # 3 products x K = 32 in steps of 8
+    # the value and the value + gradient kernels: 3 products x K = 32 in steps of 8 each
+    assert kern.count("tcgen05.mma.cta_group::1.kind::tf32") == 24
     # the table's hi / lo entries: every hi is a TF32 value (low 13 mantissa bits zero)
     import struct
     tab = src[src.index("ls_tcB_"):]

@@ -2,7 +2,7 @@
 
 An interleaved volume holds the values of all cosets at one grid index next to
 each other (element q * C + j instead of j * P + q); a bricked one cuts the
-grid into 4 x 2 x 2 bricks (4 x 2 in 2D), x fastest inside, cosets adjacent.
+grid into 2 x 2 x 2 bricks (2 x 2 in 2D), x fastest inside, cosets adjacent.
 The arrays here are made from the coset-major ones by numpy reshapes and
 transposes, independently of the library's ls_relayout, which is checked bit
 for bit on its own.  Every kernel (value, value + gradient, atomic, warp-
@@ -23,7 +23,7 @@ TOL = 2e-6
 ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
                "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6,
                "zp": ospecs.zp2d}
-# whole bricks (ext0 % 4, ext1 % 2, ext2 % 2), so both layouts take them
+# whole bricks (even extents), so both layouts take them
 SMALL_EXT = {"tricubic": (12, 10, 8), "trilinear": (8, 10, 6), "triquadratic": (12, 8, 10),
              "bcc_linear": (8, 6, 8), "bcc_quintic": (8, 6, 6), "fcc6": (8, 8, 6), "zp": (12, 10)}
 NAMES = ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "fcc6", "zp"]
@@ -49,20 +49,20 @@ def brick_np(coef, C, ext):
     x, y, z, then the coset."""
     if len(ext) == 3:
         e0, e1, e2 = ext
-        a = coef.reshape(C, e2 // 2, 2, e1 // 2, 2, e0 // 4, 4)
+        a = coef.reshape(C, e2 // 2, 2, e1 // 2, 2, e0 // 2, 2)
         return np.ascontiguousarray(a.transpose(1, 3, 5, 2, 4, 6, 0)).ravel()
     e0, e1 = ext
-    a = coef.reshape(C, e1 // 2, 2, e0 // 4, 4)
+    a = coef.reshape(C, e1 // 2, 2, e0 // 2, 2)
     return np.ascontiguousarray(a.transpose(1, 3, 2, 4, 0)).ravel()
 
 
 def unbrick_np(arr, C, ext):
     if len(ext) == 3:
         e0, e1, e2 = ext
-        a = arr.reshape(e2 // 2, e1 // 2, e0 // 4, 2, 2, 4, C)
+        a = arr.reshape(e2 // 2, e1 // 2, e0 // 2, 2, 2, 2, C)
         return np.ascontiguousarray(a.transpose(6, 0, 3, 1, 4, 2, 5)).ravel()
     e0, e1 = ext
-    a = arr.reshape(e1 // 2, e0 // 4, 2, 4, C)
+    a = arr.reshape(e1 // 2, e0 // 2, 2, 2, C)
     return np.ascontiguousarray(a.transpose(4, 0, 2, 1, 3)).ravel()
 
 
@@ -84,20 +84,20 @@ def ivolume(name, ext, coef_np, dtype="f32", layout="interleaved", **kw):
 
 def test_numpy_brick_maps_are_inverse_and_match_the_definition():
     """The test's own bricked map against the element formula, element by element."""
-    for C, ext in ((2, (8, 6, 4)), (1, (4, 2, 2)), (4, (12, 4, 6)), (2, (8, 6))):
+    for C, ext in ((2, (8, 6, 4)), (1, (4, 2, 2)), (4, (10, 4, 6)), (2, (6, 6)), (1, (2, 2, 2))):
         P = int(np.prod(ext))
         coef = np.arange(C * P, dtype=np.int64)
         b = brick_np(coef, C, ext)
         assert np.array_equal(unbrick_np(b, C, ext), coef)
         e = tuple(ext) + (1,) * (3 - len(ext))
-        V = 16 if len(ext) == 3 else 8
+        V = 8 if len(ext) == 3 else 4
         for j in range(C):
             for i2 in range(e[2]):
                 for i1 in range(e[1]):
                     for i0 in range(e[0]):
                         q = i0 + e[0] * (i1 + e[1] * i2)
-                        bk = i0 // 4 + (e[0] // 4) * (i1 // 2 + (e[1] // 2) * (i2 // 2))
-                        w = i0 % 4 + 4 * (i1 % 2) + 8 * (i2 % 2)
+                        bk = i0 // 2 + (e[0] // 2) * (i1 // 2 + (e[1] // 2) * (i2 // 2))
+                        w = i0 % 2 + 2 * (i1 % 2) + 4 * (i2 % 2)
                         assert b[(bk * V + w) * C + j] == coef[j * P + q]
 
 
@@ -116,7 +116,7 @@ def test_relayout_matches_numpy_maps(C, ext, dtype):
     il = relayout(src, C, ext, to="interleaved")
     assert np.array_equal(il.cpu().numpy(), interleave_np(ref, C))
     assert torch.equal(relayout(il, C, ext, to="coset", src="interleaved"), src)
-    if ext[0] % 4 == 0 and ext[1] % 2 == 0 and (len(ext) == 2 or ext[2] % 2 == 0):
+    if ext[0] % 2 == 0 and ext[1] % 2 == 0 and (len(ext) == 2 or ext[2] % 2 == 0):
         bk = relayout(src, C, ext, to="bricked")
         assert np.array_equal(bk.cpu().numpy(), brick_np(ref, C, ext))
         assert torch.equal(relayout(bk, C, ext, to="interleaved", src="bricked"), il)
@@ -230,7 +230,7 @@ def test_batched_plan_mixes_layouts():
         p = torch.from_numpy(workloads.points_uniform(it.n_points, lo - 1.0, hi + 1.0, seed=it.seed + 1)).cuda()
         if k % 3 == 1:
             v = Volume(sps[it.spline], it.ext, torch.from_numpy(interleave_np(c, C)).cuda(), layout="interleaved")
-        elif k % 3 == 2 and it.ext[0] % 4 == 0 and it.ext[1] % 2 == 0 and (len(it.ext) < 3 or it.ext[2] % 2 == 0):
+        elif k % 3 == 2 and it.ext[0] % 2 == 0 and it.ext[1] % 2 == 0 and (len(it.ext) < 3 or it.ext[2] % 2 == 0):
             v = Volume(sps[it.spline + "_bk"], it.ext, torch.from_numpy(brick_np(c, C, it.ext)).cuda(),
                        layout="bricked")
         else:
@@ -297,7 +297,7 @@ def test_bricked_layout_rejections():
     from paper_2102_08518_b300 import _abi
     from paper_2102_08518_b300.api import Spline, Volume
     with pytest.raises(_abi.LsError):
-        Volume(Spline("bcc_linear", "f32", brick=1), (6, 6, 6), layout="bricked")
+        Volume(Spline("bcc_linear", "f32", brick=1), (7, 6, 6), layout="bricked")
     with pytest.raises(_abi.LsError):
         Volume(Spline("bcc_linear", "f32"), (8, 6, 6), layout="bricked")
     with pytest.raises(_abi.LsError):

@@ -20,7 +20,7 @@ def _maps(C, ext):
     il = np.empty(C * P, np.int64)
     il[np.ascontiguousarray(cm.reshape(C, -1).T).ravel()] = np.arange(C * P)
     e0, e1, e2 = ext
-    bk_order = np.ascontiguousarray(cm.reshape(C, e2 // 2, 2, e1 // 2, 2, e0 // 4, 4)
+    bk_order = np.ascontiguousarray(cm.reshape(C, e2 // 2, 2, e1 // 2, 2, e0 // 2, 2)
                                     .transpose(1, 3, 5, 2, 4, 6, 0)).ravel()
     bk = np.empty(C * P, np.int64)
     bk[bk_order] = np.arange(C * P)
