@@ -2,6 +2,7 @@
 // and loading through the CUDA runtime's library API.
 #include <dlfcn.h>
 #include <sys/stat.h>
+#include <sys/time.h>
 #include <unistd.h>
 
 #include <cstdio>
@@ -113,7 +114,12 @@ ls_status get_cubin(const std::string &source, const std::string &tag, std::vect
     std::snprintf(hex, sizeof hex, "%016llx", (unsigned long long)h);
     const std::string dir = cache_dir();
     const std::string path = dir + "/" + tag + "_" + hex + ".cubin";
-    if (read_file(path, cubin)) return LS_OK;
+    if (read_file(path, cubin)) {
+        // mark the entry as used (its modification time), so a cache that has
+        // collected kernels of earlier generator versions can be pruned by age
+        utimes(path.c_str(), nullptr);
+        return LS_OK;
+    }
     ls_status st = nvrtc_compile(source, tag, cubin, err);
     if (st != LS_OK) return st;
     mkdir(dir.c_str(), 0755);
