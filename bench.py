@@ -43,7 +43,8 @@ N_RAYS, RAY_STEPS = 4096, 4096
 CASES = [("bcc_linear", "uniform"), ("bcc_linear", "rays"), ("bcc_quintic", "uniform"), ("bcc_quintic", "rays")]
 WORKLOAD = ("bcc 2x128^3 smooth field; linear + quintic box splines; 2^24 uniform + 2^24 ray points "
             "(4096 rays x 4096 steps)")
-LAYOUT = "interleaved"          # default coefficient layout of the step's volumes (--layout)
+LAYOUT = "auto"                 # coefficient layout of the step's volumes (--layout); "auto": per case the
+                                # faster of interleaved and bricked, both held in memory
 
 
 def dist_env():
@@ -228,15 +229,35 @@ def run_gpu(args):
     coef_np, pts_np = make_inputs(seed_offset=rank)
     dev = torch.device("cuda", local)
     coef_cm = torch.from_numpy(coef_np).to(dev)              # one array per coset
-    coef = relayout(coef_cm, 2, EXT, to=LAYOUT)             # the step's coefficient layout
+    # the step's coefficient layouts (relayout once, untimed): with "auto" the
+    # volume is held interleaved and bricked, and each case reads the faster one
+    layouts = ("interleaved", "bricked") if LAYOUT == "auto" else (LAYOUT,)
+    coefs = {lay: coef_cm if lay == "coset" else relayout(coef_cm, 2, EXT, to=lay) for lay in layouts}
     pts = {k: torch.from_numpy(v).to(dev) for k, v in pts_np.items()}
-    # evaluation kernel variant per (spline, point set), autotuned on the step's own points (untimed)
-    tuned = {(sp, ps): autotune(sp, "f32", EXT, coef, [pts[ps]], candidates=TUNE_CANDIDATES_SMALL,
-                                tag=f"bcc_step_{ps}", layout=LAYOUT) for sp, ps in CASES}
-    splines = {sp: tuned[(sp, "uniform")] for sp in ("bcc_linear", "bcc_quintic")}
-    vols = {n: Volume(s, EXT, coef, layout=LAYOUT) for n, s in splines.items()}
-    case_vols = {(sp, ps): Volume(tuned[(sp, ps)], EXT, coef, layout=LAYOUT) for sp, ps in CASES}
     outs = {k: torch.empty(v.shape[0], device=dev) for k, v in pts.items()}
+    # evaluation kernel variant (and layout) per (spline, point set), autotuned on
+    # the step's own points (untimed)
+    tuned, case_layout = {}, {}
+    for sp, ps in CASES:
+        best = None
+        for lay in layouts:
+            s_ = autotune(sp, "f32", EXT, coefs[lay], [pts[ps]], candidates=TUNE_CANDIDATES_SMALL,
+                          tag=f"bcc_step_{ps}", layout=lay)
+            ms_ = 0.0
+            if len(layouts) > 1:
+                v_ = Volume(s_, EXT, coefs[lay], layout=lay)
+                ms_ = time_ms(torch, lambda: v_.eval(pts[ps], outs[ps]))
+                del v_
+            if best is None or ms_ < best[0]:
+                best = (ms_, s_, lay)
+        tuned[(sp, ps)], case_layout[(sp, ps)] = best[1], best[2]
+    base_layout = layouts[0]                                # the extras' volumes
+    splines = {sp: tuned[(sp, "uniform")] if case_layout[(sp, "uniform")] == base_layout else
+               autotune(sp, "f32", EXT, coefs[base_layout], [pts["uniform"]], candidates=TUNE_CANDIDATES_SMALL,
+                        tag="bcc_step_uniform", layout=base_layout) for sp in ("bcc_linear", "bcc_quintic")}
+    vols = {n: Volume(s, EXT, coefs[base_layout], layout=base_layout) for n, s in splines.items()}
+    case_vols = {(sp, ps): Volume(tuned[(sp, ps)], EXT, coefs[case_layout[(sp, ps)]], layout=case_layout[(sp, ps)])
+                 for sp, ps in CASES}
     stream = torch.cuda.current_stream()
 
     def step(case_events=None):
@@ -278,41 +299,44 @@ def run_gpu(args):
 
     # --- gather roofline: random 32-byte-sector rate of the L2-resident volume ------
     probe_out = torch.empty(1 << 22, device=dev)
-    flat = coef.view(-1)
+    flat = coefs[base_layout].view(-1)
     probe_ms = time_ms(torch, lambda: probe_gather(flat, 32, 1 << 22, 148 * 16, probe_out))
     probe_gloads = (1 << 22) * 32 / (probe_ms * 1e-3) / 1e9
     peak_l2 = probe_gloads * 32.0                      # GB/s of 32-byte sectors
     sample = {ps: v[np.random.default_rng(7).choice(len(v), 1 << 14, replace=False)] for ps, v in pts_np.items()}
-    sectors = {sp: distinct_sectors_per_point(table(sp), EXT, sample["uniform"], layout=LAYOUT) for sp in splines}
+    sectors = {(sp, ps): distinct_sectors_per_point(table(sp), EXT, sample["uniform"], layout=case_layout[(sp, ps)])
+               for sp, ps in CASES}
     per_case = {}
     for (sp, ps), ms in zip(CASES, case_ms):
         n = N_UNIFORM if ps == "uniform" else N_RAYS * RAY_STEPS
         info = tuned[(sp, ps)].info()
-        l2_gbs = sectors[sp] * 32.0 * n / (ms * 1e-3) / 1e9
+        l2_gbs = sectors[(sp, ps)] * 32.0 * n / (ms * 1e-3) / 1e9
         fma_tf = 2.0 * info["fma_value"] * n / (ms * 1e-3) / 1e12
         per_case[f"{sp}/{ps}"] = {"gpoints_s": round(n / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 4),
                                   "l2_gather_gbs": round(l2_gbs, 1), "fp32_fma_tflops": round(fma_tf, 2)}
-    info = splines["bcc_quintic"].info()
+    dom_sp, dom_lay = tuned[("bcc_quintic", "uniform")], case_layout[("bcc_quintic", "uniform")]
+    dom_sec = sectors[("bcc_quintic", "uniform")]
+    info = dom_sp.info()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2032.0
     peak_fma = sms * 128 * 2 * max_mhz * 1e6 / 1e12
     dom = per_case["bcc_quintic/uniform"]
-    kname = "ls_eval__" + splines["bcc_quintic"].kernel_name
-    counters, cfile = profile_counters(splines["bcc_quintic"].source(), kname)
+    kname = "ls_eval__" + dom_sp.kernel_name
+    counters, cfile = profile_counters(dom_sp.source(), kname)
     traffic = None
     if counters:
         traffic = counters.get("dram_bytes_per_launch")
     roofline = {"bound": "l2", "kernel": kname, "achieved": dom["l2_gather_gbs"], "peak": round(peak_l2, 1),
                 "unit": "GB/s", "frac": round(dom["l2_gather_gbs"] / peak_l2, 4), "traffic": traffic,
-                "algorithmic_bytes_per_point": round(sectors["bcc_quintic"] * 32.0, 1),
-                "algorithmic_unit": (f"distinct 32-byte sectors of one point's stencil in the {LAYOUT} layout "
-                                     f"({sectors['bcc_quintic']:.2f} per point, 2^14-point sample)"),
+                "algorithmic_bytes_per_point": round(dom_sec * 32.0, 1),
+                "algorithmic_unit": (f"distinct 32-byte sectors of one point's stencil in the {dom_lay} layout "
+                                     f"({dom_sec:.2f} per point, 2^14-point sample)"),
                 "coef_bytes_per_point": 4 * info["n_sites"],
                 "peak_source": ("measured in this run: random 4-byte loads from the L2-resident 16 MiB volume, "
                                 f"{probe_gloads:.1f} G loads/s x 32-byte sectors"),
                 "counters_from": cfile,
-                "kernel_hash": kernel_hash(splines["bcc_quintic"].source(), kname),
+                "kernel_hash": kernel_hash(dom_sp.source(), kname),
                 "l2_sector_bytes_per_launch": counters.get("l2_sector_bytes_per_launch") if counters else None}
     # the same kernel read against HBM: its coefficient bytes (n_sites x 4 B per
     # point) plus the point stream, at the measured copy bandwidth
@@ -390,14 +414,16 @@ def run_gpu(args):
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
               "data": "synthetic",
               "config": {"workload": WORKLOAD, "points_per_step": pts_per_step, "coef_bytes": coef_np.nbytes,
-                         "coef_layout": LAYOUT,
+                         "coef_copies_resident": len(layouts),
+                         "coef_layout": {f"{sp}/{ps}": case_layout[(sp, ps)] for sp, ps in CASES},
                          "l2": "points 201 MB per set > 126 MB L2 (inputs larger than L2); coefficient volume "
                                "16 MiB L2-resident by design", "parallelism": f"replicas x{world}"},
               "per_case": per_case, "roofline": roofline, "roofline_alu": roofline_alu, "roofline_hbm": roofline_hbm,
               "roofline_tensor": roofline_tensor,
               "e2e": e2e,
               "autotuned": {f"{sp}/{ps}": {"variant": tuned[(sp, ps)].variant,
-                                            "key": tune_key(sp, "f32", EXT, [pts[ps]], f"bcc_step_{ps}", LAYOUT)}
+                                            "key": tune_key(sp, "f32", EXT, [pts[ps]], f"bcc_step_{ps}",
+                                                            case_layout[(sp, ps)])}
                             for sp, ps in CASES},
               "clocks": clocks, "gpu_launches": len(CASES) * args.steps}
     del host_pts, host_out
@@ -815,7 +841,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--layout", default=LAYOUT, choices=["coset", "interleaved", "bricked"],
+    ap.add_argument("--layout", default=LAYOUT, choices=["auto", "coset", "interleaved", "bricked"],
                     help="coefficient layout of the step's volumes")
     ap.add_argument("--only", default=None, choices=PROFILE_CASES,
                     help="run one small case for a profiler instead of the benchmark")
