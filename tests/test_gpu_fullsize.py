@@ -15,12 +15,13 @@ ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_linear": ospecs.bcc_linear,
 TOL = 2e-6
 
 
-@pytest.mark.parametrize("layout", ["interleaved", "coset"])
+@pytest.mark.parametrize("layout", ["interleaved", "bricked", "coset"])
 def test_bench_step_with_autotuned_kernels(layout):
     """The four launches of one bench step (BCC 2x128^3 smooth field, 2^24
-    uniform + 2^24 ray points), each with the variant the bench runs: with the
-    cosets interleaved (the bench's layout; the quintic on ray points runs the
-    tensor-core kernel) and coset-major."""
+    uniform + 2^24 ray points), each with the variant the bench runs in that
+    layout: interleaved cosets (the bench's choice for the ray points, where
+    the quintic runs the tensor-core kernel), 2x2x2 bricks (its choice for the
+    uniform points) and coset-major."""
     from paper_2102_08518_b300.api import TUNE_CANDIDATES_SMALL, Volume, autotune, relayout
     ext = (128, 128, 128)
     coef_np = workloads.coef_smooth("bcc", ext, seed=0)
