@@ -193,6 +193,13 @@ typedef struct {
                                           as the 512 tensor-memory columns hold (at most 8), or T if
                                           T = 2..8 is smaller; forces block = 128 S; non-separable
                                           tables.  Bounded mbarrier waits (ls_spline_status) */
+    int32_t tensor_kind;               /* with tensor and FP32 coefficients: 0 = three TF32 products
+                                          of the hi / lo split; 1 = three FP16 products: each point's
+                                          coefficients scaled by a power of two (largest magnitude in
+                                          [2^14, 2^15)), split into FP16 hi (11 significant bits) + lo
+                                          (the rounded remainder), the scale undone on the results
+                                          (half the tensor-memory columns per tile, so more tiles in
+                                          flight).  Other values: LS_ERR_INVALID_ARG at create */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */

@@ -64,14 +64,16 @@ def _ptr(t: Optional[torch.Tensor]):
 
 def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_blocks: int = 0, group: int = 0,
                 depth: int = 0, pts_per_thread: int = 1, blocks_per_sm: int = 0, expansion: str = "sparse",
-                brick: int = 0, pipeline: int = 0, producers: int = 0, stage: int = 0, tensor: int = 0) -> str:
+                brick: int = 0, pipeline: int = 0, producers: int = 0, stage: int = 0, tensor: int = 0,
+                tensor_kind: int = 0) -> str:
     """The name tag of a generated kernel variant (blocks_per_sm only sizes the
     grid, so it shares the compiled kernel)."""
     return f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + ("_br" if branchy else "") + \
         (f"_m{min_blocks}" if min_blocks else "") + (f"_g{group}d{depth}" if group and depth else "") + \
         (f"_t{pts_per_thread}" if pts_per_thread > 1 else "") + ("_ec" if expansion == "centroid" else "") + \
         ("_bk" if brick else "") + ("_pp" if pipeline else "") + (f"_ws{producers}" if producers else "") + \
-        (f"_st{stage}" if stage else "") + (("_tc" + (str(tensor) if tensor > 1 else "")) if tensor else "")
+        (f"_st{stage}" if stage else "") + (("_tc" + (str(tensor) if tensor > 1 else "")) if tensor else "") + \
+        ("h" if tensor and tensor_kind else "")
 
 
 class Spline:
@@ -80,7 +82,8 @@ class Spline:
     def __init__(self, name: str, dtype: str = "f32", block: int = 256, branchy: int = 0,
                  min_blocks: int = 0, group: int = 0, depth: int = 0, pts_per_thread: int = 1,
                  blocks_per_sm: int = 0, expansion: str = "sparse", brick: int = 0, pipeline: int = 0,
-                 producers: int = 0, stage: int = 0, tensor: int = 0, kernel_name: Optional[str] = None):
+                 producers: int = 0, stage: int = 0, tensor: int = 0, tensor_kind: int = 0,
+                 kernel_name: Optional[str] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("lattice spline kernels need a CUDA device")
         self.name = name
@@ -91,7 +94,7 @@ class Spline:
         self.scale = self.table.spline.lattice.scale
         kname = kernel_name or globals()["kernel_name"](name, dtype, block, branchy, min_blocks, group, depth,
                                                          pts_per_thread, blocks_per_sm, expansion, brick, pipeline,
-                                                         producers, stage, tensor)
+                                                         producers, stage, tensor, tensor_kind)
         self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
                         "depth": depth, "pts_per_thread": pts_per_thread, "blocks_per_sm": blocks_per_sm,
                         "expansion": expansion}
@@ -104,12 +107,14 @@ class Spline:
         if stage:
             self.variant["stage"] = stage
         if tensor:
-            self.variant["tensor"] = 1
+            self.variant["tensor"] = tensor
+        if tensor_kind:
+            self.variant["tensor_kind"] = tensor_kind
         self.kernel_name = kname
         self._desc = _abi.DescHolder(self.table, kname, expansion)
         var = _abi.variant(block=block, pts_per_thread=pts_per_thread, branchy=branchy, min_blocks=min_blocks,
                            group=group, depth=depth, blocks_per_sm=blocks_per_sm, brick=brick, pipeline=pipeline,
-                           producers=producers, stage=stage, tensor=tensor)
+                           producers=producers, stage=stage, tensor=tensor, tensor_kind=tensor_kind)
         h = ctypes.c_void_p()
         torch.cuda.init()
         _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),
@@ -481,7 +486,9 @@ TUNE_CANDIDATES_SMALL = tuple([dict(block=256, blocks_per_sm=b, expansion=x) for
                               [dict(block=512, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(block=384, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(block=128, blocks_per_sm=b) for b in (2, 4)] +
-                              [dict(tensor=1, expansion=x) for x in ("sparse", "centroid")])
+                              [dict(tensor=1, expansion=x) for x in ("sparse", "centroid")] +
+                              [dict(tensor=1, tensor_kind=1, expansion=x) for x in ("sparse", "centroid")] +
+                              [dict(tensor=4, tensor_kind=1)])
 
 
 def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_sets: Sequence[torch.Tensor],
@@ -516,6 +523,8 @@ def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_
     for cand in candidates:
         if cand.get("tensor") and separable:
             continue                      # tensor-product tables have no coefficient transform to offload
+        if cand.get("tensor_kind") and dtype != "f32":
+            continue                      # the FP16 form splits FP32 data; BF16 / FP16 data are exact in TF32
         sp = Spline(name, dtype, **cand, **({"brick": 1} if layout == "bricked" else {}))
         vol = Volume(sp, ext, coef, layout=layout)
         outs = [torch.empty(p.shape[0], device=p.device) for p in pts_sets]
@@ -555,14 +564,20 @@ def _tune_key(name, dtype, ext, pts_sets, tag, layout="coset"):
 
 
 def autotune_record(name: str, dtype: str, ext, pts_sets, tag: str = "", layout: str = "coset"):
-    """The cached autotuning entry for this workload, if any."""
+    """The autotuning entry for this workload (the local cache first, then the
+    results shipped with the package), if any: its variant and time in ms."""
     import json
     key = _tune_key(name, dtype, ext, pts_sets, tag, layout)
-    try:
-        with open(os.path.join(_CACHE_DIR, "autotune.json")) as f:
-            return json.load(f).get(key)
-    except (OSError, ValueError):
-        return None
+    for path in (os.path.join(_CACHE_DIR, "autotune.json"),
+                 os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_b300.json")):
+        try:
+            with open(path) as f:
+                rec = json.load(f).get(key)
+        except (OSError, ValueError):
+            rec = None
+        if rec is not None:
+            return rec
+    return None
 
 
 def eval_host_multi(volumes: Sequence["Volume"], pts_host: torch.Tensor, outs_host: Sequence[torch.Tensor],

@@ -1423,12 +1423,13 @@ struct TensorPlan {
 
 // split: the coefficients need a TF32 hi + lo split (FP32 storage); BF16 and
 // FP16 values are exact in TF32, so their A_lo rows and third product vanish.
-TensorPlan tensor_plan(const Table &t, const Stencil &st, bool split = true)
+// h16: the FP16 form (kind::f16, K steps of 16, two 16-bit values per column)
+TensorPlan tensor_plan(const Table &t, const Stencil &st, bool split = true, bool h16 = false)
 {
     TensorPlan p;
     const size_t K = t.ref.size();
     p.nu = (int)st.sites.size();
-    p.kp = (p.nu + 7) / 8 * 8;
+    p.kp = h16 ? (p.nu + 15) / 16 * 16 : (p.nu + 7) / 8 * 8;
     p.terms.resize(K);
     p.sup.resize(K);
     p.col.resize(K);
@@ -1437,8 +1438,41 @@ TensorPlan tensor_plan(const Table &t, const Stencil &st, bool split = true)
         for (const auto &m : p.sup[k]) p.col[k][m] = p.ncol++;
     }
     p.n = std::max(16, (p.ncol + 15) / 16 * 16);
-    p.cols = ((split ? 2 : 1) * p.kp + p.n + 15) / 16 * 16;    // one slot's columns: A hi, [A lo,] D
+    // one slot's columns: A hi, [A lo,] D (FP16: hi and lo take kp / 2 columns each)
+    p.cols = ((h16 ? p.kp : (split ? 2 : 1) * p.kp) + p.n + 15) / 16 * 16;
     return p;
+}
+
+// round to the nearest FP16 value (ties to even; subnormals kept), as its bits
+unsigned short fp16_bits(double v)
+{
+    if (v == 0.0) return std::signbit(v) ? 0x8000 : 0;
+    const unsigned short sgn = v < 0 ? 0x8000 : 0;
+    double a = std::fabs(v);
+    if (a >= 65520.0) return sgn | 0x7c00;          // beyond the largest finite value: infinity
+    int ex;
+    std::frexp(a, &ex);                             // a = m 2^ex, 0.5 <= m < 1
+    int e = ex - 1;                                 // a = 1.f 2^e
+    if (e < -14) e = -14;                           // subnormal range: fixed step 2^-24
+    const double q = std::nearbyint(std::ldexp(a, 10 - e));   // 11 significant bits (fewer below 2^-14)
+    double r = std::ldexp(q, e - 10);
+    // re-encode (the rounding may have carried into the next binade)
+    int ex2;
+    std::frexp(r, &ex2);
+    int e2 = ex2 - 1;
+    if (r >= 65520.0) return sgn | 0x7c00;
+    if (e2 < -14) {                                 // subnormal: r = mant 2^-24
+        return sgn | (unsigned short)std::lrint(std::ldexp(r, 24));
+    }
+    const unsigned short mant = (unsigned short)(std::lrint(std::ldexp(r, 10 - e2)) - 1024);
+    return sgn | (unsigned short)((e2 + 15) << 10) | mant;
+}
+
+double fp16_value(unsigned short b)
+{
+    const int sgn = (b & 0x8000) ? -1 : 1, ex = (b >> 10) & 31, man = b & 1023;
+    if (ex == 0) return sgn * std::ldexp((double)man, -24);
+    return sgn * std::ldexp(1.0 + man / 1024.0, ex - 15);
 }
 
 // round to the nearest TF32 value (11 significant bits), ties away from zero
@@ -1491,7 +1525,7 @@ std::string roe_only(const Table &t)
 // most 5 for the larger splines; var.tensor = 2..8 asks for fewer.
 int tensor_slots(const Table &t, const ls_variant &var, ls_dtype dt)
 {
-    const TensorPlan p = tensor_plan(t, union_stencil(t), dt == LS_F32);
+    const TensorPlan p = tensor_plan(t, union_stencil(t), dt == LS_F32, dt == LS_F32 && var.tensor_kind == 1);
     // registers: a thread holds its next tile's K coefficients and its last
     // tile's N products; past 5 slots (640 threads, 102 registers each) the
     // larger splines spill (measured: BCC quintic BF16 at 6 slots)
@@ -1517,9 +1551,14 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     const int D = t.dim;
     const size_t K = t.ref.size();
     const bool split = e.ld == "ls_ld_f32";     // BF16 / FP16 coefficients are exact in TF32
-    const TensorPlan P = tensor_plan(t, st, split);
+    // FP32 coefficients as FP16 products: each point's values scaled by a power
+    // of two, split into FP16 hi (11 significant bits) + lo (the remainder),
+    // three kind::f16 products, the row's scale undone on the results
+    const bool h16 = split && var.tensor_kind == 1;
+    const TensorPlan P = tensor_plan(t, st, split, h16);
     const int KP = P.kp, N = P.n, NU = P.nu, S = tensor_slots(t, var, split ? LS_F32 : LS_BF16);
-    const int DC = (split ? 2 : 1) * KP;        // first accumulator column of a slot
+    const int AC = h16 ? KP / 2 : KP;           // columns of one A split
+    const int DC = split ? 2 * AC : AC;         // first accumulator column of a slot
     int alloc = 32;
     while (alloc < S * P.cols) alloc *= 2;
     info.tmem_cols = alloc;
@@ -1530,8 +1569,33 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
             for (const auto &pr : P.terms[k].at(m)) B[(size_t)P.col[k].at(m) * KP + pr.first] += pr.second;
     // the table is emitted with the value kernel; the value + gradient kernel reads it too
     const std::string tab = "ls_tcB_" + kname(t, "eval");
-    if (!grad) o << "static __device__ const float " << tab << "[" << 2 * N * KP << "] = {\n";
-    for (int h = 0; h < (grad ? 0 : 2); ++h)
+    // FP16 form: the matrix scaled by 2^sB so that its largest entry lies in
+    // [2^14, 2^15) (every entry and its lo part then far from the FP16 subnormals)
+    int sB = 0;
+    if (h16) {
+        double bmax = 0.0;
+        for (double v : B) bmax = std::max(bmax, std::fabs(v));
+        int ex = 1;
+        if (bmax > 0.0) std::frexp(bmax, &ex);      // bmax in [2^(ex-1), 2^ex)
+        sB = 15 - ex;
+    }
+    if (!grad && h16) {
+        // FP16 hi / lo bits, (n / 8) * 8 KP + (u / 8) * 64 + (n % 8) * 8 + (u % 8)
+        o << "static __device__ const unsigned short " << tab << "[" << 2 * N * KP << "] = {\n";
+        for (int h = 0; h < 2; ++h)
+            for (int idx = 0; idx < N * KP; ++idx) {
+                const int g = idx / (8 * KP), rem = idx % (8 * KP);
+                const int ug = rem / 64, r2 = rem % 64;
+                const int nn = g * 8 + r2 / 8, u = ug * 8 + r2 % 8;
+                const double v = std::ldexp(B[(size_t)nn * KP + u], sB);
+                const unsigned short hb = fp16_bits(v);
+                const unsigned short bits = h == 0 ? hb : fp16_bits(v - fp16_value(hb));
+                o << bits << ((idx + 1) % 16 == 0 ? ",\n" : ", ");
+            }
+        o << "};\n";
+    }
+    if (!grad && !h16) o << "static __device__ const float " << tab << "[" << 2 * N * KP << "] = {\n";
+    for (int h = 0; h < (grad || h16 ? 0 : 2); ++h)
         for (int idx = 0; idx < N * KP; ++idx) {
             // idx = (n / 8) * 8 KP + (u / 4) * 32 + (n % 8) * 4 + (u % 4)
             const int g = idx / (8 * KP), rem = idx % (8 * KP);
@@ -1541,8 +1605,10 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
             const double hi = tf32_round(v);
             o << flit(h == 0 ? hi : tf32_round(v - hi)) << ((idx + 1) % 8 == 0 ? ",\n" : ", ");
         }
-    if (!grad) o << "};\n";
-    const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((128u >> 4) << 24);
+    if (!grad && !h16) o << "};\n";
+    // D FP32; A, B TF32 (2) or FP16 (0): always the same type for A and B
+    const unsigned ab = h16 ? 0u : 2u;
+    const unsigned idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((unsigned)(N >> 3) << 17) | ((128u >> 4) << 24);
     auto reglist = [](int cnt, int op0) {
         std::string r = "{";
         for (int q = 0; q < cnt; ++q) r += (q ? "," : "") + std::string("%") + std::to_string(op0 + q);
@@ -1551,7 +1617,7 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     const int fma0 = e.fma;
     o << "extern \"C\" __global__ void __launch_bounds__(" << 128 * S << ", 1) "
       << kname(t, grad ? "eval_grad" : "eval") << "(const LsEvalArgs a)\n{\n";
-    o << "  __shared__ __align__(1024) float ls_sB[" << 2 * N * KP << "];\n";
+    o << "  __shared__ __align__(1024) " << (h16 ? "unsigned short" : "float") << " ls_sB[" << 2 * N * KP << "];\n";
     o << "  __shared__ __align__(8) unsigned long long ls_bar[" << S << "];\n";
     o << "  __shared__ unsigned ls_cnt[" << S << "];\n";
     o << "  __shared__ unsigned ls_tbase;\n";
@@ -1581,6 +1647,7 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "  const unsigned sb = (unsigned)__cvta_generic_to_shared(ls_sB);\n";
     o << "  unsigned phase = 0;\n  bool pending = false, bad = false;\n";
     o << "  long long pi = 0;\n  int pst = 2, ppsi = 0;\n  float pa0 = 0.0f, pa1 = 0.0f, pa2 = 0.0f;\n";
+    if (h16) o << "  float pinv = 1.0f;   // the previous tile's scales (row and matrix), undone on its results\n";
     if (grad) {
         // the fold of the previous tile's point: reference axis and sign per Cartesian axis
         o << "  int pri0 = 0, pri1 = 1, pri2 = 2;\n  unsigned png0 = 0u, png1 = 0u, png2 = 0u;\n";
@@ -1640,7 +1707,8 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
         std::map<I3, std::string> pre;
         for (const auto &m : P.sup[k]) {
             const std::string nm = "tA" + std::to_string(P.col[k].at(m));
-            o << "      const float " << nm << " = __uint_as_float(td" << P.col[k].at(m) << ");\n";
+            o << "      const float " << nm << " = __uint_as_float(td" << P.col[k].at(m) << ")"
+              << ";\n";
             pre[m] = nm;
         }
         fk.push_back(emit_region_poly(e, t, (int)k, st.region_to_union[k], grad ? 1 : 0, &pre));
@@ -1652,7 +1720,8 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
         for (int k = (int)K - 2; k >= 0; --k)
             sel = "(psi == " + std::to_string(k) + ") ? " + fk[k][c] + " : (" + sel + ")";
         const std::string nm = c == 0 ? "tf" : "tg" + std::to_string(c - 1);
-        o << "      const float " << nm << " = " << sel << ";\n";
+        // FP16 form: the results are linear in the products, so both scales come off once here
+        o << "      const float " << nm << " = " << (h16 ? "pinv * (" + sel + ")" : sel) << ";\n";
         out.push_back(nm);
     }
     if (!grad) {
@@ -1675,7 +1744,29 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "    }\n";
     o << "    if (!have) break;\n";
     // split and stage this tile's coefficients (slot columns [0, KP) hi, [KP, 2 KP) lo)
-    for (int j = 0; j < KP; ++j) {
+    if (h16) {
+        // the row's scale: a power of two that brings max |c_j| into [2^14, 2^15)
+        // (biased exponent teb: tsc = 2^(141 - teb); rows below 2^-112 keep less scaling)
+        o << "    float tmx = 0.0f;\n";
+        for (int j = 0; j < KP; ++j) o << "    tmx = fmaxf(tmx, fabsf(tc" << j << "));\n";
+        o << "    const int teb = min(max((int)(__float_as_uint(tmx) >> 23), 15), 252);\n";
+        o << "    const float tsc = __uint_as_float((unsigned)(268 - teb) << 23);\n";
+        o << "    const float tinv = __uint_as_float((unsigned)(teb - 14) << 23) * " << flit(std::ldexp(1.0, -sB))
+          << ";\n";
+        // hi: the scaled value with its low 13 mantissa bits cleared (11
+        // significant bits, an FP16 value wherever FP16 is normal); lo: the exact
+        // remainder, rounded to FP16.  Two values per 32-bit column, the even K
+        // index in the low half (cvt.rn.f16x2.f32 puts its first operand high).
+        for (int q = 0; q < KP / 2; ++q) {
+            o << "    unsigned th" << q << ", tw" << q << ";\n";
+            o << "    { const float v0 = tc" << 2 * q << " * tsc, v1 = tc" << 2 * q + 1 << " * tsc;\n";
+            o << "      const float h0 = __uint_as_float(__float_as_uint(v0) & 0xffffe000u);\n";
+            o << "      const float h1 = __uint_as_float(__float_as_uint(v1) & 0xffffe000u);\n";
+            o << "      asm(\"cvt.rn.f16x2.f32 %0, %1, %2;\" : \"=r\"(th" << q << ") : \"f\"(h1), \"f\"(h0));\n";
+            o << "      asm(\"cvt.rn.f16x2.f32 %0, %1, %2;\" : \"=r\"(tw" << q << ") : \"f\"(v1 - h1), \"f\"(v0 - h0)); }\n";
+        }
+    }
+    for (int j = 0; j < (h16 ? 0 : KP); ++j) {
         if (split) {
             o << "    unsigned th" << j << ", tw" << j << ";\n";
             o << "    asm(\"cvt.rna.tf32.f32 %0, %1;\" : \"=r\"(th" << j << ") : \"f\"(tc" << j << "));\n";
@@ -1685,9 +1776,9 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
         }
     }
     for (int h = 0; h < (split ? 2 : 1); ++h)
-        for (const auto &ch : pow2_chunks(KP)) {
+        for (const auto &ch : pow2_chunks(AC)) {
             o << "    asm volatile(\"tcgen05.st.sync.aligned.32x32b.x" << ch.second << ".b32 [%0], "
-              << reglist(ch.second, 1) << ";\" :: \"r\"(tl + " << (h * KP + ch.first) << "u)";
+              << reglist(ch.second, 1) << ";\" :: \"r\"(tl + " << (h * AC + ch.first) << "u)";
             for (int q = 0; q < ch.second; ++q) o << ", \"r\"(" << (h ? "tw" : "th") << (ch.first + q) << ")";
             o << " : \"memory\");\n";
         }
@@ -1702,15 +1793,17 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
          "\"r\"(cnt) : \"memory\");\n";
     o << "    if (lane == 0 && (arrived & 3u) == 3u) {\n";
     o << "      asm volatile(\"tcgen05.fence::after_thread_sync;\" ::: \"memory\");\n";
-    // smem descriptors: start >> 4, LBO 128 B, SBO 32 KP B, version 1, no swizzle
-    o << "      const unsigned long long dbase = ((unsigned long long)(" << 8 * KP * 4 << " >> 4) << 32) |"
+    // smem descriptors: start >> 4, LBO 128 B, SBO = 8 rows of K elements, version 1, no swizzle
+    const int eb = h16 ? 2 : 4;                 // bytes per element
+    o << "      const unsigned long long dbase = ((unsigned long long)(" << 8 * KP * eb << " >> 4) << 32) |"
          " ((unsigned long long)(128 >> 4) << 16) | (1ull << 46);\n";
-    const char *mma =
-        "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p; }";
+    const std::string mma = std::string("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::") +
+                            (h16 ? "f16" : "tf32") + " [%0], [%1], %2, %3, p; }";
     struct Prod { int acol; int boff; };
-    const Prod prods[3] = {{0, 0}, {0, N * KP * 4}, {KP, 0}};
+    const Prod prods[3] = {{0, 0}, {0, N * KP * eb}, {AC, 0}};
+    const int kstep = h16 ? 16 : 8;              // K elements per product instruction (32 bytes)
     for (int pi = 0; pi < (split ? 3 : 2); ++pi)
-        for (int s2 = 0; s2 < KP / 8; ++s2) {
+        for (int s2 = 0; s2 < KP / kstep; ++s2) {
             o << "      asm volatile(\"" << mma << "\" :: \"r\"(tm + " << DC << "u), \"r\"(tm + "
               << (prods[pi].acol + 8 * s2) << "u), \"l\"(dbase | (unsigned long long)(((sb + "
               << (prods[pi].boff + 256 * s2) << "u) & 0x3FFFFu) >> 4)), \"r\"(" << idesc << "u), \"r\"("
@@ -1720,6 +1813,7 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
          "\"r\"(bar) : \"memory\");\n";
     o << "    }\n";
     o << "    pending = true;\n    pi = i;\n    pst = stt;\n    ppsi = tpsi;\n";
+    if (h16) o << "    pinv = tinv;\n";
     for (int q = 0; q < D; ++q) o << "    pa" << q << " = ta" << q << ";\n";
     if (grad)
         for (int q = 0; q < D; ++q) o << "    pri" << q << " = tri" << q << "; png" << q << " = tng" << q << ";\n";

@@ -105,9 +105,10 @@ def distinct_lines_per_point(table, ext, pts: np.ndarray, elem_bytes: int = 4, l
     return float(distinct.mean())
 
 
-def tensor_shape(table, expansion: str = "sparse"):
+def tensor_shape(table, expansion: str = "sparse", kstep: int = 8):
     """Shape of the coefficient-transform product of the tensor-core value
-    kernel: K = union stencil sites rounded up to 8 (the TF32 product's K step),
+    kernel: K = union stencil sites rounded up to kstep (8: the TF32 product's K
+    step; 16: the FP16 form's),
     N = the (region, monomial) columns with a nonzero entry rounded up to 16
     (at least 16), and the nonzero count of the transform matrix (the FMA
     path's multiply-adds).  Returns (K, N, nnz)."""
@@ -125,6 +126,6 @@ def tensor_shape(table, expansion: str = "sparse"):
             if col:
                 ncol += 1
                 nnz += col
-    K = (len(union) + 7) // 8 * 8
+    K = (len(union) + kstep - 1) // kstep * kstep
     N = max(16, (ncol + 15) // 16 * 16)
     return K, N, nnz

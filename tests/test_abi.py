@@ -40,7 +40,7 @@ def test_status_strings():
     L = _abi.lib()
     for code in range(9):
         assert L.ls_status_str(code)
-    assert L.ls_abi_version() == 3
+    assert L.ls_abi_version() == 4
 
 
 @pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
@@ -173,12 +173,19 @@ def test_tensor_variant_is_validated_before_any_device_call():
     L = _abi.lib()
     for name, var in (("tricubic", {"tensor": 1}), ("trilinear", {"tensor": 1}),
                       ("bcc_quintic", {"tensor": 1, "stage": 1}), ("fcc6", {"tensor": 1, "producers": 2}),
-                      ("bcc_quintic", {"tensor": 1, "pts_per_thread": 4})):
+                      ("bcc_quintic", {"tensor": 1, "pts_per_thread": 4}), ("bcc_quintic", {"tensor_kind": 1}),
+                      ("fcc6", {"tensor": 1, "tensor_kind": 2})):
         h = _abi.DescHolder(table(name), "probe")
         out = ctypes.c_void_p()
         assert L.ls_spline_create(ctypes.byref(h.desc), _abi.LS_F32, ctypes.byref(_abi.variant(**var)),
                                   ctypes.byref(out)) == 1
         assert b"tensor" in L.ls_last_error()
+    # the FP16 form is for FP32 coefficients (BF16 / FP16 data are exact in TF32)
+    h = _abi.DescHolder(table("fcc6"), "probe")
+    out = ctypes.c_void_p()
+    assert L.ls_spline_create(ctypes.byref(h.desc), _abi.LS_BF16, ctypes.byref(_abi.variant(tensor=1, tensor_kind=1)),
+                              ctypes.byref(out)) == 1
+    assert b"tensor_kind" in L.ls_last_error()
 
 
 def test_tensor_variant_source():
@@ -207,3 +214,59 @@ def test_tensor_variant_source():
         f = float.fromhex(v[:-1]) if v != "0.0f" else 0.0
         bits = struct.unpack("<I", struct.pack("<f", f))[0]
         assert bits & 0x1FFF == 0
+
+
+def _tensor_source(name, **var):
+    import re
+    from paper_2102_08518_b300 import api
+    kn = api.kernel_name(name, "f32", **var)
+    h = _abi.DescHolder(table(name), kn)
+    assert _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), _abi.LS_F32, ctypes.byref(_abi.variant(**var))) == 0
+    cache = os.path.join(ROOT, "paper_2102_08518_b300", "kcache")
+    files = sorted((f for f in os.listdir(cache) if re.fullmatch(f"ls_{kn}_f32_[0-9a-f]+\\.cu", f)),
+                   key=lambda f: os.path.getmtime(os.path.join(cache, f)))
+    return open(os.path.join(cache, files[-1])).read()
+
+
+def _table_entries(src):
+    import re
+    tab = src[src.index("ls_tcB_"):]
+    m = re.match(r"ls_tcB_\w+\[(\d+)\] = \{", tab)
+    body = tab[m.end():tab.index("};")]
+    return int(m.group(1)), [v.strip() for v in body.replace("\n", " ").split(",") if v.strip()]
+
+
+@pytest.mark.parametrize("name", ["bcc_quintic", "fcc6"])
+def test_tensor_fp16_form_source(name):
+    """The FP16 form: kind::f16 products in K steps of 16, and a transform
+    table of FP16 hi / lo pairs that is the TF32 form's matrix scaled by one
+    power of two (largest entry in [2^14, 2^15)), to 21 significant bits."""
+    import numpy as np
+    src32 = _tensor_source(name, tensor=1)
+    src16 = _tensor_source(name, tensor=1, tensor_kind=1)
+    kern = src16[src16.index("ls_eval__"):]
+    assert "kind::tf32" not in kern
+    n32, v32 = _table_entries(src32)
+    n16, v16 = _table_entries(src16)
+    f32 = np.array([float.fromhex(v[:-1]) if v != "0.0f" else 0.0 for v in v32])
+    b16 = np.array([int(v) for v in v16], dtype=np.uint16).view(np.float16).astype(np.float64)
+    # K (padded to 16 here, to 8 in the TF32 form) from the product count: 3 products x 2 kernels x K / 16
+    kp = kern.count("tcgen05.mma.cta_group::1.kind::f16") // 6 * 16
+    assert kp > 0 and (n16 // 2) % kp == 0
+    N = n16 // 2 // kp
+    kp32 = n32 // 2 // N
+    assert kp32 * N * 2 == n32 and kp - 16 < kp32 <= kp
+    m32 = np.zeros((N, kp))
+    m16 = np.zeros((N, kp))
+    for idx in range(N * kp32):
+        g, r = divmod(idx, 8 * kp32)
+        m32[g * 8 + (r % 32) // 4, (r // 32) * 4 + r % 4] += f32[idx] + f32[N * kp32 + idx]
+    for idx in range(N * kp):
+        g, r = divmod(idx, 8 * kp)
+        m16[g * 8 + (r % 64) // 8, (r // 64) * 8 + r % 8] += b16[idx] + b16[N * kp + idx]
+    scale = np.abs(m16).max() / np.abs(m32).max()
+    assert 2.0 ** np.round(np.log2(scale)) == pytest.approx(scale, rel=1e-5)
+    scale = 2.0 ** np.round(np.log2(scale))
+    assert 2.0 ** 14 <= np.abs(m16).max() < 2.0 ** 15
+    assert np.max(np.abs(m16 / scale - m32) / np.maximum(np.abs(m32), 1e-30)) < 2.0 ** -20
+    assert np.array_equal(m16 == 0, m32 == 0)

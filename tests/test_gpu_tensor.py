@@ -3,7 +3,9 @@
 The coefficient transform A = M^T c of a tile of 128 points is one tcgen05
 matrix product (three TF32 products for FP32 accuracy; two for BF16 / FP16 storage, whose
 values are exact in TF32) instead of per-thread FMAs; everything else is the
-FMA kernel's code.  Checked: every non-separable
+FMA kernel's code.  FP32 data also has an FP16 form (tensor_kind 1): each
+point's coefficients scaled by a power of two, split into FP16 hi + lo, three
+kind::f16 products, the scales undone on the results.  Checked: every non-separable
 spline, tile-ragged point counts, points beyond the arrays, non-finite and
 far points, both linear layouts and BF16 storage, several tiles per block
 (grid-stride loop over the mbarrier phases), and agreement with the FMA
@@ -45,23 +47,25 @@ def oracle_eval(name, ext, coef_np, pts):
     return oracle.eval_sum(spec, coef_np.astype(np.float64).ravel(), pts.astype(np.float64))
 
 
+@pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("name", NAMES)
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 3001])
-def test_tensor_matches_oracle(name, n):
+def test_tensor_matches_oracle(name, n, kind):
     ext = EXT[name]
     lat = workloads.SPLINE_LATTICE[name]
     coef = workloads.coef_uniform(lat, ext, seed=21)
     lo, hi = workloads.bounding_box(lat, ext)
     pts = workloads.points_uniform(n, lo - 2.5, hi + 2.5, seed=n + 7)
-    vol = volume(name, ext, coef, tensor=1)
+    vol = volume(name, ext, coef, tensor=1, tensor_kind=kind)
     got = vol.eval(torch.from_numpy(pts).cuda()).cpu().numpy().astype(np.float64)
     vol.spline.status()
     want = oracle_eval(name, ext, coef, pts)
     assert np.max(np.abs(got - want)) <= TOL * np.abs(coef).max()
 
 
+@pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("name", ["bcc_quintic", "fcc6"])
-def test_tensor_special_points(name):
+def test_tensor_special_points(name, kind):
     """NaN gives NaN, infinite and far points give 0, as in the FMA kernel."""
     ext = EXT[name]
     lat = workloads.SPLINE_LATTICE[name]
@@ -72,14 +76,14 @@ def test_tensor_special_points(name):
     pts[6, 2] = np.inf
     pts[7] = 5.0e6
     pts[8] = lo - 30.0
-    vol = volume(name, ext, coef, tensor=1)
+    vol = volume(name, ext, coef, tensor=1, tensor_kind=kind)
     got = vol.eval(torch.from_numpy(pts).cuda()).cpu().numpy()
     assert np.isnan(got[5]) and got[6] == 0.0 and got[7] == 0.0 and got[8] == 0.0
     keep = np.ones(len(pts), bool)
     keep[5:9] = False
     want = oracle_eval(name, ext, coef, pts[keep])
     assert np.max(np.abs(got[keep] - want)) <= TOL * np.abs(coef).max()
-    assert volume(name, ext, coef, tensor=1).eval(torch.empty(0, 3, device="cuda")).numel() == 0
+    assert volume(name, ext, coef, tensor=1, tensor_kind=kind).eval(torch.empty(0, 3, device="cuda")).numel() == 0
 
 
 @pytest.mark.parametrize("layout,dtype", [("interleaved", "f32"), ("coset", "bf16"), ("interleaved", "bf16"),
@@ -98,8 +102,9 @@ def test_tensor_layouts_and_storage(name, layout, dtype):
     assert np.max(np.abs(got - want)) <= tol * np.abs(coef).max()
 
 
+@pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("name", ["bcc_quintic", "fcc6", "bcc_linear"])
-def test_tensor_agrees_with_fma_kernel_on_many_points(name):
+def test_tensor_agrees_with_fma_kernel_on_many_points(name, kind):
     """2^20 points, one block per SM (hundreds of tiles per block): both
     kernels approximate the same exact sum."""
     ext = (48, 40, 36)
@@ -108,7 +113,7 @@ def test_tensor_agrees_with_fma_kernel_on_many_points(name):
     lo, hi = workloads.bounding_box(lat, ext)
     pts = torch.from_numpy(workloads.points_uniform(1 << 20, lo - 1.0, hi + 1.0, seed=5)).cuda()
     plain = volume(name, ext, coef).eval(pts)
-    vt = volume(name, ext, coef, tensor=1, blocks_per_sm=1)
+    vt = volume(name, ext, coef, tensor=1, tensor_kind=kind, blocks_per_sm=1)
     got = vt.eval(pts)
     vt.spline.status()
     assert torch.max(torch.abs(got - plain)).item() <= 2 * TOL * float(np.abs(coef).max())
@@ -120,9 +125,10 @@ def test_tensor_agrees_with_fma_kernel_on_many_points(name):
 GRAD_TOL = 1e-5
 
 
+@pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("name", NAMES)
 @pytest.mark.parametrize("n", [1, 129, 3001])
-def test_tensor_value_gradient_matches_oracle(name, n):
+def test_tensor_value_gradient_matches_oracle(name, n, kind):
     """The value + gradient kernel of a tensor-core spline: the same product,
     then the gradient's Horner forms mapped back through the fold."""
     ext = EXT[name]
@@ -130,7 +136,7 @@ def test_tensor_value_gradient_matches_oracle(name, n):
     coef = workloads.coef_uniform(lat, ext, seed=31)
     lo, hi = workloads.bounding_box(lat, ext)
     pts = workloads.points_uniform(n, lo - 2.0, hi + 2.0, seed=n + 17)
-    vol = volume(name, ext, coef, layout="interleaved", tensor=1)
+    vol = volume(name, ext, coef, layout="interleaved", tensor=1, tensor_kind=kind)
     val, grad = vol.eval_grad(torch.from_numpy(pts).cuda())
     vol.spline.status()
     spec = ORACLE_SPEC[name]().with_extent(ext)
@@ -169,3 +175,24 @@ def test_tensor_value_gradient_agrees_with_fma_kernel(name):
     assert torch.max(torch.abs(v1 - v0)).item() <= 2 * TOL * cmax
     assert torch.max(torch.abs(g1 - g0)).item() <= 2 * GRAD_TOL * cmax
     assert torch.equal(g1, g2)
+
+
+@pytest.mark.parametrize("name", ["bcc_quintic", "fcc6", "zp"])
+def test_tensor_fp16_form_is_scale_invariant(name):
+    """The FP16 form scales each point's coefficients by a power of two and
+    undoes it on the results: data scaled by 2^k (within the normal FP32
+    range) gives the results scaled by 2^k, bit for bit, values and gradients."""
+    ext = EXT[name]
+    lat = workloads.SPLINE_LATTICE[name]
+    coef = workloads.coef_uniform(lat, ext, seed=41).astype(np.float32)
+    coef[np.abs(coef) < 2.0 ** -20] = 2.0 ** -20      # scaled copies stay normal
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = torch.from_numpy(workloads.points_uniform(5000, lo - 1.0, hi + 1.0, seed=42)).cuda()
+    base = volume(name, ext, coef, layout="interleaved", tensor=1, tensor_kind=1)
+    v0, g0 = base.eval_grad(pts)
+    for k in (-90, -37, 1, 45, 90):
+        vk = volume(name, ext, np.ldexp(coef, k), layout="interleaved", tensor=1, tensor_kind=1)
+        f = 2.0 ** k
+        assert torch.equal(vk.eval(pts), v0 * f), k
+        v, g = vk.eval_grad(pts)
+        assert torch.equal(v, v0 * f) and torch.equal(g, g0 * f), k

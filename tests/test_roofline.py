@@ -80,3 +80,25 @@ def test_tensor_shape_matches_the_generated_kernel():
         m = re.search(r"float ls_sB\[(\d+)\]", src)
         assert int(m.group(1)) == 2 * N * K, name
         assert K % 8 == 0 and N % 16 == 0 and nnz <= K * N
+
+
+def test_tensor_shape_of_the_fp16_form():
+    """The FP16 form pads K to 16: its table holds 2 N K FP16 values (hi, lo)."""
+    import ctypes
+    import os
+    import re
+    from paper_2102_08518_b300 import _abi, api
+    from paper_2102_08518_b300.roofline import tensor_shape
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for name in ("bcc_quintic", "fcc6"):
+        K, N, nnz = tensor_shape(api.table(name), kstep=16)
+        kn = api.kernel_name(name, "f32", tensor=1, tensor_kind=1)
+        h = _abi.DescHolder(api.table(name), kn)
+        assert _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), _abi.LS_F32,
+                                               ctypes.byref(_abi.variant(tensor=1, tensor_kind=1))) == 0
+        cache = os.path.join(root, "paper_2102_08518_b300", "kcache")
+        files = sorted((f for f in os.listdir(cache) if re.fullmatch(f"ls_{kn}_f32_[0-9a-f]+\\.cu", f)),
+                       key=lambda f: os.path.getmtime(os.path.join(cache, f)))
+        src = open(os.path.join(cache, files[-1])).read()
+        m = re.search(r"unsigned short ls_tcB_\w+\[(\d+)\]", src)
+        assert int(m.group(1)) == 2 * N * K and K % 16 == 0, name
