@@ -164,6 +164,43 @@ def oracle_leg(coef, pts_sets):
 # helpers
 # ---------------------------------------------------------------------------
 
+def link_bound(torch, host_buf, dev_buf, h2d_bytes, d2h_bytes, step_ms):
+    """The host link's rates measured with the step's own pinned buffers
+    (host-to-device alone, device-to-host alone, both at once) and the
+    shortest time they allow for one end-to-end step's bytes: both directions
+    at the duplex rate while the smaller flow lasts, then the rest alone."""
+    back = torch.empty_like(host_buf).pin_memory()
+    nbytes = host_buf.numel() * host_buf.element_size()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def h2d():
+        dev_buf.copy_(host_buf, non_blocking=True)
+
+    def d2h():
+        back.copy_(dev_buf, non_blocking=True)
+
+    def both():
+        cur = torch.cuda.current_stream()
+        s_in.wait_stream(cur)
+        s_out.wait_stream(cur)
+        with torch.cuda.stream(s_in):
+            h2d()
+        with torch.cuda.stream(s_out):
+            d2h()
+        cur.wait_stream(s_in)
+        cur.wait_stream(s_out)
+
+    r_in = nbytes / time_ms(torch, h2d, reps=5, warm=1) / 1e6       # GB/s
+    r_out = nbytes / time_ms(torch, d2h, reps=5, warm=1) / 1e6
+    r_dup = nbytes / time_ms(torch, both, reps=5, warm=1) / 1e6      # each way
+    lo = min(h2d_bytes, d2h_bytes)
+    rest_in, rest_out = h2d_bytes - lo, d2h_bytes - lo
+    bound_ms = lo / r_dup / 1e6 + rest_in / r_in / 1e6 + rest_out / r_out / 1e6
+    return {"h2d_gbs": round(r_in, 1), "d2h_gbs": round(r_out, 1), "duplex_each_way_gbs": round(r_dup, 1),
+            "bound_ms": round(bound_ms, 3), "step_ms": round(step_ms, 3), "frac": round(bound_ms / step_ms, 3),
+            "note": "pinned copies of the step's 201 MB point buffer; bound = the step's bytes at these rates"}
+
+
 def time_ms(torch, fn, reps=10, warm=3):
     for _ in range(warm):
         fn()
@@ -417,6 +454,8 @@ def run_gpu(args):
            "h2d_bytes_per_step": sum(t.numel() * 4 for t in host_pts.values()),
            "d2h_bytes_per_step": sum(t.numel() * 4 for t in host_out.values()),
            "api": "ls_eval_host_multi per point set (pinned host memory, copies overlapped with kernels)"}
+    e2e["link"] = link_bound(torch, host_pts["uniform"], pts["uniform"], e2e["h2d_bytes_per_step"],
+                             e2e["d2h_bytes_per_step"], e2e_s * 1e3)
 
     result = {"metric": METRIC, "value": round(value, 4), "unit": "Gpoints/s", "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),

@@ -1743,7 +1743,25 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "      pending = false;\n";
     o << "    }\n";
     o << "    if (!have) break;\n";
-    // split and stage this tile's coefficients (slot columns [0, KP) hi, [KP, 2 KP) lo)
+    // split and stage this tile's coefficients (slot columns [0, KP) hi, [KP, 2 KP) lo).
+    // With several reference regions the gathers cover their union: the sites
+    // outside the point's own region are zeroed first (their weights vanish
+    // there), so that neither the row scale nor a non-finite value of a site
+    // the point does not use reaches its products (0 x inf would be NaN).
+    if (K > 1) {
+        for (int u = 0; u < NU; ++u) {
+            std::vector<int> regs;
+            for (size_t k = 0; k < K; ++k)
+                if (std::find(st.region_to_union[k].begin(), st.region_to_union[k].end(), u) !=
+                    st.region_to_union[k].end())
+                    regs.push_back((int)k);
+            if (regs.size() == K) continue;
+            o << "    if (";
+            for (size_t r = 0; r < regs.size(); ++r) o << (r ? " && " : "") << "tpsi != " << regs[r];
+            if (regs.empty()) o << "true";
+            o << ") tc" << u << " = 0.0f;\n";
+        }
+    }
     if (h16) {
         // the row's scale: a power of two that brings max |c_j| into [2^14, 2^15)
         // (biased exponent teb: tsc = 2^(141 - teb); rows below 2^-112 keep less scaling)

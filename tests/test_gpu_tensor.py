@@ -196,3 +196,67 @@ def test_tensor_fp16_form_is_scale_invariant(name):
         assert torch.equal(vk.eval(pts), v0 * f), k
         v, g = vk.eval_grad(pts)
         assert torch.equal(v, v0 * f) and torch.equal(g, g0 * f), k
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("name", ["bcc_quintic", "fcc6"])
+def test_tensor_with_coefficients_of_very_different_magnitudes(name, kind):
+    """Blocks of the volume scaled by 2^-40, 1 and 2^40: every point's result
+    must keep FP32 accuracy relative to its own stencil's coefficients, not to
+    the volume's largest one (the FP16 form scales each point's row on its
+    own; the TF32 form has FP32's exponent range)."""
+    from paper_2102_08518_b300.api import table
+    from paper_2102_08518_b300.roofline import stencil_indices
+    ext = (16, 12, 12)
+    lat = workloads.SPLINE_LATTICE[name]
+    coef = workloads.coef_uniform(lat, ext, seed=51).astype(np.float64)
+    C = coef.shape[0]
+    e2, e1, e0 = np.meshgrid(np.arange(ext[2]), np.arange(ext[1]), np.arange(ext[0]), indexing="ij")
+    block = (e0 // 4 + e1 // 4 + e2 // 4) % 3                 # 0, 1, 2 in a 4 x 4 x 4 checkerboard
+    coef = coef * np.ldexp(1.0, 40 * (block - 1))[None, :, :, :].repeat(C, axis=0)
+    coef = coef.astype(np.float32)
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = workloads.points_uniform(4000, lo + 0.5, hi - 0.5, seed=52)
+    vol = volume(name, ext, coef, layout="interleaved", tensor=1, tensor_kind=kind)
+    val, grad = vol.eval_grad(torch.from_numpy(pts).cuda())
+    vol.spline.status()
+    spec = ORACLE_SPEC[name]().with_extent(ext)
+    want, wgrad = oracle.eval_sum_grad(spec, coef.astype(np.float64).ravel(), pts.astype(np.float64))
+    idx = stencil_indices(table(name), ext, pts, "coset")
+    flat = np.abs(coef.astype(np.float64).ravel())
+    local = np.where(idx >= 0, flat[np.maximum(idx, 0)], 0.0).max(axis=1)
+    assert np.all(local > 0)
+    err = np.abs(val.cpu().numpy().astype(np.float64) - want) / local
+    gerr = np.abs(grad.cpu().numpy().astype(np.float64) - wgrad).max(axis=1) / local
+    assert err.max() <= TOL and gerr.max() <= GRAD_TOL
+    # the volume's range: points in the small blocks sit 2^80 below the largest coefficient
+    assert local.min() < 2.0 ** -30 * np.abs(coef).max()
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_tensor_non_finite_coefficient_reaches_only_its_stencils(kind):
+    """FCC: the gathers cover the union of the two reference regions' stencils.
+    An infinite coefficient must make exactly the points whose own stencil holds
+    it non-finite; the rest stay finite and equal to the FMA kernel's."""
+    from paper_2102_08518_b300.api import table
+    from paper_2102_08518_b300.roofline import stencil_indices
+    name, ext = "fcc6", (10, 10, 10)
+    lat = workloads.SPLINE_LATTICE[name]
+    coef = workloads.coef_uniform(lat, ext, seed=61)
+    flat = coef.reshape(-1)
+    site = 2 * int(np.prod(ext)) + 5 + ext[0] * (4 + ext[1] * 5)    # coset 2, grid index (5, 4, 5)
+    flat[site] = np.inf
+    lo, hi = workloads.bounding_box(lat, ext)
+    c = (lo + hi) / 2
+    pts = workloads.points_uniform(20000, c - 3.0, c + 3.0, seed=62)
+    p = torch.from_numpy(pts).cuda()
+    ref = volume(name, ext, coef, layout="interleaved").eval(p).cpu().numpy()
+    vt = volume(name, ext, coef, layout="interleaved", tensor=1, tensor_kind=kind)
+    got = vt.eval(p).cpu().numpy()
+    vt.spline.status()
+    holds = (stencil_indices(table(name), ext, pts, "coset") == site).any(axis=1)
+    assert 100 < holds.sum() < len(pts) - 100
+    assert np.array_equal(~np.isfinite(got), holds)
+    assert np.array_equal(~np.isfinite(ref), holds)
+    ok = ~holds
+    assert np.max(np.abs(got[ok] - ref[ok])) <= 2 * TOL
