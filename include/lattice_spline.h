@@ -189,10 +189,12 @@ typedef struct {
                                           A = M^T c of each tile of 128 points as one matrix product
                                           on the tensor cores (tcgen05.mma kind::tf32, three TF32
                                           products for FP32 accuracy, accumulator in tensor memory);
-                                          one block per SM with S slots of 128 points, S = as many
-                                          as the 512 tensor-memory columns hold (at most 8), or T if
-                                          T = 2..8 is smaller; forces block = 128 S; non-separable
-                                          tables.  Bounded mbarrier waits (ls_spline_status) */
+                                          one block per SM with S slots of 128 points: T = 1, as many
+                                          as the 512 tensor-memory columns hold, at most 8 (at most 5
+                                          for splines of K + N >= 64, whose registers fill the file);
+                                          T = 2..8: T, at most what the columns hold; forces
+                                          block = 128 S; non-separable tables.  Bounded mbarrier
+                                          waits (ls_spline_status) */
     int32_t tensor_kind;               /* with tensor and FP32 coefficients: 0 = three TF32 products
                                           of the hi / lo split; 1 = three FP16 products: each point's
                                           coefficients scaled by a power of two (largest magnitude in

@@ -1530,8 +1530,10 @@ int tensor_slots(const Table &t, const ls_variant &var, ls_dtype dt)
     // tile's N products; past 5 slots (640 threads, 102 registers each) the
     // larger splines spill (measured: BCC quintic BF16 at 6 slots)
     const int cap = (p.kp + p.n >= 64) ? 5 : 8;
-    int s = std::max(1, std::min(cap, 512 / p.cols));
-    if (var.tensor >= 2 && var.tensor < s) s = var.tensor;
+    const int tmem_max = std::max(1, std::min(8, 512 / p.cols));
+    int s = std::min(cap, tmem_max);
+    // an explicit slot count (tensor >= 2) may go past the register cap, up to what tensor memory holds
+    if (var.tensor >= 2) s = std::min(var.tensor, tmem_max);
     return s;
 }
 
