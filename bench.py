@@ -566,7 +566,8 @@ def extra_fwd_bwd(torch, dev, vols, pts, outs):
 
 def extra_fcc(torch, dev, vols, pts, outs):
     """FCC 4x128^3, 2^26 uniform points: unsorted vs Morton-sorted evaluation and gradient
-    (the evaluation kernel variant autotuned on the unsorted points)."""
+    (the evaluation kernel variant autotuned on the unsorted points; the sorted
+    points also with a variant autotuned on them)."""
     from paper_2102_08518_b300.api import Spline, Volume, autotune, morton_sort, permute_rows, relayout, \
         TUNE_CANDIDATES_SMALL
     ext = (128, 128, 128)
@@ -603,6 +604,14 @@ def extra_fcc(torch, dev, vols, pts, outs):
             best = (t_sorted, ent, ps)
         del perm
     res["sorted"] = best[1]
+    # the variant autotuned on the sorted points themselves
+    sps = autotune("fcc6", "f32", ext, coef, [best[2]], candidates=TUNE_CANDIDATES_SMALL,
+                   tag="fcc_sorted", layout="interleaved")
+    vss = Volume(sps, ext, coef, layout="interleaved")
+    t_ss = time_ms(torch, lambda: vss.eval(best[2], out), reps=5)
+    vss.spline.status()
+    res["sorted_autotuned"] = {"variant": sps.variant, "ms": round(t_ss, 3), "gpoints_s": round(n / t_ss / 1e6, 3)}
+    del vss
     # tile-staged value kernel (one TMA tensor copy of the block's coefficient tile)
     staged = {}
     for kw in ({"stage": 1}, {"stage": 1, "block": 128}, {"stage": 16, "block": 128}):

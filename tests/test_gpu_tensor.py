@@ -260,3 +260,26 @@ def test_tensor_non_finite_coefficient_reaches_only_its_stencils(kind):
     assert np.array_equal(~np.isfinite(ref), holds)
     ok = ~holds
     assert np.max(np.abs(got[ok] - ref[ok])) <= 2 * TOL
+
+
+@pytest.mark.parametrize("slots,kind", [(2, 0), (3, 1), (6, 1), (8, 0)])
+def test_tensor_explicit_slot_counts(slots, kind):
+    """tensor = S sets the slots per SM (at most what the 512 tensor-memory
+    columns hold): every count gives the default's results within the
+    tolerance (BCC quintic: 112 columns a slot in the TF32 form, so 8 asks
+    for more than fit and gets 4; 80 in the FP16 form)."""
+    name = "bcc_quintic"
+    ext = (24, 20, 18)
+    lat = workloads.SPLINE_LATTICE[name]
+    coef = workloads.coef_uniform(lat, ext, seed=71)
+    lo, hi = workloads.bounding_box(lat, ext)
+    pts = workloads.points_uniform(100_003, lo - 1.0, hi + 1.0, seed=72)
+    vt = volume(name, ext, coef, layout="interleaved", tensor=slots, tensor_kind=kind)
+    import re
+    m = re.search(r"__launch_bounds__\((\d+), 1\) ls_eval__", vt.spline.source())
+    assert int(m.group(1)) == 128 * min(slots, 512 // (80 if kind else 112))
+    got = vt.eval(torch.from_numpy(pts).cuda()).cpu().numpy().astype(np.float64)
+    vt.spline.status()
+    idx = np.random.default_rng(3).choice(len(pts), 1500, replace=False)
+    want = oracle_eval(name, ext, coef, pts[idx])
+    assert np.max(np.abs(got[idx] - want)) <= TOL * np.abs(coef).max()
