@@ -488,7 +488,8 @@ TUNE_CANDIDATES_SMALL = tuple([dict(block=256, blocks_per_sm=b, expansion=x) for
                               [dict(block=128, blocks_per_sm=b) for b in (2, 4)] +
                               [dict(tensor=1, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(tensor=1, tensor_kind=1, expansion=x) for x in ("sparse", "centroid")] +
-                              [dict(tensor=4, tensor_kind=1)])
+                              [dict(tensor=4, tensor_kind=1)] +
+                              [dict(tensor=6, tensor_kind=1, expansion=x) for x in ("sparse", "centroid")])
 
 
 def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_sets: Sequence[torch.Tensor],
