@@ -1541,10 +1541,12 @@ namespace {
 
 // One block per SM (a block that allocates tensor memory is the only one on
 // its SM) with S slots of 4 warps; each slot owns 128 points at a time, a
-// column range of tensor memory, an mbarrier and a named barrier, and runs
+// column range of tensor memory, an mbarrier and an arrival counter (the
+// last of its warps to stage a tile issues the product), and runs
 // independently of the others.  Within a slot the tile loop is software
-// pipelined: the gathers of tile t are issued before the results of tile
-// t - 1 are read back, so the product of t - 1 runs behind them.
+// pipelined: the product of tile t - 1 runs while tile t is gathered, and
+// (up to 5 slots, or for small splines) the gathers of tile t are issued
+// before the results of tile t - 1 are read back.
 void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
                              GenInfo &info, bool grad = false)
 {
