@@ -160,7 +160,6 @@ class DescHolder:
     """A ls_spline_desc plus the arrays it points to (kept alive together)."""
 
     def __init__(self, table, name: Optional[str] = None, expansion: str = "sparse"):
-        from .exactpoly import monomials_upto  # noqa: F401  (table monomials are explicit)
         spl = table.spline
         lat = spl.lattice
         s = lat.dim
