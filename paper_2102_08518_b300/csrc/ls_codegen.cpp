@@ -19,6 +19,7 @@
 //     tensor-product splines use per-axis Horner weights and a nested
 //     contraction instead.
 #include <algorithm>
+#include <cctype>
 #include <cmath>
 #include <cstdio>
 #include <functional>
@@ -1544,9 +1545,8 @@ namespace {
 // column range of tensor memory, an mbarrier and an arrival counter (the
 // last of its warps to stage a tile issues the product), and runs
 // independently of the others.  Within a slot the tile loop is software
-// pipelined: the product of tile t - 1 runs while tile t is gathered, and
-// (up to 5 slots, or for small splines) the gathers of tile t are issued
-// before the results of tile t - 1 are read back.
+// pipelined: the gathers of tile t are issued before the results of tile
+// t - 1 are read back, so the product of t - 1 runs behind them.
 void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
                              GenInfo &info, bool grad = false)
 {
@@ -1663,17 +1663,12 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     }
     o << "  for (long long tile = (long long)blockIdx.x * " << S << " + slot; ; tile += (long long)gridDim.x * " << S
       << ") {\n";
-    // the tile's body: this tile's point and gathers (G), the previous tile's
-    // results (R), then this tile's staging and product.  Overlapped order
-    // G R: the gathers are in flight while R runs, at the cost of holding the
-    // gathered values and the products in registers together; plain order R G
-    // holds one set at a time.  A large spline at more than 5 slots takes the
-    // plain order (the overlapped one spills there; measured, BCC quintic on
-    // ray points: 6 slots plain 0.444 ms, 6 overlapped 0.520, 5 overlapped
-    // 0.481); otherwise the overlapped one (4 slots: 0.495 against 0.534 plain).
-    const bool overlap = S <= 5 || P.kp + P.n < 64;
-    const std::string head = o.str();
-    o.str("");
+    // chunked: past 5 slots a large spline reads the products back in 8-column
+    // pieces, each just before the polynomial's first use of it, so that the
+    // next tile's gathered values and all of the products are not live
+    // together (72-80 registers instead of 96 and more: 6 slots fit without
+    // spilling)
+    const bool chunked = S > 5 && P.kp + P.n >= 64;
     o << "    const bool have = tile * 128 < a.n;\n";
     o << "    const long long i = tile * 128 + lt;\n";
     o << "    int stt = 2;\n";
@@ -1697,8 +1692,6 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     if (grad && fold)
         for (int q = 0; q < D; ++q) o << "    tri" << q << " = ri" << q << "; tng" << q << " = ng" << q << ";\n";
     o << "    }\n";
-    const std::string blockG = o.str();
-    o.str("");
     // results of the previous tile
     o << "    if (pending) {\n";
     // each warp waits for the product on its own (lane 0 polls)
@@ -1709,26 +1702,66 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "      phase ^= 1u;\n";
     o << "      asm volatile(\"tcgen05.fence::after_thread_sync;\" ::: \"memory\");\n";
     for (int q = 0; q < N; ++q) o << "      unsigned td" << q << ";\n";
-    for (const auto &ch : pow2_chunks(N)) {
-        o << "      asm volatile(\"tcgen05.ld.sync.aligned.32x32b.x" << ch.second << ".b32 " << reglist(ch.second, 0)
-          << ", [%" << ch.second << "];\" : ";
-        for (int q = 0; q < ch.second; ++q) o << (q ? ", " : "") << "\"=r\"(td" << (ch.first + q) << ")";
-        o << " : \"r\"(tl + " << (DC + ch.first) << "u) : \"memory\");\n";
-    }
-    o << "      asm volatile(\"tcgen05.wait::ld.sync.aligned;\" ::: \"memory\");\n";
-    o << "      if (pst == 0) {\n";
-    for (int q = 0; q < D; ++q) o << "      const float a" << q << " = pa" << q << ";\n";
-    o << "      const int psi = ppsi; (void)psi;\n";
+    auto emit_ld = [&](std::ostream &os, int first, int cnt) {
+        os << "      asm volatile(\"tcgen05.ld.sync.aligned.32x32b.x" << cnt << ".b32 " << reglist(cnt, 0) << ", [%"
+           << cnt << "];\" : ";
+        for (int q = 0; q < cnt; ++q) os << (q ? ", " : "") << "\"=r\"(td" << (first + q) << ")";
+        os << " : \"r\"(tl + " << (DC + first) << "u) : \"memory\");\n";
+    };
     std::vector<std::vector<std::string>> fk;
-    for (size_t k = 0; k < K; ++k) {
-        std::map<I3, std::string> pre;
-        for (const auto &m : P.sup[k]) {
-            const std::string nm = "tA" + std::to_string(P.col[k].at(m));
-            o << "      const float " << nm << " = __uint_as_float(td" << P.col[k].at(m) << ")"
-              << ";\n";
-            pre[m] = nm;
+    if (!chunked) {
+        for (const auto &ch : pow2_chunks(N)) emit_ld(o, ch.first, ch.second);
+        o << "      asm volatile(\"tcgen05.wait::ld.sync.aligned;\" ::: \"memory\");\n";
+        o << "      if (pst == 0) {\n";
+        for (int q = 0; q < D; ++q) o << "      const float a" << q << " = pa" << q << ";\n";
+        o << "      const int psi = ppsi; (void)psi;\n";
+        for (size_t k = 0; k < K; ++k) {
+            std::map<I3, std::string> pre;
+            for (const auto &m : P.sup[k]) {
+                const std::string nm = "tA" + std::to_string(P.col[k].at(m));
+                o << "      const float " << nm << " = __uint_as_float(td" << P.col[k].at(m) << ")"
+                  << ";\n";
+                pre[m] = nm;
+            }
+            fk.push_back(emit_region_poly(e, t, (int)k, st.region_to_union[k], grad ? 1 : 0, &pre));
         }
-        fk.push_back(emit_region_poly(e, t, (int)k, st.region_to_union[k], grad ? 1 : 0, &pre));
+    } else {
+        // the polynomials for every lane (the loads are warp-collective), each
+        // 8-column piece loaded right before the first line that reads it
+        for (int q = 0; q < D; ++q) o << "      const float a" << q << " = pa" << q << ";\n";
+        o << "      const int psi = ppsi; (void)psi;\n";
+        const std::string before = o.str();
+        o.str("");
+        for (size_t k = 0; k < K; ++k) {
+            std::map<I3, std::string> pre;
+            for (const auto &m : P.sup[k]) pre[m] = "__uint_as_float(td" + std::to_string(P.col[k].at(m)) + ")";
+            fk.push_back(emit_region_poly(e, t, (int)k, st.region_to_union[k], grad ? 1 : 0, &pre));
+        }
+        const std::string poly = o.str();
+        o.str("");
+        o << before;
+        std::vector<bool> loaded(N / 8, false);
+        size_t pos = 0;
+        while (pos < poly.size()) {
+            size_t end = poly.find('\n', pos);
+            if (end == std::string::npos) end = poly.size() - 1;
+            const std::string line = poly.substr(pos, end - pos + 1);
+            bool any = false;
+            for (size_t f = line.find("(td"); f != std::string::npos; f = line.find("(td", f + 3)) {
+                size_t d = f + 3;
+                int col = 0;
+                while (d < line.size() && std::isdigit((unsigned char)line[d])) col = col * 10 + (line[d++] - '0');
+                if (d > f + 3 && !loaded[col / 8]) {
+                    emit_ld(o, col / 8 * 8, 8);
+                    loaded[col / 8] = true;
+                    any = true;
+                }
+            }
+            if (any) o << "      asm volatile(\"tcgen05.wait::ld.sync.aligned;\" ::: \"memory\");\n";
+            o << line;
+            pos = end + 1;
+        }
+        o << "      if (pst == 0) {\n";
     }
     // value and (reference-frame) gradient, the region picked by psi
     std::vector<std::string> out;
@@ -1759,9 +1792,6 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "      }\n";
     o << "      pending = false;\n";
     o << "    }\n";
-    const std::string blockR = o.str();
-    o.str("");
-    o << head << (overlap ? blockG + blockR : blockR + blockG);
     o << "    if (!have) break;\n";
     // split and stage this tile's coefficients (slot columns [0, KP) hi, [KP, 2 KP) lo).
     // With several reference regions the gathers cover their union: the sites

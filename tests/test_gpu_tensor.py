@@ -287,9 +287,9 @@ def test_tensor_explicit_slot_counts(slots, kind):
 
 @pytest.mark.parametrize("name", ["bcc_quintic", "fcc6"])
 def test_tensor_slot_count_and_tile_order_do_not_change_results(name):
-    """5 slots (gathers of the next tile in flight while the last one's
-    products are read back) and 6 slots (the large splines read back first)
-    do the same arithmetic per point: bitwise equal results."""
+    """5 slots (all products read back at once) and 6 slots (a large
+    spline's products read back in 8-column pieces as the polynomial needs
+    them) do the same arithmetic per point: bitwise equal results."""
     ext = (40, 36, 30)
     lat = workloads.SPLINE_LATTICE[name]
     coef = workloads.coef_uniform(lat, ext, seed=81)
