@@ -270,3 +270,31 @@ def test_tensor_fp16_form_source(name):
     assert 2.0 ** 14 <= np.abs(m16).max() < 2.0 ** 15
     assert np.max(np.abs(m16 / scale - m32) / np.maximum(np.abs(m32), 1e-30)) < 2.0 ** -20
     assert np.array_equal(m16 == 0, m32 == 0)
+
+
+def test_tensor_kernel_readback_and_union_zeroing_in_source():
+    """Generated-source checks of two tensor-core kernel details.
+    (1) Past 5 slots a large spline reads its 48 products back in 8-column
+    pieces, each with its own wait; at 5 slots all at once, with one wait.
+    (2) With two reference regions (FCC) the union sites outside the point's
+    region are zeroed before staging, in both forms; a single-region spline
+    has nothing to zero."""
+    import re
+
+    def eval_kernel(src, name):
+        i = src.index("ls_eval__" + name + "(")
+        return src[i:src.index("ls_eval_grad__", i)]
+
+    from paper_2102_08518_b300 import api
+    q6 = _tensor_source("bcc_quintic", tensor=6, tensor_kind=1)
+    q5 = _tensor_source("bcc_quintic", tensor=1, tensor_kind=1)
+    k6 = eval_kernel(q6, api.kernel_name("bcc_quintic", "f32", tensor=6, tensor_kind=1))
+    k5 = eval_kernel(q5, api.kernel_name("bcc_quintic", "f32", tensor=1, tensor_kind=1))
+    assert "__launch_bounds__(768, 1)" in q6 and "__launch_bounds__(640, 1)" in q5
+    assert k6.count("tcgen05.ld.sync.aligned.32x32b.x8.b32") == 6 and k6.count("tcgen05.wait::ld") == 6
+    assert k5.count("tcgen05.wait::ld") == 1
+    assert len(re.findall(r"if \(tpsi != \d\) tc\d+ = 0\.0f;", k5)) == 0
+    for kw in ({"tensor": 1}, {"tensor": 1, "tensor_kind": 1}):
+        f = _tensor_source("fcc6", **kw)
+        kf = eval_kernel(f, api.kernel_name("fcc6", "f32", **kw))
+        assert len(re.findall(r"if \(tpsi != \d\) tc\d+ = 0\.0f;", kf)) > 0
