@@ -2161,7 +2161,6 @@ void emit_adjoint_atomic(Emitter &e, const Table &t, const ls_variant &var, cons
                          AdjFlavour fl)
 {
     auto &o = e.o;
-    const int D = t.dim;
     // one scatter-add of value V at address variable AD
     auto add = [&](const std::string &ad, const std::string &v) {
         if (fl == ADJ_WARPAGG) return "ls_agg_add(a.dcoef, " + ad + ", " + v + ");";
@@ -2420,7 +2419,7 @@ std::string emit_runtime_horner(Emitter &e, const RefRegion &r, int D, const std
     return pe.horner(0, I3{0, 0, 0}, coef, sup);
 }
 
-void emit_adjoint_gather(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach,
+void emit_adjoint_gather(Emitter &e, const Table &t, const ls_variant &var, const Stencil & /*st*/, int reach,
                          const std::vector<I3> &doffs)
 {
     auto &o = e.o;
