@@ -125,18 +125,19 @@ def test_tensor_agrees_with_fma_kernel_on_many_points(name, kind):
 GRAD_TOL = 1e-5
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind,slots", [(0, 1), (1, 1), (1, 6)])
 @pytest.mark.parametrize("name", NAMES)
 @pytest.mark.parametrize("n", [1, 129, 3001])
-def test_tensor_value_gradient_matches_oracle(name, n, kind):
+def test_tensor_value_gradient_matches_oracle(name, n, kind, slots):
     """The value + gradient kernel of a tensor-core spline: the same product,
-    then the gradient's Horner forms mapped back through the fold."""
+    then the gradient's Horner forms mapped back through the fold (at 6
+    slots with the products read back in pieces as the forms need them)."""
     ext = EXT[name]
     lat = workloads.SPLINE_LATTICE[name]
     coef = workloads.coef_uniform(lat, ext, seed=31)
     lo, hi = workloads.bounding_box(lat, ext)
     pts = workloads.points_uniform(n, lo - 2.0, hi + 2.0, seed=n + 17)
-    vol = volume(name, ext, coef, layout="interleaved", tensor=1, tensor_kind=kind)
+    vol = volume(name, ext, coef, layout="interleaved", tensor=slots, tensor_kind=kind)
     val, grad = vol.eval_grad(torch.from_numpy(pts).cuda())
     vol.spline.status()
     spec = ORACLE_SPEC[name]().with_extent(ext)
