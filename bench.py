@@ -892,12 +892,13 @@ def run_reference(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--gpus", type=int, default=1, help="ranks (one GPU each; N > 1 under torchrun)")
+    ap.add_argument("--steps", type=int, default=200, help="timed steps")
+    ap.add_argument("--warmup", type=int, default=5, help="untimed warm-up steps (at least 3)")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"],
+                    help="reference: the FP64 oracle on the host cores, on a bounded sample of each step")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle's timing on the host")
+    ap.add_argument("--no-extras", action="store_true", help="skip the measurements beside the headline step")
     ap.add_argument("--layout", default=LAYOUT, choices=["auto", "coset", "interleaved", "bricked"],
                     help="coefficient layout of the step's volumes")
     ap.add_argument("--only", default=None, choices=PROFILE_CASES,
