@@ -208,6 +208,8 @@ typedef struct {
 const char *ls_status_str(ls_status s);
 /* Message of the last failing call on this thread ("" if none). */
 const char *ls_last_error(void);
+/* Layout version of the structs above (4: ls_variant ends with tensor_kind);
+ * bindings compare it with their own before any other call. */
 int32_t ls_abi_version(void);
 
 /* ---- splines ----------------------------------------------------------------- */

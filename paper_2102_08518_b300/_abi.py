@@ -131,6 +131,9 @@ class LsError(RuntimeError):
         self.status = status
 
 
+ABI_VERSION = 4          # ls_abi_version() of the library these struct layouts match
+
+
 def lib():
     """The loaded libls.so (built on first use if absent)."""
     global _lib
@@ -143,6 +146,10 @@ def lib():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
+        if L.ls_abi_version() != ABI_VERSION:
+            # the structs below would be read with another layout
+            raise RuntimeError(f"{LIB_PATH} has ABI version {L.ls_abi_version()}, these bindings {ABI_VERSION}: "
+                               "rebuild it (paper_2102_08518_b300.build.build())")
         _lib = L
     return _lib
 
