@@ -164,6 +164,15 @@ def oracle_leg(coef, pts_sets):
 # helpers
 # ---------------------------------------------------------------------------
 
+def link_schedule_ms(h2d_bytes, d2h_bytes, r_in, r_out, r_dup):
+    """Shortest time (ms) for h2d_bytes in and d2h_bytes out over a link that
+    moves r_in / r_out GB/s one way alone and r_dup GB/s each way when both
+    run: both directions together while the smaller flow lasts, then the
+    rest of the larger one alone."""
+    lo = min(h2d_bytes, d2h_bytes)
+    return (lo / r_dup + (h2d_bytes - lo) / r_in + (d2h_bytes - lo) / r_out) / 1e6
+
+
 def link_bound(torch, host_buf, dev_buf, h2d_bytes, d2h_bytes, step_ms):
     """The host link's rates measured with the step's own pinned buffers
     (host-to-device alone, device-to-host alone, both at once) and the
@@ -193,9 +202,7 @@ def link_bound(torch, host_buf, dev_buf, h2d_bytes, d2h_bytes, step_ms):
     r_in = nbytes / time_ms(torch, h2d, reps=5, warm=1) / 1e6       # GB/s
     r_out = nbytes / time_ms(torch, d2h, reps=5, warm=1) / 1e6
     r_dup = nbytes / time_ms(torch, both, reps=5, warm=1) / 1e6      # each way
-    lo = min(h2d_bytes, d2h_bytes)
-    rest_in, rest_out = h2d_bytes - lo, d2h_bytes - lo
-    bound_ms = lo / r_dup / 1e6 + rest_in / r_in / 1e6 + rest_out / r_out / 1e6
+    bound_ms = link_schedule_ms(h2d_bytes, d2h_bytes, r_in, r_out, r_dup)
     return {"h2d_gbs": round(r_in, 1), "d2h_gbs": round(r_out, 1), "duplex_each_way_gbs": round(r_dup, 1),
             "bound_ms": round(bound_ms, 3), "step_ms": round(step_ms, 3), "frac": round(bound_ms / step_ms, 3),
             "note": "pinned copies of the step's 201 MB point buffer; bound = the step's bytes at these rates"}

@@ -102,3 +102,19 @@ def test_tensor_shape_of_the_fp16_form():
         src = open(os.path.join(cache, files[-1])).read()
         m = re.search(r"unsigned short ls_tcB_\w+\[(\d+)\]", src)
         assert int(m.group(1)) == 2 * N * K and K % 16 == 0, name
+
+
+def test_link_schedule_of_the_end_to_end_step():
+    """The host-link bound of the bench's end-to-end step: both directions at
+    the duplex rate while the smaller flow lasts, the rest alone; with one
+    flow empty it is that flow at its own rate, and with equal flows both
+    finish together at the duplex rate."""
+    import bench
+    GB = 1e9
+    assert bench.link_schedule_ms(10 * GB, 0, 50.0, 60.0, 30.0) == pytest.approx(200.0)
+    assert bench.link_schedule_ms(0, 6 * GB, 50.0, 60.0, 30.0) == pytest.approx(100.0)
+    assert bench.link_schedule_ms(3 * GB, 3 * GB, 50.0, 60.0, 30.0) == pytest.approx(100.0)
+    # the step: 402 MB in, 268 MB out at the measured 55.3 / 57.2 / 37.4 GB/s
+    ms = bench.link_schedule_ms(402653184, 268435456, 55.3, 57.2, 37.4)
+    assert ms == pytest.approx(268435456 / 37.4e6 + (402653184 - 268435456) / 55.3e6)
+    assert 9.5 < ms < 9.7
