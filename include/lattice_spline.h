@@ -202,13 +202,21 @@ typedef struct {
                                           (the rounded remainder), the scale undone on the results
                                           (half the tensor-memory columns per tile, so more tiles in
                                           flight).  Other values: LS_ERR_INVALID_ARG at create */
+    int32_t plain_transform;           /* 1: the FMA kernels form each monomial coefficient A_a as the
+                                          direct sum over the region's sites (one multiply-add per
+                                          nonzero of the table); 0 (default): the generator factors the
+                                          transform into sums and differences of site pairs (also of
+                                          earlier sums) followed by a sparser table, wherever two rows
+                                          of the table agree up to sign on enough monomials (the
+                                          spline's symmetries make many do): the same A_a in fewer
+                                          operations (BCC quintic 377 instead of 1016) */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */
 const char *ls_status_str(ls_status s);
 /* Message of the last failing call on this thread ("" if none). */
 const char *ls_last_error(void);
-/* Layout version of the structs above (4: ls_variant ends with tensor_kind);
+/* Layout version of the structs above (5: ls_variant ends with plain_transform);
  * bindings compare it with their own before any other call. */
 int32_t ls_abi_version(void);
 

@@ -65,7 +65,7 @@ def _ptr(t: Optional[torch.Tensor]):
 def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_blocks: int = 0, group: int = 0,
                 depth: int = 0, pts_per_thread: int = 1, blocks_per_sm: int = 0, expansion: str = "sparse",
                 brick: int = 0, pipeline: int = 0, producers: int = 0, stage: int = 0, tensor: int = 0,
-                tensor_kind: int = 0) -> str:
+                tensor_kind: int = 0, plain_transform: int = 0) -> str:
     """The name tag of a generated kernel variant (blocks_per_sm only sizes the
     grid, so it shares the compiled kernel)."""
     return f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + ("_br" if branchy else "") + \
@@ -73,7 +73,7 @@ def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_b
         (f"_t{pts_per_thread}" if pts_per_thread > 1 else "") + ("_ec" if expansion == "centroid" else "") + \
         ("_bk" if brick else "") + ("_pp" if pipeline else "") + (f"_ws{producers}" if producers else "") + \
         (f"_st{stage}" if stage else "") + (("_tc" + (str(tensor) if tensor > 1 else "")) if tensor else "") + \
-        ("h" if tensor and tensor_kind else "")
+        ("h" if tensor and tensor_kind else "") + ("_pt" if plain_transform else "")
 
 
 class Spline:
@@ -83,7 +83,7 @@ class Spline:
                  min_blocks: int = 0, group: int = 0, depth: int = 0, pts_per_thread: int = 1,
                  blocks_per_sm: int = 0, expansion: str = "sparse", brick: int = 0, pipeline: int = 0,
                  producers: int = 0, stage: int = 0, tensor: int = 0, tensor_kind: int = 0,
-                 kernel_name: Optional[str] = None):
+                 plain_transform: int = 0, kernel_name: Optional[str] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("lattice spline kernels need a CUDA device")
         self.name = name
@@ -94,7 +94,8 @@ class Spline:
         self.scale = self.table.spline.lattice.scale
         kname = kernel_name or globals()["kernel_name"](name, dtype, block, branchy, min_blocks, group, depth,
                                                          pts_per_thread, blocks_per_sm, expansion, brick, pipeline,
-                                                         producers, stage, tensor, tensor_kind)
+                                                         producers, stage, tensor, tensor_kind,
+                                                         plain_transform)
         self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
                         "depth": depth, "pts_per_thread": pts_per_thread, "blocks_per_sm": blocks_per_sm,
                         "expansion": expansion}
@@ -110,11 +111,14 @@ class Spline:
             self.variant["tensor"] = tensor
         if tensor_kind:
             self.variant["tensor_kind"] = tensor_kind
+        if plain_transform:
+            self.variant["plain_transform"] = 1
         self.kernel_name = kname
         self._desc = _abi.DescHolder(self.table, kname, expansion)
         var = _abi.variant(block=block, pts_per_thread=pts_per_thread, branchy=branchy, min_blocks=min_blocks,
                            group=group, depth=depth, blocks_per_sm=blocks_per_sm, brick=brick, pipeline=pipeline,
-                           producers=producers, stage=stage, tensor=tensor, tensor_kind=tensor_kind)
+                           producers=producers, stage=stage, tensor=tensor, tensor_kind=tensor_kind,
+                           plain_transform=plain_transform)
         h = ctypes.c_void_p()
         torch.cuda.init()
         _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),

@@ -242,7 +242,7 @@ ls_status get_kernel(ls_spline_s *s, const char *what, cudaKernel_t &k, int &per
 
 ls_variant default_variant(const ls_variant *v)
 {
-    ls_variant r{256, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    ls_variant r{256, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (v) {
         if (v->block > 0) r.block = v->block;
         if (v->pts_per_thread > 0) r.pts_per_thread = v->pts_per_thread > 64 ? 64 : v->pts_per_thread;
@@ -257,6 +257,7 @@ ls_variant default_variant(const ls_variant *v)
         r.stage = v->stage > 0 ? v->stage : 0;
         r.tensor = v->tensor > 0 ? v->tensor : 0;
         r.tensor_kind = v->tensor_kind == 1 ? 1 : 0;
+        r.plain_transform = v->plain_transform ? 1 : 0;
     }
     return r;
 }
@@ -289,7 +290,7 @@ const char *ls_status_str(ls_status s)
 
 const char *ls_last_error(void) { return g_err.c_str(); }
 
-int32_t ls_abi_version(void) { return 4; }
+int32_t ls_abi_version(void) { return 5; }
 
 ls_status ls_spline_precompile(const ls_spline_desc *desc, ls_dtype dt, const ls_variant *variant)
 {

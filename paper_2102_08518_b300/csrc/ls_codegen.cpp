@@ -47,6 +47,7 @@ struct Emitter {
     int fma = 0;
     std::string ld = "ls_ld_f32";     // coefficient loader of the spline being emitted
     bool brick = false;               // bricked coefficient layout (else linear)
+    bool sym = true;                  // factored coefficient transform (butterflies + sparser M)
     std::string fresh(const char *p) { return std::string(p) + std::to_string(tmp++); }
 };
 
@@ -592,6 +593,112 @@ std::set<I3> monomial_support(const RefRegion &r, const std::vector<int> &umap,
     return sup;
 }
 
+// ---------------------------------------------------------------------------
+// Factored coefficient transform.
+//
+// The coefficient form needs A = M^T c (A_a = sum_j M[j][a] c_j), one
+// multiply-add per nonzero of M.  The columns of M are far from independent:
+// the box spline's symmetries (w_j(sigma u) = w_pi(j)(u) for signed
+// permutations sigma that preserve the polynomial piece, Sec. 3) make many
+// pairs of rows equal or opposite on many monomials.  A butterfly on two
+// variables v, w (p = v + w, q = v - w) turns their rows r_v, r_w into
+// (r_v + r_w) / 2 and (r_v - r_w) / 2, which are zero wherever r_w = +-r_v.
+// Applied greedily (the pair with the largest saving each time, also to the
+// outputs of earlier butterflies) this gives A = M'^T (B c), with B a few
+// dozen additions and M' much sparser: the same A_a in fewer operations
+// (BCC quintic: 377 instead of 1016).  Every intermediate is a sum or
+// difference of at most 2^depth coefficients with rows scaled by 2^-depth, so
+// the rounding error stays that of the direct sums.
+// ---------------------------------------------------------------------------
+struct FactoredTransform {
+    struct Op { int v, w, p, q; };            // p = v + w, q = v - w (-1: not formed)
+    std::vector<std::vector<double>> rows;    // per variable: coefficients over the monomials
+    std::vector<Op> ops;
+    std::vector<int> live;                    // variables the final dot products read
+    int cost = 0;                             // FP32 operations: additions + nonzeros of M'
+};
+
+FactoredTransform factor_transform(const RefRegion &r)
+{
+    FactoredTransform f;
+    const size_t nj = r.sites.size(), na = r.mono.size();
+    double big = 0.0;
+    for (double c : r.coef) big = std::max(big, std::fabs(c));
+    const double tiny = 1e-12 * big;
+    auto nnz = [&](const std::vector<double> &v) {
+        int n = 0;
+        for (double x : v) n += x != 0.0;
+        return n;
+    };
+    for (size_t j = 0; j < nj; ++j) {
+        f.rows.emplace_back(r.coef.begin() + (long)(j * na), r.coef.begin() + (long)((j + 1) * na));
+        if (nnz(f.rows.back())) f.live.push_back((int)j);
+    }
+    std::vector<double> p(na), q(na), bp(na), bq(na);
+    for (;;) {
+        int best = 0, bi = -1, bk = -1;
+        for (size_t i = 0; i < f.live.size(); ++i)
+            for (size_t k = i + 1; k < f.live.size(); ++k) {
+                const auto &rv = f.rows[(size_t)f.live[i]], &rw = f.rows[(size_t)f.live[k]];
+                int before = 0, np = 0, nq = 0;
+                for (size_t a = 0; a < na; ++a) {
+                    before += (rv[a] != 0.0) + (rw[a] != 0.0);
+                    np += std::fabs(rv[a] + rw[a]) > tiny;
+                    nq += std::fabs(rv[a] - rw[a]) > tiny;
+                }
+                const int gain = before - np - nq - (np > 0) - (nq > 0);
+                if (gain > best) best = gain, bi = (int)i, bk = (int)k;
+            }
+        if (best <= 0) break;
+        const int v = f.live[(size_t)bi], w = f.live[(size_t)bk];
+        for (size_t a = 0; a < na; ++a) {
+            const double x = f.rows[(size_t)v][a], y = f.rows[(size_t)w][a];
+            bp[a] = std::fabs(x + y) > tiny ? 0.5 * (x + y) : 0.0;
+            bq[a] = std::fabs(x - y) > tiny ? 0.5 * (x - y) : 0.0;
+        }
+        FactoredTransform::Op op{v, w, -1, -1};
+        f.live.erase(f.live.begin() + bk);
+        f.live.erase(f.live.begin() + bi);
+        if (nnz(bp)) op.p = (int)f.rows.size(), f.rows.push_back(bp), f.live.push_back(op.p), f.cost++;
+        if (nnz(bq)) op.q = (int)f.rows.size(), f.rows.push_back(bq), f.live.push_back(op.q), f.cost++;
+        f.ops.push_back(op);
+    }
+    for (int v : f.live) f.cost += nnz(f.rows[(size_t)v]);
+    return f;
+}
+
+// Emits the butterflies and every nonzero A_a of the region; fills pe.aname
+// (the names the Horner forms read).
+void emit_factored_transform(Emitter &e, const RefRegion &r, const std::vector<int> &umap,
+                             const FactoredTransform &f, PolyEmit &pe)
+{
+    auto &o = e.o;
+    const size_t nj = r.sites.size(), na = r.mono.size();
+    auto vname = [&](int v) {
+        return (size_t)v < nj ? "c" + std::to_string(umap[(size_t)v]) : pe.pre + "t" + std::to_string(v);
+    };
+    for (const auto &op : f.ops) {
+        if (op.p >= 0) o << "    const float " << vname(op.p) << " = " << vname(op.v) << " + " << vname(op.w) << ";\n";
+        if (op.q >= 0) o << "    const float " << vname(op.q) << " = " << vname(op.v) << " - " << vname(op.w) << ";\n";
+        e.fma += (op.p >= 0) + (op.q >= 0);
+    }
+    for (size_t a = 0; a < na; ++a) {
+        std::string acc;
+        for (int v : f.live) {
+            const double c = f.rows[(size_t)v][a];
+            if (c == 0.0) continue;
+            acc = acc.empty() ? flit(c) + " * " + vname(v) : "fmaf(" + flit(c) + ", " + vname(v) + ", " + acc + ")";
+            e.fma++;
+        }
+        if (acc.empty()) continue;
+        const I3 &m = r.mono[a];
+        const std::string nm = pe.pre + "A" + std::to_string(m[0]) + "_" + std::to_string(m[1]) + "_" +
+                               std::to_string(m[2]);
+        o << "    const float " << nm << " = " << acc << ";\n";
+        pe.aname[m] = nm;
+    }
+}
+
 // Emits value (and optionally gradient in reference coordinates) for region k.
 // Returns names {f, g0, g1, g2}.
 // Hessian entries in the order (0,0) (1,1) (2,2) (0,1) (0,2) (1,2) in 3D, (0,0) (1,1) (0,1) in 2D.
@@ -612,6 +719,10 @@ std::vector<std::string> emit_region_poly(Emitter &e, const Table &t, int k, con
         e.o << "    const float " << pe.uvar[i] << " = a" << i << " - " << flit(r.center[i]) << ";\n";
     }
     std::set<I3> sup = monomial_support(r, umap, pe.terms);
+    if (!pre && e.sym) {
+        const FactoredTransform ft = factor_transform(r);
+        if (!ft.ops.empty()) emit_factored_transform(e, r, umap, ft, pe);
+    }
     // emit all A_a in a fixed order first (shared by value and gradient)
     for (const auto &m : sup) pe.A(m);
     auto coefA = [&](const I3 &m) -> std::string {
@@ -2679,6 +2790,7 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
     Emitter e;
     e.ld = loader_name(dt);
     e.brick = var.brick != 0;
+    e.sym = !var.plain_transform;
     emit_prologue(e);
     Stencil st = union_stencil(t);
     int reach = 0;

@@ -129,3 +129,29 @@ def tensor_shape(table, expansion: str = "sparse", kstep: int = 8):
     K = (len(union) + kstep - 1) // kstep * kstep
     N = max(16, (ncol + 15) // 16 * 16)
     return K, N, nnz
+
+
+def case_roofline(fma_per_point: int, coef_bytes_per_point: float, n: int, ms: float, sms: int, sm_mhz: float,
+                  l2_gbs: float, hbm_gbs: float, stream_bytes_per_point: float = 16.0) -> dict:
+    """Roofline of one evaluation launch over n points taking ms milliseconds.
+
+    Two roofs bound it: the FP32 FMA pipe for the generated kernel's
+    multiply-adds (fma_per_point; SMs x 128 FMA lanes per clock at the observed
+    SM clock), and the gathers: the point's coefficient bytes at the rate the
+    level they come from (L2 for a resident volume) delivers them, plus the
+    point stream (coordinates in, value out) at the HBM rate.  The binding roof
+    is the slower one; frac = its time / the measured time."""
+    t_fma = fma_per_point * n / (sms * 128.0 * sm_mhz * 1e6) * 1e3
+    t_gather = (coef_bytes_per_point * n / (l2_gbs * 1e9) + stream_bytes_per_point * n / (hbm_gbs * 1e9)) * 1e3
+    alu = t_fma >= t_gather
+    t_roof = t_fma if alu else t_gather
+    out = {"bound": "alu" if alu else "l2", "ms": round(ms, 4), "t_fma_ms": round(t_fma, 4),
+           "t_gather_ms": round(t_gather, 4), "frac": round(t_roof / ms, 4)}
+    if alu:
+        out.update(unit="TFLOP/s", achieved=round(2.0 * fma_per_point * n / (ms * 1e-3) / 1e12, 2),
+                   peak=round(2.0 * sms * 128.0 * sm_mhz * 1e6 / 1e12, 2))
+    else:
+        per_pt = coef_bytes_per_point + stream_bytes_per_point
+        out.update(unit="GB/s", achieved=round(per_pt * n / (ms * 1e-3) / 1e9, 1),
+                   peak=round(per_pt * n / (t_gather * 1e-3) / 1e9, 1))
+    return out

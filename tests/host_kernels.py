@@ -1,0 +1,123 @@
+"""Generated point functions compiled for the host (test helper only).
+
+The generator emits one CUDA C++ point function per spline and variant
+(ls_eval_pt__*, ls_eval_grad_pt__*, ls_eval_hess_pt__*).  Their arithmetic is
+plain C++ (fmaf, rintf, selects, integer address arithmetic) around a few
+device intrinsics, so with host stand-ins for those intrinsics the same text
+compiles with g++ and runs on the CPU.  The tests use this to check the
+generator's arithmetic and addressing (every layout, every variant that keeps
+the point function) against the FP64 oracle without a GPU.  The GPU parity
+tests still check the compiled kernels themselves.  Not part of the product.
+"""
+import ctypes
+import hashlib
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+
+from paper_2102_08518_b300 import _abi, api
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CACHE = os.path.join(ROOT, "paper_2102_08518_b300", "kcache")
+BUILD = os.path.join(tempfile.gettempdir(), "ls_host_kernels")
+
+SHIM = r"""
+#include <math.h>
+#include <cstring>
+#include <cstddef>
+#define __device__
+#define __forceinline__ inline
+#define __restrict__
+template <class T> static inline T __ldg(const T* p) { return *p; }
+static inline float __int_as_float(int v) { float f; std::memcpy(&f, &v, 4); return f; }
+static inline float __uint_as_float(unsigned v) { float f; std::memcpy(&f, &v, 4); return f; }
+static inline int __float_as_int(float v) { int i; std::memcpy(&i, &v, 4); return i; }
+static inline unsigned __float_as_uint(float v) { unsigned i; std::memcpy(&i, &v, 4); return i; }
+static inline int __float2int_rz(float v) { return v != v ? 0 : (int)v; }
+
+"""
+
+
+def generated_source(name: str, dtype: str = "f32", expansion: str = "sparse", **var) -> str:
+    """Source of the kernels of spline `name` with variant `var`, generated
+    and compiled into the kernel cache by ls_spline_precompile (no device)."""
+    kn = api.kernel_name(name, dtype, expansion=expansion, **var)
+    h = _abi.DescHolder(api.table(name), kn, expansion)
+    rc = _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), api.DTYPES[dtype], ctypes.byref(_abi.variant(**var)))
+    assert rc == 0, _abi.lib().ls_last_error()
+    files = sorted((f for f in os.listdir(CACHE) if re.fullmatch(f"ls_{kn}_{dtype}_[0-9a-f]+\\.cu", f)),
+                   key=lambda f: os.path.getmtime(os.path.join(CACHE, f)))
+    with open(os.path.join(CACHE, files[-1])) as f:
+        return f.read()
+
+
+def _function(src: str, fname: str) -> str:
+    i = src.index("static __device__ __forceinline__ void " + fname + "(")
+    j = src.index("\n}\n", i)
+    return src[i:j + 3]
+
+
+class HostKernels:
+    """The value, value + gradient and value + gradient + Hessian point
+    functions of one generated spline variant, built for the host."""
+
+    def __init__(self, name: str, dtype: str = "f32", expansion: str = "sparse", **var):
+        src = generated_source(name, dtype, expansion, **var)
+        tag = api.kernel_name(name, dtype, expansion=expansion, **var)
+        lines = [ln for ln in src.splitlines() if ln.startswith(("typedef", "struct LsEvalArgs", "#define LS_CSWAP"))]
+        loader = {"f32": "ls_ld_f32", "bf16": "ls_ld_bf16", "f16": "ls_ld_f16"}[dtype]
+        ld = [ln for ln in src.splitlines() if ln.startswith("static __device__ __forceinline__ float " + loader + "(")]
+        body = [_function(src, f"ls_{w}_pt__{tag}") for w in ("eval", "eval_grad", "eval_hess")]
+        drivers = "".join(
+            f'extern "C" void host_{w}(const float* pts, long long n, float* out, float* grad, float* hess,'
+            f' const void* coef, int e0, int e1, int e2, int cs, int cu) {{\n'
+            f'  LsEvalArgs a; std::memset(&a, 0, sizeof a); a.pts = pts; a.out = out; a.grad = grad; a.hess = hess;'
+            f' a.coef = coef; a.n = n; a.e0 = e0; a.e1 = e1; a.e2 = e2; a.cstride = cs; a.cunit = cu;\n'
+            f'  for (long long i = 0; i < n; ++i) ls_{w}_pt__{tag}(a, i);\n}}\n'
+            for w in ("eval", "eval_grad", "eval_hess"))
+        code = SHIM + "\n".join(lines + ld) + "\n" + "\n".join(body) + drivers
+        if dtype == "f16":
+            code = code.replace('asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(h));', "f = (float)(_Float16&)h;")
+        os.makedirs(BUILD, exist_ok=True)
+        key = hashlib.sha256(code.encode()).hexdigest()[:16]
+        so = os.path.join(BUILD, f"{tag}_{key}.so")
+        if not os.path.exists(so):
+            cpp = so[:-3] + ".cpp"
+            with open(cpp, "w") as f:
+                f.write(code)
+            tmp = so + f".tmp{os.getpid()}"
+            subprocess.run(["g++", "-O1", "-ffp-contract=off", "-shared", "-fPIC", "-w", "-o", tmp, cpp], check=True)
+            os.replace(tmp, so)
+        self.lib = ctypes.CDLL(so)
+        self.dim = api.table(name).spline.lattice.dim
+
+    def _call(self, what, pts, coef, ext, layout, n_cosets, need_grad=False, need_hess=False):
+        pts = np.ascontiguousarray(pts, dtype=np.float32)
+        n = len(pts)
+        D = self.dim
+        out = np.zeros(n, np.float32)
+        grad = np.zeros(n * D, np.float32) if need_grad else None
+        nh = 6 if D == 3 else 3
+        hess = np.zeros(n * nh, np.float32) if need_hess else None
+        e = list(ext) + [1] * (3 - len(ext))
+        P = int(np.prod(ext))
+        cs, cu = {"coset": (P, 1), "interleaved": (1, n_cosets), "bricked": (1, n_cosets)}[layout]
+        coef = np.ascontiguousarray(coef)
+        ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+        fn = getattr(self.lib, "host_" + what)
+        fn.argtypes = [ctypes.c_void_p, ctypes.c_longlong] + [ctypes.c_void_p] * 4 + [ctypes.c_int] * 5
+        fn(ptr(pts), n, ptr(out), ptr(grad), ptr(hess), ptr(coef), e[0], e[1], e[2], cs, cu)
+        return out, (grad.reshape(n, D) if need_grad else None), (hess.reshape(n, nh) if need_hess else None)
+
+    def eval(self, pts, coef, ext, layout="coset", n_cosets=1):
+        return self._call("eval", pts, coef, ext, layout, n_cosets)[0]
+
+    def eval_grad(self, pts, coef, ext, layout="coset", n_cosets=1):
+        f, g, _ = self._call("eval_grad", pts, coef, ext, layout, n_cosets, need_grad=True)
+        return f, g
+
+    def eval_hess(self, pts, coef, ext, layout="coset", n_cosets=1):
+        return self._call("eval_hess", pts, coef, ext, layout, n_cosets, need_grad=True, need_hess=True)
