@@ -279,16 +279,17 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2102_08518_b300.api import (Spline, Volume, autotune, autotune_record, eval_host_multi, probe_gather,
-                                           relayout, table, TUNE_CANDIDATES_SMALL, _tune_key as tune_key)
-    from paper_2102_08518_b300.roofline import case_roofline, distinct_sectors_per_point
+    from paper_2102_08518_b300.api import (LAYOUT_BRICK, Spline, Volume, autotune, autotune_record, eval_host_multi,
+                                           probe_gather, relayout, table, TUNE_CANDIDATES_SMALL,
+                                           _tune_key as tune_key)
+    from paper_2102_08518_b300.roofline import case_roofline, distinct_sectors_per_point, shift_masks
 
     coef_np, pts_np = make_inputs(seed_offset=rank)
     dev = torch.device("cuda", local)
     coef_cm = torch.from_numpy(coef_np).to(dev)              # one array per coset
     # the step's coefficient layouts (relayout once, untimed): with "auto" the
     # volume is held interleaved and bricked, and each case reads the faster one
-    layouts = ("interleaved", "bricked") if LAYOUT == "auto" else (LAYOUT,)
+    layouts = ("interleaved", "bricked", "bricked_shifted") if LAYOUT == "auto" else (LAYOUT,)
     coefs = {lay: coef_cm if lay == "coset" else relayout(coef_cm, 2, EXT, to=lay) for lay in layouts}
     pts = {k: torch.from_numpy(v).to(dev) for k, v in pts_np.items()}
     outs = {k: torch.empty(v.shape[0], device=dev) for k, v in pts.items()}
@@ -366,8 +367,10 @@ def run_gpu(args):
     probe_gloads = (1 << 22) * 32 / (probe_ms * 1e-3) / 1e9
     peak_l2 = probe_gloads * 32.0                      # GB/s of 32-byte sectors
     sample = {ps: v[np.random.default_rng(7).choice(len(v), 1 << 14, replace=False)] for ps, v in pts_np.items()}
-    sectors = {(sp, ps): distinct_sectors_per_point(table(sp), EXT, sample["uniform"], layout=case_layout[(sp, ps)])
-               for sp, ps in CASES}
+    sectors = {(sp, ps): distinct_sectors_per_point(
+        table(sp), EXT, sample["uniform"], layout=case_layout[(sp, ps)],
+        masks=shift_masks(tuned[(sp, ps)].source()) if case_layout[(sp, ps)] == "bricked_shifted" else None)
+        for sp, ps in CASES}
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     max_mhz = clocks.get("sm_max_mhz") or 2032.0
@@ -458,7 +461,8 @@ def run_gpu(args):
         # its results against the FMA kernel's on the same points and volume
         # (both within 2e-6 ||c||_inf of the FP64 oracle in the parity tests)
         lay = case_layout[(sp, ps)]
-        fma_vol = Volume(Spline(sp, "f32", **({"brick": 1} if lay == "bricked" else {})), EXT, coefs[lay], layout=lay)
+        fma_vol = Volume(Spline(sp, "f32", **({"brick": LAYOUT_BRICK[lay]} if LAYOUT_BRICK[lay] else {})), EXT,
+                         coefs[lay], layout=lay)
         f_ref = fma_vol.eval(pts[ps])
         f_tc = case_vols[(sp, ps)].eval(pts[ps])
         err_tc = float((f_tc - f_ref).abs().max()) / float(coef_cm.abs().max())
@@ -685,7 +689,7 @@ def extra_batched(torch, dev, vols, pts, outs):
     for it in recipe:
         lat = workloads.SPLINE_LATTICE[it.spline]
         ncos = len(workloads.LATTICES[lat][2])
-        c = workloads.coef_uniform_torch(lat, it.ext, seed=it.seed)
+        c = torch.from_numpy(workloads.coef_uniform(lat, it.ext, seed=it.seed)).to(dev)
         lays.append("interleaved" if ncos > 1 else "coset")
         coefs.append(relayout(c, ncos, it.ext, to="interleaved") if ncos > 1 else c)
         lo, hi = workloads.inner_box(it.spline, it.ext)
@@ -693,6 +697,15 @@ def extra_batched(torch, dev, vols, pts, outs):
         outl.append(torch.empty(it.n_points, device=dev))
         exts.append(it.ext)
     res = {"workload": f"64 volumes, {total} points, edges {{32..256}}, 4 spline types", "points": total}
+    golden = None
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "batched_oracle_sample.json")) as f:
+            golden = json.load(f)
+        if len(golden["volumes"]) != len(recipe) or any(g["seed"] != it.seed for g, it in zip(golden["volumes"],
+                                                                                            recipe)):
+            golden = None
+    except (OSError, ValueError, KeyError):
+        golden = None
     # plain FP32: one launch per volume
     sp32 = {n: Spline(n, "f32") for n in set(it.spline for it in recipe)}
     v32 = [Volume(sp32[it.spline], e, c, layout=l) for it, e, c, l in zip(recipe, exts, coefs, lays)]
@@ -720,6 +733,30 @@ def extra_batched(torch, dev, vols, pts, outs):
         res[dt] = {"graph_gpoints_s": round(total / tg / 1e6, 3), "ms": round(tg, 3), "tile": info["tile"],
                    "items": info["n_items"], "max_abs_err_vs_f32_storage": round(err, 7),
                    "storage_bound_u_cmax": 2.0 ** -8 if dt == "bf16" else 2.0 ** -11}
+        # error against the FP64 oracle per volume: the same batched kernel on the
+        # seeded sample points whose oracle values tests/golden holds, for the
+        # rounded coefficients (the kernel's own error) and the FP32 ones (+ storage)
+        if golden is not None:
+            sp_pts = [torch.from_numpy(workloads.points_uniform(
+                golden["sample_per_volume"], *workloads.inner_box(it.spline, it.ext), seed=it.seed + 7)).to(dev)
+                for it in recipe]
+            sp_out = [torch.empty(p.shape[0], device=dev) for p in sp_pts]
+            splan = Plan(vd, sp_pts, sp_out, tile=info["tile"])
+            splan.launch()
+            splan.status()
+            torch.cuda.synchronize()
+            e_rnd, e_f32 = [], []
+            for o, g in zip(sp_out, golden["volumes"]):
+                got = o.double().cpu().numpy()
+                e_rnd.append(float(np.max(np.abs(got - np.asarray(g[dt])))) / g["cmax"])
+                e_f32.append(float(np.max(np.abs(got - np.asarray(g["f32"])))) / g["cmax"])
+            res[dt]["oracle_err_over_cmax_per_volume"] = {
+                "rounded_coefficients": [float(f"{x:.3g}") for x in e_rnd],
+                "fp32_coefficients": [float(f"{x:.3g}") for x in e_f32],
+                "max_rounded": float(f"{max(e_rnd):.3g}"), "max_fp32": float(f"{max(e_f32):.3g}"),
+                "bound_rounded": 2e-6, "bound_fp32": (2.0 ** -8 if dt == "bf16" else 2.0 ** -11) + 2e-6,
+                "sample": f"{golden['sample_per_volume']} seeded points per volume (tests/golden)"}
+            del splan
         del plan, vd, cd
     return res
 
@@ -959,7 +996,7 @@ def main():
                     help="reference: the FP64 oracle on the host cores, on a bounded sample of each step")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle's timing on the host")
     ap.add_argument("--no-extras", action="store_true", help="skip the measurements beside the headline step")
-    ap.add_argument("--layout", default=LAYOUT, choices=["auto", "coset", "interleaved", "bricked"],
+    ap.add_argument("--layout", default=LAYOUT, choices=["auto", "coset", "interleaved", "bricked", "bricked_shifted"],
                     help="coefficient layout of the step's volumes")
     ap.add_argument("--only", default=None, choices=PROFILE_CASES,
                     help="run one small case for a profiler instead of the benchmark")

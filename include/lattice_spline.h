@@ -74,8 +74,26 @@ typedef enum { LS_F32 = 0, LS_BF16 = 1, LS_F16 = 2, LS_F64 = 3 } ls_dtype;
  *                           cosets and a 128-byte line two bricks, so a compact
  *                           stencil touches fewer sectors and lines.  Needs even
  *                           extents and a spline created with ls_variant.brick = 1.
+ *   LS_LAYOUT_BRICKED_SHIFTED: four bricked copies (3D, even extents): copy
+ *                           c = s_0 + 2 s_1 (s in {0,1}^2) stores grid index i at
+ *                           (i_0 + s_0, i_1 + s_1, i_2) of a bricked array over
+ *                           extents (ext_0 + 2, ext_1 + 2, ext_2), element
+ *                           c * Q + that array's bricked index, Q = C (ext_0 + 2)
+ *                           (ext_1 + 2) ext_2; the padding is zero.  Each point's
+ *                           gathers read the copy whose brick boundaries cut its
+ *                           stencil into the fewest 32-byte sectors (a rule the
+ *                           generator derives from the table; BCC quintic: 10.0
+ *                           sectors per point instead of 11.3).  Read-only: the
+ *                           evaluation kernels (value, gradient, Hessian, batched)
+ *                           take it, the adjoint and the fit do not.  Needs a
+ *                           spline created with ls_variant.brick = 2.
  */
-typedef enum { LS_LAYOUT_COSET_MAJOR = 0, LS_LAYOUT_INTERLEAVED = 1, LS_LAYOUT_BRICKED = 2 } ls_layout;
+typedef enum {
+    LS_LAYOUT_COSET_MAJOR = 0,
+    LS_LAYOUT_INTERLEAVED = 1,
+    LS_LAYOUT_BRICKED = 2,
+    LS_LAYOUT_BRICKED_SHIFTED = 3
+} ls_layout;
 
 typedef enum {
     LS_ROE_PARALLELEPIPED = 0, /* k = floor(x) on the storage grid (Cartesian, scale 1)      */
@@ -167,7 +185,9 @@ typedef struct {
                                           the resident warps per SM without taking L1 away (no
                                           recompilation) */
     int32_t brick;                     /* 1: the kernels address LS_LAYOUT_BRICKED volumes (and only
-                                          those); 0: the linear layouts (coset-major, interleaved) */
+                                          those); 2: LS_LAYOUT_BRICKED_SHIFTED volumes (3D, at most
+                                          two reference sub-regions); 0: the linear layouts
+                                          (coset-major, interleaved) */
     int32_t pipeline;                  /* 1: the value kernel issues the gathers of a thread's next
                                           point before evaluating the current one (software
                                           pipelining; non-separable tables; pts_per_thread ignored) */
@@ -210,15 +230,33 @@ typedef struct {
                                           of the table agree up to sign on enough monomials (the
                                           spline's symmetries make many do): the same A_a in fewer
                                           operations (BCC quintic 377 instead of 1016) */
+    int32_t wait_limit;                /* bounded mbarrier waits (warp-specialized, staged and
+                                          tensor-core kernels) give up after this many try_wait
+                                          rounds (each suspends for at most about a microsecond) and
+                                          set the status word (ls_spline_status); 0: 2^20 rounds */
+    int32_t wait_probe;                /* failure-detection test hook, warp-specialized kernel only:
+                                          1 = the producer warps never signal their slots, so every
+                                          consumer wait runs out after wait_limit rounds and the
+                                          kernel returns with the status word set and the outputs
+                                          unwritten.  0 otherwise */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */
 const char *ls_status_str(ls_status s);
 /* Message of the last failing call on this thread ("" if none). */
 const char *ls_last_error(void);
-/* Layout version of the structs above (5: ls_variant ends with plain_transform);
+/* Layout version of the structs above (5: ls_variant ends with wait_probe);
  * bindings compare it with their own before any other call. */
 int32_t ls_abi_version(void);
+/* Test hooks for failure detection (host-side injection; nothing faults on the
+ * GPU).  ls_debug_fail_alloc(after): the library's next `after` device
+ * allocations succeed and the one after them fails as if the device were out
+ * of memory, so the call that makes it returns LS_ERR_OOM; after < 0 turns
+ * the injection off (it is also off once it has fired).  The paper has no
+ * counterpart.  ls_debug_live_allocs(): the device allocations the library
+ * holds (volumes, status words, staging, plans, workspaces), for leak checks. */
+void ls_debug_fail_alloc(int32_t after);
+int64_t ls_debug_live_allocs(void);
 
 /* ---- splines ----------------------------------------------------------------- */
 /*
@@ -425,7 +463,10 @@ size_t ls_morton_scratch_bytes(int64_t n);
  *    with a message.  It calls no cudaMalloc, cudaFree or allocating routine.
  *  - The first call on a device looks up the array's device address with
  *    cudaGetSymbolAddress (with that device current); make that first call
- *    before any stream capture.
+ *    before any stream capture.  Under CUDA's lazy module loading that first
+ *    call (its symbol lookup and first kernel launches) may also load the
+ *    library's modules onto the device, which takes device memory once; the
+ *    no-allocation guarantee holds from the second call on a device.
  *  - All calls share the one array and it keeps the last call's contents;
  *    nothing in it has to start at zero.  Calls whose work overlaps on the GPU
  *    (other streams, other threads, same device) race on it: serialise them.

@@ -2,9 +2,9 @@
 
 Written independently of the product package.  Direction sets are those of the
 box splines benchmarked in Sec. 5.1 (tensor-product cubic on the Cartesian
-lattice, the linear rhombic-dodecahedron and the doubled "quintic" box splines
-on BCC, the six-direction truncated-octahedron box spline on FCC) and of the ZP
-element of Fig. 1.
+lattice, the linear rhombic-dodecahedron, the doubled "quintic" and the
+seven-direction "quartic" box splines on BCC, the six-direction
+truncated-octahedron box spline on FCC) and of the ZP element of Fig. 1.
 
 Lattices are stored as unions of Cartesian cosets of scale*Z^s:
   CC  = Z^3                                   (scale 1, |det L| = 1)
@@ -48,6 +48,14 @@ def bcc_quintic() -> OrcSpec:
     return OrcSpec(3, BCC_DIRS + BCC_DIRS, 4.0, 2, BCC_COSETS, (1, 1, 1), 0, "bcc_quintic")
 
 
+def bcc_quartic() -> OrcSpec:
+    """The seven-direction box spline on BCC: the four diagonal directions of
+    the linear spline and the three axis directions at their shortest lattice
+    length, 2 e_i (degree 7 - 3 = 4, approximation order 4)."""
+    return OrcSpec(3, BCC_DIRS + ((2, 0, 0), (0, 2, 0), (0, 0, 2)), 4.0, 2, BCC_COSETS, (1, 1, 1), 0,
+                   "bcc_quartic")
+
+
 def fcc6() -> OrcSpec:
     return OrcSpec(3, FCC_DIRS, 2.0, 2, FCC_COSETS, (1, 1, 1), 0, "fcc6")
 
@@ -59,4 +67,4 @@ def zp2d() -> OrcSpec:
 
 
 ALL_3D = {"tricubic": tricubic, "trilinear": trilinear, "triquadratic": triquadratic,
-          "bcc_linear": bcc_linear, "bcc_quintic": bcc_quintic, "fcc6": fcc6}
+          "bcc_linear": bcc_linear, "bcc_quintic": bcc_quintic, "bcc_quartic": bcc_quartic, "fcc6": fcc6}

@@ -23,7 +23,7 @@ LS_F32, LS_BF16, LS_F16, LS_F64 = 0, 1, 2, 3
 LS_ROE_PARALLELEPIPED, LS_ROE_VORONOI = 0, 1
 LS_FOLD_NONE, LS_FOLD_SIGNED_PERM = 0, 1
 # ls_layout
-LS_LAYOUT_COSET_MAJOR, LS_LAYOUT_INTERLEAVED, LS_LAYOUT_BRICKED = 0, 1, 2
+LS_LAYOUT_COSET_MAJOR, LS_LAYOUT_INTERLEAVED, LS_LAYOUT_BRICKED, LS_LAYOUT_BRICKED_SHIFTED = 0, 1, 2, 3
 # ls_adjoint_mode
 LS_ADJ_ATOMIC, LS_ADJ_DETERMINISTIC, LS_ADJ_ATOMIC_WARP, LS_ADJ_DETERMINISTIC_FIXED = 0, 1, 2, 3
 LS_ADJ_ATOMIC_TILED, LS_ADJ_DETERMINISTIC_FIXED_TILED = 4, 5
@@ -59,7 +59,8 @@ class VariantC(ctypes.Structure):
                 ("min_blocks", ctypes.c_int32), ("group", ctypes.c_int32), ("depth", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("brick", ctypes.c_int32), ("pipeline", ctypes.c_int32),
                 ("producers", ctypes.c_int32), ("stage", ctypes.c_int32), ("tensor", ctypes.c_int32),
-                ("tensor_kind", ctypes.c_int32), ("plain_transform", ctypes.c_int32)]
+                ("tensor_kind", ctypes.c_int32), ("plain_transform", ctypes.c_int32),
+                ("wait_limit", ctypes.c_int32), ("wait_probe", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); every function declared in include/lattice_spline.h
@@ -67,6 +68,8 @@ SIGNATURES = {
     "ls_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "ls_last_error": (ctypes.c_char_p, []),
     "ls_abi_version": (ctypes.c_int32, []),
+    "ls_debug_fail_alloc": (None, [ctypes.c_int32]),
+    "ls_debug_live_allocs": (ctypes.c_int64, []),
     "ls_spline_create": (ctypes.c_int, [ctypes.POINTER(SplineDescC), ctypes.c_int, ctypes.POINTER(VariantC),
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "ls_spline_destroy": (ctypes.c_int, [ctypes.c_void_p]),
@@ -235,6 +238,7 @@ class DescHolder:
 
 
 def variant(block=256, pts_per_thread=1, branchy=0, min_blocks=0, group=0, depth=0, blocks_per_sm=0,
-            brick=0, pipeline=0, producers=0, stage=0, tensor=0, tensor_kind=0, plain_transform=0) -> VariantC:
+            brick=0, pipeline=0, producers=0, stage=0, tensor=0, tensor_kind=0, plain_transform=0,
+            wait_limit=0, wait_probe=0) -> VariantC:
     return VariantC(block, pts_per_thread, branchy, min_blocks, group, depth, blocks_per_sm, brick, pipeline,
-                    producers, stage, tensor, tensor_kind, plain_transform)
+                    producers, stage, tensor, tensor_kind, plain_transform, wait_limit, wait_probe)

@@ -23,7 +23,18 @@ _CACHE_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "kcache")
 
 DTYPES = {"f32": _abi.LS_F32, "bf16": _abi.LS_BF16, "f16": _abi.LS_F16}
 LAYOUTS = {"coset": _abi.LS_LAYOUT_COSET_MAJOR, "interleaved": _abi.LS_LAYOUT_INTERLEAVED,
-           "bricked": _abi.LS_LAYOUT_BRICKED}
+           "bricked": _abi.LS_LAYOUT_BRICKED, "bricked_shifted": _abi.LS_LAYOUT_BRICKED_SHIFTED}
+# the kernels' variant.brick for each layout
+LAYOUT_BRICK = {"coset": 0, "interleaved": 0, "bricked": 1, "bricked_shifted": 2}
+
+
+def layout_elems(n_cosets: int, ext: Sequence[int], layout: str) -> int:
+    """Elements a coefficient layout holds (the shifted bricked copies: four
+    padded copies)."""
+    e = tuple(int(v) for v in ext) + (1,) * (3 - len(ext))
+    if layout == "bricked_shifted":
+        return 4 * n_cosets * (e[0] + 2) * (e[1] + 2) * e[2]
+    return n_cosets * e[0] * e[1] * e[2]
 TORCH_DTYPES = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
 
 
@@ -65,15 +76,16 @@ def _ptr(t: Optional[torch.Tensor]):
 def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_blocks: int = 0, group: int = 0,
                 depth: int = 0, pts_per_thread: int = 1, blocks_per_sm: int = 0, expansion: str = "sparse",
                 brick: int = 0, pipeline: int = 0, producers: int = 0, stage: int = 0, tensor: int = 0,
-                tensor_kind: int = 0, plain_transform: int = 0) -> str:
+                tensor_kind: int = 0, plain_transform: int = 0, wait_limit: int = 0, wait_probe: int = 0) -> str:
     """The name tag of a generated kernel variant (blocks_per_sm only sizes the
     grid, so it shares the compiled kernel)."""
     return f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + ("_br" if branchy else "") + \
         (f"_m{min_blocks}" if min_blocks else "") + (f"_g{group}d{depth}" if group and depth else "") + \
         (f"_t{pts_per_thread}" if pts_per_thread > 1 else "") + ("_ec" if expansion == "centroid" else "") + \
-        ("_bk" if brick else "") + ("_pp" if pipeline else "") + (f"_ws{producers}" if producers else "") + \
+        ("_bk2" if brick == 2 else "_bk" if brick else "") + ("_pp" if pipeline else "") + (f"_ws{producers}" if producers else "") + \
         (f"_st{stage}" if stage else "") + (("_tc" + (str(tensor) if tensor > 1 else "")) if tensor else "") + \
-        ("h" if tensor and tensor_kind else "") + ("_pt" if plain_transform else "")
+        ("h" if tensor and tensor_kind else "") + ("_pt" if plain_transform else "") + \
+        (f"_wl{wait_limit}" if wait_limit else "") + ("_wp" if wait_probe else "")
 
 
 class Spline:
@@ -83,7 +95,8 @@ class Spline:
                  min_blocks: int = 0, group: int = 0, depth: int = 0, pts_per_thread: int = 1,
                  blocks_per_sm: int = 0, expansion: str = "sparse", brick: int = 0, pipeline: int = 0,
                  producers: int = 0, stage: int = 0, tensor: int = 0, tensor_kind: int = 0,
-                 plain_transform: int = 0, kernel_name: Optional[str] = None):
+                 plain_transform: int = 0, wait_limit: int = 0, wait_probe: int = 0,
+                 kernel_name: Optional[str] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("lattice spline kernels need a CUDA device")
         self.name = name
@@ -95,12 +108,12 @@ class Spline:
         kname = kernel_name or globals()["kernel_name"](name, dtype, block, branchy, min_blocks, group, depth,
                                                          pts_per_thread, blocks_per_sm, expansion, brick, pipeline,
                                                          producers, stage, tensor, tensor_kind,
-                                                         plain_transform)
+                                                         plain_transform, wait_limit, wait_probe)
         self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
                         "depth": depth, "pts_per_thread": pts_per_thread, "blocks_per_sm": blocks_per_sm,
                         "expansion": expansion}
         if brick:
-            self.variant["brick"] = 1
+            self.variant["brick"] = brick
         if pipeline:
             self.variant["pipeline"] = 1
         if producers:
@@ -113,12 +126,16 @@ class Spline:
             self.variant["tensor_kind"] = tensor_kind
         if plain_transform:
             self.variant["plain_transform"] = 1
+        if wait_limit:
+            self.variant["wait_limit"] = wait_limit
+        if wait_probe:
+            self.variant["wait_probe"] = wait_probe
         self.kernel_name = kname
         self._desc = _abi.DescHolder(self.table, kname, expansion)
         var = _abi.variant(block=block, pts_per_thread=pts_per_thread, branchy=branchy, min_blocks=min_blocks,
                            group=group, depth=depth, blocks_per_sm=blocks_per_sm, brick=brick, pipeline=pipeline,
                            producers=producers, stage=stage, tensor=tensor, tensor_kind=tensor_kind,
-                           plain_transform=plain_transform)
+                           plain_transform=plain_transform, wait_limit=wait_limit, wait_probe=wait_probe)
         h = ctypes.c_void_p()
         torch.cuda.init()
         _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),
@@ -153,9 +170,12 @@ class Volume:
 
     ``layout``: "coset" (one array after another: shape (n_cosets, ext[dim-1],
     ..., ext[0])), "interleaved" (the cosets' values of one grid index
-    adjacent: shape (ext[dim-1], ..., ext[0], n_cosets)) or "bricked" (bricks
+    adjacent: shape (ext[dim-1], ..., ext[0], n_cosets)), "bricked" (bricks
     of 2 x 2 x 2 grid indices, cosets interleaved inside; needs a spline made
-    with brick=1); see ``relayout``.
+    with brick=1) or "bricked_shifted" (four bricked copies with shifted brick
+    grids, each point reading the one that cuts its stencil into the fewest
+    sectors; evaluation only; needs a spline made with brick=2); see
+    ``relayout``.
     ``coef`` (device tensor of the spline's storage dtype in that layout) is
     wrapped without a copy; otherwise a zero volume is allocated by the library.
     """
@@ -169,9 +189,7 @@ class Volume:
         e64 = (ctypes.c_int64 * 3)(*self.ext)
         h = ctypes.c_void_p()
         if coef is not None:
-            want = spline.n_cosets
-            for i in range(spline.dim):
-                want *= self.ext[i]
+            want = layout_elems(spline.n_cosets, self.ext[:spline.dim], layout)
             if not coef.is_cuda or not coef.is_contiguous() or coef.numel() != want or \
                     coef.dtype != TORCH_DTYPES[spline.dtype]:
                 raise ValueError("coef must be a contiguous CUDA tensor of the spline's dtype and volume size")
@@ -301,12 +319,13 @@ def _adjoint_mode(deterministic, warp_aggregated: bool, tiled: bool = False) -> 
 def relayout(coef: torch.Tensor, n_cosets: int, ext: Sequence[int], to: str = "interleaved",
              src: str = "coset", stream=None) -> torch.Tensor:
     """A copy of n_cosets coefficient arrays of extent ext (axis 0 first) moved
-    from layout ``src`` to layout ``to`` ("coset", "interleaved", "bricked")."""
+    from layout ``src`` to layout ``to`` ("coset", "interleaved", "bricked",
+    "bricked_shifted")."""
     coef = coef.contiguous()
     e = tuple(int(v) for v in ext) + (1,) * (3 - len(ext))
-    if not coef.is_cuda or coef.numel() != n_cosets * e[0] * e[1] * e[2]:
-        raise ValueError("coef must be a CUDA tensor of n_cosets * prod(ext) elements")
-    dst = torch.empty_like(coef)
+    if not coef.is_cuda or coef.numel() != layout_elems(n_cosets, e, src):
+        raise ValueError("coef must be a CUDA tensor holding the source layout's elements")
+    dst = torch.empty(layout_elems(n_cosets, e, to), dtype=coef.dtype, device=coef.device)
     _abi.check(_abi.lib().ls_relayout(_ptr(coef), LAYOUTS[src], _ptr(dst), LAYOUTS[to], int(n_cosets),
                                       (ctypes.c_int64 * 3)(*e), coef.element_size(), _stream(stream)),
                "ls_relayout")
@@ -530,7 +549,7 @@ def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_
             continue                      # tensor-product tables have no coefficient transform to offload
         if cand.get("tensor_kind") and dtype != "f32":
             continue                      # the FP16 form splits FP32 data; BF16 / FP16 data are exact in TF32
-        sp = Spline(name, dtype, **cand, **({"brick": 1} if layout == "bricked" else {}))
+        sp = Spline(name, dtype, **cand, **({"brick": LAYOUT_BRICK[layout]} if LAYOUT_BRICK[layout] else {}))
         vol = Volume(sp, ext, coef, layout=layout)
         outs = [torch.empty(p.shape[0], device=p.device) for p in pts_sets]
         for p, o in zip(pts_sets, outs):

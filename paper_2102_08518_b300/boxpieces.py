@@ -31,6 +31,10 @@ from .exactpoly import Poly
 Vec = Tuple[int, ...]
 
 
+# interior points of a breakpoint interval tried in turn (the midpoint first)
+_INTERIOR = (Fraction(1, 2), Fraction(3, 7), Fraction(5, 9), Fraction(7, 19), Fraction(13, 29), Fraction(31, 53))
+
+
 class NotGenericError(ValueError):
     """The evaluation point (or a derived point) sits on a knot plane or makes
     two crossings coincide; the caller retries with another point."""
@@ -228,9 +232,19 @@ class BoxPieces:
                         for i in range(s)]
         res = Poly(s)
         for k in range(len(bps) - 1):
-            tm = (tvals[k] + tvals[k + 1]) / 2
-            zm = tuple(zi - tm * xii for zi, xii in zip(z, xi))
-            q = self._piece(rest, zm)
+            # the smaller set's piece is one polynomial on the whole open
+            # interval; a point of it that lies on one of that set's own knot
+            # planes (possible for structured direction sets) is replaced by
+            # another point of the interval
+            for frac in _INTERIOR:
+                tm = tvals[k] + (tvals[k + 1] - tvals[k]) * frac
+                zm = tuple(zi - tm * xii for zi, xii in zip(z, xi))
+                try:
+                    q = self._piece(rest, zm)
+                    break
+                except NotGenericError:
+                    if frac is _INTERIOR[-1]:
+                        raise
             if q.is_zero():
                 continue
             anti = q.substitute(shift_images).integrate_last()          # A(x, t)

@@ -242,7 +242,7 @@ ls_status get_kernel(ls_spline_s *s, const char *what, cudaKernel_t &k, int &per
 
 ls_variant default_variant(const ls_variant *v)
 {
-    ls_variant r{256, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    ls_variant r{256, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (v) {
         if (v->block > 0) r.block = v->block;
         if (v->pts_per_thread > 0) r.pts_per_thread = v->pts_per_thread > 64 ? 64 : v->pts_per_thread;
@@ -251,18 +251,80 @@ ls_variant default_variant(const ls_variant *v)
         r.group = v->group > 0 ? v->group : 0;
         r.depth = v->depth > 0 ? v->depth : 0;
         r.blocks_per_sm = v->blocks_per_sm > 0 ? v->blocks_per_sm : 0;
-        r.brick = v->brick ? 1 : 0;
+        r.brick = v->brick == 2 ? 2 : v->brick ? 1 : 0;
         r.pipeline = v->pipeline ? 1 : 0;
         r.producers = v->producers > 0 ? v->producers : 0;
         r.stage = v->stage > 0 ? v->stage : 0;
         r.tensor = v->tensor > 0 ? v->tensor : 0;
         r.tensor_kind = v->tensor_kind == 1 ? 1 : 0;
         r.plain_transform = v->plain_transform ? 1 : 0;
+        r.wait_limit = v->wait_limit > 0 ? v->wait_limit : 0;
+        r.wait_probe = v->wait_probe;
     }
     return r;
 }
 
 }  // namespace
+
+namespace ls {
+namespace {
+std::mutex g_alloc_mu;
+long long g_fail_after = -1;       // allocations left before the injected failure (-1: off)
+long long g_live_allocs = 0;       // device allocations the library holds
+
+bool injected_failure()
+{
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_fail_after < 0) return false;
+    if (g_fail_after == 0) {
+        g_fail_after = -1;
+        return true;
+    }
+    --g_fail_after;
+    return false;
+}
+
+void count_alloc(long long d)
+{
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_live_allocs += d;
+}
+}  // namespace
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) count_alloc(1);
+    else *p = nullptr;
+    return e;
+}
+
+cudaError_t dev_malloc_async_raw(void **p, size_t bytes, cudaStream_t st)
+{
+    *p = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e == cudaSuccess) count_alloc(1);
+    else *p = nullptr;
+    return e;
+}
+
+cudaError_t dev_free(void *p)
+{
+    if (!p) return cudaSuccess;
+    count_alloc(-1);
+    return cudaFree(p);
+}
+
+cudaError_t dev_free_async(void *p, cudaStream_t st)
+{
+    if (!p) return cudaSuccess;
+    count_alloc(-1);
+    return cudaFreeAsync(p, st);
+}
+}  // namespace ls
 
 ls_status ls_fail(ls_status s, const std::string &msg)
 {
@@ -291,6 +353,18 @@ const char *ls_status_str(ls_status s)
 const char *ls_last_error(void) { return g_err.c_str(); }
 
 int32_t ls_abi_version(void) { return 5; }
+
+void ls_debug_fail_alloc(int32_t after)
+{
+    std::lock_guard<std::mutex> lk(ls::g_alloc_mu);
+    ls::g_fail_after = after < 0 ? -1 : after;
+}
+
+int64_t ls_debug_live_allocs(void)
+{
+    std::lock_guard<std::mutex> lk(ls::g_alloc_mu);
+    return ls::g_live_allocs;
+}
 
 ls_status ls_spline_precompile(const ls_spline_desc *desc, ls_dtype dt, const ls_variant *variant)
 {
@@ -343,6 +417,15 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
             return ls_fail(LS_ERR_INVALID_ARG, why);
         }
     }
+    if (s->var.brick == 2 && (s->table.dim != 3 || s->table.ref.size() > 2)) {
+        delete s;
+        return ls_fail(LS_ERR_UNSUPPORTED, "brick = 2 (shifted bricked copies) needs a 3D table with at most two "
+                                           "reference sub-regions");
+    }
+    if (s->var.wait_probe != 0 && (s->var.wait_probe != 1 || s->var.producers <= 0)) {
+        delete s;
+        return ls_fail(LS_ERR_INVALID_ARG, "wait_probe 1 needs the warp-specialized kernel (producers > 0)");
+    }
     if (variant && variant->tensor_kind != 0 && (variant->tensor_kind != 1 || !s->var.tensor || dt != LS_F32)) {
         delete s;
         return ls_fail(LS_ERR_INVALID_ARG, "tensor_kind 1 needs tensor and FP32 coefficients (0 or 1)");
@@ -381,9 +464,9 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
         delete s;
         return ls_fail(st, err);
     }
-    if (cudaMalloc((void **)&s->status, 256) != cudaSuccess || cudaMemset(s->status, 0, 256) != cudaSuccess) {
+    if (ls::dev_malloc((void **)&s->status, 256) != cudaSuccess || cudaMemset(s->status, 0, 256) != cudaSuccess) {
         cudaGetLastError();
-        if (s->status) cudaFree(s->status);
+        if (s->status) ls::dev_free(s->status);
         cudaLibraryUnload(s->mod.lib);
         delete s;
         return ls_fail(LS_ERR_OOM, "status word");
@@ -398,7 +481,7 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
         (st = get_kernel(s, "adjoint_tile_fixed", s->mod.adj_tile_fixed, s->mod.blocks_per_sm_tile_fixed)) != LS_OK ||
         (st = get_kernel(s, "adjoint_bin", s->mod.roe_key, s->mod.blocks_per_sm_gather)) != LS_OK ||
         (st = get_kernel(s, "adjoint_gather", s->mod.adj_gather, s->mod.blocks_per_sm_gather)) != LS_OK) {
-        cudaFree(s->status);
+        ls::dev_free(s->status);
         cudaLibraryUnload(s->mod.lib);
         delete s;
         return st;
@@ -413,7 +496,7 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
             e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void *)s->mod.eval, s->var.block, smem);
         if (e2 != cudaSuccess || nb < 1) {
             cudaGetLastError();
-            cudaFree(s->status);
+            ls::dev_free(s->status);
             cudaLibraryUnload(s->mod.lib);
             delete s;
             return ls_fail(LS_ERR_UNSUPPORTED, "the warp-specialized kernel does not fit on an SM (shared memory)");
@@ -452,7 +535,7 @@ ls_status ls_spline_destroy(ls_spline s)
 {
     if (!s) return LS_OK;
     if (s->mod.lib) cudaLibraryUnload(s->mod.lib);
-    if (s->status) cudaFree(s->status);
+    if (s->status) ls::dev_free(s->status);
     delete s;
     return LS_OK;
 }
@@ -488,11 +571,17 @@ ls_status ls_spline_info(ls_spline s, int32_t *n_sites, int32_t *fma_value, int3
 static ls_status init_volume(ls_spline s, const int64_t *ext, int32_t layout, ls_volume_s *v)
 {
     if (!s || !ext) return ls_fail(LS_ERR_INVALID_ARG, "spline or ext is NULL");
-    if (layout != LS_LAYOUT_COSET_MAJOR && layout != LS_LAYOUT_INTERLEAVED && layout != LS_LAYOUT_BRICKED)
+    if (layout != LS_LAYOUT_COSET_MAJOR && layout != LS_LAYOUT_INTERLEAVED && layout != LS_LAYOUT_BRICKED &&
+        layout != LS_LAYOUT_BRICKED_SHIFTED)
         return ls_fail(LS_ERR_INVALID_ARG, "unknown layout");
-    if ((layout == LS_LAYOUT_BRICKED) != (s->var.brick != 0))
-        return ls_fail(LS_ERR_INVALID_ARG, s->var.brick ? "the spline's kernels address the bricked layout only"
-                                                       : "a bricked volume needs a spline created with variant.brick = 1");
+    const int want_brick = layout == LS_LAYOUT_BRICKED ? 1 : layout == LS_LAYOUT_BRICKED_SHIFTED ? 2 : 0;
+    if (want_brick != s->var.brick)
+        return ls_fail(LS_ERR_INVALID_ARG, s->var.brick == 1 ? "the spline's kernels address the bricked layout only"
+                                           : s->var.brick == 2 ? "the spline's kernels address the shifted bricked copies only"
+                                           : "a bricked volume needs a spline created with variant.brick = 1 (2 for the "
+                                             "shifted copies)");
+    if (layout == LS_LAYOUT_BRICKED_SHIFTED && s->table.dim != 3)
+        return ls_fail(LS_ERR_UNSUPPORTED, "the shifted bricked copies are 3D only");
     v->spline = s;
     v->layout = layout;
     int64_t prod = 1;
@@ -503,9 +592,11 @@ static ls_status init_volume(ls_spline s, const int64_t *ext, int32_t layout, ls
     }
     v->coset_elems = prod;
     v->total_elems = prod * (int64_t)s->table.cosets.size();
-    if (layout == LS_LAYOUT_BRICKED &&
+    if ((layout == LS_LAYOUT_BRICKED || layout == LS_LAYOUT_BRICKED_SHIFTED) &&
         (v->ext[0] % 2 != 0 || (s->table.dim >= 2 && v->ext[1] % 2 != 0) || (s->table.dim == 3 && v->ext[2] % 2 != 0)))
         return ls_fail(LS_ERR_INVALID_ARG, "bricked layout: ext[0], ext[1] and ext[2] must be even");
+    if (layout == LS_LAYOUT_BRICKED_SHIFTED)      // four copies over the padded extents
+        v->total_elems = 4 * (int64_t)s->table.cosets.size() * (v->ext[0] + 2) * (v->ext[1] + 2) * v->ext[2];
     if (v->total_elems >= (int64_t)1 << 31)
         return ls_fail(LS_ERR_UNSUPPORTED, "volume exceeds 2^31 coefficients (32-bit addressing)");
     return LS_OK;
@@ -563,7 +654,7 @@ static ls_status volume_tensor_map(ls_volume_s *v)
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return ls_fail(LS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-    cudaError_t e = cudaMalloc(&v->tmap, sizeof(CUtensorMap));
+    cudaError_t e = ls::dev_malloc(&v->tmap, sizeof(CUtensorMap));
     if (e != cudaSuccess) {
         v->tmap = nullptr;
         return cuda_fail(e, "cudaMalloc (tensor map)");
@@ -586,7 +677,7 @@ ls_status ls_volume_create(ls_spline s, const int64_t *ext, int32_t layout, ls_v
         return st;
     }
     size_t bytes = (size_t)v->total_elems * dtype_size(s->dtype);
-    cudaError_t e = cudaMalloc(&v->coef, bytes);
+    cudaError_t e = ls::dev_malloc(&v->coef, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete v;
@@ -594,7 +685,7 @@ ls_status ls_volume_create(ls_spline s, const int64_t *ext, int32_t layout, ls_v
     }
     e = cudaMemset(v->coef, 0, bytes);
     if (e != cudaSuccess) {
-        cudaFree(v->coef);
+        ls::dev_free(v->coef);
         delete v;
         return cuda_fail(e, "cudaMemset");
     }
@@ -646,9 +737,15 @@ ls_status ls_relayout(const void *src, int32_t src_layout, void *dst, int32_t ds
     }
     if (per * n_cosets >= ((int64_t)1 << 31)) return ls_fail(LS_ERR_UNSUPPORTED, "2^31 or more elements");
     for (int32_t l : {src_layout, dst_layout}) {
-        if (l < LS_LAYOUT_COSET_MAJOR || l > LS_LAYOUT_BRICKED) return ls_fail(LS_ERR_INVALID_ARG, "unknown layout");
-        if (l == LS_LAYOUT_BRICKED && (ext[0] % 2 != 0 || ext[1] % 2 != 0 || (ext[2] != 1 && ext[2] % 2 != 0)))
+        if (l < LS_LAYOUT_COSET_MAJOR || l > LS_LAYOUT_BRICKED_SHIFTED)
+            return ls_fail(LS_ERR_INVALID_ARG, "unknown layout");
+        if ((l == LS_LAYOUT_BRICKED || l == LS_LAYOUT_BRICKED_SHIFTED) &&
+            (ext[0] % 2 != 0 || ext[1] % 2 != 0 || (ext[2] != 1 && ext[2] % 2 != 0)))
             return ls_fail(LS_ERR_INVALID_ARG, "bricked layout: extents are not whole bricks");
+        if (l == LS_LAYOUT_BRICKED_SHIFTED && ext[2] == 1)
+            return ls_fail(LS_ERR_UNSUPPORTED, "the shifted bricked copies are 3D only");
+        if (l == LS_LAYOUT_BRICKED_SHIFTED && 4 * n_cosets * (ext[0] + 2) * (ext[1] + 2) * ext[2] >= ((int64_t)1 << 31))
+            return ls_fail(LS_ERR_UNSUPPORTED, "2^31 or more elements");
     }
     if (!src || !dst || src == dst) return ls_fail(LS_ERR_INVALID_ARG, "src, dst NULL or the same buffer");
     const lsk::LayoutGeom sg{src_layout, n_cosets, (long long)per, (int)ext[0], (int)ext[1], (int)ext[2]};
@@ -681,17 +778,17 @@ ls_status ls_volume_upload(ls_volume v, const void *src, int32_t src_is_device, 
     const void *dsrc = src;
     void *tmp = nullptr;
     if (!src_is_device) {
-        cudaError_t e = cudaMallocAsync(&tmp, n * dtype_size(src_dt), st);
+        cudaError_t e = ls::dev_malloc_async(&tmp, n * dtype_size(src_dt), st);
         if (e != cudaSuccess) return ls_fail(LS_ERR_OOM, "staging allocation for upload");
         e = cudaMemcpyAsync(tmp, src, n * dtype_size(src_dt), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) {
-            cudaFreeAsync(tmp, st);
+            ls::dev_free_async(tmp, st);
             return cuda_fail(e, "cudaMemcpyAsync");
         }
         dsrc = tmp;
     }
     cudaError_t e = lsk::convert_relayout(dsrc, (int)src_dt, sg, v->coef, (int)dst_dt, dg, st);
-    if (tmp) cudaFreeAsync(tmp, st);
+    if (tmp) ls::dev_free_async(tmp, st);
     if (e != cudaSuccess) return cuda_fail(e, "convert kernel");
     return LS_OK;
 }
@@ -706,11 +803,11 @@ ls_status ls_volume_destroy(ls_volume v)
         }
     for (int i = 0; i < 3; ++i)
         if (v->hev[i]) cudaEventDestroy(v->hev[i]);
-    if (v->owned && v->coef) cudaFree(v->coef);
-    if (v->stage) cudaFree(v->stage);
+    if (v->owned && v->coef) ls::dev_free(v->coef);
+    if (v->stage) ls::dev_free(v->stage);
     if (v->tex) cudaDestroyTextureObject(v->tex);
     if (v->tex_array) cudaFreeArray(v->tex_array);
-    if (v->tmap) cudaFree(v->tmap);
+    if (v->tmap) ls::dev_free(v->tmap);
     delete v;
     return LS_OK;
 }
@@ -812,11 +909,11 @@ ls_status ls_eval_host_multi(int32_t n_vol, const ls_volume *vols, const float *
         if (v->stage) {
             cudaStreamSynchronize(v->hs[0]);
             cudaStreamSynchronize(v->hs[1]);
-            cudaFree(v->stage);
+            ls::dev_free(v->stage);
             v->stage = nullptr;
             v->stage_bytes = 0;
         }
-        if (cudaMalloc(&v->stage, need) != cudaSuccess) {
+        if (ls::dev_malloc(&v->stage, need) != cudaSuccess) {
             cudaGetLastError();
             return ls_fail(LS_ERR_OOM, "staging buffers for ls_eval_host");
         }
@@ -826,20 +923,33 @@ ls_status ls_eval_host_multi(int32_t n_vol, const ls_volume *vols, const float *
     if ((e = cudaEventRecord(v->hev[2], user)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
     for (int i = 0; i < 2; ++i)
         if ((e = cudaStreamWaitEvent(v->hs[i], v->hev[2], 0)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
+    // an error inside the chunk loop first drains both internal streams, so no
+    // copy into the caller's host buffers is still queued when the call returns
+    auto drain = [&]() {
+        cudaStreamSynchronize(v->hs[0]);
+        cudaStreamSynchronize(v->hs[1]);
+    };
     int64_t c = 0;
     for (int64_t p0 = 0; p0 < n; p0 += chunk, ++c) {
         const int si = (int)(c & 1);
         cudaStream_t s = v->hs[si];
         const int64_t m = std::min<int64_t>(chunk, n - p0);
         float *dp = (float *)((char *)v->stage + si * stage_one);
-        if ((e = cudaMemcpyAsync(dp, host_pts + p0 * D, (size_t)m * D * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        if ((e = cudaMemcpyAsync(dp, host_pts + p0 * D, (size_t)m * D * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+            drain();
             return cuda_fail(e, "cudaMemcpyAsync H2D");
+        }
         for (int k = 0; k < n_vol; ++k) {
             float *dout = (float *)((char *)dp + pbytes + k * obytes);
             ls_status st = ls_eval(vols[k], dp, m, dout, (ls_stream)s);
-            if (st != LS_OK) return st;
-            if ((e = cudaMemcpyAsync(host_out[k] + p0, dout, (size_t)m * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            if (st != LS_OK) {
+                drain();
+                return st;
+            }
+            if ((e = cudaMemcpyAsync(host_out[k] + p0, dout, (size_t)m * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+                drain();
                 return cuda_fail(e, "cudaMemcpyAsync D2H");
+            }
         }
     }
     for (int i = 0; i < 2; ++i)
@@ -893,6 +1003,8 @@ ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int6
     if (!v || (n > 0 && (!pts || !gout || !dcoef))) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
     if (n < 0) return ls_fail(LS_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return LS_OK;
+    if (v->layout == LS_LAYOUT_BRICKED_SHIFTED)
+        return ls_fail(LS_ERR_UNSUPPORTED, "the shifted bricked copies are read-only (evaluation kernels)");
     ls_spline_s *s = v->spline;
     cudaStream_t st = (cudaStream_t)stream;
     // the tiled kernels address the linear layouts; elsewhere (and if their
@@ -904,7 +1016,7 @@ ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int6
     if (mode == LS_ADJ_DETERMINISTIC_FIXED || mode == LS_ADJ_DETERMINISTIC_FIXED_TILED) {
         const size_t need = ls_adjoint_scratch_bytes(v, n);
         void *ws = scratch;
-        if (!ws && cudaMallocAsync(&ws, need, st) != cudaSuccess) {
+        if (!ws && ls::dev_malloc_async(&ws, need, st) != cudaSuccess) {
             cudaGetLastError();
             return ls_fail(LS_ERR_OOM, "scratch for the fixed-point adjoint");
         }
@@ -928,7 +1040,7 @@ ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int6
         }
         if (res == LS_OK && (e = lsk::fixed_finish(acc, inv, dcoef, v->total_elems, st)) != cudaSuccess)
             res = cuda_fail(e, "fixed-point adjoint finish");
-        if (!scratch) cudaFreeAsync(ws, st);
+        if (!scratch) ls::dev_free_async(ws, st);
         return res;
     }
     if (mode != LS_ADJ_DETERMINISTIC) {
@@ -951,7 +1063,7 @@ ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int6
     const size_t N = (size_t)n;
     const size_t need = ls_adjoint_scratch_bytes(v, n);
     void *ws = scratch;
-    if (!ws && cudaMallocAsync(&ws, need, st) != cudaSuccess) {
+    if (!ws && ls::dev_malloc_async(&ws, need, st) != cudaSuccess) {
         cudaGetLastError();
         return ls_fail(LS_ERR_OOM, "scratch for the deterministic adjoint");
     }
@@ -982,7 +1094,7 @@ ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int6
                        H};
         res = launch(s->mod.adj_gather, grid_for(v->total_elems, s->var.block, s->num_sms, 8), s->var.block, &ga, st);
     }
-    if (!scratch) cudaFreeAsync(ws, st);
+    if (!scratch) ls::dev_free_async(ws, st);
     return res;
 }
 
@@ -1009,7 +1121,7 @@ ls_status ls_morton_sort(const float *pts, int64_t n, const float *origin, float
     void *ws = scratch;
     const size_t need = ls_morton_scratch_bytes(n);
     if (!ws) {
-        if (cudaMallocAsync(&ws, need, st) != cudaSuccess) {
+        if (ls::dev_malloc_async(&ws, need, st) != cudaSuccess) {
             cudaGetLastError();
             return ls_fail(LS_ERR_OOM, "scratch for ls_morton_sort");
         }
@@ -1018,7 +1130,7 @@ ls_status ls_morton_sort(const float *pts, int64_t n, const float *origin, float
     void *sort_ws = (char *)ws + al256((size_t)n * 4);
     cudaError_t e = lsk::morton_keys(pts, n, origin, cell, keys, perm, st);
     if (e == cudaSuccess) e = lsk::radix_sort_pairs(keys, perm, n, 30, sort_ws, st);
-    if (!scratch) cudaFreeAsync(ws, st);
+    if (!scratch) ls::dev_free_async(ws, st);
     if (e != cudaSuccess) return cuda_fail(e, "morton sort kernels");
     return LS_OK;
 }

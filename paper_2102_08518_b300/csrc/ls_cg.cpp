@@ -16,7 +16,7 @@ struct Ws {
     void *base = nullptr;
     ~Ws()
     {
-        if (base) cudaFree(base);
+        if (base) ls::dev_free(base);
     }
 };
 
@@ -43,7 +43,7 @@ extern "C" ls_status ls_cg_fit(ls_volume v, const float *pts, const float *y, in
     const size_t adj_bytes = deterministic ? ls_adjoint_scratch_bytes(v, n) : 0;
     const size_t bytes = al(nc * 4) * 2 + al(nr * 4) * 2 + al(8 * sizeof(double)) + al(lsk::dot_ws_bytes()) + adj_bytes;
     Ws ws;
-    if (cudaMalloc(&ws.base, bytes) != cudaSuccess) {
+    if (ls::dev_malloc(&ws.base, bytes) != cudaSuccess) {
         cudaGetLastError();
         return ls_fail(LS_ERR_OOM, "workspace of the CG fit");
     }

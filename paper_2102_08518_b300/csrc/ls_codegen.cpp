@@ -48,6 +48,10 @@ struct Emitter {
     std::string ld = "ls_ld_f32";     // coefficient loader of the spline being emitted
     bool brick = false;               // bricked coefficient layout (else linear)
     bool sym = true;                  // factored coefficient transform (butterflies + sparser M)
+    bool brick_shift = false;         // the four shifted bricked copies (LS_LAYOUT_BRICKED_SHIFTED)
+    unsigned long long shift_mx = 0, shift_my = 0;   // their copy-choice rule (shift_rule)
+    int wait_rounds = 1 << 20;        // try_wait rounds of a bounded wait (ls_mbar_wait; polls: x4)
+    bool no_signal = false;           // test hook: warp-specialized producers never signal their slots
     std::string fresh(const char *p) { return std::string(p) + std::to_string(tmp++); }
 };
 
@@ -112,7 +116,7 @@ void emit_prologue(Emitter &e)
     // bounded wait for the completion of an mbarrier phase: gives up after about
     // a second, sets *status to 1 and returns false (the caller's warp leaves)
     o << "static __device__ __forceinline__ bool ls_mbar_wait(unsigned bar, unsigned parity, unsigned* status) {\n"
-         "  for (int it = 0; it < (1 << 20); ++it) {\n"
+         "  for (int it = 0; it < " << e.wait_rounds << "; ++it) {\n"
          "    unsigned ok;\n"
          "    asm volatile(\"{ .reg .pred p; mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, 1000;"
          " selp.u32 %0, 1, 0, p; }\" : \"=r\"(ok) : \"r\"(bar), \"r\"(parity) : \"memory\");\n"
@@ -125,7 +129,7 @@ void emit_prologue(Emitter &e)
     // try_wait suspends the thread for a system-dependent time while the phase
     // is incomplete; bounded, sets *status and returns false when it gives up
     o << "static __device__ __forceinline__ bool ls_mbar_poll(unsigned bar, unsigned parity, unsigned* status) {\n"
-         "  for (int it = 0; it < (1 << 22); ++it) {\n"
+         "  for (int it = 0; it < " << 4LL * e.wait_rounds << "; ++it) {\n"
          "    unsigned ok;\n"
          "    asm volatile(\"{ .reg .pred p; mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;"
          " selp.u32 %0, 1, 0, p; }\" : \"=r\"(ok) : \"r\"(bar), \"r\"(parity) : \"memory\");\n"
@@ -257,6 +261,137 @@ unsigned long long coset_lut(const Table &t)
 }
 
 // ---------------------------------------------------------------------------
+// Copy choice for the shifted bricked copies.
+//
+// A point's stencil is a fixed set of sites around its region-of-evaluation
+// site k, placed by the point's signed permutation; how many 32-byte sectors
+// it touches depends on where the brick boundaries cut it.  The four copies
+// shift the brick grid by (s_0, s_1) in {0,1}^2 grid indices.  The choice is
+// made per Cartesian axis i in {0, 1} from what fixes the stencil's position
+// along that axis: the reference sub-region psi, the reference axis r landing
+// on axis i, its sign, and k_i mod 4; bit key(psi, r, neg, k_i mod 4) of a
+// 64-bit mask per axis holds s_i.  The masks minimise the sectors summed over
+// all classes (sub-region, transform, k mod 4 on each axis over the lattice's
+// sites), alternating between the two axes from s = 0.
+// ---------------------------------------------------------------------------
+int shift_key(int psi, int r, int neg, int kmod4) { return ((psi * 3 + r) * 2 + neg) * 4 + kmod4; }
+
+struct ShiftRule {
+    unsigned long long mx = 0, my = 0;
+    double base = 0.0, best = 0.0;        // mean sectors per class: copy 0 only, with the rule
+};
+
+ShiftRule shift_rule(const Table &t, const std::vector<std::vector<I3>> &region_sites, int elem_bytes)
+{
+    ShiftRule rule;
+    const bool fold = t.fold == LS_FOLD_SIGNED_PERM;
+    const int a = t.scale;
+    const int C = (int)t.cosets.size();
+    const int per_sector = 32 / elem_bytes;
+    struct Cls { int kx, ky; int rx, ry, nx, ny, psi; int cnt[4]; };
+    std::vector<Cls> cls;
+    int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    const int np = fold ? 6 : 1, ns = fold ? 8 : 1;
+    for (size_t psi = 0; psi < region_sites.size(); ++psi)
+        for (int pi = 0; pi < np; ++pi)
+            for (int sg = 0; sg < ns; ++sg)
+                for (int km = 0; km < 64; ++km) {
+                    const int kq[3] = {km & 3, (km >> 2) & 3, (km >> 4) & 3};
+                    if (a == 2) {        // k must be a lattice site: its parity pattern is a coset's
+                        int par = (kq[0] & 1) | ((kq[1] & 1) << 1) | ((kq[2] & 1) << 2), hit = 0;
+                        for (const auto &l : t.cosets)
+                            hit |= ((l[0] & 1) | ((l[1] & 1) << 1) | ((l[2] & 1) << 2)) == par;
+                        if (!hit) continue;
+                    }
+                    const int *p = perms[pi];           // reference axis r lands on Cartesian axis p[r]
+                    const int g[3] = {sg & 1, (sg >> 1) & 1, (sg >> 2) & 1};   // sign bit of reference axis r
+                    Cls c{kq[0], kq[1], 0, 0, 0, 0, (int)psi, {0, 0, 0, 0}};
+                    for (int r = 0; r < 3; ++r) {
+                        if (p[r] == 0) c.rx = r, c.nx = g[r];
+                        if (p[r] == 1) c.ry = r, c.ny = g[r];
+                    }
+                    for (int cp = 0; cp < 4; ++cp) {
+                        std::set<long long> sec;
+                        for (const auto &sref : region_sites[psi]) {
+                            int n[3];
+                            for (int i = 0; i < 3; ++i) n[i] = 64 + kq[i];
+                            for (int r = 0; r < 3; ++r) n[p[r]] += g[r] ? -sref[r] : sref[r];
+                            int j = 0, q[3];
+                            if (a == 2) {
+                                const int par = (n[0] & 1) | ((n[1] & 1) << 1) | ((n[2] & 1) << 2);
+                                for (size_t cc = 0; cc < t.cosets.size(); ++cc)
+                                    if (((t.cosets[cc][0] & 1) | ((t.cosets[cc][1] & 1) << 1) |
+                                         ((t.cosets[cc][2] & 1) << 2)) == par)
+                                        j = (int)cc;
+                                for (int i = 0; i < 3; ++i) q[i] = n[i] >> 1;
+                            } else {
+                                for (int i = 0; i < 3; ++i) q[i] = n[i];
+                            }
+                            q[0] += cp & 1;
+                            q[1] += cp >> 1;
+                            const long long bk = (q[0] >> 1) + 1000LL * ((q[1] >> 1) + 1000LL * (q[2] >> 1));
+                            const int w = (q[0] & 1) + 2 * (q[1] & 1) + 4 * (q[2] & 1);
+                            sec.insert(((bk * 8 + w) * C + j) / per_sector);
+                        }
+                        c.cnt[cp] = (int)sec.size();
+                    }
+                    cls.push_back(c);
+                }
+    if (cls.empty()) return rule;
+    std::vector<int> rx(64, 0), ry(64, 0);
+    for (int it = 0; it < 4; ++it) {
+        for (int axis = 0; axis < 2; ++axis) {
+            std::vector<long long> tot0(64, 0), tot1(64, 0);
+            for (const auto &c : cls) {
+                const int kx = shift_key(c.psi, c.rx, c.nx, c.kx), ky = shift_key(c.psi, c.ry, c.ny, c.ky);
+                if (axis == 0) {
+                    tot0[kx] += c.cnt[0 + 2 * ry[ky]];
+                    tot1[kx] += c.cnt[1 + 2 * ry[ky]];
+                } else {
+                    tot0[ky] += c.cnt[rx[kx] + 0];
+                    tot1[ky] += c.cnt[rx[kx] + 2];
+                }
+            }
+            auto &rr = axis == 0 ? rx : ry;
+            for (int k = 0; k < 64; ++k) rr[k] = tot1[k] < tot0[k] ? 1 : 0;
+        }
+    }
+    double base = 0, best = 0;
+    for (const auto &c : cls) {
+        base += c.cnt[0];
+        best += c.cnt[rx[shift_key(c.psi, c.rx, c.nx, c.kx)] + 2 * ry[shift_key(c.psi, c.ry, c.ny, c.ky)]];
+    }
+    for (int k = 0; k < 64; ++k) {
+        rule.mx |= (unsigned long long)rx[k] << k;
+        rule.my |= (unsigned long long)ry[k] << k;
+    }
+    rule.base = base / (double)cls.size();
+    rule.best = best / (double)cls.size();
+    return rule;
+}
+
+// The site lists the gathers of each reference sub-region read (the product
+// stencil of a tensor-product spline), for the copy-choice rule.
+void setup_brick_shift(Emitter &e, const Table &t, int brick, ls_dtype dt)
+{
+    e.brick_shift = brick == 2;
+    if (!e.brick_shift) return;
+    std::vector<std::vector<I3>> rs;
+    if (!t.sep.empty()) {
+        std::vector<I3> sites;
+        for (int s2 : t.sep[2].sites)
+            for (int s1 : t.sep[1].sites)
+                for (int s0 : t.sep[0].sites) sites.push_back({s0, s1, s2});
+        rs.push_back(sites);
+    } else {
+        for (const auto &r : t.ref) rs.push_back(r.sites);
+    }
+    const ShiftRule rule = shift_rule(t, rs, dt == LS_F32 ? 4 : 2);
+    e.shift_mx = rule.mx;
+    e.shift_my = rule.my;
+}
+
+// ---------------------------------------------------------------------------
 // addressing + gathers: emits float cN = coefficient of union site N.
 // Fast path with unchecked addresses when the whole stencil is inside;
 // checked path otherwise.
@@ -286,7 +421,21 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
     // BA_i (q_i & 1) per axis.
     if (e.brick) {
         o << "    const int BA0 = CU, BA1 = 2 * CU, BA2 = 4 * CU;\n";
-        o << "    const int BH0 = " << (D == 3 ? 8 : 4) << " * CU, BH1 = BH0 * (ex0 >> 1), BH2 = BH1 * (ex1 >> 1);\n";
+        if (e.brick_shift) {
+            // the four shifted copies: bricks over the padded extents, copy (sx, sy)
+            // chosen per point (shift_rule), Q = CS elements per copy
+            o << "    const int BH0 = 8 * CU, BH1 = BH0 * ((ex0 + 2) >> 1), BH2 = BH1 * ((ex1 + 2) >> 1);\n";
+            auto key = [&](int i) {
+                const std::string r = fold ? "ri" + std::to_string(i) : std::to_string(i);
+                const std::string ng = fold ? "(int)ng" + std::to_string(i) : "0";
+                return "((psi * 3 + " + r + ") * 2 + " + ng + ") * 4 + (k" + std::to_string(i) + " & 3)";
+            };
+            o << "    const int sx = (int)((" << e.shift_mx << "ull >> (" << key(0) << ")) & 1ull);\n";
+            o << "    const int sy = (int)((" << e.shift_my << "ull >> (" << key(1) << ")) & 1ull);\n";
+            o << "    const int cbase = (sx + 2 * sy) * CS;\n";
+        } else {
+            o << "    const int BH0 = " << (D == 3 ? 8 : 4) << " * CU, BH1 = BH0 * (ex0 >> 1), BH2 = BH1 * (ex1 >> 1);\n";
+        }
         o << "    const int BB0 = BH0 - 2 * BA0, BB1 = BH1 - 2 * BA1, BB2 = BH2 - 2 * BA2;\n";
         o << "    (void)BA2; (void)BB2;\n";
     }
@@ -363,7 +512,9 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
         base_of_class[m] = nm;
     };
     if (a == 1) {
-        if (e.brick) {
+        if (e.brick_shift) {
+            emit_brick_class(0, "(k0 + sx)", "(k1 + sy)", "k2", "cbase");
+        } else if (e.brick) {
             emit_brick_class(0, "k0", D >= 2 ? "k1" : "0", D == 3 ? "k2" : "0", "0");
         } else {
             o << "      const int base0 = CU * (";
@@ -374,7 +525,11 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
     } else {
         const unsigned long long lut = coset_lut(t);
         for (int i = 0; i < D; ++i)
-            o << "      const int qh" << i << " = k" << i << " >> 1, cb" << i << " = k" << i << " & 1;\n";
+            if (e.brick_shift && i < 2)
+                o << "      const int qh" << i << " = (k" << i << " >> 1) + " << (i ? "sy" : "sx") << ", cb" << i
+                  << " = k" << i << " & 1;\n";
+            else
+                o << "      const int qh" << i << " = k" << i << " >> 1, cb" << i << " = k" << i << " & 1;\n";
         std::set<int> classes;
         for (const auto &s : sites) classes.insert(parity_class(s));
         for (int m : classes) {
@@ -400,7 +555,7 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
                              : std::string("0");
             };
             if (e.brick) {
-                emit_brick_class(m, q(0), q(1), q(2), "cid" + std::to_string(m));
+                emit_brick_class(m, q(0), q(1), q(2), (e.brick_shift ? "cbase + cid" : "cid") + std::to_string(m));
             } else {
                 o << "      const int " << nm << " = cid" << m << " * CS + CU * ((" << q(0) << ")";
                 if (D >= 2) o << " + ex0 * ((" << q(1) << ")";
@@ -467,9 +622,15 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             for (int i = 1; i < D; ++i) o << " | ((n" << i << " & 1) << " << i << ")";
             o << ";\n        const int cid = (int)((" << lut << "ull >> (4 * par)) & 15ull);\n";
             if (e.brick) {
-                o << "        const int adr = cid";
-                for (int i = 0; i < D; ++i)
-                    o << " + BA" << i << " * (n" << i << " >> 1) + BB" << i << " * ((n" << i << " >> 1) >> 1)";
+                o << "        const int adr = " << (e.brick_shift ? "cbase + cid" : "cid");
+                for (int i = 0; i < D; ++i) {
+                    if (e.brick_shift && i < 2) {
+                        const std::string g = "((n" + std::to_string(i) + " >> 1) + " + (i ? "sy)" : "sx)");
+                        o << " + BA" << i << " * " << g << " + BB" << i << " * (" << g << " >> 1)";
+                    } else {
+                        o << " + BA" << i << " * (n" << i << " >> 1) + BB" << i << " * ((n" << i << " >> 1) >> 1)";
+                    }
+                }
                 o << ";\n";
             } else {
                 o << "        const int adr = cid * CS + CU * ((n0 >> 1)";
@@ -480,9 +641,15 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             }
         } else {
             if (e.brick) {
-                o << "        const int adr = 0";
-                for (int i = 0; i < D; ++i)
-                    o << " + BA" << i << " * n" << i << " + BB" << i << " * (n" << i << " >> 1)";
+                o << "        const int adr = " << (e.brick_shift ? "cbase" : "0");
+                for (int i = 0; i < D; ++i) {
+                    if (e.brick_shift && i < 2) {
+                        const std::string g = "(n" + std::to_string(i) + (i ? " + sy)" : " + sx)");
+                        o << " + BA" << i << " * " << g << " + BB" << i << " * (" << g << " >> 1)";
+                    } else {
+                        o << " + BA" << i << " * n" << i << " + BB" << i << " * (n" << i << " >> 1)";
+                    }
+                }
                 o << ";\n";
             } else {
                 o << "        const int adr = CU * (n0";
@@ -1468,7 +1635,10 @@ int emit_eval_kernel_ws(Emitter &e, const Table &t, const ls_variant &var, const
     o << "        sl[" << (NS + D) * 32 << " + lane] = __int_as_float(psi_out | (sp << 8));\n";
     o << "        sl[" << (NS + D + 1) * 32 << " + lane] = sv;\n";
     o << "        __syncwarp();\n";
-    o << "        if (lane == 0) asm volatile(\"mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\" :: \"r\"(bar0 + 8u * k) : \"memory\");\n";
+    if (e.no_signal)   // test hook: the slot is never signalled, so every consumer's wait runs out
+        o << "        // (no arrival: wait_probe)\n";
+    else
+        o << "        if (lane == 0) asm volatile(\"mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\" :: \"r\"(bar0 + 8u * k) : \"memory\");\n";
     o << "      }\n    }\n    return;\n  }\n";
     // consumers
     o << "  {\n";
@@ -2790,7 +2960,10 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
     Emitter e;
     e.ld = loader_name(dt);
     e.brick = var.brick != 0;
+    setup_brick_shift(e, t, var.brick, dt);
     e.sym = !var.plain_transform;
+    if (var.wait_limit > 0) e.wait_rounds = var.wait_limit;
+    e.no_signal = var.wait_probe == 1;
     emit_prologue(e);
     Stencil st = union_stencil(t);
     int reach = 0;
@@ -2867,6 +3040,7 @@ Generated generate_batch(const std::vector<const Table *> &tables, const std::ve
         const Table &t = *tables[k];
         e.ld = loader_name(dts[k]);
         e.brick = bricks[k] != 0;
+        setup_brick_shift(e, t, bricks[k], dts[k]);
         Stencil st = union_stencil(t);
         int reach = 0;
         if (t.sep.empty()) {

@@ -131,14 +131,31 @@ struct ls_volume_s {
 // Address of coefficient (coset j, per-coset linear index q) is
 // j * vol_cstride(v) + q * vol_cunit(v) in the linear layouts; the bricked
 // layout's kernels take C = vol_cunit(v) and compute the brick address.
+// The shifted bricked copies take the elements per copy in place of the coset stride.
 inline int vol_cstride(const ls_volume_s *v)
 {
+    if (v->layout == LS_LAYOUT_BRICKED_SHIFTED) return (int)(v->total_elems / 4);
     return v->layout == LS_LAYOUT_COSET_MAJOR ? (int)v->coset_elems : 1;
 }
 inline int vol_cunit(const ls_volume_s *v)
 {
     return v->layout == LS_LAYOUT_COSET_MAJOR ? 1 : (int)v->spline->table.cosets.size();
 }
+
+// Device allocations of the library (ls_api.cpp).  One place for the
+// host-side allocation-failure injection of the tests (ls_debug_fail_alloc)
+// and the count of live allocations (ls_debug_live_allocs).
+namespace ls {
+cudaError_t dev_malloc_raw(void **p, size_t bytes);
+cudaError_t dev_malloc_async_raw(void **p, size_t bytes, cudaStream_t st);
+cudaError_t dev_free(void *p);
+cudaError_t dev_free_async(void *p, cudaStream_t st);
+template <class T> cudaError_t dev_malloc(T **p, size_t bytes) { return dev_malloc_raw((void **)p, bytes); }
+template <class T> cudaError_t dev_malloc_async(T **p, size_t bytes, cudaStream_t st)
+{
+    return dev_malloc_async_raw((void **)p, bytes, st);
+}
+}  // namespace ls
 
 // Thread-local error message helpers (ls_api.cpp).
 ls_status ls_fail(ls_status s, const std::string &msg);

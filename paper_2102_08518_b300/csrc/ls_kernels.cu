@@ -24,32 +24,55 @@ __device__ __forceinline__ double load_any(const void *p, int dt, long long i)
 
 // Element index of (coset j, grid index q) in a coefficient layout (ls_layout):
 // 0 coset-major, 1 interleaved, 2 bricked (2 x 2 x 2 grid indices per brick,
-// 2 x 2 in 2D (e2 == 1), cosets interleaved inside, x fastest).
+// 2 x 2 in 2D (e2 == 1), cosets interleaved inside, x fastest), 3 four bricked
+// copies whose brick grids are shifted by (sx, sy) in {0,1}^2 grid indices
+// (copy sx + 2 sy over extents e0 + 2, e1 + 2, e2; copy 0 is read here).
+__device__ __forceinline__ long long brick_index(int ncos, int e0, int e1, int e2, int j, int q0, int q1, int q2)
+{
+    const int bv = e2 == 1 ? 4 : 8;
+    const long long bk = (q0 >> 1) + (long long)(e0 >> 1) * ((q1 >> 1) + (long long)(e1 >> 1) * (q2 >> 1));
+    const int wi = (q0 & 1) + 2 * (q1 & 1) + 4 * (q2 & 1);
+    return (bk * bv + wi) * ncos + j;
+}
+
 __device__ __forceinline__ long long lay_index(const LayoutGeom &g, int j, int q0, int q1, int q2)
 {
     const long long lin = q0 + (long long)g.e0 * (q1 + (long long)g.e1 * q2);
     if (g.layout == 0) return (long long)j * g.per + lin;
     if (g.layout == 1) return lin * g.ncos + j;
-    const int bv = g.e2 == 1 ? 4 : 8;
-    const long long bk = (q0 >> 1) + (long long)(g.e0 >> 1) * ((q1 >> 1) + (long long)(g.e1 >> 1) * (q2 >> 1));
-    const int wi = (q0 & 1) + 2 * (q1 & 1) + 4 * (q2 & 1);
-    return (bk * bv + wi) * g.ncos + j;
+    if (g.layout == 3) return brick_index(g.ncos, g.e0 + 2, g.e1 + 2, g.e2, j, q0, q1, q2);
+    return brick_index(g.ncos, g.e0, g.e1, g.e2, j, q0, q1, q2);
 }
 
-__device__ __forceinline__ void lay_decode(const LayoutGeom &g, long long i, int &j, int &q0, int &q1, int &q2)
+__device__ __forceinline__ void brick_decode(long long i, int ncos, int e0, int e1, int e2, int &j, int &q0, int &q1,
+                                             int &q2)
 {
+    const int bv = e2 == 1 ? 4 : 8;
+    j = (int)(i % ncos);
+    const long long w = i / ncos;
+    const int wi = (int)(w % bv);
+    long long bk = w / bv;
+    q0 = (int)(bk % (e0 >> 1)) * 2 + (wi & 1);
+    bk /= (e0 >> 1);
+    q1 = (int)(bk % (e1 >> 1)) * 2 + ((wi >> 1) & 1);
+    bk /= (e1 >> 1);
+    q2 = (int)bk * 2 + (wi >> 2);
+}
+
+// (coset, grid index) of element i; false for the padding of layout 3
+__device__ __forceinline__ bool lay_decode(const LayoutGeom &g, long long i, int &j, int &q0, int &q1, int &q2)
+{
+    if (g.layout == 3) {
+        const long long copy_elems = (long long)g.ncos * (g.e0 + 2) * (g.e1 + 2) * g.e2;
+        const int c = (int)(i / copy_elems);
+        brick_decode(i % copy_elems, g.ncos, g.e0 + 2, g.e1 + 2, g.e2, j, q0, q1, q2);
+        q0 -= c & 1;
+        q1 -= c >> 1;
+        return q0 >= 0 && q0 < g.e0 && q1 >= 0 && q1 < g.e1;
+    }
     if (g.layout == 2) {
-        const int bv = g.e2 == 1 ? 4 : 8;
-        j = (int)(i % g.ncos);
-        const long long w = i / g.ncos;
-        const int wi = (int)(w % bv);
-        long long bk = w / bv;
-        q0 = (int)(bk % (g.e0 >> 1)) * 2 + (wi & 1);
-        bk /= (g.e0 >> 1);
-        q1 = (int)(bk % (g.e1 >> 1)) * 2 + ((wi >> 1) & 1);
-        bk /= (g.e1 >> 1);
-        q2 = (int)bk * 2 + (wi >> 2);
-        return;
+        brick_decode(i, g.ncos, g.e0, g.e1, g.e2, j, q0, q1, q2);
+        return true;
     }
     long long r;
     if (g.layout == 0) {
@@ -63,14 +86,16 @@ __device__ __forceinline__ void lay_decode(const LayoutGeom &g, long long i, int
     r /= g.e0;
     q1 = (int)(r % g.e1);
     q2 = (int)(r / g.e1);
+    return true;
 }
 
-// Source index of destination element i when the layout changes from s to d.
+// Source index of destination element i when the layout changes from s to d
+// (-1: padding of the destination, which gets 0).
 __device__ __forceinline__ long long relayout_src(long long i, const LayoutGeom &s, const LayoutGeom &d)
 {
     if (s.layout == d.layout) return i;
     int j, q0, q1, q2;
-    lay_decode(d, i, j, q0, q1, q2);
+    if (!lay_decode(d, i, j, q0, q1, q2)) return -1;
     return lay_index(s, j, q0, q1, q2);
 }
 
@@ -78,7 +103,8 @@ __global__ void convert_kernel(const void *src, int sdt, void *dst, int ddt, lon
                                LayoutGeom dg)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        double v = load_any(src, sdt, relayout_src(i, sg, dg));
+        const long long si = relayout_src(i, sg, dg);
+        const double v = si < 0 ? 0.0 : load_any(src, sdt, si);
         switch (ddt) {
         case DT_F32: ((float *)dst)[i] = (float)v; break;
         case DT_BF16: ((__nv_bfloat16 *)dst)[i] = __float2bfloat16_rn((float)v); break;
@@ -92,7 +118,10 @@ template <typename T>
 __global__ void relayout_kernel(const T *src, T *dst, long long n, LayoutGeom sg, LayoutGeom dg)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        dst[i] = src[relayout_src(i, sg, dg)];
+    {
+        const long long si = relayout_src(i, sg, dg);
+        dst[i] = si < 0 ? (T)0 : src[si];
+    }
 }
 
 constexpr int kDotBlocks = 296;   // 2 per SM on 148 SMs
@@ -245,7 +274,7 @@ cudaError_t convert(const void *src, int sdt, void *dst, int ddt, long long n, c
 cudaError_t convert_relayout(const void *src, int sdt, const LayoutGeom &sg, void *dst, int ddt, const LayoutGeom &dg,
                              cudaStream_t st)
 {
-    const long long n = (long long)dg.ncos * dg.per;
+    const long long n = layout_elems(dg);
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;
@@ -256,7 +285,7 @@ cudaError_t convert_relayout(const void *src, int sdt, const LayoutGeom &sg, voi
 cudaError_t relayout(const void *src, const LayoutGeom &sg, void *dst, const LayoutGeom &dg, int elem_bytes,
                      cudaStream_t st)
 {
-    const long long n = (long long)dg.ncos * dg.per;
+    const long long n = layout_elems(dg);
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;
@@ -267,6 +296,12 @@ cudaError_t relayout(const void *src, const LayoutGeom &sg, void *dst, const Lay
     else
         relayout_kernel<<<(unsigned)blocks, 256, 0, st>>>((const uint64_t *)src, (uint64_t *)dst, n, sg, dg);
     return cudaGetLastError();
+}
+
+long long layout_elems(const LayoutGeom &g)
+{
+    if (g.layout == 3) return 4LL * g.ncos * (g.e0 + 2) * (g.e1 + 2) * g.e2;
+    return (long long)g.ncos * g.per;
 }
 
 size_t dot_ws_bytes() { return kDotBlocks * sizeof(double) + 256; }

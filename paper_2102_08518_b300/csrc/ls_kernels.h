@@ -16,7 +16,10 @@ struct LayoutGeom {
     long long per;
     int e0, e1, e2;
 };
-// Conversion of all ncos * per elements from layout sg to layout dg (same
+// Elements a layout holds (ncos * per; the four shifted bricked copies of
+// layout 3 hold 4 ncos (e0 + 2)(e1 + 2) e2, their padding zero).
+long long layout_elems(const LayoutGeom &g);
+// Conversion of all layout_elems(dg) elements from layout sg to layout dg (same
 // cosets and extents), dtypes as in convert.
 cudaError_t convert_relayout(const void *src, int src_dt, const LayoutGeom &sg, void *dst, int dst_dt,
                              const LayoutGeom &dg, cudaStream_t st);

@@ -7,6 +7,7 @@
 // that reserve a fixed memory budget up front.  For them this file keeps the
 // sort's scratch in one statically sized device array that every GPU loading
 // the library holds until the process exits.
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -58,7 +59,7 @@ extern "C" ls_status ls_morton_sort_noalloc(const float *pts, int64_t n, const f
                                             int32_t *perm, uint32_t *keys_out, ls_stream stream)
 {
     if (n < 0 || (n > 0 && (!pts || !perm)) || !origin) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
-    if (!(cell > 0.0f)) return ls_fail(LS_ERR_INVALID_ARG, "cell must be positive");
+    if (!(cell > 0.0f) || !std::isfinite(cell)) return ls_fail(LS_ERR_INVALID_ARG, "cell must be positive");
     if (n > kMaxPoints)
         return ls_fail(LS_ERR_INVALID_ARG, "ls_morton_sort_noalloc sorts at most 262144 points (2^18); use "
                                            "ls_morton_sort for more");

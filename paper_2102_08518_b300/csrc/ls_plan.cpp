@@ -73,9 +73,9 @@ std::vector<BatchItem> make_items(const std::vector<BatchVol> &vols, const std::
 
 ls_status upload_items(ls_plan_s *p, const std::vector<BatchItem> &items)
 {
-    if (p->items_d) cudaFree(p->items_d);
+    if (p->items_d) ls::dev_free(p->items_d);
     p->items_d = nullptr;
-    if (cudaMalloc(&p->items_d, std::max<size_t>(1, items.size()) * sizeof(BatchItem)) != cudaSuccess) {
+    if (ls::dev_malloc(&p->items_d, std::max<size_t>(1, items.size()) * sizeof(BatchItem)) != cudaSuccess) {
         cudaGetLastError();
         return ls_fail(LS_ERR_OOM, "plan work list");
     }
@@ -157,7 +157,7 @@ ls_status ls_plan_create(int32_t n_vol, const ls_volume *vols, const float *cons
     p->block = var.block;
     p->grid = sms * per_sm;
     // device arrays: volume table and counters
-    if (cudaMalloc(&p->dev, al(n_vol * sizeof(BatchVol)) + 256) != cudaSuccess) {
+    if (ls::dev_malloc(&p->dev, al(n_vol * sizeof(BatchVol)) + 256) != cudaSuccess) {
         cudaGetLastError();
         cudaLibraryUnload(p->mod.lib);
         delete p;
@@ -251,8 +251,8 @@ ls_status ls_plan_status(ls_plan p, ls_stream stream)
 ls_status ls_plan_destroy(ls_plan p)
 {
     if (!p) return LS_OK;
-    if (p->items_d) cudaFree(p->items_d);
-    if (p->dev) cudaFree(p->dev);
+    if (p->items_d) ls::dev_free(p->items_d);
+    if (p->dev) ls::dev_free(p->dev);
     if (p->mod.lib) cudaLibraryUnload(p->mod.lib);
     delete p;
     return LS_OK;

@@ -18,6 +18,7 @@
 //               used); warps are combined by a per-digit prefix over warps, the
 //               tile is staged in shared memory in digit order and each digit's
 //               run is written to its global offset.
+#include <atomic>
 #include <cstdint>
 
 #include "ls_kernels.h"
@@ -377,13 +378,14 @@ cudaError_t radix_sort_pairs(uint32_t *keys, int32_t *vals, long long n, int nbi
     // digit counters 4x smaller
     const int rb = 8;
     // one wave: as many chunks as blocks of the scatter kernel fit on the GPU
-    static int waves[64] = {};
+    // (cached per device; any thread may fill an entry, all write the same value)
+    static std::atomic<int> waves[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         cudaGetLastError();
         dev = 0;
     }
-    int &wave = waves[dev];
+    int wave = waves[dev].load(std::memory_order_relaxed);
     if (wave == 0) {
         int sms = 0, per = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -395,6 +397,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys, int32_t *vals, long long n, int nbi
             per = 2;
         }
         wave = sms * per < kMaxChunks ? sms * per : kMaxChunks;
+        waves[dev].store(wave, std::memory_order_relaxed);
     }
     int nblk;
     long long chunk;

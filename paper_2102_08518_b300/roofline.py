@@ -11,12 +11,23 @@ from __future__ import annotations
 import numpy as np
 
 
-def stencil_indices(table, ext, pts: np.ndarray, layout: str = "coset") -> np.ndarray:
+def shift_masks(kernel_source: str):
+    """The copy-choice masks (x, y) a generated kernel for the shifted bricked
+    copies carries (see the generator's shift_rule)."""
+    import re
+    m = re.findall(r"const int s([xy]) = \(int\)\(\((\d+)ull >> ", kernel_source)
+    d = {k: int(v) for k, v in m}
+    return d["x"], d["y"]
+
+
+def stencil_indices(table, ext, pts: np.ndarray, layout: str = "coset", masks=None) -> np.ndarray:
     """Linear coefficient indices (n_points, n_sites) of every point's stencil
     in the volume layout ("coset": coset j's array after array j - 1;
     "interleaved": the cosets' values of one grid index adjacent; "bricked":
-    2 x 2 x 2 bricks of grid indices with the cosets adjacent inside); -1
-    where a site lies outside the arrays."""
+    2 x 2 x 2 bricks of grid indices with the cosets adjacent inside;
+    "bricked_shifted": the four shifted bricked copies, each point in the copy
+    the kernel's copy-choice masks pick); -1 where a site lies outside the
+    arrays."""
     spl = table.spline
     lat = spl.lattice
     D = lat.dim
@@ -50,6 +61,18 @@ def stencil_indices(table, ext, pts: np.ndarray, layout: str = "coset") -> np.nd
         sign = np.ones((n, D), dtype=np.int64)
         yref = y
     regions = np.array([table.region_of(r) for r in yref]) if len(table.regions) > 1 else np.zeros(n, int)
+    shift = np.zeros((n, 2), dtype=np.int64)
+    if layout == "bricked_shifted":
+        mx, my = masks
+        for i, mask in ((0, mx), (1, my)):
+            if table.fold == "hyperoctahedral":
+                r_i = np.argmax(order == i, axis=1)
+                neg = (sign[:, i] < 0).astype(np.int64)
+            else:
+                r_i = np.full(n, i)
+                neg = np.zeros(n, dtype=np.int64)
+            key = ((regions * 3 + r_i) * 2 + neg) * 4 + (k[:, i] & 3)
+            shift[:, i] = (np.array([mask >> int(q) for q in key], dtype=object) & 1).astype(np.int64)
     nsite = max(len(r.sites) for r in table.regions)
     out = np.full((n, nsite), -1, dtype=np.int64)
     per = int(np.prod(e))
@@ -80,6 +103,13 @@ def stencil_indices(table, ext, pts: np.ndarray, layout: str = "coset") -> np.nd
                 bk = idx[:, 0] // 2 + (e[0] // 2) * (idx[:, 1] // 2 + (e[1] // 2) * (i2 // 2))
                 w = idx[:, 0] % 2 + 2 * (idx[:, 1] % 2) + 4 * (i2 % 2)
                 lin = (bk * (8 if D == 3 else 4) + w) * C + cid
+            elif layout == "bricked_shifted":
+                sh = shift[m]
+                j0, j1, j2 = idx[:, 0] + sh[:, 0], idx[:, 1] + sh[:, 1], idx[:, 2]
+                bk = j0 // 2 + ((e[0] + 2) // 2) * (j1 // 2 + ((e[1] + 2) // 2) * (j2 // 2))
+                w = j0 % 2 + 2 * (j1 % 2) + 4 * (j2 % 2)
+                copy = C * (e[0] + 2) * (e[1] + 2) * e[2]
+                lin = (sh[:, 0] + 2 * sh[:, 1]) * copy + (bk * 8 + w) * C + cid
             elif layout == "interleaved":
                 lin = q * C + cid
             else:
@@ -88,8 +118,9 @@ def stencil_indices(table, ext, pts: np.ndarray, layout: str = "coset") -> np.nd
     return out
 
 
-def distinct_sectors_per_point(table, ext, pts: np.ndarray, elem_bytes: int = 4, layout: str = "coset") -> float:
-    idx = stencil_indices(table, ext, pts, layout)
+def distinct_sectors_per_point(table, ext, pts: np.ndarray, elem_bytes: int = 4, layout: str = "coset",
+                               masks=None) -> float:
+    idx = stencil_indices(table, ext, pts, layout, masks)
     sec = np.where(idx >= 0, (idx * elem_bytes) // 32, -1)
     sec.sort(axis=1)
     distinct = (np.diff(sec, axis=1) != 0).sum(axis=1) + 1 - (sec[:, 0] < 0)

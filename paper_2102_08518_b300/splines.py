@@ -27,7 +27,12 @@ TRILINEAR = Spline("trilinear", CC, tuple(d for d in _E for _ in range(2)), "par
 TRIQUADRATIC = Spline("triquadratic", CC, tuple(d for d in _E for _ in range(3)), "voronoi")
 BCC_LINEAR = Spline("bcc_linear", BCC, _BCC4, "voronoi")
 BCC_QUINTIC = Spline("bcc_quintic", BCC, _BCC4 + _BCC4, "voronoi")
+# the paper's other order-4 BCC spline (Sec. 5.1, "BCC quartic"): the four
+# diagonals plus the three axes at their shortest lattice length 2 e_i; seven
+# directions in 3D give degree 4, and no plane holds more than three of them,
+# so it reproduces cubics (approximation order 4)
+BCC_QUARTIC = Spline("bcc_quartic", BCC, _BCC4 + ((2, 0, 0), (0, 2, 0), (0, 0, 2)), "voronoi")
 FCC6 = Spline("fcc6", FCC, _FCC6, "voronoi")
 ZP = Spline("zp", Z2, ((1, 0), (0, 1), (1, 1), (-1, 1)), "voronoi")
 
-BY_NAME = {s.name: s for s in (TRICUBIC, TRILINEAR, TRIQUADRATIC, BCC_LINEAR, BCC_QUINTIC, FCC6, ZP)}
+BY_NAME = {s.name: s for s in (TRICUBIC, TRILINEAR, TRIQUADRATIC, BCC_LINEAR, BCC_QUINTIC, BCC_QUARTIC, FCC6, ZP)}

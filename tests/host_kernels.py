@@ -104,7 +104,9 @@ class HostKernels:
         hess = np.zeros(n * nh, np.float32) if need_hess else None
         e = list(ext) + [1] * (3 - len(ext))
         P = int(np.prod(ext))
-        cs, cu = {"coset": (P, 1), "interleaved": (1, n_cosets), "bricked": (1, n_cosets)}[layout]
+        copy = n_cosets * (e[0] + 2) * (e[1] + 2) * e[2]
+        cs, cu = {"coset": (P, 1), "interleaved": (1, n_cosets), "bricked": (1, n_cosets),
+                  "bricked_shifted": (copy, n_cosets)}[layout]
         coef = np.ascontiguousarray(coef)
         ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
         fn = getattr(self.lib, "host_" + what)

@@ -18,12 +18,12 @@ import workloads
 from oracle import specs as ospecs
 
 from tests.host_kernels import HostKernels, generated_source
-from tests.test_gpu_layout import brick_np, interleave_np
+from tests.test_gpu_layout import brick_np, brick_shifted_np, interleave_np
 
 SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
-        "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6, "zp": ospecs.zp2d}
+        "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6, "zp": ospecs.zp2d}
 EXT = {"tricubic": (8, 6, 6), "trilinear": (6, 6, 4), "triquadratic": (6, 8, 6), "bcc_linear": (6, 6, 4),
-       "bcc_quintic": (8, 6, 6), "fcc6": (6, 6, 6), "zp": (12, 10)}
+       "bcc_quintic": (8, 6, 6), "bcc_quartic": (6, 8, 6), "fcc6": (6, 6, 6), "zp": (12, 10)}
 TOL, GTOL, HTOL = 2e-6, 1e-5, 1e-4
 
 
@@ -39,16 +39,23 @@ def _case(name, n=1500, seed=2):
 
 def _layout(coef, C, ext, layout):
     flat = coef.ravel()
+    if layout == "bricked_shifted":
+        return brick_shifted_np(flat, C, ext)
     return {"coset": flat, "interleaved": interleave_np(flat, C), "bricked": brick_np(flat, C, ext)}[layout]
 
 
+BRICK = {"coset": 0, "interleaved": 0, "bricked": 1, "bricked_shifted": 2}
+
+
 @pytest.mark.parametrize("name", list(SPEC))
-@pytest.mark.parametrize("layout", ["coset", "interleaved", "bricked"])
+@pytest.mark.parametrize("layout", ["coset", "interleaved", "bricked", "bricked_shifted"])
 def test_value_and_gradient(name, layout):
+    if layout == "bricked_shifted" and name == "zp":
+        pytest.skip("the shifted bricked copies are 3D only")
     lat, ext, C, coef, pts = _case(name)
     spec = SPEC[name]().with_extent(ext)
     want, wgrad = oracle.eval_sum_grad(spec, coef.astype(np.float64).ravel(), pts.astype(np.float64))
-    hk = HostKernels(name, **({"brick": 1} if layout == "bricked" else {}))
+    hk = HostKernels(name, **({"brick": BRICK[layout]} if BRICK[layout] else {}))
     c = _layout(coef, C, ext, layout)
     f = hk.eval(pts, c, ext, layout, C)
     v, g = hk.eval_grad(pts, c, ext, layout, C)

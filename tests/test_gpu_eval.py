@@ -16,11 +16,12 @@ pytestmark = pytest.mark.gpu
 
 TOL = 2e-6
 ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
-               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6,
+               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6,
                "zp": ospecs.zp2d}
 SMALL_EXT = {"tricubic": (12, 11, 10), "trilinear": (9, 12, 10), "triquadratic": (11, 9, 12),
-             "bcc_linear": (7, 6, 8), "bcc_quintic": (8, 7, 6), "fcc6": (7, 8, 6), "zp": (13, 11)}
-ALL_NAMES = ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "fcc6", "zp"]
+             "bcc_linear": (7, 6, 8), "bcc_quintic": (8, 7, 6), "bcc_quartic": (7, 8, 7), "fcc6": (7, 8, 6),
+             "zp": (13, 11)}
+ALL_NAMES = ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "bcc_quartic", "fcc6", "zp"]
 _SPLINES = {}
 
 
@@ -65,7 +66,8 @@ def test_small_volume_every_point(name, n):
     assert np.max(np.abs(got - want)) <= TOL * np.abs(coef).max()
 
 
-@pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "fcc6"])
+@pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "bcc_quartic",
+                                  "fcc6"])
 def test_special_points(name):
     """Lattice sites, half-integers, mirror and BSP planes, and the edges."""
     lat = workloads.SPLINE_LATTICE[name]

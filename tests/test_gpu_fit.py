@@ -17,7 +17,7 @@ from oracle import specs as ospecs
 
 pytestmark = pytest.mark.gpu
 
-ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_quintic": ospecs.bcc_quintic, "bcc_linear": ospecs.bcc_linear,
+ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "bcc_linear": ospecs.bcc_linear,
                "fcc6": ospecs.fcc6}
 
 

@@ -11,7 +11,7 @@ from oracle import specs as ospecs
 pytestmark = pytest.mark.gpu
 
 ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_linear": ospecs.bcc_linear,
-               "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6}
+               "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6}
 TOL = 2e-6
 
 

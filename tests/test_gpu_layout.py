@@ -21,13 +21,16 @@ pytestmark = pytest.mark.gpu
 
 TOL = 2e-6
 ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
-               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6,
+               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6,
                "zp": ospecs.zp2d}
 # whole bricks (even extents), so both layouts take them
 SMALL_EXT = {"tricubic": (12, 10, 8), "trilinear": (8, 10, 6), "triquadratic": (12, 8, 10),
-             "bcc_linear": (8, 6, 8), "bcc_quintic": (8, 6, 6), "fcc6": (8, 8, 6), "zp": (12, 10)}
-NAMES = ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "fcc6", "zp"]
+             "bcc_linear": (8, 6, 8), "bcc_quintic": (8, 6, 6), "bcc_quartic": (6, 8, 6), "fcc6": (8, 8, 6),
+             "zp": (12, 10)}
+NAMES = ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "bcc_quartic", "fcc6", "zp"]
 LAYOUTS = ["interleaved", "bricked"]
+# the evaluation kernels also read the shifted bricked copies (3D)
+EVAL_LAYOUTS = LAYOUTS + ["bricked_shifted"]
 
 
 def n_cosets(name):
@@ -56,6 +59,21 @@ def brick_np(coef, C, ext):
     return np.ascontiguousarray(a.transpose(1, 3, 2, 4, 0)).ravel()
 
 
+def brick_shifted_np(coef, C, ext):
+    """coset-major -> the four shifted bricked copies: copy s0 + 2 s1 holds grid
+    index i at (i0 + s0, i1 + s1, i2) of a bricked array over extents
+    (e0 + 2, e1 + 2, e2), zero elsewhere."""
+    e0, e1, e2 = ext
+    a = coef.reshape(C, e2, e1, e0)
+    out = []
+    for c in range(4):
+        s0, s1 = c & 1, c >> 1
+        pad = np.zeros((C, e2, e1 + 2, e0 + 2), dtype=coef.dtype)
+        pad[:, :, s1:s1 + e1, s0:s0 + e0] = a
+        out.append(brick_np(pad.ravel(), C, (e0 + 2, e1 + 2, e2)))
+    return np.concatenate(out)
+
+
 def unbrick_np(arr, C, ext):
     if len(ext) == 3:
         e0, e1, e2 = ext
@@ -67,6 +85,8 @@ def unbrick_np(arr, C, ext):
 
 
 def to_layout_np(coef, C, ext, layout):
+    if layout == "bricked_shifted":
+        return brick_shifted_np(coef, C, ext)
     return interleave_np(coef, C) if layout == "interleaved" else brick_np(coef, C, ext)
 
 
@@ -77,8 +97,8 @@ def from_layout_np(arr, C, ext, layout):
 def ivolume(name, ext, coef_np, dtype="f32", layout="interleaved", **kw):
     from paper_2102_08518_b300.api import Spline, Volume, TORCH_DTYPES
     c = torch.from_numpy(to_layout_np(coef_np, n_cosets(name), ext, layout)).to("cuda", TORCH_DTYPES[dtype])
-    if layout == "bricked":
-        kw["brick"] = 1
+    if layout in ("bricked", "bricked_shifted"):
+        kw["brick"] = 1 if layout == "bricked" else 2
     return Volume(Spline(name, dtype, **kw), ext, c.contiguous(), layout=layout)
 
 
@@ -121,13 +141,20 @@ def test_relayout_matches_numpy_maps(C, ext, dtype):
         assert np.array_equal(bk.cpu().numpy(), brick_np(ref, C, ext))
         assert torch.equal(relayout(bk, C, ext, to="interleaved", src="bricked"), il)
         assert torch.equal(relayout(bk, C, ext, to="coset", src="bricked"), src)
+        if len(ext) == 3:
+            sh = relayout(src, C, ext, to="bricked_shifted")
+            assert np.array_equal(sh.cpu().numpy(), brick_shifted_np(ref, C, ext))
+            assert torch.equal(relayout(sh, C, ext, to="coset", src="bricked_shifted"), src)
+            assert torch.equal(relayout(il, C, ext, to="bricked_shifted", src="interleaved"), sh)
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("layout", EVAL_LAYOUTS)
 @pytest.mark.parametrize("name", NAMES)
 @pytest.mark.parametrize("n", [1, 33, 5003])
 def test_interleaved_eval_every_point(name, n, layout):
     """Points inside and beyond the arrays (unchecked and bounds-checked gathers)."""
+    if layout == "bricked_shifted" and name == "zp":
+        pytest.skip("the shifted bricked copies are 3D only")
     lat = workloads.SPLINE_LATTICE[name]
     ext = SMALL_EXT[name]
     coef = workloads.coef_uniform(lat, ext, seed=101)
@@ -139,9 +166,11 @@ def test_interleaved_eval_every_point(name, n, layout):
     assert np.max(np.abs(got - want)) <= TOL * np.abs(coef).max()
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("layout", EVAL_LAYOUTS)
 @pytest.mark.parametrize("name", NAMES)
 def test_interleaved_gradient(name, layout):
+    if layout == "bricked_shifted" and name == "zp":
+        pytest.skip("the shifted bricked copies are 3D only")
     lat = workloads.SPLINE_LATTICE[name]
     ext = SMALL_EXT[name]
     coef = workloads.coef_uniform(lat, ext, seed=102)
@@ -270,7 +299,7 @@ def test_interleaved_cg_fit_equals_coset_major_fit(layout):
     assert np.allclose(ha, hb, rtol=1e-3)
 
 
-@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("layout", EVAL_LAYOUTS)
 @pytest.mark.parametrize("name", ["bcc_linear", "bcc_quintic"])
 def test_interleaved_bcc_full_size_sampled(name, layout):
     """BCC 2 x 128^3, 2^24 uniform and 2^24 ray points, in the autotuned launch
@@ -302,3 +331,35 @@ def test_bricked_layout_rejections():
         Volume(Spline("bcc_linear", "f32"), (8, 6, 6), layout="bricked")
     with pytest.raises(_abi.LsError):
         Volume(Spline("bcc_linear", "f32", brick=1), (8, 6, 6), layout="interleaved")
+
+
+def test_shifted_copies_are_read_only():
+    """The adjoint and the fit write coefficients; the shifted copies hold four
+    of each, so those calls refuse them."""
+    name, ext = "bcc_quintic", SMALL_EXT["bcc_quintic"]
+    coef = workloads.coef_uniform("bcc", ext, seed=111)
+    vol = ivolume(name, ext, coef, layout="bricked_shifted")
+    p = torch.zeros(8, 3, device="cuda")
+    with pytest.raises(RuntimeError, match="read-only"):
+        vol.adjoint(p, torch.ones(8, device="cuda"))
+
+
+def test_shifted_copies_hessian_and_batched_plan():
+    from paper_2102_08518_b300.api import Plan, Spline, Volume
+    name, ext = "bcc_quintic", SMALL_EXT["bcc_quintic"]
+    coef = workloads.coef_uniform("bcc", ext, seed=112)
+    lo, hi = workloads.bounding_box("bcc", ext)
+    pts = workloads.points_uniform(3000, lo - 1.0, hi + 1.0, seed=113)
+    p = torch.from_numpy(pts).cuda()
+    vs = ivolume(name, ext, coef, layout="bricked_shifted")
+    vc = Volume(Spline(name, "f32"), ext, torch.from_numpy(coef).cuda())
+    f1, g1, h1 = vs.eval_hess(p)
+    f2, g2, h2 = vc.eval_hess(p)
+    cmax = float(np.abs(coef).max())
+    assert torch.max(torch.abs(f1 - f2)) <= 2 * TOL * cmax
+    assert torch.max(torch.abs(h1 - h2)) <= 2e-4 * cmax
+    out = torch.full((len(pts),), float("nan"), device="cuda")
+    plan = Plan([vs], [p], [out], tile=256)
+    plan.launch()
+    plan.status()
+    assert torch.equal(out, vs.eval(p))

@@ -217,7 +217,7 @@ def test_linear_reproduction(name):
     assert np.max(np.abs(v - (pts @ a + b))) < 1e-11
 
 
-@pytest.mark.parametrize("name", ["tricubic", "triquadratic", "bcc_quintic", "fcc6"])
+@pytest.mark.parametrize("name", ["tricubic", "triquadratic", "bcc_quintic", "bcc_quartic", "fcc6"])
 def test_quadratic_reproduction_with_moment_defect(name):
     spec = _small(ALL[name]())
     sites = _sites_and_grid(spec)
@@ -232,7 +232,7 @@ def test_quadratic_reproduction_with_moment_defect(name):
     assert np.max(np.abs(v - want)) < 1e-10
 
 
-@pytest.mark.parametrize("name", ["tricubic", "bcc_quintic"])
+@pytest.mark.parametrize("name", ["tricubic", "bcc_quintic", "bcc_quartic"])
 def test_cubic_reproduction_with_moment_defect(name):
     """Order-4 splines reproduce cubics up to the (linear) second-moment term;
     odd central moments vanish by symmetry."""
@@ -316,18 +316,41 @@ def test_support_and_positivity(name):
 
 
 @pytest.mark.parametrize("name,det", [("tricubic", 1.0), ("trilinear", 1.0), ("triquadratic", 1.0),
-                                      ("bcc_linear", 4.0), ("bcc_quintic", 4.0), ("fcc6", 2.0)])
+                                      ("bcc_linear", 4.0), ("bcc_quintic", 4.0), ("bcc_quartic", 4.0),
+                                      ("fcc6", 2.0)])
 def test_integral_equals_lattice_density(name, det):
     """integral phi = |det L| (midpoint rule on a fine grid)."""
     spec = specs.ALL_3D[name]()
-    h = 1.0 / 8.0 if name != "bcc_quintic" else 1.0 / 6.0
-    R = 2.0 if name in ("tricubic", "trilinear", "triquadratic", "bcc_linear", "fcc6") else 4.0
+    h = 1.0 / 8.0 if name not in ("bcc_quintic", "bcc_quartic") else 1.0 / 6.0
+    R = {"bcc_quintic": 4.0, "bcc_quartic": 3.0}.get(name, 2.0)
     g = np.arange(-R + h / 2, R, h)
     Y = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
     # shift by a generic offset so that no sample sits on a knot plane
     Y = Y + np.array([1e-3, 2e-3, 3e-3])
     total = oracle.phi(spec, Y).sum() * h ** 3
     assert abs(total - det) < 2e-3 * det
+
+
+@pytest.mark.parametrize("name,degree", [("bcc_linear", 1), ("fcc6", 3), ("bcc_quartic", 4), ("bcc_quintic", 5)])
+def test_piece_degree(name, degree):
+    """Each polynomial piece has degree |Xi| - 3 (the "quartic" BCC spline: 4):
+    along short segments inside one piece the (degree + 1)-th differences
+    vanish and the degree-th do not.  Segments that cross a knot plane are rare
+    and only fail the first half, so the test asks most segments (60 %) to pass."""
+    spec = specs.ALL_3D[name]()
+    rng = np.random.default_rng(40)
+    h = 2e-2
+    ok = 0
+    n = 40
+    for _ in range(n):
+        y0 = rng.uniform(-1.0, 1.0, 3)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        v = oracle.phi(spec, y0[None, :] + h * np.arange(degree + 2)[:, None] * d[None, :])
+        top = np.min(np.abs(np.diff(v, degree)))
+        if abs(np.diff(v, degree + 1)[0]) <= 1e-3 * top and top >= 1e-12:
+            ok += 1
+    assert ok >= 0.6 * n, ok
 
 
 def test_bcc_linear_interpolates():
@@ -514,7 +537,7 @@ def test_hessian_matches_central_differences_of_gradient(name):
     assert np.max(np.abs(H[smooth] - fd[smooth])) < 1e-8
 
 
-@pytest.mark.parametrize("name", ["tricubic", "triquadratic", "bcc_quintic", "fcc6"])
+@pytest.mark.parametrize("name", ["tricubic", "triquadratic", "bcc_quintic", "bcc_quartic", "fcc6"])
 def test_hessian_of_reproduced_quadratic_is_exact(name):
     """Splines of order >= 3 reproduce quadratics up to a constant (the moment
     defect), so the Hessian of sum_n p(n) phi(x - n) is the Hessian of p."""
@@ -529,7 +552,7 @@ def test_hessian_of_reproduced_quadratic_is_exact(name):
     assert np.max(np.abs(H - Q[None])) < 1e-9
 
 
-@pytest.mark.parametrize("name", ["bcc_quintic", "fcc6", "triquadratic"])
+@pytest.mark.parametrize("name", ["bcc_quintic", "bcc_quartic", "fcc6", "triquadratic"])
 def test_hessian_transforms_with_the_lattice_symmetries(name):
     """phi(R y) = phi(y) for the signed permutations R, so H(R y) = R H(y) R^T."""
     spec = specs.ALL_3D[name]()

@@ -15,7 +15,7 @@ from tests.table_eval import eval_separable, eval_table
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
-               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "fcc6": ospecs.fcc6,
+               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6,
                "zp": ospecs.zp2d}
 
 
@@ -38,7 +38,8 @@ def test_zp_table_reproduces_fig1():
     assert got == want
 
 
-@pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
+@pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "bcc_quartic",
+                                  "fcc6", "zp"])
 def test_table_weights_partition_unity_exactly(name):
     t = table(name)
     for reg in t.regions:
@@ -61,9 +62,12 @@ def test_structural_facts_from_the_paper():
     # the Cartesian comparison splines: trilinear 8 lookups (Sec. 5.1, order 2), triquadratic 27
     assert len(table("trilinear").regions[0].sites) == 8
     assert len(table("triquadratic").regions[0].sites) == 27
+    # the seven-direction BCC spline: quartic pieces (degree |Xi| - 3)
+    assert table("bcc_quartic").degree == 4
 
 
-@pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])
+@pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "bcc_quartic",
+                                  "fcc6", "zp"])
 def test_table_matches_oracle_by_brute_force(name):
     """Algorithm 1 over the table in FP64 vs the oracle's naive sum, tiny grids,
     points everywhere (inside, near and beyond the edges)."""
@@ -82,7 +86,7 @@ def test_table_matches_oracle_by_brute_force(name):
 
 def test_table_matches_oracle_on_symmetry_planes():
     """Points exactly on the folding mirrors and the FCC BSP plane."""
-    for name in ("bcc_quintic", "fcc6"):
+    for name in ("bcc_quintic", "bcc_quartic", "fcc6"):
         t = table(name)
         lat = workloads.SPLINE_LATTICE[name]
         ext = (6, 6, 6)
