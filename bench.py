@@ -794,12 +794,15 @@ def extra_tricubic_64(torch, dev, vols, pts, outs):
 def extra_paper_orders(torch, dev, vols, pts, outs):
     """The paper's per-order comparisons (Sec. 5.1: order 2 trilinear vs BCC
     linear, order 3 triquadratic vs FCC six-direction, order 4 tricubic vs the
-    BCC quintic) on its equal-memory grids: CC 128^3, BCC 202^3 (2 x 101^3 sites),
-    FCC 161^3 (4 x 81^3 sites); 2^24 uniform points in each inner box, FP32,
-    interleaved cosets, the default kernel variant."""
-    from paper_2102_08518_b300.api import Spline, Volume, relayout
+    BCC quintic and quartic; Sec. 5.2: the second-order Voronoi splines on BCC
+    and FCC against the trilinear) on its equal-memory grids: CC 128^3, BCC
+    202^3 (2 x 101^3 sites), FCC 161^3 (4 x 81^3 sites); 2^24 uniform points in
+    each inner box, FP32, interleaved cosets, the default kernel variant (and
+    the branchy one where a spline has several reference sub-regions)."""
+    from paper_2102_08518_b300.api import Spline, Volume, relayout, table
     grids = {"trilinear": ("cc", (128,) * 3), "triquadratic": ("cc", (128,) * 3), "tricubic": ("cc", (128,) * 3),
-             "bcc_linear": ("bcc", (101,) * 3), "bcc_quintic": ("bcc", (101,) * 3), "fcc6": ("fcc", (81,) * 3)}
+             "bcc_linear": ("bcc", (101,) * 3), "bcc_quintic": ("bcc", (101,) * 3), "bcc_quartic": ("bcc", (101,) * 3),
+             "fcc6": ("fcc", (81,) * 3), "voronoi2_bcc": ("bcc", (101,) * 3), "voronoi2_fcc": ("fcc", (81,) * 3)}
     n = 1 << 24
     res = {"workload": "2^24 uniform points per spline; CC 128^3, BCC 2x101^3, FCC 4x81^3 coefficients U[-1,1]"}
     out = torch.empty(n, device=dev)
@@ -813,7 +816,13 @@ def extra_paper_orders(torch, dev, vols, pts, outs):
         ms = time_ms(torch, lambda: vol.eval(p, out))
         info = sp.info()
         res[name] = {"gpoints_s": round(n / ms / 1e6, 3), "ms": round(ms, 4), "sites": info["n_sites"],
-                     "fma_per_point": info["fma_value"]}
+                     "fma_per_point": info["fma_value"], "reference_subregions": len(table(name).regions)}
+        if len(table(name).regions) > 1:
+            # the paper's branchy alternative to evaluating every sub-region and selecting
+            vbr = Volume(Spline(name, "f32", branchy=1), ext, c, layout="interleaved")
+            msr = time_ms(torch, lambda: vbr.eval(p, out))
+            res[name]["branchy_gpoints_s"] = round(n / msr / 1e6, 3)
+            del vbr
         if lat == "cc":
             # the paper's linear texture fetch (Sec. 4.4.1): pairs of sites per hardware lerp
             cl = relayout(c, 1, ext, to="coset", src="interleaved")
@@ -831,11 +840,18 @@ def extra_paper_orders(torch, dev, vols, pts, outs):
             vb = Volume(Spline(name, "f32", brick=1), ext, cb, layout="bricked")
             msb = time_ms(torch, lambda: vb.eval(p, out))
             res[name]["bricked_gpoints_s"] = round(n / msb / 1e6, 3)
-            del cb, vb
+            cs = relayout(c, ncos, ext, to="bricked_shifted", src="interleaved")
+            vs = Volume(Spline(name, "f32", brick=2), ext, cs, layout="bricked_shifted")
+            mss = time_ms(torch, lambda: vs.eval(p, out))
+            res[name]["bricked_shifted_gpoints_s"] = round(n / mss / 1e6, 3)
+            del cb, vb, cs, vs
         del c, p, vol
     res["order2_bcc_linear_vs_trilinear"] = round(res["bcc_linear"]["gpoints_s"] / res["trilinear"]["gpoints_s"], 3)
     res["order3_fcc6_vs_triquadratic"] = round(res["fcc6"]["gpoints_s"] / res["triquadratic"]["gpoints_s"], 3)
     res["order4_bcc_quintic_vs_tricubic"] = round(res["bcc_quintic"]["gpoints_s"] / res["tricubic"]["gpoints_s"], 3)
+    res["order4_bcc_quartic_vs_tricubic"] = round(res["bcc_quartic"]["gpoints_s"] / res["tricubic"]["gpoints_s"], 3)
+    for v in ("voronoi2_bcc", "voronoi2_fcc"):
+        res[f"order2_{v}_vs_trilinear"] = round(res[v]["gpoints_s"] / res["trilinear"]["gpoints_s"], 3)
     return res
 
 
@@ -885,9 +901,10 @@ def extra_cg(torch, dev, vols, pts, outs):
     return res
 
 
-PROFILE_CASES = ("fcc6_eval", "quintic_eval_interleaved", "quintic_eval_bricked", "quintic_adjoint_atomic", "quintic_adjoint_fixed", "quintic_hessian",
-                 "tricubic_linear_fetch", "morton_sort", "morton_sort_2e24", "fcc6_eval_sorted",
-                 "fcc6_eval_staged")
+PROFILE_CASES = ("fcc6_eval", "quintic_eval_interleaved", "quintic_eval_bricked", "quintic_eval_bricked_shifted",
+                 "quintic_eval_rays_interleaved", "linear_eval_interleaved", "linear_eval_rays_interleaved",
+                 "quintic_adjoint_atomic", "quintic_adjoint_fixed", "quintic_hessian", "tricubic_linear_fetch",
+                 "morton_sort", "morton_sort_2e24", "fcc6_eval_sorted", "fcc6_eval_staged")
 
 
 def run_profile_case(name: str):
@@ -910,12 +927,20 @@ def run_profile_case(name: str):
             p = permute_rows(p, morton_sort(p, cell=1.0))
         out = torch.empty(n, device=dev)
         fn = lambda: vol.eval(p, out)
-    elif name.startswith("quintic_eval_"):
+    elif name.startswith("quintic_eval_") or name.startswith("linear_eval_"):
+        # the step's case in one layout, with the variant the autotuner recorded
+        # for it (the kernel the benchmark times), else the default variant
+        from paper_2102_08518_b300.api import LAYOUT_BRICK, autotune_record
+        sp_name = "bcc_quintic" if name.startswith("quintic") else "bcc_linear"
         coef_np, pts_np = make_inputs()
-        lay = name.rsplit("_", 1)[1]
+        rest = name.split("_eval_", 1)[1]
+        ps = "rays" if rest.startswith("rays_") else "uniform"
+        lay = rest[len("rays_"):] if ps == "rays" else rest
         c = relayout(torch.from_numpy(coef_np).to(dev), 2, EXT, to=lay)
-        vol = Volume(Spline("bcc_quintic", "f32", brick=int(lay == "bricked")), EXT, c, layout=lay)
-        p = torch.from_numpy(pts_np["uniform"]).to(dev)
+        p = torch.from_numpy(pts_np[ps]).to(dev)
+        rec = autotune_record(sp_name, "f32", EXT, [p], tag=f"bcc_step_{ps}", layout=lay)
+        var = dict(rec["variant"]) if rec else ({"brick": LAYOUT_BRICK[lay]} if LAYOUT_BRICK[lay] else {})
+        vol = Volume(Spline(sp_name, "f32", **var), EXT, c, layout=lay)
         out = torch.empty(n, device=dev)
         fn = lambda: vol.eval(p, out)
     elif name.startswith("quintic_"):

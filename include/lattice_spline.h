@@ -160,7 +160,7 @@ typedef struct {
     const double *planes;
     int32_t bsp_mod;                   /* >= 1 */
     const int8_t *sigma;               /* bsp_mod entries, -1 = unused */
-    int32_t n_ref;                     /* 1..4 */
+    int32_t n_ref;                     /* 1..15 */
     const ls_ref_region *ref;
     const ls_axis_factor *separable;
 } ls_spline_desc;
@@ -185,9 +185,8 @@ typedef struct {
                                           the resident warps per SM without taking L1 away (no
                                           recompilation) */
     int32_t brick;                     /* 1: the kernels address LS_LAYOUT_BRICKED volumes (and only
-                                          those); 2: LS_LAYOUT_BRICKED_SHIFTED volumes (3D, at most
-                                          two reference sub-regions); 0: the linear layouts
-                                          (coset-major, interleaved) */
+                                          those); 2: LS_LAYOUT_BRICKED_SHIFTED volumes (3D); 0: the
+                                          linear layouts (coset-major, interleaved) */
     int32_t pipeline;                  /* 1: the value kernel issues the gathers of a thread's next
                                           point before evaluating the current one (software
                                           pipelining; non-separable tables; pts_per_thread ignored) */

@@ -174,8 +174,16 @@ def phi_grad(spec: OrcSpec, y):
     return out, g
 
 
+def _is_voronoi(spec) -> bool:
+    return type(spec).__name__ == "VoronoiSpec"
+
+
 def eval_sum(spec: OrcSpec, coef, pts, nthreads: int = 0) -> np.ndarray:
-    """Naive convolution sum (Eq. 1) at points pts (n x dim) in FP64."""
+    """Naive convolution sum (Eq. 1) at points pts (n x dim) in FP64 (Voronoi
+    splines: oracle.voronoi)."""
+    if _is_voronoi(spec):
+        from . import voronoi
+        return voronoi.eval_sum(spec, coef, pts)
     c = _f64(coef).ravel()
     if c.size != spec.n_coef():
         raise ValueError(f"coef has {c.size} values, spec wants {spec.n_coef()}")
@@ -190,6 +198,9 @@ def eval_sum(spec: OrcSpec, coef, pts, nthreads: int = 0) -> np.ndarray:
 
 def eval_sum_grad(spec: OrcSpec, coef, pts, nthreads: int = 0):
     """f and grad f (n x dim) of the naive convolution sum in FP64."""
+    if _is_voronoi(spec):
+        from . import voronoi
+        return voronoi.eval_sum_grad(spec, coef, pts)
     c = _f64(coef).ravel()
     p = _f64(pts).reshape(-1, spec.dim)
     out = np.zeros(len(p))
@@ -228,6 +239,9 @@ def eval_sum_hess(spec: OrcSpec, coef, pts, nthreads: int = 0) -> np.ndarray:
 
 def adjoint(spec: OrcSpec, pts, g) -> np.ndarray:
     """dc_n = sum_p g_p phi(x_p - n), same layout as the coefficients."""
+    if _is_voronoi(spec):
+        from . import voronoi
+        return voronoi.adjoint(spec, pts, g)
     p = _f64(pts).reshape(-1, spec.dim)
     gg = _f64(g).ravel()
     dc = np.zeros(spec.n_coef())

@@ -13,6 +13,7 @@ Lattices are stored as unions of Cartesian cosets of scale*Z^s:
   Z^2 for the ZP element                      (scale 1, |det L| = 1)
 """
 from .lib import OrcSpec
+from . import voronoi as _voronoi
 
 E1, E2, E3 = (1, 0, 0), (0, 1, 0), (0, 0, 1)
 
@@ -60,6 +61,16 @@ def fcc6() -> OrcSpec:
     return OrcSpec(3, FCC_DIRS, 2.0, 2, FCC_COSETS, (1, 1, 1), 0, "fcc6")
 
 
+def voronoi2_bcc():
+    """Second-order Voronoi spline on BCC (oracle.voronoi: cell overlap volume)."""
+    return _voronoi.BCC
+
+
+def voronoi2_fcc():
+    """Second-order Voronoi spline on FCC (oracle.voronoi: cell overlap volume)."""
+    return _voronoi.FCC
+
+
 def zp2d() -> OrcSpec:
     """ZP element of Fig. 1: directions (1,0),(0,1),(1,1),(-1,1) on Z^2."""
     return OrcSpec(2, ((1, 0), (0, 1), (1, 1), (-1, 1)), 1.0, 1, ((0, 0),), (1, 1, 1), 0,
@@ -68,3 +79,5 @@ def zp2d() -> OrcSpec:
 
 ALL_3D = {"tricubic": tricubic, "trilinear": trilinear, "triquadratic": triquadratic,
           "bcc_linear": bcc_linear, "bcc_quintic": bcc_quintic, "bcc_quartic": bcc_quartic, "fcc6": fcc6}
+# the Voronoi splines (their own oracle: oracle.voronoi)
+VORONOI = {"voronoi2_bcc": voronoi2_bcc, "voronoi2_fcc": voronoi2_fcc}

@@ -17,6 +17,8 @@ LS_OK = 0
 STATUS_NAMES = {0: "LS_OK", 1: "LS_ERR_INVALID_ARG", 2: "LS_ERR_BAD_TABLE", 3: "LS_ERR_UNSUPPORTED",
                 4: "LS_ERR_OOM", 5: "LS_ERR_CUDA", 6: "LS_ERR_COMPILE", 7: "LS_ERR_TIMEOUT",
                 8: "LS_ERR_DEVICE"}
+(LS_ERR_INVALID_ARG, LS_ERR_BAD_TABLE, LS_ERR_UNSUPPORTED, LS_ERR_OOM, LS_ERR_CUDA, LS_ERR_COMPILE, LS_ERR_TIMEOUT,
+ LS_ERR_DEVICE) = range(1, 9)
 # ls_dtype
 LS_F32, LS_BF16, LS_F16, LS_F64 = 0, 1, 2, 3
 # ls_roe / ls_fold

@@ -128,7 +128,7 @@ ls_status copy_desc(const ls_spline_desc *d, ls::Table &t)
                 if (d->generator[3 * c + r] != (r == c ? 1.0 : 0.0))
                     return ls_fail(LS_ERR_UNSUPPORTED, "parallelepiped ROE needs L = I");
     }
-    if (d->n_ref < 1 || d->n_ref > 4) return ls_fail(LS_ERR_UNSUPPORTED, "n_ref must be 1..4");
+    if (d->n_ref < 1 || d->n_ref > 15) return ls_fail(LS_ERR_UNSUPPORTED, "n_ref must be 1..15");
     if (d->n_planes < 0 || d->n_planes > 4) return ls_fail(LS_ERR_UNSUPPORTED, "n_planes must be 0..4");
     if (d->bsp_mod < 1 || d->bsp_mod > 16) return ls_fail(LS_ERR_UNSUPPORTED, "bsp_mod must be 1..16");
     if (d->n_planes > 0 && !d->planes) return ls_fail(LS_ERR_INVALID_ARG, "planes is NULL");
@@ -417,10 +417,9 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
             return ls_fail(LS_ERR_INVALID_ARG, why);
         }
     }
-    if (s->var.brick == 2 && (s->table.dim != 3 || s->table.ref.size() > 2)) {
+    if (s->var.brick == 2 && s->table.dim != 3) {
         delete s;
-        return ls_fail(LS_ERR_UNSUPPORTED, "brick = 2 (shifted bricked copies) needs a 3D table with at most two "
-                                           "reference sub-regions");
+        return ls_fail(LS_ERR_UNSUPPORTED, "brick = 2 (shifted bricked copies) needs a 3D table");
     }
     if (s->var.wait_probe != 0 && (s->var.wait_probe != 1 || s->var.producers <= 0)) {
         delete s;

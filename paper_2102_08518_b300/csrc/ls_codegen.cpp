@@ -305,7 +305,8 @@ ShiftRule shift_rule(const Table &t, const std::vector<std::vector<I3>> &region_
                     }
                     const int *p = perms[pi];           // reference axis r lands on Cartesian axis p[r]
                     const int g[3] = {sg & 1, (sg >> 1) & 1, (sg >> 2) & 1};   // sign bit of reference axis r
-                    Cls c{kq[0], kq[1], 0, 0, 0, 0, (int)psi, {0, 0, 0, 0}};
+                    // more than two sub-regions do not fit the 64-bit key: the rule then ignores psi
+                    Cls c{kq[0], kq[1], 0, 0, 0, 0, region_sites.size() <= 2 ? (int)psi : 0, {0, 0, 0, 0}};
                     for (int r = 0; r < 3; ++r) {
                         if (p[r] == 0) c.rx = r, c.nx = g[r];
                         if (p[r] == 1) c.ry = r, c.ny = g[r];
@@ -428,7 +429,8 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             auto key = [&](int i) {
                 const std::string r = fold ? "ri" + std::to_string(i) : std::to_string(i);
                 const std::string ng = fold ? "(int)ng" + std::to_string(i) : "0";
-                return "((psi * 3 + " + r + ") * 2 + " + ng + ") * 4 + (k" + std::to_string(i) + " & 3)";
+                const std::string ps = t.ref.size() <= 2 ? "psi" : "0";
+                return "((" + ps + " * 3 + " + r + ") * 2 + " + ng + ") * 4 + (k" + std::to_string(i) + " & 3)";
             };
             o << "    const int sx = (int)((" << e.shift_mx << "ull >> (" << key(0) << ")) & 1ull);\n";
             o << "    const int sy = (int)((" << e.shift_my << "ull >> (" << key(1) << ")) & 1ull);\n";
@@ -1444,7 +1446,18 @@ void emit_eval_kernel_reuse(Emitter &e, const Table &t, const ls_variant &var, c
       << " && (code == pcode) && (psi == ppsi);\n";
     o << "    if (!same) {\n";
     emit_gathers(e, t, st.sites, reach, "a.coef", false);
-    for (size_t k = 0; k < K; ++k)
+    for (size_t k = 0; k < K; ++k) {
+        // the same transform as the one-point kernel (factored when the
+        // generator factors it), so the results stay bit for bit the same
+        const FactoredTransform ft = e.sym ? factor_transform(t.ref[k]) : FactoredTransform();
+        if (!ft.ops.empty()) {
+            PolyEmit pe{e, D, "t" + std::to_string(k) + "_", {}, {}, {}};
+            o << "    {\n";
+            emit_factored_transform(e, t.ref[k], st.region_to_union[k], ft, pe);
+            for (const auto &m : sup[k]) o << "    " << aname(k, m) << " = " << pe.aname[m] << ";\n";
+            o << "    }\n";
+            continue;
+        }
         for (const auto &m : sup[k]) {
             std::string acc;
             for (auto &pr : terms[k][m]) {
@@ -1454,6 +1467,7 @@ void emit_eval_kernel_reuse(Emitter &e, const Table &t, const ls_variant &var, c
             }
             o << "    " << aname(k, m) << " = " << acc << ";\n";
         }
+    }
     o << "    pk0 = k0;" << (D > 1 ? " pk1 = k1;" : "") << (D > 2 ? " pk2 = k2;" : "") << " pcode = code; ppsi = psi;\n";
     o << "    }\n";
     std::vector<std::string> fk;

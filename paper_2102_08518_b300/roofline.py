@@ -71,7 +71,8 @@ def stencil_indices(table, ext, pts: np.ndarray, layout: str = "coset", masks=No
             else:
                 r_i = np.full(n, i)
                 neg = np.zeros(n, dtype=np.int64)
-            key = ((regions * 3 + r_i) * 2 + neg) * 4 + (k[:, i] & 3)
+            psi = regions if len(table.regions) <= 2 else np.zeros_like(regions)
+            key = ((psi * 3 + r_i) * 2 + neg) * 4 + (k[:, i] & 3)
             shift[:, i] = (np.array([mask >> int(q) for q in key], dtype=object) & 1).astype(np.int64)
     nsite = max(len(r.sites) for r in table.regions)
     out = np.full((n, nsite), -1, dtype=np.int64)

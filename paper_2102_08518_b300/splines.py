@@ -35,4 +35,11 @@ BCC_QUARTIC = Spline("bcc_quartic", BCC, _BCC4 + ((2, 0, 0), (0, 2, 0), (0, 0, 2
 FCC6 = Spline("fcc6", FCC, _FCC6, "voronoi")
 ZP = Spline("zp", Z2, ((1, 0), (0, 1), (1, 1), (-1, 1)), "voronoi")
 
-BY_NAME = {s.name: s for s in (TRICUBIC, TRILINEAR, TRIQUADRATIC, BCC_LINEAR, BCC_QUINTIC, BCC_QUARTIC, FCC6, ZP)}
+# the second-order Voronoi splines of the paper's Voronoi study (Sec. 5): the
+# Voronoi cell's indicator convolved with itself, normalised (on the Cartesian
+# lattice this is the trilinear spline)
+VORONOI2_BCC = Spline("voronoi2_bcc", BCC, (), "voronoi", "voronoi2")
+VORONOI2_FCC = Spline("voronoi2_fcc", FCC, (), "voronoi", "voronoi2")
+
+BY_NAME = {s.name: s for s in (TRICUBIC, TRILINEAR, TRIQUADRATIC, BCC_LINEAR, BCC_QUINTIC, BCC_QUARTIC, FCC6, ZP,
+                               VORONOI2_BCC, VORONOI2_FCC)}

@@ -80,6 +80,7 @@ class Spline:
     lattice: Lattice
     dirs: Tuple[Vec, ...]
     roe: str = "voronoi"                 # "voronoi" | "parallelepiped"
+    kind: str = "box"                    # "box": box spline of dirs; "voronoi2": second-order Voronoi spline
 
 
 # ---------------------------------------------------------------------------
@@ -261,10 +262,14 @@ class TableBuilder:
         self.spl = spline
         self.s = spline.lattice.dim
         self.bp = BoxPieces()
-        self.half = _half_sum(spline.dirs)
+        self.half = _half_sum(spline.dirs) if spline.dirs else (Fraction(0),) * self.s
         self.detL = spline.lattice.det()
         self.rng = random.Random(seed)
         self.hw = tuple(Fraction(sum(abs(d[i]) for d in spline.dirs), 2) for i in range(self.s))
+        self.degree = len(spline.dirs) - self.s
+
+    def _symmetric(self) -> bool:
+        return _symmetric_under_signed_perms(self.spl)
 
     # weight polynomial w(y) = |det L| M(y - n + half) of site n near generic y*
     def weight(self, n: Vec, ystar) -> Poly:
@@ -334,7 +339,7 @@ class TableBuilder:
         fold = "none"
         cons = list(base)
         if spl.roe == "voronoi" and not self._axis_aligned():
-            if not _symmetric_under_signed_perms(spl):
+            if not self._symmetric():
                 raise NotImplementedError("Voronoi ROE without full signed-permutation symmetry")
             fold = "hyperoctahedral"
             cons += _chamber_constraints(s)
@@ -389,7 +394,7 @@ class TableBuilder:
         for q, r in q_to_region.items():
             sigma[q % p] = r
         # reference regions in local coordinates
-        degree = len(spl.dirs) - s
+        degree = self.degree
         mons = monomials_upto(s, degree)
         refs = []
         refs_c = []
@@ -567,5 +572,61 @@ def _prune_planes(planes, q_to_region):
     return [planes[i] for i in keep], q_to_region
 
 
+class VoronoiTableBuilder(TableBuilder):
+    """The same construction for the second-order Voronoi spline of a lattice
+    (Sec. 5, Voronoi splines): phi(x) = vol(P n (P + x)) / vol(P) for the
+    Voronoi cell P, whose exact cubic pieces and knot planes come from
+    voronoi.OverlapPieces instead of the box-spline recurrence."""
+
+    def __init__(self, spline: Spline, seed: int = 12345):
+        from .voronoi import OverlapPieces
+        super().__init__(spline, seed)
+        self.op = OverlapPieces(_nonredundant(_voronoi_constraints(spline.lattice)))
+        self.half = (Fraction(0),) * self.s
+        self.hw = self.op.support_halfwidth()
+        self.degree = 3
+
+    def _symmetric(self) -> bool:
+        lat = self.spl.lattice
+        s = self.s
+        return all(lat.contains(tuple(sg[i] * l[perm[i]] for i in range(s)))
+                   for perm in itertools.permutations(range(s)) for sg in itertools.product((1, -1), repeat=s)
+                   for l in lat.cosets)
+
+    def _axis_aligned(self) -> bool:
+        return False
+
+    def _separable(self):
+        return None
+
+    def weight(self, n: Vec, ystar) -> Poly:
+        x = tuple(ystar[i] - n[i] for i in range(self.s))
+        if any(abs(x[i]) >= self.hw[i] for i in range(self.s)):
+            return Poly(self.s)
+        p = self.op.piece(x)
+        if p.is_zero():
+            return p
+        return p.shift([-Fraction(v) for v in n])
+
+    def _cutting_planes(self, cons):
+        verts = _vertices(cons)
+        lat = self.spl.lattice
+        lo_box = [min(v[i] for v in verts) - self.hw[i] for i in range(self.s)]
+        hi_box = [max(v[i] for v in verts) + self.hw[i] for i in range(self.s)]
+        sites = list(lat.sites_in_box([int(np.floor(float(x))) for x in lo_box],
+                                      [int(np.ceil(float(x))) for x in hi_box]))
+        planes = set()
+        for nu, d in self.op.knot_planes():
+            vals = [dot(nu, v) for v in verts]
+            lo, hi = min(vals), max(vals)
+            for n in sites:
+                dd = d + dot(nu, n)
+                if lo < dd < hi:
+                    planes.add((tuple(Fraction(v) for v in nu), Fraction(dd)))
+        return sorted(planes)
+
+
 def build_table(spline: Spline, seed: int = 12345) -> Table:
+    if spline.kind == "voronoi2":
+        return VoronoiTableBuilder(spline, seed).build()
     return TableBuilder(spline, seed).build()

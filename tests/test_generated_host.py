@@ -21,9 +21,11 @@ from tests.host_kernels import HostKernels, generated_source
 from tests.test_gpu_layout import brick_np, brick_shifted_np, interleave_np
 
 SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
-        "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6, "zp": ospecs.zp2d}
+        "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic,
+               "voronoi2_bcc": ospecs.voronoi2_bcc, "voronoi2_fcc": ospecs.voronoi2_fcc, "fcc6": ospecs.fcc6, "zp": ospecs.zp2d}
 EXT = {"tricubic": (8, 6, 6), "trilinear": (6, 6, 4), "triquadratic": (6, 8, 6), "bcc_linear": (6, 6, 4),
-       "bcc_quintic": (8, 6, 6), "bcc_quartic": (6, 8, 6), "fcc6": (6, 6, 6), "zp": (12, 10)}
+       "bcc_quintic": (8, 6, 6), "bcc_quartic": (6, 8, 6), "fcc6": (6, 6, 6), "zp": (12, 10),
+       "voronoi2_bcc": (6, 6, 6), "voronoi2_fcc": (6, 6, 6)}
 TOL, GTOL, HTOL = 2e-6, 1e-5, 1e-4
 
 
@@ -52,7 +54,8 @@ BRICK = {"coset": 0, "interleaved": 0, "bricked": 1, "bricked_shifted": 2}
 def test_value_and_gradient(name, layout):
     if layout == "bricked_shifted" and name == "zp":
         pytest.skip("the shifted bricked copies are 3D only")
-    lat, ext, C, coef, pts = _case(name)
+    voronoi = name.startswith("voronoi")
+    lat, ext, C, coef, pts = _case(name, n=200 if voronoi else 1500)
     spec = SPEC[name]().with_extent(ext)
     want, wgrad = oracle.eval_sum_grad(spec, coef.astype(np.float64).ravel(), pts.astype(np.float64))
     hk = HostKernels(name, **({"brick": BRICK[layout]} if BRICK[layout] else {}))
@@ -62,6 +65,19 @@ def test_value_and_gradient(name, layout):
     cmax = float(np.abs(coef).max())
     assert np.abs(f - want).max() <= TOL * cmax
     assert np.abs(v - want).max() <= TOL * cmax
+    if voronoi:
+        # the oracle's gradient is a central difference (h = 1e-5): compare where
+        # no knot plane lies within the difference step (one-sided slopes agree)
+        ok = np.ones(len(pts), bool)
+        c64 = coef.astype(np.float64).ravel()
+        for i in range(3):
+            e = np.zeros(3)
+            e[i] = 1e-4
+            fp = oracle.eval_sum(spec, c64, pts + e)
+            fm = oracle.eval_sum(spec, c64, pts - e)
+            ok &= np.abs((fp - want) - (want - fm)) / 1e-4 < 1e-2     # h |f''| inside a cubic piece
+        assert ok.sum() > len(pts) // 2
+        g, wgrad = g[ok], wgrad[ok]
     assert np.abs(g - wgrad).max() <= GTOL * cmax
 
 

@@ -19,7 +19,8 @@ from oracle import specs as ospecs
 pytestmark = pytest.mark.gpu
 
 ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "bcc_linear": ospecs.bcc_linear,
-               "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6, "zp": ospecs.zp2d}
+               "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic,
+               "voronoi2_bcc": ospecs.voronoi2_bcc, "voronoi2_fcc": ospecs.voronoi2_fcc, "fcc6": ospecs.fcc6, "zp": ospecs.zp2d}
 EXT = {"tricubic": (40, 36, 30), "trilinear": (40, 32, 30), "bcc_linear": (24, 22, 20),
        "bcc_quintic": (24, 20, 18), "fcc6": (24, 20, 18), "zp": (40, 36)}
 

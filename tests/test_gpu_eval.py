@@ -16,12 +16,16 @@ pytestmark = pytest.mark.gpu
 
 TOL = 2e-6
 ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
-               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6,
+               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic,
+               "voronoi2_bcc": ospecs.voronoi2_bcc, "voronoi2_fcc": ospecs.voronoi2_fcc, "fcc6": ospecs.fcc6,
                "zp": ospecs.zp2d}
 SMALL_EXT = {"tricubic": (12, 11, 10), "trilinear": (9, 12, 10), "triquadratic": (11, 9, 12),
              "bcc_linear": (7, 6, 8), "bcc_quintic": (8, 7, 6), "bcc_quartic": (7, 8, 7), "fcc6": (7, 8, 6),
-             "zp": (13, 11)}
-ALL_NAMES = ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "bcc_quartic", "fcc6", "zp"]
+             "zp": (13, 11), "voronoi2_bcc": (6, 7, 6), "voronoi2_fcc": (6, 6, 7)}
+ALL_NAMES = ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "bcc_quartic", "fcc6", "zp",
+             "voronoi2_bcc", "voronoi2_fcc"]
+# splines whose gradient jumps across knot planes (C0): gradients are compared off them
+C0_SPLINES = ("bcc_linear", "trilinear", "voronoi2_bcc", "voronoi2_fcc")
 _SPLINES = {}
 
 
@@ -67,7 +71,7 @@ def test_small_volume_every_point(name, n):
 
 
 @pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "bcc_quartic",
-                                  "fcc6"])
+                                  "fcc6", "voronoi2_bcc", "voronoi2_fcc"])
 def test_special_points(name):
     """Lattice sites, half-integers, mirror and BSP planes, and the edges."""
     lat = workloads.SPLINE_LATTICE[name]
@@ -171,7 +175,7 @@ def test_gradient_matches_oracle(name):
     ext = SMALL_EXT[name]
     coef = workloads.coef_uniform(lat, ext, seed=21)
     lo, hi = workloads.bounding_box(lat, ext)
-    pts = workloads.points_uniform(2000, lo - 1.0, hi + 1.0, seed=22)
+    pts = workloads.points_uniform(500 if name.startswith("voronoi") else 2000, lo - 1.0, hi + 1.0, seed=22)
     vol = volume(name, ext, coef)
     val, grad = vol.eval_grad(torch.from_numpy(pts).cuda())
     torch.cuda.synchronize()
@@ -179,7 +183,7 @@ def test_gradient_matches_oracle(name):
     f, g = oracle.eval_sum_grad(spec, coef.astype(np.float64).ravel(), pts.astype(np.float64))
     assert np.max(np.abs(val.cpu().numpy() - f)) <= TOL * np.abs(coef).max()
     gg = grad.cpu().numpy()
-    if name in ("bcc_linear", "trilinear"):
+    if name in C0_SPLINES:
         # C0 spline: the gradient jumps across knot planes; compare off them
         ok = np.ones(len(pts), bool)
         h = 1e-4
@@ -188,9 +192,11 @@ def test_gradient_matches_oracle(name):
             e[i] = h
             fp = oracle.eval_sum(spec, coef.astype(np.float64).ravel(), pts + e)
             fm = oracle.eval_sum(spec, coef.astype(np.float64).ravel(), pts - e)
-            ok &= np.abs((fp - f) / h - (f - fm) / h) < 1e-6
+            # inside a piece the one-sided slopes differ by h |f''|: 0 for the
+            # piecewise-linear splines, up to ~1e-3 for the cubic Voronoi pieces
+            ok &= np.abs((fp - f) / h - (f - fm) / h) < (1e-2 if name.startswith("voronoi") else 1e-6)
         gg, g = gg[ok], g[ok]
-        assert ok.sum() > 1000
+        assert ok.sum() > len(pts) // 2
     assert np.max(np.abs(gg - g)) <= 1e-5 * np.abs(coef).max()
 
 

@@ -17,7 +17,8 @@ from oracle import specs as ospecs
 
 pytestmark = pytest.mark.gpu
 
-ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "bcc_linear": ospecs.bcc_linear,
+ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic,
+               "voronoi2_bcc": ospecs.voronoi2_bcc, "voronoi2_fcc": ospecs.voronoi2_fcc, "bcc_linear": ospecs.bcc_linear,
                "fcc6": ospecs.fcc6}
 
 

@@ -22,14 +22,15 @@ from oracle import specs as ospecs
 pytestmark = pytest.mark.gpu
 
 ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
-               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6,
+               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic,
+               "voronoi2_bcc": ospecs.voronoi2_bcc, "voronoi2_fcc": ospecs.voronoi2_fcc, "fcc6": ospecs.fcc6,
                "zp": ospecs.zp2d}
 EXT = {"tricubic": (9, 8, 10), "trilinear": (9, 12, 10), "triquadratic": (11, 9, 12), "bcc_linear": (6, 7, 6),
-       "bcc_quintic": (7, 6, 7), "fcc6": (6, 7, 6), "zp": (13, 11)}
-C2 = {"tricubic", "bcc_quintic"}
+       "bcc_quintic": (7, 6, 7), "bcc_quartic": (7, 6, 7), "fcc6": (6, 7, 6), "zp": (13, 11)}
+C2 = {"tricubic", "bcc_quintic", "bcc_quartic"}
 
 
-@pytest.mark.parametrize("name", sorted(ORACLE_SPEC))
+@pytest.mark.parametrize("name", sorted(EXT))
 def test_hessian_matches_oracle(name):
     from paper_2102_08518_b300.api import Spline, Volume
     lat = workloads.SPLINE_LATTICE[name]

@@ -10,7 +10,8 @@ from oracle import specs as ospecs
 pytestmark = pytest.mark.gpu
 
 ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
-               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6,
+               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic,
+               "voronoi2_bcc": ospecs.voronoi2_bcc, "voronoi2_fcc": ospecs.voronoi2_fcc, "fcc6": ospecs.fcc6,
                "zp": ospecs.zp2d}
 SMALL_EXT = {"tricubic": (12, 11, 10), "trilinear": (9, 12, 10), "triquadratic": (11, 9, 12),
              "bcc_linear": (7, 6, 8), "bcc_quintic": (8, 7, 6), "fcc6": (7, 8, 6), "zp": (13, 11)}

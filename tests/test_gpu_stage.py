@@ -22,7 +22,8 @@ pytestmark = pytest.mark.gpu
 
 TOL = 2e-6
 ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
-               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6}
+               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic,
+               "voronoi2_bcc": ospecs.voronoi2_bcc, "voronoi2_fcc": ospecs.voronoi2_fcc, "fcc6": ospecs.fcc6}
 # extents with ext0 % 4 == 0, so the coset-major rows are whole 16-byte units
 EXT = {"tricubic": (40, 36, 30), "trilinear": (40, 32, 30), "triquadratic": (36, 32, 28),
        "bcc_linear": (24, 22, 20), "bcc_quintic": (24, 20, 18), "fcc6": (24, 20, 18)}

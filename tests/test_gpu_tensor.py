@@ -24,7 +24,8 @@ pytestmark = pytest.mark.gpu
 TOL = 2e-6
 BF16_TOL = 2.0 ** -8 + 2e-6
 F16_TOL = 2.0 ** -11 + 2e-6
-ORACLE_SPEC = {"bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6,
+ORACLE_SPEC = {"bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic,
+               "voronoi2_bcc": ospecs.voronoi2_bcc, "voronoi2_fcc": ospecs.voronoi2_fcc, "fcc6": ospecs.fcc6,
                "zp": ospecs.zp2d}
 EXT = {"bcc_linear": (10, 9, 8), "bcc_quintic": (10, 8, 9), "fcc6": (9, 10, 8), "zp": (14, 12)}
 NAMES = list(EXT)

@@ -82,6 +82,14 @@ def test_branchy_fcc(var, layout):
     _check("fcc6", var, layout)
 
 
+@pytest.mark.parametrize("var", [dict(branchy=1), dict()], ids=str)
+@pytest.mark.parametrize("name", ["voronoi2_bcc", "voronoi2_fcc"])
+def test_voronoi_branchy_and_predicated(name, var):
+    """The second-order Voronoi splines (five reference sub-regions on BCC)
+    with the sub-region chosen by a branch and by selects."""
+    _check(name, var)
+
+
 @pytest.mark.parametrize("name", ["bcc_quintic", "fcc6", "tricubic", "bcc_linear"])
 def test_plain_transform(name):
     """The coefficient transform as direct sums over the sites (the factored

@@ -15,7 +15,8 @@ from tests.table_eval import eval_separable, eval_table
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 ORACLE_SPEC = {"tricubic": ospecs.tricubic, "trilinear": ospecs.trilinear, "triquadratic": ospecs.triquadratic,
-               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic, "fcc6": ospecs.fcc6,
+               "bcc_linear": ospecs.bcc_linear, "bcc_quintic": ospecs.bcc_quintic, "bcc_quartic": ospecs.bcc_quartic,
+               "voronoi2_bcc": ospecs.voronoi2_bcc, "voronoi2_fcc": ospecs.voronoi2_fcc, "fcc6": ospecs.fcc6,
                "zp": ospecs.zp2d}
 
 
@@ -39,7 +40,7 @@ def test_zp_table_reproduces_fig1():
 
 
 @pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "bcc_quartic",
-                                  "fcc6", "zp"])
+                                  "fcc6", "zp", "voronoi2_bcc", "voronoi2_fcc"])
 def test_table_weights_partition_unity_exactly(name):
     t = table(name)
     for reg in t.regions:
@@ -64,10 +65,17 @@ def test_structural_facts_from_the_paper():
     assert len(table("triquadratic").regions[0].sites) == 27
     # the seven-direction BCC spline: quartic pieces (degree |Xi| - 3)
     assert table("bcc_quartic").degree == 4
+    # second-order Voronoi splines: cubic pieces, 8 sites per point (as the
+    # trilinear spline); more than one reference sub-region on BCC, so the
+    # branchy / predicated choice of the paper's Voronoi study applies
+    for name in ("voronoi2_bcc", "voronoi2_fcc"):
+        t = table(name)
+        assert t.degree == 3 and all(len(r.sites) == 8 for r in t.regions)
+    assert len(table("voronoi2_bcc").regions) > 1
 
 
 @pytest.mark.parametrize("name", ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "bcc_quartic",
-                                  "fcc6", "zp"])
+                                  "fcc6", "zp", "voronoi2_bcc", "voronoi2_fcc"])
 def test_table_matches_oracle_by_brute_force(name):
     """Algorithm 1 over the table in FP64 vs the oracle's naive sum, tiny grids,
     points everywhere (inside, near and beyond the edges)."""

@@ -23,10 +23,11 @@ LATTICES = {
     "z2": (2, 1, ((0, 0),)),
 }
 SPLINE_LATTICE = {"tricubic": "cc", "trilinear": "cc", "triquadratic": "cc", "bcc_linear": "bcc",
-                  "bcc_quintic": "bcc", "bcc_quartic": "bcc", "fcc6": "fcc", "zp": "z2"}
+                  "bcc_quintic": "bcc", "bcc_quartic": "bcc", "fcc6": "fcc", "zp": "z2", "voronoi2_bcc": "bcc",
+                  "voronoi2_fcc": "fcc"}
 # half-width of the support box along an axis: 1/2 sum_xi |xi_i| (input margins only)
 SUPPORT_HALF = {"tricubic": 2.0, "trilinear": 1.0, "triquadratic": 1.5, "bcc_linear": 2.0, "bcc_quintic": 4.0,
-                "bcc_quartic": 3.0, "fcc6": 2.0, "zp": 1.5}
+                "bcc_quartic": 3.0, "fcc6": 2.0, "zp": 1.5, "voronoi2_bcc": 2.0, "voronoi2_fcc": 2.0}
 
 
 def site_coords(lattice: str, ext: Sequence[int]) -> np.ndarray:
