@@ -315,6 +315,12 @@ def run_gpu(args):
                 best = (ms_, s_, lay)
         tuned[(sp, ps)], case_layout[(sp, ps)] = best[1], best[2]
     base_layout = layouts[0]                                # the extras' volumes
+    # hold only the layouts the step reads (and the extras' one) from here on:
+    # every resident copy competes for L2 with the others
+    for lay in list(coefs):
+        if lay != base_layout and lay not in case_layout.values():
+            del coefs[lay]
+    torch.cuda.empty_cache()
     splines = {sp: tuned[(sp, "uniform")] if case_layout[(sp, "uniform")] == base_layout else
                autotune(sp, "f32", EXT, coefs[base_layout], [pts["uniform"]], candidates=TUNE_CANDIDATES_SMALL,
                         tag="bcc_step_uniform", layout=base_layout) for sp in ("bcc_linear", "bcc_quintic")}
@@ -369,7 +375,7 @@ def run_gpu(args):
     sample = {ps: v[np.random.default_rng(7).choice(len(v), 1 << 14, replace=False)] for ps, v in pts_np.items()}
     sectors = {(sp, ps): distinct_sectors_per_point(
         table(sp), EXT, sample["uniform"], layout=case_layout[(sp, ps)],
-        masks=shift_masks(tuned[(sp, ps)].source()) if case_layout[(sp, ps)] == "bricked_shifted" else None)
+        masks=shift_masks(tuned[(sp, ps)].source()) if case_layout[(sp, ps)].startswith("bricked_shifted") else None)
         for sp, ps in CASES}
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
@@ -512,7 +518,7 @@ def run_gpu(args):
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
               "data": "synthetic",
               "config": {"workload": WORKLOAD, "points_per_step": pts_per_step, "coef_bytes": coef_np.nbytes,
-                         "coef_copies_resident": len(layouts),
+                         "coef_layouts_resident": sorted(coefs),
                          "coef_layout": {f"{sp}/{ps}": case_layout[(sp, ps)] for sp, ps in CASES},
                          "l2": "points 201 MB per set > 126 MB L2 (inputs larger than L2); coefficient volume "
                                "16 MiB L2-resident by design", "parallelism": f"replicas x{world}"},
@@ -844,7 +850,15 @@ def extra_paper_orders(torch, dev, vols, pts, outs):
             vs = Volume(Spline(name, "f32", brick=2), ext, cs, layout="bricked_shifted")
             mss = time_ms(torch, lambda: vs.eval(p, out))
             res[name]["bricked_shifted_gpoints_s"] = round(n / mss / 1e6, 3)
-            del cb, vb, cs, vs
+            del cs, vs
+            if lat == "cc":
+                # eight copies, also shifted on z (a Cartesian sector is a whole brick)
+                cs = relayout(c, ncos, ext, to="bricked_shifted_xyz", src="interleaved")
+                vs = Volume(Spline(name, "f32", brick=3), ext, cs, layout="bricked_shifted_xyz")
+                mss = time_ms(torch, lambda: vs.eval(p, out))
+                res[name]["bricked_shifted_xyz_gpoints_s"] = round(n / mss / 1e6, 3)
+                del cs, vs
+            del cb, vb
         del c, p, vol
     res["order2_bcc_linear_vs_trilinear"] = round(res["bcc_linear"]["gpoints_s"] / res["trilinear"]["gpoints_s"], 3)
     res["order3_fcc6_vs_triquadratic"] = round(res["fcc6"]["gpoints_s"] / res["triquadratic"]["gpoints_s"], 3)
@@ -1021,7 +1035,8 @@ def main():
                     help="reference: the FP64 oracle on the host cores, on a bounded sample of each step")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle's timing on the host")
     ap.add_argument("--no-extras", action="store_true", help="skip the measurements beside the headline step")
-    ap.add_argument("--layout", default=LAYOUT, choices=["auto", "coset", "interleaved", "bricked", "bricked_shifted"],
+    ap.add_argument("--layout", default=LAYOUT, choices=["auto", "coset", "interleaved", "bricked", "bricked_shifted",
+                                                          "bricked_shifted_xyz"],
                     help="coefficient layout of the step's volumes")
     ap.add_argument("--only", default=None, choices=PROFILE_CASES,
                     help="run one small case for a profiler instead of the benchmark")

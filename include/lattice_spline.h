@@ -87,12 +87,19 @@ typedef enum { LS_F32 = 0, LS_BF16 = 1, LS_F16 = 2, LS_F64 = 3 } ls_dtype;
  *                           evaluation kernels (value, gradient, Hessian, batched)
  *                           take it, the adjoint and the fit do not.  Needs a
  *                           spline created with ls_variant.brick = 2.
+ *   LS_LAYOUT_BRICKED_SHIFTED_XYZ: the same with eight copies, the brick grid
+ *                           also shifted on axis 2: copy c = s_0 + 2 s_1 + 4 s_2
+ *                           over extents (ext_0 + 2, ext_1 + 2, ext_2 + 2).  For
+ *                           the Cartesian splines, whose 32-byte sector is a whole
+ *                           2 x 2 x 2 brick (tricubic: 8.0 sectors per point, the
+ *                           least 64 sites can take).  ls_variant.brick = 3.
  */
 typedef enum {
     LS_LAYOUT_COSET_MAJOR = 0,
     LS_LAYOUT_INTERLEAVED = 1,
     LS_LAYOUT_BRICKED = 2,
-    LS_LAYOUT_BRICKED_SHIFTED = 3
+    LS_LAYOUT_BRICKED_SHIFTED = 3,
+    LS_LAYOUT_BRICKED_SHIFTED_XYZ = 4
 } ls_layout;
 
 typedef enum {
@@ -185,8 +192,9 @@ typedef struct {
                                           the resident warps per SM without taking L1 away (no
                                           recompilation) */
     int32_t brick;                     /* 1: the kernels address LS_LAYOUT_BRICKED volumes (and only
-                                          those); 2: LS_LAYOUT_BRICKED_SHIFTED volumes (3D); 0: the
-                                          linear layouts (coset-major, interleaved) */
+                                          those); 2: LS_LAYOUT_BRICKED_SHIFTED volumes (3D); 3:
+                                          LS_LAYOUT_BRICKED_SHIFTED_XYZ volumes (3D); 0: the linear
+                                          layouts (coset-major, interleaved) */
     int32_t pipeline;                  /* 1: the value kernel issues the gathers of a thread's next
                                           point before evaluating the current one (software
                                           pipelining; non-separable tables; pts_per_thread ignored) */

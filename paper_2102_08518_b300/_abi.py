@@ -26,6 +26,7 @@ LS_ROE_PARALLELEPIPED, LS_ROE_VORONOI = 0, 1
 LS_FOLD_NONE, LS_FOLD_SIGNED_PERM = 0, 1
 # ls_layout
 LS_LAYOUT_COSET_MAJOR, LS_LAYOUT_INTERLEAVED, LS_LAYOUT_BRICKED, LS_LAYOUT_BRICKED_SHIFTED = 0, 1, 2, 3
+LS_LAYOUT_BRICKED_SHIFTED_XYZ = 4
 # ls_adjoint_mode
 LS_ADJ_ATOMIC, LS_ADJ_DETERMINISTIC, LS_ADJ_ATOMIC_WARP, LS_ADJ_DETERMINISTIC_FIXED = 0, 1, 2, 3
 LS_ADJ_ATOMIC_TILED, LS_ADJ_DETERMINISTIC_FIXED_TILED = 4, 5

@@ -23,9 +23,10 @@ _CACHE_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "kcache")
 
 DTYPES = {"f32": _abi.LS_F32, "bf16": _abi.LS_BF16, "f16": _abi.LS_F16}
 LAYOUTS = {"coset": _abi.LS_LAYOUT_COSET_MAJOR, "interleaved": _abi.LS_LAYOUT_INTERLEAVED,
-           "bricked": _abi.LS_LAYOUT_BRICKED, "bricked_shifted": _abi.LS_LAYOUT_BRICKED_SHIFTED}
+           "bricked": _abi.LS_LAYOUT_BRICKED, "bricked_shifted": _abi.LS_LAYOUT_BRICKED_SHIFTED,
+           "bricked_shifted_xyz": _abi.LS_LAYOUT_BRICKED_SHIFTED_XYZ}
 # the kernels' variant.brick for each layout
-LAYOUT_BRICK = {"coset": 0, "interleaved": 0, "bricked": 1, "bricked_shifted": 2}
+LAYOUT_BRICK = {"coset": 0, "interleaved": 0, "bricked": 1, "bricked_shifted": 2, "bricked_shifted_xyz": 3}
 
 
 def layout_elems(n_cosets: int, ext: Sequence[int], layout: str) -> int:
@@ -34,6 +35,8 @@ def layout_elems(n_cosets: int, ext: Sequence[int], layout: str) -> int:
     e = tuple(int(v) for v in ext) + (1,) * (3 - len(ext))
     if layout == "bricked_shifted":
         return 4 * n_cosets * (e[0] + 2) * (e[1] + 2) * e[2]
+    if layout == "bricked_shifted_xyz":
+        return 8 * n_cosets * (e[0] + 2) * (e[1] + 2) * (e[2] + 2)
     return n_cosets * e[0] * e[1] * e[2]
 TORCH_DTYPES = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
 
@@ -82,7 +85,7 @@ def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_b
     return f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + ("_br" if branchy else "") + \
         (f"_m{min_blocks}" if min_blocks else "") + (f"_g{group}d{depth}" if group and depth else "") + \
         (f"_t{pts_per_thread}" if pts_per_thread > 1 else "") + ("_ec" if expansion == "centroid" else "") + \
-        ("_bk2" if brick == 2 else "_bk" if brick else "") + ("_pp" if pipeline else "") + (f"_ws{producers}" if producers else "") + \
+        (f"_bk{brick}" if brick >= 2 else "_bk" if brick else "") + ("_pp" if pipeline else "") + (f"_ws{producers}" if producers else "") + \
         (f"_st{stage}" if stage else "") + (("_tc" + (str(tensor) if tensor > 1 else "")) if tensor else "") + \
         ("h" if tensor and tensor_kind else "") + ("_pt" if plain_transform else "") + \
         (f"_wl{wait_limit}" if wait_limit else "") + ("_wp" if wait_probe else "")
@@ -509,6 +512,7 @@ TUNE_CANDIDATES_SMALL = tuple([dict(block=256, blocks_per_sm=b, expansion=x) for
                               [dict(block=512, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(block=384, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(block=128, blocks_per_sm=b) for b in (2, 4)] +
+                              [dict(block=384, min_blocks=2), dict(block=256, min_blocks=3)] +
                               [dict(tensor=1, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(tensor=1, tensor_kind=1, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(tensor=4, tensor_kind=1)] +

@@ -251,7 +251,7 @@ ls_variant default_variant(const ls_variant *v)
         r.group = v->group > 0 ? v->group : 0;
         r.depth = v->depth > 0 ? v->depth : 0;
         r.blocks_per_sm = v->blocks_per_sm > 0 ? v->blocks_per_sm : 0;
-        r.brick = v->brick == 2 ? 2 : v->brick ? 1 : 0;
+        r.brick = v->brick >= 2 && v->brick <= 3 ? v->brick : v->brick ? 1 : 0;
         r.pipeline = v->pipeline ? 1 : 0;
         r.producers = v->producers > 0 ? v->producers : 0;
         r.stage = v->stage > 0 ? v->stage : 0;
@@ -417,9 +417,9 @@ ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_var
             return ls_fail(LS_ERR_INVALID_ARG, why);
         }
     }
-    if (s->var.brick == 2 && s->table.dim != 3) {
+    if (s->var.brick >= 2 && s->table.dim != 3) {
         delete s;
-        return ls_fail(LS_ERR_UNSUPPORTED, "brick = 2 (shifted bricked copies) needs a 3D table");
+        return ls_fail(LS_ERR_UNSUPPORTED, "brick = 2 or 3 (shifted bricked copies) needs a 3D table");
     }
     if (s->var.wait_probe != 0 && (s->var.wait_probe != 1 || s->var.producers <= 0)) {
         delete s;
@@ -570,16 +570,14 @@ ls_status ls_spline_info(ls_spline s, int32_t *n_sites, int32_t *fma_value, int3
 static ls_status init_volume(ls_spline s, const int64_t *ext, int32_t layout, ls_volume_s *v)
 {
     if (!s || !ext) return ls_fail(LS_ERR_INVALID_ARG, "spline or ext is NULL");
-    if (layout != LS_LAYOUT_COSET_MAJOR && layout != LS_LAYOUT_INTERLEAVED && layout != LS_LAYOUT_BRICKED &&
-        layout != LS_LAYOUT_BRICKED_SHIFTED)
+    if (layout < LS_LAYOUT_COSET_MAJOR || layout > LS_LAYOUT_BRICKED_SHIFTED_XYZ)
         return ls_fail(LS_ERR_INVALID_ARG, "unknown layout");
-    const int want_brick = layout == LS_LAYOUT_BRICKED ? 1 : layout == LS_LAYOUT_BRICKED_SHIFTED ? 2 : 0;
+    const int want_brick = layout == LS_LAYOUT_BRICKED ? 1 : layout == LS_LAYOUT_BRICKED_SHIFTED ? 2
+                         : layout == LS_LAYOUT_BRICKED_SHIFTED_XYZ ? 3 : 0;
     if (want_brick != s->var.brick)
-        return ls_fail(LS_ERR_INVALID_ARG, s->var.brick == 1 ? "the spline's kernels address the bricked layout only"
-                                           : s->var.brick == 2 ? "the spline's kernels address the shifted bricked copies only"
-                                           : "a bricked volume needs a spline created with variant.brick = 1 (2 for the "
-                                             "shifted copies)");
-    if (layout == LS_LAYOUT_BRICKED_SHIFTED && s->table.dim != 3)
+        return ls_fail(LS_ERR_INVALID_ARG, "the volume's layout and the spline's variant.brick differ (bricked: 1, "
+                                           "shifted copies: 2, eight shifted copies: 3, linear layouts: 0)");
+    if (want_brick >= 2 && s->table.dim != 3)
         return ls_fail(LS_ERR_UNSUPPORTED, "the shifted bricked copies are 3D only");
     v->spline = s;
     v->layout = layout;
@@ -591,11 +589,13 @@ static ls_status init_volume(ls_spline s, const int64_t *ext, int32_t layout, ls
     }
     v->coset_elems = prod;
     v->total_elems = prod * (int64_t)s->table.cosets.size();
-    if ((layout == LS_LAYOUT_BRICKED || layout == LS_LAYOUT_BRICKED_SHIFTED) &&
+    if (want_brick >= 1 &&
         (v->ext[0] % 2 != 0 || (s->table.dim >= 2 && v->ext[1] % 2 != 0) || (s->table.dim == 3 && v->ext[2] % 2 != 0)))
         return ls_fail(LS_ERR_INVALID_ARG, "bricked layout: ext[0], ext[1] and ext[2] must be even");
     if (layout == LS_LAYOUT_BRICKED_SHIFTED)      // four copies over the padded extents
         v->total_elems = 4 * (int64_t)s->table.cosets.size() * (v->ext[0] + 2) * (v->ext[1] + 2) * v->ext[2];
+    if (layout == LS_LAYOUT_BRICKED_SHIFTED_XYZ)  // eight copies
+        v->total_elems = 8 * (int64_t)s->table.cosets.size() * (v->ext[0] + 2) * (v->ext[1] + 2) * (v->ext[2] + 2);
     if (v->total_elems >= (int64_t)1 << 31)
         return ls_fail(LS_ERR_UNSUPPORTED, "volume exceeds 2^31 coefficients (32-bit addressing)");
     return LS_OK;
@@ -736,14 +736,14 @@ ls_status ls_relayout(const void *src, int32_t src_layout, void *dst, int32_t ds
     }
     if (per * n_cosets >= ((int64_t)1 << 31)) return ls_fail(LS_ERR_UNSUPPORTED, "2^31 or more elements");
     for (int32_t l : {src_layout, dst_layout}) {
-        if (l < LS_LAYOUT_COSET_MAJOR || l > LS_LAYOUT_BRICKED_SHIFTED)
+        if (l < LS_LAYOUT_COSET_MAJOR || l > LS_LAYOUT_BRICKED_SHIFTED_XYZ)
             return ls_fail(LS_ERR_INVALID_ARG, "unknown layout");
-        if ((l == LS_LAYOUT_BRICKED || l == LS_LAYOUT_BRICKED_SHIFTED) &&
-            (ext[0] % 2 != 0 || ext[1] % 2 != 0 || (ext[2] != 1 && ext[2] % 2 != 0)))
+        if (l >= LS_LAYOUT_BRICKED && (ext[0] % 2 != 0 || ext[1] % 2 != 0 || (ext[2] != 1 && ext[2] % 2 != 0)))
             return ls_fail(LS_ERR_INVALID_ARG, "bricked layout: extents are not whole bricks");
-        if (l == LS_LAYOUT_BRICKED_SHIFTED && ext[2] == 1)
+        if (l >= LS_LAYOUT_BRICKED_SHIFTED && ext[2] == 1)
             return ls_fail(LS_ERR_UNSUPPORTED, "the shifted bricked copies are 3D only");
-        if (l == LS_LAYOUT_BRICKED_SHIFTED && 4 * n_cosets * (ext[0] + 2) * (ext[1] + 2) * ext[2] >= ((int64_t)1 << 31))
+        if (l >= LS_LAYOUT_BRICKED_SHIFTED &&
+            8 * n_cosets * (ext[0] + 2) * (ext[1] + 2) * (ext[2] + 2) >= ((int64_t)1 << 31))
             return ls_fail(LS_ERR_UNSUPPORTED, "2^31 or more elements");
     }
     if (!src || !dst || src == dst) return ls_fail(LS_ERR_INVALID_ARG, "src, dst NULL or the same buffer");
@@ -1002,7 +1002,7 @@ ls_status ls_adjoint_coef(ls_volume v, const float *pts, const float *gout, int6
     if (!v || (n > 0 && (!pts || !gout || !dcoef))) return ls_fail(LS_ERR_INVALID_ARG, "NULL argument");
     if (n < 0) return ls_fail(LS_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return LS_OK;
-    if (v->layout == LS_LAYOUT_BRICKED_SHIFTED)
+    if (v->layout >= LS_LAYOUT_BRICKED_SHIFTED)
         return ls_fail(LS_ERR_UNSUPPORTED, "the shifted bricked copies are read-only (evaluation kernels)");
     ls_spline_s *s = v->spline;
     cudaStream_t st = (cudaStream_t)stream;

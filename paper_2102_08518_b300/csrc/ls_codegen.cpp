@@ -48,8 +48,9 @@ struct Emitter {
     std::string ld = "ls_ld_f32";     // coefficient loader of the spline being emitted
     bool brick = false;               // bricked coefficient layout (else linear)
     bool sym = true;                  // factored coefficient transform (butterflies + sparser M)
-    bool brick_shift = false;         // the four shifted bricked copies (LS_LAYOUT_BRICKED_SHIFTED)
-    unsigned long long shift_mx = 0, shift_my = 0;   // their copy-choice rule (shift_rule)
+    bool brick_shift = false;         // shifted bricked copies (LS_LAYOUT_BRICKED_SHIFTED[_XYZ])
+    int shift_axes = 2;               // axes the copies shift (2: four copies, 3: eight)
+    unsigned long long shift_mask[3] = {0, 0, 0};   // their copy-choice rule (shift_rule)
     int wait_rounds = 1 << 20;        // try_wait rounds of a bounded wait (ls_mbar_wait; polls: x4)
     bool no_signal = false;           // test hook: warp-specialized producers never signal their slots
     std::string fresh(const char *p) { return std::string(p) + std::to_string(tmp++); }
@@ -102,6 +103,10 @@ void emit_prologue(Emitter &e)
     o << "static __device__ __forceinline__ float ls_ld_bf16(const void* p, int i) {"
          " return __uint_as_float(((unsigned)__ldg((const ls_u16*)p + i)) << 16); }\n";
     o << "static __device__ __forceinline__ float ls_sh_ld(const void* p, int i) { return ((const float*)p)[i]; }\n";
+    // point coordinates and results stream through once: evict-first in L1 and
+    // L2 (ld/st .cs), so that the coefficient lines stay resident in L2
+    o << "static __device__ __forceinline__ float ls_ld_pt(const float* p) { return __ldcs(p); }\n";
+    o << "static __device__ __forceinline__ void ls_st_out(float* p, float v) { __stcs(p, v); }\n";
     o << "static __device__ __forceinline__ float ls_ld_f16(const void* p, int i) {"
          " ls_u16 h = __ldg((const ls_u16*)p + i); float f; asm(\"cvt.f32.f16 %0, %1;\" : \"=f\"(f) : \"h\"(h));"
          " return f; }\n";
@@ -277,18 +282,20 @@ unsigned long long coset_lut(const Table &t)
 int shift_key(int psi, int r, int neg, int kmod4) { return ((psi * 3 + r) * 2 + neg) * 4 + kmod4; }
 
 struct ShiftRule {
-    unsigned long long mx = 0, my = 0;
+    unsigned long long mask[3] = {0, 0, 0};
     double base = 0.0, best = 0.0;        // mean sectors per class: copy 0 only, with the rule
 };
 
-ShiftRule shift_rule(const Table &t, const std::vector<std::vector<I3>> &region_sites, int elem_bytes)
+// nax = 2: copies shifted on x and y (4); nax = 3: also on z (8).
+ShiftRule shift_rule(const Table &t, const std::vector<std::vector<I3>> &region_sites, int elem_bytes, int nax)
 {
     ShiftRule rule;
     const bool fold = t.fold == LS_FOLD_SIGNED_PERM;
     const int a = t.scale;
     const int C = (int)t.cosets.size();
     const int per_sector = 32 / elem_bytes;
-    struct Cls { int kx, ky; int rx, ry, nx, ny, psi; int cnt[4]; };
+    const int ncopy = 1 << nax;
+    struct Cls { int key[3]; std::vector<int> cnt; };
     std::vector<Cls> cls;
     int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
     const int np = fold ? 6 : 1, ns = fold ? 8 : 1;
@@ -306,12 +313,11 @@ ShiftRule shift_rule(const Table &t, const std::vector<std::vector<I3>> &region_
                     const int *p = perms[pi];           // reference axis r lands on Cartesian axis p[r]
                     const int g[3] = {sg & 1, (sg >> 1) & 1, (sg >> 2) & 1};   // sign bit of reference axis r
                     // more than two sub-regions do not fit the 64-bit key: the rule then ignores psi
-                    Cls c{kq[0], kq[1], 0, 0, 0, 0, region_sites.size() <= 2 ? (int)psi : 0, {0, 0, 0, 0}};
-                    for (int r = 0; r < 3; ++r) {
-                        if (p[r] == 0) c.rx = r, c.nx = g[r];
-                        if (p[r] == 1) c.ry = r, c.ny = g[r];
-                    }
-                    for (int cp = 0; cp < 4; ++cp) {
+                    const int pk = region_sites.size() <= 2 ? (int)psi : 0;
+                    Cls c;
+                    for (int r = 0; r < 3; ++r) c.key[p[r]] = shift_key(pk, r, g[r], kq[p[r]]);
+                    c.cnt.assign(ncopy, 0);
+                    for (int cp = 0; cp < ncopy; ++cp) {
                         std::set<long long> sec;
                         for (const auto &sref : region_sites[psi]) {
                             int n[3];
@@ -328,8 +334,7 @@ ShiftRule shift_rule(const Table &t, const std::vector<std::vector<I3>> &region_
                             } else {
                                 for (int i = 0; i < 3; ++i) q[i] = n[i];
                             }
-                            q[0] += cp & 1;
-                            q[1] += cp >> 1;
+                            for (int i = 0; i < nax; ++i) q[i] += (cp >> i) & 1;
                             const long long bk = (q[0] >> 1) + 1000LL * ((q[1] >> 1) + 1000LL * (q[2] >> 1));
                             const int w = (q[0] & 1) + 2 * (q[1] & 1) + 4 * (q[2] & 1);
                             sec.insert(((bk * 8 + w) * C + j) / per_sector);
@@ -339,33 +344,28 @@ ShiftRule shift_rule(const Table &t, const std::vector<std::vector<I3>> &region_
                     cls.push_back(c);
                 }
     if (cls.empty()) return rule;
-    std::vector<int> rx(64, 0), ry(64, 0);
-    for (int it = 0; it < 4; ++it) {
-        for (int axis = 0; axis < 2; ++axis) {
+    std::vector<std::vector<int>> rr(3, std::vector<int>(64, 0));
+    auto copy_of = [&](const Cls &c, int axis, int bit) {
+        int cp = 0;
+        for (int i = 0; i < nax; ++i) cp |= (i == axis ? bit : rr[i][c.key[i]]) << i;
+        return cp;
+    };
+    for (int it = 0; it < 4; ++it)
+        for (int axis = 0; axis < nax; ++axis) {
             std::vector<long long> tot0(64, 0), tot1(64, 0);
             for (const auto &c : cls) {
-                const int kx = shift_key(c.psi, c.rx, c.nx, c.kx), ky = shift_key(c.psi, c.ry, c.ny, c.ky);
-                if (axis == 0) {
-                    tot0[kx] += c.cnt[0 + 2 * ry[ky]];
-                    tot1[kx] += c.cnt[1 + 2 * ry[ky]];
-                } else {
-                    tot0[ky] += c.cnt[rx[kx] + 0];
-                    tot1[ky] += c.cnt[rx[kx] + 2];
-                }
+                tot0[c.key[axis]] += c.cnt[copy_of(c, axis, 0)];
+                tot1[c.key[axis]] += c.cnt[copy_of(c, axis, 1)];
             }
-            auto &rr = axis == 0 ? rx : ry;
-            for (int k = 0; k < 64; ++k) rr[k] = tot1[k] < tot0[k] ? 1 : 0;
+            for (int k = 0; k < 64; ++k) rr[axis][k] = tot1[k] < tot0[k] ? 1 : 0;
         }
-    }
     double base = 0, best = 0;
     for (const auto &c : cls) {
         base += c.cnt[0];
-        best += c.cnt[rx[shift_key(c.psi, c.rx, c.nx, c.kx)] + 2 * ry[shift_key(c.psi, c.ry, c.ny, c.ky)]];
+        best += c.cnt[copy_of(c, 0, rr[0][c.key[0]])];
     }
-    for (int k = 0; k < 64; ++k) {
-        rule.mx |= (unsigned long long)rx[k] << k;
-        rule.my |= (unsigned long long)ry[k] << k;
-    }
+    for (int i = 0; i < nax; ++i)
+        for (int k = 0; k < 64; ++k) rule.mask[i] |= (unsigned long long)rr[i][k] << k;
     rule.base = base / (double)cls.size();
     rule.best = best / (double)cls.size();
     return rule;
@@ -375,7 +375,8 @@ ShiftRule shift_rule(const Table &t, const std::vector<std::vector<I3>> &region_
 // stencil of a tensor-product spline), for the copy-choice rule.
 void setup_brick_shift(Emitter &e, const Table &t, int brick, ls_dtype dt)
 {
-    e.brick_shift = brick == 2;
+    e.brick_shift = brick == 2 || brick == 3;
+    e.shift_axes = brick == 3 ? 3 : 2;
     if (!e.brick_shift) return;
     std::vector<std::vector<I3>> rs;
     if (!t.sep.empty()) {
@@ -387,9 +388,8 @@ void setup_brick_shift(Emitter &e, const Table &t, int brick, ls_dtype dt)
     } else {
         for (const auto &r : t.ref) rs.push_back(r.sites);
     }
-    const ShiftRule rule = shift_rule(t, rs, dt == LS_F32 ? 4 : 2);
-    e.shift_mx = rule.mx;
-    e.shift_my = rule.my;
+    const ShiftRule rule = shift_rule(t, rs, dt == LS_F32 ? 4 : 2, e.shift_axes);
+    for (int i = 0; i < 3; ++i) e.shift_mask[i] = rule.mask[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -423,7 +423,7 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
     if (e.brick) {
         o << "    const int BA0 = CU, BA1 = 2 * CU, BA2 = 4 * CU;\n";
         if (e.brick_shift) {
-            // the four shifted copies: bricks over the padded extents, copy (sx, sy)
+            // the shifted copies: bricks over the padded extents, copy (sx, sy[, sz])
             // chosen per point (shift_rule), Q = CS elements per copy
             o << "    const int BH0 = 8 * CU, BH1 = BH0 * ((ex0 + 2) >> 1), BH2 = BH1 * ((ex1 + 2) >> 1);\n";
             auto key = [&](int i) {
@@ -432,9 +432,12 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
                 const std::string ps = t.ref.size() <= 2 ? "psi" : "0";
                 return "((" + ps + " * 3 + " + r + ") * 2 + " + ng + ") * 4 + (k" + std::to_string(i) + " & 3)";
             };
-            o << "    const int sx = (int)((" << e.shift_mx << "ull >> (" << key(0) << ")) & 1ull);\n";
-            o << "    const int sy = (int)((" << e.shift_my << "ull >> (" << key(1) << ")) & 1ull);\n";
-            o << "    const int cbase = (sx + 2 * sy) * CS;\n";
+            const char *sn[3] = {"sx", "sy", "sz"};
+            for (int i = 0; i < e.shift_axes; ++i)
+                o << "    const int " << sn[i] << " = (int)((" << e.shift_mask[i] << "ull >> (" << key(i)
+                  << ")) & 1ull);\n";
+            if (e.shift_axes == 3) o << "    const int cbase = (sx + 2 * sy + 4 * sz) * CS;\n";
+            else o << "    const int cbase = (sx + 2 * sy) * CS;\n";
         } else {
             o << "    const int BH0 = " << (D == 3 ? 8 : 4) << " * CU, BH1 = BH0 * (ex0 >> 1), BH2 = BH1 * (ex1 >> 1);\n";
         }
@@ -515,7 +518,7 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
     };
     if (a == 1) {
         if (e.brick_shift) {
-            emit_brick_class(0, "(k0 + sx)", "(k1 + sy)", "k2", "cbase");
+            emit_brick_class(0, "(k0 + sx)", "(k1 + sy)", e.shift_axes == 3 ? "(k2 + sz)" : "k2", "cbase");
         } else if (e.brick) {
             emit_brick_class(0, "k0", D >= 2 ? "k1" : "0", D == 3 ? "k2" : "0", "0");
         } else {
@@ -527,9 +530,9 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
     } else {
         const unsigned long long lut = coset_lut(t);
         for (int i = 0; i < D; ++i)
-            if (e.brick_shift && i < 2)
-                o << "      const int qh" << i << " = (k" << i << " >> 1) + " << (i ? "sy" : "sx") << ", cb" << i
-                  << " = k" << i << " & 1;\n";
+            if (e.brick_shift && i < e.shift_axes)
+                o << "      const int qh" << i << " = (k" << i << " >> 1) + " << (i == 0 ? "sx" : i == 1 ? "sy" : "sz")
+                  << ", cb" << i << " = k" << i << " & 1;\n";
             else
                 o << "      const int qh" << i << " = k" << i << " >> 1, cb" << i << " = k" << i << " & 1;\n";
         std::set<int> classes;
@@ -626,8 +629,9 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             if (e.brick) {
                 o << "        const int adr = " << (e.brick_shift ? "cbase + cid" : "cid");
                 for (int i = 0; i < D; ++i) {
-                    if (e.brick_shift && i < 2) {
-                        const std::string g = "((n" + std::to_string(i) + " >> 1) + " + (i ? "sy)" : "sx)");
+                    if (e.brick_shift && i < e.shift_axes) {
+                        const std::string g = "((n" + std::to_string(i) + " >> 1) + " +
+                                              (i == 0 ? "sx)" : i == 1 ? "sy)" : "sz)");
                         o << " + BA" << i << " * " << g << " + BB" << i << " * (" << g << " >> 1)";
                     } else {
                         o << " + BA" << i << " * (n" << i << " >> 1) + BB" << i << " * ((n" << i << " >> 1) >> 1)";
@@ -645,8 +649,8 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             if (e.brick) {
                 o << "        const int adr = " << (e.brick_shift ? "cbase" : "0");
                 for (int i = 0; i < D; ++i) {
-                    if (e.brick_shift && i < 2) {
-                        const std::string g = "(n" + std::to_string(i) + (i ? " + sy)" : " + sx)");
+                    if (e.brick_shift && i < e.shift_axes) {
+                        const std::string g = "(n" + std::to_string(i) + (i == 0 ? " + sx)" : i == 1 ? " + sy)" : " + sz)");
                         o << " + BA" << i << " * " << g << " + BB" << i << " * (" << g << " >> 1)";
                     } else {
                         o << " + BA" << i << " * n" << i << " + BB" << i << " * (n" << i << " >> 1)";
@@ -1199,7 +1203,7 @@ void emit_point_load(Emitter &e, const Table &t, const char *skip = "continue")
     auto &o = e.o;
     const int D = t.dim;
     for (int i = 0; i < D; ++i)
-        o << "    const float x" << i << " = __ldg(a.pts + (size_t)i * " << D << " + " << i << ");\n";
+        o << "    const float x" << i << " = ls_ld_pt(a.pts + (size_t)i * " << D << " + " << i << ");\n";
     o << "    if (!(";
     for (int i = 0; i < D; ++i) o << (i ? " && " : "") << "fabsf(x" << i << ") < 4194304.0f";
     o << ")) {\n";
@@ -1284,19 +1288,19 @@ void emit_eval_point(Emitter &e, const Table &t, const ls_variant &var, const St
         }
     }
     if (grad) {
-        o << "    if (a.out) a.out[i] = " << fv << ";\n";
+        o << "    if (a.out) ls_st_out(a.out + i, " << fv << ");\n";
         // chain rule back to Cartesian axes: df/dy_i = sign_i * g[ref axis landing on i]
         for (int i = 0; i < D; ++i) {
             if (t.fold == LS_FOLD_SIGNED_PERM) {
                 o << "    { const float gg = ";
                 for (int r = 0; r < D - 1; ++r) o << "(ri" << i << " == " << r << ") ? " << g[r] << " : ";
-                o << g[D - 1] << "; a.grad[(size_t)i * " << D << " + " << i << "] = ng" << i << " ? -gg : gg; }\n";
+                o << g[D - 1] << "; ls_st_out(a.grad + (size_t)i * " << D << " + " << i << ", ng" << i << " ? -gg : gg); }\n";
             } else {
-                o << "    a.grad[(size_t)i * " << D << " + " << i << "] = " << g[i] << ";\n";
+                o << "    ls_st_out(a.grad + (size_t)i * " << D << " + " << i << ", " << g[i] << ");\n";
             }
         }
     } else {
-        o << "    a.out[i] = " << fv << ";\n";
+        o << "    ls_st_out(a.out + i, " << fv << ");\n";
     }
     o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
 }
@@ -1356,16 +1360,16 @@ void emit_eval_point_hess(Emitter &e, const Table &t, const ls_variant &var, con
             }
         }
     }
-    o << "    if (a.out) a.out[i] = " << res[0] << ";\n";
+    o << "    if (a.out) ls_st_out(a.out + i, " << res[0] << ");\n";
     const bool fold = t.fold == LS_FOLD_SIGNED_PERM;
     o << "    if (a.grad) {\n";
     for (int i = 0; i < D; ++i) {
         if (fold) {
             o << "    { const float gg = ";
             for (int r = 0; r < D - 1; ++r) o << "(ri" << i << " == " << r << ") ? " << res[1 + r] << " : ";
-            o << res[1 + D - 1] << "; a.grad[(size_t)i * " << D << " + " << i << "] = ng" << i << " ? -gg : gg; }\n";
+            o << res[1 + D - 1] << "; ls_st_out(a.grad + (size_t)i * " << D << " + " << i << ", ng" << i << " ? -gg : gg); }\n";
         } else {
-            o << "    a.grad[(size_t)i * " << D << " + " << i << "] = " << res[1 + i] << ";\n";
+            o << "    ls_st_out(a.grad + (size_t)i * " << D << " + " << i << ", " << res[1 + i] << ");\n";
         }
     }
     o << "    }\n";
@@ -1392,10 +1396,10 @@ void emit_eval_point_hess(Emitter &e, const Table &t, const ls_variant &var, con
                                   : "(ri" + std::to_string(ca) + " == " + std::to_string(r1) + ") ? (" + inner +
                                         ") : (" + sel + ")";
             }
-            o << "    { const float hh = " << sel << "; a.hess[(size_t)i * " << NH << " + " << q << "] = (ng" << ca
-              << " ^ ng" << cb << ") ? -hh : hh; }\n";
+            o << "    { const float hh = " << sel << "; ls_st_out(a.hess + (size_t)i * " << NH << " + " << q << ", (ng" << ca
+              << " ^ ng" << cb << ") ? -hh : hh); }\n";
         } else {
-            o << "    a.hess[(size_t)i * " << NH << " + " << q << "] = " << href(ca, cb) << ";\n";
+            o << "    ls_st_out(a.hess + (size_t)i * " << NH << " + " << q << ", " << href(ca, cb) << ");\n";
         }
     }
     o << "  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
@@ -1483,7 +1487,7 @@ void emit_eval_kernel_reuse(Emitter &e, const Table &t, const ls_variant &var, c
     }
     std::string sel = fk[K - 1];
     for (int k = (int)K - 2; k >= 0; --k) sel = "(psi == " + std::to_string(k) + ") ? " + fk[k] + " : (" + sel + ")";
-    o << "    a.out[i] = " << sel << ";\n";
+    o << "    ls_st_out(a.out + i, " << sel << ");\n";
     o << "    }\n  }\n#undef LS_OUT_OF_RANGE\n}\n\n";
     info.fma_value = e.fma - fma0;
 }
@@ -1969,7 +1973,7 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
     o << "    int stt = 2;\n";
     for (int q = 0; q < 3; ++q) o << "    float x" << q << " = 0.0f;\n";
     o << "    if (have && i < a.n) {\n";
-    for (int q = 0; q < D; ++q) o << "      x" << q << " = __ldg(a.pts + (size_t)i * " << D << " + " << q << ");\n";
+    for (int q = 0; q < D; ++q) o << "      x" << q << " = ls_ld_pt(a.pts + (size_t)i * " << D << " + " << q << ");\n";
     o << "      if (";
     for (int q = 0; q < D; ++q) o << (q ? " && " : "") << "fabsf(x" << q << ") < 4194304.0f";
     o << ") stt = 0;\n      else {\n        const bool isn = ";
@@ -2070,9 +2074,9 @@ void emit_eval_kernel_tensor(Emitter &e, const Table &t, const ls_variant &var, 
         out.push_back(nm);
     }
     if (!grad) {
-        o << "      a.out[pi] = tf;\n";
+        o << "      ls_st_out(a.out + pi, tf);\n";
     } else {
-        o << "      if (a.out) a.out[pi] = tf;\n";
+        o << "      if (a.out) ls_st_out(a.out + pi, tf);\n";
         // back to Cartesian axes: df/dx_i = sign_i * g[reference axis landing on i]
         for (int q = 0; q < D; ++q) {
             if (fold) {
@@ -2260,9 +2264,9 @@ int emit_eval_kernel_staged(Emitter &e, const Table &t, const ls_variant &var, c
     o << "    bool good = false;\n";
     o << "    int kk[3] = {0, 0, 0};\n";
     o << "    if (i < a.n) {\n";
-    o << "      x0 = __ldg(a.pts + (size_t)i * " << D << ");\n";
-    o << "      x1 = __ldg(a.pts + (size_t)i * " << D << " + 1);\n";
-    if (D == 3) o << "      x2 = __ldg(a.pts + (size_t)i * 3 + 2);\n";
+    o << "      x0 = ls_ld_pt(a.pts + (size_t)i * " << D << ");\n";
+    o << "      x1 = ls_ld_pt(a.pts + (size_t)i * " << D << " + 1);\n";
+    if (D == 3) o << "      x2 = ls_ld_pt(a.pts + (size_t)i * 3 + 2);\n";
     o << "      good = fabsf(x0) < 4194304.0f && fabsf(x1) < 4194304.0f && fabsf(x2) < 4194304.0f;\n";
     o << "    }\n";
     o << "    if (good) {\n";
@@ -2551,7 +2555,7 @@ int emit_adjoint_tiled(Emitter &e, const Table &t, const ls_variant &var, const 
     o << "    bool good = false;\n";
     o << "    int kk[3] = {0, 0, 0};\n";
     o << "    if (i < a.n) {\n";
-    for (int q = 0; q < D; ++q) o << "      x" << q << " = __ldg(a.pts + (size_t)i * " << D << " + " << q << ");\n";
+    for (int q = 0; q < D; ++q) o << "      x" << q << " = ls_ld_pt(a.pts + (size_t)i * " << D << " + " << q << ");\n";
     o << "      gp = __ldg(a.gout + i);\n";
     o << "      good = gp != 0.0f";
     for (int q = 0; q < D; ++q) o << " && fabsf(x" << q << ") < 4194304.0f";

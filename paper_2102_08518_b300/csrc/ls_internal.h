@@ -135,6 +135,7 @@ struct ls_volume_s {
 inline int vol_cstride(const ls_volume_s *v)
 {
     if (v->layout == LS_LAYOUT_BRICKED_SHIFTED) return (int)(v->total_elems / 4);
+    if (v->layout == LS_LAYOUT_BRICKED_SHIFTED_XYZ) return (int)(v->total_elems / 8);
     return v->layout == LS_LAYOUT_COSET_MAJOR ? (int)v->coset_elems : 1;
 }
 inline int vol_cunit(const ls_volume_s *v)

@@ -26,7 +26,9 @@ __device__ __forceinline__ double load_any(const void *p, int dt, long long i)
 // 0 coset-major, 1 interleaved, 2 bricked (2 x 2 x 2 grid indices per brick,
 // 2 x 2 in 2D (e2 == 1), cosets interleaved inside, x fastest), 3 four bricked
 // copies whose brick grids are shifted by (sx, sy) in {0,1}^2 grid indices
-// (copy sx + 2 sy over extents e0 + 2, e1 + 2, e2; copy 0 is read here).
+// (copy sx + 2 sy over extents e0 + 2, e1 + 2, e2; copy 0 is read here), 4 the
+// same with eight copies shifted on all three axes (copy sx + 2 sy + 4 sz over
+// extents e0 + 2, e1 + 2, e2 + 2).
 __device__ __forceinline__ long long brick_index(int ncos, int e0, int e1, int e2, int j, int q0, int q1, int q2)
 {
     const int bv = e2 == 1 ? 4 : 8;
@@ -41,6 +43,7 @@ __device__ __forceinline__ long long lay_index(const LayoutGeom &g, int j, int q
     if (g.layout == 0) return (long long)j * g.per + lin;
     if (g.layout == 1) return lin * g.ncos + j;
     if (g.layout == 3) return brick_index(g.ncos, g.e0 + 2, g.e1 + 2, g.e2, j, q0, q1, q2);
+    if (g.layout == 4) return brick_index(g.ncos, g.e0 + 2, g.e1 + 2, g.e2 + 2, j, q0, q1, q2);
     return brick_index(g.ncos, g.e0, g.e1, g.e2, j, q0, q1, q2);
 }
 
@@ -62,13 +65,15 @@ __device__ __forceinline__ void brick_decode(long long i, int ncos, int e0, int 
 // (coset, grid index) of element i; false for the padding of layout 3
 __device__ __forceinline__ bool lay_decode(const LayoutGeom &g, long long i, int &j, int &q0, int &q1, int &q2)
 {
-    if (g.layout == 3) {
-        const long long copy_elems = (long long)g.ncos * (g.e0 + 2) * (g.e1 + 2) * g.e2;
+    if (g.layout == 3 || g.layout == 4) {
+        const int pz = g.layout == 4 ? 2 : 0;
+        const long long copy_elems = (long long)g.ncos * (g.e0 + 2) * (g.e1 + 2) * (g.e2 + pz);
         const int c = (int)(i / copy_elems);
-        brick_decode(i % copy_elems, g.ncos, g.e0 + 2, g.e1 + 2, g.e2, j, q0, q1, q2);
+        brick_decode(i % copy_elems, g.ncos, g.e0 + 2, g.e1 + 2, g.e2 + pz, j, q0, q1, q2);
         q0 -= c & 1;
-        q1 -= c >> 1;
-        return q0 >= 0 && q0 < g.e0 && q1 >= 0 && q1 < g.e1;
+        q1 -= (c >> 1) & 1;
+        q2 -= c >> 2;
+        return q0 >= 0 && q0 < g.e0 && q1 >= 0 && q1 < g.e1 && q2 >= 0 && q2 < g.e2;
     }
     if (g.layout == 2) {
         brick_decode(i, g.ncos, g.e0, g.e1, g.e2, j, q0, q1, q2);
@@ -301,6 +306,7 @@ cudaError_t relayout(const void *src, const LayoutGeom &sg, void *dst, const Lay
 long long layout_elems(const LayoutGeom &g)
 {
     if (g.layout == 3) return 4LL * g.ncos * (g.e0 + 2) * (g.e1 + 2) * g.e2;
+    if (g.layout == 4) return 8LL * g.ncos * (g.e0 + 2) * (g.e1 + 2) * (g.e2 + 2);
     return (long long)g.ncos * g.per;
 }
 

@@ -16,8 +16,9 @@ struct LayoutGeom {
     long long per;
     int e0, e1, e2;
 };
-// Elements a layout holds (ncos * per; the four shifted bricked copies of
-// layout 3 hold 4 ncos (e0 + 2)(e1 + 2) e2, their padding zero).
+// Elements a layout holds (ncos * per; the shifted bricked copies of layout 3
+// hold 4 ncos (e0 + 2)(e1 + 2) e2, those of layout 4 8 ncos (e0 + 2)(e1 + 2)
+// (e2 + 2), their padding zero).
 long long layout_elems(const LayoutGeom &g);
 // Conversion of all layout_elems(dg) elements from layout sg to layout dg (same
 // cosets and extents), dtypes as in convert.

@@ -84,7 +84,7 @@ extern "C" ls_status ls_volume_texture_sync(ls_volume v, ls_stream stream)
     if (!v) return ls_fail(LS_ERR_INVALID_ARG, "volume is NULL");
     const ls::Table &t = v->spline->table;
     if (t.sep.empty() || t.dim != 3 || t.cosets.size() != 1 || v->spline->dtype != LS_F32 ||
-        v->layout == LS_LAYOUT_BRICKED || v->layout == LS_LAYOUT_BRICKED_SHIFTED)
+        v->layout >= LS_LAYOUT_BRICKED)
         return ls_fail(LS_ERR_UNSUPPORTED,
                        "linear fetch needs a 3D tensor-product spline with FP32 coefficients in one array");
     for (const auto &ax : t.sep)

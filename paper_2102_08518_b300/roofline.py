@@ -15,9 +15,9 @@ def shift_masks(kernel_source: str):
     """The copy-choice masks (x, y) a generated kernel for the shifted bricked
     copies carries (see the generator's shift_rule)."""
     import re
-    m = re.findall(r"const int s([xy]) = \(int\)\(\((\d+)ull >> ", kernel_source)
+    m = re.findall(r"const int s([xyz]) = \(int\)\(\((\d+)ull >> ", kernel_source)
     d = {k: int(v) for k, v in m}
-    return d["x"], d["y"]
+    return tuple(d[a] for a in "xyz" if a in d)
 
 
 def stencil_indices(table, ext, pts: np.ndarray, layout: str = "coset", masks=None) -> np.ndarray:
@@ -61,10 +61,9 @@ def stencil_indices(table, ext, pts: np.ndarray, layout: str = "coset", masks=No
         sign = np.ones((n, D), dtype=np.int64)
         yref = y
     regions = np.array([table.region_of(r) for r in yref]) if len(table.regions) > 1 else np.zeros(n, int)
-    shift = np.zeros((n, 2), dtype=np.int64)
-    if layout == "bricked_shifted":
-        mx, my = masks
-        for i, mask in ((0, mx), (1, my)):
+    shift = np.zeros((n, 3), dtype=np.int64)
+    if layout in ("bricked_shifted", "bricked_shifted_xyz"):
+        for i, mask in enumerate(masks):
             if table.fold == "hyperoctahedral":
                 r_i = np.argmax(order == i, axis=1)
                 neg = (sign[:, i] < 0).astype(np.int64)
@@ -104,13 +103,14 @@ def stencil_indices(table, ext, pts: np.ndarray, layout: str = "coset", masks=No
                 bk = idx[:, 0] // 2 + (e[0] // 2) * (idx[:, 1] // 2 + (e[1] // 2) * (i2 // 2))
                 w = idx[:, 0] % 2 + 2 * (idx[:, 1] % 2) + 4 * (i2 % 2)
                 lin = (bk * (8 if D == 3 else 4) + w) * C + cid
-            elif layout == "bricked_shifted":
+            elif layout in ("bricked_shifted", "bricked_shifted_xyz"):
                 sh = shift[m]
-                j0, j1, j2 = idx[:, 0] + sh[:, 0], idx[:, 1] + sh[:, 1], idx[:, 2]
+                pz = 2 if layout == "bricked_shifted_xyz" else 0
+                j0, j1, j2 = idx[:, 0] + sh[:, 0], idx[:, 1] + sh[:, 1], idx[:, 2] + sh[:, 2]
                 bk = j0 // 2 + ((e[0] + 2) // 2) * (j1 // 2 + ((e[1] + 2) // 2) * (j2 // 2))
                 w = j0 % 2 + 2 * (j1 % 2) + 4 * (j2 % 2)
-                copy = C * (e[0] + 2) * (e[1] + 2) * e[2]
-                lin = (sh[:, 0] + 2 * sh[:, 1]) * copy + (bk * 8 + w) * C + cid
+                copy = C * (e[0] + 2) * (e[1] + 2) * (e[2] + pz)
+                lin = (sh[:, 0] + 2 * sh[:, 1] + 4 * sh[:, 2]) * copy + (bk * 8 + w) * C + cid
             elif layout == "interleaved":
                 lin = q * C + cid
             else:

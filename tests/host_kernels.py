@@ -37,6 +37,8 @@ static inline float __uint_as_float(unsigned v) { float f; std::memcpy(&f, &v, 4
 static inline int __float_as_int(float v) { int i; std::memcpy(&i, &v, 4); return i; }
 static inline unsigned __float_as_uint(float v) { unsigned i; std::memcpy(&i, &v, 4); return i; }
 static inline int __float2int_rz(float v) { return v != v ? 0 : (int)v; }
+static inline float __ldcs(const float* p) { return *p; }
+static inline void __stcs(float* p, float v) { *p = v; }
 
 """
 
@@ -67,7 +69,9 @@ class HostKernels:
     def __init__(self, name: str, dtype: str = "f32", expansion: str = "sparse", **var):
         src = generated_source(name, dtype, expansion, **var)
         tag = api.kernel_name(name, dtype, expansion=expansion, **var)
-        lines = [ln for ln in src.splitlines() if ln.startswith(("typedef", "struct LsEvalArgs", "#define LS_CSWAP"))]
+        lines = [ln for ln in src.splitlines() if ln.startswith(("typedef", "struct LsEvalArgs", "#define LS_CSWAP",
+                                                                 "static __device__ __forceinline__ float ls_ld_pt",
+                                                                 "static __device__ __forceinline__ void ls_st_out"))]
         loader = {"f32": "ls_ld_f32", "bf16": "ls_ld_bf16", "f16": "ls_ld_f16"}[dtype]
         ld = [ln for ln in src.splitlines() if ln.startswith("static __device__ __forceinline__ float " + loader + "(")]
         body = [_function(src, f"ls_{w}_pt__{tag}") for w in ("eval", "eval_grad", "eval_hess")]
@@ -105,8 +109,9 @@ class HostKernels:
         e = list(ext) + [1] * (3 - len(ext))
         P = int(np.prod(ext))
         copy = n_cosets * (e[0] + 2) * (e[1] + 2) * e[2]
+        copy3 = n_cosets * (e[0] + 2) * (e[1] + 2) * (e[2] + 2)
         cs, cu = {"coset": (P, 1), "interleaved": (1, n_cosets), "bricked": (1, n_cosets),
-                  "bricked_shifted": (copy, n_cosets)}[layout]
+                  "bricked_shifted": (copy, n_cosets), "bricked_shifted_xyz": (copy3, n_cosets)}[layout]
         coef = np.ascontiguousarray(coef)
         ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
         fn = getattr(self.lib, "host_" + what)

@@ -41,18 +41,18 @@ def _case(name, n=1500, seed=2):
 
 def _layout(coef, C, ext, layout):
     flat = coef.ravel()
-    if layout == "bricked_shifted":
-        return brick_shifted_np(flat, C, ext)
+    if layout.startswith("bricked_shifted"):
+        return brick_shifted_np(flat, C, ext, xyz=layout.endswith("xyz"))
     return {"coset": flat, "interleaved": interleave_np(flat, C), "bricked": brick_np(flat, C, ext)}[layout]
 
 
-BRICK = {"coset": 0, "interleaved": 0, "bricked": 1, "bricked_shifted": 2}
+BRICK = {"coset": 0, "interleaved": 0, "bricked": 1, "bricked_shifted": 2, "bricked_shifted_xyz": 3}
 
 
 @pytest.mark.parametrize("name", list(SPEC))
-@pytest.mark.parametrize("layout", ["coset", "interleaved", "bricked", "bricked_shifted"])
+@pytest.mark.parametrize("layout", ["coset", "interleaved", "bricked", "bricked_shifted", "bricked_shifted_xyz"])
 def test_value_and_gradient(name, layout):
-    if layout == "bricked_shifted" and name == "zp":
+    if layout.startswith("bricked_shifted") and name == "zp":
         pytest.skip("the shifted bricked copies are 3D only")
     voronoi = name.startswith("voronoi")
     lat, ext, C, coef, pts = _case(name, n=200 if voronoi else 1500)

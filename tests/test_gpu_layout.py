@@ -32,7 +32,7 @@ NAMES = ["tricubic", "trilinear", "triquadratic", "bcc_linear", "bcc_quintic", "
          "voronoi2_bcc", "voronoi2_fcc"]
 LAYOUTS = ["interleaved", "bricked"]
 # the evaluation kernels also read the shifted bricked copies (3D)
-EVAL_LAYOUTS = LAYOUTS + ["bricked_shifted"]
+EVAL_LAYOUTS = LAYOUTS + ["bricked_shifted", "bricked_shifted_xyz"]
 
 
 def n_cosets(name):
@@ -61,18 +61,19 @@ def brick_np(coef, C, ext):
     return np.ascontiguousarray(a.transpose(1, 3, 2, 4, 0)).ravel()
 
 
-def brick_shifted_np(coef, C, ext):
-    """coset-major -> the four shifted bricked copies: copy s0 + 2 s1 holds grid
-    index i at (i0 + s0, i1 + s1, i2) of a bricked array over extents
-    (e0 + 2, e1 + 2, e2), zero elsewhere."""
+def brick_shifted_np(coef, C, ext, xyz=False):
+    """coset-major -> the shifted bricked copies: copy s0 + 2 s1 (+ 4 s2) holds
+    grid index i at (i0 + s0, i1 + s1, i2 (+ s2)) of a bricked array over
+    extents (e0 + 2, e1 + 2, e2 (+ 2)), zero elsewhere."""
     e0, e1, e2 = ext
     a = coef.reshape(C, e2, e1, e0)
+    pz = 2 if xyz else 0
     out = []
-    for c in range(4):
-        s0, s1 = c & 1, c >> 1
-        pad = np.zeros((C, e2, e1 + 2, e0 + 2), dtype=coef.dtype)
-        pad[:, :, s1:s1 + e1, s0:s0 + e0] = a
-        out.append(brick_np(pad.ravel(), C, (e0 + 2, e1 + 2, e2)))
+    for c in range(8 if xyz else 4):
+        s0, s1, s2 = c & 1, (c >> 1) & 1, c >> 2
+        pad = np.zeros((C, e2 + pz, e1 + 2, e0 + 2), dtype=coef.dtype)
+        pad[:, s2:s2 + e2, s1:s1 + e1, s0:s0 + e0] = a
+        out.append(brick_np(pad.ravel(), C, (e0 + 2, e1 + 2, e2 + pz)))
     return np.concatenate(out)
 
 
@@ -87,8 +88,8 @@ def unbrick_np(arr, C, ext):
 
 
 def to_layout_np(coef, C, ext, layout):
-    if layout == "bricked_shifted":
-        return brick_shifted_np(coef, C, ext)
+    if layout in ("bricked_shifted", "bricked_shifted_xyz"):
+        return brick_shifted_np(coef, C, ext, xyz=layout.endswith("xyz"))
     return interleave_np(coef, C) if layout == "interleaved" else brick_np(coef, C, ext)
 
 
@@ -99,8 +100,8 @@ def from_layout_np(arr, C, ext, layout):
 def ivolume(name, ext, coef_np, dtype="f32", layout="interleaved", **kw):
     from paper_2102_08518_b300.api import Spline, Volume, TORCH_DTYPES
     c = torch.from_numpy(to_layout_np(coef_np, n_cosets(name), ext, layout)).to("cuda", TORCH_DTYPES[dtype])
-    if layout in ("bricked", "bricked_shifted"):
-        kw["brick"] = 1 if layout == "bricked" else 2
+    if layout in ("bricked", "bricked_shifted", "bricked_shifted_xyz"):
+        kw["brick"] = {"bricked": 1, "bricked_shifted": 2, "bricked_shifted_xyz": 3}[layout]
     return Volume(Spline(name, dtype, **kw), ext, c.contiguous(), layout=layout)
 
 
@@ -144,10 +145,11 @@ def test_relayout_matches_numpy_maps(C, ext, dtype):
         assert torch.equal(relayout(bk, C, ext, to="interleaved", src="bricked"), il)
         assert torch.equal(relayout(bk, C, ext, to="coset", src="bricked"), src)
         if len(ext) == 3:
-            sh = relayout(src, C, ext, to="bricked_shifted")
-            assert np.array_equal(sh.cpu().numpy(), brick_shifted_np(ref, C, ext))
-            assert torch.equal(relayout(sh, C, ext, to="coset", src="bricked_shifted"), src)
-            assert torch.equal(relayout(il, C, ext, to="bricked_shifted", src="interleaved"), sh)
+            for lay, xyz in (("bricked_shifted", False), ("bricked_shifted_xyz", True)):
+                sh = relayout(src, C, ext, to=lay)
+                assert np.array_equal(sh.cpu().numpy(), brick_shifted_np(ref, C, ext, xyz))
+                assert torch.equal(relayout(sh, C, ext, to="coset", src=lay), src)
+                assert torch.equal(relayout(il, C, ext, to=lay, src="interleaved"), sh)
 
 
 @pytest.mark.parametrize("layout", EVAL_LAYOUTS)
@@ -155,7 +157,7 @@ def test_relayout_matches_numpy_maps(C, ext, dtype):
 @pytest.mark.parametrize("n", [1, 33, 5003])
 def test_interleaved_eval_every_point(name, n, layout):
     """Points inside and beyond the arrays (unchecked and bounds-checked gathers)."""
-    if layout == "bricked_shifted" and name == "zp":
+    if layout.startswith("bricked_shifted") and name == "zp":
         pytest.skip("the shifted bricked copies are 3D only")
     lat = workloads.SPLINE_LATTICE[name]
     ext = SMALL_EXT[name]
@@ -171,7 +173,7 @@ def test_interleaved_eval_every_point(name, n, layout):
 @pytest.mark.parametrize("layout", EVAL_LAYOUTS)
 @pytest.mark.parametrize("name", NAMES)
 def test_interleaved_gradient(name, layout):
-    if layout == "bricked_shifted" and name == "zp":
+    if layout.startswith("bricked_shifted") and name == "zp":
         pytest.skip("the shifted bricked copies are 3D only")
     if name.startswith("voronoi"):
         pytest.skip("C0 Voronoi-spline gradients: tests/test_gpu_eval.py (coset-major) and the host kernel tests")
@@ -303,7 +305,7 @@ def test_interleaved_cg_fit_equals_coset_major_fit(layout):
     assert np.allclose(ha, hb, rtol=1e-3)
 
 
-@pytest.mark.parametrize("layout", EVAL_LAYOUTS)
+@pytest.mark.parametrize("layout", LAYOUTS + ["bricked_shifted"])
 @pytest.mark.parametrize("name", ["bcc_linear", "bcc_quintic"])
 def test_interleaved_bcc_full_size_sampled(name, layout):
     """BCC 2 x 128^3, 2^24 uniform and 2^24 ray points, in the autotuned launch
