@@ -770,7 +770,8 @@ def extra_batched(torch, dev, vols, pts, outs):
 def extra_tricubic_64(torch, dev, vols, pts, outs):
     """Tricubic on a 64^3 volume (U[-1,1], seed 0) at 2^18 points U([2,61]^3):
     100 launches replayed from one CUDA graph (the kernel takes microseconds),
-    one coefficient array and the bricked layout."""
+    one coefficient array, the bricked layout and the eight shifted bricked
+    copies (vector gathers: the stencil is two whole bricks per axis)."""
     from paper_2102_08518_b300.api import Spline, Volume, relayout
     ext = (64, 64, 64)
     n = 1 << 18
@@ -780,7 +781,10 @@ def extra_tricubic_64(torch, dev, vols, pts, outs):
     res = {"workload": "tricubic 64^3 (1 MiB), 2^18 uniform points in [2,61]^3, 100 launches per graph replay"}
     for lay, vol in (("array", Volume(Spline("tricubic", "f32"), ext, c)),
                      ("bricked", Volume(Spline("tricubic", "f32", brick=1), ext, relayout(c, 1, ext, to="bricked"),
-                                        layout="bricked"))):
+                                        layout="bricked")),
+                     ("bricked_shifted_xyz", Volume(Spline("tricubic", "f32", brick=3), ext,
+                                                    relayout(c, 1, ext, to="bricked_shifted_xyz"),
+                                                    layout="bricked_shifted_xyz"))):
         vol.eval(p, out)
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
@@ -918,7 +922,8 @@ def extra_cg(torch, dev, vols, pts, outs):
 PROFILE_CASES = ("fcc6_eval", "quintic_eval_interleaved", "quintic_eval_bricked", "quintic_eval_bricked_shifted",
                  "quintic_eval_rays_interleaved", "linear_eval_interleaved", "linear_eval_rays_interleaved",
                  "quintic_adjoint_atomic", "quintic_adjoint_fixed", "quintic_hessian", "tricubic_linear_fetch",
-                 "morton_sort", "morton_sort_2e24", "fcc6_eval_sorted", "fcc6_eval_staged")
+                 "morton_sort", "morton_sort_2e24", "fcc6_eval_sorted", "fcc6_eval_staged", "tricubic_eval_coset",
+                 "tricubic_eval_bricked", "tricubic_eval_bricked_shifted_xyz")
 
 
 def run_profile_case(name: str):
@@ -969,6 +974,19 @@ def run_profile_case(name: str):
         else:
             det = "fixed" if name.endswith("fixed") else False
             fn = lambda: vol.adjoint(p, g, dcoef=dc, deterministic=det)
+    elif name.startswith("tricubic_eval_"):
+        # CC 128^3 U[-1,1] (the paper's order-4 grid), 2^24 uniform points
+        from paper_2102_08518_b300.api import LAYOUT_BRICK
+        lay = name[len("tricubic_eval_"):]
+        ext = (128, 128, 128)
+        c = relayout(torch.from_numpy(workloads.coef_uniform("cc", ext, seed=1)).to(dev), 1, ext, to=lay) \
+            if lay != "coset" else torch.from_numpy(workloads.coef_uniform("cc", ext, seed=1)).to(dev)
+        vol = Volume(Spline("tricubic", "f32", **({"brick": LAYOUT_BRICK[lay]} if LAYOUT_BRICK[lay] else {})), ext, c,
+                     layout=lay)
+        lo, hi = workloads.inner_box("tricubic", ext)
+        p = torch.from_numpy(workloads.points_uniform(n, lo, hi, seed=2)).to(dev)
+        out = torch.empty(n, device=dev)
+        fn = lambda: vol.eval(p, out)
     elif name.startswith("morton_sort"):
         from paper_2102_08518_b300.api import morton_scratch_bytes, morton_sort
         n = 1 << (24 if name.endswith("2e24") else 26)

@@ -406,6 +406,23 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
     const int D = t.dim;
     const bool fold = t.fold == LS_FOLD_SIGNED_PERM;
     const int a = t.scale;
+    // Vector gathers: on the eight shifted copies a Cartesian stencil that is a
+    // box of even, contiguous extent per axis starts on a brick boundary in the
+    // copy chosen by the parity of its first site, so it is a box of whole
+    // 2 x 2 x 2 bricks, each 32 contiguous bytes: two 16-byte loads per brick.
+    int vlo[3] = {0, 0, 0}, vn[3] = {1, 1, 1};
+    bool vec = e.brick_shift && e.shift_axes == 3 && D == 3 && a == 1 && t.cosets.size() == 1 && load &&
+               !declare_addr && group == 0 && e.ld == "ls_ld_f32" && !fold && !sites.empty();
+    if (vec) {
+        for (int i = 0; i < 3; ++i) {
+            std::set<int> vals;
+            for (const auto &sv : sites) vals.insert(sv[i]);
+            vlo[i] = *vals.begin();
+            vn[i] = (int)vals.size();
+            vec = vec && vn[i] % 2 == 0 && *vals.rbegin() - vlo[i] + 1 == vn[i];
+        }
+        vec = vec && (size_t)(vn[0] * vn[1] * vn[2]) == sites.size();
+    }
     o << "    const int ex0 = E0, ex1 = E1" << (D == 3 ? ", ex2 = E2" : "") << ";\n";
     o << "    bool inside = true;\n";
     for (int i = 0; i < D; ++i)
@@ -433,9 +450,13 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
                 return "((" + ps + " * 3 + " + r + ") * 2 + " + ng + ") * 4 + (k" + std::to_string(i) + " & 3)";
             };
             const char *sn[3] = {"sx", "sy", "sz"};
-            for (int i = 0; i < e.shift_axes; ++i)
-                o << "    const int " << sn[i] << " = (int)((" << e.shift_mask[i] << "ull >> (" << key(i)
-                  << ")) & 1ull);\n";
+            for (int i = 0; i < e.shift_axes; ++i) {
+                if (vec)   // the copy in which the stencil starts on a brick boundary on every axis
+                    o << "    const int " << sn[i] << " = (k" << i << " + (" << vlo[i] << ")) & 1;\n";
+                else
+                    o << "    const int " << sn[i] << " = (int)((" << e.shift_mask[i] << "ull >> (" << key(i)
+                      << ")) & 1ull);\n";
+            }
             if (e.shift_axes == 3) o << "    const int cbase = (sx + 2 * sy + 4 * sz) * CS;\n";
             else o << "    const int cbase = (sx + 2 * sy) * CS;\n";
         } else {
@@ -445,6 +466,27 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
         o << "    (void)BA2; (void)BB2;\n";
     }
     o << "    if (inside) {\n";
+    if (vec) {
+        o << "      const float* vb_ = (const float*)" << coef_expr << " + cbase + ((k0 + (" << vlo[0]
+          << ") + sx) >> 1) * BH0 + ((k1 + (" << vlo[1] << ") + sy) >> 1) * BH1 + ((k2 + (" << vlo[2]
+          << ") + sz) >> 1) * BH2;\n";
+        const char *comp = "xyzw";
+        for (int b2 = 0; b2 < vn[2] / 2; ++b2)
+            for (int b1 = 0; b1 < vn[1] / 2; ++b1)
+                for (int b0 = 0; b0 < vn[0] / 2; ++b0) {
+                    const std::string nm = "vq" + std::to_string(b0) + std::to_string(b1) + std::to_string(b2);
+                    const std::string off = std::to_string(b0) + " * BH0 + " + std::to_string(b1) + " * BH1 + " +
+                                            std::to_string(b2) + " * BH2";
+                    o << "      const float4 " << nm << "_0 = __ldg((const float4*)(vb_ + " << off << "));\n";
+                    o << "      const float4 " << nm << "_1 = __ldg((const float4*)(vb_ + " << off << " + 4));\n";
+                }
+        for (size_t j = 0; j < sites.size(); ++j) {
+            const int o0 = sites[j][0] - vlo[0], o1 = sites[j][1] - vlo[1], o2 = sites[j][2] - vlo[2];
+            const int w = (o0 & 1) + 2 * (o1 & 1) + 4 * (o2 & 1);
+            o << "      c" << j << " = vq" << (o0 >> 1) << (o1 >> 1) << (o2 >> 1) << "_" << (w >> 2) << "."
+              << comp[w & 3] << ";\n";
+        }
+    } else {
     // strides of the reference axes (the linear part)
     const char *st_lin[3] = {"CU", "(CU * ex0)", "(CU * ex0 * ex1)"};
     const char *st_brk[3] = {"BA0", "BA1", "BA2"};
@@ -601,6 +643,7 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
         } else {
             o << "      c" << j << " = " << e.ld << "(" << coef_expr << ", " << addr << ");\n";
         }
+    }
     }
     o << "    } else {\n";
     for (size_t j = 0; j < sites.size(); ++j) {

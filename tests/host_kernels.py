@@ -31,6 +31,7 @@ SHIM = r"""
 #define __device__
 #define __forceinline__ inline
 #define __restrict__
+struct alignas(16) float4 { float x, y, z, w; };
 template <class T> static inline T __ldg(const T* p) { return *p; }
 static inline float __int_as_float(int v) { float f; std::memcpy(&f, &v, 4); return f; }
 static inline float __uint_as_float(unsigned v) { float f; std::memcpy(&f, &v, 4); return f; }
