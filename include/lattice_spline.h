@@ -246,13 +246,16 @@ typedef struct {
                                           consumer wait runs out after wait_limit rounds and the
                                           kernel returns with the status word set and the outputs
                                           unwritten.  0 otherwise */
+    int32_t prefetch;                  /* 1: each thread of the value and value + gradient kernels
+                                          loads the coordinates of its next point before it
+                                          evaluates the current one (FMA kernels) */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */
 const char *ls_status_str(ls_status s);
 /* Message of the last failing call on this thread ("" if none). */
 const char *ls_last_error(void);
-/* Layout version of the structs above (5: ls_variant ends with wait_probe);
+/* Layout version of the structs above (6: ls_variant ends with prefetch);
  * bindings compare it with their own before any other call. */
 int32_t ls_abi_version(void);
 /* Test hooks for failure detection (host-side injection; nothing faults on the

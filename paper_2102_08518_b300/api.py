@@ -79,7 +79,8 @@ def _ptr(t: Optional[torch.Tensor]):
 def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_blocks: int = 0, group: int = 0,
                 depth: int = 0, pts_per_thread: int = 1, blocks_per_sm: int = 0, expansion: str = "sparse",
                 brick: int = 0, pipeline: int = 0, producers: int = 0, stage: int = 0, tensor: int = 0,
-                tensor_kind: int = 0, plain_transform: int = 0, wait_limit: int = 0, wait_probe: int = 0) -> str:
+                tensor_kind: int = 0, plain_transform: int = 0, wait_limit: int = 0, wait_probe: int = 0,
+                prefetch: int = 0) -> str:
     """The name tag of a generated kernel variant (blocks_per_sm only sizes the
     grid, so it shares the compiled kernel)."""
     return f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + ("_br" if branchy else "") + \
@@ -88,7 +89,7 @@ def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_b
         (f"_bk{brick}" if brick >= 2 else "_bk" if brick else "") + ("_pp" if pipeline else "") + (f"_ws{producers}" if producers else "") + \
         (f"_st{stage}" if stage else "") + (("_tc" + (str(tensor) if tensor > 1 else "")) if tensor else "") + \
         ("h" if tensor and tensor_kind else "") + ("_pt" if plain_transform else "") + \
-        (f"_wl{wait_limit}" if wait_limit else "") + ("_wp" if wait_probe else "")
+        (f"_wl{wait_limit}" if wait_limit else "") + ("_wp" if wait_probe else "") + ("_pf" if prefetch else "")
 
 
 class Spline:
@@ -98,7 +99,7 @@ class Spline:
                  min_blocks: int = 0, group: int = 0, depth: int = 0, pts_per_thread: int = 1,
                  blocks_per_sm: int = 0, expansion: str = "sparse", brick: int = 0, pipeline: int = 0,
                  producers: int = 0, stage: int = 0, tensor: int = 0, tensor_kind: int = 0,
-                 plain_transform: int = 0, wait_limit: int = 0, wait_probe: int = 0,
+                 plain_transform: int = 0, wait_limit: int = 0, wait_probe: int = 0, prefetch: int = 0,
                  kernel_name: Optional[str] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("lattice spline kernels need a CUDA device")
@@ -111,7 +112,7 @@ class Spline:
         kname = kernel_name or globals()["kernel_name"](name, dtype, block, branchy, min_blocks, group, depth,
                                                          pts_per_thread, blocks_per_sm, expansion, brick, pipeline,
                                                          producers, stage, tensor, tensor_kind,
-                                                         plain_transform, wait_limit, wait_probe)
+                                                         plain_transform, wait_limit, wait_probe, prefetch)
         self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
                         "depth": depth, "pts_per_thread": pts_per_thread, "blocks_per_sm": blocks_per_sm,
                         "expansion": expansion}
@@ -133,12 +134,15 @@ class Spline:
             self.variant["wait_limit"] = wait_limit
         if wait_probe:
             self.variant["wait_probe"] = wait_probe
+        if prefetch:
+            self.variant["prefetch"] = 1
         self.kernel_name = kname
         self._desc = _abi.DescHolder(self.table, kname, expansion)
         var = _abi.variant(block=block, pts_per_thread=pts_per_thread, branchy=branchy, min_blocks=min_blocks,
                            group=group, depth=depth, blocks_per_sm=blocks_per_sm, brick=brick, pipeline=pipeline,
                            producers=producers, stage=stage, tensor=tensor, tensor_kind=tensor_kind,
-                           plain_transform=plain_transform, wait_limit=wait_limit, wait_probe=wait_probe)
+                           plain_transform=plain_transform, wait_limit=wait_limit, wait_probe=wait_probe,
+                           prefetch=prefetch)
         h = ctypes.c_void_p()
         torch.cuda.init()
         _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),
@@ -513,6 +517,8 @@ TUNE_CANDIDATES_SMALL = tuple([dict(block=256, blocks_per_sm=b, expansion=x) for
                               [dict(block=384, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(block=128, blocks_per_sm=b) for b in (2, 4)] +
                               [dict(block=384, min_blocks=2), dict(block=256, min_blocks=3)] +
+                              [dict(block=b, prefetch=1) for b in (256, 384, 512)] +
+                              [dict(block=256, blocks_per_sm=2, prefetch=1)] +
                               [dict(tensor=1, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(tensor=1, tensor_kind=1, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(tensor=4, tensor_kind=1)] +

@@ -242,7 +242,7 @@ ls_status get_kernel(ls_spline_s *s, const char *what, cudaKernel_t &k, int &per
 
 ls_variant default_variant(const ls_variant *v)
 {
-    ls_variant r{256, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    ls_variant r{256, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     if (v) {
         if (v->block > 0) r.block = v->block;
         if (v->pts_per_thread > 0) r.pts_per_thread = v->pts_per_thread > 64 ? 64 : v->pts_per_thread;
@@ -260,6 +260,7 @@ ls_variant default_variant(const ls_variant *v)
         r.plain_transform = v->plain_transform ? 1 : 0;
         r.wait_limit = v->wait_limit > 0 ? v->wait_limit : 0;
         r.wait_probe = v->wait_probe;
+        r.prefetch = v->prefetch ? 1 : 0;
     }
     return r;
 }
@@ -352,7 +353,7 @@ const char *ls_status_str(ls_status s)
 
 const char *ls_last_error(void) { return g_err.c_str(); }
 
-int32_t ls_abi_version(void) { return 5; }
+int32_t ls_abi_version(void) { return 6; }
 
 void ls_debug_fail_alloc(int32_t after)
 {

@@ -107,6 +107,11 @@ void emit_prologue(Emitter &e)
     // L2 (ld/st .cs), so that the coefficient lines stay resident in L2
     o << "static __device__ __forceinline__ float ls_ld_pt(const float* p) { return __ldcs(p); }\n";
     o << "static __device__ __forceinline__ void ls_st_out(float* p, float v) { __stcs(p, v); }\n";
+    // one 32-byte load (a whole sector) into eight floats: p must be 32-byte aligned
+    o << "static __device__ __forceinline__ void ls_ld8(const float* p, float& r0, float& r1, float& r2, float& r3,"
+         " float& r4, float& r5, float& r6, float& r7) { asm(\"ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6,"
+         " %7}, [%8];\" : \"=f\"(r0), \"=f\"(r1), \"=f\"(r2), \"=f\"(r3), \"=f\"(r4), \"=f\"(r5), \"=f\"(r6),"
+         " \"=f\"(r7) : \"l\"(p)); }\n";
     o << "static __device__ __forceinline__ float ls_ld_f16(const void* p, int i) {"
          " ls_u16 h = __ldg((const ls_u16*)p + i); float f; asm(\"cvt.f32.f16 %0, %1;\" : \"=f\"(f) : \"h\"(h));"
          " return f; }\n";
@@ -409,7 +414,7 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
     // Vector gathers: on the eight shifted copies a Cartesian stencil that is a
     // box of even, contiguous extent per axis starts on a brick boundary in the
     // copy chosen by the parity of its first site, so it is a box of whole
-    // 2 x 2 x 2 bricks, each 32 contiguous bytes: two 16-byte loads per brick.
+    // 2 x 2 x 2 bricks, each 32 contiguous bytes: one 32-byte load per brick.
     int vlo[3] = {0, 0, 0}, vn[3] = {1, 1, 1};
     bool vec = e.brick_shift && e.shift_axes == 3 && D == 3 && a == 1 && t.cosets.size() == 1 && load &&
                !declare_addr && group == 0 && e.ld == "ls_ld_f32" && !fold && !sites.empty();
@@ -470,21 +475,22 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
         o << "      const float* vb_ = (const float*)" << coef_expr << " + cbase + ((k0 + (" << vlo[0]
           << ") + sx) >> 1) * BH0 + ((k1 + (" << vlo[1] << ") + sy) >> 1) * BH1 + ((k2 + (" << vlo[2]
           << ") + sz) >> 1) * BH2;\n";
-        const char *comp = "xyzw";
         for (int b2 = 0; b2 < vn[2] / 2; ++b2)
             for (int b1 = 0; b1 < vn[1] / 2; ++b1)
                 for (int b0 = 0; b0 < vn[0] / 2; ++b0) {
                     const std::string nm = "vq" + std::to_string(b0) + std::to_string(b1) + std::to_string(b2);
                     const std::string off = std::to_string(b0) + " * BH0 + " + std::to_string(b1) + " * BH1 + " +
                                             std::to_string(b2) + " * BH2";
-                    o << "      const float4 " << nm << "_0 = __ldg((const float4*)(vb_ + " << off << "));\n";
-                    o << "      const float4 " << nm << "_1 = __ldg((const float4*)(vb_ + " << off << " + 4));\n";
+                    o << "      float " << nm << "_0";
+                    for (int w = 1; w < 8; ++w) o << ", " << nm << "_" << w;
+                    o << ";\n      ls_ld8(vb_ + " << off;
+                    for (int w = 0; w < 8; ++w) o << ", " << nm << "_" << w;
+                    o << ");\n";
                 }
         for (size_t j = 0; j < sites.size(); ++j) {
             const int o0 = sites[j][0] - vlo[0], o1 = sites[j][1] - vlo[1], o2 = sites[j][2] - vlo[2];
             const int w = (o0 & 1) + 2 * (o1 & 1) + 4 * (o2 & 1);
-            o << "      c" << j << " = vq" << (o0 >> 1) << (o1 >> 1) << (o2 >> 1) << "_" << (w >> 2) << "."
-              << comp[w & 3] << ";\n";
+            o << "      c" << j << " = vq" << (o0 >> 1) << (o1 >> 1) << (o2 >> 1) << "_" << w << ";\n";
         }
     } else {
     // strides of the reference axes (the linear part)
@@ -1241,12 +1247,11 @@ void emit_separable_body(Emitter &e, const Table &t, int grad, std::string &fval
     }
 }
 
-void emit_point_load(Emitter &e, const Table &t, const char *skip = "continue")
+// Out-of-range and NaN coordinates: zero (NaN for NaN) instead of a value.
+void emit_point_check(Emitter &e, const Table &t, const char *skip)
 {
     auto &o = e.o;
     const int D = t.dim;
-    for (int i = 0; i < D; ++i)
-        o << "    const float x" << i << " = ls_ld_pt(a.pts + (size_t)i * " << D << " + " << i << ");\n";
     o << "    if (!(";
     for (int i = 0; i < D; ++i) o << (i ? " && " : "") << "fabsf(x" << i << ") < 4194304.0f";
     o << ")) {\n";
@@ -1255,6 +1260,15 @@ void emit_point_load(Emitter &e, const Table &t, const char *skip = "continue")
     o << ";\n";
     o << "      LS_OUT_OF_RANGE(isn ? __int_as_float(0x7fffffff) : 0.0f);\n";
     o << "      " << skip << ";\n    }\n";
+}
+
+void emit_point_load(Emitter &e, const Table &t, const char *skip = "continue")
+{
+    auto &o = e.o;
+    const int D = t.dim;
+    for (int i = 0; i < D; ++i)
+        o << "    const float x" << i << " = ls_ld_pt(a.pts + (size_t)i * " << D << " + " << i << ");\n";
+    emit_point_check(e, t, skip);
 }
 
 std::string kname(const Table &t, const char *what)
@@ -1267,7 +1281,7 @@ std::string kname(const Table &t, const char *what)
 // Per-point evaluation of value [+ gradient] as a device function, reused by
 // the per-spline kernel and by batched (multi-volume) kernels.
 void emit_eval_point(Emitter &e, const Table &t, const ls_variant &var, const Stencil &st, int reach, bool grad,
-                     const std::string &fname, bool coords_args = false)
+                     const std::string &fname, bool coords_args = false, bool check = false)
 {
     auto &o = e.o;
     const int D = t.dim;
@@ -1290,6 +1304,7 @@ void emit_eval_point(Emitter &e, const Table &t, const ls_variant &var, const St
     }
     o << "  {\n";
     if (!coords_args) emit_point_load(e, t, "return");
+    else if (check) emit_point_check(e, t, "return");
     emit_classify(e, t);
     std::string fv;
     std::string g[3];
@@ -1542,13 +1557,37 @@ void emit_eval_kernel(Emitter &e, const Table &t, const ls_variant &var, const S
     auto &o = e.o;
     const int fma0 = e.fma;
     const std::string pf = kname(t, grad ? "eval_grad_pt" : "eval_pt");
-    emit_eval_point(e, t, var, st, reach, grad, pf);
-    o << "extern \"C\" __global__ void __launch_bounds__(" << var.block;
-    if (var.min_blocks > 0) o << ", " << var.min_blocks;
-    o << ") " << kname(t, grad ? "eval_grad" : "eval") << "(const LsEvalArgs a)\n{\n";
-    o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
-    o << "  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) " << pf
-      << "(a, i);\n}\n\n";
+    const int D = t.dim;
+    if (var.prefetch) {
+        // the coordinates of a thread's next point are loaded before the current
+        // point is evaluated, so their latency (HBM: the points stream through)
+        // is off the path of the gathers
+        emit_eval_point(e, t, var, st, reach, grad, pf + "_x", true, true);
+        o << "extern \"C\" __global__ void __launch_bounds__(" << var.block;
+        if (var.min_blocks > 0) o << ", " << var.min_blocks;
+        o << ") " << kname(t, grad ? "eval_grad" : "eval") << "(const LsEvalArgs a)\n{\n";
+        o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
+        o << "  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;\n";
+        o << "  float n0 = 0.0f, n1 = 0.0f, n2 = 0.0f;\n";
+        o << "  if (i < a.n) {";
+        for (int q = 0; q < D; ++q) o << " n" << q << " = ls_ld_pt(a.pts + (size_t)i * " << D << " + " << q << ");";
+        o << " }\n";
+        o << "  for (; i < a.n; i += stride) {\n";
+        o << "    const float x0 = n0, x1 = n1, x2 = n2;\n";
+        o << "    if (i + stride < a.n) {";
+        for (int q = 0; q < D; ++q)
+            o << " n" << q << " = ls_ld_pt(a.pts + (size_t)(i + stride) * " << D << " + " << q << ");";
+        o << " }\n";
+        o << "    " << pf << "_x(a, i, x0, x1, x2);\n  }\n}\n\n";
+    } else {
+        emit_eval_point(e, t, var, st, reach, grad, pf);
+        o << "extern \"C\" __global__ void __launch_bounds__(" << var.block;
+        if (var.min_blocks > 0) o << ", " << var.min_blocks;
+        o << ") " << kname(t, grad ? "eval_grad" : "eval") << "(const LsEvalArgs a)\n{\n";
+        o << "  const long long stride = (long long)gridDim.x * blockDim.x;\n";
+        o << "  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) " << pf
+          << "(a, i);\n}\n\n";
+    }
     if (grad) info.fma_grad = e.fma - fma0;
     else info.fma_value = e.fma - fma0;
 }

@@ -31,7 +31,9 @@ SHIM = r"""
 #define __device__
 #define __forceinline__ inline
 #define __restrict__
-struct alignas(16) float4 { float x, y, z, w; };
+static inline void ls_ld8(const float* p, float& r0, float& r1, float& r2, float& r3, float& r4, float& r5,
+                          float& r6, float& r7) { r0 = p[0]; r1 = p[1]; r2 = p[2]; r3 = p[3]; r4 = p[4]; r5 = p[5];
+                                                  r6 = p[6]; r7 = p[7]; }
 template <class T> static inline T __ldg(const T* p) { return *p; }
 static inline float __int_as_float(int v) { float f; std::memcpy(&f, &v, 4); return f; }
 static inline float __uint_as_float(unsigned v) { float f; std::memcpy(&f, &v, 4); return f; }
@@ -75,13 +77,24 @@ class HostKernels:
                                                                  "static __device__ __forceinline__ void ls_st_out"))]
         loader = {"f32": "ls_ld_f32", "bf16": "ls_ld_bf16", "f16": "ls_ld_f16"}[dtype]
         ld = [ln for ln in src.splitlines() if ln.startswith("static __device__ __forceinline__ float " + loader + "(")]
-        body = [_function(src, f"ls_{w}_pt__{tag}") for w in ("eval", "eval_grad", "eval_hess")]
+        # kernels that load a thread's next point ahead (variant prefetch) take
+        # the coordinates as arguments: the driver passes them
+        D = api.table(name).spline.lattice.dim
+        fn = {w: f"ls_{w}_pt__{tag}" + ("_x" if f"ls_{w}_pt__{tag}_x(" in src else "")
+              for w in ("eval", "eval_grad", "eval_hess")}
+        body = [_function(src, fn[w]) for w in ("eval", "eval_grad", "eval_hess")]
+
+        def call(w):
+            if fn[w].endswith("_x"):
+                z = "pts[i * 3 + 2]" if D == 3 else "0.0f"
+                return f"{fn[w]}(a, i, pts[i * {D}], pts[i * {D} + 1], {z})"
+            return f"{fn[w]}(a, i)"
         drivers = "".join(
             f'extern "C" void host_{w}(const float* pts, long long n, float* out, float* grad, float* hess,'
             f' const void* coef, int e0, int e1, int e2, int cs, int cu) {{\n'
             f'  LsEvalArgs a; std::memset(&a, 0, sizeof a); a.pts = pts; a.out = out; a.grad = grad; a.hess = hess;'
             f' a.coef = coef; a.n = n; a.e0 = e0; a.e1 = e1; a.e2 = e2; a.cstride = cs; a.cunit = cu;\n'
-            f'  for (long long i = 0; i < n; ++i) ls_{w}_pt__{tag}(a, i);\n}}\n'
+            f'  for (long long i = 0; i < n; ++i) {call(w)};\n}}\n'
             for w in ("eval", "eval_grad", "eval_hess"))
         code = SHIM + "\n".join(lines + ld) + "\n" + "\n".join(body) + drivers
         if dtype == "f16":

@@ -130,7 +130,8 @@ def test_factored_transform_is_cheaper():
 @pytest.mark.parametrize("name,var", [("bcc_quintic", {"group": 4, "depth": 2}), ("bcc_quintic", {"group": 8, "depth": 1}),
                                       ("fcc6", {"group": 2, "depth": 4}), ("fcc6", {"branchy": 1}),
                                       ("fcc6", {"branchy": 1, "brick": 1}), ("tricubic", {"group": 8, "depth": 2}),
-                                      ("bcc_linear", {"group": 1, "depth": 2})])
+                                      ("bcc_linear", {"group": 1, "depth": 2}), ("bcc_quintic", {"prefetch": 1}),
+                                      ("tricubic", {"prefetch": 1}), ("zp", {"prefetch": 1})])
 def test_paper_parameter_variants(name, var):
     """The paper's group size / pipeline depth (Algorithm 2) and branchy
     sub-region selection change the generated point function; each variant
