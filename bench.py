@@ -43,6 +43,9 @@ N_RAYS, RAY_STEPS = 4096, 4096
 CASES = [("bcc_linear", "uniform"), ("bcc_linear", "rays"), ("bcc_quintic", "uniform"), ("bcc_quintic", "rays")]
 WORKLOAD = ("bcc 2x128^3 smooth field; linear + quintic box splines; 2^24 uniform + 2^24 ray points "
             "(4096 rays x 4096 steps)")
+# the roofs of the run (SMs, SM clock under load, L2 sector rate, HBM rate),
+# set by the GPU arm for the extras' rooflines
+ROOF = {}
 LAYOUT = "auto"                 # coefficient layout of the step's volumes (--layout); "auto": per case the
                                 # faster of interleaved and bricked, both held in memory
 
@@ -387,6 +390,7 @@ def run_gpu(args):
             hbm_peak, hbm_src = float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured copy)"
     except (OSError, ValueError, KeyError):
         pass
+    ROOF.update(sms=sms, mhz=run_mhz, l2_gbs=peak_l2, hbm_gbs=hbm_peak)
     per_case = {}
     for (sp, ps), ms in zip(CASES, case_ms):
         n = N_UNIFORM if ps == "uniform" else N_RAYS * RAY_STEPS
@@ -818,7 +822,8 @@ def extra_paper_orders(torch, dev, vols, pts, outs):
     out = torch.empty(n, device=dev)
     for name, (lat, ext) in grids.items():
         ncos = len(workloads.LATTICES[lat][2])
-        c = relayout(workloads.coef_uniform_torch(lat, ext, seed=1), ncos, ext, to="interleaved")
+        c0 = workloads.coef_uniform_torch(lat, ext, seed=1)
+        c = relayout(c0, ncos, ext, to="interleaved")
         lo, hi = workloads.inner_box(name, ext)
         p = workloads.points_uniform_torch(n, lo, hi, seed=2)
         sp = Spline(name, "f32")
@@ -827,6 +832,14 @@ def extra_paper_orders(torch, dev, vols, pts, outs):
         info = sp.info()
         res[name] = {"gpoints_s": round(n / ms / 1e6, 3), "ms": round(ms, 4), "sites": info["n_sites"],
                      "fma_per_point": info["fma_value"], "reference_subregions": len(table(name).regions)}
+
+        def frac(t_ms):
+            from paper_2102_08518_b300.roofline import case_roofline
+            if not ROOF:
+                return None
+            return case_roofline(info["fma_value"], 4 * info["n_sites"], n, t_ms, ROOF["sms"], ROOF["mhz"],
+                                 ROOF["l2_gbs"], ROOF["hbm_gbs"])["frac"]
+        res[name]["roofline_frac"] = frac(ms)
         if len(table(name).regions) > 1:
             # the paper's branchy alternative to evaluating every sub-region and selecting
             vbr = Volume(Spline(name, "f32", branchy=1), ext, c, layout="interleaved")
@@ -844,32 +857,38 @@ def extra_paper_orders(torch, dev, vols, pts, outs):
             res[name]["linear_fetch_gpoints_s"] = round(n / mst / 1e6, 3)
             res[name]["linear_fetch_max_abs_err"] = round(err, 6)
             del cl, vl
-        if all(e % 2 == 0 for e in ext):
-            # the same volume in 2x2x2 bricks (fewer sectors and lines per stencil)
-            cb = relayout(c, ncos, ext, to="bricked", src="interleaved")
-            vb = Volume(Spline(name, "f32", brick=1), ext, cb, layout="bricked")
+        # the same volume in 2x2x2 bricks (fewer sectors and lines per stencil);
+        # odd extents (BCC 101^3, FCC 81^3) padded by one zero plane per axis,
+        # which leaves the spline unchanged (sites beyond the arrays are zero)
+        pext = tuple(e + (e & 1) for e in ext)
+        if pext != ext:
+            res[name]["bricked_padded_ext"] = list(pext)
+        cp = torch.nn.functional.pad(c0, [0, pext[0] - ext[0], 0, pext[1] - ext[1], 0, pext[2] - ext[2]])
+        for lay, brick in (("bricked", 1), ("bricked_shifted", 2), ("bricked_shifted_xyz", 3)):
+            # 2x2x2 bricks; four copies with brick grids shifted on x and y; eight,
+            # shifted on z too (a Cartesian stencil is whole bricks)
+            cb = relayout(cp, ncos, pext, to=lay)
+            vb = Volume(Spline(name, "f32", brick=brick), pext, cb, layout=lay)
             msb = time_ms(torch, lambda: vb.eval(p, out))
-            res[name]["bricked_gpoints_s"] = round(n / msb / 1e6, 3)
-            cs = relayout(c, ncos, ext, to="bricked_shifted", src="interleaved")
-            vs = Volume(Spline(name, "f32", brick=2), ext, cs, layout="bricked_shifted")
-            mss = time_ms(torch, lambda: vs.eval(p, out))
-            res[name]["bricked_shifted_gpoints_s"] = round(n / mss / 1e6, 3)
-            del cs, vs
-            if lat == "cc":
-                # eight copies, also shifted on z (a Cartesian sector is a whole brick)
-                cs = relayout(c, ncos, ext, to="bricked_shifted_xyz", src="interleaved")
-                vs = Volume(Spline(name, "f32", brick=3), ext, cs, layout="bricked_shifted_xyz")
-                mss = time_ms(torch, lambda: vs.eval(p, out))
-                res[name]["bricked_shifted_xyz_gpoints_s"] = round(n / mss / 1e6, 3)
-                del cs, vs
+            res[name][f"{lay}_gpoints_s"] = round(n / msb / 1e6, 3)
+            res[name][f"{lay}_roofline_frac"] = frac(msb)
             del cb, vb
-        del c, p, vol
+        best = max(v for k, v in res[name].items() if k == "gpoints_s" or
+                   (k.endswith("_gpoints_s") and k.startswith("bricked")))
+        res[name]["best_layout_gpoints_s"] = best
+        del c, c0, cp, p, vol
     res["order2_bcc_linear_vs_trilinear"] = round(res["bcc_linear"]["gpoints_s"] / res["trilinear"]["gpoints_s"], 3)
     res["order3_fcc6_vs_triquadratic"] = round(res["fcc6"]["gpoints_s"] / res["triquadratic"]["gpoints_s"], 3)
     res["order4_bcc_quintic_vs_tricubic"] = round(res["bcc_quintic"]["gpoints_s"] / res["tricubic"]["gpoints_s"], 3)
     res["order4_bcc_quartic_vs_tricubic"] = round(res["bcc_quartic"]["gpoints_s"] / res["tricubic"]["gpoints_s"], 3)
     for v in ("voronoi2_bcc", "voronoi2_fcc"):
         res[f"order2_{v}_vs_trilinear"] = round(res[v]["gpoints_s"] / res["trilinear"]["gpoints_s"], 3)
+    # the same comparisons with every spline in its fastest layout
+    for a, b, tag in (("bcc_linear", "trilinear", "order2"), ("fcc6", "triquadratic", "order3"),
+                      ("bcc_quintic", "tricubic", "order4"), ("bcc_quartic", "tricubic", "order4"),
+                      ("voronoi2_bcc", "trilinear", "order2"), ("voronoi2_fcc", "trilinear", "order2")):
+        res[f"{tag}_{a}_vs_{b}_best_layouts"] = round(res[a]["best_layout_gpoints_s"] /
+                                                      res[b]["best_layout_gpoints_s"], 3)
     return res
 
 

@@ -249,13 +249,17 @@ typedef struct {
     int32_t prefetch;                  /* 1: each thread of the value and value + gradient kernels
                                           loads the coordinates of its next point before it
                                           evaluates the current one (FMA kernels) */
+    int32_t l2_keep;                   /* 1: the value and value + gradient kernels load coefficients
+                                          with an L2 evict-last cache policy (createpolicy), so the
+                                          coefficient lines outlast the point and result streams,
+                                          which are loaded and stored evict-first.  0 otherwise */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */
 const char *ls_status_str(ls_status s);
 /* Message of the last failing call on this thread ("" if none). */
 const char *ls_last_error(void);
-/* Layout version of the structs above (6: ls_variant ends with prefetch);
+/* Layout version of the structs above (7: ls_variant ends with l2_keep);
  * bindings compare it with their own before any other call. */
 int32_t ls_abi_version(void);
 /* Test hooks for failure detection (host-side injection; nothing faults on the

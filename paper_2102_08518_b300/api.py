@@ -80,7 +80,7 @@ def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_b
                 depth: int = 0, pts_per_thread: int = 1, blocks_per_sm: int = 0, expansion: str = "sparse",
                 brick: int = 0, pipeline: int = 0, producers: int = 0, stage: int = 0, tensor: int = 0,
                 tensor_kind: int = 0, plain_transform: int = 0, wait_limit: int = 0, wait_probe: int = 0,
-                prefetch: int = 0) -> str:
+                prefetch: int = 0, l2_keep: int = 0) -> str:
     """The name tag of a generated kernel variant (blocks_per_sm only sizes the
     grid, so it shares the compiled kernel)."""
     return f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + ("_br" if branchy else "") + \
@@ -89,7 +89,8 @@ def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_b
         (f"_bk{brick}" if brick >= 2 else "_bk" if brick else "") + ("_pp" if pipeline else "") + (f"_ws{producers}" if producers else "") + \
         (f"_st{stage}" if stage else "") + (("_tc" + (str(tensor) if tensor > 1 else "")) if tensor else "") + \
         ("h" if tensor and tensor_kind else "") + ("_pt" if plain_transform else "") + \
-        (f"_wl{wait_limit}" if wait_limit else "") + ("_wp" if wait_probe else "") + ("_pf" if prefetch else "")
+        (f"_wl{wait_limit}" if wait_limit else "") + ("_wp" if wait_probe else "") + ("_pf" if prefetch else "") + \
+        ("_lk" if l2_keep else "")
 
 
 class Spline:
@@ -100,7 +101,7 @@ class Spline:
                  blocks_per_sm: int = 0, expansion: str = "sparse", brick: int = 0, pipeline: int = 0,
                  producers: int = 0, stage: int = 0, tensor: int = 0, tensor_kind: int = 0,
                  plain_transform: int = 0, wait_limit: int = 0, wait_probe: int = 0, prefetch: int = 0,
-                 kernel_name: Optional[str] = None):
+                 l2_keep: int = 0, kernel_name: Optional[str] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("lattice spline kernels need a CUDA device")
         self.name = name
@@ -112,7 +113,8 @@ class Spline:
         kname = kernel_name or globals()["kernel_name"](name, dtype, block, branchy, min_blocks, group, depth,
                                                          pts_per_thread, blocks_per_sm, expansion, brick, pipeline,
                                                          producers, stage, tensor, tensor_kind,
-                                                         plain_transform, wait_limit, wait_probe, prefetch)
+                                                         plain_transform, wait_limit, wait_probe, prefetch,
+                                                         l2_keep)
         self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
                         "depth": depth, "pts_per_thread": pts_per_thread, "blocks_per_sm": blocks_per_sm,
                         "expansion": expansion}
@@ -136,13 +138,15 @@ class Spline:
             self.variant["wait_probe"] = wait_probe
         if prefetch:
             self.variant["prefetch"] = 1
+        if l2_keep:
+            self.variant["l2_keep"] = 1
         self.kernel_name = kname
         self._desc = _abi.DescHolder(self.table, kname, expansion)
         var = _abi.variant(block=block, pts_per_thread=pts_per_thread, branchy=branchy, min_blocks=min_blocks,
                            group=group, depth=depth, blocks_per_sm=blocks_per_sm, brick=brick, pipeline=pipeline,
                            producers=producers, stage=stage, tensor=tensor, tensor_kind=tensor_kind,
                            plain_transform=plain_transform, wait_limit=wait_limit, wait_probe=wait_probe,
-                           prefetch=prefetch)
+                           prefetch=prefetch, l2_keep=l2_keep)
         h = ctypes.c_void_p()
         torch.cuda.init()
         _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),
@@ -519,6 +523,8 @@ TUNE_CANDIDATES_SMALL = tuple([dict(block=256, blocks_per_sm=b, expansion=x) for
                               [dict(block=384, min_blocks=2), dict(block=256, min_blocks=3)] +
                               [dict(block=b, prefetch=1) for b in (256, 384, 512)] +
                               [dict(block=256, blocks_per_sm=2, prefetch=1)] +
+                              [dict(block=b) for b in (640, 672)] +
+                              [dict(block=b, l2_keep=1) for b in (384, 512, 672)] +
                               [dict(tensor=1, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(tensor=1, tensor_kind=1, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(tensor=4, tensor_kind=1)] +

@@ -53,6 +53,7 @@ struct Emitter {
     unsigned long long shift_mask[3] = {0, 0, 0};   // their copy-choice rule (shift_rule)
     int wait_rounds = 1 << 20;        // try_wait rounds of a bounded wait (ls_mbar_wait; polls: x4)
     bool no_signal = false;           // test hook: warp-specialized producers never signal their slots
+    bool l2_keep = false;             // coefficient loads carry an L2 evict-last cache policy
     std::string fresh(const char *p) { return std::string(p) + std::to_string(tmp++); }
 };
 
@@ -98,10 +99,29 @@ void emit_prologue(Emitter &e)
     auto &o = e.o;
     o << "// generated by the lattice spline code generator; do not edit\n";
     o << "typedef unsigned short ls_u16;\n";
-    o << "static __device__ __forceinline__ float ls_ld_f32(const void* p, int i) {"
-         " return __ldg((const float*)p + i); }\n";
-    o << "static __device__ __forceinline__ float ls_ld_bf16(const void* p, int i) {"
-         " return __uint_as_float(((unsigned)__ldg((const ls_u16*)p + i)) << 16); }\n";
+    if (e.l2_keep) {
+        // coefficient loads with an L2 evict-last policy: the volume's lines
+        // outlast the evict-first point and result streams (the policy is a
+        // pure value: one createpolicy per kernel after common-subexpression
+        // elimination)
+        o << "static __device__ __forceinline__ unsigned long long ls_keep_pol() { unsigned long long q;"
+             " asm(\"createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\" : \"=l\"(q)); return q; }\n";
+        o << "static __device__ __forceinline__ float ls_ldk_f32(const float* p) { float v;"
+             " asm(\"ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;\" : \"=f\"(v) : \"l\"(p), \"l\"(ls_keep_pol()));"
+             " return v; }\n";
+        o << "static __device__ __forceinline__ ls_u16 ls_ldk_u16(const ls_u16* p) { ls_u16 v;"
+             " asm(\"ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;\" : \"=h\"(v) : \"l\"(p), \"l\"(ls_keep_pol()));"
+             " return v; }\n";
+        o << "static __device__ __forceinline__ float ls_ld_f32(const void* p, int i) {"
+             " return ls_ldk_f32((const float*)p + i); }\n";
+        o << "static __device__ __forceinline__ float ls_ld_bf16(const void* p, int i) {"
+             " return __uint_as_float(((unsigned)ls_ldk_u16((const ls_u16*)p + i)) << 16); }\n";
+    } else {
+        o << "static __device__ __forceinline__ float ls_ld_f32(const void* p, int i) {"
+             " return __ldg((const float*)p + i); }\n";
+        o << "static __device__ __forceinline__ float ls_ld_bf16(const void* p, int i) {"
+             " return __uint_as_float(((unsigned)__ldg((const ls_u16*)p + i)) << 16); }\n";
+    }
     o << "static __device__ __forceinline__ float ls_sh_ld(const void* p, int i) { return ((const float*)p)[i]; }\n";
     // point coordinates and results stream through once: evict-first in L1 and
     // L2 (ld/st .cs), so that the coefficient lines stay resident in L2
@@ -113,7 +133,7 @@ void emit_prologue(Emitter &e)
          " %7}, [%8];\" : \"=f\"(r0), \"=f\"(r1), \"=f\"(r2), \"=f\"(r3), \"=f\"(r4), \"=f\"(r5), \"=f\"(r6),"
          " \"=f\"(r7) : \"l\"(p)); }\n";
     o << "static __device__ __forceinline__ float ls_ld_f16(const void* p, int i) {"
-         " ls_u16 h = __ldg((const ls_u16*)p + i); float f; asm(\"cvt.f32.f16 %0, %1;\" : \"=f\"(f) : \"h\"(h));"
+         " ls_u16 h = " << (e.l2_keep ? "ls_ldk_u16" : "__ldg") << "((const ls_u16*)p + i); float f; asm(\"cvt.f32.f16 %0, %1;\" : \"=f\"(f) : \"h\"(h));"
          " return f; }\n";
     o << "struct LsEvalArgs { const float* pts; float* out; float* grad; const void* coef;"
          " long long n; int e0, e1, e2, cstride, cunit; unsigned* status; float* hess; const void* tmap; };\n";
@@ -3064,6 +3084,7 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
     e.sym = !var.plain_transform;
     if (var.wait_limit > 0) e.wait_rounds = var.wait_limit;
     e.no_signal = var.wait_probe == 1;
+    e.l2_keep = var.l2_keep == 1;
     emit_prologue(e);
     Stencil st = union_stencil(t);
     int reach = 0;

@@ -42,6 +42,8 @@ static inline unsigned __float_as_uint(float v) { unsigned i; std::memcpy(&i, &v
 static inline int __float2int_rz(float v) { return v != v ? 0 : (int)v; }
 static inline float __ldcs(const float* p) { return *p; }
 static inline void __stcs(float* p, float v) { *p = v; }
+static inline float ls_ldk_f32(const float* p) { return *p; }
+static inline unsigned short ls_ldk_u16(const unsigned short* p) { return *p; }
 
 """
 

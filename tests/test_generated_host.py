@@ -131,7 +131,8 @@ def test_factored_transform_is_cheaper():
                                       ("fcc6", {"group": 2, "depth": 4}), ("fcc6", {"branchy": 1}),
                                       ("fcc6", {"branchy": 1, "brick": 1}), ("tricubic", {"group": 8, "depth": 2}),
                                       ("bcc_linear", {"group": 1, "depth": 2}), ("bcc_quintic", {"prefetch": 1}),
-                                      ("tricubic", {"prefetch": 1}), ("zp", {"prefetch": 1})])
+                                      ("tricubic", {"prefetch": 1}), ("zp", {"prefetch": 1}),
+                                      ("bcc_quintic", {"l2_keep": 1}), ("fcc6", {"l2_keep": 1, "prefetch": 1})])
 def test_paper_parameter_variants(name, var):
     """The paper's group size / pipeline depth (Algorithm 2) and branchy
     sub-region selection change the generated point function; each variant
@@ -149,10 +150,12 @@ def test_paper_parameter_variants(name, var):
     assert np.abs(g - wgrad).max() <= GTOL * cmax
 
 
+@pytest.mark.parametrize("l2_keep", [0, 1])
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
-def test_reduced_precision_loaders(dtype):
-    """BF16 / FP16 storage: the loaders widen exactly, so the result equals
-    the oracle fed the rounded coefficients."""
+def test_reduced_precision_loaders(dtype, l2_keep):
+    """BF16 / FP16 storage: the loaders (with and without the L2 evict-last
+    policy) widen exactly, so the result equals the oracle fed the rounded
+    coefficients."""
     import torch
     name = "bcc_quintic"
     lat, ext, C, coef, pts = _case(name, n=600)
@@ -161,5 +164,5 @@ def test_reduced_precision_loaders(dtype):
     raw = t.view(torch.int16).numpy().view(np.uint16)
     spec = SPEC[name]().with_extent(ext)
     want = oracle.eval_sum(spec, rounded, pts.astype(np.float64))
-    f = HostKernels(name, dtype).eval(pts, raw, ext, "coset", C)
+    f = HostKernels(name, dtype, **({"l2_keep": 1} if l2_keep else {})).eval(pts, raw, ext, "coset", C)
     assert np.abs(f - want).max() <= TOL * float(np.abs(rounded).max())

@@ -215,10 +215,16 @@ def test_adjoint_atomic_matches_oracle(name, warp):
     spec = ORACLE_SPEC[name]().with_extent(ext)
     want = oracle.adjoint(spec, pts.astype(np.float64), g.astype(np.float64))
     got = dc.cpu().numpy().astype(np.float64)
-    assert np.max(np.abs(got - want)) <= 2e-6 * max(1.0, np.abs(want).max()) * 8
-    # dot-product identity with the forward kernel
+    tol_adj = 2e-6 * max(1.0, np.abs(want).max()) * 8
+    assert np.max(np.abs(got - want)) <= tol_adj
+    # dot-product identity with the forward kernel: <A c, g> = <c, A^T g> holds
+    # exactly, so the two FP32 results differ by at most their per-value error
+    # bounds (forward TOL max|c| per point, adjoint tol_adj per site) weighted
+    # by |g| and |c|; the sums themselves may cancel to almost nothing
     fwd = gpu_eval(vol, pts)
-    assert abs(fwd @ g.astype(np.float64) - got @ coef.ravel().astype(np.float64)) <= 1e-4 * np.abs(fwd @ g)
+    c64 = coef.ravel().astype(np.float64)
+    bound = TOL * np.abs(coef).max() * np.abs(g).sum() + tol_adj * np.abs(c64).sum()
+    assert abs(fwd @ g.astype(np.float64) - got @ c64) <= bound
 
 
 @pytest.mark.parametrize("dtype,bound", [("bf16", 2.0 ** -8), ("f16", 2.0 ** -11)])
