@@ -238,6 +238,29 @@ def time_ms(torch, fn, reps=10, warm=3):
     return s.elapsed_time(e) / reps
 
 
+def step_choice(key: str, value=None):
+    """Read (value None) or store the step's layout choice in the autotuning
+    cache file of the package's kernel cache."""
+    from paper_2102_08518_b300 import api
+    path = os.path.join(api._CACHE_DIR, "autotune.json")
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    if value is None:
+        return cache.get(key)
+    cache[key] = value
+    try:
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return value
+
+
 def kernel_hash(kernel_source: str, kernel: str):
     """Hash of the generated code one evaluation kernel runs: its coefficient
     loader, its point function and the kernel itself (not the other kernels and
@@ -296,12 +319,10 @@ def run_gpu(args):
     coefs = {lay: coef_cm if lay == "coset" else relayout(coef_cm, 2, EXT, to=lay) for lay in layouts}
     pts = {k: torch.from_numpy(v).to(dev) for k, v in pts_np.items()}
     outs = {k: torch.empty(v.shape[0], device=dev) for k, v in pts.items()}
-    # evaluation kernel variant (and layout) per (spline, point set), autotuned on
-    # the step's own points (untimed); the layout is the one whose autotuned
-    # variant recorded the lower time (timed here if no record has one)
-    tuned, case_layout = {}, {}
+    # evaluation kernel variant per (spline, point set, layout), autotuned on the
+    # step's own points (untimed)
+    per_lay = {}
     for sp, ps in CASES:
-        best = None
         for lay in layouts:
             s_ = autotune(sp, "f32", EXT, coefs[lay], [pts[ps]], candidates=TUNE_CANDIDATES_SMALL,
                           tag=f"bcc_step_{ps}", layout=lay)
@@ -314,9 +335,40 @@ def run_gpu(args):
                     v_ = Volume(s_, EXT, coefs[lay], layout=lay)
                     ms_ = time_ms(torch, lambda: v_.eval(pts[ps], outs[ps]))
                     del v_
-            if best is None or ms_ < best[0]:
-                best = (ms_, s_, lay)
-        tuned[(sp, ps)], case_layout[(sp, ps)] = best[1], best[2]
+            per_lay[(sp, ps, lay)] = (ms_, s_)
+    # the layout per case: every combination whose layouts are within 10 % of
+    # each case's fastest is timed as a whole step (untimed here), since the
+    # cases share L2 and a layout another case just read starts warm
+    import itertools
+    choices = []
+    for sp, ps in CASES:
+        b = min(per_lay[(sp, ps, lay)][0] for lay in layouts)
+        choices.append([lay for lay in layouts if per_lay[(sp, ps, lay)][0] <= 1.10 * b])
+    combos = list(itertools.product(*choices))
+    best_combo = combos[0]
+    # the choice is kept beside the autotuner's records, keyed by the candidate
+    # kernels, so a second run (a profiler's) launches only the step's kernels
+    combo_key = "bcc_step_layouts|" + torch.cuda.get_device_name() + "|" + ";".join(
+        f"{sp}/{ps}:" + ",".join(f"{lay}={per_lay[(sp, ps, lay)][1].kernel_name}" for lay in ch)
+        for (sp, ps), ch in zip(CASES, choices))
+    known = step_choice(combo_key)
+    if known is not None and tuple(known) in combos:
+        best_combo = tuple(known)
+    elif len(combos) > 1:
+        vols_ = {(sp, ps, lay): Volume(per_lay[(sp, ps, lay)][1], EXT, coefs[lay], layout=lay)
+                 for (sp, ps), ch in zip(CASES, choices) for lay in ch}
+        best_t = None
+        for combo in combos:
+            def step_(combo=combo):
+                for (sp, ps), lay in zip(CASES, combo):
+                    vols_[(sp, ps, lay)].eval(pts[ps], outs[ps])
+            t_ = time_ms(torch, step_, reps=10)
+            if best_t is None or t_ < best_t:
+                best_t, best_combo = t_, combo
+        del vols_
+        step_choice(combo_key, list(best_combo))
+    tuned = {(sp, ps): per_lay[(sp, ps, lay)][1] for (sp, ps), lay in zip(CASES, best_combo)}
+    case_layout = {(sp, ps): lay for (sp, ps), lay in zip(CASES, best_combo)}
     base_layout = layouts[0]                                # the extras' volumes
     # hold only the layouts the step reads (and the extras' one) from here on:
     # every resident copy competes for L2 with the others
@@ -524,6 +576,8 @@ def run_gpu(args):
               "config": {"workload": WORKLOAD, "points_per_step": pts_per_step, "coef_bytes": coef_np.nbytes,
                          "coef_layouts_resident": sorted(coefs),
                          "coef_layout": {f"{sp}/{ps}": case_layout[(sp, ps)] for sp, ps in CASES},
+                         "coef_layout_choice": f"{len(combos)} combinations of layouts within 10 % of each "
+                                               "case's autotuned fastest, timed as whole steps (untimed)",
                          "l2": "points 201 MB per set > 126 MB L2 (inputs larger than L2); coefficient volume "
                                "16 MiB L2-resident by design", "parallelism": f"replicas x{world}"},
               "per_case": per_case, "roofline": roofline, "roofline_sectors": roofline_sectors,
@@ -561,24 +615,28 @@ def run_gpu(args):
 # ---------------------------------------------------------------------------
 
 def extra_layouts(torch, dev, coef_cm, pts, outs, per_case):
-    """The step's four cases in the other coefficient layouts (coset-major: the
-    paper's per-coset lookup; interleaved; bricked), each with its own
-    autotuned variant, beside the headline layout's times."""
-    from paper_2102_08518_b300.api import Volume, autotune, relayout, TUNE_CANDIDATES_SMALL
+    """The step's four cases in every coefficient layout (coset-major: the
+    paper's per-coset lookup; interleaved; bricked; four and eight shifted
+    bricked copies), each with its own autotuned variant, beside the times of
+    the layouts the step chose."""
+    from paper_2102_08518_b300.api import LAYOUT_BRICK, Volume, autotune, relayout, TUNE_CANDIDATES_SMALL
     res = {}
     try:
-        for lay in ("coset", "interleaved", "bricked"):
+        for lay in ("coset", "interleaved", "bricked", "bricked_shifted", "bricked_shifted_xyz"):
             if lay == LAYOUT:
                 continue
             c = coef_cm if lay == "coset" else relayout(coef_cm, 2, EXT, to=lay)
+            cands = TUNE_CANDIDATES_SMALL if LAYOUT_BRICK[lay] < 3 else \
+                [x for x in TUNE_CANDIDATES_SMALL if not x.get("tensor")]
             for sp, ps in CASES:
-                s = autotune(sp, "f32", EXT, c, [pts[ps]], candidates=TUNE_CANDIDATES_SMALL, tag=f"bcc_step_{ps}",
-                             layout=lay)
+                s = autotune(sp, "f32", EXT, c, [pts[ps]], candidates=cands, tag=f"bcc_step_{ps}", layout=lay)
                 v = Volume(s, EXT, c, layout=lay)
                 ms = time_ms(torch, lambda: v.eval(pts[ps], outs[ps]))
                 ent = res.setdefault(f"{sp}/{ps}", {f"{LAYOUT}_ms": per_case[f"{sp}/{ps}"]["ms"]})
                 ent[f"{lay}_ms"] = round(ms, 4)
                 ent[f"{lay}_variant"] = s.variant
+                del v
+            del c
     except Exception as ex:
         res["error"] = f"{type(ex).__name__}: {ex}"
     return res
@@ -939,7 +997,8 @@ def extra_cg(torch, dev, vols, pts, outs):
 
 
 PROFILE_CASES = ("fcc6_eval", "quintic_eval_interleaved", "quintic_eval_bricked", "quintic_eval_bricked_shifted",
-                 "quintic_eval_rays_interleaved", "linear_eval_interleaved", "linear_eval_rays_interleaved",
+                 "quintic_eval_rays_interleaved", "linear_eval_interleaved", "linear_eval_bricked_shifted",
+                 "linear_eval_rays_interleaved",
                  "quintic_adjoint_atomic", "quintic_adjoint_fixed", "quintic_hessian", "tricubic_linear_fetch",
                  "morton_sort", "morton_sort_2e24", "fcc6_eval_sorted", "fcc6_eval_staged", "tricubic_eval_coset",
                  "tricubic_eval_bricked", "tricubic_eval_bricked_shifted_xyz")

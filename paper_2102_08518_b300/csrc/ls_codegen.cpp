@@ -432,9 +432,11 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
     const bool fold = t.fold == LS_FOLD_SIGNED_PERM;
     const int a = t.scale;
     // Vector gathers: on the eight shifted copies a Cartesian stencil that is a
-    // box of even, contiguous extent per axis starts on a brick boundary in the
-    // copy chosen by the parity of its first site, so it is a box of whole
+    // box (contiguous extent per axis) starts on a brick boundary in the copy
+    // chosen by the parity of its first site, so it lies in a box of whole
     // 2 x 2 x 2 bricks, each 32 contiguous bytes: one 32-byte load per brick.
+    // An odd extent n reads (n + 1) / 2 bricks, the last one's far half unused
+    // (inside the copy: its padding of two planes per axis holds it).
     int vlo[3] = {0, 0, 0}, vn[3] = {1, 1, 1};
     bool vec = e.brick_shift && e.shift_axes == 3 && D == 3 && a == 1 && t.cosets.size() == 1 && load &&
                !declare_addr && group == 0 && e.ld == "ls_ld_f32" && !fold && !sites.empty();
@@ -444,7 +446,7 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             for (const auto &sv : sites) vals.insert(sv[i]);
             vlo[i] = *vals.begin();
             vn[i] = (int)vals.size();
-            vec = vec && vn[i] % 2 == 0 && *vals.rbegin() - vlo[i] + 1 == vn[i];
+            vec = vec && *vals.rbegin() - vlo[i] + 1 == vn[i];
         }
         vec = vec && (size_t)(vn[0] * vn[1] * vn[2]) == sites.size();
     }
@@ -495,9 +497,9 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
         o << "      const float* vb_ = (const float*)" << coef_expr << " + cbase + ((k0 + (" << vlo[0]
           << ") + sx) >> 1) * BH0 + ((k1 + (" << vlo[1] << ") + sy) >> 1) * BH1 + ((k2 + (" << vlo[2]
           << ") + sz) >> 1) * BH2;\n";
-        for (int b2 = 0; b2 < vn[2] / 2; ++b2)
-            for (int b1 = 0; b1 < vn[1] / 2; ++b1)
-                for (int b0 = 0; b0 < vn[0] / 2; ++b0) {
+        for (int b2 = 0; b2 < (vn[2] + 1) / 2; ++b2)
+            for (int b1 = 0; b1 < (vn[1] + 1) / 2; ++b1)
+                for (int b0 = 0; b0 < (vn[0] + 1) / 2; ++b0) {
                     const std::string nm = "vq" + std::to_string(b0) + std::to_string(b1) + std::to_string(b2);
                     const std::string off = std::to_string(b0) + " * BH0 + " + std::to_string(b1) + " * BH1 + " +
                                             std::to_string(b2) + " * BH2";

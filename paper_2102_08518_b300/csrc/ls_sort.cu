@@ -300,6 +300,45 @@ __global__ void morton_kernel(const float *pts, long long n, float o0, float o1,
     }
 }
 
+// dst row i = src row perm[i] (inverse: dst row perm[i] = src row i), rows of
+// W floats.  A thread moves kRows rows strided by the grid's thread count:
+// all their permutation entries, then all their rows' loads, are issued
+// before the first store, so each thread keeps kRows random row accesses in
+// flight (the permutation side is the random one).
+constexpr int kRows = 4;
+
+template <int W>
+__global__ void __launch_bounds__(256) permute_rows_kernel(const float *__restrict__ src,
+                                                           const int32_t *__restrict__ perm, long long n, int inverse,
+                                                           float *__restrict__ dst)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kRows) {
+        long long p[kRows];
+        float v[kRows][W];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const long long i = i0 + r * stride;
+            p[r] = i < n ? (long long)__ldcs(perm + i) : -1;
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const long long i = i0 + r * stride;
+            const long long s = inverse ? i : p[r];
+#pragma unroll
+            for (int c = 0; c < W; ++c) v[r][c] = p[r] >= 0 ? src[s * W + c] : 0.0f;
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            if (p[r] < 0) continue;
+            const long long i = i0 + r * stride;
+            const long long d = inverse ? p[r] : i;
+#pragma unroll
+            for (int c = 0; c < W; ++c) dst[d * W + c] = v[r][c];
+        }
+    }
+}
+
 __global__ void permute_kernel(const float *src, const int32_t *perm, long long n, int width, int inverse, float *dst)
 {
     const long long total = n * width;
@@ -465,6 +504,18 @@ cudaError_t permute_rows(const float *src, const int32_t *perm, long long n, int
                          cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
+    if (width >= 1 && width <= 4) {
+        // one thread per kRows rows, 148 x 8 resident blocks of 256 at most
+        long long blocks = (n + 256LL * kRows - 1) / (256LL * kRows);
+        if (blocks > 148 * 8) blocks = 148 * 8;
+        switch (width) {
+        case 1: permute_rows_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(src, perm, n, inverse, dst); break;
+        case 2: permute_rows_kernel<2><<<(unsigned)blocks, 256, 0, st>>>(src, perm, n, inverse, dst); break;
+        case 3: permute_rows_kernel<3><<<(unsigned)blocks, 256, 0, st>>>(src, perm, n, inverse, dst); break;
+        default: permute_rows_kernel<4><<<(unsigned)blocks, 256, 0, st>>>(src, perm, n, inverse, dst); break;
+        }
+        return cudaGetLastError();
+    }
     long long blocks = (n * width + 255) / 256;
     if (blocks > 148 * 32) blocks = 148 * 32;
     permute_kernel<<<(unsigned)blocks, 256, 0, st>>>(src, perm, n, width, inverse, dst);

@@ -40,11 +40,16 @@ def test_morton_sort_bit_exact(n):
     assert np.array_equal(keys.cpu().numpy().astype(np.int64) & 0xFFFFFFFF, want_keys[want_perm])
 
 
-def test_permute_rows_roundtrip():
+@pytest.mark.parametrize("n,width", [(5001, 3), (1, 3), (777, 1), (3000, 2), (4099, 4), (513, 5),
+                                     ((1 << 21) + 7, 3)])
+def test_permute_rows_roundtrip(n, width):
+    """Rows of 1-4 floats (the batched-rows kernels: several rows per thread,
+    strided by the grid; n spanning several strides and a ragged end) and a
+    wider row (the per-element kernel), forward and inverse."""
     from paper_2102_08518_b300.api import permute_rows
-    rng = np.random.default_rng(5)
-    x = torch.from_numpy(rng.normal(size=(5001, 3)).astype(np.float32)).cuda()
-    perm = torch.from_numpy(rng.permutation(5001).astype(np.int32)).cuda()
+    rng = np.random.default_rng(5 + n + width)
+    x = torch.from_numpy(rng.normal(size=(n, width)).astype(np.float32)).cuda()
+    perm = torch.from_numpy(rng.permutation(n).astype(np.int32)).cuda()
     y = permute_rows(x, perm)
     assert torch.equal(y, x[perm.long()])
     z = permute_rows(y, perm, inverse=True)
