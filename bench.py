@@ -932,7 +932,7 @@ def extra_paper_orders(torch, dev, vols, pts, outs):
             res[name][f"{lay}_roofline_frac"] = frac(msb)
             del cb, vb
         best = max(v for k, v in res[name].items() if k == "gpoints_s" or
-                   (k.endswith("_gpoints_s") and k.startswith("bricked")))
+                   (k.endswith("_gpoints_s") and k.startswith(("bricked", "branchy"))))
         res[name]["best_layout_gpoints_s"] = best
         del c, c0, cp, p, vol
     res["order2_bcc_linear_vs_trilinear"] = round(res["bcc_linear"]["gpoints_s"] / res["trilinear"]["gpoints_s"], 3)
