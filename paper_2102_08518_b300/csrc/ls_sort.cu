@@ -301,10 +301,11 @@ __global__ void morton_kernel(const float *pts, long long n, float o0, float o1,
 }
 
 // dst row i = src row perm[i] (inverse: dst row perm[i] = src row i), rows of
-// W floats.  A thread moves kRows rows strided by the grid's thread count:
-// all their permutation entries, then all their rows' loads, are issued
-// before the first store, so each thread keeps kRows random row accesses in
-// flight (the permutation side is the random one).
+// W floats.  Consecutive lanes take consecutive elements (a row's W elements
+// on neighbouring lanes, so one request serves the row's sector), and a
+// thread moves kRows elements strided by the grid's thread count: all their
+// permutation entries, then all their loads, are issued before the first
+// store, so each thread keeps kRows random accesses in flight.
 constexpr int kRows = 4;
 
 template <int W>
@@ -312,29 +313,31 @@ __global__ void __launch_bounds__(256) permute_rows_kernel(const float *__restri
                                                            const int32_t *__restrict__ perm, long long n, int inverse,
                                                            float *__restrict__ dst)
 {
+    const long long total = n * W;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += stride * kRows) {
-        long long p[kRows];
-        float v[kRows][W];
+    for (long long e0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; e0 < total; e0 += stride * kRows) {
+        long long p[kRows], row[kRows];
+        int col[kRows];
+        float v[kRows];
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
-            const long long i = i0 + r * stride;
-            p[r] = i < n ? (long long)__ldcs(perm + i) : -1;
+            const long long e = e0 + r * stride;
+            row[r] = e / W;                  // W is a constant: a multiply and a shift
+            col[r] = (int)(e - row[r] * W);
+            const bool ok = e < total;
+            const long long pr = (long long)__ldg(perm + (ok ? row[r] : 0));
+            p[r] = ok ? pr : -1;
         }
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
-            const long long i = i0 + r * stride;
-            const long long s = inverse ? i : p[r];
-#pragma unroll
-            for (int c = 0; c < W; ++c) v[r][c] = p[r] >= 0 ? src[s * W + c] : 0.0f;
+            const long long s = inverse ? row[r] : p[r];
+            v[r] = p[r] >= 0 ? src[s * W + col[r]] : 0.0f;
         }
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
             if (p[r] < 0) continue;
-            const long long i = i0 + r * stride;
-            const long long d = inverse ? p[r] : i;
-#pragma unroll
-            for (int c = 0; c < W; ++c) dst[d * W + c] = v[r][c];
+            const long long d = inverse ? p[r] : row[r];
+            dst[d * W + col[r]] = v[r];
         }
     }
 }
@@ -505,8 +508,8 @@ cudaError_t permute_rows(const float *src, const int32_t *perm, long long n, int
 {
     if (n <= 0) return cudaSuccess;
     if (width >= 1 && width <= 4) {
-        // one thread per kRows rows, 148 x 8 resident blocks of 256 at most
-        long long blocks = (n + 256LL * kRows - 1) / (256LL * kRows);
+        // kRows elements per thread, 148 x 8 resident blocks of 256 at most
+        long long blocks = (n * width + 256LL * kRows - 1) / (256LL * kRows);
         if (blocks > 148 * 8) blocks = 148 * 8;
         switch (width) {
         case 1: permute_rows_kernel<1><<<(unsigned)blocks, 256, 0, st>>>(src, perm, n, inverse, dst); break;
