@@ -141,7 +141,7 @@ class ClockSampler:
 # points per case of one oracle sample: about 10 s of host work on 16 cores
 ORACLE_SAMPLE = {"bcc_linear": 1 << 15, "bcc_quintic": 1 << 13}
 # one step of the reference arm: a smaller sample (a fresh one each step), so
-# that the driver's --steps K --warmup W run ends within a few minutes
+# that a --steps K --warmup W run ends within a few minutes
 REFERENCE_SAMPLE = {"bcc_linear": 1 << 14, "bcc_quintic": 1 << 11}
 
 
