@@ -614,6 +614,11 @@ def run_gpu(args):
 # extras: the other configurations
 # ---------------------------------------------------------------------------
 
+# the eight-copy layout in the layout comparison: a few block sizes (on the
+# four copies the full candidate list chose block 384-512)
+XYZ_CANDIDATES = (dict(block=384), dict(block=512), dict(block=512, prefetch=1))
+
+
 def extra_layouts(torch, dev, coef_cm, pts, outs, per_case):
     """The step's four cases in every coefficient layout (coset-major: the
     paper's per-coset lookup; interleaved; bricked; four and eight shifted
@@ -626,8 +631,7 @@ def extra_layouts(torch, dev, coef_cm, pts, outs, per_case):
             if lay == LAYOUT:
                 continue
             c = coef_cm if lay == "coset" else relayout(coef_cm, 2, EXT, to=lay)
-            cands = TUNE_CANDIDATES_SMALL if LAYOUT_BRICK[lay] < 3 else \
-                [x for x in TUNE_CANDIDATES_SMALL if not x.get("tensor")]
+            cands = TUNE_CANDIDATES_SMALL if LAYOUT_BRICK[lay] < 3 else XYZ_CANDIDATES
             for sp, ps in CASES:
                 s = autotune(sp, "f32", EXT, c, [pts[ps]], candidates=cands, tag=f"bcc_step_{ps}", layout=lay)
                 v = Volume(s, EXT, c, layout=lay)

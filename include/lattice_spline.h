@@ -292,6 +292,13 @@ ls_status ls_spline_precompile(const ls_spline_desc *desc, ls_dtype coef_dtype,
                                const ls_variant *variant);
 /* Generated source (NUL-terminated, owned by the spline) for inspection/tests. */
 const char *ls_spline_source(ls_spline s);
+/* The CUDA C++ source the generator emits for (desc, coef_dtype, variant),
+ * without compiling it (host only, no device).  Copies at most cap bytes,
+ * NUL-terminated, into buf (buf may be NULL with cap 0) and sets *len to the
+ * source's length without the NUL, so a caller can size buf with a first call.
+ * Errors: INVALID_ARG (len NULL) / BAD_TABLE / UNSUPPORTED. */
+ls_status ls_spline_generate_source(const ls_spline_desc *desc, ls_dtype coef_dtype,
+                                    const ls_variant *variant, char *buf, size_t cap, size_t *len);
 /* LS_ERR_TIMEOUT if a bounded wait inside an evaluation kernel of this spline gave
  * up since the last call (the affected outputs are then incomplete), else LS_OK;
  * synchronises the stream and clears the word.  Only the warp-specialized value

@@ -79,6 +79,8 @@ SIGNATURES = {
     "ls_spline_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "ls_spline_precompile": (ctypes.c_int, [ctypes.POINTER(SplineDescC), ctypes.c_int, ctypes.POINTER(VariantC)]),
     "ls_spline_source": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "ls_spline_generate_source": (ctypes.c_int, [ctypes.POINTER(SplineDescC), ctypes.c_int, ctypes.POINTER(VariantC),
+                                                 ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "ls_spline_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "ls_spline_info": (ctypes.c_int, [ctypes.c_void_p, c_i32p, c_i32p, c_i32p, c_i32p]),
     "ls_volume_create": (ctypes.c_int, [ctypes.c_void_p, c_i64p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),

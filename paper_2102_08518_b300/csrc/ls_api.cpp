@@ -386,6 +386,26 @@ ls_status ls_spline_precompile(const ls_spline_desc *desc, ls_dtype dt, const ls
     return LS_OK;
 }
 
+ls_status ls_spline_generate_source(const ls_spline_desc *desc, ls_dtype dt, const ls_variant *variant, char *buf,
+                                    size_t cap, size_t *len)
+{
+    if (!len) return ls_fail(LS_ERR_INVALID_ARG, "len is NULL");
+    ls::Table t;
+    ls_status st = copy_desc(desc, t);
+    if (st != LS_OK) return st;
+    if (dt != LS_F32 && dt != LS_BF16 && dt != LS_F16) return ls_fail(LS_ERR_UNSUPPORTED, "coef dtype");
+    ls_variant var = default_variant(variant);
+    if (var.tensor && t.sep.empty()) var.block = 128 * ls::tensor_slots(t, var, dt);
+    const ls::Generated g = ls::generate(t, dt, var);
+    *len = g.source.size();
+    if (buf && cap > 0) {
+        const size_t m = g.source.size() < cap - 1 ? g.source.size() : cap - 1;
+        std::memcpy(buf, g.source.data(), m);
+        buf[m] = '\0';
+    }
+    return LS_OK;
+}
+
 ls_status ls_spline_create(const ls_spline_desc *desc, ls_dtype dt, const ls_variant *variant, ls_spline *out)
 {
     if (!out) return ls_fail(LS_ERR_INVALID_ARG, "out is NULL");

@@ -124,7 +124,11 @@ ls_status get_cubin(const std::string &source, const std::string &tag, std::vect
     if (st != LS_OK) return st;
     mkdir(dir.c_str(), 0755);
     write_file_atomic(path, cubin);
-    write_file_atomic(dir + "/" + tag + "_" + hex + ".cu", std::vector<char>(source.begin(), source.end()));
+    // the source beside its binary only on request (LS_KEEP_KERNEL_SOURCE=1):
+    // ls_spline_source / ls_spline_generate_source give it without the file
+    const char *keep = std::getenv("LS_KEEP_KERNEL_SOURCE");
+    if (keep && keep[0] == '1')
+        write_file_atomic(dir + "/" + tag + "_" + hex + ".cu", std::vector<char>(source.begin(), source.end()));
     return LS_OK;
 }
 

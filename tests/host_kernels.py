@@ -12,7 +12,6 @@ tests still check the compiled kernels themselves.  Not part of the product.
 import ctypes
 import hashlib
 import os
-import re
 import subprocess
 import tempfile
 
@@ -21,7 +20,6 @@ import numpy as np
 from paper_2102_08518_b300 import _abi, api
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-CACHE = os.path.join(ROOT, "paper_2102_08518_b300", "kcache")
 BUILD = os.path.join(tempfile.gettempdir(), "ls_host_kernels")
 
 SHIM = r"""
@@ -49,16 +47,21 @@ static inline unsigned short ls_ldk_u16(const unsigned short* p) { return *p; }
 
 
 def generated_source(name: str, dtype: str = "f32", expansion: str = "sparse", **var) -> str:
-    """Source of the kernels of spline `name` with variant `var`, generated
-    and compiled into the kernel cache by ls_spline_precompile (no device)."""
+    """Source of the kernels of spline `name` with variant `var`, as the
+    generator emits it (ls_spline_generate_source: host only, no device)."""
     kn = api.kernel_name(name, dtype, expansion=expansion, **var)
     h = _abi.DescHolder(api.table(name), kn, expansion)
-    rc = _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), api.DTYPES[dtype], ctypes.byref(_abi.variant(**var)))
-    assert rc == 0, _abi.lib().ls_last_error()
-    files = sorted((f for f in os.listdir(CACHE) if re.fullmatch(f"ls_{kn}_{dtype}_[0-9a-f]+\\.cu", f)),
-                   key=lambda f: os.path.getmtime(os.path.join(CACHE, f)))
-    with open(os.path.join(CACHE, files[-1])) as f:
-        return f.read()
+    L = _abi.lib()
+    vr = _abi.variant(**var)
+    n = ctypes.c_size_t(0)
+    rc = L.ls_spline_generate_source(ctypes.byref(h.desc), api.DTYPES[dtype], ctypes.byref(vr), None, 0,
+                                     ctypes.byref(n))
+    assert rc == 0, L.ls_last_error()
+    buf = ctypes.create_string_buffer(n.value + 1)
+    rc = L.ls_spline_generate_source(ctypes.byref(h.desc), api.DTYPES[dtype], ctypes.byref(vr), buf, n.value + 1,
+                                     ctypes.byref(n))
+    assert rc == 0, L.ls_last_error()
+    return buf.value.decode()
 
 
 def _function(src: str, fname: str) -> str:
