@@ -594,7 +594,8 @@ def run_gpu(args):
         extras = {}
         extras["layouts"] = extra_layouts(torch, dev, coef_cm, pts, outs, per_case)
         for name, fn in (("tricubic_64", extra_tricubic_64), ("fwd_bwd", extra_fwd_bwd), ("fcc_sorted", extra_fcc),
-                         ("batched", extra_batched), ("cg", extra_cg), ("paper_orders", extra_paper_orders)):
+                         ("batched", extra_batched), ("cg", extra_cg), ("paper_orders", extra_paper_orders),
+                         ("param_sweep", extra_param_sweep)):
             try:
                 extras[name] = fn(torch, dev, vols, pts, outs)
             except Exception as ex:       # an extra must not lose the headline line
@@ -951,6 +952,48 @@ def extra_paper_orders(torch, dev, vols, pts, outs):
                       ("voronoi2_bcc", "trilinear", "order2"), ("voronoi2_fcc", "trilinear", "order2")):
         res[f"{tag}_{a}_vs_{b}_best_layouts"] = round(res[a]["best_layout_gpoints_s"] /
                                                       res[b]["best_layout_gpoints_s"], 3)
+    return res
+
+
+# the paper's parameter study (Sec. 4.4, Sec. 5; Algorithm 2's group size m
+# and pipeline depth d, branchy vs predicated selection): the variants timed
+SWEEP_SPLINES = ("tricubic", "bcc_quintic", "fcc6", "voronoi2_bcc")
+SWEEP_VARIANTS = (dict(), dict(group=16, depth=1), dict(group=8, depth=2), dict(group=8, depth=3),
+                  dict(group=4, depth=4))
+
+
+def extra_param_sweep(torch, dev, vols, pts, outs):
+    """Gpoints/s of the paper's parameter study on B300: for the order-4 pair
+    (tricubic, BCC quintic), the K = 2 FCC spline and the K = 5 Voronoi BCC
+    spline on the paper's equal-memory grids (2^24 uniform points, FP32,
+    interleaved cosets, block 256), the kernel with unlimited gathers in
+    flight against groups of m gathers that wait for the group d before them,
+    each predicated and (K > 1) branchy."""
+    from paper_2102_08518_b300.api import Spline, Volume, relayout, table
+    grids = {"tricubic": ("cc", (128,) * 3), "bcc_quintic": ("bcc", (101,) * 3), "fcc6": ("fcc", (81,) * 3),
+             "voronoi2_bcc": ("bcc", (101,) * 3)}
+    n = 1 << 24
+    res = {"workload": "2^24 uniform points per spline; CC 128^3, BCC 2x101^3, FCC 4x81^3 coefficients U[-1,1]; "
+                       "interleaved cosets, block 256; m = gathers per group, d = groups in flight (0: unlimited)"}
+    out = torch.empty(n, device=dev)
+    for name in SWEEP_SPLINES:
+        lat, ext = grids[name]
+        ncos = len(workloads.LATTICES[lat][2])
+        c = relayout(workloads.coef_uniform_torch(lat, ext, seed=1), ncos, ext, to="interleaved")
+        lo, hi = workloads.inner_box(name, ext)
+        p = workloads.points_uniform_torch(n, lo, hi, seed=2)
+        rows = []
+        for br in ((0, 1) if len(table(name).regions) > 1 else (0,)):
+            for var in SWEEP_VARIANTS:
+                if br and var:
+                    continue            # branchy: unlimited gathers only
+                vol = Volume(Spline(name, "f32", branchy=br, **var), ext, c, layout="interleaved")
+                ms = time_ms(torch, lambda: vol.eval(p, out))
+                rows.append({"m": var.get("group", 0), "d": var.get("depth", 0), "branchy": br,
+                             "gpoints_s": round(n / ms / 1e6, 3)})
+                del vol
+        res[name] = rows
+        del c, p
     return res
 
 

@@ -524,6 +524,8 @@ TUNE_CANDIDATES_SMALL = tuple([dict(block=256, blocks_per_sm=b, expansion=x) for
                               [dict(block=b, prefetch=1) for b in (256, 384, 512)] +
                               [dict(block=256, blocks_per_sm=2, prefetch=1)] +
                               [dict(block=b) for b in (640, 672)] +
+                              [dict(block=b, group=16, depth=1) for b in (256, 384, 512)] +
+                              [dict(block=512, group=8, depth=2), dict(block=512, group=4, depth=4)] +
                               [dict(block=b, l2_keep=1) for b in (384, 512, 672)] +
                               [dict(tensor=1, expansion=x) for x in ("sparse", "centroid")] +
                               [dict(tensor=1, tensor_kind=1, expansion=x) for x in ("sparse", "centroid")] +

@@ -90,6 +90,15 @@ def test_voronoi_branchy_and_predicated(name, var):
     _check(name, var)
 
 
+@pytest.mark.parametrize("var", [dict(group=16, depth=1), dict(group=8, depth=2), dict(group=8, depth=3),
+                                 dict(group=4, depth=4)], ids=str)
+@pytest.mark.parametrize("name", ["tricubic", "voronoi2_bcc"])
+def test_parameter_sweep_variants(name, var):
+    """The gather group size m and depth d of the benchmark's parameter sweep
+    on the tensor-product spline and on the five-region Voronoi spline."""
+    _check(name, var)
+
+
 @pytest.mark.parametrize("name", ["bcc_quintic", "fcc6", "tricubic", "bcc_linear"])
 def test_plain_transform(name):
     """The coefficient transform as direct sums over the sites (the factored
