@@ -12,6 +12,8 @@ from paper_2102_08518_b300.api import table
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
+from tests.host_kernels import generated_source
+
 
 def _declared_functions():
     names = set()
@@ -132,11 +134,7 @@ def test_variant_fields_reach_the_generated_code():
         h = _abi.DescHolder(table("bcc_quintic"), api.kernel_name("bcc_quintic", "f32", **var))
         assert _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), _abi.LS_F32,
                                                ctypes.byref(_abi.variant(**var))) == 0
-        cache = os.path.join(ROOT, "paper_2102_08518_b300", "kcache")
-        name = api.kernel_name("bcc_quintic", "f32", **var)
-        files = sorted((f for f in os.listdir(cache) if re.fullmatch(f"ls_{name}_f32_[0-9a-f]+\\.cu", f)),
-                       key=lambda f: os.path.getmtime(os.path.join(cache, f)))
-        srcs[tag] = open(os.path.join(cache, files[-1])).read()
+        srcs[tag] = generated_source("bcc_quintic", **var)
     assert "BB0" in srcs["brick"] and "BB0" not in srcs["plain"]
     assert "P_c0" in srcs["pipe"] and "mbarrier.try_wait" in srcs["ws"]
     assert "cp.async.bulk.tensor.3d" in srcs["stage"] and "cp.async.bulk.tensor" not in srcs["plain"]
@@ -197,10 +195,7 @@ def test_tensor_variant_source():
     name = api.kernel_name("bcc_quintic", "f32", **var)
     h = _abi.DescHolder(table("bcc_quintic"), name)
     assert _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), _abi.LS_F32, ctypes.byref(_abi.variant(**var))) == 0
-    cache = os.path.join(ROOT, "paper_2102_08518_b300", "kcache")
-    files = sorted((f for f in os.listdir(cache) if re.fullmatch(f"ls_{name}_f32_[0-9a-f]+\\.cu", f)),
-                   key=lambda f: os.path.getmtime(os.path.join(cache, f)))
-    src = open(os.path.join(cache, files[-1])).read()
+    src = generated_source("bcc_quintic", **var)
     kern = src[src.index("ls_eval__"):]
     assert "tcgen05.mma.cta_group::1.kind::tf32" in kern and "tcgen05.alloc" in kern and "tcgen05.dealloc" in kern
     # the value and the value + gradient kernels: 3 products x K = 32 in steps of 8 each
@@ -222,10 +217,7 @@ def _tensor_source(name, **var):
     kn = api.kernel_name(name, "f32", **var)
     h = _abi.DescHolder(table(name), kn)
     assert _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), _abi.LS_F32, ctypes.byref(_abi.variant(**var))) == 0
-    cache = os.path.join(ROOT, "paper_2102_08518_b300", "kcache")
-    files = sorted((f for f in os.listdir(cache) if re.fullmatch(f"ls_{kn}_f32_[0-9a-f]+\\.cu", f)),
-                   key=lambda f: os.path.getmtime(os.path.join(cache, f)))
-    return open(os.path.join(cache, files[-1])).read()
+    return generated_source(name, **var)
 
 
 def _table_entries(src):
@@ -298,3 +290,26 @@ def test_tensor_kernel_readback_and_union_zeroing_in_source():
         f = _tensor_source("fcc6", **kw)
         kf = eval_kernel(f, api.kernel_name("fcc6", "f32", **kw))
         assert len(re.findall(r"if \(tpsi != \d\) tc\d+ = 0\.0f;", kf)) > 0
+
+
+def test_generate_source_sizes_and_truncates():
+    """ls_spline_generate_source: a NULL buffer reports the length; a short
+    buffer gets a NUL-terminated prefix; NULL len is rejected; the text is
+    the same on every call and names the variant's kernels."""
+    from paper_2102_08518_b300 import api
+    L = _abi.lib()
+    kn = api.kernel_name("bcc_linear", "f32", block=512)
+    h = _abi.DescHolder(table("bcc_linear"), kn)
+    var = _abi.variant(block=512)
+    n = ctypes.c_size_t(0)
+    assert L.ls_spline_generate_source(ctypes.byref(h.desc), _abi.LS_F32, ctypes.byref(var), None, 0,
+                                       ctypes.byref(n)) == 0
+    assert n.value > 1000
+    full = generated_source("bcc_linear", block=512)
+    assert len(full) == n.value and f"ls_eval__{kn}(" in full
+    buf = ctypes.create_string_buffer(17)
+    m = ctypes.c_size_t(0)
+    assert L.ls_spline_generate_source(ctypes.byref(h.desc), _abi.LS_F32, ctypes.byref(var), buf, 17,
+                                       ctypes.byref(m)) == 0
+    assert m.value == n.value and buf.value.decode() == full[:16]
+    assert L.ls_spline_generate_source(ctypes.byref(h.desc), _abi.LS_F32, ctypes.byref(var), None, 0, None) != 0

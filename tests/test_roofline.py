@@ -12,6 +12,8 @@ import workloads
 from paper_2102_08518_b300.api import table
 from paper_2102_08518_b300.roofline import distinct_sectors_per_point, stencil_indices
 
+from tests.host_kernels import generated_source
+
 
 def _maps(C, ext):
     """Element index of every coset-major element in the interleaved and bricked layouts."""
@@ -73,10 +75,7 @@ def test_tensor_shape_matches_the_generated_kernel():
         h = _abi.DescHolder(api.table(name), kn)
         assert _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), _abi.LS_F32,
                                                ctypes.byref(_abi.variant(tensor=1))) == 0
-        cache = os.path.join(root, "paper_2102_08518_b300", "kcache")
-        files = sorted((f for f in os.listdir(cache) if re.fullmatch(f"ls_{kn}_f32_[0-9a-f]+\\.cu", f)),
-                       key=lambda f: os.path.getmtime(os.path.join(cache, f)))
-        src = open(os.path.join(cache, files[-1])).read()
+        src = generated_source(name, tensor=1)
         m = re.search(r"float ls_sB\[(\d+)\]", src)
         assert int(m.group(1)) == 2 * N * K, name
         assert K % 8 == 0 and N % 16 == 0 and nnz <= K * N
@@ -96,10 +95,7 @@ def test_tensor_shape_of_the_fp16_form():
         h = _abi.DescHolder(api.table(name), kn)
         assert _abi.lib().ls_spline_precompile(ctypes.byref(h.desc), _abi.LS_F32,
                                                ctypes.byref(_abi.variant(tensor=1, tensor_kind=1))) == 0
-        cache = os.path.join(root, "paper_2102_08518_b300", "kcache")
-        files = sorted((f for f in os.listdir(cache) if re.fullmatch(f"ls_{kn}_f32_[0-9a-f]+\\.cu", f)),
-                       key=lambda f: os.path.getmtime(os.path.join(cache, f)))
-        src = open(os.path.join(cache, files[-1])).read()
+        src = generated_source(name, tensor=1, tensor_kind=1)
         m = re.search(r"unsigned short ls_tcB_\w+\[(\d+)\]", src)
         assert int(m.group(1)) == 2 * N * K and K % 16 == 0, name
 
