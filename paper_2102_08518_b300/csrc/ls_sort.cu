@@ -144,12 +144,26 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint32_t *keys,
     int32_t *sval = (int32_t *)(skey + kTile);     // [kTile]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
+    int whole = 0;
     for (int q = 0; q < kPer; ++q) {
         const int b = threadIdx.x * kPer + q;
         run[b] = offs[(size_t)b * nblk + blockIdx.x];
+        // the digit's count over all blocks (offsets are digit-major)
+        const uint32_t end = b + 1 < kBins ? offs[(size_t)(b + 1) * nblk] : (uint32_t)n;
+        whole |= (long long)(end - offs[(size_t)b * nblk]) == n;
     }
     const long long c0 = (long long)blockIdx.x * chunk;
     const long long c1 = (c0 + chunk < n) ? c0 + chunk : n;
+    // every key has the same digit in this pass (keys narrower than the sort's
+    // bits, e.g. Morton keys of a 256-cell box have a zero top digit): the
+    // stable order is the input order, so the chunk is copied through
+    if (__syncthreads_or(whole)) {
+        for (long long i = c0 + threadIdx.x; i < c1; i += kThreads) {
+            keys_out[i] = __ldg(keys + i);
+            vals_out[i] = __ldg(vals + i);
+        }
+        return;
+    }
     uint32_t nkey[kItems];
     int32_t nval[kItems];
     {

@@ -26,11 +26,16 @@ def _expected_morton(pts, origin, cell):
     return keys
 
 
-@pytest.mark.parametrize("n", [1, 1000, 4096 * 3 + 17, 200003])
-def test_morton_sort_bit_exact(n):
+@pytest.mark.parametrize("n,hi", [(1, 300.0), (1000, 300.0), (4096 * 3 + 17, 300.0), (200003, 300.0),
+                                  (200003, 2500.0), (70001, 7.0), (50000, 1.0)])
+def test_morton_sort_bit_exact(n, hi):
+    """Keys of 30 bits (box 2500 / cell 2: cells clamped at 1023), 24 bits
+    (the top digit constant), 6 bits (three constant digits) and one key for
+    every point (points in [0, 1) with cell 2: every pass keeps the input
+    order)."""
     from paper_2102_08518_b300.api import morton_sort
     rng = np.random.default_rng(n)
-    pts = rng.uniform(-5, 300, (n, 3)).astype(np.float32)
+    pts = rng.uniform(-5 if hi > 2 else 0, hi, (n, 3)).astype(np.float32)
     pts[: n // 3] = np.round(pts[: n // 3])        # many equal keys: stability matters
     perm, keys = morton_sort(torch.from_numpy(pts).cuda(), origin=(0.0, 0.0, 0.0), cell=2.0, want_keys=True)
     torch.cuda.synchronize()
