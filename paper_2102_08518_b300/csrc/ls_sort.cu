@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(1024) scan_down(const uint32_t *in, long long 
 // running offset of that digit: consecutive threads write consecutive
 // addresses.
 template <int RB>
-__global__ void __launch_bounds__(kThreads) scatter_kernel(const uint32_t *keys, const int32_t *vals, long long n,
+__global__ void __launch_bounds__(kThreads, 2) scatter_kernel(const uint32_t *keys, const int32_t *vals, long long n,
                                                             int shift, long long chunk, const uint32_t *offs,
                                                             int nblk, uint32_t *keys_out, int32_t *vals_out)
 {
@@ -158,7 +158,37 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint32_t *keys,
     // bits, e.g. Morton keys of a 256-cell box have a zero top digit): the
     // stable order is the input order, so the chunk is copied through
     if (__syncthreads_or(whole)) {
-        for (long long i = c0 + threadIdx.x; i < c1; i += kThreads) {
+        // 16-byte copies, four in flight per thread, when all four arrays
+        // allow them at this chunk; scalar copies for the rest
+        long long done = c0;
+        const uintptr_t al = (uintptr_t)(keys + c0) | (uintptr_t)(vals + c0) | (uintptr_t)(keys_out + c0) |
+                             (uintptr_t)(vals_out + c0);
+        if ((al & 15) == 0) {
+            const long long nv = (c1 - c0) >> 2;
+            const uint4 *ks = (const uint4 *)(keys + c0), *vs = (const uint4 *)(vals + c0);
+            uint4 *kd = (uint4 *)(keys_out + c0), *vd = (uint4 *)(vals_out + c0);
+            for (long long v = threadIdx.x; v < nv; v += 4LL * kThreads) {
+                uint4 a[4], b[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const long long w = v + (long long)u * kThreads;
+                    if (w < nv) {
+                        a[u] = __ldg(ks + w);
+                        b[u] = __ldg(vs + w);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const long long w = v + (long long)u * kThreads;
+                    if (w < nv) {
+                        kd[w] = a[u];
+                        vd[w] = b[u];
+                    }
+                }
+            }
+            done = c0 + (nv << 2);
+        }
+        for (long long i = done + threadIdx.x; i < c1; i += kThreads) {
             keys_out[i] = __ldg(keys + i);
             vals_out[i] = __ldg(vals + i);
         }
