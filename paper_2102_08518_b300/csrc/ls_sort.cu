@@ -42,7 +42,31 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const uint32_t *keys, lo
     __syncthreads();
     const long long c0 = (long long)blockIdx.x * chunk;
     const long long c1 = (c0 + chunk < n) ? c0 + chunk : n;
-    for (long long i = c0 + threadIdx.x; i < c1; i += kThreads) atomicAdd(&h[(__ldg(keys + i) >> shift) & (kBins - 1)], 1u);
+    long long done = c0;
+    if (((uintptr_t)(keys + c0) & 15) == 0) {
+        // 16-byte loads, four in flight per thread
+        const long long nv = (c1 - c0) >> 2;
+        const uint4 *k4 = (const uint4 *)(keys + c0);
+        for (long long v = threadIdx.x; v < nv; v += 4LL * kThreads) {
+            uint4 q[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long w = v + (long long)u * kThreads;
+                q[u] = w < nv ? __ldg(k4 + w) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (v + (long long)u * kThreads >= nv) continue;
+                atomicAdd(&h[(q[u].x >> shift) & (kBins - 1)], 1u);
+                atomicAdd(&h[(q[u].y >> shift) & (kBins - 1)], 1u);
+                atomicAdd(&h[(q[u].z >> shift) & (kBins - 1)], 1u);
+                atomicAdd(&h[(q[u].w >> shift) & (kBins - 1)], 1u);
+            }
+        }
+        done = c0 + (nv << 2);
+    }
+    for (long long i = done + threadIdx.x; i < c1; i += kThreads)
+        atomicAdd(&h[(__ldg(keys + i) >> shift) & (kBins - 1)], 1u);
     __syncthreads();
     for (int b = threadIdx.x; b < kBins; b += kThreads) hist[(size_t)b * nblk + blockIdx.x] = h[b];
 }
