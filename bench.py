@@ -830,6 +830,25 @@ def extra_batched(torch, dev, vols, pts, outs):
                 "bound_rounded": 2e-6, "bound_fp32": (2.0 ** -8 if dt == "bf16" else 2.0 ** -11) + 2e-6,
                 "sample": f"{golden['sample_per_volume']} seeded points per volume (tests/golden)"}
             del splan
+        # the same volumes in 2x2x2 bricks and as four shifted bricked copies
+        # (every extent of the recipe is even)
+        for lay, brick in (("bricked", 1), ("bricked_shifted", 2)):
+            cb = [relayout(c, len(workloads.LATTICES[workloads.SPLINE_LATTICE[it.spline]][2]), e, to=lay,
+                           src=l) for it, e, c, l in zip(recipe, exts, cd, lays)]
+            spb = {n: Spline(n, dt, brick=brick) for n in sp32}
+            vb = [Volume(spb[it.spline], e, c, layout=lay) for it, e, c in zip(recipe, exts, cb)]
+            bplan = Plan(vb, ptsl, outl, tile=0)
+            bplan.launch()
+            torch.cuda.synchronize()
+            bgraph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(bgraph):
+                bplan.launch(stream=torch.cuda.current_stream())
+            tb = time_ms(torch, bgraph.replay, reps=5)
+            bplan.status()
+            errb = max(float((o - r).abs().max()) for o, r in zip(outl, ref) if o.numel())
+            res[dt][f"{lay}_graph_gpoints_s"] = round(total / tb / 1e6, 3)
+            res[dt][f"{lay}_max_abs_err_vs_f32_storage"] = round(errb, 7)
+            del bplan, bgraph, vb, cb
         del plan, vd, cd
     return res
 

@@ -15,8 +15,8 @@ ORACLE_SPEC = {"tricubic": ospecs.tricubic, "bcc_linear": ospecs.bcc_linear,
 TORCH = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
 
 
-def _batch(n_vol, seed, dtypes=("f32", "bf16", "f16")):
-    from paper_2102_08518_b300.api import Spline, Volume
+def _batch(n_vol, seed, dtypes=("f32", "bf16", "f16"), layout="coset"):
+    from paper_2102_08518_b300.api import LAYOUT_BRICK, Spline, Volume, relayout
     recipe = workloads.batch_recipe(n_vol, seed=seed, edges=(8, 12, 16, 24), log2_lo=4, log2_hi=13)
     rng = np.random.default_rng(seed)
     splines, vols, pts, outs, coefs, exts = {}, [], [], [], [], []
@@ -24,13 +24,14 @@ def _batch(n_vol, seed, dtypes=("f32", "bf16", "f16")):
         dt = dtypes[k % len(dtypes)]
         lat = workloads.SPLINE_LATTICE[it.spline]
         if (it.spline, dt) not in splines:
-            splines[(it.spline, dt)] = Spline(it.spline, dt)
+            splines[(it.spline, dt)] = Spline(it.spline, dt, brick=LAYOUT_BRICK[layout])
         c = workloads.coef_uniform(lat, it.ext, seed=it.seed)
         lo, hi = workloads.bounding_box(lat, it.ext)
         n = it.n_points if k != 3 else 0                       # one empty volume
         p = workloads.points_uniform(n, lo - 1.0, hi + 1.0, seed=it.seed + 1)
         ct = torch.from_numpy(c).to("cuda", TORCH[dt]).contiguous()
-        vols.append(Volume(splines[(it.spline, dt)], it.ext, ct))
+        cl = ct if layout == "coset" else relayout(ct, len(workloads.LATTICES[lat][2]), it.ext, to=layout)
+        vols.append(Volume(splines[(it.spline, dt)], it.ext, cl, layout=layout))
         pts.append(torch.from_numpy(p).cuda())
         outs.append(torch.full((n,), float("nan"), device="cuda"))
         coefs.append(ct.float().cpu().numpy())
@@ -38,10 +39,14 @@ def _batch(n_vol, seed, dtypes=("f32", "bf16", "f16")):
     return recipe, splines, vols, pts, outs, coefs, exts
 
 
-@pytest.mark.parametrize("tile", [0, 100, 4096])
-def test_plan_matches_per_volume_kernels_and_oracle(tile):
+@pytest.mark.parametrize("tile,layout", [(0, "coset"), (100, "coset"), (4096, "coset"), (0, "bricked"),
+                                         (100, "bricked_shifted")])
+def test_plan_matches_per_volume_kernels_and_oracle(tile, layout):
+    """The plan against each volume's own kernel and the oracle, FP32 / BF16 /
+    FP16 volumes mixed, in the linear, bricked and shifted-copy layouts (the
+    recipe's extents are even)."""
     from paper_2102_08518_b300.api import Plan
-    recipe, splines, vols, pts, outs, coefs, exts = _batch(14, seed=3)
+    recipe, splines, vols, pts, outs, coefs, exts = _batch(14, seed=3, layout=layout)
     plan = Plan(vols, pts, outs, tile=tile)
     for o in outs:
         o.fill_(float("nan"))
