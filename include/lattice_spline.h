@@ -253,13 +253,17 @@ typedef struct {
                                           with an L2 evict-last cache policy (createpolicy), so the
                                           coefficient lines outlast the point and result streams,
                                           which are loaded and stored evict-first.  0 otherwise */
+    int32_t fma2;                      /* 1: the factored coefficient transform forms pairs of monomial
+                                          coefficients with paired FP32 FMA (fma.rn.f32x2), the constant
+                                          pairs in __constant__ tables; same values (a variable only one
+                                          of the pair reads adds an exact 0 to the other).  0 otherwise */
 } ls_variant;
 
 /* ---- status ---------------------------------------------------------------- */
 const char *ls_status_str(ls_status s);
 /* Message of the last failing call on this thread ("" if none). */
 const char *ls_last_error(void);
-/* Layout version of the structs above (7: ls_variant ends with l2_keep);
+/* Layout version of the structs above (8: ls_variant ends with fma2);
  * bindings compare it with their own before any other call. */
 int32_t ls_abi_version(void);
 /* Test hooks for failure detection (host-side injection; nothing faults on the

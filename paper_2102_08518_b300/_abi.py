@@ -64,7 +64,7 @@ class VariantC(ctypes.Structure):
                 ("producers", ctypes.c_int32), ("stage", ctypes.c_int32), ("tensor", ctypes.c_int32),
                 ("tensor_kind", ctypes.c_int32), ("plain_transform", ctypes.c_int32),
                 ("wait_limit", ctypes.c_int32), ("wait_probe", ctypes.c_int32), ("prefetch", ctypes.c_int32),
-                ("l2_keep", ctypes.c_int32)]
+                ("l2_keep", ctypes.c_int32), ("fma2", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); every function declared in include/lattice_spline.h
@@ -140,7 +140,7 @@ class LsError(RuntimeError):
         self.status = status
 
 
-ABI_VERSION = 7          # ls_abi_version() of the library these struct layouts match
+ABI_VERSION = 8          # ls_abi_version() of the library these struct layouts match
 
 
 def lib():
@@ -245,7 +245,7 @@ class DescHolder:
 
 def variant(block=256, pts_per_thread=1, branchy=0, min_blocks=0, group=0, depth=0, blocks_per_sm=0,
             brick=0, pipeline=0, producers=0, stage=0, tensor=0, tensor_kind=0, plain_transform=0,
-            wait_limit=0, wait_probe=0, prefetch=0, l2_keep=0) -> VariantC:
+            wait_limit=0, wait_probe=0, prefetch=0, l2_keep=0, fma2=0) -> VariantC:
     return VariantC(block, pts_per_thread, branchy, min_blocks, group, depth, blocks_per_sm, brick, pipeline,
                     producers, stage, tensor, tensor_kind, plain_transform, wait_limit, wait_probe, prefetch,
-                    l2_keep)
+                    l2_keep, fma2)

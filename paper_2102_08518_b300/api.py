@@ -80,7 +80,7 @@ def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_b
                 depth: int = 0, pts_per_thread: int = 1, blocks_per_sm: int = 0, expansion: str = "sparse",
                 brick: int = 0, pipeline: int = 0, producers: int = 0, stage: int = 0, tensor: int = 0,
                 tensor_kind: int = 0, plain_transform: int = 0, wait_limit: int = 0, wait_probe: int = 0,
-                prefetch: int = 0, l2_keep: int = 0) -> str:
+                prefetch: int = 0, l2_keep: int = 0, fma2: int = 0) -> str:
     """The name tag of a generated kernel variant (blocks_per_sm only sizes the
     grid, so it shares the compiled kernel)."""
     return f"{name}_{dtype}" + (f"_b{block}" if block != 256 else "") + ("_br" if branchy else "") + \
@@ -90,7 +90,7 @@ def kernel_name(name: str, dtype: str, block: int = 256, branchy: int = 0, min_b
         (f"_st{stage}" if stage else "") + (("_tc" + (str(tensor) if tensor > 1 else "")) if tensor else "") + \
         ("h" if tensor and tensor_kind else "") + ("_pt" if plain_transform else "") + \
         (f"_wl{wait_limit}" if wait_limit else "") + ("_wp" if wait_probe else "") + ("_pf" if prefetch else "") + \
-        ("_lk" if l2_keep else "")
+        ("_lk" if l2_keep else "") + ("_f2" if fma2 else "")
 
 
 class Spline:
@@ -101,7 +101,7 @@ class Spline:
                  blocks_per_sm: int = 0, expansion: str = "sparse", brick: int = 0, pipeline: int = 0,
                  producers: int = 0, stage: int = 0, tensor: int = 0, tensor_kind: int = 0,
                  plain_transform: int = 0, wait_limit: int = 0, wait_probe: int = 0, prefetch: int = 0,
-                 l2_keep: int = 0, kernel_name: Optional[str] = None):
+                 l2_keep: int = 0, fma2: int = 0, kernel_name: Optional[str] = None):
         if not torch.cuda.is_available():
             raise RuntimeError("lattice spline kernels need a CUDA device")
         self.name = name
@@ -114,7 +114,7 @@ class Spline:
                                                          pts_per_thread, blocks_per_sm, expansion, brick, pipeline,
                                                          producers, stage, tensor, tensor_kind,
                                                          plain_transform, wait_limit, wait_probe, prefetch,
-                                                         l2_keep)
+                                                         l2_keep, fma2)
         self.variant = {"block": block, "branchy": branchy, "min_blocks": min_blocks, "group": group,
                         "depth": depth, "pts_per_thread": pts_per_thread, "blocks_per_sm": blocks_per_sm,
                         "expansion": expansion}
@@ -140,13 +140,15 @@ class Spline:
             self.variant["prefetch"] = 1
         if l2_keep:
             self.variant["l2_keep"] = 1
+        if fma2:
+            self.variant["fma2"] = 1
         self.kernel_name = kname
         self._desc = _abi.DescHolder(self.table, kname, expansion)
         var = _abi.variant(block=block, pts_per_thread=pts_per_thread, branchy=branchy, min_blocks=min_blocks,
                            group=group, depth=depth, blocks_per_sm=blocks_per_sm, brick=brick, pipeline=pipeline,
                            producers=producers, stage=stage, tensor=tensor, tensor_kind=tensor_kind,
                            plain_transform=plain_transform, wait_limit=wait_limit, wait_probe=wait_probe,
-                           prefetch=prefetch, l2_keep=l2_keep)
+                           prefetch=prefetch, l2_keep=l2_keep, fma2=fma2)
         h = ctypes.c_void_p()
         torch.cuda.init()
         _abi.check(_abi.lib().ls_spline_create(ctypes.byref(self._desc.desc), DTYPES[dtype], ctypes.byref(var),
@@ -565,6 +567,8 @@ def autotune(name: str, dtype: str, ext: Sequence[int], coef: torch.Tensor, pts_
     for cand in candidates:
         if cand.get("tensor") and separable:
             continue                      # tensor-product tables have no coefficient transform to offload
+        if cand.get("tensor") and LAYOUT_BRICK[layout]:
+            continue                      # on B300 the tensor-core kernels never won on bricks: linear layouts only
         if cand.get("tensor_kind") and dtype != "f32":
             continue                      # the FP16 form splits FP32 data; BF16 / FP16 data are exact in TF32
         sp = Spline(name, dtype, **cand, **({"brick": LAYOUT_BRICK[layout]} if LAYOUT_BRICK[layout] else {}))

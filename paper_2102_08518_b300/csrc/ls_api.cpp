@@ -262,6 +262,7 @@ ls_variant default_variant(const ls_variant *v)
         r.wait_probe = v->wait_probe;
         r.prefetch = v->prefetch ? 1 : 0;
         r.l2_keep = v->l2_keep ? 1 : 0;
+        r.fma2 = v->fma2 ? 1 : 0;
     }
     return r;
 }
@@ -354,7 +355,7 @@ const char *ls_status_str(ls_status s)
 
 const char *ls_last_error(void) { return g_err.c_str(); }
 
-int32_t ls_abi_version(void) { return 7; }
+int32_t ls_abi_version(void) { return 8; }
 
 void ls_debug_fail_alloc(int32_t after)
 {

@@ -54,6 +54,9 @@ struct Emitter {
     int wait_rounds = 1 << 20;        // try_wait rounds of a bounded wait (ls_mbar_wait; polls: x4)
     bool no_signal = false;           // test hook: warp-specialized producers never signal their slots
     bool l2_keep = false;             // coefficient loads carry an L2 evict-last cache policy
+    bool fma2 = false;                // factored transform in paired FP32 FMA (fma.rn.f32x2)
+    std::string ktabs;                // __constant__ tables of the paired transform's constant pairs
+    std::map<std::string, std::string> kname_of;   // table text -> its name (shared by the kernels)
     std::string fresh(const char *p) { return std::string(p) + std::to_string(tmp++); }
 };
 
@@ -926,7 +929,91 @@ void emit_factored_transform(Emitter &e, const RefRegion &r, const std::vector<i
         if (op.q >= 0) o << "    const float " << vname(op.q) << " = " << vname(op.v) << " - " << vname(op.w) << ";\n";
         e.fma += (op.p >= 0) + (op.q >= 0);
     }
+    auto mono_name = [&](size_t a) {
+        const I3 &m = r.mono[a];
+        return pe.pre + "A" + std::to_string(m[0]) + "_" + std::to_string(m[1]) + "_" + std::to_string(m[2]);
+    };
+    std::vector<int> partner(na, -1);
+    if (e.fma2) {
+        // Paired FMA (Blackwell's fma.rn.f32x2): two monomials whose sums read
+        // many of the same variables are formed together, one instruction per
+        // variable either reads, with the pair of constants from a __constant__
+        // table (a constant-bank operand: no register per pair) and the
+        // variable duplicated into both halves once.  A variable only one of
+        // the two reads adds 0 to the other (exact).  Greedy: each monomial in
+        // turn takes the free one sharing the most variables, if it shares 2+.
+        std::vector<std::vector<char>> in(na, std::vector<char>(f.rows.size(), 0));
+        std::vector<int> cnt(na, 0);
+        for (size_t a = 0; a < na; ++a)
+            for (int v : f.live)
+                if (f.rows[(size_t)v][a] != 0.0) in[a][(size_t)v] = 1, cnt[a]++;
+        std::vector<size_t> order(na);
+        for (size_t a = 0; a < na; ++a) order[a] = a;
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cnt[x] > cnt[y]; });
+        for (size_t a : order) {
+            if (partner[a] >= 0 || cnt[a] == 0) continue;
+            int best = -1, bshare = 1;
+            for (size_t b : order) {
+                if (b == a || partner[b] >= 0 || cnt[b] == 0) continue;
+                int share = 0;
+                for (int v : f.live) share += in[a][(size_t)v] && in[b][(size_t)v];
+                if (share > bshare) bshare = share, best = (int)b;
+            }
+            if (best >= 0) partner[a] = best, partner[(size_t)best] = (int)a;
+        }
+        std::vector<std::pair<float, float>> kv;
+        std::ostringstream body;
+        std::set<int> dup;
+        std::vector<std::pair<size_t, size_t>> pairs;
+        for (size_t a : order)
+            if (partner[a] >= 0 && (size_t)partner[a] > a) pairs.push_back({a, (size_t)partner[a]});
+        for (const auto &pr : pairs) {
+            std::string acc;
+            for (int v : f.live) {
+                const double ca = f.rows[(size_t)v][pr.first], cb = f.rows[(size_t)v][pr.second];
+                if (ca == 0.0 && cb == 0.0) continue;
+                if (!dup.count(v)) {
+                    body << "    const float2 " << pe.pre << "uu" << v << " = make_float2(" << vname(v) << ", "
+                         << vname(v) << ");\n";
+                    dup.insert(v);
+                }
+                const std::string k = "@K[" + std::to_string(kv.size()) + "]";
+                kv.push_back({(float)ca, (float)cb});
+                const std::string uu = pe.pre + "uu" + std::to_string(v);
+                acc = acc.empty() ? "__fmul2_rn(" + uu + ", " + k + ")" : "__ffma2_rn(" + uu + ", " + k + ", " + acc + ")";
+                e.fma += (ca != 0.0) + (cb != 0.0);     // the useful products (the kernel's FMA count)
+            }
+            const std::string pn = pe.pre + "P" + std::to_string(pr.first) + "_" + std::to_string(pr.second);
+            body << "    const float2 " << pn << " = " << acc << ";\n";
+            body << "    const float " << mono_name(pr.first) << " = " << pn << ".x;\n";
+            body << "    const float " << mono_name(pr.second) << " = " << pn << ".y;\n";
+            pe.aname[r.mono[pr.first]] = mono_name(pr.first);
+            pe.aname[r.mono[pr.second]] = mono_name(pr.second);
+        }
+        if (!kv.empty()) {
+            std::ostringstream tab;
+            for (size_t i = 0; i < kv.size(); ++i)
+                tab << (i ? ", " : "") << "{" << flit(kv[i].first) << ", " << flit(kv[i].second) << "}";
+            std::string name;
+            auto it = e.kname_of.find(tab.str());
+            if (it != e.kname_of.end()) {
+                name = it->second;
+            } else {
+                name = "ls_K2_" + std::to_string(e.kname_of.size());
+                e.kname_of[tab.str()] = name;
+                e.ktabs += "__constant__ float2 " + name + "[" + std::to_string(kv.size()) + "] = {" + tab.str() +
+                           "};\n";
+            }
+            std::string b = body.str(), out;
+            for (size_t i = 0; i < b.size(); ++i) {
+                if (b.compare(i, 2, "@K") == 0) out += name, i += 1;
+                else out += b[i];
+            }
+            o << out;
+        }
+    }
     for (size_t a = 0; a < na; ++a) {
+        if (partner[a] >= 0) continue;
         std::string acc;
         for (int v : f.live) {
             const double c = f.rows[(size_t)v][a];
@@ -935,11 +1022,9 @@ void emit_factored_transform(Emitter &e, const RefRegion &r, const std::vector<i
             e.fma++;
         }
         if (acc.empty()) continue;
-        const I3 &m = r.mono[a];
-        const std::string nm = pe.pre + "A" + std::to_string(m[0]) + "_" + std::to_string(m[1]) + "_" +
-                               std::to_string(m[2]);
+        const std::string nm = mono_name(a);
         o << "    const float " << nm << " = " << acc << ";\n";
-        pe.aname[m] = nm;
+        pe.aname[r.mono[a]] = nm;
     }
 }
 
@@ -3087,7 +3172,9 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
     if (var.wait_limit > 0) e.wait_rounds = var.wait_limit;
     e.no_signal = var.wait_probe == 1;
     e.l2_keep = var.l2_keep == 1;
+    e.fma2 = var.fma2 == 1;
     emit_prologue(e);
+    const size_t tab_at = e.o.str().size();    // the paired transform's constant tables go here
     Stencil st = union_stencil(t);
     int reach = 0;
     if (t.sep.empty()) {
@@ -3150,6 +3237,7 @@ Generated generate(const Table &t, ls_dtype dt, const ls_variant &var)
     g.info.n_reverse = (int)doffs.size();
     g.info.halo = bin_halo(t, reach);
     g.source = e.o.str();
+    g.source.insert(tab_at, e.ktabs);
     return g;
 }
 
@@ -3158,7 +3246,9 @@ Generated generate_batch(const std::vector<const Table *> &tables, const std::ve
 {
     Generated g;
     Emitter e;
+    e.fma2 = var.fma2 == 1;
     emit_prologue(e);
+    const size_t tab_at = e.o.str().size();
     for (size_t k = 0; k < tables.size(); ++k) {
         const Table &t = *tables[k];
         e.ld = loader_name(dts[k]);
@@ -3212,6 +3302,7 @@ Generated generate_batch(const std::vector<const Table *> &tables, const std::ve
     o << "    default: if (threadIdx.x == 0) atomicOr(b.status, 1u); break;\n";
     o << "    }\n  }\n}\n";
     g.source = e.o.str();
+    g.source.insert(tab_at, e.ktabs);
     return g;
 }
 

@@ -41,6 +41,11 @@ static inline int __float2int_rz(float v) { return v != v ? 0 : (int)v; }
 static inline float __ldcs(const float* p) { return *p; }
 static inline void __stcs(float* p, float v) { *p = v; }
 static inline float ls_ldk_f32(const float* p) { return *p; }
+#define __constant__
+struct float2 { float x, y; };
+static inline float2 make_float2(float a, float b) { float2 r; r.x = a; r.y = b; return r; }
+static inline float2 __ffma2_rn(float2 a, float2 b, float2 c) { return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)); }
+static inline float2 __fmul2_rn(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
 static inline unsigned short ls_ldk_u16(const unsigned short* p) { return *p; }
 
 """
@@ -78,6 +83,7 @@ class HostKernels:
         src = generated_source(name, dtype, expansion, **var)
         tag = api.kernel_name(name, dtype, expansion=expansion, **var)
         lines = [ln for ln in src.splitlines() if ln.startswith(("typedef", "struct LsEvalArgs", "#define LS_CSWAP",
+                                                                 "__constant__ float2 ls_K2_",
                                                                  "static __device__ __forceinline__ float ls_ld_pt",
                                                                  "static __device__ __forceinline__ void ls_st_out"))]
         loader = {"f32": "ls_ld_f32", "bf16": "ls_ld_bf16", "f16": "ls_ld_f16"}[dtype]

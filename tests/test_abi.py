@@ -42,7 +42,7 @@ def test_status_strings():
     L = _abi.lib()
     for code in range(9):
         assert L.ls_status_str(code)
-    assert L.ls_abi_version() == 7
+    assert L.ls_abi_version() == 8
 
 
 @pytest.mark.parametrize("name", ["tricubic", "bcc_linear", "bcc_quintic", "fcc6", "zp"])

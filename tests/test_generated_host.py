@@ -132,7 +132,10 @@ def test_factored_transform_is_cheaper():
                                       ("fcc6", {"branchy": 1, "brick": 1}), ("tricubic", {"group": 8, "depth": 2}),
                                       ("bcc_linear", {"group": 1, "depth": 2}), ("bcc_quintic", {"prefetch": 1}),
                                       ("tricubic", {"prefetch": 1}), ("zp", {"prefetch": 1}),
-                                      ("bcc_quintic", {"l2_keep": 1}), ("fcc6", {"l2_keep": 1, "prefetch": 1})])
+                                      ("bcc_quintic", {"l2_keep": 1}), ("fcc6", {"l2_keep": 1, "prefetch": 1}),
+                                      ("bcc_quintic", {"fma2": 1}), ("fcc6", {"fma2": 1}), ("bcc_quartic", {"fma2": 1}),
+                                      ("voronoi2_bcc", {"fma2": 1}), ("bcc_linear", {"fma2": 1}),
+                                      ("fcc6", {"fma2": 1, "branchy": 1})])
 def test_paper_parameter_variants(name, var):
     """The paper's group size / pipeline depth (Algorithm 2) and branchy
     sub-region selection change the generated point function; each variant
@@ -166,3 +169,16 @@ def test_reduced_precision_loaders(dtype, l2_keep):
     want = oracle.eval_sum(spec, rounded, pts.astype(np.float64))
     f = HostKernels(name, dtype, **({"l2_keep": 1} if l2_keep else {})).eval(pts, raw, ext, "coset", C)
     assert np.abs(f - want).max() <= TOL * float(np.abs(rounded).max())
+
+
+@pytest.mark.parametrize("name", ["bcc_quintic", "fcc6", "voronoi2_bcc"])
+def test_paired_fma_transform_gives_the_same_values(name):
+    """The paired-FMA transform (fma2 = 1) forms the same sums in the same
+    order (a variable only one monomial of a pair reads adds an exact 0), so
+    values and gradients equal the scalar transform's."""
+    lat, ext, C, coef, pts = _case(name, n=600)
+    a, b = HostKernels(name), HostKernels(name, fma2=1)
+    fa, ga = a.eval_grad(pts, coef.ravel(), ext, "coset", C)
+    fb, gb = b.eval_grad(pts, coef.ravel(), ext, "coset", C)
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+

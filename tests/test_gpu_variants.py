@@ -99,6 +99,15 @@ def test_parameter_sweep_variants(name, var):
     _check(name, var)
 
 
+@pytest.mark.parametrize("var", [dict(fma2=1), dict(fma2=1, block=512), dict(fma2=1, branchy=1)], ids=str)
+@pytest.mark.parametrize("name", ["bcc_quintic", "fcc6", "voronoi2_bcc"])
+def test_paired_fma_transform(name, var):
+    """The coefficient transform in paired FP32 FMA with constant-bank pairs."""
+    if var.get("branchy") and name == "bcc_quintic":
+        pytest.skip("one reference sub-region")
+    _check(name, var)
+
+
 @pytest.mark.parametrize("name", ["bcc_quintic", "fcc6", "tricubic", "bcc_linear"])
 def test_plain_transform(name):
     """The coefficient transform as direct sums over the sites (the factored
