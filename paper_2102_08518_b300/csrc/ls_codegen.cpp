@@ -205,9 +205,50 @@ void emit_classify(Emitter &e, const Table &t, const char *kshift = nullptr)
 {
     auto &o = e.o;
     const int D = t.dim;
+    // the two 3D lattices stored as cosets of 2Z^3 whose nearest site has a
+    // closed form: BCC = 2Z^3 u (2Z^3 + (1,1,1)), FCC = D3 (integer points
+    // with an even coordinate sum)
+    auto has_cosets = [&](std::vector<I3> want) {
+        if (D != 3 || t.scale != 2 || t.cosets.size() != want.size()) return false;
+        for (const auto &c : t.cosets) {
+            auto it = std::find(want.begin(), want.end(), I3{c[0], c[1], c[2]});
+            if (it == want.end()) return false;
+            want.erase(it);
+        }
+        return true;
+    };
+    const bool bcc = t.roe != LS_ROE_PARALLELEPIPED && has_cosets({I3{0, 0, 0}, I3{1, 1, 1}});
+    const bool fcc = t.roe != LS_ROE_PARALLELEPIPED &&
+                     has_cosets({I3{0, 0, 0}, I3{1, 1, 0}, I3{1, 0, 1}, I3{0, 1, 1}});
     if (t.roe == LS_ROE_PARALLELEPIPED) {
         for (int i = 0; i < D; ++i)
             o << "    const float kf" << i << " = floorf(x" << i << ");\n";
+    } else if (bcc) {
+        // nearest even site c; the nearest odd site is c + sign(x - c) per axis,
+        // and it is nearer iff sum |x - c| > 3/2 (|x - c'|^2 - |x - c|^2 =
+        // 3 - 2 sum |x - c|)
+        for (int i = 0; i < 3; ++i) {
+            o << "    const float ce" << i << " = 2.0f * rintf(x" << i << " * 0.5f);\n";
+            o << "    const float de" << i << " = x" << i << " - ce" << i << ";\n";
+        }
+        o << "    const bool odd_ = fabsf(de0) + fabsf(de1) + fabsf(de2) > 1.5f;\n";
+        for (int i = 0; i < 3; ++i)
+            o << "    const float kf" << i << " = odd_ ? ce" << i << " + (de" << i << " < 0.0f ? -1.0f : 1.0f) : ce"
+              << i << ";\n";
+    } else if (fcc) {
+        // D3: round every coordinate; if the sum of the rounded coordinates is
+        // odd, move the coordinate with the largest rounding error to the other
+        // neighbouring integer
+        for (int i = 0; i < 3; ++i) {
+            o << "    const float rr" << i << " = rintf(x" << i << ");\n";
+            o << "    const float ee" << i << " = x" << i << " - rr" << i << ";\n";
+        }
+        o << "    const bool oddsum_ = ((__float2int_rn(rr0) + __float2int_rn(rr1) + __float2int_rn(rr2)) & 1) != 0;\n";
+        o << "    const float ae0_ = fabsf(ee0), ae1_ = fabsf(ee1), ae2_ = fabsf(ee2);\n";
+        o << "    const int mx_ = (ae0_ >= ae1_ && ae0_ >= ae2_) ? 0 : (ae1_ >= ae2_ ? 1 : 2);\n";
+        for (int i = 0; i < 3; ++i)
+            o << "    const float kf" << i << " = (oddsum_ && mx_ == " << i << ") ? rr" << i << " + (ee" << i
+              << " < 0.0f ? -1.0f : 1.0f) : rr" << i << ";\n";
     } else {
         for (size_t j = 0; j < t.cosets.size(); ++j) {
             for (int i = 0; i < D; ++i) {

@@ -38,6 +38,7 @@ static inline float __uint_as_float(unsigned v) { float f; std::memcpy(&f, &v, 4
 static inline int __float_as_int(float v) { int i; std::memcpy(&i, &v, 4); return i; }
 static inline unsigned __float_as_uint(float v) { unsigned i; std::memcpy(&i, &v, 4); return i; }
 static inline int __float2int_rz(float v) { return v != v ? 0 : (int)v; }
+static inline int __float2int_rn(float v) { return v != v ? 0 : (int)rintf(v); }
 static inline float __ldcs(const float* p) { return *p; }
 static inline void __stcs(float* p, float v) { *p = v; }
 static inline float ls_ldk_f32(const float* p) { return *p; }

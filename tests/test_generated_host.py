@@ -182,3 +182,28 @@ def test_paired_fma_transform_gives_the_same_values(name):
     fb, gb = b.eval_grad(pts, coef.ravel(), ext, "coset", C)
     assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
 
+
+
+@pytest.mark.parametrize("name", ["bcc_linear", "bcc_quintic", "fcc6", "voronoi2_bcc", "voronoi2_fcc"])
+def test_region_of_evaluation_ties(name):
+    """The closed-form nearest site (BCC: the nearer of the even and odd
+    candidates; FCC: rounding with the parity fix of D3) on points where
+    several sites are nearest: half-integers, the BCC boundary sum |x - c| =
+    3/2, integer points with an odd coordinate sum (FCC), lattice sites; the
+    value is the oracle's whichever of the tied sites is taken."""
+    lat, ext, C, coef, _ = _case(name, n=10)
+    lo, hi = workloads.bounding_box(lat, ext)
+    rng = np.random.default_rng(7)
+    c = rng.integers(2, 2 * min(ext) - 3, (400, 3)).astype(np.float64)
+    p = c.copy()
+    p[:80] += 0.5                                             # half-integers
+    d = rng.uniform(0.0, 1.0, (80, 2))
+    p[80:160] = 2 * np.round(c[80:160] / 2) + np.stack([d[:, 0], d[:, 1], 1.5 - d[:, 0] - d[:, 1]], 1)
+    p[160:240] = np.round(c[160:240])                         # integer points (odd sums among them)
+    p[240:320] = 2 * np.round(c[240:320] / 2)                 # even lattice sites
+    p[320:] += rng.choice([-0.5, 0.5], (80, 3))
+    pts = np.clip(p, lo, hi).astype(np.float32)
+    spec = SPEC[name]().with_extent(ext)
+    want = oracle.eval_sum(spec, coef.astype(np.float64).ravel(), pts.astype(np.float64))
+    f = HostKernels(name).eval(pts, coef.ravel(), ext, "coset", C)
+    assert np.abs(f - want).max() <= TOL * float(np.abs(coef).max())
