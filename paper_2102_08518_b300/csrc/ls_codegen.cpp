@@ -979,10 +979,10 @@ void emit_factored_transform(Emitter &e, const RefRegion &r, const std::vector<i
         // Paired FMA (Blackwell's fma.rn.f32x2): two monomials whose sums read
         // many of the same variables are formed together, one instruction per
         // variable either reads, with the pair of constants from a __constant__
-        // table (a constant-bank operand: no register per pair) and the
-        // variable duplicated into both halves once.  A variable only one of
-        // the two reads adds 0 to the other (exact).  Greedy: each monomial in
-        // turn takes the free one sharing the most variables, if it shares 2+.
+        // table and the variable duplicated into both halves once.  A variable
+        // only one of the two reads adds 0 to the other (exact).  Greedy: each
+        // monomial in turn takes the free one sharing the most variables, if it
+        // shares 2+.  Measured slower than the scalar sums on B300 (a variant).
         std::vector<std::vector<char>> in(na, std::vector<char>(f.rows.size(), 0));
         std::vector<int> cnt(na, 0);
         for (size_t a = 0; a < na; ++a)
