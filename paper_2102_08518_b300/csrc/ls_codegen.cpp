@@ -656,7 +656,10 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             for (int i = 0; i < D; ++i) {
                 // component of R^T e on Cartesian axis i: e[ri_i], negated if axis i is negative
                 if (fold)
-                    o << "      const int ce" << m << "_" << i << " = (" << m << " >> ri" << i << ") & 1;\n";
+                    o << "      const int ce" << m << "_" << i << " = "
+                      << (m == 0 ? std::string("0") : m == (1 << D) - 1 ? std::string("1")
+                                                       : "(" + std::to_string(m) + " >> ri" + std::to_string(i) + ") & 1")
+                      << ";\n";
                 else
                     o << "      const int ce" << m << "_" << i << " = " << ((m >> i) & 1) << ";\n";
                 o << "      const int v" << m << "_" << i << " = cb" << i << " + "
@@ -668,7 +671,7 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             o << "      const int par" << m << " = (v" << m << "_0 & 1)";
             for (int i = 1; i < D; ++i) o << " | ((v" << m << "_" << i << " & 1) << " << i << ")";
             o << ";\n";
-            o << "      const int cid" << m << " = (int)((" << lut << "ull >> (4 * par" << m << ")) & 15ull);\n";
+            o << "      const int cid" << m << " = (int)((" << (lut & 0xFFFFFFFFull) << "u >> (4 * par" << m << ")) & 15u);\n";
             auto q = [&](int i) {
                 return i < D ? "qh" + std::to_string(i) + " + (v" + std::to_string(m) + "_" + std::to_string(i) + " >> 1)"
                              : std::string("0");
@@ -740,7 +743,7 @@ void emit_gathers(Emitter &e, const Table &t, const std::vector<I3> &sites, int 
             const unsigned long long lut = coset_lut(t);
             o << "        const int par = (n0 & 1)";
             for (int i = 1; i < D; ++i) o << " | ((n" << i << " & 1) << " << i << ")";
-            o << ";\n        const int cid = (int)((" << lut << "ull >> (4 * par)) & 15ull);\n";
+            o << ";\n        const int cid = (int)((" << (lut & 0xFFFFFFFFull) << "u >> (4 * par)) & 15u);\n";
             if (e.brick) {
                 o << "        const int adr = " << (e.brick_shift ? "cbase + cid" : "cid");
                 for (int i = 0; i < D; ++i) {
